@@ -1,0 +1,369 @@
+"""CPU oracle for mixed-precision Paterson--Stockmeyer (arXiv 2312.17396).
+
+TEST INFRASTRUCTURE ONLY.  Only the test-suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  It shares no code with the
+CUDA library (``paper_2312_17396_gb300``) and never imports it.
+
+Contents
+--------
+* ``mpps_oracle.c`` (built here with gcc into ``_liboracle.so``): Algorithm 2.1 literally
+  in double-double and plain double, Horner, explicit powers, scaling and squaring
+  (eq. (3.6)), column-block application p(X)^k V, the adjoint as the defining double sum
+  of the Frechet derivative, and the 1-norm.
+* Coefficient sequences as exact rationals (``fractions.Fraction``), converted to
+  double-double: Taylor exp b_i = 1/i! (Section 3), the [q/q] Pade numerator and
+  denominator of exp (Section 4.1; the Ward example of Section 2 prints the first eight
+  numerator coefficients for q = 13), and the Taylor cosine as a polynomial in X^2
+  (Section 4.2).
+* ``plan``: the precision rule, written step by step from eq. (2.8) and the
+  ``fix_params`` branch of Algorithm 3.1 / Algorithm 4.1, with the format ladder of
+  Section 4.1.1 generalised to the GPU formats.
+* ``cost_ratio``: eq. (3.8).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import platform
+import subprocess
+from fractions import Fraction
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mpps_oracle.c")
+_LIB = os.path.join(_HERE, "_liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP, no fast-math, no FP contraction)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    flags = ["-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-std=c11"]
+    if platform.machine() in ("x86_64", "AMD64"):
+        flags.append("-mfma")  # hardware FMA instead of the libm call; same correctly rounded result
+    tmp = _LIB + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", *flags, _SRC, "-o", tmp, "-lm"])
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        dp = ctypes.POINTER(ctypes.c_double)
+        lp = ctypes.POINTER(ctypes.c_long)
+        i = ctypes.c_int
+        L.orc_ps_dd.argtypes = [dp, dp, i, i, dp, i, dp, dp, lp]
+        L.orc_horner_dd.argtypes = [dp, dp, i, dp, i, dp, dp, lp]
+        L.orc_powers_dd.argtypes = [dp, dp, i, dp, i, dp, dp]
+        L.orc_expm_ss_dd.argtypes = [dp, dp, i, i, dp, i, i, dp, dp]
+        L.orc_ps_apply_dd.argtypes = [dp, dp, i, dp, i, dp, i, ctypes.c_long, dp, dp]
+        L.orc_adjoint_dd.argtypes = [dp, dp, i, dp, dp, i, dp, dp]
+        L.orc_matmul_dd.argtypes = [dp, dp, dp, dp, i, dp, dp]
+        L.orc_ps_d.argtypes = [dp, i, i, dp, i, dp, lp]
+        L.orc_expm_ss_d.argtypes = [dp, i, i, dp, i, i, dp]
+        L.orc_norm1.argtypes = [dp, i, i]
+        L.orc_norm1.restype = ctypes.c_double
+        L.orc_num_threads.restype = ctypes.c_int
+        for name in ("orc_ps_dd", "orc_horner_dd", "orc_powers_dd", "orc_expm_ss_dd",
+                     "orc_ps_apply_dd", "orc_adjoint_dd", "orc_matmul_dd", "orc_ps_d",
+                     "orc_expm_ss_d"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if a is not None else None
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ---------------------------------------------------------------------------------
+# coefficient sequences as exact rationals, then double-double
+# ---------------------------------------------------------------------------------
+def taylor_exp_rational(m: int):
+    """b_i = 1/i!, i = 0..m (Section 3)."""
+    return [Fraction(1, math.factorial(i)) for i in range(m + 1)]
+
+
+def pade_exp_num_rational(q: int):
+    """Numerator of the [q/q] Pade approximant to exp:
+    c_j = (2q-j)! q! / ((2q)! j! (q-j)!), j = 0..q (Section 4.1).  For q = 13 the first
+    eight values are the ones printed in the Ward example of Section 2."""
+    f = math.factorial
+    return [Fraction(f(2 * q - j) * f(q), f(2 * q) * f(j) * f(q - j)) for j in range(q + 1)]
+
+
+def pade_exp_den_rational(q: int):
+    """Denominator q_qq(X) = p_qq(-X): coefficients (-1)^j c_j (Section 4.1)."""
+    return [c * (-1) ** j for j, c in enumerate(pade_exp_num_rational(q))]
+
+
+def cos_taylor_rational(m: int):
+    """Taylor cosine as a polynomial in B = X^2: sum_{k=0}^m (-1)^k B^k / (2k)!
+    (Section 4.2 evaluates c_m(X^2) by PS)."""
+    return [Fraction((-1) ** k, math.factorial(2 * k)) for k in range(m + 1)]
+
+
+def to_dd(coefs):
+    """Exact rationals -> (hi, lo) double-double arrays (hi = nearest double, lo = nearest
+    double of the remainder)."""
+    hi = np.array([float(c) for c in coefs], dtype=np.float64)
+    lo = np.array([float(Fraction(c) - Fraction(float(h))) for c, h in zip(coefs, hi)],
+                  dtype=np.float64)
+    return hi, lo
+
+
+def _coef_arrays(coefs):
+    if isinstance(coefs, tuple) and len(coefs) == 2:
+        return _f64(coefs[0]), _f64(coefs[1])
+    coefs = list(coefs)
+    if coefs and isinstance(coefs[0], Fraction):
+        return to_dd(coefs)
+    hi = _f64(coefs)
+    return hi, np.zeros_like(hi)
+
+
+def ceil_sqrt(m: int) -> int:
+    """s = ceil(sqrt(m)) computed in integers (Algorithm 2.1, first line)."""
+    if m <= 1:
+        return 1
+    s = math.isqrt(m)
+    return s if s * s == m else s + 1
+
+
+# ---------------------------------------------------------------------------------
+# wrappers
+# ---------------------------------------------------------------------------------
+def ps_dd(coefs, X, s: int = 0):
+    """Algorithm 2.1 in double-double.  Returns (P_hi, P_lo, products)."""
+    ch, cl = _coef_arrays(coefs)
+    m = len(ch) - 1
+    X = _f64(X)
+    n = X.shape[0]
+    ph = np.empty((n, n)); pl = np.empty((n, n))
+    cnt = ctypes.c_long(0)
+    rc = lib().orc_ps_dd(_p(ch), _p(cl), m, int(s), _p(X), n, _p(ph), _p(pl), ctypes.byref(cnt))
+    if rc != 0:
+        raise ValueError("orc_ps_dd: bad arguments")
+    return ph, pl, cnt.value
+
+
+def horner_dd(coefs, X):
+    ch, cl = _coef_arrays(coefs)
+    m = len(ch) - 1
+    X = _f64(X); n = X.shape[0]
+    ph = np.empty((n, n)); pl = np.empty((n, n)); cnt = ctypes.c_long(0)
+    if lib().orc_horner_dd(_p(ch), _p(cl), m, _p(X), n, _p(ph), _p(pl), ctypes.byref(cnt)):
+        raise ValueError("orc_horner_dd: bad arguments")
+    return ph, pl, cnt.value
+
+
+def powers_dd(coefs, X):
+    ch, cl = _coef_arrays(coefs)
+    m = len(ch) - 1
+    X = _f64(X); n = X.shape[0]
+    ph = np.empty((n, n)); pl = np.empty((n, n))
+    if lib().orc_powers_dd(_p(ch), _p(cl), m, _p(X), n, _p(ph), _p(pl)):
+        raise ValueError("orc_powers_dd: bad arguments")
+    return ph, pl
+
+
+def expm_ss_dd(A, m: int, sigma: int, s: int = 0, coefs=None):
+    """p_m(2^-sigma A)^(2^sigma) in double-double, p_m the degree-m Taylor polynomial."""
+    ch, cl = _coef_arrays(coefs if coefs is not None else taylor_exp_rational(m))
+    m = len(ch) - 1
+    A = _f64(A); n = A.shape[0]
+    eh = np.empty((n, n)); el = np.empty((n, n))
+    if lib().orc_expm_ss_dd(_p(ch), _p(cl), m, int(s), _p(A), n, int(sigma), _p(eh), _p(el)):
+        raise ValueError("orc_expm_ss_dd: bad arguments")
+    return eh, el
+
+
+def ps_apply_dd(coefs, X, V, reps: int = 1):
+    """p(X)^reps V by Horner on the column block V (n x k)."""
+    ch, cl = _coef_arrays(coefs)
+    m = len(ch) - 1
+    X = _f64(X); n = X.shape[0]
+    V = _f64(V).reshape(n, -1); k = V.shape[1]
+    wh = np.empty((n, k)); wl = np.empty((n, k))
+    if lib().orc_ps_apply_dd(_p(ch), _p(cl), m, _p(X), n, _p(V), k, int(reps), _p(wh), _p(wl)):
+        raise ValueError("orc_ps_apply_dd: bad arguments")
+    return wh, wl
+
+
+def adjoint_dd(coefs, A, G):
+    """Gradient of <G, p(A)> with respect to A: sum_k c_k sum_{j<k} (A^T)^j G (A^T)^(k-1-j)."""
+    ch, cl = _coef_arrays(coefs)
+    m = len(ch) - 1
+    A = _f64(A); G = _f64(G); n = A.shape[0]
+    dh = np.empty((n, n)); dl = np.empty((n, n))
+    if lib().orc_adjoint_dd(_p(ch), _p(cl), m, _p(A), _p(G), n, _p(dh), _p(dl)):
+        raise ValueError("orc_adjoint_dd: bad arguments")
+    return dh, dl
+
+
+def matmul_dd(Ah, Al, Bh, Bl):
+    Ah = _f64(Ah); Bh = _f64(Bh); n = Ah.shape[0]
+    Al = _f64(Al) if Al is not None else np.zeros_like(Ah)
+    Bl = _f64(Bl) if Bl is not None else np.zeros_like(Bh)
+    ch = np.empty((n, n)); cl = np.empty((n, n))
+    lib().orc_matmul_dd(_p(Ah), _p(Al), _p(Bh), _p(Bl), n, _p(ch), _p(cl))
+    return ch, cl
+
+
+def ps_d(coefs, X, s: int = 0):
+    """Algorithm 2.1 in plain double (the timed CPU baseline)."""
+    c = _f64([float(x) for x in coefs]) if not isinstance(coefs, np.ndarray) else _f64(coefs)
+    m = len(c) - 1
+    X = _f64(X); n = X.shape[0]
+    P = np.empty((n, n)); cnt = ctypes.c_long(0)
+    if lib().orc_ps_d(_p(c), m, int(s), _p(X), n, _p(P), ctypes.byref(cnt)):
+        raise ValueError("orc_ps_d: bad arguments")
+    return P, cnt.value
+
+
+def expm_ss_d(A, m: int, sigma: int, s: int = 0):
+    c = np.array([float(x) for x in taylor_exp_rational(m)])
+    A = _f64(A); n = A.shape[0]
+    E = np.empty((n, n))
+    if lib().orc_expm_ss_d(_p(c), m, int(s), _p(A), n, int(sigma), _p(E)):
+        raise ValueError("orc_expm_ss_d: bad arguments")
+    return E
+
+
+def norm1(M) -> float:
+    M = _f64(M)
+    M2 = M.reshape(M.shape[0], -1)
+    return float(lib().orc_norm1(_p(M2), M2.shape[0], M2.shape[1]))
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+def rel_err_1norm(P_hat, ref_hi, ref_lo=None) -> float:
+    """eps = ||P_hat - P||_1 / ||P||_1 (Section 3.4), P given as double-double."""
+    D = (np.asarray(P_hat, dtype=np.float64) - ref_hi)
+    if ref_lo is not None:
+        D = D - ref_lo
+    return norm1(D) / norm1(ref_hi)
+
+
+def sigma_for(A) -> int:
+    """Number of squarings so that ||2^-sigma A||_1 <= 1: sigma = max(0, ceil(log2 ||A||_1))."""
+    nrm = norm1(A)
+    if nrm <= 1.0:
+        return 0
+    m, e = math.frexp(nrm)          # nrm = m * 2^e, 0.5 <= m < 1
+    return e - 1 if m == 0.5 else e
+
+
+# ---------------------------------------------------------------------------------
+# block norms of eq. (1.1) in double-double (inputs to the precision rule)
+# ---------------------------------------------------------------------------------
+def block_norms_dd(coefs, X, s: int = 0):
+    """||B_i||_1 for i = 0..r and ||X^s||_1, from double-double powers of X.
+    B_i = sum_{j<s} b_{si+j} X^j (i < r), B_r = sum_{j<=m-sr} b_{sr+j} X^j (eq. (1.1))."""
+    ch, cl = _coef_arrays(coefs)
+    m = len(ch) - 1
+    X = _f64(X); n = X.shape[0]
+    s = s if s > 0 else ceil_sqrt(m)
+    r = m // s
+    pw = [np.eye(n)]
+    cur_h, cur_l = np.eye(n), np.zeros((n, n))
+    for _ in range(s):
+        cur_h, cur_l = matmul_dd(cur_h, cur_l, X, None)
+        pw.append(cur_h + cur_l)
+    norms = []
+    for i in range(r + 1):
+        top = s - 1 if i < r else m - s * r
+        B = np.zeros((n, n))
+        for j in range(top + 1):
+            B = B + float(ch[s * i + j]) * pw[j]
+        norms.append(norm1(B))
+    return norms, norm1(pw[s])
+
+
+# ---------------------------------------------------------------------------------
+# precision rule (eq. (2.8); Algorithm 3.1 fix_params branch; Algorithm 4.1)
+# ---------------------------------------------------------------------------------
+FMT_FP64, FMT_BF16X3, FMT_TF32, FMT_BF16, FMT_FP8 = 0, 1, 2, 3, 4
+FMT_NONE = -1
+# unit roundoff of each format's inputs (Section 4.1.1 uses bf16 u = 2^-8 ~ 3.9e-3)
+U_FMT = {FMT_FP64: 2.0 ** -53, FMT_BF16X3: 2.0 ** -16, FMT_TF32: 2.0 ** -11,
+         FMT_BF16: 2.0 ** -8, FMT_FP8: 2.0 ** -4}
+FP32_ACC = 2.0 ** -24
+MODE_FIXED, MODE_PAPER, MODE_NS = 0, 1, 2
+
+
+def plan(m: int, n: int, norms, normY: float, mode: int = MODE_PAPER, tol: float = 2.0 ** -53,
+         delta: float = 10.0, s: int = 0, formats: int = 0x1F, floor_steps: int = 2):
+    """Per-step precisions for the Horner products P_i Y, i = r..1.
+
+    1. s = ceil(sqrt(m)) unless given; r = floor(m/s).
+    2. u_i = ||B_0|| tol / (||B_i|| ||Y||^i): eq. (2.8) with nu = 1 (the closed form that
+       Algorithm 3.1 uses in its variable-s branch); y^i by repeated multiplication.
+       The rule never asks for more than the working precision: u_i = max(tol, u_i).
+       A zero block or zero Y contributes nothing: u_i = +inf.
+    3. nu = min{i : u_i >= delta * tol} (r+1 if none); u_1..u_{nu-1} = tol.
+    4. format_i = the cheapest allowed format F with U_FMT[F] <= u_i and, for formats that
+       accumulate in FP32, n * 2^-24 <= u_i (Section 4.1.1's rule max{u* <= u_i}, with the
+       accumulation error of the tensor cores added).  FP64 is always allowed.
+    5. mode NS: steps i <= floor_steps stay FP64.  mode FIXED: every step FP64.
+    6. When s divides m, B_r = b_m I and step r is a scalar multiple of Y: no product
+       (format NONE).
+    Returns dict(s, r, nu, u (list, index 1..r), fmt (index 1..r), fold).
+    """
+    if m <= 0:
+        return dict(s=1, r=0, nu=1, u=[None], fmt=[None], fold=False)
+    s = s if s > 0 else ceil_sqrt(m)
+    r = m // s
+    fold = (m % s == 0)
+    eta0 = float(norms[0])
+    u = [None] * (r + 1)
+    for i in range(1, r + 1):
+        eta = float(norms[i])
+        yi = 1.0
+        for _ in range(i):
+            yi = yi * float(normY)
+        den = eta * yi
+        ui = math.inf if den == 0.0 else (eta0 * tol) / den
+        u[i] = max(tol, ui)
+    nu = r + 1
+    for i in range(1, r + 1):
+        if u[i] >= delta * tol:
+            nu = i
+            break
+    for i in range(1, nu):
+        u[i] = tol
+    order = [FMT_FP8, FMT_BF16, FMT_TF32, FMT_BF16X3]
+    fmt = [None] * (r + 1)
+    for i in range(1, r + 1):
+        f = FMT_FP64
+        if mode != MODE_FIXED and not (mode == MODE_NS and i <= floor_steps):
+            for F in order:
+                if not (formats >> F) & 1:
+                    continue
+                if U_FMT[F] <= u[i] and n * FP32_ACC <= u[i]:
+                    f = F
+                    break
+        fmt[i] = f
+    if fold:
+        fmt[r] = FMT_NONE
+    return dict(s=s, r=r, nu=nu, u=u, fmt=fmt, fold=fold)
+
+
+def cost_ratio(s: int, r: int, digits_wp: float, d):
+    """Eq. (3.8) read as a ratio of digit-weighted product counts:
+    C_r = ((s-1) D + sum_i d_i) / ((s+r-1) D), D = digits of the working precision.
+    (The printed formula writes log10 u for D; Table 1's column is 1 - C_r.)"""
+    return ((s - 1) * digits_wp + sum(d)) / ((s + r - 1) * digits_wp)

@@ -1,0 +1,450 @@
+"""Pins for the CPU oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: exact rational
+arithmetic, closed forms, special cases that reduce to a textbook or library routine,
+printed values of the paper, and invariants.  All run on the CPU.
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from conftest import GOLDEN
+
+RNG = np.random.default_rng(20231217)
+
+
+# --------------------------------------------------------------------------------
+# helpers: exact rational matrix algebra (small n only)
+# --------------------------------------------------------------------------------
+def fr_matmul(A, B):
+    n = len(A)
+    return [[sum((A[i][k] * B[k][j] for k in range(n)), Fraction(0)) for j in range(n)]
+            for i in range(n)]
+
+
+def fr_poly(coefs, X):
+    """sum_k c_k X^k, the plain definition, in exact rationals."""
+    n = len(X)
+    I = [[Fraction(int(i == j)) for j in range(n)] for i in range(n)]
+    P = [[Fraction(0)] * n for _ in range(n)]
+    K = I
+    for k, c in enumerate(coefs):
+        if k > 0:
+            K = fr_matmul(K, X)
+        for i in range(n):
+            for j in range(n):
+                P[i][j] += c * K[i][j]
+    return P
+
+
+def dyadic_matrix(n, denom=8, lo=-6, hi=7, rng=RNG):
+    ints = rng.integers(lo, hi, size=(n, n))
+    return ints / denom, [[Fraction(int(v), denom) for v in row] for row in ints]
+
+
+def max_rel_exact(ph, pl, exact):
+    """max_ij |(hi + lo) - exact| / max_ij |exact|, in exact arithmetic."""
+    n = len(exact)
+    scale = max(abs(v) for row in exact for v in row)
+    err = max(abs(Fraction(float(ph[i, j])) + Fraction(float(pl[i, j])) - exact[i][j])
+              for i in range(n) for j in range(n))
+    return float(err / scale) if scale else float(err)
+
+
+# --------------------------------------------------------------------------------
+# 1. the double-double PS core against exact rational arithmetic
+# --------------------------------------------------------------------------------
+@pytest.mark.parametrize("n,m", [(2, 4), (3, 9), (4, 16), (3, 13)])
+def test_ps_dd_matches_exact_rationals(n, m):
+    Xf, Xq = dyadic_matrix(n)
+    Xf /= 4.0
+    Xq = [[v / 4 for v in row] for row in Xq]
+    coefs = oracle.taylor_exp_rational(m)
+    exact = fr_poly(coefs, Xq)
+    ph, pl, _ = oracle.ps_dd(coefs, Xf)
+    assert max_rel_exact(ph, pl, exact) < 1e-30
+
+
+def test_ps_dd_general_coefficients_exact():
+    # signed, non-decaying coefficients: catches sign and index slips in B_i assembly
+    coefs = [Fraction(k * (-1) ** k + 1, k + 2) for k in range(12)]
+    Xf, Xq = dyadic_matrix(4)
+    exact = fr_poly(coefs, Xq)
+    for s in (1, 2, 3, 4, 5, 11, 12):
+        ph, pl, _ = oracle.ps_dd(coefs, Xf, s=s)
+        assert max_rel_exact(ph, pl, exact) < 1e-30, s
+
+
+def test_planted_mistake_is_caught():
+    """A plausible oracle mistake (one coefficient dropped) must fail the exact pin."""
+    coefs = oracle.taylor_exp_rational(9)
+    Xf, Xq = dyadic_matrix(3)
+    exact = fr_poly(coefs, Xq)
+    wrong = list(coefs)
+    wrong[5] = Fraction(0)
+    ph, pl, _ = oracle.ps_dd(wrong, Xf)
+    assert max_rel_exact(ph, pl, exact) > 1e-6
+
+
+# --------------------------------------------------------------------------------
+# 2. PS = Horner = explicit powers (eq. (1.1) with s = 1, ceil(sqrt(m)), m)
+# --------------------------------------------------------------------------------
+@pytest.mark.parametrize("m", [1, 2, 7, 16, 30])
+def test_schemes_agree(m):
+    n = 9
+    X = RNG.standard_normal((n, n))
+    X /= oracle.norm1(X)
+    c = oracle.taylor_exp_rational(m)
+    ref_h, ref_l = oracle.powers_dd(c, X)
+    scale = oracle.norm1(ref_h)
+    for s in sorted({1, oracle.ceil_sqrt(m), m}):
+        ph, pl, _ = oracle.ps_dd(c, X, s=s)
+        assert oracle.norm1((ph - ref_h) + (pl - ref_l)) / scale < 1e-29
+    hh, hl, cnt = oracle.horner_dd(c, X)
+    assert cnt == m
+    assert oracle.norm1((hh - ref_h) + (hl - ref_l)) / scale < 1e-29
+
+
+# --------------------------------------------------------------------------------
+# 3. multiplication count of Algorithm 2.1: s - 1 + r (Section 3.4)
+# --------------------------------------------------------------------------------
+@pytest.mark.parametrize("m,s,expected", [(16, 4, 7), (30, 6, 10), (12, 4, 6), (18, 5, 7),
+                                          (24, 5, 8), (13, 4, 6), (42, 7, 12), (182, 14, 26)])
+def test_multiplication_count(m, s, expected):
+    assert oracle.ceil_sqrt(m) == s
+    X = np.diag(np.linspace(0.1, 0.2, 3))
+    _, _, cnt = oracle.ps_dd(oracle.taylor_exp_rational(m), X)
+    assert cnt == expected == s - 1 + m // s
+
+
+# --------------------------------------------------------------------------------
+# 4. nilpotent Jordan block and lambda*I + J (closed forms; X^s = 0 gives p = B_0)
+# --------------------------------------------------------------------------------
+@pytest.mark.parametrize("m", [5, 16, 30])
+def test_nilpotent_jordan_exact(m):
+    n = 8
+    J = np.diag(np.ones(n - 1), 1)
+    c = oracle.taylor_exp_rational(m)
+    chi, clo = oracle.to_dd(c)
+    ph, pl, _ = oracle.ps_dd(c, J)
+    for i in range(n):
+        for j in range(n):
+            k = j - i
+            if 0 <= k <= m:
+                assert ph[i, j] == chi[k] and pl[i, j] == clo[k], (i, j)
+            else:
+                assert ph[i, j] == 0.0 and pl[i, j] == 0.0
+
+
+def test_shifted_jordan_derivatives():
+    n, m, lam = 6, 12, Fraction(1, 2)
+    X = 0.5 * np.eye(n) + np.diag(np.ones(n - 1), 1)
+    c = [Fraction(k + 1, 3 ** k) * (-1) ** (k // 2) for k in range(m + 1)]
+    ph, pl, _ = oracle.ps_dd(c, X)
+    for k in range(n):
+        # p^{(k)}(lam)/k! = sum_j c_j binom(j, k) lam^(j-k)
+        exact = sum((cj * math.comb(j, k) * lam ** (j - k) for j, cj in enumerate(c) if j >= k),
+                    Fraction(0))
+        got = Fraction(float(ph[0, k])) + Fraction(float(pl[0, k]))
+        assert abs(float((got - exact) / exact)) < 1e-29
+
+
+def test_nilpotent_strictly_upper_triangular():
+    """100*triu(randn(n),1) (Section 3.4.3 class B): X^n = 0, p(X) = sum_{k<n} b_k X^k."""
+    n = 5
+    X = 100 * np.triu(RNG.standard_normal((n, n)), 1)
+    X = np.round(X * 4) / 4  # dyadic entries: exact rationals available
+    Xq = [[Fraction(float(v)) for v in row] for row in X]
+    c = oracle.taylor_exp_rational(20)
+    exact = fr_poly(c[:n], Xq)       # higher powers vanish
+    ph, pl, _ = oracle.ps_dd(c, X)
+    assert max_rel_exact(ph, pl, exact) < 1e-30
+
+
+# --------------------------------------------------------------------------------
+# 5. diagonal matrices: p(D) = diag(p(d_i))
+# --------------------------------------------------------------------------------
+def test_diagonal():
+    d = [Fraction(k, 8) for k in (-7, -3, 0, 1, 5, 9)]
+    c = oracle.pade_exp_num_rational(13)
+    ph, pl, _ = oracle.ps_dd(c, np.diag([float(x) for x in d]))
+    for i, di in enumerate(d):
+        exact = sum((cj * di ** j for j, cj in enumerate(c)), Fraction(0))
+        got = Fraction(float(ph[i, i])) + Fraction(float(pl[i, i]))
+        assert abs(float(got - exact)) <= 1e-30 * max(1.0, abs(float(exact)))
+    off = ph - np.diag(np.diag(ph))
+    assert np.all(off == 0.0)
+
+
+# --------------------------------------------------------------------------------
+# 6. exp via scaling and squaring: rotations, group property, library routines
+# --------------------------------------------------------------------------------
+@pytest.mark.parametrize("theta", [0.3, 1.0, 2.5, 7.0])
+def test_rotation_generator(theta):
+    A = np.array([[0.0, -theta], [theta, 0.0]])
+    sigma = oracle.sigma_for(A)
+    eh, el = oracle.expm_ss_dd(A, 30, sigma)
+    E = eh + el
+    ref = np.array([[math.cos(theta), -math.sin(theta)], [math.sin(theta), math.cos(theta)]])
+    assert np.max(np.abs(E - ref)) < 4e-16
+
+
+def test_rotation_generator_high_precision():
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    theta = 2.5
+    A = np.array([[0.0, -theta], [theta, 0.0]])
+    eh, el = oracle.expm_ss_dd(A, 30, oracle.sigma_for(A))
+    c, s = mp.cos(theta), mp.sin(theta)
+    ref = [[c, -s], [s, c]]
+    for i in range(2):
+        for j in range(2):
+            got = mp.mpf(float(eh[i, j])) + mp.mpf(float(el[i, j]))
+            assert abs(got - ref[i][j]) < mp.mpf("1e-29")
+
+
+def test_group_property_exp_a_exp_minus_a():
+    n = 12
+    A = RNG.standard_normal((n, n))
+    A *= 3.0 / oracle.norm1(A)
+    sg = oracle.sigma_for(A)
+    ph, pl = oracle.expm_ss_dd(A, 30, sg)
+    mh, ml = oracle.expm_ss_dd(-A, 30, sg)
+    ch, cl = oracle.matmul_dd(ph, pl, mh, ml)
+    assert np.max(np.abs((ch - np.eye(n)) + cl)) < 1e-27
+    # p(A) commutes with A
+    ah, al = oracle.matmul_dd(ph, pl, A, None)
+    bh, bl = oracle.matmul_dd(A, None, ph, pl)
+    assert np.max(np.abs((ah - bh) + (al - bl))) < 1e-27 * np.max(np.abs(ah))
+
+
+def test_against_scipy_expm():
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    for n, nrm in [(16, 0.5), (16, 4.0), (24, 32.0)]:
+        A = RNG.standard_normal((n, n))
+        A *= nrm / oracle.norm1(A)
+        eh, el = oracle.expm_ss_dd(A, 30, oracle.sigma_for(A))
+        ref = scipy_linalg.expm(A)
+        assert oracle.norm1(eh - ref) / oracle.norm1(ref) < 5e-14
+
+
+def test_against_mpmath_expm():
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 45
+    n = 5
+    A = RNG.standard_normal((n, n))
+    A *= 2.0 / oracle.norm1(A)
+    eh, el = oracle.expm_ss_dd(A, 30, oracle.sigma_for(A))
+    ref = mp.expm(mp.matrix(A.tolist()))
+    err = max(abs(mp.mpf(float(eh[i, j])) + mp.mpf(float(el[i, j])) - ref[i, j])
+              for i in range(n) for j in range(n))
+    scale = max(abs(ref[i, j]) for i in range(n) for j in range(n))
+    assert err / scale < mp.mpf("1e-29")
+
+
+def test_sigma_rule():
+    assert oracle.sigma_for(np.array([[0.5]])) == 0
+    assert oracle.sigma_for(np.array([[1.0]])) == 0
+    assert oracle.sigma_for(np.array([[1.0000001]])) == 1
+    assert oracle.sigma_for(np.array([[4.0]])) == 2
+    assert oracle.sigma_for(np.array([[32.0]])) == 5
+    assert oracle.sigma_for(np.array([[33.0]])) == 6
+
+
+# --------------------------------------------------------------------------------
+# 7. columns of p(X)^k by Horner on vectors agree with the full evaluation
+# --------------------------------------------------------------------------------
+def test_apply_columns_matches_full():
+    n = 20
+    A = RNG.standard_normal((n, n))
+    A *= 4.0 / oracle.norm1(A)
+    sg = oracle.sigma_for(A)
+    X = np.ldexp(A, -sg)
+    c = oracle.taylor_exp_rational(30)
+    eh, el = oracle.expm_ss_dd(A, 30, sg)
+    cols = [0, 7, 19]
+    V = np.zeros((n, len(cols)))
+    for t, j in enumerate(cols):
+        V[j, t] = 1.0
+    wh, wl = oracle.ps_apply_dd(c, X, V, reps=2 ** sg)
+    ref = (eh + el)[:, cols]
+    assert np.max(np.abs((wh + wl) - ref)) < 1e-28 * np.max(np.abs(ref)) + 1e-300
+    assert np.max(np.abs((wh - eh[:, cols]) + (wl - el[:, cols]))) < 1e-28 * np.max(np.abs(ref))
+
+
+# --------------------------------------------------------------------------------
+# 8. adjoint: block-triangular identity, duality, Daleckii-Krein, finite differences
+# --------------------------------------------------------------------------------
+def frechet_block(c, A, E):
+    """L_p(A, E) from p([[A, E], [0, A]]) = [[p(A), L_p(A, E)], [0, p(A)]]."""
+    n = A.shape[0]
+    M = np.zeros((2 * n, 2 * n))
+    M[:n, :n] = A; M[n:, n:] = A; M[:n, n:] = E
+    ph, pl, _ = oracle.ps_dd(c, M)
+    return ph[:n, n:], pl[:n, n:]
+
+
+def test_adjoint_block_identity_duality():
+    n, m = 6, 10
+    c = oracle.taylor_exp_rational(m)
+    A = RNG.standard_normal((n, n)) * 0.4
+    G = RNG.standard_normal((n, n))
+    E = RNG.standard_normal((n, n))
+    gh, gl = oracle.adjoint_dd(c, A, G)
+    Lh, Ll = frechet_block(c, A, E)
+    lhs = np.sum((gh + gl) * E)
+    rhs = np.sum((Lh + Ll) * G)
+    assert abs(lhs - rhs) < 1e-13 * abs(rhs)
+    # the gradient is L_p(A^T, G): check it entrywise with the block identity
+    Lt_h, Lt_l = frechet_block(c, A.T.copy(), G)
+    assert np.max(np.abs((gh - Lt_h) + (gl - Lt_l))) < 1e-28 * np.max(np.abs(gh))
+
+
+def test_adjoint_diagonal_closed_form():
+    d = np.array([-0.7, -0.1, 0.3, 0.9])
+    n = len(d)
+    c = oracle.taylor_exp_rational(14)
+    cf = [float(x) for x in c]
+    p = lambda x: sum(cj * x ** j for j, cj in enumerate(cf))
+    dp = lambda x: sum(j * cj * x ** (j - 1) for j, cj in enumerate(cf) if j > 0)
+    G = RNG.standard_normal((n, n))
+    gh, gl = oracle.adjoint_dd(c, np.diag(d), G)
+    for i in range(n):
+        for j in range(n):
+            ref = G[i, j] * (dp(d[i]) if i == j else (p(d[i]) - p(d[j])) / (d[i] - d[j]))
+            assert abs(gh[i, j] - ref) < 1e-14 * max(1.0, abs(ref))
+
+
+def test_adjoint_central_differences():
+    n, m = 5, 8
+    c = oracle.taylor_exp_rational(m)
+    A = RNG.standard_normal((n, n)) * 0.3
+    G = RNG.standard_normal((n, n))
+    gh, gl = oracle.adjoint_dd(c, A, G)
+    h = 1e-6
+    for (i, j) in [(0, 0), (1, 3), (4, 2)]:
+        E = np.zeros((n, n)); E[i, j] = h
+        ph, pl, _ = oracle.ps_dd(c, A + E)
+        mh, ml, _ = oracle.ps_dd(c, A - E)
+        fd = (np.sum(G * (ph - mh)) + np.sum(G * (pl - ml))) / (2 * h)
+        assert abs(fd - gh[i, j]) < 1e-9 * max(1.0, abs(gh[i, j]))
+
+
+# --------------------------------------------------------------------------------
+# 9. the paper's printed worked example and tables
+# --------------------------------------------------------------------------------
+def _read_kv(path):
+    out = {}
+    for line in open(path):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        key, *vals = line.split()
+        out.setdefault(key, []).append(vals)
+    return out
+
+
+def test_ward_pade13_coefficients_exact():
+    g = _read_kv(os.path.join(GOLDEN, "ward_pade13.txt"))
+    c = oracle.pade_exp_num_rational(13)
+    assert c[:4] == [Fraction(v) for v in g["B0_coefficients"][0]]
+    assert c[4:8] == [Fraction(v) for v in g["B1_coefficients"][0]]
+    # denominator is p(-X)
+    assert oracle.pade_exp_den_rational(13) == [(-1) ** j * cj for j, cj in enumerate(c)]
+    # c_j sum to the [13/13] approximant's value at 1 over its value at -1 -> e to 1e-25
+    num = sum(c); den = sum(oracle.pade_exp_den_rational(13))
+    assert abs(float(num / den) - math.e) < 1e-15
+
+
+def test_ward_example_decay():
+    """eq. (2.5) holds on the Ward example with nu = 1: tau_1 << 1 and tau_3 < tau_2 < tau_1.
+    The printed magnitudes are not reproducible from the printed data (see the readings
+    of the paper in the design notes); only the decay they illustrate is pinned."""
+    g = _read_kv(os.path.join(GOLDEN, "ward_pade13.txt"))
+    A = np.array([[float(v) for v in row] for row in g["matrix_row"]])
+    ell = int(g["scaling_exponent"][0][0]); s = int(g["s"][0][0])
+    X = np.ldexp(A, -ell)
+    norms, y = oracle.block_norms_dd(oracle.pade_exp_num_rational(13), X, s)
+    tau = [norms[i] * y / norms[i - 1] for i in range(1, len(norms))]
+    assert tau[0] < 1e-2 and tau[1] < tau[0] and tau[2] < tau[1]
+
+
+def test_table1_parameters_and_cost_ratio():
+    rows = []
+    for line in open(os.path.join(GOLDEN, "table1_cauchy100.txt")):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        head, ds, pct = line.split("|")
+        D, m, s, r = (int(v) for v in head.split())
+        rows.append((D, m, s, r, [int(v) for v in ds.split()], float(pct)))
+    assert len(rows) == 4
+    for D, m, s, r, d, pct in rows:
+        assert oracle.ceil_sqrt(m) == s and m // s == r and len(d) == r
+        assert all(d[i] >= d[i + 1] for i in range(r - 1))
+        saving = 100.0 * (1.0 - oracle.cost_ratio(s, r, D, d))
+        assert abs(saving - pct) < 0.05, (D, saving, pct)
+
+
+# --------------------------------------------------------------------------------
+# 10. the precision rule with hand-derived answers
+# --------------------------------------------------------------------------------
+F = oracle
+
+
+def test_plan_hand_case_paper_mode():
+    # m = 16, s = 4, r = 4, s | m -> step 4 folded.  tol = 2^-53 = 1.11e-16.
+    # u_1 = 1 * tol / (1e-3 * 0.5)     = 2.2e-13 -> only FP64 (nu = 1 since >= 10 tol)
+    # u_2 = tol / (1e-9 * 0.25)        = 4.4e-7  -> below 2^-16 -> FP64
+    # u_3 = tol / (1e-15 * 0.125)      = 0.89    -> FP8 (2^-4 <= 0.89, 64 * 2^-24 <= 0.89)
+    p = F.plan(16, 64, [1.0, 1e-3, 1e-9, 1e-15, 1e-21], 0.5, mode=F.MODE_PAPER)
+    assert (p["s"], p["r"], p["nu"], p["fold"]) == (4, 4, 1, True)
+    assert p["fmt"][1:] == [F.FMT_FP64, F.FMT_FP64, F.FMT_FP8, F.FMT_NONE]
+    assert p["u"][1] == pytest.approx(2.0 ** -53 / 5e-4)
+    assert p["u"][3] == pytest.approx(2.0 ** -53 / 1.25e-16)
+
+
+def test_plan_hand_case_ladder():
+    # u_i chosen so that each format boundary is crossed once; n = 16
+    tol = 2.0 ** -53
+    y = 1.0
+    # u_i = tol / eta_i: pick eta_i = tol / target
+    targets = [None, 2e-5, 6e-4, 5e-3, 0.07]     # -> BF16X3, TF32, BF16, FP8
+    norms = [1.0] + [tol / t for t in targets[1:]] + [1e-30]
+    p = F.plan(20, 16, norms, y, mode=F.MODE_PAPER, s=4)   # r = 5, 4 does not... 20 % 4 == 0
+    assert p["r"] == 5 and p["fold"]
+    assert p["fmt"][1:5] == [F.FMT_BF16X3, F.FMT_TF32, F.FMT_BF16, F.FMT_FP8]
+    # masks remove formats: without FP8 and BF16, the 0.07 step falls back to TF32
+    mask = (1 << F.FMT_FP64) | (1 << F.FMT_BF16X3) | (1 << F.FMT_TF32)
+    q = F.plan(20, 16, norms, y, mode=F.MODE_PAPER, s=4, formats=mask)
+    assert q["fmt"][1:5] == [F.FMT_BF16X3, F.FMT_TF32, F.FMT_TF32, F.FMT_TF32]
+    # NS floors keep steps 1 and 2 in FP64
+    ns = F.plan(20, 16, norms, y, mode=F.MODE_NS, s=4)
+    assert ns["fmt"][1:5] == [F.FMT_FP64, F.FMT_FP64, F.FMT_BF16, F.FMT_FP8]
+    fx = F.plan(20, 16, norms, y, mode=F.MODE_FIXED, s=4)
+    assert fx["fmt"][1:5] == [F.FMT_FP64] * 4 and fx["fmt"][5] == F.FMT_NONE
+
+
+def test_plan_nu_and_accumulation_check():
+    tol = 2.0 ** -53
+    # u_1 = tol (not >= 10 tol), u_2 huge -> nu = 2, u_1 reset to tol
+    p = F.plan(9, 64, [1.0, 1.0, 1e-20, 1e-30], 1.0, mode=F.MODE_PAPER)
+    assert p["s"] == 3 and p["r"] == 3 and p["nu"] == 2
+    assert p["u"][1] == tol and p["fmt"][1] == F.FMT_FP64
+    assert p["fmt"][2] == F.FMT_FP8
+    # with n = 2^20 every FP32-accumulated format needs u_i >= 1/16
+    big = F.plan(9, 2 ** 20, [1.0, 1.0, tol / 0.05, 1e-30], 1.0, mode=F.MODE_PAPER)
+    assert big["fmt"][2] == F.FMT_FP64
+    # zero block: no error contribution -> cheapest format
+    z = F.plan(9, 64, [1.0, 0.0, 1e-20, 1e-30], 1.0, mode=F.MODE_PAPER)
+    assert z["fmt"][1] == F.FMT_FP8 and z["nu"] == 1
+
+
+def test_plan_degenerate():
+    assert F.plan(0, 8, [1.0], 0.0)["r"] == 0
+    p1 = F.plan(1, 8, [1.0, 1.0], 1.0)      # s = 1, r = 1, folded (b_1 I)
+    assert (p1["s"], p1["r"], p1["fold"]) == (1, 1, True)
