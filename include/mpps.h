@@ -1,0 +1,183 @@
+/*
+ * mpps.h -- C ABI of the GB300 (sm_103a) library for mixed-precision Paterson--Stockmeyer
+ * evaluation of matrix polynomials (Liu, "Mixed-Precision Paterson--Stockmeyer Method for
+ * Evaluating Polynomials of Matrices", arXiv 2312.17396).
+ *
+ * Problem (Section 2, Algorithm 2.1; Algorithm 4.1 for general coefficients): given
+ * X in R^{n x n} and scalars b_0..b_m, compute p_m(X) = sum_i b_i X^i in the
+ * Paterson--Stockmeyer form of eq. (1.1),
+ *     p_m(X) = sum_{i=0}^{r} B_i (X^s)^i,  r = floor(m/s),
+ *     B_i = sum_{j=0}^{s-1} b_{si+j} X^j  (i < r),   B_r = sum_{j=0}^{m-sr} b_{sr+j} X^j,
+ * by Horner's rule in Y = X^s (eq. (2.4)), with the product of Horner step i done in the
+ * precision u_i chosen by eq. (2.8) (Section 2, Algorithm 3.1 `fix_params` branch,
+ * Algorithm 4.1) and the sums in FP64.
+ *
+ * Conventions shared by every entry point:
+ *  - Matrices are real FP64, n x n, row-major and contiguous; a batch of `batch` matrices
+ *    is contiguous with stride n*n elements.  Row-major is harmless: p(A^T) = p(A)^T.
+ *  - Matrix pointers may be device pointers (cudaMalloc, torch CUDA tensors) or host
+ *    pointers (pageable or pinned).  The library inspects each pointer.  When any matrix
+ *    argument is on the host, the call copies it to the device, runs, copies the result
+ *    back and synchronises the stream before returning.  When all are device pointers the
+ *    call is asynchronous on `stream` except where noted.
+ *  - `coeffs` is always a host array of m+1 doubles (b_0..b_m), read during the call.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *  - Workspace is allocated by the library with cudaMallocAsync on `stream` and released
+ *    with cudaFreeAsync before the call returns (stream-ordered).
+ *  - Every call returns a status; none aborts.  On failure mpps_last_error() returns a
+ *    description (thread-local, valid until the next call on the same thread).  Invalid
+ *    sizes or null pointers give MPPS_EINVAL before any GPU work is issued.
+ *  - The caller owns all pointers passed in; the library keeps none after returning.
+ */
+#ifndef MPPS_H
+#define MPPS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MPPS_OK = 0,
+    MPPS_EINVAL = 1,    /* invalid argument (size, pointer, policy) */
+    MPPS_ENOMEM = 2,    /* device allocation failed */
+    MPPS_ECUDA = 3,     /* a CUDA runtime/driver call or kernel launch failed */
+    MPPS_ETIMEOUT = 4,  /* a bounded wait inside a kernel gave up (device error word set) */
+    MPPS_ENOTSUP = 5    /* not supported on this device / build */
+} mpps_status;
+
+/* Precision modes.  FIXED: every product in FP64 (Algorithm 2.1).  MIXED_PAPER: eq. (2.8)
+ * with nu chosen as in Algorithm 3.1 and the format ladder of Section 4.1.1 extended to the
+ * GPU formats.  MIXED_NS: as MIXED_PAPER but the Horner steps i <= fp64_floor_steps (the
+ * products feeding B_0, B_1, ...) stay FP64. */
+typedef enum { MPPS_FIXED_FP64 = 0, MPPS_MIXED_PAPER = 1, MPPS_MIXED_NS = 2 } mpps_mode;
+
+/* Product formats, ordered from most to least precise.  The unit roundoff of each format's
+ * rounded inputs: FP64 2^-53; BF16X3 (operands split into bf16 hi+lo, three products
+ * hi*hi + hi*lo + lo*hi accumulated in FP32) 2^-16; TF32 2^-11; BF16 2^-8; FP8 (E4M3, with a
+ * power-of-two scale per operand) 2^-4.  All but FP64 accumulate in FP32 (unit 2^-24).
+ * NONE marks a step with no product (B_r a scalar multiple of I, i.e. s divides m). */
+typedef enum {
+    MPPS_FMT_NONE = -1,
+    MPPS_FMT_FP64 = 0,
+    MPPS_FMT_BF16X3 = 1,
+    MPPS_FMT_TF32 = 2,
+    MPPS_FMT_BF16 = 3,
+    MPPS_FMT_FP8 = 4
+} mpps_format;
+
+#define MPPS_NUM_FORMATS 5
+#define MPPS_MAX_R 64      /* largest r = floor(m/s) a report can describe */
+#define MPPS_MAX_S 32      /* largest block size s */
+
+typedef struct {
+    int mode;               /* mpps_mode */
+    double tol;             /* working precision u (u_0 of eq. (2.8)); <= 0 -> 2^-53 */
+    double delta;           /* switch threshold delta of Algorithm 3.1; <= 0 -> 10 */
+    int s;                  /* PS block size; 0 -> ceil(sqrt(m)) (Algorithm 2.1) */
+    unsigned formats;       /* bit f allows format f; 0 -> all; FP64 is always allowed */
+    int fp64_floor_steps;   /* MIXED_NS: steps i <= this stay FP64; < 0 -> 2 */
+} mpps_policy;
+
+/* Per-matrix description of what a call did (filled when `rep` is non-NULL). */
+typedef struct {
+    int s, r, nu;                    /* block size, floor(m/s), first low-precision step */
+    int sigma;                       /* squarings (expm only; 0 otherwise) */
+    int fold;                        /* 1 when s divides m (step r has no product) */
+    int fmt[MPPS_MAX_R + 1];         /* fmt[i]: format of the product P_i Y, i = 1..r */
+    double u[MPPS_MAX_R + 1];        /* u[i]: precision asked for by eq. (2.8), i = 1..r */
+    double normB[MPPS_MAX_R + 1];    /* ||B_i||_1, i = 0..r */
+    double normY;                    /* ||X^s||_1 */
+    double normX;                    /* ||X||_1 (after scaling, for expm) */
+    int gemms[MPPS_NUM_FORMATS + 1]; /* products per format; [MPPS_NUM_FORMATS] = squarings */
+    double cost_ratio;               /* eq. (3.8) with the digits of the chosen formats */
+} mpps_report;
+
+/* Fill *p with the defaults: MIXED_NS, tol 2^-53, delta 10, s 0, all formats, floor 2. */
+void mpps_policy_default(mpps_policy* p);
+
+/*
+ * Host-only precision planner (no GPU work): eq. (2.8) at nu = 1,
+ *   u_i = max(tol, ||B_0|| tol / (||B_i|| ||Y||^i)),  i = 1..r  (||Y||^i by repeated
+ *   multiplication; a zero denominator gives u_i = +inf),
+ * nu = min{i : u_i >= delta*tol} (r+1 if none) and u_1..u_{nu-1} = tol (Algorithm 3.1,
+ * Algorithm 4.1); format_i = the cheapest allowed format whose unit roundoff is <= u_i and,
+ * for FP32-accumulated formats, n 2^-24 <= u_i (Section 4.1.1's rule max{u* <= u_i}).
+ * normB: r+1 values ||B_0||..||B_r|| with r = floor(m/s); normY = ||X^s||_1.
+ * Writes s, r, nu, fold, fmt, u, normB, normY and cost_ratio of *out.
+ * Returns MPPS_EINVAL for m < 0, n <= 0, r > MPPS_MAX_R, s > MPPS_MAX_S or a NULL pointer.
+ */
+mpps_status mpps_plan(int m, int n, const double* normB, double normY, const mpps_policy* policy,
+                      mpps_report* out);
+
+/*
+ * p_m(A) for a batch of matrices (Algorithm 2.1 / Algorithm 4.1).
+ *   coeffs : host, m+1 doubles b_0..b_m.            m >= 0.
+ *   A      : batch x n x n input (host or device), not modified.
+ *   out    : batch x n x n result (host or device); may not alias A.
+ *   policy : NULL -> defaults (mpps_policy_default).
+ *   rep    : NULL, or `batch` reports (host memory).
+ * Steps: powers X^2..X^s in FP64; ||B_i||_1 and ||Y||_1 in FP64; the host planner; Horner
+ * products in the planned formats with the block sums fused into their epilogues.  The
+ * norms are read back to the host once per call, so the call synchronises `stream` once.
+ */
+mpps_status ps_eval(const double* coeffs, int m, const double* A, int n, int batch,
+                    const mpps_policy* policy, double* out, mpps_report* rep, void* stream);
+
+/*
+ * exp(A) by the degree-m Taylor polynomial with scaling and squaring, eq. (3.6):
+ * sigma = max(0, ceil(log2 ||A||_1)) so that ||2^-sigma A||_1 <= 1, X = 2^-sigma A (exact),
+ * P = p_m(X) evaluated as in ps_eval with b_i = 1/i!, then sigma squarings in FP64.
+ *   m      : Taylor degree (0 -> 30).
+ *   Others as in ps_eval.  Synchronises `stream` once (norms for sigma and the planner).
+ */
+mpps_status expm_taylor_ss(const double* A, int n, int batch, int m, const mpps_policy* policy,
+                           double* out, mpps_report* rep, void* stream);
+
+/*
+ * Gradient of f(A) = <G, p_m(A)> = sum_ij G_ij p_m(A)_ij with respect to A, i.e. the
+ * Frechet derivative L_p(A^T, G) (the paper states no adjoint; this is the derivative of
+ * the PS evaluation, computed by reverse-mode through its steps, in FP64).
+ *   coeffs : host, m+1 doubles.   A, G : batch x n x n (host or device).
+ *   gradA  : batch x n x n output (host or device).
+ */
+mpps_status ps_eval_adjoint(const double* coeffs, int m, const double* A, const double* G,
+                            int n, int batch, double* gradA, void* stream);
+
+/*
+ * C = A B for a batch of n x n FP64 matrices, the product computed in `format`
+ * (an mpps_format other than NONE): the building block of every step above.  For the
+ * low-precision formats each operand is scaled by a power of two chosen from its largest
+ * entry, rounded to the format, multiplied on the tensor cores with FP32 accumulation,
+ * and the result scaled back in FP64.  Asynchronous for device pointers.
+ */
+mpps_status mpps_matmul(const double* A, const double* B, double* C, int n, int batch,
+                        int format, void* stream);
+
+/* Benchmark instrumentation (off by default).  When enabled, every kernel launch of the
+ * library is bracketed by two CUDA events recorded on the launch stream and tagged with a
+ * kernel class: MPPS_PROF_GEMM_F64 (FP64 products), MPPS_PROF_GEMM_TC (tensor-core
+ * products), MPPS_PROF_ELEMENTWISE (block sums, norms, conversions, copies).
+ * mpps_profile_read waits for the recorded events and returns the number of launches and
+ * their summed durations (ms) of one class since the last reset.  Do not enable it while
+ * a stream is being captured into a CUDA graph. */
+#define MPPS_PROF_GEMM_F64 0
+#define MPPS_PROF_GEMM_TC 1
+#define MPPS_PROF_ELEMENTWISE 2
+#define MPPS_PROF_NUM_CLASSES 3
+void mpps_profile_enable(int on);
+void mpps_profile_reset(void);
+mpps_status mpps_profile_read(int kernel_class, long long* launches, double* total_ms);
+
+/* Description of the last failure on this thread ("" if none). */
+const char* mpps_last_error(void);
+
+/* Library version string. */
+const char* mpps_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPPS_H */

@@ -1,0 +1,372 @@
+"""mpps -- mixed-precision Paterson--Stockmeyer evaluation of matrix polynomials on GB300.
+
+Python binding of the C ABI in ``include/mpps.h`` (library ``libmpps.so`` built in-tree by
+``paper_2312_17396_gb300._build``).  Argument marshalling only: every step of the
+evaluation runs in the CUDA kernels of the library.  If the library is missing the calls
+raise; there is no CPU fallback.
+
+Matrices are float64, shape (n, n) or (batch, n, n), row-major contiguous.  Inputs may be
+CUDA torch tensors (the call is asynchronous on the current torch stream, except for one
+read-back of the block norms that the precision rule needs) or host arrays (numpy or CPU
+tensors; the library copies them in and out and synchronises).
+
+Paper: X. Liu, "Mixed-Precision Paterson--Stockmeyer Method for Evaluating Polynomials of
+Matrices", arXiv 2312.17396.  Algorithm 2.1 (fixed PS), eq. (2.8) (precision rule),
+Algorithm 3.1 (Taylor exp), Algorithm 4.1 (general coefficients), eq. (3.6) (scaling and
+squaring).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_PKG, "libmpps.so")
+_lib = None
+
+FIXED_FP64, MIXED_PAPER, MIXED_NS = 0, 1, 2
+FMT_NONE, FMT_FP64, FMT_BF16X3, FMT_TF32, FMT_BF16, FMT_FP8 = -1, 0, 1, 2, 3, 4
+FORMAT_NAMES = {FMT_NONE: "none", FMT_FP64: "fp64", FMT_BF16X3: "bf16x3", FMT_TF32: "tf32",
+                FMT_BF16: "bf16", FMT_FP8: "fp8"}
+_FMT_BY_NAME = {v: k for k, v in FORMAT_NAMES.items()}
+MAX_R = 64
+MAX_S = 32
+NUM_FORMATS = 5
+
+STATUS = {0: "MPPS_OK", 1: "MPPS_EINVAL", 2: "MPPS_ENOMEM", 3: "MPPS_ECUDA", 4: "MPPS_ETIMEOUT",
+          5: "MPPS_ENOTSUP"}
+
+
+class MppsError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class _Policy(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("tol", ctypes.c_double), ("delta", ctypes.c_double),
+                ("s", ctypes.c_int), ("formats", ctypes.c_uint), ("fp64_floor_steps", ctypes.c_int)]
+
+
+class _Report(ctypes.Structure):
+    _fields_ = [("s", ctypes.c_int), ("r", ctypes.c_int), ("nu", ctypes.c_int),
+                ("sigma", ctypes.c_int), ("fold", ctypes.c_int),
+                ("fmt", ctypes.c_int * (MAX_R + 1)), ("u", ctypes.c_double * (MAX_R + 1)),
+                ("normB", ctypes.c_double * (MAX_R + 1)), ("normY", ctypes.c_double),
+                ("normX", ctypes.c_double), ("gemms", ctypes.c_int * (NUM_FORMATS + 1)),
+                ("cost_ratio", ctypes.c_double)]
+
+
+EXPORTS = ("mpps_policy_default", "mpps_plan", "ps_eval", "expm_taylor_ss", "ps_eval_adjoint",
+           "mpps_matmul", "mpps_last_error", "mpps_version", "mpps_profile_enable",
+           "mpps_profile_reset", "mpps_profile_read")
+PROF_GEMM_F64, PROF_GEMM_TC, PROF_ELEMENTWISE = 0, 1, 2
+
+
+def lib():
+    """Load libmpps.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(f"{_LIB_PATH} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(_LIB_PATH)
+        vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
+        L.mpps_policy_default.argtypes = [ctypes.POINTER(_Policy)]
+        L.mpps_policy_default.restype = None
+        L.mpps_plan.argtypes = [ip, ip, dp, ctypes.c_double, ctypes.POINTER(_Policy),
+                                ctypes.POINTER(_Report)]
+        L.ps_eval.argtypes = [dp, ip, vp, ip, ip, ctypes.POINTER(_Policy), vp,
+                              ctypes.POINTER(_Report), vp]
+        L.expm_taylor_ss.argtypes = [vp, ip, ip, ip, ctypes.POINTER(_Policy), vp,
+                                     ctypes.POINTER(_Report), vp]
+        L.ps_eval_adjoint.argtypes = [dp, ip, vp, vp, ip, ip, vp, vp]
+        L.mpps_matmul.argtypes = [vp, vp, vp, ip, ip, ip, vp]
+        for f in ("mpps_plan", "ps_eval", "expm_taylor_ss", "ps_eval_adjoint", "mpps_matmul"):
+            getattr(L, f).restype = ctypes.c_int
+        L.mpps_profile_enable.argtypes = [ctypes.c_int]
+        L.mpps_profile_enable.restype = None
+        L.mpps_profile_reset.argtypes = []
+        L.mpps_profile_reset.restype = None
+        L.mpps_profile_read.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
+                                        ctypes.POINTER(ctypes.c_double)]
+        L.mpps_profile_read.restype = ctypes.c_int
+        L.mpps_last_error.restype = ctypes.c_char_p
+        L.mpps_version.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != 0:
+        raise MppsError(status, lib().mpps_last_error().decode(errors="replace"))
+
+
+# ------------------------------------------------------------------------------------
+# policy and reports
+# ------------------------------------------------------------------------------------
+@dataclass
+class Policy:
+    """Precision policy (see ``mpps_policy`` in include/mpps.h)."""
+    mode: int = MIXED_NS
+    tol: float = 2.0 ** -53
+    delta: float = 10.0
+    s: int = 0
+    formats: object = 0x1F          # bitmask or iterable of format names
+    fp64_floor_steps: int = 2
+
+    def _c(self):
+        fm = self.formats
+        if not isinstance(fm, int):
+            mask = 0
+            for name in fm:
+                mask |= 1 << _FMT_BY_NAME[name]
+            fm = mask
+        return _Policy(int(self.mode), float(self.tol), float(self.delta), int(self.s),
+                       int(fm), int(self.fp64_floor_steps))
+
+
+FIXED = Policy(mode=FIXED_FP64)
+PAPER = Policy(mode=MIXED_PAPER)
+NS = Policy(mode=MIXED_NS)
+
+
+def _report_dict(R: _Report) -> dict:
+    r = R.r
+    return dict(s=R.s, r=r, nu=R.nu, sigma=R.sigma, fold=bool(R.fold),
+                fmt=[None] + [FORMAT_NAMES[R.fmt[i]] for i in range(1, r + 1)],
+                u=[None] + [R.u[i] for i in range(1, r + 1)],
+                normB=[R.normB[i] for i in range(r + 1)], normY=R.normY, normX=R.normX,
+                gemms={FORMAT_NAMES[f]: R.gemms[f] for f in range(NUM_FORMATS)} |
+                {"squarings": R.gemms[NUM_FORMATS]},
+                cost_ratio=R.cost_ratio)
+
+
+def plan(m: int, n: int, normB, normY: float, policy: Policy | None = None) -> dict:
+    """Host-only precision planner of the library (eq. (2.8); no GPU needed)."""
+    nb = np.ascontiguousarray(normB, dtype=np.float64)
+    R = _Report()
+    pol = (policy or Policy())._c()
+    _check(lib().mpps_plan(int(m), int(n), nb.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                           float(normY), ctypes.byref(pol), ctypes.byref(R)))
+    return _report_dict(R)
+
+
+# ------------------------------------------------------------------------------------
+# coefficient sequences (double precision; b_i rounded once)
+# ------------------------------------------------------------------------------------
+def taylor_exp_coeffs(m: int) -> np.ndarray:
+    """b_i = 1/i! (Section 3)."""
+    return np.array([1 / math.factorial(i) for i in range(m + 1)])   # int/int: correctly rounded
+
+
+def pade_exp_num_coeffs(q: int) -> np.ndarray:
+    """[q/q] Pade numerator of exp: (2q-j)! q! / ((2q)! j! (q-j)!) (Section 4.1)."""
+    f = math.factorial
+    return np.array([f(2 * q - j) * f(q) / (f(2 * q) * f(j) * f(q - j)) for j in range(q + 1)])
+
+
+def pade_exp_den_coeffs(q: int) -> np.ndarray:
+    """[q/q] Pade denominator of exp: p_qq(-X) (Section 4.1)."""
+    c = pade_exp_num_coeffs(q)
+    return c * (-1.0) ** np.arange(q + 1)
+
+
+def cos_taylor_coeffs(m: int) -> np.ndarray:
+    """Taylor cosine in B = X^2: (-1)^k / (2k)! (Section 4.2)."""
+    return np.array([(-1) ** k / math.factorial(2 * k) for k in range(m + 1)])
+
+
+# ------------------------------------------------------------------------------------
+# marshalling
+# ------------------------------------------------------------------------------------
+def _torch():
+    try:
+        import torch
+        return torch
+    except ImportError:  # pragma: no cover
+        return None
+
+
+def _is_torch(x):
+    t = _torch()
+    return t is not None and isinstance(x, t.Tensor)
+
+
+def _prep(A, name):
+    """Returns (pointer, batch, n, kind, keepalive) for a float64 square matrix stack."""
+    if _is_torch(A):
+        torch = _torch()
+        if A.dtype != torch.float64:
+            raise TypeError(f"{name} must be float64 (got {A.dtype})")
+        if not A.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        shape = tuple(A.shape)
+        ptr = A.data_ptr()
+        kind = "cuda" if A.is_cuda else "host"
+        keep = A
+    else:
+        A = np.ascontiguousarray(A, dtype=np.float64)
+        shape = A.shape
+        ptr = A.ctypes.data
+        kind, keep = "host", A
+    if len(shape) == 2:
+        batch, n = 1, shape[0]
+        if shape[1] != n:
+            raise ValueError(f"{name} must be square")
+    elif len(shape) == 3:
+        batch, n = shape[0], shape[1]
+        if shape[2] != n:
+            raise ValueError(f"{name} must be a stack of square matrices")
+    else:
+        raise ValueError(f"{name} must have shape (n, n) or (batch, n, n)")
+    return ptr, batch, n, kind, keep
+
+
+def _empty_like(A, keep):
+    if _is_torch(keep):
+        return _torch().empty_like(keep)
+    return np.empty_like(keep)
+
+
+def _stream_for(kind, stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    if kind == "cuda":
+        return ctypes.c_void_p(_torch().cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+def _coef_ptr(coeffs):
+    c = np.ascontiguousarray(coeffs, dtype=np.float64)
+    return c, c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(c) - 1
+
+
+# ------------------------------------------------------------------------------------
+# entry points
+# ------------------------------------------------------------------------------------
+def ps_eval(coeffs, A, policy: Policy | None = None, out=None, report: bool = False, stream=None):
+    """p(A) = sum_i coeffs[i] A^i by Paterson--Stockmeyer with the per-step precision rule."""
+    ptr, batch, n, kind, keep = _prep(A, "A")
+    if out is None:
+        out = _empty_like(A, keep)
+    optr, ob, on, okind, okeep = _prep(out, "out")
+    if (ob, on) != (batch, n):
+        raise ValueError("out has the wrong shape")
+    c, cp, m = _coef_ptr(coeffs)
+    reps = (_Report * batch)() if report else None
+    pol = (policy or Policy())._c()
+    _check(lib().ps_eval(cp, m, ctypes.c_void_p(ptr), n, batch, ctypes.byref(pol),
+                         ctypes.c_void_p(optr), reps, _stream_for(kind, stream)))
+    if report:
+        return out, [_report_dict(r) for r in reps]
+    return out
+
+
+def expm(A, m: int = 30, policy: Policy | None = None, out=None, report: bool = False, stream=None):
+    """exp(A) by the degree-m Taylor polynomial with scaling and squaring (eq. (3.6))."""
+    ptr, batch, n, kind, keep = _prep(A, "A")
+    if out is None:
+        out = _empty_like(A, keep)
+    optr, ob, on, _, _ = _prep(out, "out")
+    if (ob, on) != (batch, n):
+        raise ValueError("out has the wrong shape")
+    reps = (_Report * batch)() if report else None
+    pol = (policy or Policy())._c()
+    _check(lib().expm_taylor_ss(ctypes.c_void_p(ptr), n, batch, int(m), ctypes.byref(pol),
+                                ctypes.c_void_p(optr), reps, _stream_for(kind, stream)))
+    if report:
+        return out, [_report_dict(r) for r in reps]
+    return out
+
+
+def ps_eval_adjoint(coeffs, A, G, out=None, stream=None):
+    """Gradient of <G, p(A)> with respect to A (reverse mode through the PS steps, FP64)."""
+    ptr, batch, n, kind, keep = _prep(A, "A")
+    gptr, gb, gn, _, _ = _prep(G, "G")
+    if (gb, gn) != (batch, n):
+        raise ValueError("G must have the shape of A")
+    if out is None:
+        out = _empty_like(A, keep)
+    optr, _, _, _, _ = _prep(out, "out")
+    c, cp, m = _coef_ptr(coeffs)
+    _check(lib().ps_eval_adjoint(cp, m, ctypes.c_void_p(ptr), ctypes.c_void_p(gptr), n, batch,
+                                 ctypes.c_void_p(optr), _stream_for(kind, stream)))
+    return out
+
+
+def matmul(A, B, fmt="fp64", out=None, stream=None):
+    """C = A B with the product computed in format `fmt` (name or FMT_* code)."""
+    f = _FMT_BY_NAME[fmt] if isinstance(fmt, str) else int(fmt)
+    ptr, batch, n, kind, keep = _prep(A, "A")
+    bptr, bb, bn, _, _ = _prep(B, "B")
+    if (bb, bn) != (batch, n):
+        raise ValueError("B must have the shape of A")
+    if out is None:
+        out = _empty_like(A, keep)
+    optr, _, _, _, _ = _prep(out, "out")
+    _check(lib().mpps_matmul(ctypes.c_void_p(ptr), ctypes.c_void_p(bptr), ctypes.c_void_p(optr),
+                             n, batch, f, _stream_for(kind, stream)))
+    return out
+
+
+def profile_enable(on: bool = True) -> None:
+    """Record CUDA events around every library kernel launch (benchmark instrumentation)."""
+    lib().mpps_profile_enable(1 if on else 0)
+
+
+def profile_reset() -> None:
+    lib().mpps_profile_reset()
+
+
+def profile_read(kernel_class: int):
+    """(launches, total ms) of one kernel class since the last reset."""
+    cnt = ctypes.c_longlong(0)
+    ms = ctypes.c_double(0.0)
+    _check(lib().mpps_profile_read(int(kernel_class), ctypes.byref(cnt), ctypes.byref(ms)))
+    return int(cnt.value), float(ms.value)
+
+
+def version() -> str:
+    return lib().mpps_version().decode()
+
+
+def _make_autograd():
+    torch = _torch()
+    if torch is None:  # pragma: no cover
+        return None
+
+    class PolyFn(torch.autograd.Function):
+        """p(A) with a hand-written reverse mode: forward ps_eval, backward ps_eval_adjoint.
+        FP32 inputs are evaluated in FP64 and the result is returned in the input dtype."""
+
+        @staticmethod
+        def forward(ctx, A, coeffs, policy=None):
+            c = np.asarray(coeffs, dtype=np.float64)
+            A64 = A.detach().to(torch.float64).contiguous()
+            P = ps_eval(c, A64, policy=policy)
+            ctx.save_for_backward(A64)
+            ctx.coeffs = c
+            ctx.in_dtype = A.dtype
+            return P.to(A.dtype)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (A64,) = ctx.saved_tensors
+            G = grad_out.detach().to(torch.float64).contiguous()
+            gA = ps_eval_adjoint(ctx.coeffs, A64, G)
+            return gA.to(ctx.in_dtype), None, None
+
+    return PolyFn
+
+
+PolyFn = _make_autograd()
+
+
+def poly(A, coeffs, policy: Policy | None = None):
+    """Differentiable p(A) (torch): ``PolyFn.apply`` with a default policy."""
+    return PolyFn.apply(A, coeffs, policy)

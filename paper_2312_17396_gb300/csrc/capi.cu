@@ -1,0 +1,855 @@
+// capi.cu -- the C ABI of include/mpps.h: argument checks, the host precision planner
+// (eq. (2.8), Algorithm 3.1 `fix_params` branch, Algorithm 4.1), workspace layout and the
+// order of kernel launches for ps_eval, expm_taylor_ss, ps_eval_adjoint and mpps_matmul.
+#include "common.cuh"
+
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+namespace mpps {
+
+// ---- errors -------------------------------------------------------------------------
+static thread_local char g_err[1024];
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+void clear_error() { g_err[0] = '\0'; }
+
+// ---- policy -------------------------------------------------------------------------
+struct Pol {
+    int mode;
+    double tol, delta;
+    int s;
+    unsigned formats;
+    int floor_steps;
+};
+
+static Pol resolve(const mpps_policy* p) {
+    mpps_policy d;
+    mpps_policy_default(&d);
+    if (!p) p = &d;
+    Pol r;
+    r.mode = p->mode;
+    r.tol = p->tol > 0 ? p->tol : 0x1p-53;
+    r.delta = p->delta > 0 ? p->delta : 10.0;
+    r.s = p->s;
+    r.formats = (p->formats ? p->formats : 0x1Fu) | 1u;
+    r.floor_steps = p->fp64_floor_steps < 0 ? 2 : p->fp64_floor_steps;
+    return r;
+}
+
+static int ceil_sqrt_int(int m) {
+    if (m <= 1) return 1;
+    int s = (int)sqrt((double)m);
+    while (s * s < m) ++s;
+    while (s > 1 && (s - 1) * (s - 1) >= m) --s;
+    return s;
+}
+
+// unit roundoff of the rounded inputs of each format, and the FP32 accumulation unit
+static const double kUFmt[MPPS_NUM_FORMATS] = {0x1p-53, 0x1p-16, 0x1p-11, 0x1p-8, 0x1p-4};
+static const double kAcc = 0x1p-24;
+
+static bool is_low(int f) { return f >= MPPS_FMT_BF16X3 && f <= MPPS_FMT_FP8; }
+
+// Planner for one matrix.  normB: r+1 norms ||B_0||..||B_r||; normY = ||X^s||.
+static mpps_status plan_one(int m, int n, const double* normB, double normY, const Pol& P,
+                            mpps_report* out) {
+    memset(out, 0, sizeof(*out));
+    for (int i = 0; i <= MPPS_MAX_R; ++i) out->fmt[i] = MPPS_FMT_NONE;
+    if (m == 0) {
+        out->s = 1; out->r = 0; out->nu = 1;
+        out->normB[0] = normB ? normB[0] : 0.0;
+        out->cost_ratio = 1.0;
+        return MPPS_OK;
+    }
+    int s = P.s > 0 ? std::min(P.s, m) : ceil_sqrt_int(m);
+    if (s > MPPS_MAX_S) {
+        set_error("block size s=%d exceeds %d", s, MPPS_MAX_S);
+        return MPPS_EINVAL;
+    }
+    const int r = m / s;
+    if (r > MPPS_MAX_R) {
+        set_error("r=floor(m/s)=%d exceeds %d", r, MPPS_MAX_R);
+        return MPPS_EINVAL;
+    }
+    out->s = s;
+    out->r = r;
+    out->fold = (m % s == 0) ? 1 : 0;
+    out->normY = normY;
+    for (int i = 0; i <= r; ++i) out->normB[i] = normB[i];
+    const double tol = P.tol;
+    // eq. (2.8) with nu = 1, clamped at the working precision
+    for (int i = 1; i <= r; ++i) {
+        double yi = 1.0;
+        for (int k = 0; k < i; ++k) yi = yi * normY;
+        const double den = normB[i] * yi;
+        const double ui = (den == 0.0) ? INFINITY : (normB[0] * tol) / den;
+        out->u[i] = (ui > tol) ? ui : tol;
+    }
+    // nu: first step allowed below the working precision; earlier steps get u
+    int nu = r + 1;
+    for (int i = 1; i <= r; ++i)
+        if (out->u[i] >= P.delta * tol) { nu = i; break; }
+    for (int i = 1; i < nu; ++i) out->u[i] = tol;
+    out->nu = nu;
+    // formats: cheapest allowed with unit roundoff <= u_i (and FP32 accumulation <= u_i)
+    static const int order[4] = {MPPS_FMT_FP8, MPPS_FMT_BF16, MPPS_FMT_TF32, MPPS_FMT_BF16X3};
+    for (int i = 1; i <= r; ++i) {
+        int f = MPPS_FMT_FP64;
+        const bool floor_fp64 = (P.mode == MPPS_MIXED_NS && i <= P.floor_steps);
+        if (P.mode != MPPS_FIXED_FP64 && !floor_fp64) {
+            for (int k = 0; k < 4; ++k) {
+                const int F = order[k];
+                if (!((P.formats >> F) & 1u)) continue;
+                if (kUFmt[F] <= out->u[i] && (double)n * kAcc <= out->u[i]) { f = F; break; }
+            }
+        }
+        out->fmt[i] = f;
+    }
+    if (out->fold) out->fmt[r] = MPPS_FMT_NONE;
+    return MPPS_OK;
+}
+
+// eq. (3.8): ((s-1) D + sum d_i) / ((s+r-1) D), D = digits of u, d_i = digits of the
+// format that ran step i (0 for a step without a product).
+static double cost_ratio(const mpps_report& rp, double tol) {
+    const double D = -log10(tol);
+    double sum = 0.0;
+    for (int i = 1; i <= rp.r; ++i)
+        if (rp.fmt[i] >= 0) sum += std::min(D, -log10(kUFmt[rp.fmt[i]]));
+    const double den = (rp.s + rp.r - 1) * D;
+    return den > 0 ? ((rp.s - 1) * D + sum) / den : 1.0;
+}
+
+// ---- workspace ----------------------------------------------------------------------
+struct Arena {
+    char* base = nullptr;
+    size_t off = 0;
+    template <class T>
+    T* take(size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T* p = base ? (T*)(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+struct DevBuf {
+    void* p = nullptr;
+    cudaStream_t st = nullptr;
+    ~DevBuf() {
+        if (p) cudaFreeAsync(p, st);
+    }
+    mpps_status alloc(size_t bytes, cudaStream_t s) {
+        st = s;
+        if (bytes == 0) bytes = 256;
+        cudaError_t e = cudaMallocAsync(&p, bytes, s);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            cudaGetLastError();
+            set_error("cudaMallocAsync(%zu) failed: %s", bytes, cudaGetErrorString(e));
+            return e == cudaErrorMemoryAllocation ? MPPS_ENOMEM : MPPS_ECUDA;
+        }
+        return MPPS_OK;
+    }
+};
+
+static bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static int low_target_exp(int f) { return f == MPPS_FMT_FP8 ? 8 : 0; }
+
+static int exp_above(double x) {   // e with x < 2^e (x > 0), 0 otherwise
+    if (!(x > 0.0) || !isfinite(x)) return 0;
+    int e;
+    frexp(x, &e);
+    return e;
+}
+
+// ---- the PS evaluation --------------------------------------------------------------
+// Evaluates p(X) for a device batch; for expm, X = 2^-sigma A and sigma squarings follow.
+static mpps_status eval_device(const double* coeffs, int m, const double* dA, int n, int batch,
+                               const Pol& pol, double* dOut, mpps_report* rep, cudaStream_t st,
+                               bool expm) {
+    const long long nn = (long long)n * n;
+    // ---- m == 0: p = b_0 I
+    if (m == 0) {
+        Epilogue ep = epilogue_plain(dOut, nn);
+        ep.nt = 0;
+        ep.coef[0] = coeffs[0];
+        ep.alpha = 0.0;
+        mpps_status rc = launch_combine(n, batch, nullptr, 0, ep, st);
+        if (rc) return rc;
+        if (rep)
+            for (int b = 0; b < batch; ++b) {
+                double nb = fabs(coeffs[0]);
+                plan_one(0, n, &nb, 0.0, pol, &rep[b]);
+            }
+        return MPPS_OK;
+    }
+    const int s = pol.s > 0 ? std::min(pol.s, m) : ceil_sqrt_int(m);
+    if (s > MPPS_MAX_S || m / s > MPPS_MAX_R) {
+        set_error("m=%d with s=%d is outside the supported range (s<=%d, r<=%d)", m, s, MPPS_MAX_S,
+                  MPPS_MAX_R);
+        return MPPS_EINVAL;
+    }
+    const int r = m / s;
+    const bool fold = (m % s) == 0;
+    const int q = block_norms_count(m, s);
+    const long long pw_bs = (long long)s * nn;
+
+    // ---- phase-1 workspace (FP64 part)
+    Arena L;
+    double *d_coef, *pw, *Pb0, *Pb1, *partial, *norms;
+    int *d_sigma, *d_err, *d_bidx;
+    auto layout1 = [&](Arena& a) {
+        d_coef = a.take<double>(m + 1);
+        pw = a.take<double>((size_t)batch * pw_bs);
+        Pb0 = a.take<double>((size_t)batch * nn);
+        Pb1 = a.take<double>((size_t)batch * nn);
+        partial = a.take<double>(std::max(block_norms_partial_elems(n, batch, m, s),
+                                          norm1_partial_elems(n, batch)));
+        norms = a.take<double>((size_t)batch * q);
+        d_sigma = a.take<int>(batch);
+        d_err = a.take<int>(1);
+        d_bidx = a.take<int>((size_t)batch * 64);
+    };
+    layout1(L);
+    DevBuf ws1;
+    mpps_status rc = ws1.alloc(L.off, st);
+    if (rc) return rc;
+    L.base = (char*)ws1.p;
+    L.off = 0;
+    layout1(L);
+    MPPS_CUDA_TRY(cudaMemcpyAsync(d_coef, coeffs, sizeof(double) * (m + 1), cudaMemcpyHostToDevice, st));
+    MPPS_CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), st));
+
+    // ---- a1: scaling (expm) or plain copy into X_1
+    std::vector<int> sigma(batch, 0);
+    std::vector<double> h_norm(batch, 0.0);
+    if (expm) {
+        rc = launch_norm1(dA, nn, n, batch, partial, norms, st);
+        if (rc) return rc;
+        MPPS_CUDA_TRY(cudaMemcpyAsync(h_norm.data(), norms, sizeof(double) * batch,
+                                      cudaMemcpyDeviceToHost, st));
+        MPPS_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int b = 0; b < batch; ++b) {
+            const double a = h_norm[b];
+            int e = 0;
+            if (a > 1.0 && isfinite(a)) {
+                double f = frexp(a, &e);        // a = f 2^e, f in [0.5, 1)
+                if (f == 0.5) e -= 1;           // a a power of two: log2 a exactly
+            }
+            sigma[b] = e;                        // max(0, ceil(log2 ||A||_1))
+        }
+        MPPS_CUDA_TRY(cudaMemcpyAsync(d_sigma, sigma.data(), sizeof(int) * batch,
+                                      cudaMemcpyHostToDevice, st));
+        rc = launch_scale_copy(dA, nn, pw, pw_bs, n, batch, d_sigma, st);
+    } else {
+        rc = launch_scale_copy(dA, nn, pw, pw_bs, n, batch, nullptr, st);
+    }
+    if (rc) return rc;
+
+    // ---- a2: powers X_j = X_{j-1} X_1, FP64
+    for (int j = 2; j <= s; ++j) {
+        Epilogue ep = epilogue_plain(pw + (long long)(j - 1) * nn, pw_bs);
+        rc = launch_gemm_f64(pw + (long long)(j - 2) * nn, pw_bs, pw, pw_bs, n, batch, ep, st);
+        if (rc) return rc;
+    }
+
+    // ---- a3: ||B_i||_1, ||Y||_1, ||X||_1
+    rc = launch_block_norms(pw, pw_bs, n, batch, s, m, d_coef, partial, norms, st);
+    if (rc) return rc;
+    std::vector<double> hn((size_t)batch * q);
+    MPPS_CUDA_TRY(cudaMemcpyAsync(hn.data(), norms, sizeof(double) * hn.size(),
+                                  cudaMemcpyDeviceToHost, st));
+    MPPS_CUDA_TRY(cudaStreamSynchronize(st));
+
+    // ---- a4: plan per matrix; a batch runs each step in the most precise format any of
+    // its matrices asks for
+    std::vector<mpps_report> rp(batch);
+    Pol pol_s = pol;
+    pol_s.s = s;
+    for (int b = 0; b < batch; ++b) {
+        rc = plan_one(m, n, &hn[(size_t)b * q], hn[(size_t)b * q + r + 1], pol_s, &rp[b]);
+        if (rc) return rc;
+        rp[b].normX = hn[(size_t)b * q + r + 2];
+        rp[b].sigma = sigma[b];
+    }
+    int fmt[MPPS_MAX_R + 1];
+    for (int i = 1; i <= r; ++i) {
+        int f = MPPS_FMT_FP8;
+        for (int b = 0; b < batch; ++b) f = std::min(f, rp[b].fmt[i]);
+        fmt[i] = (fold && i == r) ? MPPS_FMT_NONE : f;
+    }
+    bool used[MPPS_NUM_FORMATS] = {false, false, false, false, false};
+    int max_es = 1;
+    for (int i = 1; i <= r; ++i)
+        if (is_low(fmt[i])) {
+            used[fmt[i]] = true;
+            max_es = std::max(max_es, low_elem_bytes(fmt[i]));
+        }
+    const bool any_low = used[1] || used[2] || used[3] || used[4];
+
+    // ---- phase-2 workspace: rounded copies and their power-of-two scales
+    const int lld = low_ld(n);
+    const long long low_bs = (long long)n * lld;
+    Arena L2;
+    void *Ylo_hi[MPPS_NUM_FORMATS] = {}, *Ylo_lo[MPPS_NUM_FORMATS] = {};
+    void *Pl_hi[2] = {}, *Pl_lo[2] = {};
+    double *d_sY, *d_sP, *d_alpha;
+    auto layout2 = [&](Arena& a) {
+        for (int f = 1; f < MPPS_NUM_FORMATS; ++f)
+            if (used[f]) {
+                Ylo_hi[f] = a.take<char>((size_t)batch * low_bs * low_elem_bytes(f));
+                if (f == MPPS_FMT_BF16X3) Ylo_lo[f] = a.take<char>((size_t)batch * low_bs * 2);
+            }
+        for (int k = 0; k < 2; ++k) {
+            Pl_hi[k] = a.take<char>(any_low ? (size_t)batch * low_bs * max_es : 0);
+            Pl_lo[k] = a.take<char>(used[MPPS_FMT_BF16X3] ? (size_t)batch * low_bs * 2 : 0);
+        }
+        // one contiguous block (filled by a single copy): sY | sP | alpha
+        d_sY = a.take<double>((size_t)(MPPS_NUM_FORMATS + 2 * (r + 1)) * batch);
+        d_sP = d_sY ? d_sY + (size_t)MPPS_NUM_FORMATS * batch : nullptr;
+        d_alpha = d_sP ? d_sP + (size_t)(r + 1) * batch : nullptr;
+    };
+    DevBuf ws2;
+    if (any_low) {
+        layout2(L2);
+        rc = ws2.alloc(L2.off, st);
+        if (rc) return rc;
+        L2.base = (char*)ws2.p;
+        L2.off = 0;
+        layout2(L2);
+        std::vector<double> hs((size_t)(MPPS_NUM_FORMATS + 2 * (r + 1)) * batch, 1.0);
+        double* h_sY = hs.data();
+        double* h_sP = h_sY + (size_t)MPPS_NUM_FORMATS * batch;
+        double* h_al = h_sP + (size_t)(r + 1) * batch;
+        for (int b = 0; b < batch; ++b) {
+            const double* eta = &hn[(size_t)b * q];
+            const double y = hn[(size_t)b * q + r + 1];
+            const int eY = exp_above(y);
+            for (int f = 1; f < MPPS_NUM_FORMATS; ++f)
+                h_sY[(size_t)f * batch + b] = ldexp(1.0, low_target_exp(f) - eY);
+            // beta_i = sum_{k>=i} ||B_k|| ||Y||^{k-i} >= ||P_i||_1 >= max |P_i|
+            double beta = 0.0;
+            for (int i = r; i >= 1; --i) {
+                beta = eta[i] + y * beta;
+                if (is_low(fmt[i])) {
+                    const int T = low_target_exp(fmt[i]);
+                    const int eP = exp_above(beta);
+                    h_sP[(size_t)i * batch + b] = ldexp(1.0, T - eP);
+                    h_al[(size_t)i * batch + b] = ldexp(1.0, eP + eY - 2 * T);
+                }
+            }
+        }
+        MPPS_CUDA_TRY(cudaMemcpyAsync(d_sY, hs.data(), sizeof(double) * hs.size(),
+                                      cudaMemcpyHostToDevice, st));
+        for (int f = 1; f < MPPS_NUM_FORMATS; ++f)
+            if (used[f]) {
+                rc = launch_convert(f, pw + (long long)(s - 1) * nn, pw_bs, n, batch, Ylo_hi[f],
+                                    Ylo_lo[f], low_bs, lld, d_sY + (size_t)f * batch, true, st);
+                if (rc) return rc;
+            }
+    }
+
+    // ---- a5/a6: Horner in Y with the block sums fused into the product epilogues
+    int sig_max = 0;
+    for (int b = 0; b < batch; ++b) sig_max = std::max(sig_max, sigma[b]);
+    double* Pbuf[2] = {Pb0, Pb1};
+    double* dst0 = (expm && sig_max > 0) ? Pb0 : dOut;
+    const double* Y = pw + (long long)(s - 1) * nn;
+
+    auto make_ep = [&](int i) {   // epilogue producing P_{i-1} = B_{i-1} + (...)
+        Epilogue ep = epilogue_plain((i - 1 == 0) ? dst0 : Pbuf[(i - 1) & 1], nn);
+        ep.nt = s - 1;
+        for (int j = 0; j < s; ++j) ep.coef[j] = coeffs[(i - 1) * s + j];
+        ep.pw = pw;
+        ep.pw_bstride = pw_bs;
+        if (i - 1 >= 1 && is_low(fmt[i - 1])) {
+            ep.low_fmt = fmt[i - 1];
+            ep.low_hi = Pl_hi[(i - 1) & 1];
+            ep.low_lo = Pl_lo[(i - 1) & 1];
+            ep.low_bstride = low_bs;
+            ep.lld = lld;
+            ep.low_scale_b = d_sP + (size_t)(i - 1) * batch;
+        }
+        return ep;
+    };
+
+    int i_start;
+    if (fold) {
+        // B_r = b_m I: P_{r-1} = B_{r-1} + b_m Y, no product
+        Epilogue ep = make_ep(r);
+        ep.alpha = coeffs[m];
+        rc = launch_combine(n, batch, Y, pw_bs, ep, st);
+        i_start = r - 1;
+    } else {
+        // P_r = B_r = sum_{j<=m-sr} b_{sr+j} X_j
+        Epilogue ep = epilogue_plain(Pbuf[r & 1], nn);
+        ep.nt = m - s * r;
+        for (int j = 0; j <= ep.nt; ++j) ep.coef[j] = coeffs[s * r + j];
+        ep.pw = pw;
+        ep.pw_bstride = pw_bs;
+        ep.alpha = 0.0;
+        if (is_low(fmt[r])) {
+            ep.low_fmt = fmt[r];
+            ep.low_hi = Pl_hi[r & 1];
+            ep.low_lo = Pl_lo[r & 1];
+            ep.low_bstride = low_bs;
+            ep.lld = lld;
+            ep.low_scale_b = d_sP + (size_t)r * batch;
+        }
+        rc = launch_combine(n, batch, nullptr, 0, ep, st);
+        i_start = r;
+    }
+    if (rc) return rc;
+    for (int i = i_start; i >= 1; --i) {
+        Epilogue ep = make_ep(i);
+        if (fmt[i] == MPPS_FMT_FP64) {
+            rc = launch_gemm_f64(Pbuf[i & 1], nn, Y, pw_bs, n, batch, ep, st);
+        } else {
+            ep.alpha_b = d_alpha + (size_t)i * batch;
+            rc = launch_gemm_tc(fmt[i], Pl_hi[i & 1], Pl_lo[i & 1], Ylo_hi[fmt[i]], Ylo_lo[fmt[i]],
+                                low_bs, low_bs, lld, n, batch, ep, d_err, st);
+        }
+        if (rc) return rc;
+    }
+
+    // ---- a7: squarings (eq. (3.6)), FP64, per-matrix counts
+    if (expm && sig_max > 0) {
+        std::vector<int> lists((size_t)sig_max * batch);
+        std::vector<int> counts(sig_max, 0);
+        for (int k = 0; k < sig_max; ++k)
+            for (int b = 0; b < batch; ++b)
+                if (sigma[b] > k) lists[(size_t)k * batch + counts[k]++] = b;
+        int* d_lists = d_bidx;
+        DevBuf extra;
+        if ((size_t)sig_max * batch > (size_t)batch * 64) {
+            rc = extra.alloc(sizeof(int) * lists.size(), st);
+            if (rc) return rc;
+            d_lists = (int*)extra.p;
+        }
+        MPPS_CUDA_TRY(cudaMemcpyAsync(d_lists, lists.data(), sizeof(int) * lists.size(),
+                                      cudaMemcpyHostToDevice, st));
+        for (int k = 0; k < sig_max; ++k) {
+            Epilogue ep = epilogue_plain(Pbuf[(k + 1) & 1], nn);
+            rc = launch_gemm_f64(Pbuf[k & 1], nn, Pbuf[k & 1], nn, n, counts[k], ep, st,
+                                 d_lists + (size_t)k * batch);
+            if (rc) return rc;
+        }
+        rc = launch_select_copy(Pb0, Pb1, d_sigma, dOut, n, batch, st);
+        if (rc) return rc;
+    }
+
+    if (any_low) {
+        int h_err = 0;
+        MPPS_CUDA_TRY(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        MPPS_CUDA_TRY(cudaStreamSynchronize(st));
+        if (h_err) {
+            set_error("a bounded wait in the tensor-core product timed out");
+            return MPPS_ETIMEOUT;
+        }
+    }
+
+    if (rep) {
+        for (int b = 0; b < batch; ++b) {
+            mpps_report& R = rp[b];
+            for (int i = 1; i <= r; ++i) R.fmt[i] = fmt[i];
+            for (int f = 0; f <= MPPS_NUM_FORMATS; ++f) R.gemms[f] = 0;
+            R.gemms[MPPS_FMT_FP64] += s - 1;
+            for (int i = 1; i <= r; ++i)
+                if (fmt[i] >= 0) R.gemms[fmt[i]] += 1;
+            R.gemms[MPPS_NUM_FORMATS] = sigma[b];
+            R.cost_ratio = cost_ratio(R, pol.tol);
+            rep[b] = R;
+        }
+    }
+    return MPPS_OK;
+}
+
+// Host/device marshalling around a device implementation.
+struct Staged {
+    const double* dev = nullptr;
+    DevBuf buf;
+};
+
+static mpps_status stage_in(const double* p, size_t elems, cudaStream_t st, Staged& out) {
+    if (is_device_ptr(p)) {
+        out.dev = p;
+        return MPPS_OK;
+    }
+    mpps_status rc = out.buf.alloc(elems * sizeof(double), st);
+    if (rc) return rc;
+    MPPS_CUDA_TRY(cudaMemcpyAsync(out.buf.p, p, elems * sizeof(double), cudaMemcpyHostToDevice, st));
+    out.dev = (const double*)out.buf.p;
+    return MPPS_OK;
+}
+
+}  // namespace mpps
+
+using namespace mpps;
+
+extern "C" {
+
+void mpps_policy_default(mpps_policy* p) {
+    if (!p) return;
+    p->mode = MPPS_MIXED_NS;
+    p->tol = 0x1p-53;
+    p->delta = 10.0;
+    p->s = 0;
+    p->formats = 0x1Fu;
+    p->fp64_floor_steps = 2;
+}
+
+const char* mpps_last_error(void) { return g_err; }
+
+const char* mpps_version(void) { return "mpps 0.1 (sm_103a)"; }
+
+mpps_status mpps_plan(int m, int n, const double* normB, double normY, const mpps_policy* policy,
+                      mpps_report* out) {
+    clear_error();
+    if (m < 0 || n <= 0 || !normB || !out) {
+        set_error("mpps_plan: invalid argument");
+        return MPPS_EINVAL;
+    }
+    Pol P = resolve(policy);
+    mpps_status rc = plan_one(m, n, normB, normY, P, out);
+    if (rc == MPPS_OK) out->cost_ratio = cost_ratio(*out, P.tol);
+    return rc;
+}
+
+static mpps_status check_sizes(int n, int batch) {
+    if (n <= 0 || batch < 0 || batch > 65535) {
+        set_error("invalid size: n=%d batch=%d (need n>0, 0<=batch<=65535)", n, batch);
+        return MPPS_EINVAL;
+    }
+    return MPPS_OK;
+}
+
+static mpps_status run_eval(const double* coeffs, int m, const double* A, int n, int batch,
+                            const mpps_policy* policy, double* out, mpps_report* rep, void* stream,
+                            bool expm) {
+    clear_error();
+    mpps_status rc = check_sizes(n, batch);
+    if (rc) return rc;
+    if (m < 0 || !coeffs || !A || !out) {
+        set_error("invalid argument (m=%d, null pointer?)", m);
+        return MPPS_EINVAL;
+    }
+    if (batch == 0) return MPPS_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t elems = (size_t)batch * n * n;
+    Staged a;
+    rc = stage_in(A, elems, st, a);
+    if (rc) return rc;
+    const bool out_dev = is_device_ptr(out);
+    DevBuf ob;
+    double* dOut = out;
+    if (!out_dev) {
+        rc = ob.alloc(elems * sizeof(double), st);
+        if (rc) return rc;
+        dOut = (double*)ob.p;
+    }
+    Pol P = resolve(policy);
+    rc = eval_device(coeffs, m, a.dev, n, batch, P, dOut, rep, st, expm);
+    if (rc) return rc;
+    if (!out_dev) {
+        MPPS_CUDA_TRY(cudaMemcpyAsync(out, dOut, elems * sizeof(double), cudaMemcpyDeviceToHost, st));
+        MPPS_CUDA_TRY(cudaStreamSynchronize(st));
+    } else if (!is_device_ptr(A)) {
+        MPPS_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    return MPPS_OK;
+}
+
+mpps_status ps_eval(const double* coeffs, int m, const double* A, int n, int batch,
+                    const mpps_policy* policy, double* out, mpps_report* rep, void* stream) {
+    return run_eval(coeffs, m, A, n, batch, policy, out, rep, stream, false);
+}
+
+mpps_status expm_taylor_ss(const double* A, int n, int batch, int m, const mpps_policy* policy,
+                           double* out, mpps_report* rep, void* stream) {
+    if (m <= 0) m = 30;
+    if (m > 170) {
+        set_error("expm_taylor_ss: degree m=%d too large", m);
+        return MPPS_EINVAL;
+    }
+    // b_i = 1/i!: each quotient in extended precision, then rounded once to double
+    std::vector<double> c(m + 1);
+    long double f = 1.0L;
+    for (int i = 0; i <= m; ++i) {
+        if (i > 0) f /= (long double)i;
+        c[i] = (double)f;
+    }
+    return run_eval(c.data(), m, A, n, batch, policy, out, rep, stream, true);
+}
+
+mpps_status mpps_matmul(const double* A, const double* B, double* C, int n, int batch, int format,
+                        void* stream) {
+    clear_error();
+    mpps_status rc = check_sizes(n, batch);
+    if (rc) return rc;
+    if (!A || !B || !C || format < MPPS_FMT_FP64 || format > MPPS_FMT_FP8) {
+        set_error("mpps_matmul: invalid argument");
+        return MPPS_EINVAL;
+    }
+    if (batch == 0) return MPPS_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long nn = (long long)n * n;
+    const size_t elems = (size_t)batch * nn;
+    Staged a, b;
+    if ((rc = stage_in(A, elems, st, a))) return rc;
+    if ((rc = stage_in(B, elems, st, b))) return rc;
+    const bool c_dev = is_device_ptr(C);
+    DevBuf cb;
+    double* dC = C;
+    if (!c_dev) {
+        if ((rc = cb.alloc(elems * sizeof(double), st))) return rc;
+        dC = (double*)cb.p;
+    }
+    Epilogue ep = epilogue_plain(dC, nn);
+    if (format == MPPS_FMT_FP64) {
+        rc = launch_gemm_f64(a.dev, nn, b.dev, nn, n, batch, ep, st);
+        if (rc) return rc;
+    } else {
+        const int lld = low_ld(n);
+        const long long low_bs = (long long)n * lld;
+        const int es = low_elem_bytes(format);
+        const bool x3 = format == MPPS_FMT_BF16X3;
+        Arena L;
+        char *ahi, *alo, *bhi, *blo;
+        double *ma, *mb, *sa, *sb, *un;
+        int* err;
+        auto lay = [&](Arena& z) {
+            ahi = z.take<char>((size_t)batch * low_bs * es);
+            alo = z.take<char>(x3 ? (size_t)batch * low_bs * es : 0);
+            bhi = z.take<char>((size_t)batch * low_bs * es);
+            blo = z.take<char>(x3 ? (size_t)batch * low_bs * es : 0);
+            ma = z.take<double>(batch);
+            mb = z.take<double>(batch);
+            sa = z.take<double>(batch);
+            sb = z.take<double>(batch);
+            un = z.take<double>(batch);
+            err = z.take<int>(1);
+        };
+        lay(L);
+        DevBuf ws;
+        if ((rc = ws.alloc(L.off, st))) return rc;
+        L.base = (char*)ws.p;
+        L.off = 0;
+        lay(L);
+        MPPS_CUDA_TRY(cudaMemsetAsync(ma, 0, sizeof(double) * batch, st));
+        MPPS_CUDA_TRY(cudaMemsetAsync(mb, 0, sizeof(double) * batch, st));
+        MPPS_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+        if ((rc = launch_maxabs(a.dev, nn, n, batch, ma, st))) return rc;
+        if ((rc = launch_maxabs(b.dev, nn, n, batch, mb, st))) return rc;
+        if ((rc = launch_pow2_scales(ma, mb, batch, low_target_exp(format), sa, sb, un, st))) return rc;
+        if ((rc = launch_convert(format, a.dev, nn, n, batch, ahi, alo, low_bs, lld, sa, false, st)))
+            return rc;
+        if ((rc = launch_convert(format, b.dev, nn, n, batch, bhi, blo, low_bs, lld, sb, true, st)))
+            return rc;
+        ep.alpha_b = un;
+        rc = launch_gemm_tc(format, ahi, alo, bhi, blo, low_bs, low_bs, lld, n, batch, ep, err, st);
+        if (rc) return rc;
+        int h_err = 0;
+        MPPS_CUDA_TRY(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        MPPS_CUDA_TRY(cudaStreamSynchronize(st));
+        if (h_err) {
+            set_error("a bounded wait in the tensor-core product timed out");
+            return MPPS_ETIMEOUT;
+        }
+    }
+    if (!c_dev) {
+        MPPS_CUDA_TRY(cudaMemcpyAsync(C, dC, elems * sizeof(double), cudaMemcpyDeviceToHost, st));
+        MPPS_CUDA_TRY(cudaStreamSynchronize(st));
+    } else if (!is_device_ptr(A) || !is_device_ptr(B)) {
+        MPPS_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    return MPPS_OK;
+}
+
+// Reverse mode through the PS steps (FP64).  Forward: powers X_1..X_s and Horner iterates
+// P_r..P_1 are kept.  Backward (f = <G, P_0>):
+//   Pbar_0 = G;  for i = 1..r: Bbar_{i-1} = Pbar_{i-1};  Ybar += P_i^T Pbar_{i-1};
+//                              Pbar_i = Pbar_{i-1} Y^T;   (fold: step r has P_r = b_m I,
+//                              so Ybar += b_m Pbar_{r-1} and the loop stops)
+//   Bbar_r = Pbar_r;  Xbar_j += sum_i b_{si+j} Bbar_i;  Xbar_s += Ybar;
+//   for j = s..2: Xbar_{j-1} += Xbar_j X_1^T;  Xbar_1 += X_{j-1}^T Xbar_j;   grad = Xbar_1.
+mpps_status ps_eval_adjoint(const double* coeffs, int m, const double* A, const double* G, int n,
+                            int batch, double* gradA, void* stream) {
+    clear_error();
+    mpps_status rc = check_sizes(n, batch);
+    if (rc) return rc;
+    if (m < 0 || !coeffs || !A || !G || !gradA) {
+        set_error("ps_eval_adjoint: invalid argument");
+        return MPPS_EINVAL;
+    }
+    if (batch == 0) return MPPS_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long nn = (long long)n * n;
+    const size_t elems = (size_t)batch * nn;
+    Staged a, g;
+    if ((rc = stage_in(A, elems, st, a))) return rc;
+    if ((rc = stage_in(G, elems, st, g))) return rc;
+    const bool o_dev = is_device_ptr(gradA);
+    DevBuf ob;
+    double* dGrad = gradA;
+    if (!o_dev) {
+        if ((rc = ob.alloc(elems * sizeof(double), st))) return rc;
+        dGrad = (double*)ob.p;
+    }
+    if (m == 0) {
+        MPPS_CUDA_TRY(cudaMemsetAsync(dGrad, 0, elems * sizeof(double), st));
+    } else {
+        const int s = ceil_sqrt_int(m);
+        const int r = m / s;
+        const bool fold = (m % s) == 0;
+        const long long pw_bs = (long long)s * nn;
+        Arena L;
+        double *pw, *xbar, *Pst, *Ybar, *Pbar0, *Pbar1, *Yt, *X1t, *T;
+        auto lay = [&](Arena& z) {
+            pw = z.take<double>((size_t)batch * pw_bs);
+            xbar = z.take<double>((size_t)batch * pw_bs);
+            Pst = z.take<double>((size_t)batch * nn * (r + 1));   // P_i at slot i
+            Ybar = z.take<double>(elems);
+            Pbar0 = z.take<double>(elems);
+            Pbar1 = z.take<double>(elems);
+            Yt = z.take<double>(elems);
+            X1t = z.take<double>(elems);
+            T = z.take<double>(elems);
+        };
+        lay(L);
+        DevBuf ws;
+        if ((rc = ws.alloc(L.off, st))) return rc;
+        L.base = (char*)ws.p;
+        L.off = 0;
+        lay(L);
+        auto P_at = [&](int i) { return Pst + (size_t)i * batch * nn; };
+        // forward
+        if ((rc = launch_scale_copy(a.dev, nn, pw, pw_bs, n, batch, nullptr, st))) return rc;
+        for (int j = 2; j <= s; ++j) {
+            Epilogue ep = epilogue_plain(pw + (long long)(j - 1) * nn, pw_bs);
+            if ((rc = launch_gemm_f64(pw + (long long)(j - 2) * nn, pw_bs, pw, pw_bs, n, batch, ep, st)))
+                return rc;
+        }
+        const double* Y = pw + (long long)(s - 1) * nn;
+        int i_top;   // highest Horner iterate that is a real matrix
+        if (fold) {
+            Epilogue ep = epilogue_plain(P_at(r - 1), nn);
+            ep.nt = s - 1;
+            for (int j = 0; j < s; ++j) ep.coef[j] = coeffs[(r - 1) * s + j];
+            ep.pw = pw; ep.pw_bstride = pw_bs; ep.alpha = coeffs[m];
+            if ((rc = launch_combine(n, batch, Y, pw_bs, ep, st))) return rc;
+            i_top = r - 1;
+        } else {
+            Epilogue ep = epilogue_plain(P_at(r), nn);
+            ep.nt = m - s * r;
+            for (int j = 0; j <= ep.nt; ++j) ep.coef[j] = coeffs[s * r + j];
+            ep.pw = pw; ep.pw_bstride = pw_bs; ep.alpha = 0.0;
+            if ((rc = launch_combine(n, batch, nullptr, 0, ep, st))) return rc;
+            i_top = r;
+        }
+        for (int i = i_top; i >= 2; --i) {   // P_{i-1} = B_{i-1} + P_i Y (P_0 not needed)
+            Epilogue ep = epilogue_plain(P_at(i - 1), nn);
+            ep.nt = s - 1;
+            for (int j = 0; j < s; ++j) ep.coef[j] = coeffs[(i - 1) * s + j];
+            ep.pw = pw; ep.pw_bstride = pw_bs;
+            if ((rc = launch_gemm_f64(P_at(i), nn, Y, pw_bs, n, batch, ep, st))) return rc;
+        }
+        // backward
+        MPPS_CUDA_TRY(cudaMemsetAsync(xbar, 0, sizeof(double) * batch * pw_bs, st));
+        MPPS_CUDA_TRY(cudaMemsetAsync(Ybar, 0, elems * sizeof(double), st));
+        // Y^T and X_1^T (strided power table -> contiguous copies first)
+        if ((rc = launch_scale_copy(Y, pw_bs, T, nn, n, batch, nullptr, st))) return rc;
+        if ((rc = launch_transpose(T, Yt, n, batch, st))) return rc;
+        if ((rc = launch_scale_copy(pw, pw_bs, T, nn, n, batch, nullptr, st))) return rc;
+        if ((rc = launch_transpose(T, X1t, n, batch, st))) return rc;
+        double* Pbar[2] = {Pbar0, Pbar1};
+        if ((rc = launch_scale_copy(g.dev, nn, Pbar[0], nn, n, batch, nullptr, st))) return rc;
+        int cur = 0;
+        for (int i = 1; i <= r; ++i) {
+            // Bbar_{i-1} = Pbar_{i-1}: Xbar_j += b_{(i-1)s+j} Pbar for j = 1..s-1
+            double c[MPPS_MAX_S + 1];
+            for (int j = 0; j < s; ++j) c[j] = coeffs[(i - 1) * s + j];
+            if ((rc = launch_axpy_blocks(xbar, pw_bs, n, batch, s - 1, c, Pbar[cur], nn, st))) return rc;
+            if (fold && i == r) {
+                // P_r = b_m I: Ybar += b_m Pbar_{r-1}
+                Epilogue ep = epilogue_plain(Ybar, nn);
+                ep.alpha = coeffs[m];
+                ep.add = Ybar; ep.add_bstride = nn; ep.add_coef = 1.0;
+                if ((rc = launch_combine(n, batch, Pbar[cur], nn, ep, st))) return rc;
+                cur = -1;
+                break;
+            }
+            // Ybar += P_i^T Pbar_{i-1}
+            if ((rc = launch_transpose(P_at(i), T, n, batch, st))) return rc;
+            {
+                Epilogue ep = epilogue_plain(Ybar, nn);
+                ep.add = Ybar; ep.add_bstride = nn; ep.add_coef = 1.0;
+                if ((rc = launch_gemm_f64(T, nn, Pbar[cur], nn, n, batch, ep, st))) return rc;
+            }
+            // Pbar_i = Pbar_{i-1} Y^T
+            {
+                Epilogue ep = epilogue_plain(Pbar[cur ^ 1], nn);
+                if ((rc = launch_gemm_f64(Pbar[cur], nn, Yt, nn, n, batch, ep, st))) return rc;
+            }
+            cur ^= 1;
+        }
+        if (cur >= 0) {   // not folded: Bbar_r = Pbar_r, B_r = sum_{j<=m-sr} b_{sr+j} X_j
+            double c[MPPS_MAX_S + 1];
+            const int t = m - s * r;
+            for (int j = 0; j <= t; ++j) c[j] = coeffs[s * r + j];
+            if ((rc = launch_axpy_blocks(xbar, pw_bs, n, batch, t, c, Pbar[cur], nn, st))) return rc;
+        }
+        // Xbar_s += Ybar
+        {
+            double c[MPPS_MAX_S + 1] = {0};
+            double* xs = xbar + (long long)(s - 1) * nn;
+            c[1] = 1.0;
+            if ((rc = launch_axpy_blocks(xs, pw_bs, n, batch, 1, c, Ybar, nn, st))) return rc;
+        }
+        // powers: X_j = X_{j-1} X_1, j = s..2
+        for (int j = s; j >= 2; --j) {
+            double* xj = xbar + (long long)(j - 1) * nn;
+            double* xjm = xbar + (long long)(j - 2) * nn;
+            // Xbar_{j-1} += Xbar_j X_1^T
+            Epilogue e1 = epilogue_plain(xjm, pw_bs);
+            e1.add = xjm; e1.add_bstride = pw_bs; e1.add_coef = 1.0;
+            if ((rc = launch_gemm_f64(xj, pw_bs, X1t, nn, n, batch, e1, st))) return rc;
+            // Xbar_1 += X_{j-1}^T Xbar_j
+            if ((rc = launch_scale_copy(pw + (long long)(j - 2) * nn, pw_bs, T, nn, n, batch, nullptr, st)))
+                return rc;
+            if ((rc = launch_transpose(T, Pbar0, n, batch, st))) return rc;
+            Epilogue e2 = epilogue_plain(xbar, pw_bs);
+            e2.add = xbar; e2.add_bstride = pw_bs; e2.add_coef = 1.0;
+            if ((rc = launch_gemm_f64(Pbar0, nn, xj, pw_bs, n, batch, e2, st))) return rc;
+        }
+        if ((rc = launch_scale_copy(xbar, pw_bs, dGrad, nn, n, batch, nullptr, st))) return rc;
+    }
+    if (!o_dev) {
+        MPPS_CUDA_TRY(cudaMemcpyAsync(gradA, dGrad, elems * sizeof(double), cudaMemcpyDeviceToHost, st));
+        MPPS_CUDA_TRY(cudaStreamSynchronize(st));
+    } else if (!is_device_ptr(A) || !is_device_ptr(G)) {
+        MPPS_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    return MPPS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,206 @@
+// common.cuh -- shared declarations of the mpps CUDA library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <stdint.h>
+
+#include "../../include/mpps.h"
+
+namespace mpps {
+
+// ---- error reporting ------------------------------------------------------------
+void set_error(const char* fmt, ...);
+void clear_error();
+
+#define MPPS_CUDA_TRY(call)                                                            \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess) {                                                       \
+            ::mpps::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),   \
+                              __FILE__, __LINE__);                                     \
+            return MPPS_ECUDA;                                                         \
+        }                                                                              \
+    } while (0)
+
+#define MPPS_LAUNCH_CHECK()                                                            \
+    do {                                                                               \
+        cudaError_t e_ = cudaGetLastError();                                           \
+        if (e_ != cudaSuccess) {                                                       \
+            ::mpps::set_error("kernel launch failed: %s (%s:%d)", cudaGetErrorString(e_), \
+                              __FILE__, __LINE__);                                     \
+            return MPPS_ECUDA;                                                         \
+        }                                                                              \
+    } while (0)
+
+// ---- optional launch timing (profile.cu) -----------------------------------------
+// RAII: when profiling is enabled, records CUDA events on `st` around the launches made
+// while the scope is alive, tagged with a kernel class (MPPS_PROF_*).
+struct ProfScope {
+    ProfScope(int cls, cudaStream_t st);
+    ~ProfScope();
+    int cls;
+    cudaStream_t st;
+    cudaEvent_t a, b;
+    bool on;
+};
+
+// ---- fused epilogue of every product ---------------------------------------------
+// out = alpha * (A B) + sum_{j=0}^{nt} coef[j] X_j  with X_0 = I and X_j the j-th power
+// stored at pw + (j-1) n^2 (+ b * pw_bstride for batch element b).  nt = -1: no sum.
+// Optionally also writes a rounded copy of out (times low_scale) for the next product:
+// row-major with leading dimension lld, in format low_fmt (BF16X3 writes hi and lo).
+struct Epilogue {
+    int nt;
+    double coef[MPPS_MAX_S + 1];
+    const double* pw;
+    long long pw_bstride;
+    double alpha;                 // used when alpha_b is null
+    const double* alpha_b;        // per batch element (device), or null
+    const double* add;            // optional addend: v += add_coef * add[b][row][col]
+    long long add_bstride;
+    double add_coef;
+    double* out;
+    long long out_bstride;
+    int low_fmt;
+    void* low_hi;
+    void* low_lo;
+    long long low_bstride;
+    int lld;
+    double low_scale;             // used when low_scale_b is null
+    const double* low_scale_b;    // per batch element (device), or null
+};
+
+inline Epilogue epilogue_plain(double* out, long long out_bstride) {
+    Epilogue e;
+    e.nt = -1;
+    for (int j = 0; j <= MPPS_MAX_S; ++j) e.coef[j] = 0.0;
+    e.pw = nullptr; e.pw_bstride = 0; e.alpha = 1.0; e.alpha_b = nullptr;
+    e.add = nullptr; e.add_bstride = 0; e.add_coef = 0.0;
+    e.out = out; e.out_bstride = out_bstride;
+    e.low_fmt = MPPS_FMT_NONE; e.low_hi = nullptr; e.low_lo = nullptr;
+    e.low_bstride = 0; e.lld = 0; e.low_scale = 1.0; e.low_scale_b = nullptr;
+    return e;
+}
+
+// ---- rounding of one FP64 value to a product format ----------------------------
+// (round to nearest; TF32 is produced as an FP32 bit pattern with the low 13 bits
+// cleared after round-to-nearest-even on them)
+__device__ __forceinline__ float to_tf32(double v) {
+    float f = (float)v;
+    uint32_t u = __float_as_uint(f);
+    if ((u & 0x7f800000u) != 0x7f800000u) {        // finite: RNE on the 13 dropped bits
+        u += 0x0fffu + ((u >> 13) & 1u);
+        u &= 0xffffe000u;
+    }
+    return __uint_as_float(u);
+}
+
+__device__ __forceinline__ void store_low(int fmt, void* hi, void* lo, long long idx, double v) {
+    if (fmt == MPPS_FMT_BF16) {
+        ((__nv_bfloat16*)hi)[idx] = __double2bfloat16(v);
+    } else if (fmt == MPPS_FMT_BF16X3) {
+        __nv_bfloat16 h = __double2bfloat16(v);
+        ((__nv_bfloat16*)hi)[idx] = h;
+        ((__nv_bfloat16*)lo)[idx] = __double2bfloat16(v - (double)__bfloat162float(h));
+    } else if (fmt == MPPS_FMT_TF32) {
+        ((float*)hi)[idx] = to_tf32(v);
+    } else if (fmt == MPPS_FMT_FP8) {
+        ((__nv_fp8_storage_t*)hi)[idx] = __nv_cvt_double_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+    }
+}
+
+// Epilogue value for element (row, col) of batch element b, given the product acc.
+__device__ __forceinline__ double epilogue_value(const Epilogue& ep, int b, int row, int col,
+                                                 int n, double acc) {
+    double v = (ep.alpha_b ? ep.alpha_b[b] : ep.alpha) * acc;
+    if (ep.nt >= 0) {
+        if (row == col) v += ep.coef[0];
+        const double* base = ep.pw + (long long)b * ep.pw_bstride + (long long)row * n + col;
+        const long long nn = (long long)n * n;
+        for (int j = 1; j <= ep.nt; ++j) v += ep.coef[j] * __ldg(base + (long long)(j - 1) * nn);
+    }
+    if (ep.add) v += ep.add_coef * ep.add[(long long)b * ep.add_bstride + (long long)row * n + col];
+    return v;
+}
+
+__device__ __forceinline__ void epilogue_store(const Epilogue& ep, int b, int row, int col, int n,
+                                               double v) {
+    ep.out[(long long)b * ep.out_bstride + (long long)row * n + col] = v;
+    if (ep.low_fmt != MPPS_FMT_NONE)
+        store_low(ep.low_fmt, ep.low_hi, ep.low_lo,
+                  (long long)b * ep.low_bstride + (long long)row * ep.lld + col,
+                  v * (ep.low_scale_b ? ep.low_scale_b[b] : ep.low_scale));
+}
+
+// ---- launchers (defined in the .cu files) ----------------------------------------
+// FP64 product C = A B on the FP64 tensor pipe (DMMA), batch-strided, fused epilogue.
+// bidx (device, optional): grid slice z processes matrix bidx[z] (for batches in which only
+// some matrices take a step, e.g. squarings with per-matrix counts).
+mpps_status launch_gemm_f64(const double* A, long long a_bs, const double* B, long long b_bs,
+                            int n, int batch, const Epilogue& ep, cudaStream_t st,
+                            const int* bidx = nullptr);
+
+// Low-precision product on tcgen05: A_low (row-major, K-major, ld = lld) times B_low^T
+// where B_low holds B transposed (row j = column j of B), in format fmt.  acc * alpha is
+// passed to the epilogue (alpha undoes the operand scales).
+mpps_status launch_gemm_tc(int fmt, const void* A_hi, const void* A_lo, const void* Bt_hi,
+                           const void* Bt_lo, long long a_bs, long long b_bs, int lld, int n,
+                           int batch, const Epilogue& ep, int* d_err, cudaStream_t st);
+
+// Element size in bytes of a low-precision operand copy.
+inline int low_elem_bytes(int fmt) {
+    switch (fmt) {
+        case MPPS_FMT_BF16: case MPPS_FMT_BF16X3: return 2;
+        case MPPS_FMT_TF32: return 4;
+        case MPPS_FMT_FP8: return 1;
+        default: return 8;
+    }
+}
+// Leading dimension of low-precision copies: n rounded up to 64 elements (keeps every
+// row 16-byte aligned for TMA and the K extent a whole number of 128-byte rows).
+inline int low_ld(int n) { return (n + 63) / 64 * 64; }
+
+// Elementwise helpers (elementwise.cu).
+// out = ep.alpha * extra + sum_j ep.coef[j] X_j  (extra may be null: treated as 0).
+mpps_status launch_combine(int n, int batch, const double* extra, long long extra_bs,
+                           const Epilogue& ep, cudaStream_t st);
+// ||B_i||_1 (i = 0..r), ||X^s||_1, ||X||_1 per matrix from the power table pw (X_1..X_s,
+// batch stride pw_bs) and the device copy of the coefficients b_0..b_m.  partial must hold
+// block_norms_partial_elems(...) doubles; norms gets block_norms_count(m, s) per matrix.
+int block_norms_count(int m, int s);
+size_t block_norms_partial_elems(int n, int batch, int m, int s);
+mpps_status launch_block_norms(const double* pw, long long pw_bs, int n, int batch, int s,
+                               int m, const double* d_coeffs, double* partial, double* norms,
+                               cudaStream_t st);
+// ||M||_1 per matrix (partial: norm1_partial_elems doubles).
+size_t norm1_partial_elems(int n, int batch);
+mpps_status launch_norm1(const double* M, long long bs, int n, int batch, double* partial,
+                         double* norms, cudaStream_t st);
+// X = 2^-sigma[b] A (exact power-of-two scaling; d_sigma null -> plain copy).
+mpps_status launch_scale_copy(const double* A, long long a_bs, double* X, long long x_bs, int n,
+                              int batch, const int* d_sigma, cudaStream_t st);
+// out[b] = (sigma[b] odd ? q1 : q0)[b]  (all contiguous, stride n*n).
+mpps_status launch_select_copy(const double* q0, const double* q1, const int* d_sigma, double* out,
+                               int n, int batch, cudaStream_t st);
+// Rounded copies (times scale[b], or 1 if scale is null) for the low-precision products:
+// convert keeps the layout, convert_t writes the transpose (row j = column j).
+mpps_status launch_convert(int fmt, const double* M, long long bs, int n, int batch, void* hi,
+                           void* lo, long long low_bs, int lld, const double* d_scale,
+                           bool transpose, cudaStream_t st);
+// max_ij |M_ij| per matrix, written to out[b] (out must be zeroed first).
+mpps_status launch_maxabs(const double* M, long long bs, int n, int batch, double* out,
+                          cudaStream_t st);
+// For each matrix b: scale[b] = 2^(target - e) and unscale... (power-of-two operand scales)
+mpps_status launch_pow2_scales(const double* maxabs_a, const double* maxabs_b, int batch,
+                               int target_exp, double* scale_a, double* scale_b,
+                               double* unscale, cudaStream_t st);
+// X_j += c_j * G for j = 1..t (power-table adjoint of a block sum); c is a host array.
+mpps_status launch_axpy_blocks(double* xbar, long long xbar_bs, int n, int batch, int t,
+                               const double* c, const double* G, long long g_bs,
+                               cudaStream_t st);
+// At = A^T per matrix.
+mpps_status launch_transpose(const double* A, double* At, int n, int batch, cudaStream_t st);
+
+}  // namespace mpps

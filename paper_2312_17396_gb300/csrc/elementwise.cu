@@ -1,0 +1,340 @@
+// elementwise.cu -- HBM-bound steps of the PS evaluation: block sums B_i (eq. (1.1)),
+// their 1-norms (the inputs of eq. (2.8)), exact power-of-two scaling (eq. (3.6)),
+// rounded operand copies for the low-precision products, and small reductions.
+#include "common.cuh"
+
+#include <math.h>
+
+namespace mpps {
+
+namespace {
+
+constexpr int kColsPerBlock = 128;   // one thread per column (coalesced row reads)
+constexpr int kRowsPerChunk = 64;    // rows summed by one thread before writing a partial
+
+__device__ __forceinline__ double block_max(double v) {
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    int nw = (blockDim.x + 31) >> 5;
+    v = (threadIdx.x < nw) ? red[threadIdx.x] : 0.0;
+    if (w == 0)
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;   // valid in thread 0
+}
+
+// Partial column sums of |B_i| (i = 0..r), |X_s| and |X_1| over one chunk of rows.
+// B_i = sum_{j=0}^{top_i} b_{si+j} X_j, top_i = s-1 (i < r), m - s r (i = r); X_0 = I.
+__global__ void k_block_norms_partial(const double* __restrict__ pw, long long pw_bs, int n,
+                                      int s, int m, const double* __restrict__ coef,
+                                      double* __restrict__ partial) {
+    const int col = blockIdx.x * kColsPerBlock + threadIdx.x;
+    const int chunk = blockIdx.y, chunks = gridDim.y, b = blockIdx.z;
+    const int r = m / s, q = r + 3;
+    if (col >= n) return;
+    double acc[MPPS_MAX_R + 3];
+    double x[MPPS_MAX_S + 1];
+    for (int t = 0; t < q; ++t) acc[t] = 0.0;
+    const long long nn = (long long)n * n;
+    const double* base = pw + (long long)b * pw_bs;
+    const int r0 = chunk * kRowsPerChunk, r1 = min(n, r0 + kRowsPerChunk);
+    for (int row = r0; row < r1; ++row) {
+        x[0] = (row == col) ? 1.0 : 0.0;
+        for (int j = 1; j <= s; ++j) x[j] = __ldg(base + (long long)(j - 1) * nn + (long long)row * n + col);
+        for (int i = 0; i <= r; ++i) {
+            const int top = (i < r) ? s - 1 : m - s * r;
+            double v = 0.0;
+            for (int j = 0; j <= top; ++j) v += __ldg(coef + s * i + j) * x[j];
+            acc[i] += fabs(v);
+        }
+        acc[r + 1] += fabs(x[s]);
+        acc[r + 2] += fabs(x[1]);
+    }
+    for (int t = 0; t < q; ++t)
+        partial[(((long long)b * chunks + chunk) * q + t) * n + col] = acc[t];
+}
+
+// norms[b*q + t] = max_col sum_chunk partial[b][chunk][t][col]  (fixed summation order).
+__global__ void k_norms_finalize(const double* __restrict__ partial, int n, int chunks, int q,
+                                 double* __restrict__ norms) {
+    const int t = blockIdx.x, b = blockIdx.y;
+    double best = 0.0;
+    for (int col = threadIdx.x; col < n; col += blockDim.x) {
+        double sum = 0.0;
+        for (int c = 0; c < chunks; ++c)
+            sum += partial[(((long long)b * chunks + c) * q + t) * n + col];
+        best = fmax(best, sum);
+    }
+    best = block_max(best);
+    if (threadIdx.x == 0) norms[(long long)b * q + t] = best;
+}
+
+// Column sums of |M| accumulated row by row in order 0..n-1 (one thread per column), so
+// that ||M||_1 is the same double as a plain sequential loop computes.
+__global__ void k_colsum_seq(const double* __restrict__ M, long long bs, int n,
+                             double* __restrict__ colsum) {
+    const int col = blockIdx.x * kColsPerBlock + threadIdx.x;
+    const int b = blockIdx.y;
+    if (col >= n) return;
+    const double* base = M + (long long)b * bs;
+    double acc = 0.0;
+    for (int row = 0; row < n; ++row) acc += fabs(__ldg(base + (long long)row * n + col));
+    colsum[(long long)b * n + col] = acc;
+}
+
+__global__ void k_scale_copy(const double* __restrict__ A, long long a_bs, double* __restrict__ X,
+                             long long x_bs, long long nn, const int* __restrict__ sigma) {
+    const int b = blockIdx.y;
+    const int e = sigma ? -sigma[b] : 0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
+         t += (long long)gridDim.x * blockDim.x)
+        X[b * x_bs + t] = ldexp(A[b * a_bs + t], e);
+}
+
+__global__ void k_select_copy(const double* __restrict__ q0, const double* __restrict__ q1,
+                              const int* __restrict__ sigma, double* __restrict__ out,
+                              long long nn) {
+    const int b = blockIdx.y;
+    const double* src = (sigma[b] & 1) ? q1 : q0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
+         t += (long long)gridDim.x * blockDim.x)
+        out[b * nn + t] = src[b * nn + t];
+}
+
+__global__ void k_combine(int n, const double* __restrict__ extra, long long extra_bs,
+                          Epilogue ep) {
+    const int b = blockIdx.y;
+    const long long nn = (long long)n * n;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int row = (int)(t / n), col = (int)(t % n);
+        const double e = extra ? extra[b * extra_bs + t] : 0.0;
+        epilogue_store(ep, b, row, col, n, epilogue_value(ep, b, row, col, n, e));
+    }
+}
+
+__global__ void k_convert(int fmt, const double* __restrict__ M, long long bs, int n, void* hi,
+                          void* lo, long long low_bs, int lld, const double* __restrict__ scale) {
+    const int b = blockIdx.y;
+    const double sc = scale ? scale[b] : 1.0;
+    const long long nn = (long long)n * n;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int row = (int)(t / n), col = (int)(t % n);
+        store_low(fmt, hi, lo, b * low_bs + (long long)row * lld + col, M[b * bs + t] * sc);
+    }
+}
+
+// Transposed copy through a 32 x 33 shared tile: out[col][row] = round(M[row][col] * scale).
+__global__ void k_convert_t(int fmt, const double* __restrict__ M, long long bs, int n, void* hi,
+                            void* lo, long long low_bs, int lld,
+                            const double* __restrict__ scale) {
+    __shared__ double tile[32][33];
+    const int b = blockIdx.z;
+    const double sc = scale ? scale[b] : 1.0;
+    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    const double* base = M + (long long)b * bs;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int row = r0 + i, col = c0 + threadIdx.x;
+        tile[i][threadIdx.x] = (row < n && col < n) ? base[(long long)row * n + col] : 0.0;
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int orow = c0 + i, ocol = r0 + threadIdx.x;   // out row = source column
+        if (orow < n && ocol < n)
+            store_low(fmt, hi, lo, (long long)b * low_bs + (long long)orow * lld + ocol,
+                      tile[threadIdx.x][i] * sc);
+    }
+}
+
+struct BlockCoefs {
+    double c[MPPS_MAX_S + 1];
+};
+
+__global__ void k_axpy_blocks(double* __restrict__ xbar, long long xbar_bs, int n, int t,
+                              BlockCoefs c, const double* __restrict__ G, long long g_bs) {
+    const int b = blockIdx.y;
+    const long long nn = (long long)n * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nn;
+         e += (long long)gridDim.x * blockDim.x) {
+        const double gv = G[b * g_bs + e];
+        for (int j = 1; j <= t; ++j) xbar[b * xbar_bs + (long long)(j - 1) * nn + e] += c.c[j] * gv;
+    }
+}
+
+__global__ void k_transpose(const double* __restrict__ A, double* __restrict__ At, int n) {
+    __shared__ double tile[32][33];
+    const int b = blockIdx.z;
+    const long long nn = (long long)n * n;
+    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int row = r0 + i, col = c0 + threadIdx.x;
+        if (row < n && col < n) tile[i][threadIdx.x] = A[b * nn + (long long)row * n + col];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int orow = c0 + i, ocol = r0 + threadIdx.x;
+        if (orow < n && ocol < n) At[b * nn + (long long)orow * n + ocol] = tile[threadIdx.x][i];
+    }
+}
+
+__global__ void k_maxabs(const double* __restrict__ M, long long bs, long long nn,
+                         double* __restrict__ out) {
+    const int b = blockIdx.y;
+    double v = 0.0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
+         t += (long long)gridDim.x * blockDim.x)
+        v = fmax(v, fabs(M[b * bs + t]));
+    v = block_max(v);
+    // non-negative doubles order like their bit patterns
+    if (threadIdx.x == 0)
+        atomicMax((unsigned long long*)(out + b), (unsigned long long)__double_as_longlong(v));
+}
+
+// scale = 2^(target - e) with max < 2^e (frexp), so scaled entries are < 2^target.
+__device__ __forceinline__ int pow2_exp_above(double mx) {
+    if (!(mx > 0.0) || !isfinite(mx)) return 0;
+    int e;
+    frexp(mx, &e);
+    return e;
+}
+
+__global__ void k_pow2_scales(const double* __restrict__ ma, const double* __restrict__ mb,
+                              int batch, int target, double* sa, double* sb, double* unscale) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= batch) return;
+    const int ea = pow2_exp_above(ma[b]), eb = pow2_exp_above(mb[b]);
+    sa[b] = ldexp(1.0, target - ea);
+    sb[b] = ldexp(1.0, target - eb);
+    unscale[b] = ldexp(1.0, ea + eb - 2 * target);
+}
+
+inline int grid1d(long long work, int threads, int cap = 4096) {
+    long long g = (work + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+}  // namespace
+
+int block_norms_count(int m, int s) { return m / s + 3; }
+
+size_t block_norms_partial_elems(int n, int batch, int m, int s) {
+    const int chunks = (n + kRowsPerChunk - 1) / kRowsPerChunk;
+    return (size_t)batch * chunks * block_norms_count(m, s) * n;
+}
+
+size_t norm1_partial_elems(int n, int batch) { return (size_t)batch * n; }
+
+mpps_status launch_block_norms(const double* pw, long long pw_bs, int n, int batch, int s, int m,
+                               const double* d_coeffs, double* partial, double* norms,
+                               cudaStream_t st) {
+    ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
+    const int chunks = (n + kRowsPerChunk - 1) / kRowsPerChunk;
+    const int q = block_norms_count(m, s);
+    dim3 g((n + kColsPerBlock - 1) / kColsPerBlock, chunks, batch);
+    k_block_norms_partial<<<g, kColsPerBlock, 0, st>>>(pw, pw_bs, n, s, m, d_coeffs, partial);
+    MPPS_LAUNCH_CHECK();
+    k_norms_finalize<<<dim3(q, batch), 256, 0, st>>>(partial, n, chunks, q, norms);
+    MPPS_LAUNCH_CHECK();
+    return MPPS_OK;
+}
+
+mpps_status launch_norm1(const double* M, long long bs, int n, int batch, double* partial,
+                         double* norms, cudaStream_t st) {
+    ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
+    dim3 g((n + kColsPerBlock - 1) / kColsPerBlock, batch);
+    k_colsum_seq<<<g, kColsPerBlock, 0, st>>>(M, bs, n, partial);
+    MPPS_LAUNCH_CHECK();
+    k_norms_finalize<<<dim3(1, batch), 256, 0, st>>>(partial, n, 1, 1, norms);
+    MPPS_LAUNCH_CHECK();
+    return MPPS_OK;
+}
+
+mpps_status launch_scale_copy(const double* A, long long a_bs, double* X, long long x_bs, int n,
+                              int batch, const int* d_sigma, cudaStream_t st) {
+    ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
+    const long long nn = (long long)n * n;
+    k_scale_copy<<<dim3(grid1d(nn, 256), batch), 256, 0, st>>>(A, a_bs, X, x_bs, nn, d_sigma);
+    MPPS_LAUNCH_CHECK();
+    return MPPS_OK;
+}
+
+mpps_status launch_select_copy(const double* q0, const double* q1, const int* d_sigma, double* out,
+                               int n, int batch, cudaStream_t st) {
+    ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
+    const long long nn = (long long)n * n;
+    k_select_copy<<<dim3(grid1d(nn, 256), batch), 256, 0, st>>>(q0, q1, d_sigma, out, nn);
+    MPPS_LAUNCH_CHECK();
+    return MPPS_OK;
+}
+
+mpps_status launch_combine(int n, int batch, const double* extra, long long extra_bs,
+                           const Epilogue& ep, cudaStream_t st) {
+    ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
+    const long long nn = (long long)n * n;
+    k_combine<<<dim3(grid1d(nn, 256), batch), 256, 0, st>>>(n, extra, extra_bs, ep);
+    MPPS_LAUNCH_CHECK();
+    return MPPS_OK;
+}
+
+mpps_status launch_convert(int fmt, const double* M, long long bs, int n, int batch, void* hi,
+                           void* lo, long long low_bs, int lld, const double* d_scale,
+                           bool transpose, cudaStream_t st) {
+    ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
+    if (transpose) {
+        dim3 g((n + 31) / 32, (n + 31) / 32, batch);
+        k_convert_t<<<g, dim3(32, 8), 0, st>>>(fmt, M, bs, n, hi, lo, low_bs, lld, d_scale);
+    } else {
+        const long long nn = (long long)n * n;
+        k_convert<<<dim3(grid1d(nn, 256), batch), 256, 0, st>>>(fmt, M, bs, n, hi, lo, low_bs,
+                                                                  lld, d_scale);
+    }
+    MPPS_LAUNCH_CHECK();
+    return MPPS_OK;
+}
+
+mpps_status launch_maxabs(const double* M, long long bs, int n, int batch, double* out,
+                          cudaStream_t st) {
+    ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
+    const long long nn = (long long)n * n;
+    k_maxabs<<<dim3(grid1d(nn, 256, 1024), batch), 256, 0, st>>>(M, bs, nn, out);
+    MPPS_LAUNCH_CHECK();
+    return MPPS_OK;
+}
+
+mpps_status launch_pow2_scales(const double* maxabs_a, const double* maxabs_b, int batch,
+                               int target_exp, double* scale_a, double* scale_b, double* unscale,
+                               cudaStream_t st) {
+    ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
+    k_pow2_scales<<<(batch + 127) / 128, 128, 0, st>>>(maxabs_a, maxabs_b, batch, target_exp,
+                                                         scale_a, scale_b, unscale);
+    MPPS_LAUNCH_CHECK();
+    return MPPS_OK;
+}
+
+mpps_status launch_axpy_blocks(double* xbar, long long xbar_bs, int n, int batch, int t,
+                               const double* c, const double* G, long long g_bs,
+                               cudaStream_t st) {
+    ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
+    if (t <= 0) return MPPS_OK;
+    BlockCoefs bc;
+    for (int j = 0; j <= MPPS_MAX_S; ++j) bc.c[j] = (j <= t) ? c[j] : 0.0;
+    const long long nn = (long long)n * n;
+    k_axpy_blocks<<<dim3(grid1d(nn, 256), batch), 256, 0, st>>>(xbar, xbar_bs, n, t, bc, G, g_bs);
+    MPPS_LAUNCH_CHECK();
+    return MPPS_OK;
+}
+
+mpps_status launch_transpose(const double* A, double* At, int n, int batch, cudaStream_t st) {
+    ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
+    dim3 g((n + 31) / 32, (n + 31) / 32, batch);
+    k_transpose<<<g, dim3(32, 8), 0, st>>>(A, At, n);
+    MPPS_LAUNCH_CHECK();
+    return MPPS_OK;
+}
+
+}  // namespace mpps

@@ -1,0 +1,369 @@
+// gemm_tc.cu -- low-precision Horner products P_i Y on the 5th-generation tensor cores
+// (tcgen05.mma, accumulator in TMEM, operands staged in shared memory by TMA).  These are
+// the products that eq. (2.8) lets run at u_i > u: the paper's q(X) part (eq. (2.6)),
+// evaluated in the format chosen per step (Section 4.1.1's ladder, GPU formats):
+//   BF16    kind::f16,     1 product                        (u = 2^-8)
+//   BF16X3  kind::f16,     hi*hi + hi*lo + lo*hi, one TMEM accumulator (u ~ 2^-16)
+//   TF32    kind::tf32,    1 product                        (u = 2^-11)
+//   FP8     kind::f8f6f4 (E4M3 x E4M3), 1 product          (u = 2^-4)
+// all accumulated in FP32.  The epilogue reads the 128 x 128 FP32 tile out of TMEM,
+// undoes the operand scales and adds B_{i-1} in FP64 (fused Horner add).
+//
+// Structure: one CTA (4 warps) per 128 x 128 output tile, K walked in 128-byte slabs
+// (64 bf16 / 32 tf32 / 128 fp8 per row) through a 3-4 stage TMA ring with full/empty
+// mbarriers.  Warp 0 lane 0 issues TMA, warp 1 lane 0 issues tcgen05.mma; all 4 warps run
+// the epilogue (warp w owns TMEM lanes 32w..32w+31 = tile rows).  Both operands are
+// K-major with the 128-byte swizzle.  Every mbarrier wait is bounded (about 2 s of
+// %globaltimer); on expiry the kernel sets *err, skips further waits and exits normally.
+#include "common.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+namespace mpps {
+
+namespace {
+
+constexpr int TM = 128, TN = 128;
+constexpr int SLAB = 128;                 // bytes of K per smem row
+constexpr int TILE_BYTES = TM * SLAB;     // 16 KB: one 128-row operand slab
+constexpr unsigned long long kWaitNs = 2000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+// Bounded wait for phase `parity` of an mbarrier.  Returns false (and sets *err) when the
+// time limit passes or another thread already gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+    const uint32_t addr = smem_u32(bar);
+    unsigned long long t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if ((it & 63) == 0) {
+            if (*(volatile int*)err != 0) return false;
+            const unsigned long long now = globaltimer();
+            if (t0 == 0) t0 = now;
+            else if (now - t0 > kWaitNs) {
+                atomicExch(err, 1);
+                return false;
+            }
+        }
+    }
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, int c0, int c1, int c2,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+        "%3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)tm), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;              // leading byte offset (unused for this layout)
+    d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset
+    d |= (uint64_t)1 << 46;              // descriptor version
+    d |= (uint64_t)2 << 61;              // 128-byte swizzle
+    return d;
+}
+
+template <int FMT>
+struct Tc;
+template <>
+struct Tc<MPPS_FMT_BF16> {
+    static constexpr int kOps = 2, kStages = 4, kAB = 1;
+};
+template <>
+struct Tc<MPPS_FMT_BF16X3> {
+    static constexpr int kOps = 4, kStages = 3, kAB = 1;
+};
+template <>
+struct Tc<MPPS_FMT_TF32> {
+    static constexpr int kOps = 2, kStages = 4, kAB = 2;
+};
+template <>
+struct Tc<MPPS_FMT_FP8> {
+    static constexpr int kOps = 2, kStages = 4, kAB = 0;
+};
+
+template <int FMT>
+__host__ __device__ constexpr uint32_t instr_desc() {
+    // D format F32 (bit 4), A/B formats (bits 7-9, 10-12), K-major A and B, N>>3 at
+    // bit 17, M>>4 at bit 24.
+    return (1u << 4) | ((uint32_t)Tc<FMT>::kAB << 7) | ((uint32_t)Tc<FMT>::kAB << 10) |
+           ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+}
+
+template <int FMT>
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+    constexpr uint32_t id = instr_desc<FMT>();
+    if constexpr (FMT == MPPS_FMT_TF32) {
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+            "l"(a), "l"(b), "r"(id), "r"(acc));
+    } else if constexpr (FMT == MPPS_FMT_FP8) {
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+            "l"(a), "l"(b), "r"(id), "r"(acc));
+    } else {
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+            "l"(a), "l"(b), "r"(id), "r"(acc));
+    }
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+          "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+          "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+          "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <int FMT>
+__host__ __device__ constexpr int smem_bytes() {
+    return Tc<FMT>::kStages * Tc<FMT>::kOps * TILE_BYTES + 1024 + 256;
+}
+
+template <int FMT>
+__global__ void __launch_bounds__(128, 1)
+    k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2,
+              int n, Epilogue ep, int* err) {
+    constexpr int OPS = Tc<FMT>::kOps, STAGES = Tc<FMT>::kStages;
+    constexpr int STAGE_BYTES = OPS * TILE_BYTES;
+    constexpr int ESIZE = (FMT == MPPS_FMT_TF32) ? 4 : (FMT == MPPS_FMT_FP8 ? 1 : 2);
+    constexpr int KSLAB = SLAB / ESIZE;   // K elements per stage
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* done = empty + STAGES;
+    uint32_t* tmem_slot = (uint32_t*)(done + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.z, m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+    const int nk = (n + KSLAB - 1) / KSLAB;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(TN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // TMA producer
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % STAGES;
+            if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1, err)) break;
+            mbar_expect_tx(&full[s], STAGE_BYTES);
+            uint8_t* st = smem + s * STAGE_BYTES;
+            const int kc = kb * KSLAB;
+            tma_load_3d(st, &tmA, kc, m0, b, &full[s]);
+            tma_load_3d(st + TILE_BYTES, &tmB, kc, n0, b, &full[s]);
+            if constexpr (OPS == 4) {
+                tma_load_3d(st + 2 * TILE_BYTES, &tmA2, kc, m0, b, &full[s]);
+                tma_load_3d(st + 3 * TILE_BYTES, &tmB2, kc, n0, b, &full[s]);
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer: 4 instructions per 128-byte slab (K advance of 32 bytes each)
+        bool ok = true;
+        for (int kb = 0; kb < nk && ok; ++kb) {
+            const int s = kb % STAGES;
+            ok = mbar_wait(&full[s], (kb / STAGES) & 1, err);
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(smem + s * STAGE_BYTES);
+            const uint32_t b0 = a0 + TILE_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const uint64_t ad = sw128_desc(a0 + kk * 32), bd = sw128_desc(b0 + kk * 32);
+                tc_mma<FMT>(tmem, ad, bd, (kb | kk) != 0 ? 1u : 0u);
+                if constexpr (OPS == 4) {
+                    const uint64_t ad2 = sw128_desc(a0 + 2 * TILE_BYTES + kk * 32);
+                    const uint64_t bd2 = sw128_desc(a0 + 3 * TILE_BYTES + kk * 32);
+                    tc_mma<FMT>(tmem, ad, bd2, 1u);   // hi * lo
+                    tc_mma<FMT>(tmem, ad2, bd, 1u);   // lo * hi
+                }
+            }
+            tc_commit(&empty[s]);
+        }
+        tc_commit(done);
+    }
+    __syncwarp();
+
+    mbar_wait(done, 0, err);
+    tc_fence_after();
+
+    const int row = m0 + warp * 32 + lane;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+#pragma unroll 1
+    for (int c0 = 0; c0 < TN; c0 += 32) {
+        uint32_t v[32];
+        tmem_ld32(tmem + lane_base + (uint32_t)c0, v);
+        if (row < n) {
+#pragma unroll 4
+            for (int j = 0; j < 32; ++j) {
+                const int col = n0 + c0 + j;
+                if (col < n)
+                    epilogue_store(ep, b, row, col, n,
+                                   epilogue_value(ep, b, row, col, n, (double)__uint_as_float(v[j])));
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TN));
+}
+
+// ---- host side ----------------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    });
+    return fn;
+}
+
+// 3-D map over (K = n columns, n rows, batch) of a row-major low-precision copy with
+// leading dimension lld and batch stride bs (elements); box = one 128-byte slab x 128 rows.
+bool make_map(CUtensorMap* tm, int fmt, const void* ptr, int n, int batch, int lld, long long bs) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const int es = low_elem_bytes(fmt);
+    CUtensorMapDataType dt = fmt == MPPS_FMT_TF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                             : fmt == MPPS_FMT_FP8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                                   : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)batch};
+    cuuint64_t strides[2] = {(cuuint64_t)lld * es, (cuuint64_t)bs * es};
+    cuuint32_t box[3] = {(cuuint32_t)(SLAB / es), (cuuint32_t)TM, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(tm, dt, 3, const_cast<void*>(ptr), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+template <int FMT>
+mpps_status launch_fmt(const void* A_hi, const void* A_lo, const void* Bt_hi, const void* Bt_lo,
+                       long long a_bs, long long b_bs, int lld, int n, int batch, const Epilogue& ep,
+                       int* d_err, cudaStream_t st) {
+    CUtensorMap ta, tb, ta2, tb2;
+    bool ok = make_map(&ta, FMT, A_hi, n, batch, lld, a_bs) &&
+              make_map(&tb, FMT, Bt_hi, n, batch, lld, b_bs);
+    if (FMT == MPPS_FMT_BF16X3)
+        ok = ok && make_map(&ta2, FMT, A_lo, n, batch, lld, a_bs) &&
+             make_map(&tb2, FMT, Bt_lo, n, batch, lld, b_bs);
+    else {
+        ta2 = ta;
+        tb2 = tb;
+    }
+    if (!ok) {
+        set_error("cuTensorMapEncodeTiled failed (n=%d, lld=%d)", n, lld);
+        return MPPS_ECUDA;
+    }
+    constexpr int smem = smem_bytes<FMT>();
+    static bool attr_set = false;
+    if (!attr_set) {
+        MPPS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           smem));
+        attr_set = true;
+    }
+    dim3 grid((n + TN - 1) / TN, (n + TM - 1) / TM, batch);
+    ProfScope prof(MPPS_PROF_GEMM_TC, st);
+    k_gemm_tc<FMT><<<grid, 128, smem, st>>>(ta, tb, ta2, tb2, n, ep, d_err);
+    MPPS_LAUNCH_CHECK();
+    return MPPS_OK;
+}
+
+}  // namespace
+
+mpps_status launch_gemm_tc(int fmt, const void* A_hi, const void* A_lo, const void* Bt_hi,
+                           const void* Bt_lo, long long a_bs, long long b_bs, int lld, int n,
+                           int batch, const Epilogue& ep, int* d_err, cudaStream_t st) {
+    switch (fmt) {
+        case MPPS_FMT_BF16:
+            return launch_fmt<MPPS_FMT_BF16>(A_hi, A_lo, Bt_hi, Bt_lo, a_bs, b_bs, lld, n, batch, ep,
+                                             d_err, st);
+        case MPPS_FMT_BF16X3:
+            return launch_fmt<MPPS_FMT_BF16X3>(A_hi, A_lo, Bt_hi, Bt_lo, a_bs, b_bs, lld, n, batch,
+                                               ep, d_err, st);
+        case MPPS_FMT_TF32:
+            return launch_fmt<MPPS_FMT_TF32>(A_hi, A_lo, Bt_hi, Bt_lo, a_bs, b_bs, lld, n, batch, ep,
+                                             d_err, st);
+        case MPPS_FMT_FP8:
+            return launch_fmt<MPPS_FMT_FP8>(A_hi, A_lo, Bt_hi, Bt_lo, a_bs, b_bs, lld, n, batch, ep,
+                                            d_err, st);
+        default:
+            set_error("launch_gemm_tc: unsupported format %d", fmt);
+            return MPPS_EINVAL;
+    }
+}
+
+}  // namespace mpps

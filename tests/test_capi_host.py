@@ -1,0 +1,95 @@
+"""Host-side checks of the C ABI (no GPU): the library loads, exports every entry point
+declared in include/mpps.h, and its precision planner agrees exactly with the oracle's
+statement of the rule (eq. (2.8), Algorithm 3.1 / 4.1, Section 4.1.1)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from conftest import ROOT
+
+
+@pytest.fixture(scope="module")
+def mpps():
+    from paper_2312_17396_gb300 import _build
+    _build.build()
+    import paper_2312_17396_gb300 as m
+    m.lib()
+    return m
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "mpps.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z_0-9]*\s*\*?\s*([A-Za-z_][A-Za-z_0-9]*)\s*\(",
+                       text, flags=re.M)
+    return sorted(set(n for n in names if n not in ("if", "while", "for", "sizeof")))
+
+
+def test_header_declares_the_entry_points():
+    names = declared_functions()
+    for must in ("ps_eval", "expm_taylor_ss", "ps_eval_adjoint", "mpps_plan", "mpps_matmul",
+                 "mpps_last_error", "mpps_version", "mpps_policy_default"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(mpps):
+    L = mpps.lib()
+    for name in declared_functions():
+        assert hasattr(L, name), name
+    assert "sm_103a" in mpps.version()
+
+
+def test_library_binding_lists_all_exports(mpps):
+    assert set(declared_functions()) <= set(mpps.EXPORTS)
+
+
+def test_invalid_arguments_rejected_without_gpu(mpps):
+    with pytest.raises(mpps.MppsError) as e:
+        mpps.plan(-1, 4, [1.0], 1.0)
+    assert e.value.status == 1
+    with pytest.raises(mpps.MppsError):
+        mpps.plan(16, 0, [1.0] * 5, 1.0)
+
+
+def _rand_case(rng):
+    m = int(rng.integers(1, 60))
+    s = oracle.ceil_sqrt(m)
+    r = m // s
+    n = int(rng.choice([1, 8, 64, 1024, 4096, 2 ** 20]))
+    norms = [float(x) for x in 10.0 ** rng.uniform(-40, 3, size=r + 1)]
+    if rng.random() < 0.1:
+        norms[int(rng.integers(0, r + 1))] = 0.0
+    y = float(10.0 ** rng.uniform(-6, 2))
+    return m, n, norms, y
+
+
+@pytest.mark.parametrize("mode", [oracle.MODE_FIXED, oracle.MODE_PAPER, oracle.MODE_NS])
+def test_planner_matches_oracle_rule(mpps, mode):
+    rng = np.random.default_rng(7 + mode)
+    masks = [0x1F, 0x07, 0x19, 0x01, 0x11]
+    for _ in range(400):
+        m, n, norms, y = _rand_case(rng)
+        mask = int(rng.choice(masks))
+        tol = float(rng.choice([2.0 ** -53, 1e-15, 1e-10]))
+        ref = oracle.plan(m, n, norms, y, mode=mode, tol=tol, formats=mask, floor_steps=2)
+        got = mpps.plan(m, n, norms, y, mpps.Policy(mode=mode, tol=tol, formats=mask,
+                                                    fp64_floor_steps=2))
+        assert (got["s"], got["r"], got["nu"], got["fold"]) == \
+            (ref["s"], ref["r"], ref["nu"], ref["fold"])
+        names = [None] + [mpps.FORMAT_NAMES[f] for f in ref["fmt"][1:]]
+        assert got["fmt"] == names
+        assert got["u"][1:] == ref["u"][1:]
+
+
+def test_planner_cost_ratio_reproduces_eq_3_8(mpps):
+    # FP64 everywhere -> ratio 1; one product in FP8 -> digits drop by 16 - 1.2
+    p = mpps.plan(16, 64, [1.0, 1e-3, 1e-9, 1e-15, 1e-21], 0.5, mpps.Policy(mode=mpps.MIXED_PAPER))
+    assert p["fmt"][1:] == ["fp64", "fp64", "fp8", "none"]
+    D = -np.log10(2.0 ** -53)
+    expect = (3 * D + D + D + (-np.log10(2.0 ** -4)) + 0.0) / ((4 + 4 - 1) * D)
+    assert abs(p["cost_ratio"] - expect) < 1e-12
+    f = mpps.plan(16, 64, [1.0, 1e-3, 1e-9, 1e-15, 1e-21], 0.5, mpps.FIXED)
+    assert abs(f["cost_ratio"] - (3 * D + 3 * D) / (7 * D)) < 1e-12

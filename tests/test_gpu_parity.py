@@ -1,0 +1,268 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances
+* FP64 products and fixed-FP64 PS: 1-norm relative error <= 50 n 2^-53 (the fixed path's
+  bound used throughout; Section 3.4 reports errors of order r n u).
+* Low-precision products: normwise |C - AB| <= k u_F |A||B| with u_F the format's unit
+  roundoff, plus exactness on integer inputs that every format represents exactly.
+* Mixed PS: the same 50 n 2^-53 bound, and within 2x of the fixed-FP64 error up to an
+  absolute floor of n u (both are measured against the double-double oracle).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2312_17396_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+U = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def mpps():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2312_17396_gb300 as m
+    m.lib()
+    return m
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+# ------------------------------------------------------------------------------------
+# products
+# ------------------------------------------------------------------------------------
+SIZES = [1, 2, 3, 17, 64, 127, 130, 257]
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_matmul_fp64_vs_oracle(mpps, n):
+    rng = np.random.default_rng(n)
+    A = rng.standard_normal((2, n, n)); B = rng.standard_normal((2, n, n))
+    C = host(mpps.matmul(dev(A), dev(B), "fp64"))
+    for b in range(2):
+        ch, cl = oracle.matmul_dd(A[b], None, B[b], None)
+        bound = n * U * (np.abs(A[b]) @ np.abs(B[b])) + 1e-300
+        assert np.all(np.abs(C[b] - ch - cl) <= bound)
+
+
+LOW = {"bf16": 2.0 ** -8, "bf16x3": 2.0 ** -16, "tf32": 2.0 ** -11, "fp8": 2.0 ** -4}
+
+
+@pytest.mark.parametrize("fmt", list(LOW))
+@pytest.mark.parametrize("n", [8, 64, 127, 130, 257])
+def test_matmul_low_exact_on_integers(mpps, fmt, n):
+    """Small integers are exact in every format and their products sum exactly in FP32:
+    the tensor-core path must reproduce A B bit for bit (checks operand layout, swizzle,
+    descriptors, K/M/N tails and the scaling round trip)."""
+    rng = np.random.default_rng(100 + n)
+    lim = 4 if fmt == "fp8" else 8
+    A = rng.integers(-lim, lim + 1, size=(2, n, n)).astype(np.float64)
+    B = rng.integers(-lim, lim + 1, size=(2, n, n)).astype(np.float64)
+    A[:, 0, 0] = lim; B[:, 0, 0] = lim     # pin the scale exponents
+    C = host(mpps.matmul(dev(A), dev(B), fmt))
+    assert np.array_equal(C, A @ B)
+
+
+@pytest.mark.parametrize("fmt", list(LOW))
+@pytest.mark.parametrize("n", [64, 257])
+def test_matmul_low_error_bound(mpps, fmt, n):
+    rng = np.random.default_rng(200 + n)
+    A = rng.standard_normal((1, n, n)); B = rng.standard_normal((1, n, n))
+    C = host(mpps.matmul(dev(A), dev(B), fmt))[0]
+    exact = A[0] @ B[0]
+    absprod = np.abs(A[0]) @ np.abs(B[0])
+    uf = LOW[fmt]
+    # rounding of both operands (2 u_F), FP32 accumulation (n 2^-24); FP8 also loses
+    # entries below its subnormal range relative to the per-matrix scale
+    k = 3.0 if fmt != "fp8" else 4.0
+    err = np.linalg.norm(C - exact)
+    assert err <= k * (uf + n * 2.0 ** -24) * np.linalg.norm(absprod)
+
+
+# ------------------------------------------------------------------------------------
+# PS evaluation
+# ------------------------------------------------------------------------------------
+@pytest.mark.parametrize("n", SIZES)
+@pytest.mark.parametrize("m", [1, 2, 5, 16, 30])
+def test_ps_eval_fixed_vs_oracle(mpps, n, m):
+    A = inputs.gaussian_matrix(n, seed=1000 + n + m, norm1=1.0)
+    coef = mpps.taylor_exp_coeffs(m)
+    P = host(mpps.ps_eval(coef, dev(A), policy=mpps.FIXED))
+    ph, pl, _ = oracle.ps_dd(oracle.taylor_exp_rational(m), A)
+    assert oracle.rel_err_1norm(P, ph, pl) <= 50 * n * U
+
+
+@pytest.mark.parametrize("n", [17, 64, 130, 257])
+@pytest.mark.parametrize("norm", [0.05, 0.5, 1.0])
+def test_ps_eval_mixed_vs_fixed(mpps, n, norm):
+    m = 30
+    A = inputs.gaussian_matrix(n, seed=2000 + n, norm1=norm)
+    coef = mpps.taylor_exp_coeffs(m)
+    ph, pl, _ = oracle.ps_dd(oracle.taylor_exp_rational(m), A)
+    Pf = host(mpps.ps_eval(coef, dev(A), policy=mpps.FIXED))
+    ef = oracle.rel_err_1norm(Pf, ph, pl)
+    for pol in (mpps.PAPER, mpps.NS):
+        Pm, rep = mpps.ps_eval(coef, dev(A), policy=pol, report=True)
+        em = oracle.rel_err_1norm(host(Pm), ph, pl)
+        assert em <= 50 * n * U
+        assert em <= 2 * ef + n * U, (pol.mode, em, ef, rep[0]["fmt"])
+
+
+def test_ps_eval_general_coefficients(mpps):
+    n = 96
+    A = inputs.gaussian_matrix(n, seed=5, norm1=2.0)
+    for coefs_q, coefs_d in [(oracle.pade_exp_num_rational(13), mpps.pade_exp_num_coeffs(13)),
+                             (oracle.pade_exp_den_rational(13), mpps.pade_exp_den_coeffs(13)),
+                             (oracle.cos_taylor_rational(16), mpps.cos_taylor_coeffs(16))]:
+        ph, pl, _ = oracle.ps_dd(coefs_q, A)
+        for pol in (mpps.FIXED, mpps.PAPER):
+            P = host(mpps.ps_eval(coefs_d, dev(A), policy=pol))
+            assert oracle.rel_err_1norm(P, ph, pl) <= 50 * n * U
+
+
+def test_ps_eval_block_sizes_and_nilpotent(mpps):
+    n, m = 40, 20
+    coefq = oracle.taylor_exp_rational(m)
+    coef = mpps.taylor_exp_coeffs(m)
+    A = inputs.gaussian_matrix(n, seed=9, norm1=1.5)
+    ph, pl, _ = oracle.ps_dd(coefq, A)
+    for s in (1, 2, 3, 7, 20):
+        P = host(mpps.ps_eval(coef, dev(A), policy=mpps.Policy(mode=mpps.FIXED_FP64, s=s)))
+        assert oracle.rel_err_1norm(P, ph, pl) <= 50 * n * U, s
+    N = inputs.strictly_upper(n, seed=3, scale=1.0)
+    nh, nl, _ = oracle.ps_dd(coefq, N)
+    for pol in (mpps.FIXED, mpps.PAPER):
+        P = host(mpps.ps_eval(coef, dev(N), policy=pol))
+        assert oracle.rel_err_1norm(P, nh, nl) <= 50 * n * U
+
+
+def test_ps_eval_batch_and_host_pointers(mpps):
+    n, m = 33, 16
+    A = inputs.gaussian_batch(3, n, seed=11, norm1=[0.2, 1.0, 3.0])
+    coef = mpps.taylor_exp_coeffs(m)
+    Pd = host(mpps.ps_eval(coef, dev(A), policy=mpps.NS))
+    Ph = mpps.ps_eval(coef, A, policy=mpps.NS)          # numpy in, numpy out
+    assert np.array_equal(Pd, Ph)
+    for b in range(3):
+        ph, pl, _ = oracle.ps_dd(oracle.taylor_exp_rational(m), A[b])
+        assert oracle.rel_err_1norm(Pd[b], ph, pl) <= 50 * n * U
+
+
+def test_degenerate_cases(mpps):
+    A = inputs.gaussian_matrix(5, seed=1, norm1=1.0)
+    P = host(mpps.ps_eval([2.5], dev(A)))
+    assert np.array_equal(P, 2.5 * np.eye(5))
+    P1 = host(mpps.ps_eval([1.0], dev(np.array([[3.0]]))))
+    assert P1[0, 0] == 1.0
+    one = host(mpps.ps_eval(mpps.taylor_exp_coeffs(12), dev(np.array([[0.5]])), policy=mpps.FIXED))
+    exact = float(sum(oracle.Fraction(1, 2 ** k) * c for k, c in enumerate(oracle.taylor_exp_rational(12))))
+    assert abs(one[0, 0] - exact) <= 4 * U * exact
+    empty = torch.empty((0, 4, 4), dtype=torch.float64, device="cuda:0")
+    assert mpps.ps_eval([1.0, 1.0], empty).shape == (0, 4, 4)
+    with pytest.raises(mpps.MppsError):
+        mpps.ps_eval([1.0] * 2000, dev(A))      # r beyond the supported range
+
+
+# ------------------------------------------------------------------------------------
+# scaling and squaring
+# ------------------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [16, 130])
+@pytest.mark.parametrize("norm", [0.5, 4.0, 32.0])
+def test_expm_vs_oracle(mpps, n, norm):
+    A = inputs.gaussian_matrix(n, seed=3000 + n, norm1=norm)
+    sg = oracle.sigma_for(A)
+    eh, el = oracle.expm_ss_dd(A, 30, sg)
+    Ef, rf = mpps.expm(dev(A), m=30, policy=mpps.FIXED, report=True)
+    ef = oracle.rel_err_1norm(host(Ef), eh, el)
+    assert rf[0]["sigma"] == sg
+    # squaring amplifies the polynomial's error by about 2^sigma (Section 3.2)
+    tol = 50 * n * U * max(1, 2 ** sg)
+    assert ef <= tol
+    for pol in (mpps.PAPER, mpps.NS):
+        Em = host(mpps.expm(dev(A), m=30, policy=pol))
+        em = oracle.rel_err_1norm(Em, eh, el)
+        assert em <= tol and em <= 2 * ef + n * U * 2 ** sg
+
+
+def test_expm_batch_mixed_sigma(mpps):
+    n = 24
+    A = inputs.gaussian_batch(4, n, seed=12, norm1=[0.3, 2.0, 9.0, 40.0])
+    E, reps = mpps.expm(dev(A), m=30, policy=mpps.NS, report=True)
+    E = host(E)
+    for b in range(4):
+        sg = oracle.sigma_for(A[b])
+        assert reps[b]["sigma"] == sg
+        eh, el = oracle.expm_ss_dd(A[b], 30, sg)
+        assert oracle.rel_err_1norm(E[b], eh, el) <= 50 * n * U * max(1, 2 ** sg)
+
+
+def test_expm_rotation_and_group_property(mpps):
+    theta = 2.5
+    R = np.array([[0.0, -theta], [theta, 0.0]])
+    E = host(mpps.expm(dev(R), policy=mpps.NS))
+    ref = np.array([[np.cos(theta), -np.sin(theta)], [np.sin(theta), np.cos(theta)]])
+    assert np.max(np.abs(E - ref)) < 1e-15
+    A = inputs.gaussian_matrix(50, seed=4, norm1=3.0)
+    Ep = host(mpps.expm(dev(A), policy=mpps.NS)); Em = host(mpps.expm(dev(-A), policy=mpps.NS))
+    assert np.max(np.abs(Ep @ Em - np.eye(50))) < 1e-12
+
+
+# ------------------------------------------------------------------------------------
+# adjoint
+# ------------------------------------------------------------------------------------
+@pytest.mark.parametrize("n,m", [(1, 3), (6, 4), (16, 8), (33, 18), (40, 13)])
+def test_adjoint_vs_oracle(mpps, n, m):
+    rng = np.random.default_rng(n * 100 + m)
+    A = rng.standard_normal((n, n)) / np.sqrt(n)
+    G = rng.standard_normal((n, n))
+    c = oracle.taylor_exp_rational(m)
+    gh, gl = oracle.adjoint_dd(c, A, G)
+    g = host(mpps.ps_eval_adjoint(mpps.taylor_exp_coeffs(m), dev(A), dev(G)))
+    assert oracle.norm1(g - gh - gl) / oracle.norm1(gh) <= 100 * n * U
+
+
+def test_autograd_function(mpps):
+    n, m, batch = 12, 18, 3
+    rng = np.random.default_rng(5)
+    A = torch.tensor(rng.standard_normal((batch, n, n)) / np.sqrt(n), device="cuda:0",
+                     dtype=torch.float64, requires_grad=True)
+    coef = mpps.taylor_exp_coeffs(m)
+    P = mpps.poly(A, coef, mpps.FIXED)
+    G = torch.randn_like(P)
+    (P * G).sum().backward()
+    for b in range(batch):
+        gh, gl = oracle.adjoint_dd(oracle.taylor_exp_rational(m), A[b].detach().cpu().numpy(),
+                                   G[b].cpu().numpy())
+        got = A.grad[b].cpu().numpy()
+        assert oracle.norm1(got - gh - gl) / oracle.norm1(gh) <= 100 * n * U
+
+
+# ------------------------------------------------------------------------------------
+# full-size configuration (n = 1024, m = 30, s = 6): sampled columns against the oracle
+# ------------------------------------------------------------------------------------
+@pytest.mark.parametrize("norm", [0.5, 4.0, 32.0])
+def test_expm_n1024_sampled_columns(mpps, norm):
+    n = 1024
+    A = inputs.gaussian_matrix(n, seed=2, norm1=norm)
+    sg = oracle.sigma_for(A)
+    X = np.ldexp(A, -sg)
+    cols = [0, 511, 1023]
+    V = np.zeros((n, len(cols)))
+    for t, j in enumerate(cols):
+        V[j, t] = 1.0
+    wh, wl = oracle.ps_apply_dd(oracle.taylor_exp_rational(30), X, V, reps=2 ** sg)
+    ref_norm = np.abs(wh).sum(axis=0)
+    for pol in (mpps.FIXED, mpps.NS, mpps.PAPER):
+        E = host(mpps.expm(dev(A), m=30, policy=pol))
+        err = np.abs(E[:, cols] - wh - wl).sum(axis=0) / ref_norm
+        assert np.all(err <= 50 * n * U * max(1, 2 ** sg)), (pol.mode, err)
