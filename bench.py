@@ -58,7 +58,7 @@ def run_kernel(args):
     import paper_2312_17396_gb300 as mpps
     from paper_2312_17396_gb300 import inputs
     dev = torch.device("cuda", 0)
-    fmt = args.kernel.split("_", 1)[1]
+    fmt = {"f64": "fp64"}.get(args.kernel.split("_", 1)[1], args.kernel.split("_", 1)[1])
     n, b = args.n, args.batch
     A = torch.from_numpy(inputs.gaussian_batch(b, n, seed=1)).to(dev)
     B = torch.from_numpy(inputs.gaussian_batch(b, n, seed=2)).to(dev)

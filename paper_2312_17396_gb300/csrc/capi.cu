@@ -549,11 +549,15 @@ static mpps_status run_eval(const double* coeffs, int m, const double* A, int n,
     clear_error();
     mpps_status rc = check_sizes(n, batch);
     if (rc) return rc;
-    if (m < 0 || !coeffs || !A || !out) {
-        set_error("invalid argument (m=%d, null pointer?)", m);
+    if (m < 0 || !coeffs) {
+        set_error("invalid argument (m=%d, coeffs=%p)", m, (const void*)coeffs);
         return MPPS_EINVAL;
     }
-    if (batch == 0) return MPPS_OK;
+    if (batch == 0) return MPPS_OK;   // nothing to do; empty tensors may have null data
+    if (!A || !out) {
+        set_error("invalid argument: null matrix pointer");
+        return MPPS_EINVAL;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     const size_t elems = (size_t)batch * n * n;
     Staged a;
@@ -606,11 +610,15 @@ mpps_status mpps_matmul(const double* A, const double* B, double* C, int n, int 
     clear_error();
     mpps_status rc = check_sizes(n, batch);
     if (rc) return rc;
-    if (!A || !B || !C || format < MPPS_FMT_FP64 || format > MPPS_FMT_FP8) {
-        set_error("mpps_matmul: invalid argument");
+    if (format < MPPS_FMT_FP64 || format > MPPS_FMT_FP8) {
+        set_error("mpps_matmul: invalid format %d", format);
         return MPPS_EINVAL;
     }
     if (batch == 0) return MPPS_OK;
+    if (!A || !B || !C) {
+        set_error("mpps_matmul: null matrix pointer");
+        return MPPS_EINVAL;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     const long long nn = (long long)n * n;
     const size_t elems = (size_t)batch * nn;
@@ -697,11 +705,15 @@ mpps_status ps_eval_adjoint(const double* coeffs, int m, const double* A, const 
     clear_error();
     mpps_status rc = check_sizes(n, batch);
     if (rc) return rc;
-    if (m < 0 || !coeffs || !A || !G || !gradA) {
-        set_error("ps_eval_adjoint: invalid argument");
+    if (m < 0 || !coeffs) {
+        set_error("ps_eval_adjoint: invalid argument (m=%d)", m);
         return MPPS_EINVAL;
     }
     if (batch == 0) return MPPS_OK;
+    if (!A || !G || !gradA) {
+        set_error("ps_eval_adjoint: null matrix pointer");
+        return MPPS_EINVAL;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     const long long nn = (long long)n * n;
     const size_t elems = (size_t)batch * nn;
