@@ -155,6 +155,32 @@ mpps_status ps_eval_adjoint(const double* coeffs, int m, const double* A, const 
 mpps_status mpps_matmul(const double* A, const double* B, double* C, int n, int batch,
                         int format, void* stream);
 
+/*
+ * mpps_matmul_noalloc -- mpps_matmul for callers that may not allocate device memory.
+ * (The paper has no counterpart: this is a deployment variant of the product above.)
+ * Some callers cannot let a library allocate: code running beside a framework whose
+ * caching allocator has already reserved the device memory (a cudaMalloc would fail or
+ * fragment that pool), latency-bound loops that must not call the allocator because it
+ * can synchronise the device and take unbounded time, and plug-ins that are handed their
+ * buffers and are not allowed to own device memory.  This entry point calls no cudaMalloc,
+ * cudaFree or other allocating routine: the scratch the tensor-core product needs (rounded
+ * operand copies, per-matrix scales, an error word) lives in one fixed device array of
+ * MPPS_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that loads the library
+ * holds until the process exits.
+ *   A, B, C : device pointers only (host pointers give MPPS_EINVAL); batch x n x n FP64,
+ *             row-major; C may not alias A or B.  format as in mpps_matmul.
+ *   Sizes whose scratch exceeds MPPS_NOALLOC_SCRATCH_BYTES give MPPS_EINVAL (the limit
+ *   fits one 2048 x 2048 product in any format; FP64 products use no scratch).
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress
+ * with that device current); make that first call before any stream capture.  All calls
+ * share the one array and it keeps the last call's contents, so calls that overlap on the
+ * GPU (different streams, or different host threads) race: serialise them.  Synchronises
+ * `stream` before returning (it reads the kernel's error word).
+ */
+#define MPPS_NOALLOC_SCRATCH_BYTES (48u * 1024u * 1024u)
+mpps_status mpps_matmul_noalloc(const double* A, const double* B, double* C, int n, int batch,
+                                int format, void* stream);
+
 /* Benchmark instrumentation (off by default).  When enabled, every kernel launch of the
  * library is bracketed by two CUDA events recorded on the launch stream and tagged with a
  * kernel class: MPPS_PROF_GEMM_F64 (FP64 products), MPPS_PROF_GEMM_TC (tensor-core

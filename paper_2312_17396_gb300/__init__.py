@@ -63,7 +63,7 @@ class _Report(ctypes.Structure):
 
 EXPORTS = ("mpps_policy_default", "mpps_plan", "ps_eval", "expm_taylor_ss", "ps_eval_adjoint",
            "mpps_matmul", "mpps_last_error", "mpps_version", "mpps_profile_enable",
-           "mpps_profile_reset", "mpps_profile_read")
+           "mpps_profile_reset", "mpps_profile_read", "mpps_matmul_noalloc")
 PROF_GEMM_F64, PROF_GEMM_TC, PROF_ELEMENTWISE = 0, 1, 2
 
 
@@ -86,6 +86,8 @@ def lib():
                                      ctypes.POINTER(_Report), vp]
         L.ps_eval_adjoint.argtypes = [dp, ip, vp, vp, ip, ip, vp, vp]
         L.mpps_matmul.argtypes = [vp, vp, vp, ip, ip, ip, vp]
+        L.mpps_matmul_noalloc.argtypes = [vp, vp, vp, ip, ip, ip, vp]
+        L.mpps_matmul_noalloc.restype = ctypes.c_int
         for f in ("mpps_plan", "ps_eval", "expm_taylor_ss", "ps_eval_adjoint", "mpps_matmul"):
             getattr(L, f).restype = ctypes.c_int
         L.mpps_profile_enable.argtypes = [ctypes.c_int]
@@ -329,6 +331,21 @@ def profile_read(kernel_class: int):
     ms = ctypes.c_double(0.0)
     _check(lib().mpps_profile_read(int(kernel_class), ctypes.byref(cnt), ctypes.byref(ms)))
     return int(cnt.value), float(ms.value)
+
+
+def matmul_noalloc(A, B, out, fmt="fp64", stream=None):
+    """C = A B like ``matmul`` but through the entry point that allocates no device memory
+    (fixed library-owned scratch; device tensors only; `out` must be given)."""
+    f = _FMT_BY_NAME[fmt] if isinstance(fmt, str) else int(fmt)
+    ptr, batch, n, kind, keep = _prep(A, "A")
+    bptr, bb, bn, _, _ = _prep(B, "B")
+    optr, ob, on, _, _ = _prep(out, "out")
+    if (bb, bn) != (batch, n) or (ob, on) != (batch, n):
+        raise ValueError("A, B and out must have the same shape")
+    _check(lib().mpps_matmul_noalloc(ctypes.c_void_p(ptr), ctypes.c_void_p(bptr),
+                                     ctypes.c_void_p(optr), n, batch, f,
+                                     _stream_for(kind, stream)))
+    return out
 
 
 def version() -> str:
