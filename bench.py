@@ -3,10 +3,11 @@
 
 Workload (one step): exp(A) for three seeded FP64 1024 x 1024 matrices with N(0,1) entries
 rescaled to ||A||_1 = 0.5, 4 and 32 (0, 2 and 5 squarings), Taylor degree m = 30, s = 6,
-evaluated by ``expm_taylor_ss`` through the C ABI.  The headline value is the mixed
-policy (per-step precision by eq. (2.8), FP64 floors on the last two Horner steps); the
-fixed-FP64 path (Algorithm 2.1 in FP64 throughout) is timed beside it, and both errors are
-measured against the double-double oracle on sampled columns.
+evaluated by ``expm_taylor_ss`` through the C ABI.  The headline value is the mixed policy
+(per-step precision by eq. (2.8), the last two Horner steps in the working precision) with
+the working-precision products emulated on the tensor cores; the fixed-FP64 path
+(Algorithm 2.1 on the FP64 pipe throughout) and the other policies are timed beside it,
+and every policy's error is measured against the double-double oracle on sampled columns.
 
 One JSON line on rank 0.  Under torchrun (N > 1) every rank evaluates its own copy of the
 workload (independent replicas, no collective); value = evaluations of all ranks / slowest
@@ -40,11 +41,14 @@ def parse():
     ap.add_argument("--impl", default="mpps", choices=["mpps", "reference"])
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--m", type=int, default=30)
-    ap.add_argument("--policy", default="ns", choices=["ns", "paper", "fixed"])
+    ap.add_argument("--policy", default="ns_e",
+                    choices=["ns_e", "paper_e", "fixed_e", "ns", "paper", "fixed"],
+                    help="headline policy (the others are timed beside it)")
     ap.add_argument("--no-check", action="store_true", help="skip the oracle error check")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel", default=None,
-                    choices=["gemm_f64", "gemm_bf16", "gemm_bf16x3", "gemm_tf32", "gemm_fp8"],
+                    choices=["gemm_f64", "gemm_bf16", "gemm_bf16x3", "gemm_tf32", "gemm_fp8",
+                             "gemm_f64e9", "gemm_f64e6"],
                     help="time one product kernel alone (mpps_matmul) instead of the workload")
     ap.add_argument("--batch", type=int, default=1, help="batch for --kernel")
     return ap.parse_args()
@@ -67,14 +71,15 @@ def run_kernel(args):
     for _ in range(args.warmup):
         mpps.matmul(A, B, fmt, out=C)
     torch.cuda.synchronize()
-    cls = mpps.PROF_GEMM_F64 if fmt == "fp64" else mpps.PROF_GEMM_TC
+    cls = (mpps.PROF_GEMM_F64 if fmt == "fp64" else
+           mpps.PROF_GEMM_F64E if fmt.startswith("f64e") else mpps.PROF_GEMM_TC)
     mpps.profile_enable(True)
     mpps.profile_reset()
     for _ in range(args.steps):
         flush.fill_(1.0)
         mpps.matmul(A, B, fmt, out=C)
     torch.cuda.synchronize()
-    launches, ms = mpps.profile_read(cls)
+    launches, ms, _ = mpps.profile_read(cls)
     mpps.profile_enable(False)
     avg = ms / max(1, launches)
     tflops = 2.0 * n ** 3 * b / (avg / 1e3) / 1e12
@@ -198,6 +203,25 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+POLICY_DESC = {
+    "ns_e": "mixed (eq. (2.8), FP64 floors on steps 1-2), working-precision products emulated "
+            "with 9 exact bf16 slices on tcgen05",
+    "paper_e": "mixed (eq. (2.8) as in Algorithm 3.1), emulated working precision",
+    "fixed_e": "fixed working precision, every product emulated (9 slices)",
+    "ns": "mixed (eq. (2.8), FP64 floors on steps 1-2), working precision on the FP64 pipe",
+    "paper": "mixed (eq. (2.8) as in Algorithm 3.1), FP64 pipe",
+    "fixed": "fixed FP64 on the FP64 pipe (Algorithm 2.1 + eq. (3.6))",
+}
+
+
+def peak_bf16_tflops():
+    try:
+        pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return pk.get("bf16_tflops_sustained", 1700.0), "measured bf16 sustained"
+    except Exception:
+        return 1700.0, "fallback bf16 sustained"
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -224,88 +248,89 @@ def main():
     torch.cuda.set_device(dev)
     mpps.lib()
     n, m = args.n, args.m
-    pol = {"ns": mpps.NS, "paper": mpps.PAPER, "fixed": mpps.FIXED}[args.policy]
+    pols = {"ns_e": mpps.NS_E, "paper_e": mpps.PAPER_E, "fixed_e": mpps.FIXED_E,
+            "ns": mpps.NS, "paper": mpps.PAPER, "fixed": mpps.FIXED}
+    head = args.policy
+    order = [head] + [p for p in ("fixed", "ns", "fixed_e", "ns_e") if p != head]
     mats = make_inputs(n)
     dA = [torch.from_numpy(A).to(dev) for A in mats]
-    dE = [torch.empty_like(a) for a in dA]
+    outs = {p: [torch.empty_like(a) for a in dA] for p in order}
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
     stream = torch.cuda.current_stream(dev)
+    classes = (mpps.PROF_GEMM_F64, mpps.PROF_GEMM_F64E, mpps.PROF_GEMM_TC, mpps.PROF_ELEMENTWISE)
+    cname = {mpps.PROF_GEMM_F64: "gemm_f64", mpps.PROF_GEMM_F64E: "gemm_f64e",
+             mpps.PROF_GEMM_TC: "gemm_tc", mpps.PROF_ELEMENTWISE: "elementwise"}
 
-    def step(policy, reports=None):
+    def step(p, reports=None):
         for k in range(len(dA)):
             if reports is not None:
-                _, rep = mpps.expm(dA[k], m=m, policy=policy, out=dE[k], report=True)
+                _, rep = mpps.expm(dA[k], m=m, policy=pols[p], out=outs[p][k], report=True)
                 reports.append(rep[0])
             else:
-                mpps.expm(dA[k], m=m, policy=policy, out=dE[k])
+                mpps.expm(dA[k], m=m, policy=pols[p], out=outs[p][k])
 
-    def timed(policy, steps, sampler=None, profile=False):
+    def timed(p, steps):
         times = []
-        if profile:
-            mpps.profile_enable(True)
-            mpps.profile_reset()
+        mpps.profile_enable(True)
+        mpps.profile_reset()
         for _ in range(steps):
             flush.fill_(1.0)
             e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            step(policy)
+            step(p)
             e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
-        prof = None
-        if profile:
-            prof = {c: mpps.profile_read(c) for c in (mpps.PROF_GEMM_F64, mpps.PROF_GEMM_TC,
-                                                      mpps.PROF_ELEMENTWISE)}
-            mpps.profile_enable(False)
-            mpps.profile_reset()
+        prof = {c: mpps.profile_read(c) for c in classes}
+        mpps.profile_enable(False)
+        mpps.profile_reset()
         return times, prof
 
-    # warm-up (both policies), reports for the flop counts
-    reps_mixed, reps_fixed = [], []
-    step(pol, reps_mixed)
-    step(mpps.FIXED, reps_fixed)
-    for _ in range(max(0, args.warmup - 1)):
-        step(pol); step(mpps.FIXED)
+    reps = {}
+    for p in order:
+        reps[p] = []
+        step(p, reps[p])
+        for _ in range(max(0, args.warmup - 1)):
+            step(p)
     torch.cuda.synchronize()
 
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(dev.index) as clk:
-        t_mixed, prof = timed(pol, args.steps, profile=True)
-    torch.cuda.synchronize()
-    t_fixed, _ = timed(mpps.FIXED, args.steps)
-    torch.cuda.synchronize()
+    results = {}
+    clk = None
+    for p in order:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if p == head:
+            with ClockSampler(dev.index) as clk:
+                t, prof = timed(p, args.steps)
+        else:
+            t, prof = timed(p, args.steps)
+        torch.cuda.synchronize()
+        ms = sum(t) / len(t)
+        if dist:
+            tt = torch.tensor([ms], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms = float(tt[0])
+        prods = sum(sum(v for k, v in R["gemms"].items()) for R in reps[p])
+        results[p] = {"evals_per_s": len(dA) * world / (ms / 1e3), "ms_per_step": ms,
+                      "tflops_fp64_equiv": prods * 2.0 * n ** 3 * world / (ms / 1e3) / 1e12,
+                      "kernels": {cname[c]: {"launches": prof[c][0] // args.steps,
+                                             "ms_per_step": prof[c][1] / args.steps,
+                                             "executed_tflops": (prof[c][2] / prof[c][1] / 1e9)
+                                             if prof[c][1] > 0 and prof[c][2] > 0 else None}
+                                  for c in classes},
+                      "formats": [R["fmt"][1:] for R in reps[p]],
+                      "policy": POLICY_DESC[p], "_prof": prof}
 
-    ms_mixed = sum(t_mixed) / len(t_mixed)
-    ms_fixed = sum(t_fixed) / len(t_fixed)
-    if dist:
-        tt = torch.tensor([ms_mixed, ms_fixed], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_mixed, ms_fixed = float(tt[0]), float(tt[1])
-    evals = len(dA) * world
-    value = evals / (ms_mixed / 1e3)
-    fixed_value = evals / (ms_fixed / 1e3)
-
-    def flops(reps):
-        tot = 0
-        for R in reps:
-            g = sum(v for k, v in R["gemms"].items() if k != "squarings") + R["gemms"]["squarings"]
-            tot += g * 2.0 * n ** 3
-        return tot
-
-    tflops_mixed = flops(reps_mixed) * world / (ms_mixed / 1e3) / 1e12
-    tflops_fixed = flops(reps_fixed) * world / (ms_fixed / 1e3) / 1e12
-
-    # e2e: host buffers through the C ABI (H2D + D2H inside the timed region)
+    # e2e: host buffers through the C ABI (H2D + D2H inside the timed region), headline policy
     host_in = [np.ascontiguousarray(A) for A in mats]
     host_out = [np.empty_like(A) for A in mats]
     for k in range(len(mats)):
-        mpps.expm(host_in[k], m=m, policy=pol, out=host_out[k])
+        mpps.expm(host_in[k], m=m, policy=pols[head], out=host_out[k])
     t0 = time.perf_counter()
     for _ in range(args.steps):
         for k in range(len(mats)):
-            mpps.expm(host_in[k], m=m, policy=pol, out=host_out[k])
+            mpps.expm(host_in[k], m=m, policy=pols[head], out=host_out[k])
     e2e_s = time.perf_counter() - t0
     e2e_value = len(mats) * args.steps * world / e2e_s
 
@@ -315,27 +340,12 @@ def main():
             dist.destroy_process_group()
         return
 
-    # dominant kernel: the FP64 product (powers, early Horner steps, squarings)
-    f64_launches, f64_ms = prof[mpps.PROF_GEMM_F64]
-    tc_launches, tc_ms = prof[mpps.PROF_GEMM_TC]
-    el_launches, el_ms = prof[mpps.PROF_ELEMENTWISE]
-    peak, peak_src = peak_fp64_tflops()
-    avg_f64 = f64_ms / max(1, f64_launches)
-    achieved = 2.0 * n ** 3 / (avg_f64 / 1e3) / 1e12
-    roofline = {"bound": "tensor", "kernel": "k_gemm_f64 (DMMA m16n8k4 f64)", "achieved": achieved,
-                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": peak_src,
-                "share_of_step": f64_ms / max(1e-9, sum(t_mixed))}
-
     errs = None
     if not args.no_check:
         import oracle
         cols = [0, n // 2, n - 1]
-        errs = {"mixed": [], "fixed": []}
-        E_mixed = [e.cpu().numpy() for e in dE]
-        step(mpps.FIXED)
         torch.cuda.synchronize()
-        E_fixed = [e.cpu().numpy() for e in dE]
+        errs = {p: [] for p in order}
         for k, A in enumerate(mats):
             sg = oracle.sigma_for(A)
             V = np.zeros((n, len(cols)))
@@ -343,32 +353,55 @@ def main():
                 V[j, t] = 1.0
             wh, wl = oracle.ps_apply_dd(oracle.taylor_exp_rational(m), np.ldexp(A, -sg), V, 2 ** sg)
             ref = np.abs(wh).sum(axis=0)
-            for name, E in (("mixed", E_mixed[k]), ("fixed", E_fixed[k])):
-                errs[name].append(float(np.max(np.abs(E[:, cols] - wh - wl).sum(axis=0) / ref)))
+            for p in order:
+                E = outs[p][k].cpu().numpy()
+                errs[p].append(float(np.max(np.abs(E[:, cols] - wh - wl).sum(axis=0) / ref)))
+        for p in order:
+            results[p]["rel_err_1norm_sampled"] = errs[p]
 
+    # roofline of the headline path's dominant kernel class
+    hp = results[head]["_prof"]
+    dom = max(classes, key=lambda c: hp[c][1])
+    launches, ms_tot, work = hp[dom]
+    achieved = work / (ms_tot / 1e3) / 1e12 if ms_tot > 0 else 0.0
+    if dom == mpps.PROF_GEMM_F64:
+        peak, src = peak_fp64_tflops()
+        kern = "k_gemm_f64 (DMMA m16n8k4 f64)"
+    else:
+        peak, src = peak_bf16_tflops()
+        kern = ("k_gemm_f64e (tcgen05 kind::f16, exact bf16 slice products; achieved counts "
+                "executed bf16 flops)" if dom == mpps.PROF_GEMM_F64E else "k_gemm_tc (tcgen05)")
+    step_ms_tot = results[head]["ms_per_step"] * args.steps
+    roofline = {"bound": "tensor", "kernel": kern, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "peak_source": src,
+                "share_of_step": ms_tot / step_ms_tot, "launches_per_step": launches // args.steps}
+    for p in order:
+        results[p].pop("_prof")
+
+    value = results[head]["evals_per_s"]
+    fixed_value = results["fixed"]["evals_per_s"]
+    gpu_launches = sum(results[head]["kernels"][k]["launches"] for k in results[head]["kernels"]) * args.steps
     line = {
         "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_mixed,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": results[head]["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64 (mixed: low-precision tensor-core Horner products)", "data": "synthetic",
+        "dtype": "f64 (mixed: bf16 tensor-core slices and low-precision Horner products)",
+        "data": "synthetic",
         "config": {"workload": f"expm_taylor_ss n={n} m={m} s=6, one matrix each at "
                                f"||A||_1 in {list(NORMS)} (sigma 0/2/5), N(0,1) entries, seed {SEED}+k",
-                   "policy": args.policy, "l2": "flushed (256 MiB write) before every step",
+                   "policy": head, "l2": "flushed (256 MiB write) before every step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "tflops": tflops_mixed,
-        "fixed": {"value": fixed_value, "unit": "evals/s", "ms_per_step": ms_fixed,
-                  "tflops": tflops_fixed},
+        "tflops": results[head]["tflops_fp64_equiv"],
+        "fixed": {"value": fixed_value, "unit": "evals/s", "ms_per_step": results["fixed"]["ms_per_step"],
+                  "tflops": results["fixed"]["tflops_fp64_equiv"], "policy": POLICY_DESC["fixed"]},
         "speedup_vs_fixed": value / fixed_value,
-        "rel_err_1norm_sampled": errs,
-        "formats": [R["fmt"][1:] for R in reps_mixed],
+        "policies": results,
         "roofline": roofline,
-        "kernels_ms_per_step": {"gemm_f64": f64_ms / args.steps, "gemm_tc": tc_ms / args.steps,
-                                "elementwise": el_ms / args.steps},
-        "gpu_launches": int(f64_launches + tc_launches + el_launches),
+        "gpu_launches": int(gpu_launches),
         "e2e": {"value": e2e_value, "unit": "evals/s",
                 "h2d_bytes_per_step": len(mats) * n * n * 8,
                 "d2h_bytes_per_step": len(mats) * n * n * 8},
-        "clocks": clk.summary(),
+        "clocks": clk.summary() if clk else None,
     }
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(n, m, mats)

@@ -67,6 +67,14 @@ typedef enum {
     MPPS_FMT_FP8 = 4
 } mpps_format;
 
+/* FP64 products emulated on the BF16 tensor cores with k exact integer slices per operand
+ * (MPPS_FMT_F64E(k), 1 <= k <= MPPS_F64E_MAX_SLICES): error about 2^(3-6k) relative to the
+ * row and column maxima of the operands; k = 9 is FP64-level.  Cost k(k+1)/2 BF16 products. */
+#define MPPS_F64E_MAX_SLICES 10
+#define MPPS_FMT_F64E(k) (16 + (k))
+#define MPPS_FMT_IS_F64E(f) ((f) > 16 && (f) <= 16 + MPPS_F64E_MAX_SLICES)
+#define MPPS_F64E_SLICES(f) ((f) - 16)
+
 #define MPPS_NUM_FORMATS 5
 #define MPPS_MAX_R 64      /* largest r = floor(m/s) a report can describe */
 #define MPPS_MAX_S 32      /* largest block size s */
@@ -78,6 +86,9 @@ typedef struct {
     int s;                  /* PS block size; 0 -> ceil(sqrt(m)) (Algorithm 2.1) */
     unsigned formats;       /* bit f allows format f; 0 -> all; FP64 is always allowed */
     int fp64_floor_steps;   /* MIXED_NS: steps i <= this stay FP64; < 0 -> 2 */
+    int f64_slices;         /* 0: working-precision products on the FP64 pipe (DMMA);
+                               k in 1..MPPS_F64E_MAX_SLICES: emulate them as MPPS_FMT_F64E(k),
+                               and let mixed steps use F64E(k') for k' < k as well */
 } mpps_policy;
 
 /* Per-matrix description of what a call did (filled when `rep` is non-NULL). */
@@ -94,7 +105,8 @@ typedef struct {
     double cost_ratio;               /* eq. (3.8) with the digits of the chosen formats */
 } mpps_report;
 
-/* Fill *p with the defaults: MIXED_NS, tol 2^-53, delta 10, s 0, all formats, floor 2. */
+/* Fill *p with the defaults: MIXED_NS, tol 2^-53, delta 10, s 0, all formats, floor 2,
+ * f64_slices 0 (working-precision products on the FP64 pipe). */
 void mpps_policy_default(mpps_policy* p);
 
 /*
@@ -147,7 +159,9 @@ mpps_status ps_eval_adjoint(const double* coeffs, int m, const double* A, const 
 
 /*
  * C = A B for a batch of n x n FP64 matrices, the product computed in `format`
- * (an mpps_format other than NONE): the building block of every step above.  For the
+ * (an mpps_format other than NONE, or MPPS_FMT_F64E(k)): the building block of every step
+ * above.  MPPS_FMT_F64E(k) splits the rows of A and the columns of B into k exact bf16
+ * slices and sums the slice products exactly on the tensor cores.  For the
  * low-precision formats each operand is scaled by a power of two chosen from its largest
  * entry, rounded to the format, multiplied on the tensor cores with FP32 accumulation,
  * and the result scaled back in FP64.  Asynchronous for device pointers.
@@ -168,7 +182,8 @@ mpps_status mpps_matmul(const double* A, const double* B, double* C, int n, int 
  * MPPS_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that loads the library
  * holds until the process exits.
  *   A, B, C : device pointers only (host pointers give MPPS_EINVAL); batch x n x n FP64,
- *             row-major; C may not alias A or B.  format as in mpps_matmul.
+ *             row-major; C may not alias A or B.  format: MPPS_FMT_FP64 .. MPPS_FMT_FP8
+ *             (the emulated MPPS_FMT_F64E(k) products are not offered here).
  *   Sizes whose scratch exceeds MPPS_NOALLOC_SCRATCH_BYTES give MPPS_EINVAL (the limit
  *   fits one 2048 x 2048 product in any format; FP64 products use no scratch).
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress
@@ -183,18 +198,22 @@ mpps_status mpps_matmul_noalloc(const double* A, const double* B, double* C, int
 
 /* Benchmark instrumentation (off by default).  When enabled, every kernel launch of the
  * library is bracketed by two CUDA events recorded on the launch stream and tagged with a
- * kernel class: MPPS_PROF_GEMM_F64 (FP64 products), MPPS_PROF_GEMM_TC (tensor-core
- * products), MPPS_PROF_ELEMENTWISE (block sums, norms, conversions, copies).
- * mpps_profile_read waits for the recorded events and returns the number of launches and
- * their summed durations (ms) of one class since the last reset.  Do not enable it while
- * a stream is being captured into a CUDA graph. */
+ * kernel class: MPPS_PROF_GEMM_F64 (FP64-pipe products), MPPS_PROF_GEMM_TC (low-precision
+ * tensor-core products), MPPS_PROF_ELEMENTWISE (block sums, norms, conversions, slicing,
+ * copies), MPPS_PROF_GEMM_F64E (emulated FP64 products).  mpps_profile_read waits for the
+ * recorded events and returns, for one class since the last reset, the number of launches,
+ * their summed durations (ms) and their summed executed flops (products: 2 n^3 per matrix
+ * times the number of tensor-core products issued; total_work may be NULL).  Do not enable
+ * it while a stream is being captured into a CUDA graph. */
 #define MPPS_PROF_GEMM_F64 0
 #define MPPS_PROF_GEMM_TC 1
 #define MPPS_PROF_ELEMENTWISE 2
-#define MPPS_PROF_NUM_CLASSES 3
+#define MPPS_PROF_GEMM_F64E 3
+#define MPPS_PROF_NUM_CLASSES 4
 void mpps_profile_enable(int on);
 void mpps_profile_reset(void);
-mpps_status mpps_profile_read(int kernel_class, long long* launches, double* total_ms);
+mpps_status mpps_profile_read(int kernel_class, long long* launches, double* total_ms,
+                              double* total_work);
 
 /* Description of the last failure on this thread ("" if none). */
 const char* mpps_last_error(void);

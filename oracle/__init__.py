@@ -305,8 +305,14 @@ FP32_ACC = 2.0 ** -24
 MODE_FIXED, MODE_PAPER, MODE_NS = 0, 1, 2
 
 
+def FMT_F64E(k):
+    """Format code of a product emulated with k exact slices (same numbering as the library)."""
+    return 16 + k
+
+
 def plan(m: int, n: int, norms, normY: float, mode: int = MODE_PAPER, tol: float = 2.0 ** -53,
-         delta: float = 10.0, s: int = 0, formats: int = 0x1F, floor_steps: int = 2):
+         delta: float = 10.0, s: int = 0, formats: int = 0x1F, floor_steps: int = 2,
+         f64_slices: int = 0):
     """Per-step precisions for the Horner products P_i Y, i = r..1.
 
     1. s = ceil(sqrt(m)) unless given; r = floor(m/s).
@@ -318,7 +324,10 @@ def plan(m: int, n: int, norms, normY: float, mode: int = MODE_PAPER, tol: float
     4. format_i = the cheapest allowed format F with U_FMT[F] <= u_i and, for formats that
        accumulate in FP32, n * 2^-24 <= u_i (Section 4.1.1's rule max{u* <= u_i}, with the
        accumulation error of the tensor cores added).  FP64 is always allowed.
-    5. mode NS: steps i <= floor_steps stay FP64.  mode FIXED: every step FP64.
+       With f64_slices = K > 0 the working precision is an emulated product with K slices
+       (format F64E(K)) and the ladder continues after BF16X3 with F64E(k), k = 4..K-1,
+       whose unit roundoff is taken as 2^(3-6k) (exact accumulation: no n 2^-24 term).
+    5. mode NS: steps i <= floor_steps stay in the working precision.  FIXED: every step.
     6. When s divides m, B_r = b_m I and step r is a scalar multiple of Y: no product
        (format NONE).
     Returns dict(s, r, nu, u (list, index 1..r), fmt (index 1..r), fold).
@@ -346,16 +355,24 @@ def plan(m: int, n: int, norms, normY: float, mode: int = MODE_PAPER, tol: float
     for i in range(1, nu):
         u[i] = tol
     order = [FMT_FP8, FMT_BF16, FMT_TF32, FMT_BF16X3]
+    wp = FMT_F64E(f64_slices) if f64_slices > 0 else FMT_FP64
     fmt = [None] * (r + 1)
     for i in range(1, r + 1):
-        f = FMT_FP64
+        f = wp
         if mode != MODE_FIXED and not (mode == MODE_NS and i <= floor_steps):
+            found = False
             for F in order:
                 if not (formats >> F) & 1:
                     continue
                 if U_FMT[F] <= u[i] and n * FP32_ACC <= u[i]:
                     f = F
+                    found = True
                     break
+            if not found:
+                for k in range(4, f64_slices):
+                    if 2.0 ** (3 - 6 * k) <= u[i]:
+                        f = FMT_F64E(k)
+                        break
         fmt[i] = f
     if fold:
         fmt[r] = FMT_NONE

@@ -30,8 +30,17 @@ _lib = None
 
 FIXED_FP64, MIXED_PAPER, MIXED_NS = 0, 1, 2
 FMT_NONE, FMT_FP64, FMT_BF16X3, FMT_TF32, FMT_BF16, FMT_FP8 = -1, 0, 1, 2, 3, 4
+F64E_MAX_SLICES = 10
+
+
+def FMT_F64E(k: int) -> int:
+    """Format code of an FP64 product emulated with k exact bf16 slices per operand."""
+    return 16 + int(k)
+
+
 FORMAT_NAMES = {FMT_NONE: "none", FMT_FP64: "fp64", FMT_BF16X3: "bf16x3", FMT_TF32: "tf32",
                 FMT_BF16: "bf16", FMT_FP8: "fp8"}
+FORMAT_NAMES.update({FMT_F64E(k): f"f64e{k}" for k in range(1, F64E_MAX_SLICES + 1)})
 _FMT_BY_NAME = {v: k for k, v in FORMAT_NAMES.items()}
 MAX_R = 64
 MAX_S = 32
@@ -49,7 +58,8 @@ class MppsError(RuntimeError):
 
 class _Policy(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("tol", ctypes.c_double), ("delta", ctypes.c_double),
-                ("s", ctypes.c_int), ("formats", ctypes.c_uint), ("fp64_floor_steps", ctypes.c_int)]
+                ("s", ctypes.c_int), ("formats", ctypes.c_uint), ("fp64_floor_steps", ctypes.c_int),
+                ("f64_slices", ctypes.c_int)]
 
 
 class _Report(ctypes.Structure):
@@ -64,7 +74,7 @@ class _Report(ctypes.Structure):
 EXPORTS = ("mpps_policy_default", "mpps_plan", "ps_eval", "expm_taylor_ss", "ps_eval_adjoint",
            "mpps_matmul", "mpps_last_error", "mpps_version", "mpps_profile_enable",
            "mpps_profile_reset", "mpps_profile_read", "mpps_matmul_noalloc")
-PROF_GEMM_F64, PROF_GEMM_TC, PROF_ELEMENTWISE = 0, 1, 2
+PROF_GEMM_F64, PROF_GEMM_TC, PROF_ELEMENTWISE, PROF_GEMM_F64E = 0, 1, 2, 3
 
 
 def lib():
@@ -95,6 +105,7 @@ def lib():
         L.mpps_profile_reset.argtypes = []
         L.mpps_profile_reset.restype = None
         L.mpps_profile_read.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
+                                        ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_double)]
         L.mpps_profile_read.restype = ctypes.c_int
         L.mpps_last_error.restype = ctypes.c_char_p
@@ -120,6 +131,7 @@ class Policy:
     s: int = 0
     formats: object = 0x1F          # bitmask or iterable of format names
     fp64_floor_steps: int = 2
+    f64_slices: int = 0             # 0: FP64 pipe; k: emulate FP64 products with k slices
 
     def _c(self):
         fm = self.formats
@@ -129,12 +141,16 @@ class Policy:
                 mask |= 1 << _FMT_BY_NAME[name]
             fm = mask
         return _Policy(int(self.mode), float(self.tol), float(self.delta), int(self.s),
-                       int(fm), int(self.fp64_floor_steps))
+                       int(fm), int(self.fp64_floor_steps), int(self.f64_slices))
 
 
 FIXED = Policy(mode=FIXED_FP64)
 PAPER = Policy(mode=MIXED_PAPER)
 NS = Policy(mode=MIXED_NS)
+# the same rules with the working-precision products emulated on the tensor cores (9 slices)
+FIXED_E = Policy(mode=FIXED_FP64, f64_slices=9)
+PAPER_E = Policy(mode=MIXED_PAPER, f64_slices=9)
+NS_E = Policy(mode=MIXED_NS, f64_slices=9)
 
 
 def _report_dict(R: _Report) -> dict:
@@ -326,11 +342,13 @@ def profile_reset() -> None:
 
 
 def profile_read(kernel_class: int):
-    """(launches, total ms) of one kernel class since the last reset."""
+    """(launches, total ms, total executed flops) of one kernel class since the last reset."""
     cnt = ctypes.c_longlong(0)
     ms = ctypes.c_double(0.0)
-    _check(lib().mpps_profile_read(int(kernel_class), ctypes.byref(cnt), ctypes.byref(ms)))
-    return int(cnt.value), float(ms.value)
+    work = ctypes.c_double(0.0)
+    _check(lib().mpps_profile_read(int(kernel_class), ctypes.byref(cnt), ctypes.byref(ms),
+                                   ctypes.byref(work)))
+    return int(cnt.value), float(ms.value), float(work.value)
 
 
 def matmul_noalloc(A, B, out, fmt="fp64", stream=None):

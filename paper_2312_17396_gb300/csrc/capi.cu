@@ -31,6 +31,7 @@ struct Pol {
     int s;
     unsigned formats;
     int floor_steps;
+    int f64k;   // 0: FP64 pipe; k > 0: working-precision products emulated with k slices
 };
 
 static Pol resolve(const mpps_policy* p) {
@@ -44,6 +45,7 @@ static Pol resolve(const mpps_policy* p) {
     r.s = p->s;
     r.formats = (p->formats ? p->formats : 0x1Fu) | 1u;
     r.floor_steps = p->fp64_floor_steps < 0 ? 2 : p->fp64_floor_steps;
+    r.f64k = p->f64_slices;
     return r;
 }
 
@@ -61,6 +63,31 @@ static const double kAcc = 0x1p-24;
 
 static bool is_low(int f) { return f >= MPPS_FMT_BF16X3 && f <= MPPS_FMT_FP8; }
 
+// Unit roundoff assigned to an emulated product with k slices: 2^(3-6k) (the slices keep 6k
+// bits below the row/column maxima; the constant covers the dropped diagonal t + q = k).
+static double u_f64e(int k) { return ldexp(1.0, 3 - 6 * k); }
+
+static double unit_roundoff(int f) {
+    if (MPPS_FMT_IS_F64E(f)) return u_f64e(MPPS_F64E_SLICES(f));
+    return (f >= 0 && f < MPPS_NUM_FORMATS) ? kUFmt[f] : 1.0;
+}
+
+// Precision rank: larger = more precise (used to run a batch step at its most precise ask).
+static int prec_rank(int f) {
+    if (f == MPPS_FMT_FP64) return 1000;
+    if (MPPS_FMT_IS_F64E(f)) return 100 + MPPS_F64E_SLICES(f);
+    switch (f) {
+        case MPPS_FMT_BF16X3: return 4;
+        case MPPS_FMT_TF32: return 3;
+        case MPPS_FMT_BF16: return 2;
+        case MPPS_FMT_FP8: return 1;
+        default: return 0;
+    }
+}
+
+// Smallest emulated slice count that always counts as "cheaper than the working precision".
+static const int kF64eMinRung = 4;
+
 // Planner for one matrix.  normB: r+1 norms ||B_0||..||B_r||; normY = ||X^s||.
 static mpps_status plan_one(int m, int n, const double* normB, double normY, const Pol& P,
                             mpps_report* out) {
@@ -75,6 +102,10 @@ static mpps_status plan_one(int m, int n, const double* normB, double normY, con
     int s = P.s > 0 ? std::min(P.s, m) : ceil_sqrt_int(m);
     if (s > MPPS_MAX_S) {
         set_error("block size s=%d exceeds %d", s, MPPS_MAX_S);
+        return MPPS_EINVAL;
+    }
+    if (P.f64k < 0 || P.f64k > MPPS_F64E_MAX_SLICES) {
+        set_error("f64_slices=%d outside 0..%d", P.f64k, MPPS_F64E_MAX_SLICES);
         return MPPS_EINVAL;
     }
     const int r = m / s;
@@ -102,17 +133,23 @@ static mpps_status plan_one(int m, int n, const double* normB, double normY, con
         if (out->u[i] >= P.delta * tol) { nu = i; break; }
     for (int i = 1; i < nu; ++i) out->u[i] = tol;
     out->nu = nu;
-    // formats: cheapest allowed with unit roundoff <= u_i (and FP32 accumulation <= u_i)
+    // formats: cheapest allowed with unit roundoff <= u_i (and FP32 accumulation <= u_i for
+    // the hardware formats); with emulation on, the slice counts 4..k-1 sit between BF16X3
+    // and the working precision (their accumulation is exact)
     static const int order[4] = {MPPS_FMT_FP8, MPPS_FMT_BF16, MPPS_FMT_TF32, MPPS_FMT_BF16X3};
+    const int wp = P.f64k > 0 ? MPPS_FMT_F64E(P.f64k) : MPPS_FMT_FP64;
     for (int i = 1; i <= r; ++i) {
-        int f = MPPS_FMT_FP64;
+        int f = wp;
         const bool floor_fp64 = (P.mode == MPPS_MIXED_NS && i <= P.floor_steps);
         if (P.mode != MPPS_FIXED_FP64 && !floor_fp64) {
-            for (int k = 0; k < 4; ++k) {
+            bool found = false;
+            for (int k = 0; k < 4 && !found; ++k) {
                 const int F = order[k];
                 if (!((P.formats >> F) & 1u)) continue;
-                if (kUFmt[F] <= out->u[i] && (double)n * kAcc <= out->u[i]) { f = F; break; }
+                if (kUFmt[F] <= out->u[i] && (double)n * kAcc <= out->u[i]) { f = F; found = true; }
             }
+            for (int k = kF64eMinRung; k < P.f64k && !found; ++k)
+                if (u_f64e(k) <= out->u[i]) { f = MPPS_FMT_F64E(k); found = true; }
         }
         out->fmt[i] = f;
     }
@@ -126,7 +163,7 @@ static double cost_ratio(const mpps_report& rp, double tol) {
     const double D = -log10(tol);
     double sum = 0.0;
     for (int i = 1; i <= rp.r; ++i)
-        if (rp.fmt[i] >= 0) sum += std::min(D, -log10(kUFmt[rp.fmt[i]]));
+        if (rp.fmt[i] >= 0) sum += std::min(D, -log10(unit_roundoff(rp.fmt[i])));
     const double den = (rp.s + rp.r - 1) * D;
     return den > 0 ? ((rp.s - 1) * D + sum) / den : 1.0;
 }
@@ -214,10 +251,12 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
     const int q = block_norms_count(m, s);
     const long long pw_bs = (long long)s * nn;
 
-    // ---- phase-1 workspace (FP64 part)
+    // ---- phase-1 workspace (FP64 part, and slice planes when FP64 is emulated)
+    const int K = pol.f64k;                      // slices of an emulated working-precision product
     Arena L;
-    double *d_coef, *pw, *Pb0, *Pb1, *partial, *norms;
-    int *d_sigma, *d_err, *d_bidx;
+    double *d_coef, *pw, *Pb0, *Pb1, *partial, *norms, *d_anorm, *tmpT = nullptr;
+    int *d_sigma, *d_err, *d_bidx, *eA = nullptr, *eB = nullptr, *eY = nullptr;
+    __nv_bfloat16 *slA = nullptr, *slB = nullptr, *slY = nullptr;
     auto layout1 = [&](Arena& a) {
         d_coef = a.take<double>(m + 1);
         pw = a.take<double>((size_t)batch * pw_bs);
@@ -226,9 +265,19 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
         partial = a.take<double>(std::max(block_norms_partial_elems(n, batch, m, s),
                                           norm1_partial_elems(n, batch)));
         norms = a.take<double>((size_t)batch * q);
+        d_anorm = a.take<double>(batch);
         d_sigma = a.take<int>(batch);
         d_err = a.take<int>(1);
         d_bidx = a.take<int>((size_t)batch * 64);
+        if (K > 0) {
+            slA = a.take<__nv_bfloat16>(f64e_plane_elems(n, batch, K));
+            slB = a.take<__nv_bfloat16>(f64e_plane_elems(n, batch, K));
+            slY = a.take<__nv_bfloat16>(f64e_plane_elems(n, batch, K));
+            eA = a.take<int>((size_t)batch * n);
+            eB = a.take<int>((size_t)batch * n);
+            eY = a.take<int>((size_t)batch * n);
+            tmpT = a.take<double>((size_t)batch * nn);
+        }
     };
     layout1(L);
     DevBuf ws1;
@@ -240,36 +289,37 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
     MPPS_CUDA_TRY(cudaMemcpyAsync(d_coef, coeffs, sizeof(double) * (m + 1), cudaMemcpyHostToDevice, st));
     MPPS_CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), st));
 
+    // emulated product helper: B^T rows (= columns of B) sliced straight from B
+    auto slice_cols = [&](const double* Bm, long long bs, int k, __nv_bfloat16* planes,
+                          int* ex) -> mpps_status {
+        return launch_slice_cols(Bm, bs, n, batch, k, planes, ex, (unsigned long long*)tmpT, st);
+    };
+
     // ---- a1: scaling (expm) or plain copy into X_1
     std::vector<int> sigma(batch, 0);
-    std::vector<double> h_norm(batch, 0.0);
     if (expm) {
-        rc = launch_norm1(dA, nn, n, batch, partial, norms, st);
-        if (rc) return rc;
-        MPPS_CUDA_TRY(cudaMemcpyAsync(h_norm.data(), norms, sizeof(double) * batch,
-                                      cudaMemcpyDeviceToHost, st));
-        MPPS_CUDA_TRY(cudaStreamSynchronize(st));
-        for (int b = 0; b < batch; ++b) {
-            const double a = h_norm[b];
-            int e = 0;
-            if (a > 1.0 && isfinite(a)) {
-                double f = frexp(a, &e);        // a = f 2^e, f in [0.5, 1)
-                if (f == 0.5) e -= 1;           // a a power of two: log2 a exactly
-            }
-            sigma[b] = e;                        // max(0, ceil(log2 ||A||_1))
-        }
-        MPPS_CUDA_TRY(cudaMemcpyAsync(d_sigma, sigma.data(), sizeof(int) * batch,
-                                      cudaMemcpyHostToDevice, st));
-        rc = launch_scale_copy(dA, nn, pw, pw_bs, n, batch, d_sigma, st);
+        // sigma = max(0, ceil(log2 ||A||_1)) on the device; read back with the block norms
+        rc = launch_norm1(dA, nn, n, batch, partial, d_anorm, st);
+        if (!rc) rc = launch_sigma(d_anorm, batch, d_sigma, st);
+        if (!rc) rc = launch_scale_copy(dA, nn, pw, pw_bs, n, batch, d_sigma, st);
     } else {
         rc = launch_scale_copy(dA, nn, pw, pw_bs, n, batch, nullptr, st);
     }
     if (rc) return rc;
 
-    // ---- a2: powers X_j = X_{j-1} X_1, FP64
+    // ---- a2: powers X_j = X_{j-1} X_1 in the working precision (FP64 pipe or emulated)
+    if (K > 0 && s >= 2) {
+        rc = slice_cols(pw, pw_bs, K, slB, eB);
+        if (rc) return rc;
+    }
     for (int j = 2; j <= s; ++j) {
         Epilogue ep = epilogue_plain(pw + (long long)(j - 1) * nn, pw_bs);
-        rc = launch_gemm_f64(pw + (long long)(j - 2) * nn, pw_bs, pw, pw_bs, n, batch, ep, st);
+        if (K > 0) {
+            rc = launch_slice_rows(pw + (long long)(j - 2) * nn, pw_bs, n, batch, K, slA, eA, st);
+            if (!rc) rc = launch_gemm_f64e(K, slA, K, eA, slB, K, eB, n, batch, batch, ep, d_err, st);
+        } else {
+            rc = launch_gemm_f64(pw + (long long)(j - 2) * nn, pw_bs, pw, pw_bs, n, batch, ep, st);
+        }
         if (rc) return rc;
     }
 
@@ -279,6 +329,9 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
     std::vector<double> hn((size_t)batch * q);
     MPPS_CUDA_TRY(cudaMemcpyAsync(hn.data(), norms, sizeof(double) * hn.size(),
                                   cudaMemcpyDeviceToHost, st));
+    if (expm)
+        MPPS_CUDA_TRY(cudaMemcpyAsync(sigma.data(), d_sigma, sizeof(int) * batch,
+                                      cudaMemcpyDeviceToHost, st));
     MPPS_CUDA_TRY(cudaStreamSynchronize(st));
 
     // ---- a4: plan per matrix; a batch runs each step in the most precise format any of
@@ -293,10 +346,13 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
         rp[b].sigma = sigma[b];
     }
     int fmt[MPPS_MAX_R + 1];
+    bool any_f64e = false;
     for (int i = 1; i <= r; ++i) {
-        int f = MPPS_FMT_FP8;
-        for (int b = 0; b < batch; ++b) f = std::min(f, rp[b].fmt[i]);
+        int f = rp[0].fmt[i];
+        for (int b = 1; b < batch; ++b)
+            if (prec_rank(rp[b].fmt[i]) > prec_rank(f)) f = rp[b].fmt[i];
         fmt[i] = (fold && i == r) ? MPPS_FMT_NONE : f;
+        if (MPPS_FMT_IS_F64E(fmt[i])) any_f64e = true;
     }
     bool used[MPPS_NUM_FORMATS] = {false, false, false, false, false};
     int max_es = 1;
@@ -369,17 +425,27 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
             }
     }
 
+    if (any_f64e) {   // Y^T slices for every emulated Horner step (first k planes used)
+        rc = slice_cols(pw + (long long)(s - 1) * nn, pw_bs, K, slY, eY);
+        if (rc) return rc;
+    }
+
     // ---- a5/a6: Horner in Y with the block sums fused into the product epilogues
     int sig_max = 0;
     for (int b = 0; b < batch; ++b) sig_max = std::max(sig_max, sigma[b]);
     double* Pbuf[2] = {Pb0, Pb1};
     double* dst0 = (expm && sig_max > 0) ? Pb0 : dOut;
     const double* Y = pw + (long long)(s - 1) * nn;
+    // Emulated squarings work on Q = P - I (Q <- Q Q + 2 Q, exact algebra): the slices of a
+    // matrix close to I would be aligned to its unit diagonal and lose the small entries'
+    // low bits; Q has no dominant identity part.  The last Horner step writes Q_0 directly.
+    const bool qform = expm && sig_max > 0 && K > 0;
 
     auto make_ep = [&](int i) {   // epilogue producing P_{i-1} = B_{i-1} + (...)
         Epilogue ep = epilogue_plain((i - 1 == 0) ? dst0 : Pbuf[(i - 1) & 1], nn);
         ep.nt = s - 1;
         for (int j = 0; j < s; ++j) ep.coef[j] = coeffs[(i - 1) * s + j];
+        if (i - 1 == 0 && qform) ep.coef[0] -= 1.0;
         ep.pw = pw;
         ep.pw_bstride = pw_bs;
         if (i - 1 >= 1 && is_low(fmt[i - 1])) {
@@ -424,6 +490,11 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
         Epilogue ep = make_ep(i);
         if (fmt[i] == MPPS_FMT_FP64) {
             rc = launch_gemm_f64(Pbuf[i & 1], nn, Y, pw_bs, n, batch, ep, st);
+        } else if (MPPS_FMT_IS_F64E(fmt[i])) {
+            const int k = MPPS_F64E_SLICES(fmt[i]);
+            rc = launch_slice_rows(Pbuf[i & 1], nn, n, batch, k, slA, eA, st);
+            if (!rc)
+                rc = launch_gemm_f64e(k, slA, k, eA, slY, K, eY, n, batch, batch, ep, d_err, st);
         } else {
             ep.alpha_b = d_alpha + (size_t)i * batch;
             rc = launch_gemm_tc(fmt[i], Pl_hi[i & 1], Pl_lo[i & 1], Ylo_hi[fmt[i]], Ylo_lo[fmt[i]],
@@ -450,15 +521,28 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
                                       cudaMemcpyHostToDevice, st));
         for (int k = 0; k < sig_max; ++k) {
             Epilogue ep = epilogue_plain(Pbuf[(k + 1) & 1], nn);
-            rc = launch_gemm_f64(Pbuf[k & 1], nn, Pbuf[k & 1], nn, n, counts[k], ep, st,
-                                 d_lists + (size_t)k * batch);
+            if (qform) {   // Q_{k+1} = Q_k Q_k + 2 Q_k
+                ep.add = Pbuf[k & 1];
+                ep.add_bstride = nn;
+                ep.add_coef = 2.0;
+            }
+            if (K > 0) {
+                rc = launch_slice_rows(Pbuf[k & 1], nn, n, batch, K, slA, eA, st);
+                if (!rc) rc = slice_cols(Pbuf[k & 1], nn, K, slB, eB);
+                if (!rc)
+                    rc = launch_gemm_f64e(K, slA, K, eA, slB, K, eB, n, counts[k], batch, ep, d_err,
+                                          st, d_lists + (size_t)k * batch);
+            } else {
+                rc = launch_gemm_f64(Pbuf[k & 1], nn, Pbuf[k & 1], nn, n, counts[k], ep, st,
+                                     d_lists + (size_t)k * batch);
+            }
             if (rc) return rc;
         }
-        rc = launch_select_copy(Pb0, Pb1, d_sigma, dOut, n, batch, st);
+        rc = launch_select_copy(Pb0, Pb1, d_sigma, dOut, n, batch, qform ? 1.0 : 0.0, st);
         if (rc) return rc;
     }
 
-    if (any_low) {
+    if (any_low || K > 0) {
         int h_err = 0;
         MPPS_CUDA_TRY(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
         MPPS_CUDA_TRY(cudaStreamSynchronize(st));
@@ -473,9 +557,12 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
             mpps_report& R = rp[b];
             for (int i = 1; i <= r; ++i) R.fmt[i] = fmt[i];
             for (int f = 0; f <= MPPS_NUM_FORMATS; ++f) R.gemms[f] = 0;
-            R.gemms[MPPS_FMT_FP64] += s - 1;
-            for (int i = 1; i <= r; ++i)
-                if (fmt[i] >= 0) R.gemms[fmt[i]] += 1;
+            R.gemms[MPPS_FMT_FP64] += s - 1;   // emulated working-precision products count as FP64
+            for (int i = 1; i <= r; ++i) {
+                if (fmt[i] == MPPS_FMT_NONE) continue;
+                const int slot = MPPS_FMT_IS_F64E(fmt[i]) ? MPPS_FMT_FP64 : fmt[i];
+                R.gemms[slot] += 1;
+            }
             R.gemms[MPPS_NUM_FORMATS] = sigma[b];
             R.cost_ratio = cost_ratio(R, pol.tol);
             rep[b] = R;
@@ -516,6 +603,7 @@ void mpps_policy_default(mpps_policy* p) {
     p->s = 0;
     p->formats = 0x1Fu;
     p->fp64_floor_steps = 2;
+    p->f64_slices = 0;
 }
 
 const char* mpps_last_error(void) { return g_err; }
@@ -610,7 +698,7 @@ mpps_status mpps_matmul(const double* A, const double* B, double* C, int n, int 
     clear_error();
     mpps_status rc = check_sizes(n, batch);
     if (rc) return rc;
-    if (format < MPPS_FMT_FP64 || format > MPPS_FMT_FP8) {
+    if (!(format >= MPPS_FMT_FP64 && format <= MPPS_FMT_FP8) && !MPPS_FMT_IS_F64E(format)) {
         set_error("mpps_matmul: invalid format %d", format);
         return MPPS_EINVAL;
     }
@@ -636,6 +724,38 @@ mpps_status mpps_matmul(const double* A, const double* B, double* C, int n, int 
     if (format == MPPS_FMT_FP64) {
         rc = launch_gemm_f64(a.dev, nn, b.dev, nn, n, batch, ep, st);
         if (rc) return rc;
+    } else if (MPPS_FMT_IS_F64E(format)) {
+        const int k = MPPS_F64E_SLICES(format);
+        Arena L;
+        __nv_bfloat16 *sa, *sb;
+        int *ea, *eb, *err;
+        double* bt;
+        auto lay = [&](Arena& z) {
+            sa = z.take<__nv_bfloat16>(f64e_plane_elems(n, batch, k));
+            sb = z.take<__nv_bfloat16>(f64e_plane_elems(n, batch, k));
+            ea = z.take<int>((size_t)batch * n);
+            eb = z.take<int>((size_t)batch * n);
+            bt = z.take<double>(elems);
+            err = z.take<int>(1);
+        };
+        lay(L);
+        DevBuf ws;
+        if ((rc = ws.alloc(L.off, st))) return rc;
+        L.base = (char*)ws.p;
+        L.off = 0;
+        lay(L);
+        MPPS_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+        if ((rc = launch_slice_rows(a.dev, nn, n, batch, k, sa, ea, st))) return rc;
+        if ((rc = launch_slice_cols(b.dev, nn, n, batch, k, sb, eb, (unsigned long long*)bt, st)))
+            return rc;
+        if ((rc = launch_gemm_f64e(k, sa, k, ea, sb, k, eb, n, batch, batch, ep, err, st))) return rc;
+        int h_err = 0;
+        MPPS_CUDA_TRY(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        MPPS_CUDA_TRY(cudaStreamSynchronize(st));
+        if (h_err) {
+            set_error("a bounded wait in the emulated FP64 product timed out");
+            return MPPS_ETIMEOUT;
+        }
     } else {
         const int lld = low_ld(n);
         const long long low_bs = (long long)n * lld;
@@ -790,9 +910,9 @@ mpps_status ps_eval_adjoint(const double* coeffs, int m, const double* A, const 
         MPPS_CUDA_TRY(cudaMemsetAsync(Ybar, 0, elems * sizeof(double), st));
         // Y^T and X_1^T (strided power table -> contiguous copies first)
         if ((rc = launch_scale_copy(Y, pw_bs, T, nn, n, batch, nullptr, st))) return rc;
-        if ((rc = launch_transpose(T, Yt, n, batch, st))) return rc;
+        if ((rc = launch_transpose(T, nn, Yt, n, batch, st))) return rc;
         if ((rc = launch_scale_copy(pw, pw_bs, T, nn, n, batch, nullptr, st))) return rc;
-        if ((rc = launch_transpose(T, X1t, n, batch, st))) return rc;
+        if ((rc = launch_transpose(T, nn, X1t, n, batch, st))) return rc;
         double* Pbar[2] = {Pbar0, Pbar1};
         if ((rc = launch_scale_copy(g.dev, nn, Pbar[0], nn, n, batch, nullptr, st))) return rc;
         int cur = 0;
@@ -811,7 +931,7 @@ mpps_status ps_eval_adjoint(const double* coeffs, int m, const double* A, const 
                 break;
             }
             // Ybar += P_i^T Pbar_{i-1}
-            if ((rc = launch_transpose(P_at(i), T, n, batch, st))) return rc;
+            if ((rc = launch_transpose(P_at(i), nn, T, n, batch, st))) return rc;
             {
                 Epilogue ep = epilogue_plain(Ybar, nn);
                 ep.add = Ybar; ep.add_bstride = nn; ep.add_coef = 1.0;
@@ -848,7 +968,7 @@ mpps_status ps_eval_adjoint(const double* coeffs, int m, const double* A, const 
             // Xbar_1 += X_{j-1}^T Xbar_j
             if ((rc = launch_scale_copy(pw + (long long)(j - 2) * nn, pw_bs, T, nn, n, batch, nullptr, st)))
                 return rc;
-            if ((rc = launch_transpose(T, Pbar0, n, batch, st))) return rc;
+            if ((rc = launch_transpose(T, nn, Pbar0, n, batch, st))) return rc;
             Epilogue e2 = epilogue_plain(xbar, pw_bs);
             e2.add = xbar; e2.add_bstride = pw_bs; e2.add_coef = 1.0;
             if ((rc = launch_gemm_f64(Pbar0, nn, xj, pw_bs, n, batch, e2, st))) return rc;

@@ -38,12 +38,13 @@ void clear_error();
 // RAII: when profiling is enabled, records CUDA events on `st` around the launches made
 // while the scope is alive, tagged with a kernel class (MPPS_PROF_*).
 struct ProfScope {
-    ProfScope(int cls, cudaStream_t st);
+    ProfScope(int cls, cudaStream_t st, double work = 0.0);
     ~ProfScope();
     int cls;
     cudaStream_t st;
     cudaEvent_t a, b;
     bool on;
+    double work;   // algorithmic flops of the launch (products), 0 for the rest
 };
 
 // ---- fused epilogue of every product ---------------------------------------------
@@ -149,6 +150,22 @@ mpps_status launch_gemm_tc(int fmt, const void* A_hi, const void* A_lo, const vo
                            const void* Bt_lo, long long a_bs, long long b_bs, int lld, int n,
                            int batch, const Epilogue& ep, int* d_err, cudaStream_t st);
 
+// FP64-accurate product from exact bf16 slices (gemm_f64e.cu).  Slice planes of A (rows)
+// and of B^T (rows of B^T = columns of B) come from launch_slice_rows; eA/eB are the
+// per-row exponents it returns.  Planes: [batch][k][n][low_ld(n)] bf16.
+size_t f64e_plane_elems(int n, int batch, int k);
+mpps_status launch_slice_rows(const double* M, long long bs, int n, int batch, int k, void* planes,
+                              int* exps, cudaStream_t st);
+// Column slices of M written as rows of the B^T planes; colmax: batch * n scratch words.
+mpps_status launch_slice_cols(const double* M, long long bs, int n, int batch, int k, void* planes,
+                              int* exps, unsigned long long* colmax, cudaStream_t st);
+// k slices are used; ksA / ksB planes are stored per matrix (>= k); nmat matrices are
+// stored, `batch` of them are processed (all, or those listed in bidx).
+mpps_status launch_gemm_f64e(int k, const void* slicesA, int ksA, const int* eA,
+                             const void* slicesBt, int ksB, const int* eB, int n, int batch,
+                             int nmat, const Epilogue& ep, int* d_err, cudaStream_t st,
+                             const int* bidx = nullptr);
+
 // Element size in bytes of a low-precision operand copy.
 inline int low_elem_bytes(int fmt) {
     switch (fmt) {
@@ -181,9 +198,11 @@ mpps_status launch_norm1(const double* M, long long bs, int n, int batch, double
 // X = 2^-sigma[b] A (exact power-of-two scaling; d_sigma null -> plain copy).
 mpps_status launch_scale_copy(const double* A, long long a_bs, double* X, long long x_bs, int n,
                               int batch, const int* d_sigma, cudaStream_t st);
-// out[b] = (sigma[b] odd ? q1 : q0)[b]  (all contiguous, stride n*n).
+// sigma[b] = max(0, ceil(log2 norms[b])) on the device.
+mpps_status launch_sigma(const double* norms, int batch, int* sigma, cudaStream_t st);
+// out[b] = (sigma[b] odd ? q1 : q0)[b] + diag I  (all contiguous, stride n*n).
 mpps_status launch_select_copy(const double* q0, const double* q1, const int* d_sigma, double* out,
-                               int n, int batch, cudaStream_t st);
+                               int n, int batch, double diag, cudaStream_t st);
 // Rounded copies (times scale[b], or 1 if scale is null) for the low-precision products:
 // convert keeps the layout, convert_t writes the transpose (row j = column j).
 mpps_status launch_convert(int fmt, const double* M, long long bs, int n, int batch, void* hi,
@@ -200,7 +219,8 @@ mpps_status launch_pow2_scales(const double* maxabs_a, const double* maxabs_b, i
 mpps_status launch_axpy_blocks(double* xbar, long long xbar_bs, int n, int batch, int t,
                                const double* c, const double* G, long long g_bs,
                                cudaStream_t st);
-// At = A^T per matrix.
-mpps_status launch_transpose(const double* A, double* At, int n, int batch, cudaStream_t st);
+// At = A^T per matrix (A with batch stride a_bs, At contiguous).
+mpps_status launch_transpose(const double* A, long long a_bs, double* At, int n, int batch,
+                             cudaStream_t st);
 
 }  // namespace mpps

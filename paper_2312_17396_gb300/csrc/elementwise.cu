@@ -93,14 +93,28 @@ __global__ void k_scale_copy(const double* __restrict__ A, long long a_bs, doubl
         X[b * x_bs + t] = ldexp(A[b * a_bs + t], e);
 }
 
+// sigma[b] = max(0, ceil(log2 norms[b])) (0 for a non-finite norm), exactly as the host rule.
+__global__ void k_sigma(const double* __restrict__ norms, int batch, int* __restrict__ sigma) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= batch) return;
+    const double a = norms[b];
+    int e = 0;
+    if (a > 1.0 && isfinite(a)) {
+        const double f = frexp(a, &e);     // a = f 2^e, f in [0.5, 1)
+        if (f == 0.5) e -= 1;              // a power of two: log2 a exactly
+    }
+    sigma[b] = e;
+}
+
 __global__ void k_select_copy(const double* __restrict__ q0, const double* __restrict__ q1,
-                              const int* __restrict__ sigma, double* __restrict__ out,
-                              long long nn) {
+                              const int* __restrict__ sigma, double* __restrict__ out, int n,
+                              double diag) {
     const int b = blockIdx.y;
+    const long long nn = (long long)n * n;
     const double* src = (sigma[b] & 1) ? q1 : q0;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
          t += (long long)gridDim.x * blockDim.x)
-        out[b * nn + t] = src[b * nn + t];
+        out[b * nn + t] = src[b * nn + t] + ((t / n == t % n) ? diag : 0.0);
 }
 
 __global__ void k_combine(int n, const double* __restrict__ extra, long long extra_bs,
@@ -164,14 +178,15 @@ __global__ void k_axpy_blocks(double* __restrict__ xbar, long long xbar_bs, int 
     }
 }
 
-__global__ void k_transpose(const double* __restrict__ A, double* __restrict__ At, int n) {
+__global__ void k_transpose(const double* __restrict__ A, long long a_bs, double* __restrict__ At,
+                            int n) {
     __shared__ double tile[32][33];
     const int b = blockIdx.z;
     const long long nn = (long long)n * n;
     const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
     for (int i = threadIdx.y; i < 32; i += blockDim.y) {
         const int row = r0 + i, col = c0 + threadIdx.x;
-        if (row < n && col < n) tile[i][threadIdx.x] = A[b * nn + (long long)row * n + col];
+        if (row < n && col < n) tile[i][threadIdx.x] = A[b * a_bs + (long long)row * n + col];
     }
     __syncthreads();
     for (int i = threadIdx.y; i < 32; i += blockDim.y) {
@@ -263,11 +278,18 @@ mpps_status launch_scale_copy(const double* A, long long a_bs, double* X, long l
     return MPPS_OK;
 }
 
+mpps_status launch_sigma(const double* norms, int batch, int* sigma, cudaStream_t st) {
+    ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
+    k_sigma<<<(batch + 127) / 128, 128, 0, st>>>(norms, batch, sigma);
+    MPPS_LAUNCH_CHECK();
+    return MPPS_OK;
+}
+
 mpps_status launch_select_copy(const double* q0, const double* q1, const int* d_sigma, double* out,
-                               int n, int batch, cudaStream_t st) {
+                               int n, int batch, double diag, cudaStream_t st) {
     ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
     const long long nn = (long long)n * n;
-    k_select_copy<<<dim3(grid1d(nn, 256), batch), 256, 0, st>>>(q0, q1, d_sigma, out, nn);
+    k_select_copy<<<dim3(grid1d(nn, 256), batch), 256, 0, st>>>(q0, q1, d_sigma, out, n, diag);
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }
@@ -329,10 +351,11 @@ mpps_status launch_axpy_blocks(double* xbar, long long xbar_bs, int n, int batch
     return MPPS_OK;
 }
 
-mpps_status launch_transpose(const double* A, double* At, int n, int batch, cudaStream_t st) {
+mpps_status launch_transpose(const double* A, long long a_bs, double* At, int n, int batch,
+                             cudaStream_t st) {
     ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
     dim3 g((n + 31) / 32, (n + 31) / 32, batch);
-    k_transpose<<<g, dim3(32, 8), 0, st>>>(A, At, n);
+    k_transpose<<<g, dim3(32, 8), 0, st>>>(A, a_bs, At, n);
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }

@@ -148,7 +148,7 @@ mpps_status launch_gemm_f64(const double* A, long long a_bs, const double* B, lo
                             int n, int batch, const Epilogue& ep, cudaStream_t st,
                             const int* bidx) {
     if (batch <= 0) return MPPS_OK;
-    ProfScope prof(MPPS_PROF_GEMM_F64, st);
+    ProfScope prof(MPPS_PROF_GEMM_F64, st, 2.0 * n * (double)n * n * batch);
     const long long sms = num_sms();
     const long long t64 = (long long)((n + 63) / 64) * ((n + 63) / 64) * batch;
     const long long t32 = (long long)((n + 31) / 32) * ((n + 31) / 32) * batch;

@@ -16,6 +16,7 @@
 // K-major with the 128-byte swizzle.  Every mbarrier wait is bounded (about 2 s of
 // %globaltimer); on expiry the kernel sets *err, skips further waits and exits normally.
 #include "common.cuh"
+#include "tcgen05.cuh"
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -26,81 +27,11 @@ namespace mpps {
 
 namespace {
 
+using namespace tc;
+
 constexpr int TM = 128, TN = 128;
 constexpr int SLAB = 128;                 // bytes of K per smem row
 constexpr int TILE_BYTES = TM * SLAB;     // 16 KB: one 128-row operand slab
-constexpr unsigned long long kWaitNs = 2000000000ull;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ unsigned long long globaltimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-// Bounded wait for phase `parity` of an mbarrier.  Returns false (and sets *err) when the
-// time limit passes or another thread already gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
-    const uint32_t addr = smem_u32(bar);
-    unsigned long long t0 = 0;
-    for (uint32_t it = 0;; ++it) {
-        uint32_t ok;
-        asm volatile(
-            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            "selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(addr), "r"(parity)
-            : "memory");
-        if (ok) return true;
-        if ((it & 63) == 0) {
-            if (*(volatile int*)err != 0) return false;
-            const unsigned long long now = globaltimer();
-            if (t0 == 0) t0 = now;
-            else if (now - t0 > kWaitNs) {
-                atomicExch(err, 1);
-                return false;
-            }
-        }
-    }
-}
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, int c0, int c1, int c2,
-                                            uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
-        "%3, %4}], [%5];" ::"r"(smem_u32(dst)),
-        "l"((uint64_t)tm), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
-        : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                     smem_u32(bar))
-                 : "memory");
-}
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;              // leading byte offset (unused for this layout)
-    d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset
-    d |= (uint64_t)1 << 46;              // descriptor version
-    d |= (uint64_t)2 << 61;              // 128-byte swizzle
-    return d;
-}
-
 template <int FMT>
 struct Tc;
 template <>
@@ -147,19 +78,6 @@ __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint3
             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
             "l"(a), "l"(b), "r"(id), "r"(acc));
     }
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-          "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
-          "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
-          "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 template <int FMT>
@@ -254,21 +172,27 @@ __global__ void __launch_bounds__(128, 1)
     mbar_wait(done, 0, err);
     tc_fence_after();
 
-    const int row = m0 + warp * 32 + lane;
+    // Epilogue: TMEM rows -> a 32 x 33 shared tile per warp (the ring is idle now), then
+    // each lane takes one column so that global reads of the power table and the stores are
+    // coalesced along rows.
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    float* stile = (float*)smem + warp * 32 * 33;
 #pragma unroll 1
     for (int c0 = 0; c0 < TN; c0 += 32) {
         uint32_t v[32];
         tmem_ld32(tmem + lane_base + (uint32_t)c0, v);
-        if (row < n) {
-#pragma unroll 4
-            for (int j = 0; j < 32; ++j) {
-                const int col = n0 + c0 + j;
-                if (col < n)
-                    epilogue_store(ep, b, row, col, n,
-                                   epilogue_value(ep, b, row, col, n, (double)__uint_as_float(v[j])));
-            }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) stile[lane * 33 + j] = __uint_as_float(v[j]);
+        __syncwarp();
+        const int col = n0 + c0 + lane;
+#pragma unroll 1
+        for (int rr = 0; rr < 32; ++rr) {
+            const int row = m0 + warp * 32 + rr;
+            if (row < n && col < n)
+                epilogue_store(ep, b, row, col, n,
+                               epilogue_value(ep, b, row, col, n, (double)stile[rr * 33 + lane]));
         }
+        __syncwarp();
     }
     tc_fence_before();
     __syncthreads();
@@ -336,7 +260,8 @@ mpps_status launch_fmt(const void* A_hi, const void* A_lo, const void* Bt_hi, co
         attr_set = true;
     }
     dim3 grid((n + TN - 1) / TN, (n + TM - 1) / TM, batch);
-    ProfScope prof(MPPS_PROF_GEMM_TC, st);
+    ProfScope prof(MPPS_PROF_GEMM_TC, st,
+                   2.0 * n * (double)n * n * batch * (FMT == MPPS_FMT_BF16X3 ? 3 : 1));
     k_gemm_tc<FMT><<<grid, 128, smem, st>>>(ta, tb, ta2, tb2, n, ep, d_err);
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;

@@ -11,6 +11,7 @@ namespace mpps {
 namespace {
 struct Rec {
     int cls;
+    double work;
     cudaEvent_t a, b;
 };
 std::mutex g_mu;
@@ -33,7 +34,8 @@ cudaEvent_t take_event() {
 }
 }  // namespace
 
-ProfScope::ProfScope(int c, cudaStream_t s) : cls(c), st(s), a(nullptr), b(nullptr), on(false) {
+ProfScope::ProfScope(int c, cudaStream_t s, double w)
+    : cls(c), st(s), a(nullptr), b(nullptr), on(false), work(w) {
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_on) return;
     a = take_event();
@@ -45,7 +47,7 @@ ProfScope::ProfScope(int c, cudaStream_t s) : cls(c), st(s), a(nullptr), b(nullp
 ProfScope::~ProfScope() {
     if (!on) return;
     std::lock_guard<std::mutex> lk(g_mu);
-    if (cudaEventRecord(b, st) == cudaSuccess) g_recs.push_back({cls, a, b});
+    if (cudaEventRecord(b, st) == cudaSuccess) g_recs.push_back({cls, work, a, b});
 }
 
 }  // namespace mpps
@@ -68,7 +70,8 @@ void mpps_profile_reset(void) {
     g_recs.clear();
 }
 
-mpps_status mpps_profile_read(int kernel_class, long long* launches, double* total_ms) {
+mpps_status mpps_profile_read(int kernel_class, long long* launches, double* total_ms,
+                              double* total_work) {
     clear_error();
     if (!launches || !total_ms || kernel_class < 0 || kernel_class >= MPPS_PROF_NUM_CLASSES) {
         set_error("mpps_profile_read: invalid argument");
@@ -76,7 +79,7 @@ mpps_status mpps_profile_read(int kernel_class, long long* launches, double* tot
     }
     std::lock_guard<std::mutex> lk(g_mu);
     long long cnt = 0;
-    double tot = 0.0;
+    double tot = 0.0, work = 0.0;
     for (auto& r : g_recs) {
         if (r.cls != kernel_class) continue;
         if (cudaEventSynchronize(r.b) != cudaSuccess) {
@@ -86,10 +89,12 @@ mpps_status mpps_profile_read(int kernel_class, long long* launches, double* tot
         float ms = 0.f;
         cudaEventElapsedTime(&ms, r.a, r.b);
         tot += ms;
+        work += r.work;
         ++cnt;
     }
     *launches = cnt;
     *total_ms = tot;
+    if (total_work) *total_work = work;
     return MPPS_OK;
 }
 

@@ -74,9 +74,11 @@ def test_planner_matches_oracle_rule(mpps, mode):
         m, n, norms, y = _rand_case(rng)
         mask = int(rng.choice(masks))
         tol = float(rng.choice([2.0 ** -53, 1e-15, 1e-10]))
-        ref = oracle.plan(m, n, norms, y, mode=mode, tol=tol, formats=mask, floor_steps=2)
+        k = int(rng.choice([0, 0, 7, 9, 10]))
+        ref = oracle.plan(m, n, norms, y, mode=mode, tol=tol, formats=mask, floor_steps=2,
+                          f64_slices=k)
         got = mpps.plan(m, n, norms, y, mpps.Policy(mode=mode, tol=tol, formats=mask,
-                                                    fp64_floor_steps=2))
+                                                    fp64_floor_steps=2, f64_slices=k))
         assert (got["s"], got["r"], got["nu"], got["fold"]) == \
             (ref["s"], ref["r"], ref["nu"], ref["fold"])
         names = [None] + [mpps.FORMAT_NAMES[f] for f in ref["fmt"][1:]]
@@ -93,3 +95,17 @@ def test_planner_cost_ratio_reproduces_eq_3_8(mpps):
     assert abs(p["cost_ratio"] - expect) < 1e-12
     f = mpps.plan(16, 64, [1.0, 1e-3, 1e-9, 1e-15, 1e-21], 0.5, mpps.FIXED)
     assert abs(f["cost_ratio"] - (3 * D + 3 * D) / (7 * D)) < 1e-12
+
+
+def test_planner_emulated_ladder(mpps):
+    """With emulation (K = 9 slices) the rungs F64E(4..8) sit between BF16X3 and the working
+    precision F64E(9): u_i = 1e-9 needs 2^(3-6k) <= 1e-9, i.e. k = 6 (2^-33 = 1.2e-10);
+    u_i = 1e-13 needs k = 8 (2^-45 = 2.8e-14)."""
+    tol = 2.0 ** -53
+    norms = [1.0, tol / 1e-9, tol / 1e-13, 1e-40]          # y = 1 -> u_1 = 1e-9, u_2 = 1e-13
+    p = mpps.plan(9, 64, norms, 1.0, mpps.Policy(mode=mpps.MIXED_PAPER, f64_slices=9))
+    assert p["fmt"][1:] == ["f64e6", "f64e8", "none"]
+    f = mpps.plan(9, 64, norms, 1.0, mpps.Policy(mode=mpps.FIXED_FP64, f64_slices=9))
+    assert f["fmt"][1:] == ["f64e9", "f64e9", "none"]
+    with pytest.raises(mpps.MppsError):
+        mpps.plan(9, 64, norms, 1.0, mpps.Policy(f64_slices=11))

@@ -262,7 +262,94 @@ def test_expm_n1024_sampled_columns(mpps, norm):
         V[j, t] = 1.0
     wh, wl = oracle.ps_apply_dd(oracle.taylor_exp_rational(30), X, V, reps=2 ** sg)
     ref_norm = np.abs(wh).sum(axis=0)
-    for pol in (mpps.FIXED, mpps.NS, mpps.PAPER):
+    for pol in (mpps.FIXED, mpps.NS, mpps.PAPER, mpps.FIXED_E, mpps.NS_E):
         E = host(mpps.expm(dev(A), m=30, policy=pol))
         err = np.abs(E[:, cols] - wh - wl).sum(axis=0) / ref_norm
         assert np.all(err <= 50 * n * U * max(1, 2 ** sg)), (pol.mode, err)
+
+
+# ------------------------------------------------------------------------------------
+# FP64 products emulated by exact bf16 slices on the tensor cores
+# ------------------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [8, 64, 130, 257])
+def test_matmul_f64e_exact_on_small_integers(mpps, n):
+    """Integers below 64 in magnitude are one exact slice; their products sum exactly."""
+    rng = np.random.default_rng(300 + n)
+    A = rng.integers(-63, 64, size=(2, n, n)).astype(np.float64)
+    B = rng.integers(-63, 64, size=(2, n, n)).astype(np.float64)
+    for k in (1, 9):
+        C = host(mpps.matmul(dev(A), dev(B), f"f64e{k}"))
+        assert np.array_equal(C, A @ B), k
+
+
+@pytest.mark.parametrize("n", [1, 3, 17, 64, 130, 257, 1100])
+def test_matmul_f64e_vs_oracle(mpps, n):
+    """9 slices: FP64-level error.  n = 1100 crosses the 1024-long exact-accumulation chunk."""
+    rng = np.random.default_rng(400 + n)
+    A = rng.standard_normal((1, n, n)); B = rng.standard_normal((1, n, n))
+    A[0, 0, :] *= 1e-9                      # a row far below the others: row scaling matters
+    C = host(mpps.matmul(dev(A), dev(B), "f64e9"))[0]
+    ch, cl = oracle.matmul_dd(A[0], None, B[0], None)
+    err = np.abs(C - ch - cl)
+    absprod = np.abs(A[0]) @ np.abs(B[0])
+    # slices keep 54 bits below each row / column maximum; bound by those maxima
+    rmax = np.abs(A[0]).max(axis=1)[:, None]; cmax = np.abs(B[0]).max(axis=0)[None, :]
+    bound = 8 * U * (rmax * np.abs(B[0]).sum(axis=0)[None, :] + cmax * np.abs(A[0]).sum(axis=1)[:, None])
+    assert np.all(err <= bound + 1e-300)
+    assert np.linalg.norm(err) <= 4 * n * U * np.linalg.norm(absprod)
+
+
+def test_matmul_f64e_error_falls_with_slices(mpps):
+    n = 200
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((1, n, n)); B = rng.standard_normal((1, n, n))
+    exact = A[0] @ B[0]
+    ch, cl = oracle.matmul_dd(A[0], None, B[0], None)
+    scale = np.linalg.norm(np.abs(A[0]) @ np.abs(B[0]))
+    prev = None
+    for k in range(1, 10):
+        C = host(mpps.matmul(dev(A), dev(B), f"f64e{k}"))[0]
+        err = np.linalg.norm(C - ch - cl) / scale
+        assert err <= 2.0 ** (3 - 6 * k), (k, err)
+        if prev is not None and k < 9:
+            assert err < prev
+        prev = err
+
+
+@pytest.mark.parametrize("n", [17, 130, 257])
+def test_ps_eval_emulated_vs_oracle(mpps, n):
+    m = 30
+    A = inputs.gaussian_matrix(n, seed=5000 + n, norm1=0.8)
+    coef = mpps.taylor_exp_coeffs(m)
+    ph, pl, _ = oracle.ps_dd(oracle.taylor_exp_rational(m), A)
+    Pf = host(mpps.ps_eval(coef, dev(A), policy=mpps.FIXED))
+    ef = oracle.rel_err_1norm(Pf, ph, pl)
+    for pol in (mpps.FIXED_E, mpps.PAPER_E, mpps.NS_E):
+        P, rep = mpps.ps_eval(coef, dev(A), policy=pol, report=True)
+        e = oracle.rel_err_1norm(host(P), ph, pl)
+        assert e <= 50 * n * U, (pol.mode, e, rep[0]["fmt"])
+        assert e <= 2 * ef + n * U, (pol.mode, e, ef, rep[0]["fmt"])
+
+
+@pytest.mark.parametrize("norm", [0.5, 4.0, 32.0])
+def test_expm_emulated_vs_oracle(mpps, norm):
+    n = 130
+    A = inputs.gaussian_matrix(n, seed=6000, norm1=norm)
+    sg = oracle.sigma_for(A)
+    eh, el = oracle.expm_ss_dd(A, 30, sg)
+    ef = oracle.rel_err_1norm(host(mpps.expm(dev(A), policy=mpps.FIXED)), eh, el)
+    for pol in (mpps.FIXED_E, mpps.NS_E, mpps.PAPER_E):
+        E = host(mpps.expm(dev(A), policy=pol))
+        e = oracle.rel_err_1norm(E, eh, el)
+        assert e <= 50 * n * U * max(1, 2 ** sg) and e <= 2 * ef + n * U * 2 ** sg, (pol.mode, e, ef)
+
+
+def test_expm_emulated_batch_mixed_sigma(mpps):
+    n = 40
+    A = inputs.gaussian_batch(3, n, seed=13, norm1=[0.3, 5.0, 40.0])
+    E, reps = mpps.expm(dev(A), policy=mpps.NS_E, report=True)
+    E = host(E)
+    for b in range(3):
+        sg = oracle.sigma_for(A[b])
+        eh, el = oracle.expm_ss_dd(A[b], 30, sg)
+        assert oracle.rel_err_1norm(E[b], eh, el) <= 50 * n * U * max(1, 2 ** sg)
