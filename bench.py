@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--policy", default="ns_e",
                     choices=["ns_e", "paper_e", "fixed_e", "ns", "paper", "fixed"],
                     help="headline policy (the others are timed beside it)")
+    ap.add_argument("--policies", default="fixed,ns,fixed_e,ns_e",
+                    help="comma list of policies timed beside the headline (fixed is always kept)")
     ap.add_argument("--no-check", action="store_true", help="skip the oracle error check")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel", default=None,
@@ -251,7 +253,8 @@ def main():
     pols = {"ns_e": mpps.NS_E, "paper_e": mpps.PAPER_E, "fixed_e": mpps.FIXED_E,
             "ns": mpps.NS, "paper": mpps.PAPER, "fixed": mpps.FIXED}
     head = args.policy
-    order = [head] + [p for p in ("fixed", "ns", "fixed_e", "ns_e") if p != head]
+    extra = [p for p in args.policies.split(",") if p in pols]
+    order = [head] + [p for p in dict.fromkeys(["fixed"] + extra) if p != head]
     mats = make_inputs(n)
     dA = [torch.from_numpy(A).to(dev) for A in mats]
     outs = {p: [torch.empty_like(a) for a in dA] for p in order}

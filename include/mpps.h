@@ -215,6 +215,12 @@ void mpps_profile_reset(void);
 mpps_status mpps_profile_read(int kernel_class, long long* launches, double* total_ms,
                               double* total_work);
 
+/* Self-test of the failure path of the library's bounded waits (no counterpart in the
+ * paper): launches one CTA that waits on an mbarrier nothing arrives on; the wait gives up
+ * after limit_us microseconds, sets an error word and the kernel returns normally, so the
+ * call returns MPPS_ETIMEOUT and the CUDA context stays usable.  limit_us in 1..2000000. */
+mpps_status mpps_selftest_bounded_wait(int limit_us, void* stream);
+
 /* Description of the last failure on this thread ("" if none). */
 const char* mpps_last_error(void);
 

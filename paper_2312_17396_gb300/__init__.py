@@ -73,7 +73,8 @@ class _Report(ctypes.Structure):
 
 EXPORTS = ("mpps_policy_default", "mpps_plan", "ps_eval", "expm_taylor_ss", "ps_eval_adjoint",
            "mpps_matmul", "mpps_last_error", "mpps_version", "mpps_profile_enable",
-           "mpps_profile_reset", "mpps_profile_read", "mpps_matmul_noalloc")
+           "mpps_profile_reset", "mpps_profile_read", "mpps_matmul_noalloc",
+           "mpps_selftest_bounded_wait")
 PROF_GEMM_F64, PROF_GEMM_TC, PROF_ELEMENTWISE, PROF_GEMM_F64E = 0, 1, 2, 3
 
 
@@ -98,6 +99,8 @@ def lib():
         L.mpps_matmul.argtypes = [vp, vp, vp, ip, ip, ip, vp]
         L.mpps_matmul_noalloc.argtypes = [vp, vp, vp, ip, ip, ip, vp]
         L.mpps_matmul_noalloc.restype = ctypes.c_int
+        L.mpps_selftest_bounded_wait.argtypes = [ctypes.c_int, vp]
+        L.mpps_selftest_bounded_wait.restype = ctypes.c_int
         for f in ("mpps_plan", "ps_eval", "expm_taylor_ss", "ps_eval_adjoint", "mpps_matmul"):
             getattr(L, f).restype = ctypes.c_int
         L.mpps_profile_enable.argtypes = [ctypes.c_int]

@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 namespace mpps {
@@ -219,11 +220,78 @@ static int exp_above(double x) {   // e with x < 2^e (x > 0), 0 otherwise
     return e;
 }
 
+// ---- sticky per-device error word of the bounded waits --------------------------------
+// The tensor-core kernels set *err when a bounded wait gives up.  Instead of synchronising
+// every call to read it, each call enqueues a copy of the word into pinned host memory
+// behind an event; the word is reported (and cleared) by the first later call on the device
+// that finds the event complete, or at once by calls that synchronise anyway.
+struct DevErr {
+    int* d = nullptr;
+    int* h = nullptr;
+    cudaEvent_t ev = nullptr;
+    bool pending = false;
+};
+static std::mutex g_errmu;
+static DevErr g_deverr[64];
+
+static mpps_status dev_err_get(DevErr** out) {
+    int dev = 0;
+    MPPS_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) {
+        set_error("device index %d out of range", dev);
+        return MPPS_ENOTSUP;
+    }
+    std::lock_guard<std::mutex> lk(g_errmu);
+    DevErr& e = g_deverr[dev];
+    if (!e.d) {
+        MPPS_CUDA_TRY(cudaMalloc(&e.d, sizeof(int)));
+        MPPS_CUDA_TRY(cudaMemset(e.d, 0, sizeof(int)));
+        MPPS_CUDA_TRY(cudaHostAlloc(&e.h, sizeof(int), cudaHostAllocDefault));
+        *e.h = 0;
+        MPPS_CUDA_TRY(cudaEventCreateWithFlags(&e.ev, cudaEventDisableTiming));
+    }
+    *out = &e;
+    return MPPS_OK;
+}
+
+// Report a failure recorded by an earlier call (if its copy has landed).  `wait` forces the
+// check (used right after a stream synchronisation).
+static mpps_status dev_err_check(DevErr* e, bool wait) {
+    std::lock_guard<std::mutex> lk(g_errmu);
+    if (!e->pending) return MPPS_OK;
+    if (!wait) {
+        cudaError_t q = cudaEventQuery(e->ev);
+        if (q == cudaErrorNotReady) return MPPS_OK;
+        if (q != cudaSuccess) {
+            set_error("cudaEventQuery failed: %s", cudaGetErrorString(q));
+            return MPPS_ECUDA;
+        }
+    } else {
+        MPPS_CUDA_TRY(cudaEventSynchronize(e->ev));
+    }
+    e->pending = false;
+    if (*e->h) {
+        *e->h = 0;
+        MPPS_CUDA_TRY(cudaMemset(e->d, 0, sizeof(int)));
+        set_error("a bounded wait in a tensor-core product timed out (device error word set)");
+        return MPPS_ETIMEOUT;
+    }
+    return MPPS_OK;
+}
+
+static mpps_status dev_err_enqueue(DevErr* e, cudaStream_t st) {
+    std::lock_guard<std::mutex> lk(g_errmu);
+    MPPS_CUDA_TRY(cudaMemcpyAsync(e->h, e->d, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MPPS_CUDA_TRY(cudaEventRecord(e->ev, st));
+    e->pending = true;
+    return MPPS_OK;
+}
+
 // ---- the PS evaluation --------------------------------------------------------------
 // Evaluates p(X) for a device batch; for expm, X = 2^-sigma A and sigma squarings follow.
 static mpps_status eval_device(const double* coeffs, int m, const double* dA, int n, int batch,
                                const Pol& pol, double* dOut, mpps_report* rep, cudaStream_t st,
-                               bool expm) {
+                               bool expm, bool sync_at_end) {
     const long long nn = (long long)n * n;
     // ---- m == 0: p = b_0 I
     if (m == 0) {
@@ -262,12 +330,12 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
         pw = a.take<double>((size_t)batch * pw_bs);
         Pb0 = a.take<double>((size_t)batch * nn);
         Pb1 = a.take<double>((size_t)batch * nn);
-        partial = a.take<double>(std::max(block_norms_partial_elems(n, batch, m, s),
+        partial = a.take<double>(std::max(std::max(block_norms_partial_elems(n, batch, m, s),
+                                                   block_norms_f32_partial_elems(n, batch, m, s)),
                                           norm1_partial_elems(n, batch)));
         norms = a.take<double>((size_t)batch * q);
         d_anorm = a.take<double>(batch);
         d_sigma = a.take<int>(batch);
-        d_err = a.take<int>(1);
         d_bidx = a.take<int>((size_t)batch * 64);
         if (K > 0) {
             slA = a.take<__nv_bfloat16>(f64e_plane_elems(n, batch, K));
@@ -287,7 +355,10 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
     L.off = 0;
     layout1(L);
     MPPS_CUDA_TRY(cudaMemcpyAsync(d_coef, coeffs, sizeof(double) * (m + 1), cudaMemcpyHostToDevice, st));
-    MPPS_CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), st));
+    DevErr* derr = nullptr;
+    if ((rc = dev_err_get(&derr))) return rc;
+    if ((rc = dev_err_check(derr, false))) return rc;
+    d_err = derr->d;
 
     // emulated product helper: B^T rows (= columns of B) sliced straight from B
     auto slice_cols = [&](const double* Bm, long long bs, int k, __nv_bfloat16* planes,
@@ -324,7 +395,12 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
     }
 
     // ---- a3: ||B_i||_1, ||Y||_1, ||X||_1
-    rc = launch_block_norms(pw, pw_bs, n, batch, s, m, d_coef, partial, norms, st);
+    // ||X||_1 <= 1 after the scaling of exp: FP32 sums suffice for the precision rule
+    // (the paper notes the norms are only needed to the right order of magnitude)
+    if (expm)
+        rc = launch_block_norms_f32(pw, pw_bs, n, batch, s, m, coeffs, partial, norms, st);
+    else
+        rc = launch_block_norms(pw, pw_bs, n, batch, s, m, d_coef, partial, norms, st);
     if (rc) return rc;
     std::vector<double> hn((size_t)batch * q);
     MPPS_CUDA_TRY(cudaMemcpyAsync(hn.data(), norms, sizeof(double) * hn.size(),
@@ -543,13 +619,8 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
     }
 
     if (any_low || K > 0) {
-        int h_err = 0;
-        MPPS_CUDA_TRY(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
-        MPPS_CUDA_TRY(cudaStreamSynchronize(st));
-        if (h_err) {
-            set_error("a bounded wait in the tensor-core product timed out");
-            return MPPS_ETIMEOUT;
-        }
+        if ((rc = dev_err_enqueue(derr, st))) return rc;
+        if (sync_at_end && (rc = dev_err_check(derr, true))) return rc;
     }
 
     if (rep) {
@@ -660,7 +731,8 @@ static mpps_status run_eval(const double* coeffs, int m, const double* A, int n,
         dOut = (double*)ob.p;
     }
     Pol P = resolve(policy);
-    rc = eval_device(coeffs, m, a.dev, n, batch, P, dOut, rep, st, expm);
+    const bool host_io = !out_dev || !is_device_ptr(A);
+    rc = eval_device(coeffs, m, a.dev, n, batch, P, dOut, rep, st, expm, host_io);
     if (rc) return rc;
     if (!out_dev) {
         MPPS_CUDA_TRY(cudaMemcpyAsync(out, dOut, elems * sizeof(double), cudaMemcpyDeviceToHost, st));

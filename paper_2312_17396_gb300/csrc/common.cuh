@@ -191,6 +191,13 @@ size_t block_norms_partial_elems(int n, int batch, int m, int s);
 mpps_status launch_block_norms(const double* pw, long long pw_bs, int n, int batch, int s,
                                int m, const double* d_coeffs, double* partial, double* norms,
                                cudaStream_t st);
+// The same norms in FP32 arithmetic, valid when ||X||_1 <= 1 (the scaled argument of exp):
+// the block sums only steer the precision rule and the operand scales, where a relative
+// error of 2^-20 is immaterial.  coeffs is the host array b_0..b_m.
+size_t block_norms_f32_partial_elems(int n, int batch, int m, int s);
+mpps_status launch_block_norms_f32(const double* pw, long long pw_bs, int n, int batch, int s,
+                                   int m, const double* coeffs, double* partial, double* norms,
+                                   cudaStream_t st);
 // ||M||_1 per matrix (partial: norm1_partial_elems doubles).
 size_t norm1_partial_elems(int n, int batch);
 mpps_status launch_norm1(const double* M, long long bs, int n, int batch, double* partial,

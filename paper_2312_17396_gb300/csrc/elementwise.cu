@@ -72,16 +72,90 @@ __global__ void k_norms_finalize(const double* __restrict__ partial, int n, int 
 }
 
 // Column sums of |M| accumulated row by row in order 0..n-1 (one thread per column), so
-// that ||M||_1 is the same double as a plain sequential loop computes.
+// that ||M||_1 is the same double as a plain sequential loop computes.  32 rows are
+// loaded ahead (independent loads in flight), then added in order; rows past n add 0.
 __global__ void k_colsum_seq(const double* __restrict__ M, long long bs, int n,
                              double* __restrict__ colsum) {
     const int col = blockIdx.x * kColsPerBlock + threadIdx.x;
     const int b = blockIdx.y;
     if (col >= n) return;
-    const double* base = M + (long long)b * bs;
+    const double* base = M + (long long)b * bs + col;
     double acc = 0.0;
-    for (int row = 0; row < n; ++row) acc += fabs(__ldg(base + (long long)row * n + col));
+    for (int r0 = 0; r0 < n; r0 += 32) {
+        double v[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k)
+            v[k] = (r0 + k < n) ? __ldg(base + (long long)(r0 + k) * n) : 0.0;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) acc += fabs(v[k]);
+    }
     colsum[(long long)b * n + col] = acc;
+}
+
+// FP64 -> FP32 by bit manipulation (truncating the significand; underflow to 0, overflow to
+// inf): keeps the conversion off the FP64 pipe.  Used where only magnitudes matter.
+__device__ __forceinline__ float narrow(double x) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const unsigned sgn = (unsigned)(u >> 63) << 31;
+    const int e = (int)((u >> 52) & 0x7ff) - 1023 + 127;
+    if (e <= 0) return __uint_as_float(sgn);
+    if (e >= 255) return __uint_as_float(sgn | 0x7f800000u);
+    return __uint_as_float(sgn | ((unsigned)e << 23) | (unsigned)((u >> 29) & 0x7fffffu));
+}
+
+struct NormCoefs {
+    float c[(MPPS_MAX_R + 1) * MPPS_MAX_S];   // b_{is+j} / scale_i
+};
+
+// Block norms in FP32 for ||X||_1 <= 1 (every power entry is at most 1 in magnitude):
+// coefficients come normalised per block (|c| <= 1), so nothing overflows; entries that
+// underflow are negligible against the block's norm.  Partial sums in 16-row chunks.
+__global__ void k_block_norms_partial_f32(const double* __restrict__ pw, long long pw_bs, int n,
+                                          int s, int m, NormCoefs cf,
+                                          double* __restrict__ partial) {
+    const int col = blockIdx.x * kColsPerBlock + threadIdx.x;
+    const int chunk = blockIdx.y, chunks = gridDim.y, b = blockIdx.z;
+    const int r = m / s, q = r + 3;
+    if (col >= n) return;
+    float acc[MPPS_MAX_R + 3];
+    float x[MPPS_MAX_S + 1];
+    for (int t = 0; t < q; ++t) acc[t] = 0.f;
+    const long long nn = (long long)n * n;
+    const double* base = pw + (long long)b * pw_bs;
+    const int r0 = chunk * 16, r1 = min(n, r0 + 16);
+    for (int row = r0; row < r1; ++row) {
+        x[0] = (row == col) ? 1.f : 0.f;
+        for (int j = 1; j <= s; ++j)
+            x[j] = narrow(__ldg(base + (long long)(j - 1) * nn + (long long)row * n + col));
+        for (int i = 0; i <= r; ++i) {
+            const int top = (i < r) ? s - 1 : m - s * r;
+            float v = 0.f;
+            for (int j = 0; j <= top; ++j) v = fmaf(cf.c[s * i + j], x[j], v);
+            acc[i] += fabsf(v);
+        }
+        acc[r + 1] += fabsf(x[s]);
+        acc[r + 2] += fabsf(x[1]);
+    }
+    for (int t = 0; t < q; ++t)
+        partial[(((long long)b * chunks + chunk) * q + t) * n + col] = (double)acc[t];
+}
+
+struct BlockScales {
+    double c[MPPS_MAX_R + 3];
+};
+
+__global__ void k_norms_finalize_scaled(const double* __restrict__ partial, int n, int chunks,
+                                        int q, BlockScales sc, double* __restrict__ norms) {
+    const int t = blockIdx.x, b = blockIdx.y;
+    double best = 0.0;
+    for (int col = threadIdx.x; col < n; col += blockDim.x) {
+        double sum = 0.0;
+        for (int c = 0; c < chunks; ++c)
+            sum += partial[(((long long)b * chunks + c) * q + t) * n + col];
+        best = fmax(best, sum);
+    }
+    best = block_max(best);
+    if (threadIdx.x == 0) norms[(long long)b * q + t] = best * sc.c[t];
 }
 
 __global__ void k_scale_copy(const double* __restrict__ A, long long a_bs, double* __restrict__ X,
@@ -243,6 +317,36 @@ size_t block_norms_partial_elems(int n, int batch, int m, int s) {
 }
 
 size_t norm1_partial_elems(int n, int batch) { return (size_t)batch * n; }
+
+size_t block_norms_f32_partial_elems(int n, int batch, int m, int s) {
+    return (size_t)batch * ((n + 15) / 16) * block_norms_count(m, s) * n;
+}
+
+mpps_status launch_block_norms_f32(const double* pw, long long pw_bs, int n, int batch, int s,
+                                   int m, const double* coeffs, double* partial, double* norms,
+                                   cudaStream_t st) {
+    ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
+    const int r = m / s, q = block_norms_count(m, s);
+    NormCoefs cf;
+    BlockScales sc;
+    for (int i = 0; i <= r; ++i) {
+        const int top = (i < r) ? s - 1 : m - s * r;
+        double mx = 0.0;
+        for (int j = 0; j <= top; ++j) mx = fmax(mx, fabs(coeffs[s * i + j]));
+        sc.c[i] = mx > 0.0 ? mx : 1.0;
+        for (int j = 0; j < s; ++j)
+            cf.c[s * i + j] = (j <= top) ? (float)(coeffs[s * i + j] / sc.c[i]) : 0.f;
+    }
+    sc.c[r + 1] = 1.0;
+    sc.c[r + 2] = 1.0;
+    const int chunks = (n + 15) / 16;
+    dim3 g((n + kColsPerBlock - 1) / kColsPerBlock, chunks, batch);
+    k_block_norms_partial_f32<<<g, kColsPerBlock, 0, st>>>(pw, pw_bs, n, s, m, cf, partial);
+    MPPS_LAUNCH_CHECK();
+    k_norms_finalize_scaled<<<dim3(q, batch), 256, 0, st>>>(partial, n, chunks, q, sc, norms);
+    MPPS_LAUNCH_CHECK();
+    return MPPS_OK;
+}
 
 mpps_status launch_block_norms(const double* pw, long long pw_bs, int n, int batch, int s, int m,
                                const double* d_coeffs, double* partial, double* norms,

@@ -29,7 +29,8 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
 }
 // Bounded wait for phase `parity` of an mbarrier.  Returns false (and sets *err) when the
 // time limit passes or another thread already gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err,
+                                          unsigned long long limit_ns = kWaitNs) {
     const uint32_t addr = smem_u32(bar);
     unsigned long long t0 = 0;
     for (uint32_t it = 0;; ++it) {
@@ -45,7 +46,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* e
             if (*(volatile int*)err != 0) return false;
             const unsigned long long now = globaltimer();
             if (t0 == 0) t0 = now;
-            else if (now - t0 > kWaitNs) {
+            else if (now - t0 > limit_ns) {
                 atomicExch(err, 1);
                 return false;
             }

@@ -353,3 +353,18 @@ def test_expm_emulated_batch_mixed_sigma(mpps):
         sg = oracle.sigma_for(A[b])
         eh, el = oracle.expm_ss_dd(A[b], 30, sg)
         assert oracle.rel_err_1norm(E[b], eh, el) <= 50 * n * U * max(1, 2 ** sg)
+
+
+# ------------------------------------------------------------------------------------
+# failure path of the bounded waits (no fault: a wait that nothing completes gives up)
+# ------------------------------------------------------------------------------------
+def test_bounded_wait_reports_timeout_and_context_survives(mpps):
+    st = torch.cuda.current_stream().cuda_stream
+    rc = mpps.lib().mpps_selftest_bounded_wait(20000, st)      # 20 ms limit
+    assert rc == 4                                            # MPPS_ETIMEOUT
+    assert b"bounded wait" in mpps.lib().mpps_last_error()
+    # the context is still usable: a normal evaluation succeeds afterwards
+    A = inputs.gaussian_matrix(32, seed=77, norm1=1.0)
+    P = host(mpps.ps_eval(mpps.taylor_exp_coeffs(12), dev(A), policy=mpps.NS_E))
+    ph, pl, _ = oracle.ps_dd(oracle.taylor_exp_rational(12), A)
+    assert oracle.rel_err_1norm(P, ph, pl) <= 50 * 32 * U
