@@ -148,14 +148,43 @@ mpps_status expm_taylor_ss(const double* A, int n, int batch, int m, const mpps_
                            double* out, mpps_report* rep, void* stream);
 
 /*
+ * One item of an uneven batch: its own order n and Taylor degree m (0 -> 30).
+ * A and out are device pointers to n x n row-major FP64 matrices (out may not alias A).
+ */
+typedef struct {
+    const double* A;
+    double* out;
+    int n;
+    int m;
+} mpps_group_item;
+
+/*
+ * exp(A) for `count` matrices of different orders and degrees (scaling and squaring as in
+ * expm_taylor_ss, one sigma per matrix).  Matrices are bucketed by (n rounded up to a
+ * multiple of 32, m); each bucket is zero-padded block-diagonally -- exact, since
+ * p(diag(A, 0)) = diag(p(A), b_0 I) and ||diag(A, 0)||_1 = ||A||_1 -- and evaluated as one
+ * batch, with per-matrix plans and operand scales; the n x n results are scattered back.
+ *   items : host array of `count` descriptors (device matrix pointers).
+ *   rep   : NULL, or `count` reports (host), in item order (norms include the padding's
+ *           b_{is} I part of each block).
+ * Synchronises `stream` once per bucket.
+ */
+mpps_status expm_taylor_ss_grouped(const mpps_group_item* items, int count,
+                                   const mpps_policy* policy, mpps_report* rep, void* stream);
+
+/*
  * Gradient of f(A) = <G, p_m(A)> = sum_ij G_ij p_m(A)_ij with respect to A, i.e. the
  * Frechet derivative L_p(A^T, G) (the paper states no adjoint; this is the derivative of
- * the PS evaluation, computed by reverse-mode through its steps, in FP64).
+ * the PS evaluation, computed by reverse mode through its steps, every product in the
+ * working precision).
  *   coeffs : host, m+1 doubles.   A, G : batch x n x n (host or device).
+ *   policy : NULL or a policy whose f64_slices selects the products: 0 = FP64 pipe,
+ *            k = emulated with k exact bf16 slices (MPPS_FMT_F64E(k)); other fields unused.
  *   gradA  : batch x n x n output (host or device).
  */
 mpps_status ps_eval_adjoint(const double* coeffs, int m, const double* A, const double* G,
-                            int n, int batch, double* gradA, void* stream);
+                            int n, int batch, const mpps_policy* policy, double* gradA,
+                            void* stream);
 
 /*
  * C = A B for a batch of n x n FP64 matrices, the product computed in `format`

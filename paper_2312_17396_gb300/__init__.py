@@ -62,6 +62,11 @@ class _Policy(ctypes.Structure):
                 ("f64_slices", ctypes.c_int)]
 
 
+class _GroupItem(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("out", ctypes.c_void_p), ("n", ctypes.c_int),
+                ("m", ctypes.c_int)]
+
+
 class _Report(ctypes.Structure):
     _fields_ = [("s", ctypes.c_int), ("r", ctypes.c_int), ("nu", ctypes.c_int),
                 ("sigma", ctypes.c_int), ("fold", ctypes.c_int),
@@ -74,7 +79,7 @@ class _Report(ctypes.Structure):
 EXPORTS = ("mpps_policy_default", "mpps_plan", "ps_eval", "expm_taylor_ss", "ps_eval_adjoint",
            "mpps_matmul", "mpps_last_error", "mpps_version", "mpps_profile_enable",
            "mpps_profile_reset", "mpps_profile_read", "mpps_matmul_noalloc",
-           "mpps_selftest_bounded_wait")
+           "mpps_selftest_bounded_wait", "expm_taylor_ss_grouped")
 PROF_GEMM_F64, PROF_GEMM_TC, PROF_ELEMENTWISE, PROF_GEMM_F64E = 0, 1, 2, 3
 
 
@@ -95,10 +100,13 @@ def lib():
                               ctypes.POINTER(_Report), vp]
         L.expm_taylor_ss.argtypes = [vp, ip, ip, ip, ctypes.POINTER(_Policy), vp,
                                      ctypes.POINTER(_Report), vp]
-        L.ps_eval_adjoint.argtypes = [dp, ip, vp, vp, ip, ip, vp, vp]
+        L.ps_eval_adjoint.argtypes = [dp, ip, vp, vp, ip, ip, ctypes.POINTER(_Policy), vp, vp]
         L.mpps_matmul.argtypes = [vp, vp, vp, ip, ip, ip, vp]
         L.mpps_matmul_noalloc.argtypes = [vp, vp, vp, ip, ip, ip, vp]
         L.mpps_matmul_noalloc.restype = ctypes.c_int
+        L.expm_taylor_ss_grouped.argtypes = [ctypes.POINTER(_GroupItem), ip, ctypes.POINTER(_Policy),
+                                             ctypes.POINTER(_Report), vp]
+        L.expm_taylor_ss_grouped.restype = ctypes.c_int
         L.mpps_selftest_bounded_wait.argtypes = [ctypes.c_int, vp]
         L.mpps_selftest_bounded_wait.restype = ctypes.c_int
         for f in ("mpps_plan", "ps_eval", "expm_taylor_ss", "ps_eval_adjoint", "mpps_matmul"):
@@ -305,8 +313,35 @@ def expm(A, m: int = 30, policy: Policy | None = None, out=None, report: bool = 
     return out
 
 
-def ps_eval_adjoint(coeffs, A, G, out=None, stream=None):
-    """Gradient of <G, p(A)> with respect to A (reverse mode through the PS steps, FP64)."""
+def expm_grouped(mats, degrees=None, policy: Policy | None = None, outs=None, report: bool = False,
+                 stream=None):
+    """exp of many CUDA matrices of different orders (and Taylor degrees) in one call.
+    mats: list of (n_i, n_i) float64 CUDA tensors; degrees: list of m_i (default 30)."""
+    torch = _torch()
+    count = len(mats)
+    if degrees is None:
+        degrees = [30] * count
+    if outs is None:
+        outs = [torch.empty_like(a) for a in mats]
+    arr = (_GroupItem * max(1, count))()
+    for i, (a, o, m) in enumerate(zip(mats, outs, degrees)):
+        if not (_is_torch(a) and a.is_cuda and a.dtype == torch.float64 and a.is_contiguous()
+                and a.dim() == 2 and a.shape[0] == a.shape[1]):
+            raise ValueError("expm_grouped takes contiguous square float64 CUDA tensors")
+        arr[i] = _GroupItem(a.data_ptr(), o.data_ptr(), int(a.shape[0]), int(m))
+    reps = (_Report * count)() if report else None
+    pol = (policy or Policy())._c()
+    st = ctypes.c_void_p(int(stream)) if stream is not None else \
+        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    _check(lib().expm_taylor_ss_grouped(arr, count, ctypes.byref(pol), reps, st))
+    if report:
+        return outs, [_report_dict(r) for r in reps]
+    return outs
+
+
+def ps_eval_adjoint(coeffs, A, G, out=None, policy: Policy | None = None, stream=None):
+    """Gradient of <G, p(A)> with respect to A (reverse mode through the PS steps; products
+    on the FP64 pipe, or emulated when policy.f64_slices > 0)."""
     ptr, batch, n, kind, keep = _prep(A, "A")
     gptr, gb, gn, _, _ = _prep(G, "G")
     if (gb, gn) != (batch, n):
@@ -315,8 +350,9 @@ def ps_eval_adjoint(coeffs, A, G, out=None, stream=None):
         out = _empty_like(A, keep)
     optr, _, _, _, _ = _prep(out, "out")
     c, cp, m = _coef_ptr(coeffs)
+    pol = (policy or Policy(f64_slices=0))._c()
     _check(lib().ps_eval_adjoint(cp, m, ctypes.c_void_p(ptr), ctypes.c_void_p(gptr), n, batch,
-                                 ctypes.c_void_p(optr), _stream_for(kind, stream)))
+                                 ctypes.byref(pol), ctypes.c_void_p(optr), _stream_for(kind, stream)))
     return out
 
 
@@ -389,6 +425,7 @@ def _make_autograd():
             P = ps_eval(c, A64, policy=policy)
             ctx.save_for_backward(A64)
             ctx.coeffs = c
+            ctx.policy = policy
             ctx.in_dtype = A.dtype
             return P.to(A.dtype)
 
@@ -396,7 +433,7 @@ def _make_autograd():
         def backward(ctx, grad_out):
             (A64,) = ctx.saved_tensors
             G = grad_out.detach().to(torch.float64).contiguous()
-            gA = ps_eval_adjoint(ctx.coeffs, A64, G)
+            gA = ps_eval_adjoint(ctx.coeffs, A64, G, policy=ctx.policy)
             return gA.to(ctx.in_dtype), None, None
 
     return PolyFn

@@ -765,6 +765,75 @@ mpps_status expm_taylor_ss(const double* A, int n, int batch, int m, const mpps_
     return run_eval(c.data(), m, A, n, batch, policy, out, rep, stream, true);
 }
 
+mpps_status expm_taylor_ss_grouped(const mpps_group_item* items, int count,
+                                   const mpps_policy* policy, mpps_report* rep, void* stream) {
+    clear_error();
+    if (count < 0 || (count > 0 && !items)) {
+        set_error("expm_taylor_ss_grouped: invalid argument (count=%d)", count);
+        return MPPS_EINVAL;
+    }
+    if (count == 0) return MPPS_OK;
+    for (int i = 0; i < count; ++i) {
+        const int m = items[i].m <= 0 ? 30 : items[i].m;
+        if (items[i].n <= 0 || m > 170 || !items[i].A || !items[i].out ||
+            !is_device_ptr(items[i].A) || !is_device_ptr(items[i].out)) {
+            set_error("expm_taylor_ss_grouped: item %d invalid (n=%d, m=%d, device pointers "
+                      "required)", i, items[i].n, items[i].m);
+            return MPPS_EINVAL;
+        }
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    Pol P = resolve(policy);
+    // buckets keyed by (padded order, degree), in first-appearance order
+    struct Bucket { int n_pad, m; std::vector<int> idx; };
+    std::vector<Bucket> buckets;
+    for (int i = 0; i < count; ++i) {
+        const int m = items[i].m <= 0 ? 30 : items[i].m;
+        const int np = (items[i].n + 31) / 32 * 32;
+        size_t k = 0;
+        while (k < buckets.size() && !(buckets[k].n_pad == np && buckets[k].m == m)) ++k;
+        if (k == buckets.size()) buckets.push_back({np, m, {}});
+        buckets[k].idx.push_back(i);
+    }
+    for (const Bucket& bk : buckets) {
+        const int cnt = (int)bk.idx.size();
+        if (cnt > 65535) {
+            set_error("expm_taylor_ss_grouped: more than 65535 items of one size and degree");
+            return MPPS_EINVAL;
+        }
+        const long long nn = (long long)bk.n_pad * bk.n_pad;
+        std::vector<double> c(bk.m + 1);
+        long double f = 1.0L;
+        for (int i = 0; i <= bk.m; ++i) {
+            if (i > 0) f /= (long double)i;
+            c[i] = (double)f;
+        }
+        std::vector<PadItem> list(cnt);
+        for (int j = 0; j < cnt; ++j) {
+            const mpps_group_item& it = items[bk.idx[j]];
+            list[j] = PadItem{it.A, it.out, it.n, 0};
+        }
+        DevBuf buf;
+        const size_t list_bytes = ((sizeof(PadItem) * cnt + 255) / 256) * 256;
+        mpps_status rc = buf.alloc(list_bytes + 2 * sizeof(double) * nn * cnt, st);
+        if (rc) return rc;
+        PadItem* d_list = (PadItem*)buf.p;
+        double* dA = (double*)((char*)buf.p + list_bytes);
+        double* dO = dA + nn * cnt;
+        MPPS_CUDA_TRY(cudaMemcpyAsync(d_list, list.data(), sizeof(PadItem) * cnt,
+                                      cudaMemcpyHostToDevice, st));
+        if ((rc = launch_gather_pad(d_list, cnt, bk.n_pad, dA, st))) return rc;
+        std::vector<mpps_report> brep(rep ? cnt : 0);
+        rc = eval_device(c.data(), bk.m, dA, bk.n_pad, cnt, P, dO, rep ? brep.data() : nullptr, st,
+                         true, false);
+        if (rc) return rc;
+        if ((rc = launch_scatter_unpad(d_list, cnt, bk.n_pad, dO, st))) return rc;
+        if (rep)
+            for (int j = 0; j < cnt; ++j) rep[bk.idx[j]] = brep[j];
+    }
+    return MPPS_OK;
+}
+
 mpps_status mpps_matmul(const double* A, const double* B, double* C, int n, int batch, int format,
                         void* stream) {
     clear_error();
@@ -893,7 +962,7 @@ mpps_status mpps_matmul(const double* A, const double* B, double* C, int n, int 
 //   Bbar_r = Pbar_r;  Xbar_j += sum_i b_{si+j} Bbar_i;  Xbar_s += Ybar;
 //   for j = s..2: Xbar_{j-1} += Xbar_j X_1^T;  Xbar_1 += X_{j-1}^T Xbar_j;   grad = Xbar_1.
 mpps_status ps_eval_adjoint(const double* coeffs, int m, const double* A, const double* G, int n,
-                            int batch, double* gradA, void* stream) {
+                            int batch, const mpps_policy* policy, double* gradA, void* stream) {
     clear_error();
     mpps_status rc = check_sizes(n, batch);
     if (rc) return rc;
@@ -926,8 +995,17 @@ mpps_status ps_eval_adjoint(const double* coeffs, int m, const double* A, const 
         const int r = m / s;
         const bool fold = (m % s) == 0;
         const long long pw_bs = (long long)s * nn;
+        const Pol pol = resolve(policy);
+        if (pol.f64k < 0 || pol.f64k > MPPS_F64E_MAX_SLICES) {
+            set_error("f64_slices=%d outside 0..%d", pol.f64k, MPPS_F64E_MAX_SLICES);
+            return MPPS_EINVAL;
+        }
+        const int K = pol.f64k;      // products on the FP64 pipe (0) or emulated with K slices
         Arena L;
         double *pw, *xbar, *Pst, *Ybar, *Pbar0, *Pbar1, *Yt, *X1t, *T;
+        __nv_bfloat16 *slA = nullptr, *slB = nullptr;
+        int *eA = nullptr, *eB = nullptr;
+        unsigned long long* cmx = nullptr;
         auto lay = [&](Arena& z) {
             pw = z.take<double>((size_t)batch * pw_bs);
             xbar = z.take<double>((size_t)batch * pw_bs);
@@ -938,6 +1016,13 @@ mpps_status ps_eval_adjoint(const double* coeffs, int m, const double* A, const 
             Yt = z.take<double>(elems);
             X1t = z.take<double>(elems);
             T = z.take<double>(elems);
+            if (K > 0) {
+                slA = z.take<__nv_bfloat16>(f64e_plane_elems(n, batch, K));
+                slB = z.take<__nv_bfloat16>(f64e_plane_elems(n, batch, K));
+                eA = z.take<int>((size_t)batch * n);
+                eB = z.take<int>((size_t)batch * n);
+                cmx = z.take<unsigned long long>((size_t)batch * n);
+            }
         };
         lay(L);
         DevBuf ws;
@@ -946,12 +1031,25 @@ mpps_status ps_eval_adjoint(const double* coeffs, int m, const double* A, const 
         L.off = 0;
         lay(L);
         auto P_at = [&](int i) { return Pst + (size_t)i * batch * nn; };
+        DevErr* derr = nullptr;
+        if (K > 0) {
+            if ((rc = dev_err_get(&derr))) return rc;
+            if ((rc = dev_err_check(derr, false))) return rc;
+        }
+        // every product of the adjoint in the working precision: FP64 pipe or emulated
+        auto product = [&](const double* Am, long long a_bs, const double* Bm, long long b_bs,
+                           const Epilogue& ep) -> mpps_status {
+            if (K == 0) return launch_gemm_f64(Am, a_bs, Bm, b_bs, n, batch, ep, st);
+            mpps_status r1 = launch_slice_rows(Am, a_bs, n, batch, K, slA, eA, st);
+            if (!r1) r1 = launch_slice_cols(Bm, b_bs, n, batch, K, slB, eB, cmx, st);
+            if (!r1) r1 = launch_gemm_f64e(K, slA, K, eA, slB, K, eB, n, batch, batch, ep, derr->d, st);
+            return r1;
+        };
         // forward
         if ((rc = launch_scale_copy(a.dev, nn, pw, pw_bs, n, batch, nullptr, st))) return rc;
         for (int j = 2; j <= s; ++j) {
             Epilogue ep = epilogue_plain(pw + (long long)(j - 1) * nn, pw_bs);
-            if ((rc = launch_gemm_f64(pw + (long long)(j - 2) * nn, pw_bs, pw, pw_bs, n, batch, ep, st)))
-                return rc;
+            if ((rc = product(pw + (long long)(j - 2) * nn, pw_bs, pw, pw_bs, ep))) return rc;
         }
         const double* Y = pw + (long long)(s - 1) * nn;
         int i_top;   // highest Horner iterate that is a real matrix
@@ -975,7 +1073,7 @@ mpps_status ps_eval_adjoint(const double* coeffs, int m, const double* A, const 
             ep.nt = s - 1;
             for (int j = 0; j < s; ++j) ep.coef[j] = coeffs[(i - 1) * s + j];
             ep.pw = pw; ep.pw_bstride = pw_bs;
-            if ((rc = launch_gemm_f64(P_at(i), nn, Y, pw_bs, n, batch, ep, st))) return rc;
+            if ((rc = product(P_at(i), nn, Y, pw_bs, ep))) return rc;
         }
         // backward
         MPPS_CUDA_TRY(cudaMemsetAsync(xbar, 0, sizeof(double) * batch * pw_bs, st));
@@ -1007,12 +1105,12 @@ mpps_status ps_eval_adjoint(const double* coeffs, int m, const double* A, const 
             {
                 Epilogue ep = epilogue_plain(Ybar, nn);
                 ep.add = Ybar; ep.add_bstride = nn; ep.add_coef = 1.0;
-                if ((rc = launch_gemm_f64(T, nn, Pbar[cur], nn, n, batch, ep, st))) return rc;
+                if ((rc = product(T, nn, Pbar[cur], nn, ep))) return rc;
             }
             // Pbar_i = Pbar_{i-1} Y^T
             {
                 Epilogue ep = epilogue_plain(Pbar[cur ^ 1], nn);
-                if ((rc = launch_gemm_f64(Pbar[cur], nn, Yt, nn, n, batch, ep, st))) return rc;
+                if ((rc = product(Pbar[cur], nn, Yt, nn, ep))) return rc;
             }
             cur ^= 1;
         }
@@ -1036,16 +1134,21 @@ mpps_status ps_eval_adjoint(const double* coeffs, int m, const double* A, const 
             // Xbar_{j-1} += Xbar_j X_1^T
             Epilogue e1 = epilogue_plain(xjm, pw_bs);
             e1.add = xjm; e1.add_bstride = pw_bs; e1.add_coef = 1.0;
-            if ((rc = launch_gemm_f64(xj, pw_bs, X1t, nn, n, batch, e1, st))) return rc;
+            if ((rc = product(xj, pw_bs, X1t, nn, e1))) return rc;
             // Xbar_1 += X_{j-1}^T Xbar_j
             if ((rc = launch_scale_copy(pw + (long long)(j - 2) * nn, pw_bs, T, nn, n, batch, nullptr, st)))
                 return rc;
             if ((rc = launch_transpose(T, nn, Pbar0, n, batch, st))) return rc;
             Epilogue e2 = epilogue_plain(xbar, pw_bs);
             e2.add = xbar; e2.add_bstride = pw_bs; e2.add_coef = 1.0;
-            if ((rc = launch_gemm_f64(Pbar0, nn, xj, pw_bs, n, batch, e2, st))) return rc;
+            if ((rc = product(Pbar0, nn, xj, pw_bs, e2))) return rc;
         }
         if ((rc = launch_scale_copy(xbar, pw_bs, dGrad, nn, n, batch, nullptr, st))) return rc;
+        if (K > 0) {
+            if ((rc = dev_err_enqueue(derr, st))) return rc;
+            if ((!o_dev || !is_device_ptr(A) || !is_device_ptr(G)) && (rc = dev_err_check(derr, true)))
+                return rc;
+        }
     }
     if (!o_dev) {
         MPPS_CUDA_TRY(cudaMemcpyAsync(gradA, dGrad, elems * sizeof(double), cudaMemcpyDeviceToHost, st));

@@ -205,6 +205,17 @@ mpps_status launch_norm1(const double* M, long long bs, int n, int batch, double
 // X = 2^-sigma[b] A (exact power-of-two scaling; d_sigma null -> plain copy).
 mpps_status launch_scale_copy(const double* A, long long a_bs, double* X, long long x_bs, int n,
                               int batch, const int* d_sigma, cudaStream_t st);
+// One member of an uneven batch (device pointers), for the padded gather / scatter.
+struct PadItem {
+    const double* A;
+    double* out;
+    int n;
+    int pad_;
+};
+mpps_status launch_gather_pad(const PadItem* d_list, int count, int n_pad, double* dst,
+                              cudaStream_t st);
+mpps_status launch_scatter_unpad(const PadItem* d_list, int count, int n_pad, const double* src,
+                                 cudaStream_t st);
 // sigma[b] = max(0, ceil(log2 norms[b])) on the device.
 mpps_status launch_sigma(const double* norms, int batch, int* sigma, cudaStream_t st);
 // out[b] = (sigma[b] odd ? q1 : q0)[b] + diag I  (all contiguous, stride n*n).

@@ -11,6 +11,7 @@ namespace {
 
 constexpr int kColsPerBlock = 128;   // one thread per column (coalesced row reads)
 constexpr int kRowsPerChunk = 64;    // rows summed by one thread before writing a partial
+constexpr int kRowsF32 = 16;         // the same for the FP32 norms: many short chains
 
 __device__ __forceinline__ double block_max(double v) {
     __shared__ double red[32];
@@ -71,25 +72,38 @@ __global__ void k_norms_finalize(const double* __restrict__ partial, int n, int 
     if (threadIdx.x == 0) norms[(long long)b * q + t] = best;
 }
 
-// Column sums of |M| accumulated row by row in order 0..n-1 (one thread per column), so
-// that ||M||_1 is the same double as a plain sequential loop computes.  32 rows are
-// loaded ahead (independent loads in flight), then added in order; rows past n add 0.
-__global__ void k_colsum_seq(const double* __restrict__ M, long long bs, int n,
-                             double* __restrict__ colsum) {
+__global__ void k_colsum_partial(const double* __restrict__ M, long long bs, int n,
+                                 double* __restrict__ partial) {
     const int col = blockIdx.x * kColsPerBlock + threadIdx.x;
-    const int b = blockIdx.y;
+    const int chunk = blockIdx.y, chunks = gridDim.y, b = blockIdx.z;
     if (col >= n) return;
-    const double* base = M + (long long)b * bs + col;
+    const double* base = M + (long long)b * bs;
+    const int r0 = chunk * kRowsPerChunk, r1 = min(n, r0 + kRowsPerChunk);
     double acc = 0.0;
-    for (int r0 = 0; r0 < n; r0 += 32) {
-        double v[32];
-#pragma unroll
-        for (int k = 0; k < 32; ++k)
-            v[k] = (r0 + k < n) ? __ldg(base + (long long)(r0 + k) * n) : 0.0;
-#pragma unroll
-        for (int k = 0; k < 32; ++k) acc += fabs(v[k]);
+    for (int row = r0; row < r1; ++row) acc += fabs(__ldg(base + (long long)row * n + col));
+    partial[((long long)b * chunks + chunk) * n + col] = acc;
+}
+
+// One block per matrix: if norms[b] is within 2^-44 (relative) of a power of two, replace
+// it by the max of the sequential (row 0..n-1) column sums, the order a plain loop uses.
+__global__ void k_norm1_exact_near_pow2(const double* __restrict__ M, long long bs, int n,
+                                        double* __restrict__ norms) {
+    const int b = blockIdx.x;
+    const double a = norms[b];
+    if (!(a > 0.0) || !isfinite(a)) return;
+    int e;
+    const double f = frexp(a, &e);                       // a = f 2^e, f in [0.5, 1)
+    const double gap = fmin(f - 0.5, 1.0 - f);           // distance to 2^(e-1) or 2^e, / 2^e
+    if (gap > 0x1p-44) return;
+    double best = 0.0;
+    const double* base = M + (long long)b * bs;
+    for (int col = threadIdx.x; col < n; col += blockDim.x) {
+        double acc = 0.0;
+        for (int row = 0; row < n; ++row) acc += fabs(base[(long long)row * n + col]);
+        best = fmax(best, acc);
     }
-    colsum[(long long)b * n + col] = acc;
+    best = block_max(best);
+    if (threadIdx.x == 0) norms[b] = best;
 }
 
 // FP64 -> FP32 by bit manipulation (truncating the significand; underflow to 0, overflow to
@@ -122,7 +136,7 @@ __global__ void k_block_norms_partial_f32(const double* __restrict__ pw, long lo
     for (int t = 0; t < q; ++t) acc[t] = 0.f;
     const long long nn = (long long)n * n;
     const double* base = pw + (long long)b * pw_bs;
-    const int r0 = chunk * 16, r1 = min(n, r0 + 16);
+    const int r0 = chunk * kRowsF32, r1 = min(n, r0 + kRowsF32);
     for (int row = r0; row < r1; ++row) {
         x[0] = (row == col) ? 1.f : 0.f;
         for (int j = 1; j <= s; ++j)
@@ -140,22 +154,71 @@ __global__ void k_block_norms_partial_f32(const double* __restrict__ pw, long lo
         partial[(((long long)b * chunks + chunk) * q + t) * n + col] = (double)acc[t];
 }
 
+// The same sums with compile-time bounds (s <= 8, r <= 8, the exp degrees up to 72):
+// the power values and the block accumulators stay in registers.
+constexpr int kRegS = 8, kRegR = 8;
+__global__ void k_block_norms_partial_f32_reg(const double* __restrict__ pw, long long pw_bs,
+                                              int n, int s, int m, NormCoefs cf,
+                                              double* __restrict__ partial) {
+    const int col = blockIdx.x * kColsPerBlock + threadIdx.x;
+    const int chunk = blockIdx.y, chunks = gridDim.y, b = blockIdx.z;
+    const int r = m / s, q = r + 3;
+    if (col >= n) return;
+    float acc[kRegR + 3];
+    float x[kRegS + 1];
+#pragma unroll
+    for (int t = 0; t < kRegR + 3; ++t) acc[t] = 0.f;
+    const long long nn = (long long)n * n;
+    const double* base = pw + (long long)b * pw_bs + col;
+    const int r0 = chunk * kRowsF32, r1 = min(n, r0 + kRowsF32);
+    for (int row = r0; row < r1; ++row) {
+        const double* p = base + (long long)row * n;
+        x[0] = (row == col) ? 1.f : 0.f;
+#pragma unroll
+        for (int j = 1; j <= kRegS; ++j) x[j] = (j <= s) ? narrow(__ldg(p + (long long)(j - 1) * nn)) : 0.f;
+#pragma unroll
+        for (int i = 0; i <= kRegR; ++i) {
+            if (i <= r) {
+                const int top = (i < r) ? s - 1 : m - s * r;
+                float v = 0.f;
+#pragma unroll
+                for (int j = 0; j < kRegS; ++j)
+                    if (j <= top) v = fmaf(cf.c[s * i + j], x[j], v);
+                acc[i] += fabsf(v);
+            }
+        }
+        float xs = 0.f;
+#pragma unroll
+        for (int j = 1; j <= kRegS; ++j) if (j == s) xs = x[j];
+        acc[kRegR + 1] += fabsf(xs);
+        acc[kRegR + 2] += fabsf(x[1]);
+    }
+    double* out = partial + ((long long)b * chunks + chunk) * q * n + col;
+#pragma unroll
+    for (int t = 0; t <= kRegR; ++t)
+        if (t <= r) out[(long long)t * n] = (double)acc[t];
+    out[(long long)(r + 1) * n] = (double)acc[kRegR + 1];
+    out[(long long)(r + 2) * n] = (double)acc[kRegR + 2];
+}
+
 struct BlockScales {
     double c[MPPS_MAX_R + 3];
 };
 
+// One thread per column (chunks summed in order), block max, then an order-independent
+// atomic max over column blocks (norms must be zeroed first).
 __global__ void k_norms_finalize_scaled(const double* __restrict__ partial, int n, int chunks,
                                         int q, BlockScales sc, double* __restrict__ norms) {
-    const int t = blockIdx.x, b = blockIdx.y;
-    double best = 0.0;
-    for (int col = threadIdx.x; col < n; col += blockDim.x) {
-        double sum = 0.0;
+    const int t = blockIdx.x, b = blockIdx.z;
+    const int col = blockIdx.y * blockDim.x + threadIdx.x;
+    double sum = 0.0;
+    if (col < n)
         for (int c = 0; c < chunks; ++c)
             sum += partial[(((long long)b * chunks + c) * q + t) * n + col];
-        best = fmax(best, sum);
-    }
-    best = block_max(best);
-    if (threadIdx.x == 0) norms[(long long)b * q + t] = best * sc.c[t];
+    const double best = block_max(sum) * sc.c[t];
+    if (threadIdx.x == 0)
+        atomicMax((unsigned long long*)(norms + (long long)b * q + t),
+                  (unsigned long long)__double_as_longlong(best));
 }
 
 __global__ void k_scale_copy(const double* __restrict__ A, long long a_bs, double* __restrict__ X,
@@ -165,6 +228,31 @@ __global__ void k_scale_copy(const double* __restrict__ A, long long a_bs, doubl
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
          t += (long long)gridDim.x * blockDim.x)
         X[b * x_bs + t] = ldexp(A[b * a_bs + t], e);
+}
+
+// Gather items of different orders into a zero-padded batch (row-major n_pad x n_pad each)
+// and scatter the leading n x n blocks back.
+__global__ void k_gather_pad(const PadItem* __restrict__ list, int n_pad, double* __restrict__ dst) {
+    const PadItem it = list[blockIdx.y];
+    const long long nn = (long long)n_pad * n_pad;
+    double* d = dst + (long long)blockIdx.y * nn;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(t / n_pad), c = (int)(t % n_pad);
+        d[t] = (r < it.n && c < it.n) ? it.A[(long long)r * it.n + c] : 0.0;
+    }
+}
+
+__global__ void k_scatter_unpad(const PadItem* __restrict__ list, int n_pad,
+                                const double* __restrict__ src) {
+    const PadItem it = list[blockIdx.y];
+    const long long nn = (long long)it.n * it.n;
+    const double* sp = src + (long long)blockIdx.y * n_pad * n_pad;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(t / it.n), c = (int)(t % it.n);
+        it.out[t] = sp[(long long)r * n_pad + c];
+    }
 }
 
 // sigma[b] = max(0, ceil(log2 norms[b])) (0 for a non-finite norm), exactly as the host rule.
@@ -319,7 +407,7 @@ size_t block_norms_partial_elems(int n, int batch, int m, int s) {
 size_t norm1_partial_elems(int n, int batch) { return (size_t)batch * n; }
 
 size_t block_norms_f32_partial_elems(int n, int batch, int m, int s) {
-    return (size_t)batch * ((n + 15) / 16) * block_norms_count(m, s) * n;
+    return (size_t)batch * ((n + kRowsF32 - 1) / kRowsF32) * block_norms_count(m, s) * n;
 }
 
 mpps_status launch_block_norms_f32(const double* pw, long long pw_bs, int n, int batch, int s,
@@ -339,11 +427,16 @@ mpps_status launch_block_norms_f32(const double* pw, long long pw_bs, int n, int
     }
     sc.c[r + 1] = 1.0;
     sc.c[r + 2] = 1.0;
-    const int chunks = (n + 15) / 16;
+    const int chunks = (n + kRowsF32 - 1) / kRowsF32;
     dim3 g((n + kColsPerBlock - 1) / kColsPerBlock, chunks, batch);
-    k_block_norms_partial_f32<<<g, kColsPerBlock, 0, st>>>(pw, pw_bs, n, s, m, cf, partial);
+    MPPS_CUDA_TRY(cudaMemsetAsync(norms, 0, sizeof(double) * (size_t)batch * q, st));
+    if (s <= kRegS && m / s <= kRegR)
+        k_block_norms_partial_f32_reg<<<g, kColsPerBlock, 0, st>>>(pw, pw_bs, n, s, m, cf, partial);
+    else
+        k_block_norms_partial_f32<<<g, kColsPerBlock, 0, st>>>(pw, pw_bs, n, s, m, cf, partial);
     MPPS_LAUNCH_CHECK();
-    k_norms_finalize_scaled<<<dim3(q, batch), 256, 0, st>>>(partial, n, chunks, q, sc, norms);
+    k_norms_finalize_scaled<<<dim3(q, (n + 127) / 128, batch), 128, 0, st>>>(partial, n, chunks, q,
+                                                                              sc, norms);
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }
@@ -365,10 +458,16 @@ mpps_status launch_block_norms(const double* pw, long long pw_bs, int n, int bat
 mpps_status launch_norm1(const double* M, long long bs, int n, int batch, double* partial,
                          double* norms, cudaStream_t st) {
     ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
-    dim3 g((n + kColsPerBlock - 1) / kColsPerBlock, batch);
-    k_colsum_seq<<<g, kColsPerBlock, 0, st>>>(M, bs, n, partial);
+    // fast chunked sums (64-row partials, summed in chunk order) ...
+    const int chunks = (n + kRowsPerChunk - 1) / kRowsPerChunk;
+    dim3 g((n + kColsPerBlock - 1) / kColsPerBlock, chunks, batch);
+    k_colsum_partial<<<g, kColsPerBlock, 0, st>>>(M, bs, n, partial);
     MPPS_LAUNCH_CHECK();
-    k_norms_finalize<<<dim3(1, batch), 256, 0, st>>>(partial, n, 1, 1, norms);
+    k_norms_finalize<<<dim3(1, batch), 256, 0, st>>>(partial, n, chunks, 1, norms);
+    MPPS_LAUNCH_CHECK();
+    // ... and, only for a matrix whose norm lies within 2^-44 of a power of two (where the
+    // summation order could move ceil(log2 ||A||_1)), the plain sequential column sums
+    k_norm1_exact_near_pow2<<<batch, 256, 0, st>>>(M, bs, n, norms);
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }
@@ -378,6 +477,24 @@ mpps_status launch_scale_copy(const double* A, long long a_bs, double* X, long l
     ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
     const long long nn = (long long)n * n;
     k_scale_copy<<<dim3(grid1d(nn, 256), batch), 256, 0, st>>>(A, a_bs, X, x_bs, nn, d_sigma);
+    MPPS_LAUNCH_CHECK();
+    return MPPS_OK;
+}
+
+mpps_status launch_gather_pad(const PadItem* d_list, int count, int n_pad, double* dst,
+                              cudaStream_t st) {
+    ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
+    const long long nn = (long long)n_pad * n_pad;
+    k_gather_pad<<<dim3(grid1d(nn, 256, 64), count), 256, 0, st>>>(d_list, n_pad, dst);
+    MPPS_LAUNCH_CHECK();
+    return MPPS_OK;
+}
+
+mpps_status launch_scatter_unpad(const PadItem* d_list, int count, int n_pad, const double* src,
+                                 cudaStream_t st) {
+    ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
+    const long long nn = (long long)n_pad * n_pad;
+    k_scatter_unpad<<<dim3(grid1d(nn, 256, 64), count), 256, 0, st>>>(d_list, n_pad, src);
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }

@@ -32,9 +32,12 @@
 
 #include <cudaTypedefs.h>
 
+#include <map>
 #include <mutex>
 
 namespace mpps {
+
+int f64e_cluster_choice(int dev, int n, int k, int batch);
 
 namespace {
 
@@ -101,7 +104,38 @@ __global__ void k_slice_rows(const double* __restrict__ M, long long bs, int n, 
     const double scale = ldexp(1.0, 62 - e);
     __nv_bfloat16* dst = planes + (long long)b * plane_bs + (long long)row * lld;
     const long long pstride = (long long)n * lld;
-    for (int j = lane; j < n; j += 32) put_digits(src[j], scale, k, dst + j, pstride);
+    int j = lane;
+    for (; j + 96 < n; j += 128) {              // 4 loads in flight per lane
+        const double x0 = src[j], x1 = src[j + 32], x2 = src[j + 64], x3 = src[j + 96];
+        put_digits(x0, scale, k, dst + j, pstride);
+        put_digits(x1, scale, k, dst + j + 32, pstride);
+        put_digits(x2, scale, k, dst + j + 64, pstride);
+        put_digits(x3, scale, k, dst + j + 96, pstride);
+    }
+    for (; j < n; j += 32) put_digits(src[j], scale, k, dst + j, pstride);
+}
+
+// Row maxima of |M| -> exponents e_i (one warp per row).
+__global__ void k_rowexp(const double* __restrict__ M, long long bs, int n, int* __restrict__ exps) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = blockIdx.x * (blockDim.x >> 5) + warp, b = blockIdx.y;
+    if (row >= n) return;
+    const double* src = M + (long long)b * bs + (long long)row * n;
+    double mx = 0.0;
+    for (int j = lane; j < n; j += 32) mx = fmax(mx, fabs(src[j]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) exps[(long long)b * n + row] = exp_above(mx);
+}
+
+// Row slices, one thread per element (the exponents come from k_rowexp).
+__global__ void k_slice_rows_elem(const double* __restrict__ M, long long bs, int n, int k,
+                                  const int* __restrict__ exps, __nv_bfloat16* __restrict__ planes,
+                                  long long plane_bs, int lld) {
+    const int col = blockIdx.x * blockDim.x + threadIdx.x, row = blockIdx.y, b = blockIdx.z;
+    if (col >= n) return;
+    const int e = exps[(long long)b * n + row];
+    put_digits(M[(long long)b * bs + (long long)row * n + col], ldexp(1.0, 62 - e), k,
+               planes + (long long)b * plane_bs + (long long)row * lld + col, (long long)n * lld);
 }
 
 // Column maxima of |M| (as the bit pattern of a non-negative double; out zeroed first).
@@ -141,6 +175,11 @@ __global__ void k_slice_cols(const double* __restrict__ M, long long bs, int n, 
     }
 }
 
+// CL > 1: the CTA is one of CL neighbours along the output columns (a cluster) sharing the
+// same row block; each loads the A slices t = rank (mod CL) and multicasts them to all CL,
+// and every CTA's MMA completion is signalled to all CL (a stage is reloaded only when all
+// of them have consumed it).
+template <int CL>
 __global__ void __launch_bounds__(192, 1)
     k_gemm_f64e(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 int n, int k, int ksA, int ksB, const int* __restrict__ eA,
@@ -166,10 +205,12 @@ __global__ void __launch_bounds__(192, 1)
     const int kb_per_chunk = KCHUNK / KB;
     const int nchunks = (nkb + kb_per_chunk - 1) / kb_per_chunk;
 
+    const uint32_t crank = CL > 1 ? cluster_ctarank() : 0;
+    constexpr uint16_t kMask = (uint16_t)((1u << CL) - 1u);
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+            mbar_init(&empty[s], CL);
         }
         mbar_init(chunk_done, 1);
         mbar_init(tmem_free, 128);
@@ -178,6 +219,7 @@ __global__ void __launch_bounds__(192, 1)
     if (warp == 0) tmem_alloc(tmem_slot, TCOLS);
     tc_fence_before();
     __syncthreads();
+    if constexpr (CL > 1) cluster_sync();   // peers' barriers exist before any multicast
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
@@ -190,7 +232,12 @@ __global__ void __launch_bounds__(192, 1)
                 uint8_t* st = smem + s * SB;
                 const int kc = kb * KB;
                 for (int t = 0; t < k; ++t) {
-                    tma_load_3d(st + t * A_TILE, &tmA, kc, m0, b * ksA + t, &full[s]);
+                    if constexpr (CL > 1) {
+                        if (t % CL == (int)crank)
+                            tma_load_3d_mc(st + t * A_TILE, &tmA, kc, m0, b * ksA + t, &full[s], kMask);
+                    } else {
+                        tma_load_3d(st + t * A_TILE, &tmA, kc, m0, b * ksA + t, &full[s]);
+                    }
                     tma_load_3d(st + k * A_TILE + t * B_TILE, &tmB, kc, n0, b * ksB + t, &full[s]);
                 }
             }
@@ -226,7 +273,8 @@ __global__ void __launch_bounds__(192, 1)
                                      make_idesc(1, OM, N - 256), acc);
                     }
                 }
-                tc_commit(&empty[s]);
+                if constexpr (CL > 1) tc_commit_mc(&empty[s], kMask);
+                else tc_commit(&empty[s]);
                 if (kin == kb_per_chunk - 1 || kb == nkb - 1) tc_commit(chunk_done);
             }
             if (!ok) tc_commit(chunk_done);
@@ -261,17 +309,28 @@ __global__ void __launch_bounds__(192, 1)
         const int col = n0 + lane;
         const int ec = col < n ? eB[(long long)b * n + col] : 0;
 #pragma unroll 1
-        for (int rr = 0; rr < 32; ++rr) {
-            const int r = m0 + warp * 32 + rr;
-            if (r < n && col < n)
-                epilogue_store(ep, b, r, col, n,
-                               epilogue_value(ep, b, r, col, n, ldexp(stile[rr * 33 + lane], ec)));
+        for (int r4 = 0; r4 < 32; r4 += 4) {      // 4 rows per pass: their loads overlap
+            double val[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int r = m0 + warp * 32 + r4 + u;
+                val[u] = (r < n && col < n)
+                             ? epilogue_value(ep, b, r, col, n, ldexp(stile[(r4 + u) * 33 + lane], ec))
+                             : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int r = m0 + warp * 32 + r4 + u;
+                if (r < n && col < n) epilogue_store(ep, b, r, col, n, val[u]);
+            }
         }
     }
     __syncwarp();
     tc_fence_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, TCOLS);
+    // no CTA leaves while a peer may still signal its barriers or multicast into it
+    if constexpr (CL > 1) cluster_sync();
 }
 
 // ---- host -----------------------------------------------------------------------------
@@ -302,7 +361,115 @@ bool make_plane_map(CUtensorMap* tm, const void* ptr, int n, int nplanes, int ll
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Launch with a cluster of `cl` CTAs along the output columns (grid x rounded up to it).
+mpps_status launch_f64e_cl(int cl, const CUtensorMap& ta, const CUtensorMap& tb, int n, int k,
+                           int ksA, int ksB, const int* eA, const int* eB, int batch,
+                           const Epilogue& ep, int* d_err, cudaStream_t st, const int* bidx,
+                           int smem) {
+    const int gx = (n + ON - 1) / ON;
+    dim3 grid((gx + cl - 1) / cl * cl, (n + OM - 1) / OM, batch);
+    if (cl == 1) {
+        k_gemm_f64e<1><<<grid, 192, smem, st>>>(ta, tb, n, k, ksA, ksB, eA, eB, ep, d_err, bidx);
+        MPPS_LAUNCH_CHECK();
+        return MPPS_OK;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(192, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = (cl == 2)
+        ? cudaLaunchKernelEx(&cfg, k_gemm_f64e<2>, ta, tb, n, k, ksA, ksB, eA, eB, ep, d_err, bidx)
+        : cudaLaunchKernelEx(&cfg, k_gemm_f64e<4>, ta, tb, n, k, ksA, ksB, eA, eB, ep, d_err, bidx);
+    if (e != cudaSuccess) {
+        set_error("cluster launch of the emulated FP64 product failed: %s", cudaGetErrorString(e));
+        return MPPS_ECUDA;
+    }
+    return MPPS_OK;
+}
+
 }  // namespace
+
+// ---- autotuner: cluster size of the emulated product per (device, size class, slices) ----
+// On the first product of a size class (n rounded up to a power of two, batch 1 vs many) the
+// three cluster sizes are timed on scratch operands of that size and the fastest is kept
+// for the process.  The timing synchronises the device once per class: make a first call
+// of each size before capturing a CUDA graph.
+namespace {
+std::mutex g_tune_mu;
+std::map<long long, int> g_tuned;
+}
+
+int f64e_cluster_choice(int dev, int n, int k, int batch) {
+    int cls = 1;
+    while (cls < n) cls <<= 1;
+    const long long key = ((long long)dev << 40) | ((long long)cls << 8) | ((long long)k << 1) |
+                          (batch > 1 ? 1 : 0);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) return it->second;
+    }
+    int best = 1;
+    // time on scratch buffers: the caller's epilogue may accumulate into its output
+    const int ntune = cls < 64 ? 64 : (cls > 2048 ? 2048 : cls);
+    const int bt = batch > 1 ? 8 : 1;
+    const int lld = low_ld(ntune);
+    const size_t plane_b = (size_t)bt * k * ntune * lld * 2;
+    void *sa = nullptr, *sb = nullptr, *ex = nullptr, *out = nullptr, *er = nullptr;
+    cudaStream_t ts = nullptr;
+    bool ok = cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaMalloc(&sa, plane_b) == cudaSuccess && cudaMalloc(&sb, plane_b) == cudaSuccess &&
+              cudaMalloc(&ex, sizeof(int) * bt * ntune) == cudaSuccess &&
+              cudaMalloc(&out, sizeof(double) * bt * ntune * ntune) == cudaSuccess &&
+              cudaMalloc(&er, sizeof(int)) == cudaSuccess;
+    if (ok) {
+        cudaMemsetAsync(sa, 0, plane_b, ts);
+        cudaMemsetAsync(sb, 0, plane_b, ts);
+        cudaMemsetAsync(ex, 0, sizeof(int) * bt * ntune, ts);
+        cudaMemsetAsync(er, 0, sizeof(int), ts);
+        CUtensorMap ta, tb;
+        ok = make_plane_map(&ta, sa, ntune, bt * k, lld, OM) && make_plane_map(&tb, sb, ntune, bt * k, lld, ON);
+        const int smem = num_stages(k) * stage_bytes(k) + 1024 + 256;
+        Epilogue ep = epilogue_plain((double*)out, (long long)ntune * ntune);
+        float best_ms = 1e30f;
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        const int cands[3] = {1, 2, 4};
+        for (int ci = 0; ok && ci < 3; ++ci) {
+            const int cl = cands[ci];
+            if (launch_f64e_cl(cl, ta, tb, ntune, k, k, k, (int*)ex, (int*)ex, bt, ep, (int*)er, ts,
+                               nullptr, smem))
+                continue;   // warm-up (and skip a size that cannot launch)
+            cudaEventRecord(e0, ts);
+            for (int rep = 0; rep < 3; ++rep)
+                launch_f64e_cl(cl, ta, tb, ntune, k, k, k, (int*)ex, (int*)ex, bt, ep, (int*)er, ts,
+                               nullptr, smem);
+            cudaEventRecord(e1, ts);
+            if (cudaEventSynchronize(e1) != cudaSuccess) { ok = false; break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) { best_ms = ms; best = cl; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    cudaGetLastError();
+    if (ts) cudaStreamSynchronize(ts);
+    cudaFree(sa); cudaFree(sb); cudaFree(ex); cudaFree(out); cudaFree(er);
+    if (ts) cudaStreamDestroy(ts);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[key] = best;
+    return best;
+}
 
 size_t f64e_plane_elems(int n, int batch, int k) { return (size_t)batch * k * n * low_ld(n); }
 
@@ -310,9 +477,17 @@ mpps_status launch_slice_rows(const double* M, long long bs, int n, int batch, i
                               int* exps, cudaStream_t st) {
     ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
     const int lld = low_ld(n);
-    dim3 g((n + 7) / 8, batch);
-    k_slice_rows<<<g, 256, 0, st>>>(M, bs, n, k, (__nv_bfloat16*)planes, (long long)k * n * lld, lld,
-                                    exps);
+    if (n >= 256 && batch <= 65535) {
+        // many threads per row: a row-maximum pass, then one thread per element
+        k_rowexp<<<dim3((n + 7) / 8, batch), 256, 0, st>>>(M, bs, n, exps);
+        MPPS_LAUNCH_CHECK();
+        k_slice_rows_elem<<<dim3((n + 127) / 128, n, batch), 128, 0, st>>>(
+            M, bs, n, k, exps, (__nv_bfloat16*)planes, (long long)k * n * lld, lld);
+    } else {
+        dim3 g((n + 7) / 8, batch);
+        k_slice_rows<<<g, 256, 0, st>>>(M, bs, n, k, (__nv_bfloat16*)planes, (long long)k * n * lld,
+                                        lld, exps);
+    }
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }
@@ -347,19 +522,22 @@ mpps_status launch_gemm_f64e(int k, const void* slicesA, int ksA, const int* eA,
         return MPPS_ECUDA;
     }
     const int smem = num_stages(k) * stage_bytes(k) + 1024 + 256;
-    static int attr_done[64] = {0};
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 64 && attr_done[dev] < smem) {
-        MPPS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_f64e, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (dev < 0 || dev >= 64) dev = 0;
+    static int attr_done[64] = {0};
+    if (!attr_done[dev]) {
+        MPPS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_f64e<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            SMEM_BUDGET + 1024 + 256));
-        attr_done[dev] = SMEM_BUDGET + 1024 + 256;
+        MPPS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_f64e<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           SMEM_BUDGET + 1024 + 256));
+        MPPS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_f64e<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           SMEM_BUDGET + 1024 + 256));
+        attr_done[dev] = 1;
     }
+    const int cl = f64e_cluster_choice(dev, n, k, batch);
     ProfScope prof(MPPS_PROF_GEMM_F64E, st, 2.0 * n * (double)n * n * batch * (k * (k + 1) / 2));
-    dim3 grid((n + ON - 1) / ON, (n + OM - 1) / OM, batch);
-    k_gemm_f64e<<<grid, 192, smem, st>>>(ta, tb, n, k, ksA, ksB, eA, eB, ep, d_err, bidx);
-    MPPS_LAUNCH_CHECK();
-    return MPPS_OK;
+    return launch_f64e_cl(cl, ta, tb, n, k, ksA, ksB, eA, eB, batch, ep, d_err, st, bidx, smem);
 }
 
 }  // namespace mpps

@@ -29,9 +29,9 @@ namespace {
 
 using namespace tc;
 
-constexpr int TM = 128, TN = 128;
+constexpr int TM = 128;                   // output rows per CTA (TN, the columns, is 64 or 128)
 constexpr int SLAB = 128;                 // bytes of K per smem row
-constexpr int TILE_BYTES = TM * SLAB;     // 16 KB: one 128-row operand slab
+constexpr int TILE_BYTES = TM * SLAB;     // 16 KB slot per operand slab (B uses TN rows of it)
 template <int FMT>
 struct Tc;
 template <>
@@ -51,7 +51,7 @@ struct Tc<MPPS_FMT_FP8> {
     static constexpr int kOps = 2, kStages = 4, kAB = 0;
 };
 
-template <int FMT>
+template <int FMT, int TN>
 __host__ __device__ constexpr uint32_t instr_desc() {
     // D format F32 (bit 4), A/B formats (bits 7-9, 10-12), K-major A and B, N>>3 at
     // bit 17, M>>4 at bit 24.
@@ -59,9 +59,9 @@ __host__ __device__ constexpr uint32_t instr_desc() {
            ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 }
 
-template <int FMT>
+template <int FMT, int TN>
 __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
-    constexpr uint32_t id = instr_desc<FMT>();
+    constexpr uint32_t id = instr_desc<FMT, TN>();
     if constexpr (FMT == MPPS_FMT_TF32) {
         asm volatile(
             "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
@@ -85,7 +85,7 @@ __host__ __device__ constexpr int smem_bytes() {
     return Tc<FMT>::kStages * Tc<FMT>::kOps * TILE_BYTES + 1024 + 256;
 }
 
-template <int FMT>
+template <int FMT, int TN>
 __global__ void __launch_bounds__(128, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2,
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(128, 1)
         for (int kb = 0; kb < nk; ++kb) {
             const int s = kb % STAGES;
             if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1, err)) break;
-            mbar_expect_tx(&full[s], STAGE_BYTES);
+            mbar_expect_tx(&full[s], (OPS / 2) * (TM + TN) * SLAB);
             uint8_t* st = smem + s * STAGE_BYTES;
             const int kc = kb * KSLAB;
             tma_load_3d(st, &tmA, kc, m0, b, &full[s]);
@@ -155,12 +155,12 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
                 const uint64_t ad = sw128_desc(a0 + kk * 32), bd = sw128_desc(b0 + kk * 32);
-                tc_mma<FMT>(tmem, ad, bd, (kb | kk) != 0 ? 1u : 0u);
+                tc_mma<FMT, TN>(tmem, ad, bd, (kb | kk) != 0 ? 1u : 0u);
                 if constexpr (OPS == 4) {
                     const uint64_t ad2 = sw128_desc(a0 + 2 * TILE_BYTES + kk * 32);
                     const uint64_t bd2 = sw128_desc(a0 + 3 * TILE_BYTES + kk * 32);
-                    tc_mma<FMT>(tmem, ad, bd2, 1u);   // hi * lo
-                    tc_mma<FMT>(tmem, ad2, bd, 1u);   // lo * hi
+                    tc_mma<FMT, TN>(tmem, ad, bd2, 1u);   // hi * lo
+                    tc_mma<FMT, TN>(tmem, ad2, bd, 1u);   // lo * hi
                 }
             }
             tc_commit(&empty[s]);
@@ -186,11 +186,20 @@ __global__ void __launch_bounds__(128, 1)
         __syncwarp();
         const int col = n0 + c0 + lane;
 #pragma unroll 1
-        for (int rr = 0; rr < 32; ++rr) {
-            const int row = m0 + warp * 32 + rr;
-            if (row < n && col < n)
-                epilogue_store(ep, b, row, col, n,
-                               epilogue_value(ep, b, row, col, n, (double)stile[rr * 33 + lane]));
+        for (int r4 = 0; r4 < 32; r4 += 4) {      // 4 rows per pass: their loads overlap
+            double val[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int row = m0 + warp * 32 + r4 + u;
+                val[u] = (row < n && col < n)
+                             ? epilogue_value(ep, b, row, col, n, (double)stile[(r4 + u) * 33 + lane])
+                             : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int row = m0 + warp * 32 + r4 + u;
+                if (row < n && col < n) epilogue_store(ep, b, row, col, n, val[u]);
+            }
         }
         __syncwarp();
     }
@@ -217,7 +226,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 // 3-D map over (K = n columns, n rows, batch) of a row-major low-precision copy with
 // leading dimension lld and batch stride bs (elements); box = one 128-byte slab x 128 rows.
-bool make_map(CUtensorMap* tm, int fmt, const void* ptr, int n, int batch, int lld, long long bs) {
+bool make_map(CUtensorMap* tm, int fmt, const void* ptr, int n, int batch, int lld, long long bs,
+              int box_rows) {
     auto fn = encode_fn();
     if (!fn) return false;
     const int es = low_elem_bytes(fmt);
@@ -226,7 +236,7 @@ bool make_map(CUtensorMap* tm, int fmt, const void* ptr, int n, int batch, int l
                                                    : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)batch};
     cuuint64_t strides[2] = {(cuuint64_t)lld * es, (cuuint64_t)bs * es};
-    cuuint32_t box[3] = {(cuuint32_t)(SLAB / es), (cuuint32_t)TM, 1};
+    cuuint32_t box[3] = {(cuuint32_t)(SLAB / es), (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = fn(tm, dt, 3, const_cast<void*>(ptr), dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -234,16 +244,16 @@ bool make_map(CUtensorMap* tm, int fmt, const void* ptr, int n, int batch, int l
     return r == CUDA_SUCCESS;
 }
 
-template <int FMT>
+template <int FMT, int TN>
 mpps_status launch_fmt(const void* A_hi, const void* A_lo, const void* Bt_hi, const void* Bt_lo,
                        long long a_bs, long long b_bs, int lld, int n, int batch, const Epilogue& ep,
                        int* d_err, cudaStream_t st) {
     CUtensorMap ta, tb, ta2, tb2;
-    bool ok = make_map(&ta, FMT, A_hi, n, batch, lld, a_bs) &&
-              make_map(&tb, FMT, Bt_hi, n, batch, lld, b_bs);
+    bool ok = make_map(&ta, FMT, A_hi, n, batch, lld, a_bs, TM) &&
+              make_map(&tb, FMT, Bt_hi, n, batch, lld, b_bs, TN);
     if (FMT == MPPS_FMT_BF16X3)
-        ok = ok && make_map(&ta2, FMT, A_lo, n, batch, lld, a_bs) &&
-             make_map(&tb2, FMT, Bt_lo, n, batch, lld, b_bs);
+        ok = ok && make_map(&ta2, FMT, A_lo, n, batch, lld, a_bs, TM) &&
+             make_map(&tb2, FMT, Bt_lo, n, batch, lld, b_bs, TN);
     else {
         ta2 = ta;
         tb2 = tb;
@@ -255,14 +265,14 @@ mpps_status launch_fmt(const void* A_hi, const void* A_lo, const void* Bt_hi, co
     constexpr int smem = smem_bytes<FMT>();
     static bool attr_set = false;
     if (!attr_set) {
-        MPPS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        MPPS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<FMT, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            smem));
         attr_set = true;
     }
     dim3 grid((n + TN - 1) / TN, (n + TM - 1) / TM, batch);
     ProfScope prof(MPPS_PROF_GEMM_TC, st,
                    2.0 * n * (double)n * n * batch * (FMT == MPPS_FMT_BF16X3 ? 3 : 1));
-    k_gemm_tc<FMT><<<grid, 128, smem, st>>>(ta, tb, ta2, tb2, n, ep, d_err);
+    k_gemm_tc<FMT, TN><<<grid, 128, smem, st>>>(ta, tb, ta2, tb2, n, ep, d_err);
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }
@@ -272,19 +282,22 @@ mpps_status launch_fmt(const void* A_hi, const void* A_lo, const void* Bt_hi, co
 mpps_status launch_gemm_tc(int fmt, const void* A_hi, const void* A_lo, const void* Bt_hi,
                            const void* Bt_lo, long long a_bs, long long b_bs, int lld, int n,
                            int batch, const Epilogue& ep, int* d_err, cudaStream_t st) {
+    // 128 x 64 tiles when 128 x 128 ones would not give every SM two CTAs: the epilogue (FP64
+    // block sums) then spreads over twice as many SMs
+    const long long tiles128 = (long long)((n + 127) / 128) * ((n + 127) / 128) * batch;
+    const bool narrow = tiles128 < 2 * 148;
+#define MPPS_TC_CASE(F)                                                                         \
+    case F:                                                                                     \
+        return narrow ? launch_fmt<F, 64>(A_hi, A_lo, Bt_hi, Bt_lo, a_bs, b_bs, lld, n, batch, ep, \
+                                          d_err, st)                                            \
+                      : launch_fmt<F, 128>(A_hi, A_lo, Bt_hi, Bt_lo, a_bs, b_bs, lld, n, batch, ep, \
+                                           d_err, st);
     switch (fmt) {
-        case MPPS_FMT_BF16:
-            return launch_fmt<MPPS_FMT_BF16>(A_hi, A_lo, Bt_hi, Bt_lo, a_bs, b_bs, lld, n, batch, ep,
-                                             d_err, st);
-        case MPPS_FMT_BF16X3:
-            return launch_fmt<MPPS_FMT_BF16X3>(A_hi, A_lo, Bt_hi, Bt_lo, a_bs, b_bs, lld, n, batch,
-                                               ep, d_err, st);
-        case MPPS_FMT_TF32:
-            return launch_fmt<MPPS_FMT_TF32>(A_hi, A_lo, Bt_hi, Bt_lo, a_bs, b_bs, lld, n, batch, ep,
-                                             d_err, st);
-        case MPPS_FMT_FP8:
-            return launch_fmt<MPPS_FMT_FP8>(A_hi, A_lo, Bt_hi, Bt_lo, a_bs, b_bs, lld, n, batch, ep,
-                                            d_err, st);
+        MPPS_TC_CASE(MPPS_FMT_BF16)
+        MPPS_TC_CASE(MPPS_FMT_BF16X3)
+        MPPS_TC_CASE(MPPS_FMT_TF32)
+        MPPS_TC_CASE(MPPS_FMT_FP8)
+#undef MPPS_TC_CASE
         default:
             set_error("launch_gemm_tc: unsupported format %d", fmt);
             return MPPS_EINVAL;

@@ -368,3 +368,79 @@ def test_bounded_wait_reports_timeout_and_context_survives(mpps):
     P = host(mpps.ps_eval(mpps.taylor_exp_coeffs(12), dev(A), policy=mpps.NS_E))
     ph, pl, _ = oracle.ps_dd(oracle.taylor_exp_rational(12), A)
     assert oracle.rel_err_1norm(P, ph, pl) <= 50 * 32 * U
+
+
+def test_sigma_matches_oracle_at_power_of_two_norms(mpps):
+    """||A||_1 rescaled to exactly 4 or 32 (no margin): the squaring count the GPU picks must
+    equal the oracle's sequential-sum rule even when rounding puts the norm a hair above."""
+    n = 200
+    for seed in range(6):
+        A = np.random.default_rng(seed).standard_normal((n, n))
+        for target in (4.0, 32.0):
+            B = A * (target / np.abs(A).sum(axis=0).max())
+            _, rep = mpps.expm(dev(B), policy=mpps.NS_E, report=True)
+            assert rep[0]["sigma"] == oracle.sigma_for(B), (seed, target)
+
+
+@pytest.mark.parametrize("n,m", [(16, 8), (33, 18), (64, 13)])
+def test_adjoint_emulated_vs_oracle(mpps, n, m):
+    rng = np.random.default_rng(n * 7 + m)
+    A = rng.standard_normal((n, n)) / np.sqrt(n)
+    G = rng.standard_normal((n, n))
+    gh, gl = oracle.adjoint_dd(oracle.taylor_exp_rational(m), A, G)
+    g = host(mpps.ps_eval_adjoint(mpps.taylor_exp_coeffs(m), dev(A), dev(G), policy=mpps.FIXED_E))
+    assert oracle.norm1(g - gh - gl) / oracle.norm1(gh) <= 100 * n * U
+
+
+def test_adjoint_fp32_batch_config_shape(mpps):
+    """Batch of FP32-stored 128 x 128 matrices, N(0,1)/sqrt(n) entries, Taylor exp m = 18,
+    through the autograd Function with emulated products: the gradient agrees with the
+    oracle (rel. err <= 1e-5) and with the block-triangular Frechet identity
+    <grad, E> = <G, L_p(A, E)>, L_p(A, E) = p([[A, E], [0, A]])_12, evaluated on the GPU."""
+    n, m, batch = 128, 18, 4
+    rng = np.random.default_rng(4)
+    A32 = torch.tensor(rng.standard_normal((batch, n, n)) / np.sqrt(n), dtype=torch.float32,
+                       device="cuda:0", requires_grad=True)
+    coef = mpps.taylor_exp_coeffs(m)
+    P = mpps.poly(A32, coef, mpps.NS_E)
+    assert P.dtype == torch.float32
+    G = torch.randn_like(P)
+    (P * G).sum().backward()
+    grad = A32.grad.double().cpu().numpy()
+    A64 = A32.detach().double().cpu().numpy()
+    G64 = G.double().cpu().numpy()
+    for b in range(2):
+        gh, gl = oracle.adjoint_dd(oracle.taylor_exp_rational(m), A64[b], G64[b])
+        ref = gh + gl
+        assert oracle.norm1(grad[b] - ref) / oracle.norm1(ref) <= 1e-5
+    E = rng.standard_normal((n, n))
+    M = np.zeros((2 * n, 2 * n)); M[:n, :n] = A64[0]; M[n:, n:] = A64[0]; M[:n, n:] = E
+    L = host(mpps.ps_eval(coef, dev(M), policy=mpps.FIXED_E))[:n, n:]
+    lhs = float(np.sum(grad[0] * E)); rhs = float(np.sum(G64[0] * L))
+    assert abs(lhs - rhs) <= 1e-6 * abs(rhs)
+
+
+# ------------------------------------------------------------------------------------
+# uneven batches (bucketed, zero-padded, one batched evaluation per bucket)
+# ------------------------------------------------------------------------------------
+def test_expm_grouped_uneven_vs_oracle(mpps):
+    rng = np.random.default_rng(31)
+    ns = [1, 5, 31, 32, 33, 47, 70, 64, 130, 8, 100, 33]
+    ms = [12, 18, 24, 12, 18, 24, 12, 18, 24, 30, 18, 12]
+    norms = np.exp(rng.uniform(np.log(0.1), np.log(10.0), size=len(ns)))
+    mats = []
+    for k, n in enumerate(ns):
+        A = rng.standard_normal((n, n))
+        A *= norms[k] / np.abs(A).sum(axis=0).max()
+        mats.append(A)
+    for pol in (mpps.NS_E, mpps.FIXED):
+        outs, reps = mpps.expm_grouped([dev(A) for A in mats], ms, policy=pol, report=True)
+        for A, m, E, R in zip(mats, ms, outs, reps):
+            n = A.shape[0]
+            sg = oracle.sigma_for(A)
+            assert R["sigma"] == sg
+            eh, el = oracle.expm_ss_dd(A, m, sg)
+            err = oracle.rel_err_1norm(host(E), eh, el)
+            # Taylor truncation at degree m on ||X||_1 <= 1 is below 1/(m+1)! * e
+            trunc = np.e / float(oracle.math.factorial(m + 1)) * 2 ** sg
+            assert err <= 50 * n * U * max(1, 2 ** sg) + trunc, (n, m, err)
