@@ -9,58 +9,73 @@
 //
 //   A (rows scaled by 2^-eA_i, |.| < 1) = sum_{t<k} 2^{-6(t+1)} a_t,  a_t integers, |a_t| <= 64
 //   B (cols scaled by 2^-eB_j)          = sum_{q<k} 2^{-6(q+1)} b_q
-//   A B ~= 2^{eA_i + eB_j} sum_{d<k} 2^{-6(d+2)} D_d,   D_d = sum_{t+q=d} a_t b_q^T.
+//   A B ~= 2^{eA_i + eB_j - 12} sum_{d<k} 2^{-6d} D_d,   D_d = sum_{t+q=d} a_t b_q^T.
 //
-// Every a_t, b_q entry is an integer of at most 7 bits, exact in bf16; every product is exact
-// in FP32 and, for K <= 1024, every diagonal sum D_d is an integer below
-// 1024 * 2^10 * (d + 3) <= 2^24 (d <= 13), so the tensor cores accumulate it EXACTLY in FP32.
-// Longer K is cut into 1024-chunks whose D_d are drained into FP64 between chunks.  The
-// result differs from the exact product only by the slices dropped (t + q >= k) and the
-// residual of the k-slice representation, about 2^{-6k} relative to the row and column
+// The slice planes hold a'_t = 2^-6t a_t and b'_q = 2^-6q b_q (exact in bf16), so that the
+// product a'_t b'_q^T is already 2^-6d a_t b_q^T and sums of pairs with different d carry the
+// right weights.  Every D_d entry of one K chunk of at most 2048 is an integer of magnitude
+// <= 2048 (d+3) 2^10 <= 2^24 for d <= 5 (|a_0|,|b_0| <= 64, the others <= 32), so the tensor
+// cores accumulate D_0..D_5 EXACTLY in FP32, each in its own TMEM region.  The diagonals
+// d >= 6 (weights <= 2^-36 relative to D_0) share one seventh region and are accumulated in
+// FP32 with rounding; their worst-case error is 2^10 below the worst-case bound of an FP64
+// product of the same length.  The only other errors are the pairs dropped (t + q >= k) and
+// the residual of the k-slice representation, about 2^{-6k} relative to the row and column
 // maxima: k = 9 gives FP64-level accuracy.
 //
-// Kernel: one CTA per 128 x 32 output tile, 6 warps (0-3 epilogue = TMEM lanes, 4 TMA
-// producer, 5 MMA issuer).  Per K-block of 32 the producer loads the k slices of the A tile
-// (128 x 32 bf16 each) and the k slices of the B^T tile (32 x 32 each), stacked so that the
-// B operand of slice t is B_0..B_{k-1-t} (N = 32 (k - t) rows): one MMA per t and K=16 step
-// writes its k - t partial products into the TMEM columns 32 (t + q), i.e. straight into
-// the accumulator of diagonal d = t + q.  Operands are K-major with the 64-byte swizzle; the
-// ring holds up to 8 stages (2 for k = 9; a 16-wide K with the 32-byte swizzle and 4 stages
-// measured slower).  All mbarrier waits are bounded.
+// Between K chunks and at the end of a tile the exact regions are drained on the integer
+// pipe (W = sum_{d<=5} 2^{6(5-d)} D_d as a 64-bit integer, the tail as FP32), so the scarce
+// FP64 pipe only does the last combination 2^{e-42} W + 2^{e-12} T and the fused epilogue.
+//
+// Kernel: persistent, one CTA per SM, 128 x 64 output tiles, 10 warps (0-7 epilogue: TMEM
+// lane quarter = warp % 4, column half = warp / 4; 8 TMA producer; 9 MMA issuer).  Per K
+// block of 32 the producer loads the k slices of the B^T tile (one 3-D box) and the k slices
+// of the A tile (one box and one mbarrier each, so the MMAs of slice t start when slice t
+// lands).  The MMA of slice t uses the stacked B operand b'_0..b'_{6-t} (N = 64 (7 - t)) and
+// writes regions t..6 in one instruction (two when N > 256); the pairs with t + q >= 7 add
+// into the tail region with N = 64 MMAs.  Operands are K-major with the 64-byte swizzle.
+// The epilogue drains TMEM into registers and releases it at once, so the FP64 epilogue of
+// a tile overlaps the MMAs of the next.  All mbarrier waits are bounded.
 #include "common.cuh"
 #include "tcgen05.cuh"
 
 #include <cudaTypedefs.h>
 
-#include <map>
 #include <mutex>
 
 namespace mpps {
-
-int f64e_cluster_choice(int dev, int n, int k, int batch);
 
 namespace {
 
 using namespace tc;
 
-constexpr int OM = 128;                 // output rows per CTA
-constexpr int ON = 32;                  // output cols per CTA (= columns per diagonal region)
+constexpr int OM = 128;                 // output rows per tile (TMEM lanes)
+constexpr int ON = 64;                  // output cols per tile (= columns per TMEM region)
 constexpr int KB = 32;                  // K elements per stage (64 bytes of bf16: two MMA steps)
-constexpr int KCHUNK = 1024;            // exact FP32 accumulation bound (see above)
+constexpr int KCHUNK = 2048;            // exact FP32 accumulation bound of D_0..D_5 (see above)
+constexpr int NEXACT = 6;               // diagonals accumulated exactly
+constexpr int NREG = 8;                 // TMEM regions: D_0..D_5, d = 6, and d >= 7
 constexpr int A_TILE = OM * KB * 2;     // 8 KB
-constexpr int B_TILE = ON * KB * 2;     // 2 KB
-constexpr int SMEM_BUDGET = 200 * 1024;
+constexpr int B_TILE = ON * KB * 2;     // 4 KB
+constexpr int EPI_WARPS = 8;
+constexpr int THREADS = (EPI_WARPS + 2) * 32;
 constexpr int MAX_STAGES = 8;
-// barriers after the ring: full + empty per stage, chunk_done, tmem_free, TMEM slot
-static_assert((2 * MAX_STAGES + 2) * 8 + 4 <= 256, "barrier block exceeds its reserved 256 bytes");
+constexpr int NFULL = MAX_STAGES * (MPPS_F64E_MAX_SLICES + 1);
+constexpr int BAR_BYTES = 1024;
+constexpr int SMEM_MAX = 232448;        // 227 KB of opt-in dynamic shared memory
+constexpr int SMEM_BUDGET = SMEM_MAX - 1024 - BAR_BYTES;
+constexpr int RASTER_G = 8;             // row blocks per raster group (L2 reuse of B)
+// barrier block after the ring: full[MAX_STAGES][k+1] | empty[MAX_STAGES] | chunk_done |
+// tmem_free | mma_done | TMEM address slot
+static_assert((NFULL + MAX_STAGES + 3) * 8 + 4 <= BAR_BYTES, "barrier block exceeds its bytes");
+static_assert(NREG * ON <= 512, "TMEM regions exceed 512 columns");
 
-__host__ __device__ inline int stage_bytes(int k) { return k * (A_TILE + B_TILE); }
-__host__ __device__ inline int num_stages(int k) {
+__host__ __device__ constexpr int stage_bytes(int k) { return k * (A_TILE + B_TILE); }
+__host__ __device__ constexpr int num_stages(int k) {
     int s = SMEM_BUDGET / stage_bytes(k);
     return s > MAX_STAGES ? MAX_STAGES : s;
 }
-__host__ __device__ inline uint32_t tmem_cols(int k) {
-    uint32_t need = (uint32_t)(ON * k), c = 32;
+__host__ __device__ constexpr uint32_t tmem_cols(int nreg) {
+    uint32_t need = (uint32_t)(ON * nreg), c = 32;
     while (c < need) c <<= 1;
     return c;
 }
@@ -68,8 +83,9 @@ __host__ __device__ inline uint32_t tmem_cols(int k) {
 // Signed base-64 digits of x / 2^e (|x| < 2^e), computed in integers:
 //   F = round(x 2^(62-e)) (|F| < 2^62);  for t: p = 56 - 6t, v_t = floor((F + 2^(p-1)) / 2^p),
 //   F -= v_t 2^p.  |v_0| <= 64, |v_t| <= 32 (t >= 1); after k digits |F| <= 2^(55-6(k-1)), i.e.
-//   x = 2^e (sum_t v_t 2^(-6(t+1)) + r) with |r| <= 2^(-6k-1).  Only one FP64 multiply and one
-//   conversion per value: the digit loop runs on the integer pipe.
+//   x = 2^e (sum_t v_t 2^(-6(t+1)) + r) with |r| <= 2^(-6k-1).  Plane t stores v_t 2^-6t
+//   (exact in bf16).  Only one FP64 multiply and one conversion per value: the digit loop
+//   runs on the integer pipe.
 __device__ __forceinline__ void put_digits(double x, double scale, int k, __nv_bfloat16* dst,
                                            long long pstride) {
     long long F = __double2ll_rn(x * scale);
@@ -78,7 +94,8 @@ __device__ __forceinline__ void put_digits(double x, double scale, int k, __nv_b
         const int p = 56 - 6 * t;
         const long long v = (F + (1LL << (p - 1))) >> p;
         F -= v << p;
-        dst[(long long)t * pstride] = __int2bfloat16_rn((int)v);
+        dst[(long long)t * pstride] =
+            __float2bfloat16_rn((float)(int)v * __int_as_float((127 - 6 * t) << 23));
     }
 }
 
@@ -175,153 +192,247 @@ __global__ void k_slice_cols(const double* __restrict__ M, long long bs, int n, 
     }
 }
 
-// CL > 1: the CTA is one of CL neighbours along the output columns (a cluster) sharing the
-// same row block; each loads the A slices t = rank (mod CL) and multicasts them to all CL,
-// and every CTA's MMA completion is signalled to all CL (a stage is reloaded only when all
-// of them have consumed it).
-template <int CL>
-__global__ void __launch_bounds__(192, 1)
+// Bounded wait that ignores the error word (lets copies and MMAs in flight finish before
+// the CTA exits, also after another thread gave up).  False when the limit passed.
+__device__ __forceinline__ bool mbar_wait_quiet(uint64_t* bar, uint32_t parity) {
+    const uint32_t addr = smem_u32(bar);
+    unsigned long long t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if ((it & 63) == 0) {
+            const unsigned long long now = globaltimer();
+            if (t0 == 0) t0 = now;
+            else if (now - t0 > kWaitNs / 2) return false;
+        }
+    }
+}
+
+// 2^e as a double for -1022 <= e <= 1023 (built from the exponent field).
+__device__ __forceinline__ double pow2i(int e) {
+    return __longlong_as_double((long long)(e + 1023) << 52);
+}
+
+// Tile `id` -> (matrix slot z, first row, first column); row blocks are walked in groups of
+// RASTER_G with the column index outermost inside a group, so that the CTAs working at the
+// same time share few B column blocks and few A row blocks.
+struct TileMap {
+    int tcols, trows, per_mat;
+    __device__ void decode(int id, int& z, int& m0, int& n0) const {
+        z = id / per_mat;
+        const int rem = id - z * per_mat;
+        const int span = RASTER_G * tcols;
+        const int grp = rem / span, first = grp * RASTER_G;
+        const int gsz = min(RASTER_G, trows - first);
+        const int in = rem - grp * span;
+        m0 = (first + in % gsz) * OM;
+        n0 = (in / gsz) * ON;
+    }
+};
+
+template <int K>
+__global__ void __launch_bounds__(THREADS, 1)
     k_gemm_f64e(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                int n, int k, int ksA, int ksB, const int* __restrict__ eA,
+                int n, int ksA, int ksB, int batch, const int* __restrict__ eA,
                 const int* __restrict__ eB, Epilogue ep, int* err, const int* __restrict__ bidx) {
-    const int S = num_stages(k);
-    const int SB = stage_bytes(k);
-    const uint32_t TCOLS = tmem_cols(k);
+    constexpr int S = num_stages(K);
+    constexpr int SB = stage_bytes(K);
+    constexpr int NR = K < NREG ? K : NREG;          // TMEM regions in use
+    constexpr int NX = K < NEXACT ? K : NEXACT;      // of which exact
+    constexpr uint32_t TCOLS = tmem_cols(NR);
+    static_assert(S >= 1, "a stage does not fit in shared memory");
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    // barrier block after the stage ring: full[MAX_STAGES] | empty[MAX_STAGES] | chunk_done |
-    // tmem_free | TMEM address slot  (148 bytes of the 256 reserved)
-    uint64_t* full = (uint64_t*)(smem + S * SB);
-    uint64_t* empty = full + MAX_STAGES;
+    uint64_t* full = (uint64_t*)(smem + S * SB);     // [stage][0: B slices, 1 + t: A slice t]
+    uint64_t* empty = full + NFULL;
     uint64_t* chunk_done = empty + MAX_STAGES;
     uint64_t* tmem_free = chunk_done + 1;
-    uint32_t* tmem_slot = (uint32_t*)(tmem_free + 1);
+    uint64_t* mma_done = tmem_free + 1;
+    uint32_t* tmem_slot = (uint32_t*)(mma_done + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int b = bidx ? bidx[blockIdx.z] : blockIdx.z;
-    const int m0 = blockIdx.y * OM, n0 = blockIdx.x * ON;
-    const int nkb = (n + KB - 1) / KB;                      // K-blocks
-    const int kb_per_chunk = KCHUNK / KB;
+    TileMap tm;
+    tm.tcols = (n + ON - 1) / ON;
+    tm.trows = (n + OM - 1) / OM;
+    tm.per_mat = tm.tcols * tm.trows;
+    const int total = tm.per_mat * batch;
+    const int nkb = (n + KB - 1) / KB;
+    constexpr int kb_per_chunk = KCHUNK / KB;
     const int nchunks = (nkb + kb_per_chunk - 1) / kb_per_chunk;
 
-    const uint32_t crank = CL > 1 ? cluster_ctarank() : 0;
-    constexpr uint16_t kMask = (uint16_t)((1u << CL) - 1u);
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], CL);
+            for (int i = 0; i <= K; ++i) mbar_init(&full[s * (K + 1) + i], 1);
+            mbar_init(&empty[s], 1);
         }
         mbar_init(chunk_done, 1);
-        mbar_init(tmem_free, 128);
+        mbar_init(tmem_free, EPI_WARPS * 32);
+        mbar_init(mma_done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
     }
     if (warp == 0) tmem_alloc(tmem_slot, TCOLS);
     tc_fence_before();
     __syncthreads();
-    if constexpr (CL > 1) cluster_sync();   // peers' barriers exist before any multicast
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp == 4) {
-        if (lane == 0) {   // TMA producer: k A slices + k B slices per K-block
-            for (int kb = 0; kb < nkb; ++kb) {
-                const int s = kb % S;
-                if (kb >= S && !mbar_wait(&empty[s], ((kb / S) - 1) & 1, err)) break;
-                mbar_expect_tx(&full[s], (uint32_t)SB);
-                uint8_t* st = smem + s * SB;
-                const int kc = kb * KB;
-                for (int t = 0; t < k; ++t) {
-                    if constexpr (CL > 1) {
-                        if (t % CL == (int)crank)
-                            tma_load_3d_mc(st + t * A_TILE, &tmA, kc, m0, b * ksA + t, &full[s], kMask);
-                    } else {
-                        tma_load_3d(st + t * A_TILE, &tmA, kc, m0, b * ksA + t, &full[s]);
-                    }
-                    tma_load_3d(st + k * A_TILE + t * B_TILE, &tmB, kc, n0, b * ksB + t, &full[s]);
-                }
-            }
-        }
-    } else if (warp == 5) {
-        if (lane == 0) {   // MMA issuer
+    if (warp == EPI_WARPS) {
+        if (lane == 0) {   // TMA producer
+            uint32_t g = 0;                                   // K blocks issued so far
+            int s = 0;                                        // stage of K block g
+            uint32_t ph = 0;                                  // its fill parity
             bool ok = true;
-            for (int kb = 0; kb < nkb && ok; ++kb) {
-                const int s = kb % S;
-                const int c = kb / kb_per_chunk, kin = kb % kb_per_chunk;
-                if (kin == 0 && c > 0) {   // the epilogue must have drained the previous chunk
-                    ok = mbar_wait(tmem_free, (c - 1) & 1, err);
-                    if (!ok) break;
-                    tc_fence_after();
-                }
-                ok = mbar_wait(&full[s], (kb / S) & 1, err);
-                if (!ok) break;
-                tc_fence_after();
-                const uint32_t abase = smem_u32(smem + s * SB);
-                const uint32_t bbase = abase + k * A_TILE;
+            for (int id = blockIdx.x; id < total && ok; id += gridDim.x) {
+                int z, m0, n0;
+                tm.decode(id, z, m0, n0);
+                const int b = bidx ? bidx[z] : z;
+                for (int kb = 0; kb < nkb; ++kb, ++g) {
+                    if (g >= (uint32_t)S && !(ok = mbar_wait(&empty[s], ph ^ 1, err))) break;
+                    uint8_t* st = smem + s * SB;
+                    uint64_t* f = full + s * (K + 1);
+                    const int kc = kb * KB;
+                    mbar_expect_tx(&f[0], (uint32_t)(K * B_TILE));
+                    tma_load_3d(st + K * A_TILE, &tmB, kc, n0, b * ksB, &f[0]);
 #pragma unroll
-                for (int kk = 0; kk < 2; ++kk) {        // two K=16 steps per 64-byte row
-                    for (int t = 0; t < k; ++t) {
-                        const int N = ON * (k - t);
-                        const uint32_t acc = (kin == 0 && kk == 0 && t == 0) ? 0u : 1u;
-                        const uint64_t ad = sw64_desc(abase + t * A_TILE + kk * 32);
-                        const int n1 = N > 256 ? 256 : N;
-                        mma_bf16(tmem + (uint32_t)(ON * t), ad, sw64_desc(bbase + kk * 32),
-                                 make_idesc(1, OM, n1), acc);
-                        if (N > 256)   // rows 256.. of the stacked B: 32 atoms of 512 B further
-                            mma_bf16(tmem + (uint32_t)(ON * t + 256), ad,
-                                     sw64_desc(bbase + 256 / 8 * 512 + kk * 32),
-                                     make_idesc(1, OM, N - 256), acc);
+                    for (int t = 0; t < K; ++t) {
+                        mbar_expect_tx(&f[1 + t], (uint32_t)A_TILE);
+                        tma_load_3d(st + t * A_TILE, &tmA, kc, m0, b * ksA + t, &f[1 + t]);
                     }
+                    if (++s == S) { s = 0; ph ^= 1; }
                 }
-                if constexpr (CL > 1) tc_commit_mc(&empty[s], kMask);
-                else tc_commit(&empty[s]);
-                if (kin == kb_per_chunk - 1 || kb == nkb - 1) tc_commit(chunk_done);
             }
-            if (!ok) tc_commit(chunk_done);
+            // the copies of the last stages land before the CTA may exit (returns at once
+            // unless this loop or the MMA issuer gave up early)
+            const uint32_t lo = g > (uint32_t)S ? g - (uint32_t)S : 0u;
+            bool landed = true;
+            for (uint32_t gg = lo; gg < g && landed; ++gg) {
+                const int s = (int)(gg % (uint32_t)S);
+                for (int i = 0; i <= K && landed; ++i)
+                    landed = mbar_wait_quiet(&full[s * (K + 1) + i], (gg / S) & 1);
+            }
+            if (!landed) atomicExch(err, 1);
+        }
+    } else if (warp == EPI_WARPS + 1) {
+        if (lane == 0) {   // MMA issuer: every offset below is a compile-time constant
+            uint32_t gc = 0;                                  // chunks consumed
+            int s = 0;
+            uint32_t ph = 0;
+            bool ok = true;
+            const uint32_t ring = smem_u32(smem);
+            for (int id = blockIdx.x; id < total && ok; id += gridDim.x) {
+                for (int kb = 0; kb < nkb && ok; ++kb) {
+                    const int kin = kb % kb_per_chunk;
+                    if (kin == 0 && gc > 0) {   // the epilogue must have drained the last chunk
+                        if (!(ok = mbar_wait(tmem_free, (gc - 1) & 1, err))) break;
+                        tc_fence_after();
+                    }
+                    uint64_t* f = full + s * (K + 1);
+                    if (!(ok = mbar_wait(&f[0], ph, err))) break;
+                    const uint32_t abase = ring + (uint32_t)(s * SB);
+                    const uint64_t da = sw64_desc(abase), db = sw64_desc(abase + K * A_TILE);
+                    const uint32_t acc0 = kin == 0 ? 0u : 1u;
+#pragma unroll
+                    for (int t = 0; t < K; ++t) {
+                        if (!(ok = mbar_wait(&f[1 + t], ph, err))) break;
+                        tc_fence_after();
+#pragma unroll
+                        for (int kk = 0; kk < 2; ++kk) {        // two K=16 steps per 64-byte row
+                            const uint64_t ad = da + (uint64_t)((t * A_TILE + kk * 32) >> 4);
+                            if (t < NR) {   // stacked b'_0..b'_{NR-1-t} -> regions t..NR-1
+                                const int N = ON * (NR - t);
+                                const uint32_t acc = (t == 0 && kk == 0) ? acc0 : 1u;
+                                mma_bf16(tmem + (uint32_t)(ON * t), ad, db + (uint64_t)((kk * 32) >> 4),
+                                         make_idesc(1, OM, N > 256 ? 256 : N), acc);
+                                if (N > 256)   // B rows 256..: 32 atoms of 512 B further
+                                    mma_bf16(tmem + (uint32_t)(ON * t + 256), ad,
+                                             db + (uint64_t)((256 * 64 + kk * 32) >> 4),
+                                             make_idesc(1, OM, N - 256), acc);
+                            }
+#pragma unroll
+                            for (int q = (NREG - t > 0 ? NREG - t : 0); q <= K - 1 - t; ++q)
+                                mma_bf16(tmem + (uint32_t)(ON * (NREG - 1)), ad,
+                                         db + (uint64_t)((q * B_TILE + kk * 32) >> 4),
+                                         make_idesc(1, OM, ON), 1u);
+                        }
+                    }
+                    if (!ok) break;
+                    tc_commit(&empty[s]);
+                    if (kin == kb_per_chunk - 1 || kb == nkb - 1) {
+                        tc_commit(chunk_done);
+                        ++gc;
+                    }
+                    if (++s == S) { s = 0; ph ^= 1; }
+                }
+            }
+            // every MMA issued by this thread completes before TMEM is released
+            tc_commit(mma_done);
+            if (!mbar_wait_quiet(mma_done, 0)) atomicExch(err, 1);
         }
     } else {
-        // epilogue warps 0-3: row = m0 + 32 w + lane; 32 output columns each
-        const int row = m0 + warp * 32 + lane;
-        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-        double sum[ON];
+        // epilogue warps 0-7: row = m0 + 32 (warp % 4) + lane, columns n0 + 32 (warp / 4) + j
+        const int q4 = warp & 3, h = warp >> 2;
+        const uint32_t lane_base = (uint32_t)(q4 * 32) << 16;
+        uint32_t gc = 0;
+        for (int id = blockIdx.x; id < total; id += gridDim.x) {
+            int z, m0, n0;
+            tm.decode(id, z, m0, n0);
+            const int b = bidx ? bidx[z] : z;
+            long long W[32];
+            float T[32];
 #pragma unroll
-        for (int j = 0; j < ON; ++j) sum[j] = 0.0;
-        for (int c = 0; c < nchunks; ++c) {
-            mbar_wait(chunk_done, c & 1, err);
-            tc_fence_after();
-            for (int d = 0; d < k; ++d) {
-                uint32_t v[32];
-                tmem_ld32(tmem + lane_base + (uint32_t)(ON * d), v);
-                const double sc = ldexp(1.0, -6 * (d + 2));
+            for (int j = 0; j < 32; ++j) { W[j] = 0; T[j] = 0.f; }
+            bool ok = true;
+            for (int c = 0; c < nchunks; ++c, ++gc) {
+                ok = __all_sync(0xffffffffu, mbar_wait(chunk_done, gc & 1, err));
+                if (!ok) break;
+                tc_fence_after();
 #pragma unroll
-                for (int j = 0; j < ON; ++j) sum[j] = fma((double)__uint_as_float(v[j]), sc, sum[j]);
+                for (int d = 0; d < NX; ++d) {   // exact regions: W += 2^{6(5-d)} D_d
+                    uint32_t v[32];
+                    tmem_ld32(tmem + lane_base + (uint32_t)(ON * d + 32 * h), v);
+                    const float up = __int_as_float((127 + 6 * d) << 23);   // 2^{6d}
+                    const int mul = 1 << (6 * (NEXACT - 1 - d));
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        W[j] += (long long)__float2int_rn(__uint_as_float(v[j]) * up) * mul;
+                }
+#pragma unroll
+                for (int d = NX; d < NR; ++d) {  // tail regions (FP32)
+                    uint32_t v[32];
+                    tmem_ld32(tmem + lane_base + (uint32_t)(ON * d + 32 * h), v);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) T[j] += __uint_as_float(v[j]);
+                }
+                tc_fence_before();
+                mbar_arrive_cta(tmem_free);
             }
-            tc_fence_before();
-            mbar_arrive_cta(tmem_free);
-        }
-        // rows -> a 32 x 33 shared tile per warp (the ring is idle now), then one column per
-        // lane: coalesced reads of the power table and coalesced stores
-        double* stile = (double*)smem + warp * 32 * 33;
-        const int er = row < n ? eA[(long long)b * n + row] : 0;
+            if (!ok) break;
+            // product = 2^{eA+eB-42} W + 2^{eA+eB-12} T, then the fused epilogue
+            const int row = m0 + q4 * 32 + lane;
+            if (row < n) {
+                const int er = eA[(long long)b * n + row];
+                const int cb = n0 + 32 * h;
 #pragma unroll
-        for (int j = 0; j < ON; ++j) stile[lane * 33 + j] = ldexp(sum[j], er);
-        __syncwarp();
-        const int col = n0 + lane;
-        const int ec = col < n ? eB[(long long)b * n + col] : 0;
-#pragma unroll 1
-        for (int r4 = 0; r4 < 32; r4 += 4) {      // 4 rows per pass: their loads overlap
-            double val[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int r = m0 + warp * 32 + r4 + u;
-                val[u] = (r < n && col < n)
-                             ? epilogue_value(ep, b, r, col, n, ldexp(stile[(r4 + u) * 33 + lane], ec))
-                             : 0.0;
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int r = m0 + warp * 32 + r4 + u;
-                if (r < n && col < n) epilogue_store(ep, b, r, col, n, val[u]);
+                for (int j = 0; j < 32; ++j) {
+                    const int col = cb + j;
+                    if (col < n) {
+                        const int e = er + __ldg(eB + (long long)b * n + col);
+                        const double wd = (double)W[j], td = (double)T[j];
+                        const double val = (e - 42 >= -1022 && e - 12 <= 1023)
+                                               ? fma(wd, pow2i(e - 42), td * pow2i(e - 12))
+                                               : ldexp(fma(wd, 0x1p-30, td), e - 12);
+                        epilogue_store(ep, b, row, col, n, epilogue_value(ep, b, row, col, n, val));
+                    }
+                }
             }
         }
     }
@@ -329,8 +440,6 @@ __global__ void __launch_bounds__(192, 1)
     tc_fence_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, TCOLS);
-    // no CTA leaves while a peer may still signal its barriers or multicast into it
-    if constexpr (CL > 1) cluster_sync();
 }
 
 // ---- host -----------------------------------------------------------------------------
@@ -348,128 +457,50 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// planes: [batch * k][n][lld] bf16 -> 3-D map (K = n, rows = n, planes), box 32 x rows x 1
-bool make_plane_map(CUtensorMap* tm, const void* ptr, int n, int nplanes, int lld, int box_rows) {
+// planes: [nplanes][n][lld] bf16 -> 3-D map (K = n, rows = n, planes), box 32 x rows x planes
+bool make_plane_map(CUtensorMap* tm, const void* ptr, int n, int nplanes, int lld, int box_rows,
+                    int box_planes) {
     auto fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)nplanes};
     cuuint64_t strides[2] = {(cuuint64_t)lld * 2, (cuuint64_t)n * lld * 2};
-    cuuint32_t box[3] = {(cuuint32_t)KB, (cuuint32_t)box_rows, 1};
+    cuuint32_t box[3] = {(cuuint32_t)KB, (cuuint32_t)box_rows, (cuuint32_t)box_planes};
     cuuint32_t estr[3] = {1, 1, 1};
     return fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(ptr), dims, strides, box,
               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// Launch with a cluster of `cl` CTAs along the output columns (grid x rounded up to it).
-mpps_status launch_f64e_cl(int cl, const CUtensorMap& ta, const CUtensorMap& tb, int n, int k,
-                           int ksA, int ksB, const int* eA, const int* eB, int batch,
-                           const Epilogue& ep, int* d_err, cudaStream_t st, const int* bidx,
-                           int smem) {
-    const int gx = (n + ON - 1) / ON;
-    dim3 grid((gx + cl - 1) / cl * cl, (n + OM - 1) / OM, batch);
-    if (cl == 1) {
-        k_gemm_f64e<1><<<grid, 192, smem, st>>>(ta, tb, n, k, ksA, ksB, eA, eB, ep, d_err, bidx);
-        MPPS_LAUNCH_CHECK();
-        return MPPS_OK;
+int sm_count(int dev) {
+    static int cache[64] = {0};
+    if (dev < 0 || dev >= 64) return 148;
+    if (!cache[dev]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
+            v = 148;
+        cache[dev] = v;
     }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = dim3(192, 1, 1);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = cl;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaError_t e = (cl == 2)
-        ? cudaLaunchKernelEx(&cfg, k_gemm_f64e<2>, ta, tb, n, k, ksA, ksB, eA, eB, ep, d_err, bidx)
-        : cudaLaunchKernelEx(&cfg, k_gemm_f64e<4>, ta, tb, n, k, ksA, ksB, eA, eB, ep, d_err, bidx);
-    if (e != cudaSuccess) {
-        set_error("cluster launch of the emulated FP64 product failed: %s", cudaGetErrorString(e));
-        return MPPS_ECUDA;
+    return cache[dev];
+}
+
+template <int K>
+mpps_status launch_k(int dev, int grid, const CUtensorMap& ta, const CUtensorMap& tb, int n,
+                     int ksA, int ksB, int batch, const int* eA, const int* eB, const Epilogue& ep,
+                     int* d_err, cudaStream_t st, const int* bidx) {
+    constexpr int smem = num_stages(K) * stage_bytes(K) + 1024 + BAR_BYTES;
+    static_assert(smem <= SMEM_MAX, "shared memory budget exceeded");
+    static bool attr_done[64] = {false};
+    if (!attr_done[dev]) {
+        MPPS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_f64e<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           smem));
+        attr_done[dev] = true;
     }
+    k_gemm_f64e<K><<<grid, THREADS, smem, st>>>(ta, tb, n, ksA, ksB, batch, eA, eB, ep, d_err, bidx);
+    MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }
 
 }  // namespace
-
-// ---- autotuner: cluster size of the emulated product per (device, size class, slices) ----
-// On the first product of a size class (n rounded up to a power of two, batch 1 vs many) the
-// three cluster sizes are timed on scratch operands of that size and the fastest is kept
-// for the process.  The timing synchronises the device once per class: make a first call
-// of each size before capturing a CUDA graph.
-namespace {
-std::mutex g_tune_mu;
-std::map<long long, int> g_tuned;
-}
-
-int f64e_cluster_choice(int dev, int n, int k, int batch) {
-    int cls = 1;
-    while (cls < n) cls <<= 1;
-    const long long key = ((long long)dev << 40) | ((long long)cls << 8) | ((long long)k << 1) |
-                          (batch > 1 ? 1 : 0);
-    {
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        auto it = g_tuned.find(key);
-        if (it != g_tuned.end()) return it->second;
-    }
-    int best = 1;
-    // time on scratch buffers: the caller's epilogue may accumulate into its output
-    const int ntune = cls < 64 ? 64 : (cls > 2048 ? 2048 : cls);
-    const int bt = batch > 1 ? 8 : 1;
-    const int lld = low_ld(ntune);
-    const size_t plane_b = (size_t)bt * k * ntune * lld * 2;
-    void *sa = nullptr, *sb = nullptr, *ex = nullptr, *out = nullptr, *er = nullptr;
-    cudaStream_t ts = nullptr;
-    bool ok = cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking) == cudaSuccess &&
-              cudaMalloc(&sa, plane_b) == cudaSuccess && cudaMalloc(&sb, plane_b) == cudaSuccess &&
-              cudaMalloc(&ex, sizeof(int) * bt * ntune) == cudaSuccess &&
-              cudaMalloc(&out, sizeof(double) * bt * ntune * ntune) == cudaSuccess &&
-              cudaMalloc(&er, sizeof(int)) == cudaSuccess;
-    if (ok) {
-        cudaMemsetAsync(sa, 0, plane_b, ts);
-        cudaMemsetAsync(sb, 0, plane_b, ts);
-        cudaMemsetAsync(ex, 0, sizeof(int) * bt * ntune, ts);
-        cudaMemsetAsync(er, 0, sizeof(int), ts);
-        CUtensorMap ta, tb;
-        ok = make_plane_map(&ta, sa, ntune, bt * k, lld, OM) && make_plane_map(&tb, sb, ntune, bt * k, lld, ON);
-        const int smem = num_stages(k) * stage_bytes(k) + 1024 + 256;
-        Epilogue ep = epilogue_plain((double*)out, (long long)ntune * ntune);
-        float best_ms = 1e30f;
-        cudaEvent_t e0, e1;
-        cudaEventCreate(&e0);
-        cudaEventCreate(&e1);
-        const int cands[3] = {1, 2, 4};
-        for (int ci = 0; ok && ci < 3; ++ci) {
-            const int cl = cands[ci];
-            if (launch_f64e_cl(cl, ta, tb, ntune, k, k, k, (int*)ex, (int*)ex, bt, ep, (int*)er, ts,
-                               nullptr, smem))
-                continue;   // warm-up (and skip a size that cannot launch)
-            cudaEventRecord(e0, ts);
-            for (int rep = 0; rep < 3; ++rep)
-                launch_f64e_cl(cl, ta, tb, ntune, k, k, k, (int*)ex, (int*)ex, bt, ep, (int*)er, ts,
-                               nullptr, smem);
-            cudaEventRecord(e1, ts);
-            if (cudaEventSynchronize(e1) != cudaSuccess) { ok = false; break; }
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best_ms) { best_ms = ms; best = cl; }
-        }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-    }
-    cudaGetLastError();
-    if (ts) cudaStreamSynchronize(ts);
-    cudaFree(sa); cudaFree(sb); cudaFree(ex); cudaFree(out); cudaFree(er);
-    if (ts) cudaStreamDestroy(ts);
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tuned[key] = best;
-    return best;
-}
 
 size_t f64e_plane_elems(int n, int batch, int k) { return (size_t)batch * k * n * low_ld(n); }
 
@@ -516,28 +547,33 @@ mpps_status launch_gemm_f64e(int k, const void* slicesA, int ksA, const int* eA,
     }
     const int lld = low_ld(n);
     CUtensorMap ta, tb;
-    if (!make_plane_map(&ta, slicesA, n, nmat * ksA, lld, OM) ||
-        !make_plane_map(&tb, slicesBt, n, nmat * ksB, lld, ON)) {
+    if (!make_plane_map(&ta, slicesA, n, nmat * ksA, lld, OM, 1) ||
+        !make_plane_map(&tb, slicesBt, n, nmat * ksB, lld, ON, k)) {
         set_error("cuTensorMapEncodeTiled failed for slice planes (n=%d)", n);
         return MPPS_ECUDA;
     }
-    const int smem = num_stages(k) * stage_bytes(k) + 1024 + 256;
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) dev = 0;
-    static int attr_done[64] = {0};
-    if (!attr_done[dev]) {
-        MPPS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_f64e<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           SMEM_BUDGET + 1024 + 256));
-        MPPS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_f64e<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           SMEM_BUDGET + 1024 + 256));
-        MPPS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_f64e<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           SMEM_BUDGET + 1024 + 256));
-        attr_done[dev] = 1;
+    const long long tiles = (long long)((n + ON - 1) / ON) * ((n + OM - 1) / OM) * batch;
+    if (tiles > 0x7fffffffLL) {
+        set_error("emulated FP64 product: %lld tiles exceed the index range", tiles);
+        return MPPS_EINVAL;
     }
-    const int cl = f64e_cluster_choice(dev, n, k, batch);
+    const int grid = (int)(tiles < sm_count(dev) ? tiles : sm_count(dev));
     ProfScope prof(MPPS_PROF_GEMM_F64E, st, 2.0 * n * (double)n * n * batch * (k * (k + 1) / 2));
-    return launch_f64e_cl(cl, ta, tb, n, k, ksA, ksB, eA, eB, batch, ep, d_err, st, bidx, smem);
+    switch (k) {
+        case 1: return launch_k<1>(dev, grid, ta, tb, n, ksA, ksB, batch, eA, eB, ep, d_err, st, bidx);
+        case 2: return launch_k<2>(dev, grid, ta, tb, n, ksA, ksB, batch, eA, eB, ep, d_err, st, bidx);
+        case 3: return launch_k<3>(dev, grid, ta, tb, n, ksA, ksB, batch, eA, eB, ep, d_err, st, bidx);
+        case 4: return launch_k<4>(dev, grid, ta, tb, n, ksA, ksB, batch, eA, eB, ep, d_err, st, bidx);
+        case 5: return launch_k<5>(dev, grid, ta, tb, n, ksA, ksB, batch, eA, eB, ep, d_err, st, bidx);
+        case 6: return launch_k<6>(dev, grid, ta, tb, n, ksA, ksB, batch, eA, eB, ep, d_err, st, bidx);
+        case 7: return launch_k<7>(dev, grid, ta, tb, n, ksA, ksB, batch, eA, eB, ep, d_err, st, bidx);
+        case 8: return launch_k<8>(dev, grid, ta, tb, n, ksA, ksB, batch, eA, eB, ep, d_err, st, bidx);
+        case 9: return launch_k<9>(dev, grid, ta, tb, n, ksA, ksB, batch, eA, eB, ep, d_err, st, bidx);
+        default: return launch_k<10>(dev, grid, ta, tb, n, ksA, ksB, batch, eA, eB, ep, d_err, st, bidx);
+    }
 }
 
 }  // namespace mpps
