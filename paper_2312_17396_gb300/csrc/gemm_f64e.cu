@@ -80,22 +80,48 @@ __host__ __device__ constexpr uint32_t tmem_cols(int nreg) {
     return c;
 }
 
-// Signed base-64 digits of x / 2^e (|x| < 2^e), computed in integers:
+// round_half_even(x 2^(62-e)) for |x| < 2^e (so the result is below 2^62 in magnitude),
+// computed from the bit fields of x on the integer pipe: equal to rounding the exact
+// product x 2^(62-e) to the nearest integer, ties to even.  Non-finite x gives 0.
+__device__ __forceinline__ long long scaled_int(double x, int e) {
+    const long long bits = __double_as_longlong(x);
+    const int ef = (int)((bits >> 52) & 0x7FF);
+    if (ef == 0x7FF) return 0;
+    long long m = bits & 0xFFFFFFFFFFFFFLL;
+    int E = -1074;                                   // x = m 2^E
+    if (ef != 0) { m |= 1LL << 52; E = ef - 1075; }
+    const int sh = E + 62 - e;
+    long long F;
+    if (sh >= 0) {
+        F = m << sh;                                 // exact: m 2^sh < 2^62
+    } else if (sh < -53) {
+        F = 0;                                       // m 2^sh < 1/2
+    } else {
+        const int k = -sh;
+        const long long q = m >> k, r = m & ((1LL << k) - 1), half = 1LL << (k - 1);
+        F = q + ((r > half || (r == half && (q & 1))) ? 1 : 0);
+    }
+    return bits < 0 ? -F : F;
+}
+
+// Signed base-64 digits of x / 2^e (|x| < 2^e):
 //   F = round(x 2^(62-e)) (|F| < 2^62);  for t: p = 56 - 6t, v_t = floor((F + 2^(p-1)) / 2^p),
 //   F -= v_t 2^p.  |v_0| <= 64, |v_t| <= 32 (t >= 1); after k digits |F| <= 2^(55-6(k-1)), i.e.
-//   x = 2^e (sum_t v_t 2^(-6(t+1)) + r) with |r| <= 2^(-6k-1).  Plane t stores v_t 2^-6t
-//   (exact in bf16).  Only one FP64 multiply and one conversion per value: the digit loop
-//   runs on the integer pipe.
-__device__ __forceinline__ void put_digits(double x, double scale, int k, __nv_bfloat16* dst,
+//   x = 2^e (sum_t v_t 2^(-6(t+1)) + r) with |r| <= 2^(-6k-1).  Plane t stores v_t 2^-6t,
+//   exact in bf16 (at most 7 significant bits, so the bf16 is the upper half of the FP32
+//   value; (float)v is formed by adding v to the bit pattern of 1.5 2^23).  No FP64
+//   arithmetic: the integer and FP32 pipes do all of it.
+__device__ __forceinline__ void put_digits(double x, int e, int k, __nv_bfloat16* dst,
                                            long long pstride) {
-    long long F = __double2ll_rn(x * scale);
+    long long F = scaled_int(x, e);
 #pragma unroll 1
     for (int t = 0; t < k; ++t) {
         const int p = 56 - 6 * t;
         const long long v = (F + (1LL << (p - 1))) >> p;
         F -= v << p;
-        dst[(long long)t * pstride] =
-            __float2bfloat16_rn((float)(int)v * __int_as_float((127 - 6 * t) << 23));
+        const float f = (__int_as_float(0x4B400000 + (int)v) - 12582912.0f) *
+                        __int_as_float((127 - 6 * t) << 23);
+        dst[(long long)t * pstride] = __ushort_as_bfloat16((unsigned short)(__float_as_uint(f) >> 16));
     }
 }
 
@@ -118,18 +144,17 @@ __global__ void k_slice_rows(const double* __restrict__ M, long long bs, int n, 
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     const int e = exp_above(mx);
     if (lane == 0) exps[(long long)b * n + row] = e;
-    const double scale = ldexp(1.0, 62 - e);
     __nv_bfloat16* dst = planes + (long long)b * plane_bs + (long long)row * lld;
     const long long pstride = (long long)n * lld;
     int j = lane;
     for (; j + 96 < n; j += 128) {              // 4 loads in flight per lane
         const double x0 = src[j], x1 = src[j + 32], x2 = src[j + 64], x3 = src[j + 96];
-        put_digits(x0, scale, k, dst + j, pstride);
-        put_digits(x1, scale, k, dst + j + 32, pstride);
-        put_digits(x2, scale, k, dst + j + 64, pstride);
-        put_digits(x3, scale, k, dst + j + 96, pstride);
+        put_digits(x0, e, k, dst + j, pstride);
+        put_digits(x1, e, k, dst + j + 32, pstride);
+        put_digits(x2, e, k, dst + j + 64, pstride);
+        put_digits(x3, e, k, dst + j + 96, pstride);
     }
-    for (; j < n; j += 32) put_digits(src[j], scale, k, dst + j, pstride);
+    for (; j < n; j += 32) put_digits(src[j], e, k, dst + j, pstride);
 }
 
 // Row maxima of |M| -> exponents e_i (one warp per row).
@@ -151,7 +176,7 @@ __global__ void k_slice_rows_elem(const double* __restrict__ M, long long bs, in
     const int col = blockIdx.x * blockDim.x + threadIdx.x, row = blockIdx.y, b = blockIdx.z;
     if (col >= n) return;
     const int e = exps[(long long)b * n + row];
-    put_digits(M[(long long)b * bs + (long long)row * n + col], ldexp(1.0, 62 - e), k,
+    put_digits(M[(long long)b * bs + (long long)row * n + col], e, k,
                planes + (long long)b * plane_bs + (long long)row * lld + col, (long long)n * lld);
 }
 
@@ -187,30 +212,8 @@ __global__ void k_slice_cols(const double* __restrict__ M, long long bs, int n, 
         if (col >= n || row >= n) continue;
         const int e = exp_above(__longlong_as_double((long long)colmax[(long long)b * n + col]));
         if (blockIdx.y == 0 && threadIdx.x == 0) exps[(long long)b * n + col] = e;
-        put_digits(tile[threadIdx.x][i], ldexp(1.0, 62 - e), k,
+        put_digits(tile[threadIdx.x][i], e, k,
                    planes + (long long)b * plane_bs + (long long)col * lld + row, pstride);
-    }
-}
-
-// Bounded wait that ignores the error word (lets copies and MMAs in flight finish before
-// the CTA exits, also after another thread gave up).  False when the limit passed.
-__device__ __forceinline__ bool mbar_wait_quiet(uint64_t* bar, uint32_t parity) {
-    const uint32_t addr = smem_u32(bar);
-    unsigned long long t0 = 0;
-    for (uint32_t it = 0;; ++it) {
-        uint32_t ok;
-        asm volatile(
-            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            "selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(addr), "r"(parity)
-            : "memory");
-        if (ok) return true;
-        if ((it & 63) == 0) {
-            const unsigned long long now = globaltimer();
-            if (t0 == 0) t0 = now;
-            else if (now - t0 > kWaitNs / 2) return false;
-        }
     }
 }
 

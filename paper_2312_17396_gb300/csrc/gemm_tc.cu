@@ -9,12 +9,15 @@
 // all accumulated in FP32.  The epilogue reads the 128 x 128 FP32 tile out of TMEM,
 // undoes the operand scales and adds B_{i-1} in FP64 (fused Horner add).
 //
-// Structure: one CTA (4 warps) per 128 x 128 output tile, K walked in 128-byte slabs
-// (64 bf16 / 32 tf32 / 128 fp8 per row) through a 3-4 stage TMA ring with full/empty
-// mbarriers.  Warp 0 lane 0 issues TMA, warp 1 lane 0 issues tcgen05.mma; all 4 warps run
-// the epilogue (warp w owns TMEM lanes 32w..32w+31 = tile rows).  Both operands are
-// K-major with the 128-byte swizzle.  Every mbarrier wait is bounded (about 2 s of
-// %globaltimer); on expiry the kernel sets *err, skips further waits and exits normally.
+// Structure: one CTA (8 warps) per 128 x TN output tile (TN = 64 when 128 x 128 tiles would
+// leave SMs idle, else 128), K walked in 128-byte slabs (64 bf16 / 32 tf32 / 128 fp8 per
+// row) through a 3-4 stage TMA ring with full/empty mbarriers.  Warp 0 lane 0 issues TMA,
+// warp 1 lane 0 issues tcgen05.mma (descriptors formed once per stage); then the FP32 tile
+// is staged from TMEM into the idle ring and all 8 warps run the FP64 epilogue over it in
+// row-major order (coalesced power-table reads and stores, four elements in flight per
+// thread).  Both operands are K-major with the 128-byte swizzle.  Every mbarrier wait is
+// bounded (about 2 s of %globaltimer); on expiry the kernel sets *err, skips further
+// waits, lets the copies in flight land and exits normally.
 #include "common.cuh"
 #include "tcgen05.cuh"
 
@@ -85,8 +88,10 @@ __host__ __device__ constexpr int smem_bytes() {
     return Tc<FMT>::kStages * Tc<FMT>::kOps * TILE_BYTES + 1024 + 256;
 }
 
+constexpr int TC_THREADS = 256;           // 8 warps: all of them run the epilogue
+
 template <int FMT, int TN>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(TC_THREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2,
               int n, Epilogue ep, int* err) {
@@ -129,7 +134,8 @@ __global__ void __launch_bounds__(128, 1)
 
     if (warp == 0 && lane == 0) {
         // TMA producer
-        for (int kb = 0; kb < nk; ++kb) {
+        int kb = 0;
+        for (; kb < nk; ++kb) {
             const int s = kb % STAGES;
             if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1, err)) break;
             mbar_expect_tx(&full[s], (OPS / 2) * (TM + TN) * SLAB);
@@ -142,6 +148,12 @@ __global__ void __launch_bounds__(128, 1)
                 tma_load_3d(st + 3 * TILE_BYTES, &tmB2, kc, n0, b, &full[s]);
             }
         }
+        // the copies of the last stages land before the ring is reused or the CTA exits
+        // (returns at once unless a wait above gave up)
+        bool landed = true;
+        for (int k2 = kb > STAGES ? kb - STAGES : 0; k2 < kb && landed; ++k2)
+            landed = mbar_wait_quiet(&full[k2 % STAGES], (k2 / STAGES) & 1);
+        if (!landed) atomicExch(err, 1);
     } else if (warp == 1 && lane == 0) {
         // MMA issuer: 4 instructions per 128-byte slab (K advance of 32 bytes each)
         bool ok = true;
@@ -150,15 +162,16 @@ __global__ void __launch_bounds__(128, 1)
             ok = mbar_wait(&full[s], (kb / STAGES) & 1, err);
             if (!ok) break;
             tc_fence_after();
-            const uint32_t a0 = smem_u32(smem + s * STAGE_BYTES);
-            const uint32_t b0 = a0 + TILE_BYTES;
+            // descriptors of this stage; the K advance of 32 bytes is +2 in the address field
+            const uint64_t da = sw128_desc(smem_u32(smem + s * STAGE_BYTES));
+            const uint64_t db = da + (uint64_t)(TILE_BYTES >> 4);
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
-                const uint64_t ad = sw128_desc(a0 + kk * 32), bd = sw128_desc(b0 + kk * 32);
+                const uint64_t ad = da + (uint64_t)(2 * kk), bd = db + (uint64_t)(2 * kk);
                 tc_mma<FMT, TN>(tmem, ad, bd, (kb | kk) != 0 ? 1u : 0u);
                 if constexpr (OPS == 4) {
-                    const uint64_t ad2 = sw128_desc(a0 + 2 * TILE_BYTES + kk * 32);
-                    const uint64_t bd2 = sw128_desc(a0 + 3 * TILE_BYTES + kk * 32);
+                    const uint64_t ad2 = da + (uint64_t)((2 * TILE_BYTES >> 4) + 2 * kk);
+                    const uint64_t bd2 = da + (uint64_t)((3 * TILE_BYTES >> 4) + 2 * kk);
                     tc_mma<FMT, TN>(tmem, ad, bd2, 1u);   // hi * lo
                     tc_mma<FMT, TN>(tmem, ad2, bd, 1u);   // lo * hi
                 }
@@ -172,36 +185,43 @@ __global__ void __launch_bounds__(128, 1)
     mbar_wait(done, 0, err);
     tc_fence_after();
 
-    // Epilogue: TMEM rows -> a 32 x 33 shared tile per warp (the ring is idle now), then
-    // each lane takes one column so that global reads of the power table and the stores are
-    // coalesced along rows.
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-    float* stile = (float*)smem + warp * 32 * 33;
-#pragma unroll 1
-    for (int c0 = 0; c0 < TN; c0 += 32) {
-        uint32_t v[32];
-        tmem_ld32(tmem + lane_base + (uint32_t)c0, v);
+    // Epilogue: the FP32 tile goes from TMEM to shared memory (the ring is idle now; warps w
+    // and w + 4 share TMEM lanes 32 (w % 4).. and split the columns), then all 256 threads
+    // walk it row-major, so that the reads of the power table and the stores are coalesced
+    // along rows, with four elements' loads in flight per thread.
+    constexpr int PITCH = TN + 1;
+    float* stile = (float*)smem;
+    {
+        const int q4 = warp & 3, h = warp >> 2;
+        const uint32_t lane_base = (uint32_t)(q4 * 32) << 16;
+        const int row = q4 * 32 + lane;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) stile[lane * 33 + j] = __uint_as_float(v[j]);
-        __syncwarp();
-        const int col = n0 + c0 + lane;
-#pragma unroll 1
-        for (int r4 = 0; r4 < 32; r4 += 4) {      // 4 rows per pass: their loads overlap
-            double val[4];
+        for (int c0 = 32 * h; c0 < TN; c0 += 64) {
+            uint32_t v[32];
+            tmem_ld32(tmem + lane_base + (uint32_t)c0, v);
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int row = m0 + warp * 32 + r4 + u;
-                val[u] = (row < n && col < n)
-                             ? epilogue_value(ep, b, row, col, n, (double)stile[(r4 + u) * 33 + lane])
-                             : 0.0;
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int row = m0 + warp * 32 + r4 + u;
-                if (row < n && col < n) epilogue_store(ep, b, row, col, n, val[u]);
-            }
+            for (int j = 0; j < 32; ++j) stile[row * PITCH + c0 + j] = __uint_as_float(v[j]);
         }
-        __syncwarp();
+    }
+    __syncthreads();
+    constexpr int U = 4;
+#pragma unroll 1
+    for (int e0 = threadIdx.x; e0 < TM * TN; e0 += TC_THREADS * U) {
+        double val[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * TC_THREADS;
+            const int r = e / TN, c = e % TN, row = m0 + r, col = n0 + c;
+            val[u] = (e < TM * TN && row < n && col < n)
+                         ? epilogue_value(ep, b, row, col, n, (double)stile[r * PITCH + c])
+                         : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * TC_THREADS;
+            const int r = e / TN, c = e % TN, row = m0 + r, col = n0 + c;
+            if (e < TM * TN && row < n && col < n) epilogue_store(ep, b, row, col, n, val[u]);
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -272,7 +292,7 @@ mpps_status launch_fmt(const void* A_hi, const void* A_lo, const void* Bt_hi, co
     dim3 grid((n + TN - 1) / TN, (n + TM - 1) / TM, batch);
     ProfScope prof(MPPS_PROF_GEMM_TC, st,
                    2.0 * n * (double)n * n * batch * (FMT == MPPS_FMT_BF16X3 ? 3 : 1));
-    k_gemm_tc<FMT, TN><<<grid, 128, smem, st>>>(ta, tb, ta2, tb2, n, ep, d_err);
+    k_gemm_tc<FMT, TN><<<grid, TC_THREADS, smem, st>>>(ta, tb, ta2, tb2, n, ep, d_err);
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }

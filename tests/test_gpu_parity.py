@@ -284,7 +284,7 @@ def test_matmul_f64e_exact_on_small_integers(mpps, n):
 
 @pytest.mark.parametrize("n", [1, 3, 17, 64, 130, 257, 1100])
 def test_matmul_f64e_vs_oracle(mpps, n):
-    """9 slices: FP64-level error.  n = 1100 crosses the 1024-long exact-accumulation chunk."""
+    """9 slices: FP64-level error (n up to several 128 x 64 tiles with ragged tails)."""
     rng = np.random.default_rng(400 + n)
     A = rng.standard_normal((1, n, n)); B = rng.standard_normal((1, n, n))
     A[0, 0, :] *= 1e-9                      # a row far below the others: row scaling matters
@@ -297,6 +297,44 @@ def test_matmul_f64e_vs_oracle(mpps, n):
     bound = 8 * U * (rmax * np.abs(B[0]).sum(axis=0)[None, :] + cmax * np.abs(A[0]).sum(axis=1)[:, None])
     assert np.all(err <= bound + 1e-300)
     assert np.linalg.norm(err) <= 4 * n * U * np.linalg.norm(absprod)
+
+
+@pytest.mark.parametrize("shift", [(-990, -20), (990, 20), (-600, 580)])
+def test_matmul_f64e_extreme_magnitudes(mpps, shift):
+    """Rows and columns far from 1 (down to 2^-1010 products): the slicing works from the
+    exponent fields and the result scale 2^(eA+eB) leaves the fast power-of-two path when it
+    would leave the normal range; against the oracle product scaled by the same powers."""
+    n = 130
+    rng = np.random.default_rng(77)
+    A0 = rng.standard_normal((n, n)); B0 = rng.standard_normal((n, n))
+    A = np.ldexp(A0, shift[0]); B = np.ldexp(B0, shift[1])
+    C = host(mpps.matmul(dev(A[None]), dev(B[None]), "f64e9"))[0]
+    ch, cl = oracle.matmul_dd(A0, None, B0, None)
+    ref = np.ldexp(ch, shift[0] + shift[1]); refl = np.ldexp(cl, shift[0] + shift[1])
+    rmax = np.abs(A0).max(axis=1)[:, None]; cmax = np.abs(B0).max(axis=0)[None, :]
+    bound = 8 * U * (rmax * np.abs(B0).sum(axis=0)[None, :] + cmax * np.abs(A0).sum(axis=1)[:, None])
+    err = np.abs(np.ldexp(C, -(shift[0] + shift[1])) - np.ldexp(ref, -(shift[0] + shift[1]))
+                 - np.ldexp(refl, -(shift[0] + shift[1])))
+    assert np.all(np.isfinite(C))
+    assert np.all(err <= bound)
+
+
+def test_matmul_f64e_multichunk_sampled(mpps):
+    """n = 2100 crosses the 2048-long exact-accumulation chunk (the exact diagonals are
+    drained into the 64-bit integer accumulator twice); 8 sampled columns against an
+    extended-precision (long double) dot product."""
+    n = 2100
+    rng = np.random.default_rng(2100)
+    A = rng.standard_normal((n, n)); B = rng.standard_normal((n, n))
+    A[5, :] *= 1e-7
+    C = host(mpps.matmul(dev(A[None]), dev(B[None]), "f64e9"))[0]
+    cols = rng.choice(n, size=8, replace=False)
+    ref = (A.astype(np.longdouble) @ B[:, cols].astype(np.longdouble))
+    err = np.abs(C[:, cols].astype(np.longdouble) - ref).astype(np.float64)
+    rmax = np.abs(A).max(axis=1)[:, None]; cmax = np.abs(B[:, cols]).max(axis=0)[None, :]
+    bound = 8 * U * (rmax * np.abs(B[:, cols]).sum(axis=0)[None, :]
+                     + cmax * np.abs(A).sum(axis=1)[:, None])
+    assert np.all(err <= bound)
 
 
 def test_matmul_f64e_error_falls_with_slices(mpps):
