@@ -250,6 +250,14 @@ mpps_status mpps_profile_read(int kernel_class, long long* launches, double* tot
  * call returns MPPS_ETIMEOUT and the CUDA context stays usable.  limit_us in 1..2000000. */
 mpps_status mpps_selftest_bounded_wait(int limit_us, void* stream);
 
+/* The library keeps its device workspaces (the power table, the slice planes, the
+ * rounded operand copies) in a private stream-ordered memory pool per device that does not
+ * give freed memory back between calls, so that repeated calls of one size allocate at no
+ * cost.  mpps_release_workspace waits for every device that has such a pool
+ * (cudaDeviceSynchronize) and returns the pool's unused memory to the driver.  Returns
+ * MPPS_ECUDA if a synchronisation or the trim fails. */
+mpps_status mpps_release_workspace(void);
+
 /* Description of the last failure on this thread ("" if none). */
 const char* mpps_last_error(void);
 

@@ -79,7 +79,7 @@ class _Report(ctypes.Structure):
 EXPORTS = ("mpps_policy_default", "mpps_plan", "ps_eval", "expm_taylor_ss", "ps_eval_adjoint",
            "mpps_matmul", "mpps_last_error", "mpps_version", "mpps_profile_enable",
            "mpps_profile_reset", "mpps_profile_read", "mpps_matmul_noalloc",
-           "mpps_selftest_bounded_wait", "expm_taylor_ss_grouped")
+           "mpps_selftest_bounded_wait", "expm_taylor_ss_grouped", "mpps_release_workspace")
 PROF_GEMM_F64, PROF_GEMM_TC, PROF_ELEMENTWISE, PROF_GEMM_F64E = 0, 1, 2, 3
 
 
@@ -109,6 +109,8 @@ def lib():
         L.expm_taylor_ss_grouped.restype = ctypes.c_int
         L.mpps_selftest_bounded_wait.argtypes = [ctypes.c_int, vp]
         L.mpps_selftest_bounded_wait.restype = ctypes.c_int
+        L.mpps_release_workspace.argtypes = []
+        L.mpps_release_workspace.restype = ctypes.c_int
         for f in ("mpps_plan", "ps_eval", "expm_taylor_ss", "ps_eval_adjoint", "mpps_matmul"):
             getattr(L, f).restype = ctypes.c_int
         L.mpps_profile_enable.argtypes = [ctypes.c_int]
@@ -407,6 +409,12 @@ def matmul_noalloc(A, B, out, fmt="fp64", stream=None):
 
 def version() -> str:
     return lib().mpps_version().decode()
+
+
+def release_workspace() -> None:
+    """Return the library's cached device workspaces to the driver (waits for the devices
+    that hold them)."""
+    _check(lib().mpps_release_workspace())
 
 
 def _make_autograd():

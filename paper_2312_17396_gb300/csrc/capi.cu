@@ -182,6 +182,35 @@ struct Arena {
     }
 };
 
+// Workspaces come from a private stream-ordered pool per device that keeps freed memory
+// (release threshold = all of it): with the default threshold of 0 every synchronisation
+// would hand the previous call's workspace back to the driver and the next call would map
+// it again.  mpps_release_workspace() trims the pools.
+static std::mutex g_poolmu;
+static cudaMemPool_t g_pool[64];
+
+static mpps_status workspace_pool(cudaMemPool_t* out) {
+    int dev = 0;
+    MPPS_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) {
+        set_error("device index %d out of range", dev);
+        return MPPS_ENOTSUP;
+    }
+    std::lock_guard<std::mutex> lk(g_poolmu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        MPPS_CUDA_TRY(cudaMemPoolCreate(&g_pool[dev], &props));
+        uint64_t keep = ~(uint64_t)0;
+        MPPS_CUDA_TRY(cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &keep));
+    }
+    *out = g_pool[dev];
+    return MPPS_OK;
+}
+
 struct DevBuf {
     void* p = nullptr;
     cudaStream_t st = nullptr;
@@ -191,11 +220,14 @@ struct DevBuf {
     mpps_status alloc(size_t bytes, cudaStream_t s) {
         st = s;
         if (bytes == 0) bytes = 256;
-        cudaError_t e = cudaMallocAsync(&p, bytes, s);
+        cudaMemPool_t pool = nullptr;
+        mpps_status rc = workspace_pool(&pool);
+        if (rc) return rc;
+        cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, pool, s);
         if (e != cudaSuccess) {
             p = nullptr;
             cudaGetLastError();
-            set_error("cudaMallocAsync(%zu) failed: %s", bytes, cudaGetErrorString(e));
+            set_error("cudaMallocFromPoolAsync(%zu) failed: %s", bytes, cudaGetErrorString(e));
             return e == cudaErrorMemoryAllocation ? MPPS_ENOMEM : MPPS_ECUDA;
         }
         return MPPS_OK;
@@ -675,6 +707,25 @@ void mpps_policy_default(mpps_policy* p) {
     p->formats = 0x1Fu;
     p->fp64_floor_steps = 2;
     p->f64_slices = 0;
+}
+
+mpps_status mpps_release_workspace(void) {
+    clear_error();
+    std::lock_guard<std::mutex> lk(g_poolmu);
+    for (int d = 0; d < 64; ++d)
+        if (g_pool[d]) {
+            int cur = 0;
+            MPPS_CUDA_TRY(cudaGetDevice(&cur));
+            MPPS_CUDA_TRY(cudaSetDevice(d));
+            cudaError_t e = cudaDeviceSynchronize();
+            if (e == cudaSuccess) e = cudaMemPoolTrimTo(g_pool[d], 0);
+            cudaSetDevice(cur);
+            if (e != cudaSuccess) {
+                set_error("mpps_release_workspace: %s", cudaGetErrorString(e));
+                return MPPS_ECUDA;
+            }
+        }
+    return MPPS_OK;
 }
 
 const char* mpps_last_error(void) { return g_err; }

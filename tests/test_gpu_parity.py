@@ -408,6 +408,15 @@ def test_bounded_wait_reports_timeout_and_context_survives(mpps):
     assert oracle.rel_err_1norm(P, ph, pl) <= 50 * 32 * U
 
 
+def test_workspace_release_between_calls(mpps):
+    """The cached workspace pool can be trimmed between calls; results are unchanged."""
+    A = inputs.gaussian_matrix(96, seed=96, norm1=3.0)
+    E1 = host(mpps.expm(dev(A), policy=mpps.NS_E))
+    mpps.release_workspace()
+    E2 = host(mpps.expm(dev(A), policy=mpps.NS_E))
+    assert np.array_equal(E1, E2)
+
+
 def test_sigma_matches_oracle_at_power_of_two_norms(mpps):
     """||A||_1 rescaled to exactly 4 or 32 (no margin): the squaring count the GPU picks must
     equal the oracle's sequential-sum rule even when rounding puts the norm a hair above."""
