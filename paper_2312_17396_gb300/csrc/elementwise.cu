@@ -80,7 +80,14 @@ __global__ void k_colsum_partial(const double* __restrict__ M, long long bs, int
     const double* base = M + (long long)b * bs;
     const int r0 = chunk * kRowsPerChunk, r1 = min(n, r0 + kRowsPerChunk);
     double acc = 0.0;
-    for (int row = r0; row < r1; ++row) acc += fabs(__ldg(base + (long long)row * n + col));
+    for (int row = r0; row < r1; row += 16) {   // 16 loads in flight, summed in row order
+        double v[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+            v[i] = row + i < r1 ? __ldg(base + (long long)(row + i) * n + col) : 0.0;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) acc += fabs(v[i]);
+    }
     partial[((long long)b * chunks + chunk) * n + col] = acc;
 }
 
@@ -171,11 +178,22 @@ __global__ void k_block_norms_partial_f32_reg(const double* __restrict__ pw, lon
     const long long nn = (long long)n * n;
     const double* base = pw + (long long)b * pw_bs + col;
     const int r0 = chunk * kRowsF32, r1 = min(n, r0 + kRowsF32);
-    for (int row = r0; row < r1; ++row) {
-        const double* p = base + (long long)row * n;
+    for (int row4 = r0; row4 < r1; row4 += 4) {
+      double ld[4][kRegS];   // the powers of four rows: 4 s loads in flight
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int j = 1; j <= kRegS; ++j)
+            ld[u][j - 1] = (j <= s && row4 + u < r1)
+                               ? __ldg(base + (long long)(row4 + u) * n + (long long)(j - 1) * nn)
+                               : 0.0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int row = row4 + u;
+        if (row >= r1) break;
         x[0] = (row == col) ? 1.f : 0.f;
 #pragma unroll
-        for (int j = 1; j <= kRegS; ++j) x[j] = (j <= s) ? narrow(__ldg(p + (long long)(j - 1) * nn)) : 0.f;
+        for (int j = 1; j <= kRegS; ++j) x[j] = narrow(ld[u][j - 1]);
 #pragma unroll
         for (int i = 0; i <= kRegR; ++i) {
             if (i <= r) {
@@ -192,6 +210,7 @@ __global__ void k_block_norms_partial_f32_reg(const double* __restrict__ pw, lon
         for (int j = 1; j <= kRegS; ++j) if (j == s) xs = x[j];
         acc[kRegR + 1] += fabsf(xs);
         acc[kRegR + 2] += fabsf(x[1]);
+      }
     }
     double* out = partial + ((long long)b * chunks + chunk) * q * n + col;
 #pragma unroll
@@ -212,9 +231,11 @@ __global__ void k_norms_finalize_scaled(const double* __restrict__ partial, int 
     const int t = blockIdx.x, b = blockIdx.z;
     const int col = blockIdx.y * blockDim.x + threadIdx.x;
     double sum = 0.0;
-    if (col < n)
+    if (col < n) {
+#pragma unroll 8
         for (int c = 0; c < chunks; ++c)
             sum += partial[(((long long)b * chunks + c) * q + t) * n + col];
+    }
     const double best = block_max(sum) * sc.c[t];
     if (threadIdx.x == 0)
         atomicMax((unsigned long long*)(norms + (long long)b * q + t),
@@ -463,7 +484,11 @@ mpps_status launch_norm1(const double* M, long long bs, int n, int batch, double
     dim3 g((n + kColsPerBlock - 1) / kColsPerBlock, chunks, batch);
     k_colsum_partial<<<g, kColsPerBlock, 0, st>>>(M, bs, n, partial);
     MPPS_LAUNCH_CHECK();
-    k_norms_finalize<<<dim3(1, batch), 256, 0, st>>>(partial, n, chunks, 1, norms);
+    MPPS_CUDA_TRY(cudaMemsetAsync(norms, 0, sizeof(double) * (size_t)batch, st));
+    BlockScales one;
+    one.c[0] = 1.0;
+    k_norms_finalize_scaled<<<dim3(1, (n + 127) / 128, batch), 128, 0, st>>>(partial, n, chunks, 1,
+                                                                             one, norms);
     MPPS_LAUNCH_CHECK();
     // ... and, only for a matrix whose norm lies within 2^-44 of a power of two (where the
     // summation order could move ceil(log2 ||A||_1)), the plain sequential column sums

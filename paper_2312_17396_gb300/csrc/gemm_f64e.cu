@@ -104,22 +104,29 @@ __device__ __forceinline__ long long scaled_int(double x, int e) {
     return bits < 0 ? -F : F;
 }
 
-// Signed base-64 digits of x / 2^e (|x| < 2^e):
-//   F = round(x 2^(62-e)) (|F| < 2^62);  for t: p = 56 - 6t, v_t = floor((F + 2^(p-1)) / 2^p),
-//   F -= v_t 2^p.  |v_0| <= 64, |v_t| <= 32 (t >= 1); after k digits |F| <= 2^(55-6(k-1)), i.e.
-//   x = 2^e (sum_t v_t 2^(-6(t+1)) + r) with |r| <= 2^(-6k-1).  Plane t stores v_t 2^-6t,
-//   exact in bf16 (at most 7 significant bits, so the bf16 is the upper half of the FP32
-//   value; (float)v is formed by adding v to the bit pattern of 1.5 2^23).  No FP64
-//   arithmetic: the integer and FP32 pipes do all of it.
-__device__ __forceinline__ void put_digits(double x, int e, int k, __nv_bfloat16* dst,
-                                           long long pstride) {
-    long long F = scaled_int(x, e);
+// Signed base-64 digits of x / 2^e (|x| < 2^e), in offset form: with F = round(x 2^(62-e))
+// (|F| < 2^62), p_t = 56 - 6t and G = F + 2^(p_{k-1} - 1) + sum_{t=1}^{k-1} 32 2^(p_t),
+//   v_0 = floor(G / 2^56),   v_t = ((G >> p_t) mod 64) - 32   (t >= 1),
+// so that F = sum_t v_t 2^(p_t) + r with |r| <= 2^(p_{k-1} - 1): x = 2^e (sum_t v_t 2^(-6(t+1))
+// + r 2^-62), |r 2^-62| <= 2^(-6k-1); |v_0| <= 64, -32 <= v_t <= 31.  Every digit comes from G
+// alone (no chain through a remainder).  Plane t stores v_t 2^-6t, exact in bf16 (at most 7
+// significant bits, so the bf16 is the upper half of the FP32 value; (float)v is formed by
+// adding v to the bit pattern of 1.5 2^23).  No FP64 arithmetic: the integer and FP32
+// pipes do all of it.
+__host__ __device__ inline long long digit_offset(int k) {
+    long long o = 1LL << (55 - 6 * (k - 1));
+    for (int t = 1; t < k; ++t) o += 32LL << (56 - 6 * t);
+    return o;
+}
+
+__device__ __forceinline__ void put_digits(double x, int e, int k, long long goff,
+                                           __nv_bfloat16* dst, long long pstride) {
+    const long long G = scaled_int(x, e) + goff;
 #pragma unroll 1
     for (int t = 0; t < k; ++t) {
         const int p = 56 - 6 * t;
-        const long long v = (F + (1LL << (p - 1))) >> p;
-        F -= v << p;
-        const float f = (__int_as_float(0x4B400000 + (int)v) - 12582912.0f) *
+        const int v = t == 0 ? (int)(G >> 56) : (int)((G >> p) & 63) - 32;
+        const float f = (__int_as_float(0x4B400000 + v) - 12582912.0f) *
                         __int_as_float((127 - 6 * t) << 23);
         dst[(long long)t * pstride] = __ushort_as_bfloat16((unsigned short)(__float_as_uint(f) >> 16));
     }
@@ -131,10 +138,11 @@ __device__ __forceinline__ int exp_above(double mx) {
     return e;
 }
 
-// Row slices (A operand): one warp per row; e_i from the row maximum.
+// Row slices (A operand) for short rows (n < 256): one warp per row; e_i from the row
+// maximum.
 __global__ void k_slice_rows(const double* __restrict__ M, long long bs, int n, int k,
-                             __nv_bfloat16* __restrict__ planes, long long plane_bs, int lld,
-                             int* __restrict__ exps) {
+                             long long goff, __nv_bfloat16* __restrict__ planes,
+                             long long plane_bs, int lld, int* __restrict__ exps) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row = blockIdx.x * (blockDim.x >> 5) + warp, b = blockIdx.y;
     if (row >= n) return;
@@ -146,18 +154,51 @@ __global__ void k_slice_rows(const double* __restrict__ M, long long bs, int n, 
     if (lane == 0) exps[(long long)b * n + row] = e;
     __nv_bfloat16* dst = planes + (long long)b * plane_bs + (long long)row * lld;
     const long long pstride = (long long)n * lld;
-    int j = lane;
-    for (; j + 96 < n; j += 128) {              // 4 loads in flight per lane
-        const double x0 = src[j], x1 = src[j + 32], x2 = src[j + 64], x3 = src[j + 96];
-        put_digits(x0, e, k, dst + j, pstride);
-        put_digits(x1, e, k, dst + j + 32, pstride);
-        put_digits(x2, e, k, dst + j + 64, pstride);
-        put_digits(x3, e, k, dst + j + 96, pstride);
-    }
-    for (; j < n; j += 32) put_digits(src[j], e, k, dst + j, pstride);
+    for (int j = lane; j < n; j += 32) put_digits(src[j], e, k, goff, dst + j, pstride);
 }
 
-// Row maxima of |M| -> exponents e_i (one warp per row).
+// Row slices for rows of up to 256 VPT elements: one 256-thread block per row holds the row
+// in registers (VPT values per thread), reduces its maximum (as the bit pattern of a
+// non-negative double) and writes the k planes: the row is read once.
+template <int VPT>
+__global__ void __launch_bounds__(256) k_slice_rows_blk(const double* __restrict__ M, long long bs,
+                                                        int n, int k, long long goff,
+                                                        __nv_bfloat16* __restrict__ planes,
+                                                        long long plane_bs, int lld,
+                                                        int* __restrict__ exps) {
+    __shared__ unsigned long long red[8];
+    const int row = blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
+    const double* src = M + (long long)b * bs + (long long)row * n;
+    double v[VPT];
+    unsigned long long mx = 0;
+#pragma unroll
+    for (int i = 0; i < VPT; ++i) {
+        const int j = tid + 256 * i;
+        v[i] = j < n ? src[j] : 0.0;
+        const unsigned long long a = (unsigned long long)__double_as_longlong(v[i]) & 0x7fffffffffffffffULL;
+        mx = a > mx ? a : mx;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = t > mx ? t : mx;
+    }
+    if ((tid & 31) == 0) red[tid >> 5] = mx;
+    __syncthreads();
+    mx = red[0];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) mx = red[w] > mx ? red[w] : mx;
+    const int e = exp_above(__longlong_as_double((long long)mx));
+    if (tid == 0) exps[(long long)b * n + row] = e;
+    __nv_bfloat16* dst = planes + (long long)b * plane_bs + (long long)row * lld;
+    const long long pstride = (long long)n * lld;
+#pragma unroll
+    for (int i = 0; i < VPT; ++i) {
+        const int j = tid + 256 * i;
+        if (j < n) put_digits(v[i], e, k, goff, dst + j, pstride);
+    }
+}
+
+// Row maxima of |M| -> exponents e_i (one warp per row), for rows too long for the above.
 __global__ void k_rowexp(const double* __restrict__ M, long long bs, int n, int* __restrict__ exps) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row = blockIdx.x * (blockDim.x >> 5) + warp, b = blockIdx.y;
@@ -171,31 +212,39 @@ __global__ void k_rowexp(const double* __restrict__ M, long long bs, int n, int*
 
 // Row slices, one thread per element (the exponents come from k_rowexp).
 __global__ void k_slice_rows_elem(const double* __restrict__ M, long long bs, int n, int k,
-                                  const int* __restrict__ exps, __nv_bfloat16* __restrict__ planes,
-                                  long long plane_bs, int lld) {
+                                  long long goff, const int* __restrict__ exps,
+                                  __nv_bfloat16* __restrict__ planes, long long plane_bs, int lld) {
     const int col = blockIdx.x * blockDim.x + threadIdx.x, row = blockIdx.y, b = blockIdx.z;
     if (col >= n) return;
     const int e = exps[(long long)b * n + row];
-    put_digits(M[(long long)b * bs + (long long)row * n + col], e, k,
+    put_digits(M[(long long)b * bs + (long long)row * n + col], e, k, goff,
                planes + (long long)b * plane_bs + (long long)row * lld + col, (long long)n * lld);
 }
 
-// Column maxima of |M| (as the bit pattern of a non-negative double; out zeroed first).
+// Column maxima of |M| (as the bit pattern of a non-negative double; out zeroed first): one
+// thread per column over a 16-row chunk, all 16 loads in flight.
 __global__ void k_colmax(const double* __restrict__ M, long long bs, int n,
                          unsigned long long* __restrict__ out) {
     const int col = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.z;
     if (col >= n) return;
-    const int r0 = blockIdx.y * 64, r1 = min(n, r0 + 64);
-    const double* src = M + (long long)b * bs + col;
-    double mx = 0.0;
-    for (int row = r0; row < r1; ++row) mx = fmax(mx, fabs(src[(long long)row * n]));
-    atomicMax(out + (long long)b * n + col, (unsigned long long)__double_as_longlong(mx));
+    const int r0 = blockIdx.y * 16;
+    const double* src = M + (long long)b * bs + (long long)r0 * n + col;
+    unsigned long long mx = 0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        if (r0 + i < n) {
+            const unsigned long long a =
+                (unsigned long long)__double_as_longlong(__ldg(src + (long long)i * n)) & 0x7fffffffffffffffULL;
+            mx = a > mx ? a : mx;
+        }
+    }
+    atomicMax(out + (long long)b * n + col, mx);
 }
 
 // Column slices (B operand, written transposed: plane row j = column j of M), 32 x 32 tiles
 // through shared memory; e_j from the column maxima.
 __global__ void k_slice_cols(const double* __restrict__ M, long long bs, int n, int k,
-                             const unsigned long long* __restrict__ colmax,
+                             long long goff, const unsigned long long* __restrict__ colmax,
                              __nv_bfloat16* __restrict__ planes, long long plane_bs, int lld,
                              int* __restrict__ exps) {
     __shared__ double tile[32][33];
@@ -212,7 +261,7 @@ __global__ void k_slice_cols(const double* __restrict__ M, long long bs, int n, 
         if (col >= n || row >= n) continue;
         const int e = exp_above(__longlong_as_double((long long)colmax[(long long)b * n + col]));
         if (blockIdx.y == 0 && threadIdx.x == 0) exps[(long long)b * n + col] = e;
-        put_digits(tile[threadIdx.x][i], e, k,
+        put_digits(tile[threadIdx.x][i], e, k, goff,
                    planes + (long long)b * plane_bs + (long long)col * lld + row, pstride);
     }
 }
@@ -511,16 +560,30 @@ mpps_status launch_slice_rows(const double* M, long long bs, int n, int batch, i
                               int* exps, cudaStream_t st) {
     ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
     const int lld = low_ld(n);
-    if (n >= 256 && batch <= 65535) {
-        // many threads per row: a row-maximum pass, then one thread per element
+    const long long goff = digit_offset(k), pbs = (long long)k * n * lld;
+    __nv_bfloat16* pl = (__nv_bfloat16*)planes;
+    if (batch > 65535) {
+        set_error("slice_rows: batch %d exceeds the grid limit", batch);
+        return MPPS_EINVAL;
+    }
+    if (n < 256) {
+        k_slice_rows<<<dim3((n + 7) / 8, batch), 256, 0, st>>>(M, bs, n, k, goff, pl, pbs, lld, exps);
+    } else if (n <= 4096) {
+        const dim3 g(n, batch);
+        if (n <= 512)
+            k_slice_rows_blk<2><<<g, 256, 0, st>>>(M, bs, n, k, goff, pl, pbs, lld, exps);
+        else if (n <= 1024)
+            k_slice_rows_blk<4><<<g, 256, 0, st>>>(M, bs, n, k, goff, pl, pbs, lld, exps);
+        else if (n <= 2048)
+            k_slice_rows_blk<8><<<g, 256, 0, st>>>(M, bs, n, k, goff, pl, pbs, lld, exps);
+        else
+            k_slice_rows_blk<16><<<g, 256, 0, st>>>(M, bs, n, k, goff, pl, pbs, lld, exps);
+    } else {
+        // long rows: a row-maximum pass, then one thread per element
         k_rowexp<<<dim3((n + 7) / 8, batch), 256, 0, st>>>(M, bs, n, exps);
         MPPS_LAUNCH_CHECK();
-        k_slice_rows_elem<<<dim3((n + 127) / 128, n, batch), 128, 0, st>>>(
-            M, bs, n, k, exps, (__nv_bfloat16*)planes, (long long)k * n * lld, lld);
-    } else {
-        dim3 g((n + 7) / 8, batch);
-        k_slice_rows<<<g, 256, 0, st>>>(M, bs, n, k, (__nv_bfloat16*)planes, (long long)k * n * lld,
-                                        lld, exps);
+        k_slice_rows_elem<<<dim3((n + 127) / 128, n, batch), 128, 0, st>>>(M, bs, n, k, goff, exps, pl,
+                                                                          pbs, lld);
     }
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
@@ -531,10 +594,11 @@ mpps_status launch_slice_cols(const double* M, long long bs, int n, int batch, i
     ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
     const int lld = low_ld(n);
     MPPS_CUDA_TRY(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * (size_t)batch * n, st));
-    k_colmax<<<dim3((n + 127) / 128, (n + 63) / 64, batch), 128, 0, st>>>(M, bs, n, colmax);
+    k_colmax<<<dim3((n + 127) / 128, (n + 15) / 16, batch), 128, 0, st>>>(M, bs, n, colmax);
     MPPS_LAUNCH_CHECK();
     k_slice_cols<<<dim3((n + 31) / 32, (n + 31) / 32, batch), dim3(32, 8), 0, st>>>(
-        M, bs, n, k, colmax, (__nv_bfloat16*)planes, (long long)k * n * lld, lld, exps);
+        M, bs, n, k, digit_offset(k), colmax, (__nv_bfloat16*)planes, (long long)k * n * lld, lld,
+        exps);
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }
