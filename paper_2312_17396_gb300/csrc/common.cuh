@@ -115,7 +115,9 @@ __device__ __forceinline__ void store_low(int fmt, void* hi, void* lo, long long
 // Epilogue value for element (row, col) of batch element b, given the product acc.
 __device__ __forceinline__ double epilogue_value(const Epilogue& ep, int b, int row, int col,
                                                  int n, double acc) {
-    double v = (ep.alpha_b ? ep.alpha_b[b] : ep.alpha) * acc;
+    const double al = ep.alpha_b ? ep.alpha_b[b] : ep.alpha;
+    double v = acc;
+    if (__double_as_longlong(al) != 0x3FF0000000000000LL) v = al * acc;   // no multiply by 1
     if (ep.nt >= 0) {
         if (row == col) v += ep.coef[0];
         const double* base = ep.pw + (long long)b * ep.pw_bstride + (long long)row * n + col;

@@ -26,8 +26,8 @@
 // pipe (W = sum_{d<=5} 2^{6(5-d)} D_d as a 64-bit integer, the tail as FP32), so the scarce
 // FP64 pipe only does the last combination 2^{e-42} W + 2^{e-12} T and the fused epilogue.
 //
-// Kernel: persistent, one CTA per SM, 128 x 64 output tiles, 10 warps (0-7 epilogue: TMEM
-// lane quarter = warp % 4, column half = warp / 4; 8 TMA producer; 9 MMA issuer).  Per K
+// Kernel: persistent, one CTA per SM, 128 x 64 output tiles, 18 warps (0-15 epilogue: TMEM
+// lane quarter = warp % 4, 16-column group = warp / 4; 16 TMA producer; 17 MMA issuer).  Per K
 // block of 32 the producer loads the k slices of the B^T tile (one 3-D box) and the k slices
 // of the A tile (one box and one mbarrier each, so the MMAs of slice t start when slice t
 // lands).  The MMA of slice t uses the stacked B operand b'_0..b'_{6-t} (N = 64 (7 - t)) and
@@ -56,8 +56,10 @@ constexpr int NEXACT = 6;               // diagonals accumulated exactly
 constexpr int NREG = 8;                 // TMEM regions: D_0..D_5, d = 6, and d >= 7
 constexpr int A_TILE = OM * KB * 2;     // 8 KB
 constexpr int B_TILE = ON * KB * 2;     // 4 KB
-constexpr int EPI_WARPS = 8;
+constexpr int EPI_WARPS = 16;            // 4 per TMEM lane quarter, 16 columns each
+constexpr int EPI_COLS = ON / (EPI_WARPS / 4);
 constexpr int THREADS = (EPI_WARPS + 2) * 32;
+static_assert(EPI_COLS == 16, "the drain loads 16 TMEM columns per thread");
 constexpr int MAX_STAGES = 8;
 constexpr int NFULL = MAX_STAGES * (MPPS_F64E_MAX_SLICES + 1);
 constexpr int BAR_BYTES = 1024;
@@ -266,9 +268,44 @@ __global__ void k_slice_cols(const double* __restrict__ M, long long bs, int n, 
     }
 }
 
-// 2^e as a double for -1022 <= e <= 1023 (built from the exponent field).
-__device__ __forceinline__ double pow2i(int e) {
-    return __longlong_as_double((long long)(e + 1023) << 52);
+// w 2^s rounded to the nearest double (ties to even) on the integer pipe; false (and *out
+// untouched) when the result would not be a normal double.
+__device__ __forceinline__ bool i64_to_f64_scaled(long long w, int s, double* out) {
+    if (w == 0) { *out = 0.0; return true; }
+    const unsigned long long sgn = w < 0 ? 0x8000000000000000ULL : 0ULL;
+    const unsigned long long a = w < 0 ? 0ULL - (unsigned long long)w : (unsigned long long)w;
+    const int msb = 63 - __clzll((long long)a);
+    int ed = msb + 1023 + s;
+    unsigned long long m;
+    if (msb <= 52) {
+        m = a << (52 - msb);
+    } else {
+        const int sh = msb - 52;
+        const unsigned long long rem = a & ((1ULL << sh) - 1), half = 1ULL << (sh - 1);
+        m = a >> sh;
+        if (rem > half || (rem == half && (m & 1))) {
+            ++m;
+            if (m >> 53) { m >>= 1; ++ed; }
+        }
+    }
+    if (ed <= 0 || ed >= 2047) return false;
+    *out = __longlong_as_double((long long)(sgn | ((unsigned long long)ed << 52) | (m & 0xFFFFFFFFFFFFFULL)));
+    return true;
+}
+
+// f 2^s as a double (exact) on the integer pipe; false for subnormal, non-finite or
+// out-of-range results.
+__device__ __forceinline__ bool f32_to_f64_scaled(float f, int s, double* out) {
+    const unsigned u = __float_as_uint(f);
+    if ((u << 1) == 0) { *out = __longlong_as_double((long long)(u >> 31) << 63); return true; }
+    const int ef = (int)((u >> 23) & 0xff);
+    if (ef == 0 || ef == 0xff) return false;
+    const int ed = ef - 127 + 1023 + s;
+    if (ed <= 0 || ed >= 2047) return false;
+    *out = __longlong_as_double((long long)(((unsigned long long)(u >> 31) << 63) |
+                                            ((unsigned long long)ed << 52) |
+                                            ((unsigned long long)(u & 0x7fffff) << 29)));
+    return true;
 }
 
 // Tile `id` -> (matrix slot z, first row, first column); row blocks are walked in groups of
@@ -430,18 +467,18 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (!mbar_wait_quiet(mma_done, 0)) atomicExch(err, 1);
         }
     } else {
-        // epilogue warps 0-7: row = m0 + 32 (warp % 4) + lane, columns n0 + 32 (warp / 4) + j
-        const int q4 = warp & 3, h = warp >> 2;
+        // epilogue warps: row = m0 + 32 (warp % 4) + lane, columns n0 + 16 (warp / 4) + j
+        const int q4 = warp & 3, h = warp >> 2;   // lane quarter, column group
         const uint32_t lane_base = (uint32_t)(q4 * 32) << 16;
         uint32_t gc = 0;
         for (int id = blockIdx.x; id < total; id += gridDim.x) {
             int z, m0, n0;
             tm.decode(id, z, m0, n0);
             const int b = bidx ? bidx[z] : z;
-            long long W[32];
-            float T[32];
+            long long W[EPI_COLS];
+            float T[EPI_COLS];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) { W[j] = 0; T[j] = 0.f; }
+            for (int j = 0; j < EPI_COLS; ++j) { W[j] = 0; T[j] = 0.f; }
             bool ok = true;
             for (int c = 0; c < nchunks; ++c, ++gc) {
                 ok = __all_sync(0xffffffffu, mbar_wait(chunk_done, gc & 1, err));
@@ -449,20 +486,20 @@ __global__ void __launch_bounds__(THREADS, 1)
                 tc_fence_after();
 #pragma unroll
                 for (int d = 0; d < NX; ++d) {   // exact regions: W += 2^{6(5-d)} D_d
-                    uint32_t v[32];
-                    tmem_ld32(tmem + lane_base + (uint32_t)(ON * d + 32 * h), v);
+                    uint32_t v[EPI_COLS];
+                    tmem_ld16(tmem + lane_base + (uint32_t)(ON * d + EPI_COLS * h), v);
                     const float up = __int_as_float((127 + 6 * d) << 23);   // 2^{6d}
                     const int mul = 1 << (6 * (NEXACT - 1 - d));
 #pragma unroll
-                    for (int j = 0; j < 32; ++j)
+                    for (int j = 0; j < EPI_COLS; ++j)
                         W[j] += (long long)__float2int_rn(__uint_as_float(v[j]) * up) * mul;
                 }
 #pragma unroll
                 for (int d = NX; d < NR; ++d) {  // tail regions (FP32)
-                    uint32_t v[32];
-                    tmem_ld32(tmem + lane_base + (uint32_t)(ON * d + 32 * h), v);
+                    uint32_t v[EPI_COLS];
+                    tmem_ld16(tmem + lane_base + (uint32_t)(ON * d + EPI_COLS * h), v);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) T[j] += __uint_as_float(v[j]);
+                    for (int j = 0; j < EPI_COLS; ++j) T[j] += __uint_as_float(v[j]);
                 }
                 tc_fence_before();
                 mbar_arrive_cta(tmem_free);
@@ -472,16 +509,18 @@ __global__ void __launch_bounds__(THREADS, 1)
             const int row = m0 + q4 * 32 + lane;
             if (row < n) {
                 const int er = eA[(long long)b * n + row];
-                const int cb = n0 + 32 * h;
+                const int cb = n0 + EPI_COLS * h;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
+                for (int j = 0; j < EPI_COLS; ++j) {
                     const int col = cb + j;
                     if (col < n) {
                         const int e = er + __ldg(eB + (long long)b * n + col);
-                        const double wd = (double)W[j], td = (double)T[j];
-                        const double val = (e - 42 >= -1022 && e - 12 <= 1023)
-                                               ? fma(wd, pow2i(e - 42), td * pow2i(e - 12))
-                                               : ldexp(fma(wd, 0x1p-30, td), e - 12);
+                        // 2^(e-42) W and 2^(e-12) T formed on the integer pipe, one FP64 add
+                        double wd, td, val;
+                        if (i64_to_f64_scaled(W[j], e - 42, &wd) && f32_to_f64_scaled(T[j], e - 12, &td))
+                            val = wd + td;
+                        else
+                            val = ldexp(fma((double)W[j], 0x1p-30, (double)T[j]), e - 12);
                         epilogue_store(ep, b, row, col, n, epilogue_value(ep, b, row, col, n, val));
                     }
                 }
