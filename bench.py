@@ -17,6 +17,7 @@ the same workload instead.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -30,6 +31,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "p(A) evals/s and TFLOP/s, mixed vs fixed FP64 PS, at equal 1-norm rel. error"
 NORMS = (0.5, 4.0, 32.0)
+C2_FORMATS = ("fp64", "bf16x3", "tf32", "bf16")
 SEED = 2
 
 
@@ -250,8 +252,12 @@ def main():
     torch.cuda.set_device(dev)
     mpps.lib()
     n, m = args.n, args.m
-    pols = {"ns_e": mpps.NS_E, "paper_e": mpps.PAPER_E, "fixed_e": mpps.FIXED_E,
-            "ns": mpps.NS, "paper": mpps.PAPER, "fixed": mpps.FIXED}
+    # the n = 1024 exp workload's mixed ladder is FP64 / 3xBF16 / TF32 / BF16 (no FP8 steps)
+    c2 = dict(formats=C2_FORMATS)
+    pols = {"ns_e": dataclasses.replace(mpps.NS_E, **c2),
+            "paper_e": dataclasses.replace(mpps.PAPER_E, **c2), "fixed_e": mpps.FIXED_E,
+            "ns": dataclasses.replace(mpps.NS, **c2), "paper": dataclasses.replace(mpps.PAPER, **c2),
+            "fixed": mpps.FIXED}
     head = args.policy
     extra = [p for p in args.policies.split(",") if p in pols]
     order = [head] + [p for p in dict.fromkeys(["fixed"] + extra) if p != head]
@@ -392,7 +398,8 @@ def main():
         "data": "synthetic",
         "config": {"workload": f"expm_taylor_ss n={n} m={m} s=6, one matrix each at "
                                f"||A||_1 in {list(NORMS)} (sigma 0/2/5), N(0,1) entries, seed {SEED}+k",
-                   "policy": head, "l2": "flushed (256 MiB write) before every step",
+                   "policy": head, "formats": "+".join(C2_FORMATS),
+                   "l2": "flushed (256 MiB write) before every step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "tflops": results[head]["tflops_fp64_equiv"],
         "fixed": {"value": fixed_value, "unit": "evals/s", "ms_per_step": results["fixed"]["ms_per_step"],

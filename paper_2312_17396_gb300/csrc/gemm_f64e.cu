@@ -121,6 +121,14 @@ __host__ __device__ inline long long digit_offset(int k) {
     return o;
 }
 
+// bf16 bits of digit t of G (see above).
+__device__ __forceinline__ unsigned digit_bits(long long G, int t) {
+    const int p = 56 - 6 * t;
+    const int v = t == 0 ? (int)(G >> 56) : (int)((G >> p) & 63) - 32;
+    const float f = (__int_as_float(0x4B400000 + v) - 12582912.0f) * __int_as_float((127 - 6 * t) << 23);
+    return __float_as_uint(f) >> 16;
+}
+
 __device__ __forceinline__ void put_digits(double x, int e, int k, long long goff,
                                            __nv_bfloat16* dst, long long pstride) {
     const long long G = scaled_int(x, e) + goff;
@@ -197,6 +205,65 @@ __global__ void __launch_bounds__(256) k_slice_rows_blk(const double* __restrict
     for (int i = 0; i < VPT; ++i) {
         const int j = tid + 256 * i;
         if (j < n) put_digits(v[i], e, k, goff, dst + j, pstride);
+    }
+}
+
+// The same with four consecutive columns per thread (n a multiple of 4): two 16-byte loads
+// and one 8-byte store per plane for each group.  NG groups per thread, n <= 1024 NG.
+template <int NG>
+__global__ void __launch_bounds__(256) k_slice_rows_blk4(const double* __restrict__ M, long long bs,
+                                                         int n, int k, long long goff,
+                                                         __nv_bfloat16* __restrict__ planes,
+                                                         long long plane_bs, int lld,
+                                                         int* __restrict__ exps) {
+    __shared__ unsigned long long red[8];
+    const int row = blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
+    const double* src = M + (long long)b * bs + (long long)row * n;
+    double v[NG][4];
+    unsigned long long mx = 0;
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+        const int j = 4 * (tid + 256 * g);
+        if (j < n) {
+            const double2 a = *reinterpret_cast<const double2*>(src + j);
+            const double2 c = *reinterpret_cast<const double2*>(src + j + 2);
+            v[g][0] = a.x; v[g][1] = a.y; v[g][2] = c.x; v[g][3] = c.y;
+        } else {
+            v[g][0] = v[g][1] = v[g][2] = v[g][3] = 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const unsigned long long a = (unsigned long long)__double_as_longlong(v[g][u]) & 0x7fffffffffffffffULL;
+            mx = a > mx ? a : mx;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = t > mx ? t : mx;
+    }
+    if ((tid & 31) == 0) red[tid >> 5] = mx;
+    __syncthreads();
+    mx = red[0];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) mx = red[w] > mx ? red[w] : mx;
+    const int e = exp_above(__longlong_as_double((long long)mx));
+    if (tid == 0) exps[(long long)b * n + row] = e;
+    __nv_bfloat16* dst = planes + (long long)b * plane_bs + (long long)row * lld;
+    const long long pstride = (long long)n * lld;
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+        const int j = 4 * (tid + 256 * g);
+        if (j >= n) continue;
+        long long G[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) G[u] = scaled_int(v[g][u], e) + goff;
+#pragma unroll 1
+        for (int t = 0; t < k; ++t) {
+            uint2 w;
+            w.x = digit_bits(G[0], t) | (digit_bits(G[1], t) << 16);
+            w.y = digit_bits(G[2], t) | (digit_bits(G[3], t) << 16);
+            *reinterpret_cast<uint2*>(dst + (long long)t * pstride + j) = w;
+        }
     }
 }
 
@@ -607,6 +674,14 @@ mpps_status launch_slice_rows(const double* M, long long bs, int n, int batch, i
     }
     if (n < 256) {
         k_slice_rows<<<dim3((n + 7) / 8, batch), 256, 0, st>>>(M, bs, n, k, goff, pl, pbs, lld, exps);
+    } else if (n <= 4096 && n % 4 == 0 && ((uintptr_t)M & 15) == 0 && bs % 2 == 0) {
+        const dim3 g(n, batch);
+        if (n <= 1024)
+            k_slice_rows_blk4<1><<<g, 256, 0, st>>>(M, bs, n, k, goff, pl, pbs, lld, exps);
+        else if (n <= 2048)
+            k_slice_rows_blk4<2><<<g, 256, 0, st>>>(M, bs, n, k, goff, pl, pbs, lld, exps);
+        else
+            k_slice_rows_blk4<4><<<g, 256, 0, st>>>(M, bs, n, k, goff, pl, pbs, lld, exps);
     } else if (n <= 4096) {
         const dim3 g(n, batch);
         if (n <= 512)
