@@ -32,6 +32,9 @@ sys.path.insert(0, ROOT)
 METRIC = "p(A) evals/s and TFLOP/s, mixed vs fixed FP64 PS, at equal 1-norm rel. error"
 NORMS = (0.5, 4.0, 32.0)
 C2_FORMATS = ("fp64", "bf16x3", "tf32", "bf16")
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_gemm_f64e<9> launch at n = 1024
+# (profiles/gemm_f64e_n1024_bench.md): 38.16 MB + 0.59 MB
+F64E_N1024_DRAM_BYTES = 38.75e6
 SEED = 2
 
 
@@ -381,8 +384,16 @@ def main():
         kern = ("k_gemm_f64e (tcgen05 kind::f16, exact bf16 slice products; achieved counts "
                 "executed bf16 flops)" if dom == mpps.PROF_GEMM_F64E else "k_gemm_tc (tcgen05)")
     step_ms_tot = results[head]["ms_per_step"] * args.steps
+    # DRAM bytes (read + write) of one launch of the dominant kernel, from the ncu capture
+    # summarised in profiles/ (null when no capture of the current kernel at this size exists)
+    traffic, traffic_src = None, None
+    if dom == mpps.PROF_GEMM_F64E and n == 1024:
+        traffic = F64E_N1024_DRAM_BYTES
+        traffic_src = "profiles/gemm_f64e_n1024_bench.md (one power-product launch)"
     roofline = {"bound": "tensor", "kernel": kern, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "peak_source": src,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                "traffic_unit": "bytes per launch", "traffic_source": traffic_src,
+                "peak_source": src,
                 "share_of_step": ms_tot / step_ms_tot, "launches_per_step": launches // args.steps}
     for p in order:
         results[p].pop("_prof")
