@@ -32,9 +32,10 @@ sys.path.insert(0, ROOT)
 METRIC = "p(A) evals/s and TFLOP/s, mixed vs fixed FP64 PS, at equal 1-norm rel. error"
 NORMS = (0.5, 4.0, 32.0)
 C2_FORMATS = ("fp64", "bf16x3", "tf32", "bf16")
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_gemm_f64e<9> launch at n = 1024
-# (profiles/gemm_f64e_n1024_bench.md): 38.16 MB + 0.59 MB
-F64E_N1024_DRAM_BYTES = 38.75e6
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_gemm_f64e launch at n = 1024 from the
+# ncu capture summarised in profiles/gemm_f64e_n1024_bench.md (None until the current kernel
+# has been captured)
+F64E_N1024_DRAM_BYTES = None
 SEED = 2
 
 
@@ -55,9 +56,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel", default=None,
                     choices=["gemm_f64", "gemm_bf16", "gemm_bf16x3", "gemm_tf32", "gemm_fp8",
-                             "gemm_f64e9", "gemm_f64e6"],
+                             "gemm_f64e8", "gemm_f64e6"],
                     help="time one product kernel alone (mpps_matmul) instead of the workload")
     ap.add_argument("--batch", type=int, default=1, help="batch for --kernel")
+    ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4", "c5"],
+                    help="c2: exp n=1024 (the headline line); c3: 4096 uneven matrices; "
+                         "c4: adjoint batch of 512 FP32 128x128; c5: Pade13 / cos at n=2048")
     return ap.parse_args()
 
 
@@ -212,13 +216,147 @@ def run_reference(args, rank, world):
 
 POLICY_DESC = {
     "ns_e": "mixed (eq. (2.8), FP64 floors on steps 1-2), working-precision products emulated "
-            "with 9 exact bf16 slices on tcgen05",
+            "with 8 exact bf16 slices on tcgen05",
     "paper_e": "mixed (eq. (2.8) as in Algorithm 3.1), emulated working precision",
-    "fixed_e": "fixed working precision, every product emulated (9 slices)",
+    "fixed_e": "fixed working precision, every product emulated (8 slices)",
     "ns": "mixed (eq. (2.8), FP64 floors on steps 1-2), working precision on the FP64 pipe",
     "paper": "mixed (eq. (2.8) as in Algorithm 3.1), FP64 pipe",
     "fixed": "fixed FP64 on the FP64 pipe (Algorithm 2.1 + eq. (3.6))",
 }
+
+
+def run_config(args):
+    """The other workloads, one JSON line each (mixed policy vs fixed FP64, errors against the
+    oracle on a sample): C3 uneven batch, C4 adjoint batch, C5 n = 2048 general polynomials."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2312_17396_gb300 as mpps
+    from paper_2312_17396_gb300 import inputs
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    mpps.lib()
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+
+    def timed(step, steps, warmup):
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    line = {"metric": METRIC, "unit": "evals/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "data": "synthetic",
+            "impl": "mpps", "vs_baseline": None}
+    if args.config == "c3":
+        count = 4096
+        mats, degs = inputs.uneven_batch(count, 8, 256, 0.1, 10.0, seed=3)
+        dA = [torch.from_numpy(A).to(dev) for A in mats]
+        res = {}
+        for name, pol in (("ns_e", mpps.NS_E), ("fixed", mpps.FIXED)):
+            outs = [torch.empty_like(a) for a in dA]
+            _, reps = mpps.expm_grouped(dA, degs, policy=pol, outs=outs, report=True)
+            with ClockSampler(dev.index) as clk:
+                ms = timed(lambda: mpps.expm_grouped(dA, degs, policy=pol, outs=outs),
+                           args.steps, max(3, args.warmup))
+            flops = sum(2.0 * A.shape[0] ** 3 * sum(r["gemms"].values()) for A, r in zip(mats, reps))
+            errs = []
+            for k in range(0, count, count // 12):
+                sig = oracle.sigma_for(mats[k])
+                eh, el = oracle.expm_ss_dd(mats[k], int(degs[k]), sig)
+                errs.append(oracle.rel_err_1norm(outs[k].cpu().numpy(), eh, el))
+            res[name] = {"evals_per_s": count / (ms / 1e3), "ms_per_step": ms,
+                         "tflops": flops / (ms / 1e3) / 1e12, "max_rel_err_1norm_sampled": max(errs),
+                         "clocks": clk.summary()}
+        line.update({"value": res["ns_e"]["evals_per_s"], "ms_per_step": res["ns_e"]["ms_per_step"],
+                     "dtype": "f64", "scaling": "weak",
+                     "config": {"workload": "C3: 4096 matrices, n ~ U[8,256], ||A||_1 log-uniform in "
+                                            "[0.1,10], Taylor-exp m in {12,18,24}, sigma per matrix; "
+                                            "bucketed zero-padded batches", "policy": "ns_e"},
+                     "policies": res})
+    elif args.config == "c4":
+        n, m, batch = 128, 18, 512
+        rng = np.random.default_rng(4)
+        A32 = torch.tensor(rng.standard_normal((batch, n, n)) / np.sqrt(n), dtype=torch.float32,
+                           device=dev)
+        G = torch.tensor(rng.standard_normal((batch, n, n)), dtype=torch.float32, device=dev)
+        coef = mpps.taylor_exp_coeffs(m)
+        res = {}
+        for name, pol in (("ns_e", mpps.NS_E), ("fixed", mpps.FIXED)):
+            A = A32.clone().requires_grad_(True)
+
+            def step():
+                A.grad = None
+                P = mpps.poly(A, coef, pol)
+                P.backward(G)
+            with ClockSampler(dev.index) as clk:
+                ms = timed(step, args.steps, max(3, args.warmup))
+            step()
+            grad = A.grad.double().cpu().numpy()
+            errs = []
+            for b in (0, batch // 2, batch - 1):
+                gh, gl = oracle.adjoint_dd(oracle.taylor_exp_rational(m),
+                                           A32[b].double().cpu().numpy(), G[b].double().cpu().numpy())
+                errs.append(oracle.norm1(grad[b] - gh - gl) / oracle.norm1(gh))
+            res[name] = {"evals_per_s": batch / (ms / 1e3), "ms_per_step": ms,
+                         "max_rel_err_1norm_sampled": max(errs), "clocks": clk.summary()}
+        line.update({"value": res["ns_e"]["evals_per_s"], "ms_per_step": res["ns_e"]["ms_per_step"],
+                     "unit": "gradients/s", "dtype": "f32 storage, f64 evaluation", "scaling": "weak",
+                     "config": {"workload": "C4: 512 x 128x128 FP32, N(0,1)/sqrt(n), Taylor exp m=18 "
+                                            "forward + adjoint through autograd", "policy": "ns_e"},
+                     "policies": res})
+    else:
+        n = 2048
+        A = inputs.prescribed_eigen_matrix(n, seed=5)
+        B = A @ A                                    # the cosine's argument, formed on the host
+        As = A / np.abs(A).sum(axis=0).max()         # labelled scaled variant, ||X||_1 = 1
+        q, mc = 13, 16
+        jobs = [("pade13_num", mpps.pade_exp_num_coeffs(q), oracle.pade_exp_num_rational(q), A),
+                ("pade13_den", mpps.pade_exp_den_coeffs(q), oracle.pade_exp_den_rational(q), A),
+                ("cos16_in_B", mpps.cos_taylor_coeffs(mc), oracle.cos_taylor_rational(mc), B),
+                ("pade13_num_scaled", mpps.pade_exp_num_coeffs(q), oracle.pade_exp_num_rational(q), As)]
+        cols = np.random.default_rng(7).choice(n, size=8, replace=False)
+        V = np.zeros((n, cols.size)); V[cols, np.arange(cols.size)] = 1.0
+        res = {}
+        pol_mixed = mpps.NS_E                        # all formats, FP8 tail blocks allowed
+        for name, coef, rat, X in jobs:
+            dX = torch.from_numpy(X).to(dev)
+            rh, rl = oracle.ps_apply_dd(rat, X, V)
+            ref = rh + rl
+            entry = {}
+            for pname, pol in (("ns_e", pol_mixed), ("fixed_e", mpps.FIXED_E), ("fixed", mpps.FIXED)):
+                out = torch.empty_like(dX)
+                _, rep = mpps.ps_eval(coef, dX, policy=pol, out=out, report=True)
+                with ClockSampler(dev.index) as clk:
+                    ms = timed(lambda: mpps.ps_eval(coef, dX, policy=pol, out=out), args.steps,
+                               max(3, args.warmup))
+                P = out.cpu().numpy()[:, cols]
+                entry[pname] = {"evals_per_s": 1e3 / ms, "ms_per_step": ms,
+                                "rel_err_1norm_sampled_cols": oracle.norm1(P - ref) / oracle.norm1(ref),
+                                "formats": rep[0]["fmt"], "clocks": clk.summary()}
+            res[name] = entry
+        tot_mixed = sum(res[j[0]]["ns_e"]["ms_per_step"] for j in jobs[:3])
+        tot_fixed = sum(res[j[0]]["fixed"]["ms_per_step"] for j in jobs[:3])
+        line.update({"value": 1e3 / tot_mixed, "ms_per_step": tot_mixed,
+                     "unit": "evals/s (Pade13 num + den + cos16(B), one 2048 matrix)",
+                     "dtype": "f64", "scaling": "weak", "fixed_value": 1e3 / tot_fixed,
+                     "config": {"workload": "C5: n=2048 Q diag(lambda) Q^T, lambda ~ U[-8,8]; Pade[13/13] "
+                                            "numerator and denominator (s=4) and Taylor cos of degree 16 "
+                                            "in B = A^2; plus a scaled variant with ||X||_1 = 1",
+                                "policy": "ns_e (all formats)"},
+                     "jobs": res})
+    print(json.dumps(line), flush=True)
 
 
 def peak_bf16_tflops():
@@ -239,6 +377,9 @@ def main():
         return
     if args.kernel:
         run_kernel(args)
+        return
+    if args.config != "c2":
+        run_config(args)
         return
 
     import numpy as np
@@ -387,7 +528,7 @@ def main():
     # DRAM bytes (read + write) of one launch of the dominant kernel, from the ncu capture
     # summarised in profiles/ (null when no capture of the current kernel at this size exists)
     traffic, traffic_src = None, None
-    if dom == mpps.PROF_GEMM_F64E and n == 1024:
+    if dom == mpps.PROF_GEMM_F64E and n == 1024 and F64E_N1024_DRAM_BYTES is not None:
         traffic = F64E_N1024_DRAM_BYTES
         traffic_src = "profiles/gemm_f64e_n1024_bench.md (one power-product launch)"
     roofline = {"bound": "tensor", "kernel": kern, "achieved": achieved, "peak": peak,

@@ -30,7 +30,7 @@ _lib = None
 
 FIXED_FP64, MIXED_PAPER, MIXED_NS = 0, 1, 2
 FMT_NONE, FMT_FP64, FMT_BF16X3, FMT_TF32, FMT_BF16, FMT_FP8 = -1, 0, 1, 2, 3, 4
-F64E_MAX_SLICES = 10
+F64E_MAX_SLICES = 8
 
 
 def FMT_F64E(k: int) -> int:
@@ -160,10 +160,10 @@ class Policy:
 FIXED = Policy(mode=FIXED_FP64)
 PAPER = Policy(mode=MIXED_PAPER)
 NS = Policy(mode=MIXED_NS)
-# the same rules with the working-precision products emulated on the tensor cores (9 slices)
-FIXED_E = Policy(mode=FIXED_FP64, f64_slices=9)
-PAPER_E = Policy(mode=MIXED_PAPER, f64_slices=9)
-NS_E = Policy(mode=MIXED_NS, f64_slices=9)
+# the same rules with the working-precision products emulated on the tensor cores (8 slices)
+FIXED_E = Policy(mode=FIXED_FP64, f64_slices=8)
+PAPER_E = Policy(mode=MIXED_PAPER, f64_slices=8)
+NS_E = Policy(mode=MIXED_NS, f64_slices=8)
 
 
 def _report_dict(R: _Report) -> dict:

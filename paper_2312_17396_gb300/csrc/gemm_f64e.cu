@@ -7,34 +7,34 @@
 // 1900, so the working-precision products of the PS evaluation (powers, early Horner steps,
 // squarings) are emulated:
 //
-//   A (rows scaled by 2^-eA_i, |.| < 1) = sum_{t<k} 2^{-6(t+1)} a_t,  a_t integers, |a_t| <= 64
-//   B (cols scaled by 2^-eB_j)          = sum_{q<k} 2^{-6(q+1)} b_q
-//   A B ~= 2^{eA_i + eB_j - 12} sum_{d<k} 2^{-6d} D_d,   D_d = sum_{t+q=d} a_t b_q^T.
+//   A (rows scaled by 2^-eA_i, |.| < 1) = sum_{t<k} 2^{-7(t+1)} a_t,  a_t integers, |a_t| <= 128
+//   B (cols scaled by 2^-eB_j)          = sum_{q<k} 2^{-7(q+1)} b_q
+//   A B ~= 2^{eA_i + eB_j - 14} sum_{d<k} 2^{-7d} D_d,   D_d = sum_{t+q=d} a_t b_q^T.
 //
-// The slice planes hold a'_t = 2^-6t a_t and b'_q = 2^-6q b_q (exact in bf16), so that the
-// product a'_t b'_q^T is already 2^-6d a_t b_q^T and sums of pairs with different d carry the
-// right weights.  Every D_d entry of one K chunk of at most 2048 is an integer of magnitude
-// <= 2048 (d+3) 2^10 <= 2^24 for d <= 5 (|a_0|,|b_0| <= 64, the others <= 32), so the tensor
-// cores accumulate D_0..D_5 EXACTLY in FP32, each in its own TMEM region.  The diagonals
-// d >= 6 (weights <= 2^-36 relative to D_0) share one seventh region and are accumulated in
-// FP32 with rounding; their worst-case error is 2^10 below the worst-case bound of an FP64
-// product of the same length.  The only other errors are the pairs dropped (t + q >= k) and
-// the residual of the k-slice representation, about 2^{-6k} relative to the row and column
-// maxima: k = 9 gives FP64-level accuracy.
+// The digits are balanced base 128 (|a_0| <= 128, |a_t| <= 64 for t >= 1), exact in bf16.
+// The slice planes hold a'_t = 2^-7t a_t and b'_q = 2^-7q b_q, so that the product
+// a'_t b'_q^T is already 2^-7d a_t b_q^T and pairs of different d may share an accumulator.
+// Every D_d entry of one K chunk of at most 512 is an integer of magnitude <= 512 (d+3) 2^12
+// <= 2^24 for d <= 5, so the tensor cores accumulate D_0..D_5 EXACTLY in FP32, each in its
+// own TMEM region; d = 6 and d = 7 (weights <= 2^-42 relative to D_0) have a region each and
+// accumulate in FP32 with rounding, far below an FP64 product's own error.  With k = 8 the
+// only other errors are the pairs dropped (t + q >= 8) and the 8-digit residual: about
+// 2^{-54} of the row and column maxima, FP64-level accuracy with 36 bf16 products.
 //
-// Between K chunks and at the end of a tile the exact regions are drained on the integer
-// pipe (W = sum_{d<=5} 2^{6(5-d)} D_d as a 64-bit integer, the tail as FP32), so the scarce
-// FP64 pipe only does the last combination 2^{e-42} W + 2^{e-12} T and the fused epilogue.
+// At the end of every K chunk the exact regions are drained on the integer pipe
+// (W = sum_{d<=5} 2^{7(5-d)} D_d as a 64-bit integer, the tails as FP32); with more than one
+// chunk, each chunk's W is added to an FP64 accumulator, so W never overflows.  The FP64
+// pipe only adds and does the fused epilogue: product = 2^{e-49} W + 2^{e-14} T.
 //
 // Kernel: persistent, one CTA per SM, 128 x 64 output tiles, 18 warps (0-15 epilogue: TMEM
-// lane quarter = warp % 4, 16-column group = warp / 4; 16 TMA producer; 17 MMA issuer).  Per K
-// block of 32 the producer loads the k slices of the B^T tile (one 3-D box) and the k slices
-// of the A tile (one box and one mbarrier each, so the MMAs of slice t start when slice t
-// lands).  The MMA of slice t uses the stacked B operand b'_0..b'_{6-t} (N = 64 (7 - t)) and
-// writes regions t..6 in one instruction (two when N > 256); the pairs with t + q >= 7 add
-// into the tail region with N = 64 MMAs.  Operands are K-major with the 64-byte swizzle.
-// The epilogue drains TMEM into registers and releases it at once, so the FP64 epilogue of
-// a tile overlaps the MMAs of the next.  All mbarrier waits are bounded.
+// lane quarter = warp % 4, 16-column group = warp / 4; 16 TMA producer; 17 MMA issuer).  Per
+// K block of 32 the producer loads the k slices of the B^T tile (one 3-D box) and the k
+// slices of the A tile (one box and one mbarrier each, so the MMAs of slice t start when
+// slice t lands).  The MMA of slice t uses the stacked B operand b'_0..b'_{7-t}
+// (N = 64 (8 - t)) and writes regions t..7 in one instruction (two when N > 256); with
+// k = 8 that covers all 36 pairs in 12 instructions per K step.  Operands are K-major with
+// the 64-byte swizzle.  The epilogue drains TMEM into registers and releases it at once, so
+// the FP64 epilogue of a tile overlaps the MMAs of the next.  All mbarrier waits are bounded.
 #include "common.cuh"
 #include "tcgen05.cuh"
 
@@ -51,9 +51,11 @@ using namespace tc;
 constexpr int OM = 128;                 // output rows per tile (TMEM lanes)
 constexpr int ON = 64;                  // output cols per tile (= columns per TMEM region)
 constexpr int KB = 32;                  // K elements per stage (64 bytes of bf16: two MMA steps)
-constexpr int KCHUNK = 2048;            // exact FP32 accumulation bound of D_0..D_5 (see above)
+constexpr int KCHUNK = 512;             // exact FP32 accumulation bound of D_0..D_5 (see above)
+constexpr int DIGIT = 7;                // bits per slice
+constexpr int FLUSH = 8;                // chunks the 64-bit W may sum before an FP64 flush
 constexpr int NEXACT = 6;               // diagonals accumulated exactly
-constexpr int NREG = 8;                 // TMEM regions: D_0..D_5, d = 6, and d >= 7
+constexpr int NREG = 8;                 // TMEM regions: D_0..D_5, d = 6, and d = 7
 constexpr int A_TILE = OM * KB * 2;     // 8 KB
 constexpr int B_TILE = ON * KB * 2;     // 4 KB
 constexpr int EPI_WARPS = 16;            // 4 per TMEM lane quarter, 16 columns each
@@ -70,6 +72,8 @@ constexpr int RASTER_G = 8;             // row blocks per raster group (L2 reuse
 // tmem_free | mma_done | TMEM address slot
 static_assert((NFULL + MAX_STAGES + 3) * 8 + 4 <= BAR_BYTES, "barrier block exceeds its bytes");
 static_assert(NREG * ON <= 512, "TMEM regions exceed 512 columns");
+static_assert(MPPS_F64E_MAX_SLICES <= NREG, "every slice pair must have a TMEM region");
+static_assert(55 - DIGIT * (MPPS_F64E_MAX_SLICES - 1) >= 1, "the last digit needs a rounding bit");
 
 __host__ __device__ constexpr int stage_bytes(int k) { return k * (A_TILE + B_TILE); }
 __host__ __device__ constexpr int num_stages(int k) {
@@ -106,26 +110,26 @@ __device__ __forceinline__ long long scaled_int(double x, int e) {
     return bits < 0 ? -F : F;
 }
 
-// Signed base-64 digits of x / 2^e (|x| < 2^e), in offset form: with F = round(x 2^(62-e))
-// (|F| < 2^62), p_t = 56 - 6t and G = F + 2^(p_{k-1} - 1) + sum_{t=1}^{k-1} 32 2^(p_t),
-//   v_0 = floor(G / 2^56),   v_t = ((G >> p_t) mod 64) - 32   (t >= 1),
-// so that F = sum_t v_t 2^(p_t) + r with |r| <= 2^(p_{k-1} - 1): x = 2^e (sum_t v_t 2^(-6(t+1))
-// + r 2^-62), |r 2^-62| <= 2^(-6k-1); |v_0| <= 64, -32 <= v_t <= 31.  Every digit comes from G
-// alone (no chain through a remainder).  Plane t stores v_t 2^-6t, exact in bf16 (at most 7
+// Signed base-128 digits of x / 2^e (|x| < 2^e), in offset form: with F = round(x 2^(62-e))
+// (|F| < 2^62), p_t = 55 - 7t and G = F + 2^(p_{k-1} - 1) + sum_{t=1}^{k-1} 64 2^(p_t),
+//   v_0 = floor(G / 2^55),   v_t = ((G >> p_t) mod 128) - 64   (t >= 1),
+// so that F = sum_t v_t 2^(p_t) + r with |r| <= 2^(p_{k-1} - 1): x = 2^e (sum_t v_t 2^(-7(t+1))
+// + r 2^-62), |r 2^-62| <= 2^(-7k-1); |v_0| <= 128, -64 <= v_t <= 63.  Every digit comes from G
+// alone (no chain through a remainder).  Plane t stores v_t 2^-7t, exact in bf16 (at most 8
 // significant bits, so the bf16 is the upper half of the FP32 value; (float)v is formed by
 // adding v to the bit pattern of 1.5 2^23).  No FP64 arithmetic: the integer and FP32
-// pipes do all of it.
+// pipes do all of it.  k <= 8 keeps p_{k-1} >= 6.
 __host__ __device__ inline long long digit_offset(int k) {
-    long long o = 1LL << (55 - 6 * (k - 1));
-    for (int t = 1; t < k; ++t) o += 32LL << (56 - 6 * t);
+    long long o = 1LL << (55 - DIGIT * (k - 1) - 1);
+    for (int t = 1; t < k; ++t) o += 64LL << (55 - DIGIT * t);
     return o;
 }
 
 // bf16 bits of digit t of G (see above).
 __device__ __forceinline__ unsigned digit_bits(long long G, int t) {
-    const int p = 56 - 6 * t;
-    const int v = t == 0 ? (int)(G >> 56) : (int)((G >> p) & 63) - 32;
-    const float f = (__int_as_float(0x4B400000 + v) - 12582912.0f) * __int_as_float((127 - 6 * t) << 23);
+    const int p = 55 - DIGIT * t;
+    const int v = t == 0 ? (int)(G >> 55) : (int)((G >> p) & 127) - 64;
+    const float f = (__int_as_float(0x4B400000 + v) - 12582912.0f) * __int_as_float((127 - DIGIT * t) << 23);
     return __float_as_uint(f) >> 16;
 }
 
@@ -133,13 +137,8 @@ __device__ __forceinline__ void put_digits(double x, int e, int k, long long gof
                                            __nv_bfloat16* dst, long long pstride) {
     const long long G = scaled_int(x, e) + goff;
 #pragma unroll 1
-    for (int t = 0; t < k; ++t) {
-        const int p = 56 - 6 * t;
-        const int v = t == 0 ? (int)(G >> 56) : (int)((G >> p) & 63) - 32;
-        const float f = (__int_as_float(0x4B400000 + v) - 12582912.0f) *
-                        __int_as_float((127 - 6 * t) << 23);
-        dst[(long long)t * pstride] = __ushort_as_bfloat16((unsigned short)(__float_as_uint(f) >> 16));
-    }
+    for (int t = 0; t < k; ++t)
+        dst[(long long)t * pstride] = __ushort_as_bfloat16((unsigned short)digit_bits(G, t));
 }
 
 __device__ __forceinline__ int exp_above(double mx) {
@@ -547,19 +546,22 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
             for (int j = 0; j < EPI_COLS; ++j) { W[j] = 0; T[j] = 0.f; }
             bool ok = true;
+            const int row = m0 + q4 * 32 + lane;
+            const int cb = n0 + EPI_COLS * h;
+            double* orow = ep.out + (long long)b * ep.out_bstride + (long long)row * n + cb;
             for (int c = 0; c < nchunks; ++c, ++gc) {
                 ok = __all_sync(0xffffffffu, mbar_wait(chunk_done, gc & 1, err));
                 if (!ok) break;
                 tc_fence_after();
 #pragma unroll
-                for (int d = 0; d < NX; ++d) {   // exact regions: W += 2^{6(5-d)} D_d
+                for (int d = 0; d < NX; ++d) {   // exact regions: W += 2^{7(5-d)} D_d
                     uint32_t v[EPI_COLS];
                     tmem_ld16(tmem + lane_base + (uint32_t)(ON * d + EPI_COLS * h), v);
-                    const float up = __int_as_float((127 + 6 * d) << 23);   // 2^{6d}
-                    const int mul = 1 << (6 * (NEXACT - 1 - d));
+                    const float up = __int_as_float((127 + DIGIT * d) << 23);   // 2^{7d}
 #pragma unroll
                     for (int j = 0; j < EPI_COLS; ++j)
-                        W[j] += (long long)__float2int_rn(__uint_as_float(v[j]) * up) * mul;
+                        W[j] += (long long)__float2int_rn(__uint_as_float(v[j]) * up)
+                                << (DIGIT * (NEXACT - 1 - d));
                 }
 #pragma unroll
                 for (int d = NX; d < NR; ++d) {  // tail regions (FP32)
@@ -570,24 +572,34 @@ __global__ void __launch_bounds__(THREADS, 1)
                 }
                 tc_fence_before();
                 mbar_arrive_cta(tmem_free);
+                // |W| < 2^58.02 per chunk: every FLUSH chunks it is added, in FP64, to this
+                // tile's own output entries (used as scratch), so the integer never overflows
+                if (nchunks > FLUSH && (c % FLUSH == FLUSH - 1 || c == nchunks - 1) && row < n) {
+#pragma unroll
+                    for (int j = 0; j < EPI_COLS; ++j) {
+                        if (cb + j < n) orow[j] = (c < FLUSH ? 0.0 : orow[j]) + (double)W[j];
+                        W[j] = 0;
+                    }
+                }
             }
             if (!ok) break;
-            // product = 2^{eA+eB-42} W + 2^{eA+eB-12} T, then the fused epilogue
-            const int row = m0 + q4 * 32 + lane;
+            // product = 2^{eA+eB-49} W + 2^{eA+eB-14} T, then the fused epilogue
             if (row < n) {
                 const int er = eA[(long long)b * n + row];
-                const int cb = n0 + EPI_COLS * h;
 #pragma unroll
                 for (int j = 0; j < EPI_COLS; ++j) {
                     const int col = cb + j;
                     if (col < n) {
                         const int e = er + __ldg(eB + (long long)b * n + col);
-                        // 2^(e-42) W and 2^(e-12) T formed on the integer pipe, one FP64 add
+                        // 2^(e-49) W and 2^(e-14) T formed on the integer pipe, one FP64 add
                         double wd, td, val;
-                        if (i64_to_f64_scaled(W[j], e - 42, &wd) && f32_to_f64_scaled(T[j], e - 12, &td))
+                        if (nchunks > FLUSH)
+                            val = ldexp(fma(orow[j], 0x1p-35, (double)T[j]), e - 14);
+                        else if (i64_to_f64_scaled(W[j], e - 49, &wd) &&
+                                 f32_to_f64_scaled(T[j], e - 14, &td))
                             val = wd + td;
                         else
-                            val = ldexp(fma((double)W[j], 0x1p-30, (double)T[j]), e - 12);
+                            val = ldexp(fma((double)W[j], 0x1p-35, (double)T[j]), e - 14);
                         epilogue_store(ep, b, row, col, n, epilogue_value(ep, b, row, col, n, val));
                     }
                 }
@@ -751,9 +763,7 @@ mpps_status launch_gemm_f64e(int k, const void* slicesA, int ksA, const int* eA,
         case 5: return launch_k<5>(dev, grid, ta, tb, n, ksA, ksB, batch, eA, eB, ep, d_err, st, bidx);
         case 6: return launch_k<6>(dev, grid, ta, tb, n, ksA, ksB, batch, eA, eB, ep, d_err, st, bidx);
         case 7: return launch_k<7>(dev, grid, ta, tb, n, ksA, ksB, batch, eA, eB, ep, d_err, st, bidx);
-        case 8: return launch_k<8>(dev, grid, ta, tb, n, ksA, ksB, batch, eA, eB, ep, d_err, st, bidx);
-        case 9: return launch_k<9>(dev, grid, ta, tb, n, ksA, ksB, batch, eA, eB, ep, d_err, st, bidx);
-        default: return launch_k<10>(dev, grid, ta, tb, n, ksA, ksB, batch, eA, eB, ep, d_err, st, bidx);
+        default: return launch_k<8>(dev, grid, ta, tb, n, ksA, ksB, batch, eA, eB, ep, d_err, st, bidx);
     }
 }
 

@@ -277,18 +277,18 @@ def test_matmul_f64e_exact_on_small_integers(mpps, n):
     rng = np.random.default_rng(300 + n)
     A = rng.integers(-63, 64, size=(2, n, n)).astype(np.float64)
     B = rng.integers(-63, 64, size=(2, n, n)).astype(np.float64)
-    for k in (1, 9):
+    for k in (1, 8):
         C = host(mpps.matmul(dev(A), dev(B), f"f64e{k}"))
         assert np.array_equal(C, A @ B), k
 
 
 @pytest.mark.parametrize("n", [1, 3, 17, 64, 130, 257, 1100])
 def test_matmul_f64e_vs_oracle(mpps, n):
-    """9 slices: FP64-level error (n up to several 128 x 64 tiles with ragged tails)."""
+    """8 slices: FP64-level error (n up to several 128 x 64 tiles with ragged tails)."""
     rng = np.random.default_rng(400 + n)
     A = rng.standard_normal((1, n, n)); B = rng.standard_normal((1, n, n))
     A[0, 0, :] *= 1e-9                      # a row far below the others: row scaling matters
-    C = host(mpps.matmul(dev(A), dev(B), "f64e9"))[0]
+    C = host(mpps.matmul(dev(A), dev(B), "f64e8"))[0]
     ch, cl = oracle.matmul_dd(A[0], None, B[0], None)
     err = np.abs(C - ch - cl)
     absprod = np.abs(A[0]) @ np.abs(B[0])
@@ -308,7 +308,7 @@ def test_matmul_f64e_extreme_magnitudes(mpps, shift):
     rng = np.random.default_rng(77)
     A0 = rng.standard_normal((n, n)); B0 = rng.standard_normal((n, n))
     A = np.ldexp(A0, shift[0]); B = np.ldexp(B0, shift[1])
-    C = host(mpps.matmul(dev(A[None]), dev(B[None]), "f64e9"))[0]
+    C = host(mpps.matmul(dev(A[None]), dev(B[None]), "f64e8"))[0]
     ch, cl = oracle.matmul_dd(A0, None, B0, None)
     ref = np.ldexp(ch, shift[0] + shift[1]); refl = np.ldexp(cl, shift[0] + shift[1])
     rmax = np.abs(A0).max(axis=1)[:, None]; cmax = np.abs(B0).max(axis=0)[None, :]
@@ -327,7 +327,7 @@ def test_matmul_f64e_multichunk_sampled(mpps):
     rng = np.random.default_rng(2100)
     A = rng.standard_normal((n, n)); B = rng.standard_normal((n, n))
     A[5, :] *= 1e-7
-    C = host(mpps.matmul(dev(A[None]), dev(B[None]), "f64e9"))[0]
+    C = host(mpps.matmul(dev(A[None]), dev(B[None]), "f64e8"))[0]
     cols = rng.choice(n, size=8, replace=False)
     ref = (A.astype(np.longdouble) @ B[:, cols].astype(np.longdouble))
     err = np.abs(C[:, cols].astype(np.longdouble) - ref).astype(np.float64)
@@ -345,10 +345,10 @@ def test_matmul_f64e_error_falls_with_slices(mpps):
     ch, cl = oracle.matmul_dd(A[0], None, B[0], None)
     scale = np.linalg.norm(np.abs(A[0]) @ np.abs(B[0]))
     prev = None
-    for k in range(1, 10):
+    for k in range(1, 9):
         C = host(mpps.matmul(dev(A), dev(B), f"f64e{k}"))[0]
         err = np.linalg.norm(C - ch - cl) / scale
-        assert err <= 2.0 ** (3 - 6 * k), (k, err)
+        assert err <= 2.0 ** (2 - 7 * k), (k, err)
         if prev is not None and k < 9:
             assert err < prev
         prev = err
