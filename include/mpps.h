@@ -67,11 +67,13 @@ typedef enum {
     MPPS_FMT_FP8 = 4
 } mpps_format;
 
-/* FP64 products emulated on the BF16 tensor cores with k exact integer slices per operand,
- * 7 bits each (MPPS_FMT_F64E(k), 1 <= k <= MPPS_F64E_MAX_SLICES): error below 2^(2-7k)
- * relative to the row and column maxima of the operands; k = 8 is FP64-level.  Cost
- * k(k+1)/2 BF16 products. */
-#define MPPS_F64E_MAX_SLICES 8
+/* FP64 products emulated on the BF16 tensor cores with exact integer slices of 7 bits
+ * (MPPS_FMT_F64E(k), 1 <= k <= MPPS_F64E_MAX_SLICES).  k <= 8: k slices per operand and the
+ * slice pairs of order t + q <= k - 1, k(k+1)/2 BF16 products, error below 2^(2-7k) relative
+ * to the row and column maxima of the operands (k = 8: FP64-level for products of moderate
+ * length).  k = 9: the 8 slices with the pairs of order t + q <= 8 as well, 43 BF16 products,
+ * error below 2^-55 (below an FP64 product's at every length). */
+#define MPPS_F64E_MAX_SLICES 9
 #define MPPS_FMT_F64E(k) (16 + (k))
 #define MPPS_FMT_IS_F64E(f) ((f) > 16 && (f) <= 16 + MPPS_F64E_MAX_SLICES)
 #define MPPS_F64E_SLICES(f) ((f) - 16)

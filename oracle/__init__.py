@@ -327,7 +327,7 @@ def plan(m: int, n: int, norms, normY: float, mode: int = MODE_PAPER, tol: float
        With f64_slices = K > 0 the working precision is an emulated product with K slices
        (format F64E(K)) and the ladder continues after BF16X3 with F64E(k), k = 4..K-1,
        whose unit roundoff is taken as 2^(2-7k) (k slices of 7 bits; exact accumulation: no
-       n 2^-24 term).
+       n 2^-24 term), and 2^-55 for k = 9 (8 slices with the pairs of order 8).
     5. mode NS: steps i <= floor_steps stay in the working precision.  FIXED: every step.
     6. When s divides m, B_r = b_m I and step r is a scalar multiple of Y: no product
        (format NONE).
@@ -371,7 +371,7 @@ def plan(m: int, n: int, norms, normY: float, mode: int = MODE_PAPER, tol: float
                     break
             if not found:
                 for k in range(4, f64_slices):
-                    if 2.0 ** (2 - 7 * k) <= u[i]:
+                    if (2.0 ** (2 - 7 * k) if k <= 8 else 2.0 ** -55) <= u[i]:
                         f = FMT_F64E(k)
                         break
         fmt[i] = f

@@ -30,7 +30,7 @@ _lib = None
 
 FIXED_FP64, MIXED_PAPER, MIXED_NS = 0, 1, 2
 FMT_NONE, FMT_FP64, FMT_BF16X3, FMT_TF32, FMT_BF16, FMT_FP8 = -1, 0, 1, 2, 3, 4
-F64E_MAX_SLICES = 8
+F64E_MAX_SLICES = 9
 
 
 def FMT_F64E(k: int) -> int:

@@ -64,9 +64,11 @@ static const double kAcc = 0x1p-24;
 
 static bool is_low(int f) { return f >= MPPS_FMT_BF16X3 && f <= MPPS_FMT_FP8; }
 
-// Unit roundoff assigned to an emulated product with k slices of 7 bits: 2^(2-7k) (the slices
-// keep 7k bits below the row/column maxima; the constant covers the dropped pairs t + q >= k).
-static double u_f64e(int k) { return ldexp(1.0, 2 - 7 * k); }
+// Unit roundoff assigned to an emulated product F64E(k): 2^(2-7k) for k <= 8 slices of 7 bits
+// (the slices keep 7k bits below the row/column maxima; the constant covers the dropped pairs
+// t + q >= k); 2^-55 for k = 9 (8 slices, pairs up to order 8: the 2^-57 residual of each
+// operand dominates).
+static double u_f64e(int k) { return k <= 8 ? ldexp(1.0, 2 - 7 * k) : 0x1p-55; }
 
 static double unit_roundoff(int f) {
     if (MPPS_FMT_IS_F64E(f)) return u_f64e(MPPS_F64E_SLICES(f));

@@ -168,6 +168,10 @@ mpps_status launch_gemm_f64e(int k, const void* slicesA, int ksA, const int* eA,
                              int nmat, const Epilogue& ep, int* d_err, cudaStream_t st,
                              const int* bidx = nullptr);
 
+// Slice planes per operand of an emulated product MPPS_FMT_F64E(k): k, at most 8 (k = 9
+// adds slice pairs, not slices).
+inline int f64e_planes(int k) { return k < 8 ? k : 8; }
+
 // Element size in bytes of a low-precision operand copy.
 inline int low_elem_bytes(int fmt) {
     switch (fmt) {

@@ -63,7 +63,7 @@ constexpr int EPI_COLS = ON / (EPI_WARPS / 4);
 constexpr int THREADS = (EPI_WARPS + 2) * 32;
 static_assert(EPI_COLS == 16, "the drain loads 16 TMEM columns per thread");
 constexpr int MAX_STAGES = 8;
-constexpr int NFULL = MAX_STAGES * (MPPS_F64E_MAX_SLICES + 1);
+constexpr int NFULL = MAX_STAGES * (8 + 1);
 constexpr int BAR_BYTES = 1024;
 constexpr int SMEM_MAX = 232448;        // 227 KB of opt-in dynamic shared memory
 constexpr int SMEM_BUDGET = SMEM_MAX - 1024 - BAR_BYTES;
@@ -72,8 +72,9 @@ constexpr int RASTER_G = 8;             // row blocks per raster group (L2 reuse
 // tmem_free | mma_done | TMEM address slot
 static_assert((NFULL + MAX_STAGES + 3) * 8 + 4 <= BAR_BYTES, "barrier block exceeds its bytes");
 static_assert(NREG * ON <= 512, "TMEM regions exceed 512 columns");
-static_assert(MPPS_F64E_MAX_SLICES <= NREG, "every slice pair must have a TMEM region");
-static_assert(55 - DIGIT * (MPPS_F64E_MAX_SLICES - 1) >= 1, "the last digit needs a rounding bit");
+constexpr int MAX_PLANES = 8;           // slices per operand (F64E(9) adds pairs, not slices)
+static_assert(MAX_PLANES <= NREG, "every slice must start a TMEM region");
+static_assert(55 - DIGIT * (MAX_PLANES - 1) >= 1, "the last digit needs a rounding bit");
 
 __host__ __device__ constexpr int stage_bytes(int k) { return k * (A_TILE + B_TILE); }
 __host__ __device__ constexpr int num_stages(int k) {
@@ -396,10 +397,11 @@ __global__ void __launch_bounds__(THREADS, 1)
     k_gemm_f64e(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 int n, int ksA, int ksB, int batch, const int* __restrict__ eA,
                 const int* __restrict__ eB, Epilogue ep, int* err, const int* __restrict__ bidx) {
-    constexpr int S = num_stages(K);
-    constexpr int SB = stage_bytes(K);
-    constexpr int NR = K < NREG ? K : NREG;          // TMEM regions in use
-    constexpr int NX = K < NEXACT ? K : NEXACT;      // of which exact
+    constexpr int NP = K < MAX_PLANES ? K : MAX_PLANES;   // slices per operand
+    constexpr int S = num_stages(NP);
+    constexpr int SB = stage_bytes(NP);
+    constexpr int NR = NP < NREG ? NP : NREG;         // TMEM regions in use
+    constexpr int NX = NP < NEXACT ? NP : NEXACT;     // of which exact
     constexpr uint32_t TCOLS = tmem_cols(NR);
     static_assert(S >= 1, "a stage does not fit in shared memory");
 
@@ -424,7 +426,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
-            for (int i = 0; i <= K; ++i) mbar_init(&full[s * (K + 1) + i], 1);
+            for (int i = 0; i <= NP; ++i) mbar_init(&full[s * (NP + 1) + i], 1);
             mbar_init(&empty[s], 1);
         }
         mbar_init(chunk_done, 1);
@@ -453,12 +455,12 @@ __global__ void __launch_bounds__(THREADS, 1)
                 for (int kb = 0; kb < nkb; ++kb, ++g) {
                     if (g >= (uint32_t)S && !(ok = mbar_wait(&empty[s], ph ^ 1, err))) break;
                     uint8_t* st = smem + s * SB;
-                    uint64_t* f = full + s * (K + 1);
+                    uint64_t* f = full + s * (NP + 1);
                     const int kc = kb * KB;
-                    mbar_expect_tx(&f[0], (uint32_t)(K * B_TILE));
-                    tma_load_3d(st + K * A_TILE, &tmB, kc, n0, b * ksB, &f[0]);
+                    mbar_expect_tx(&f[0], (uint32_t)(NP * B_TILE));
+                    tma_load_3d(st + NP * A_TILE, &tmB, kc, n0, b * ksB, &f[0]);
 #pragma unroll
-                    for (int t = 0; t < K; ++t) {
+                    for (int t = 0; t < NP; ++t) {
                         mbar_expect_tx(&f[1 + t], (uint32_t)A_TILE);
                         tma_load_3d(st + t * A_TILE, &tmA, kc, m0, b * ksA + t, &f[1 + t]);
                     }
@@ -471,8 +473,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             bool landed = true;
             for (uint32_t gg = lo; gg < g && landed; ++gg) {
                 const int s = (int)(gg % (uint32_t)S);
-                for (int i = 0; i <= K && landed; ++i)
-                    landed = mbar_wait_quiet(&full[s * (K + 1) + i], (gg / S) & 1);
+                for (int i = 0; i <= NP && landed; ++i)
+                    landed = mbar_wait_quiet(&full[s * (NP + 1) + i], (gg / S) & 1);
             }
             if (!landed) atomicExch(err, 1);
         }
@@ -490,13 +492,13 @@ __global__ void __launch_bounds__(THREADS, 1)
                         if (!(ok = mbar_wait(tmem_free, (gc - 1) & 1, err))) break;
                         tc_fence_after();
                     }
-                    uint64_t* f = full + s * (K + 1);
+                    uint64_t* f = full + s * (NP + 1);
                     if (!(ok = mbar_wait(&f[0], ph, err))) break;
                     const uint32_t abase = ring + (uint32_t)(s * SB);
-                    const uint64_t da = sw64_desc(abase), db = sw64_desc(abase + K * A_TILE);
+                    const uint64_t da = sw64_desc(abase), db = sw64_desc(abase + NP * A_TILE);
                     const uint32_t acc0 = kin == 0 ? 0u : 1u;
 #pragma unroll
-                    for (int t = 0; t < K; ++t) {
+                    for (int t = 0; t < NP; ++t) {
                         if (!(ok = mbar_wait(&f[1 + t], ph, err))) break;
                         tc_fence_after();
 #pragma unroll
@@ -512,8 +514,9 @@ __global__ void __launch_bounds__(THREADS, 1)
                                              db + (uint64_t)((256 * 64 + kk * 32) >> 4),
                                              make_idesc(1, OM, N - 256), acc);
                             }
+                            // pairs of order NREG..K-1 (K = 9: t + q = 8) -> last region
 #pragma unroll
-                            for (int q = (NREG - t > 0 ? NREG - t : 0); q <= K - 1 - t; ++q)
+                            for (int q = (NREG - t > 0 ? NREG - t : 0); q <= K - 1 - t && q < NP; ++q)
                                 mma_bf16(tmem + (uint32_t)(ON * (NREG - 1)), ad,
                                          db + (uint64_t)((q * B_TILE + kk * 32) >> 4),
                                          make_idesc(1, OM, ON), 1u);
@@ -657,7 +660,8 @@ template <int K>
 mpps_status launch_k(int dev, int grid, const CUtensorMap& ta, const CUtensorMap& tb, int n,
                      int ksA, int ksB, int batch, const int* eA, const int* eB, const Epilogue& ep,
                      int* d_err, cudaStream_t st, const int* bidx) {
-    constexpr int smem = num_stages(K) * stage_bytes(K) + 1024 + BAR_BYTES;
+    constexpr int NP = K < MAX_PLANES ? K : MAX_PLANES;
+    constexpr int smem = num_stages(NP) * stage_bytes(NP) + 1024 + BAR_BYTES;
     static_assert(smem <= SMEM_MAX, "shared memory budget exceeded");
     static bool attr_done[64] = {false};
     if (!attr_done[dev]) {
@@ -672,10 +676,13 @@ mpps_status launch_k(int dev, int grid, const CUtensorMap& ta, const CUtensorMap
 
 }  // namespace
 
-size_t f64e_plane_elems(int n, int batch, int k) { return (size_t)batch * k * n * low_ld(n); }
+size_t f64e_plane_elems(int n, int batch, int k) {
+    return (size_t)batch * f64e_planes(k) * n * low_ld(n);
+}
 
 mpps_status launch_slice_rows(const double* M, long long bs, int n, int batch, int k, void* planes,
                               int* exps, cudaStream_t st) {
+    k = f64e_planes(k);
     ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
     const int lld = low_ld(n);
     const long long goff = digit_offset(k), pbs = (long long)k * n * lld;
@@ -717,6 +724,7 @@ mpps_status launch_slice_rows(const double* M, long long bs, int n, int batch, i
 
 mpps_status launch_slice_cols(const double* M, long long bs, int n, int batch, int k, void* planes,
                               int* exps, unsigned long long* colmax, cudaStream_t st) {
+    k = f64e_planes(k);
     ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
     const int lld = low_ld(n);
     MPPS_CUDA_TRY(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * (size_t)batch * n, st));
@@ -734,14 +742,16 @@ mpps_status launch_gemm_f64e(int k, const void* slicesA, int ksA, const int* eA,
                              int nmat, const Epilogue& ep, int* d_err, cudaStream_t st,
                              const int* bidx) {
     if (batch <= 0) return MPPS_OK;
-    if (k < 1 || k > MPPS_F64E_MAX_SLICES || ksA < k || ksB < k) {
+    ksA = f64e_planes(ksA);    // planes stored per matrix
+    ksB = f64e_planes(ksB);
+    if (k < 1 || k > MPPS_F64E_MAX_SLICES || ksA < f64e_planes(k) || ksB < f64e_planes(k)) {
         set_error("emulated FP64 product: slice count %d outside 1..%d", k, MPPS_F64E_MAX_SLICES);
         return MPPS_EINVAL;
     }
     const int lld = low_ld(n);
     CUtensorMap ta, tb;
     if (!make_plane_map(&ta, slicesA, n, nmat * ksA, lld, OM, 1) ||
-        !make_plane_map(&tb, slicesBt, n, nmat * ksB, lld, ON, k)) {
+        !make_plane_map(&tb, slicesBt, n, nmat * ksB, lld, ON, f64e_planes(k))) {
         set_error("cuTensorMapEncodeTiled failed for slice planes (n=%d)", n);
         return MPPS_ECUDA;
     }
@@ -754,7 +764,8 @@ mpps_status launch_gemm_f64e(int k, const void* slicesA, int ksA, const int* eA,
         return MPPS_EINVAL;
     }
     const int grid = (int)(tiles < sm_count(dev) ? tiles : sm_count(dev));
-    ProfScope prof(MPPS_PROF_GEMM_F64E, st, 2.0 * n * (double)n * n * batch * (k * (k + 1) / 2));
+    const int pairs = k <= 8 ? k * (k + 1) / 2 : 43;
+    ProfScope prof(MPPS_PROF_GEMM_F64E, st, 2.0 * n * (double)n * n * batch * pairs);
     switch (k) {
         case 1: return launch_k<1>(dev, grid, ta, tb, n, ksA, ksB, batch, eA, eB, ep, d_err, st, bidx);
         case 2: return launch_k<2>(dev, grid, ta, tb, n, ksA, ksB, batch, eA, eB, ep, d_err, st, bidx);
@@ -763,7 +774,8 @@ mpps_status launch_gemm_f64e(int k, const void* slicesA, int ksA, const int* eA,
         case 5: return launch_k<5>(dev, grid, ta, tb, n, ksA, ksB, batch, eA, eB, ep, d_err, st, bidx);
         case 6: return launch_k<6>(dev, grid, ta, tb, n, ksA, ksB, batch, eA, eB, ep, d_err, st, bidx);
         case 7: return launch_k<7>(dev, grid, ta, tb, n, ksA, ksB, batch, eA, eB, ep, d_err, st, bidx);
-        default: return launch_k<8>(dev, grid, ta, tb, n, ksA, ksB, batch, eA, eB, ep, d_err, st, bidx);
+        case 8: return launch_k<8>(dev, grid, ta, tb, n, ksA, ksB, batch, eA, eB, ep, d_err, st, bidx);
+        default: return launch_k<9>(dev, grid, ta, tb, n, ksA, ksB, batch, eA, eB, ep, d_err, st, bidx);
     }
 }
 
