@@ -47,6 +47,33 @@ struct ProfScope {
     double work;   // algorithmic flops of the launch (products), 0 for the rest
 };
 
+// ---- programmatic dependent launch ------------------------------------------------
+// Every kernel of the library is launched with programmatic stream serialization: it may be
+// scheduled while the previous kernel on the stream drains, and it calls pdl_wait() before
+// it touches memory that an earlier kernel writes (griddepcontrol.wait returns when every
+// prerequisite grid has completed and its writes are visible) and lets its own dependents
+// launch at once (their CTAs then wait in pdl_wait()).
+__device__ __forceinline__ void pdl_wait() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // ---- fused epilogue of every product ---------------------------------------------
 // out = alpha * (A B) + sum_{j=0}^{nt} coef[j] X_j  with X_0 = I and X_j the j-th power
 // stored at pw + (j-1) n^2 (+ b * pw_bstride for batch element b).  nt = -1: no sum.

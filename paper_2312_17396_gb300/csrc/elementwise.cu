@@ -31,6 +31,7 @@ __device__ __forceinline__ double block_max(double v) {
 __global__ void k_block_norms_partial(const double* __restrict__ pw, long long pw_bs, int n,
                                       int s, int m, const double* __restrict__ coef,
                                       double* __restrict__ partial) {
+    pdl_wait();
     const int col = blockIdx.x * kColsPerBlock + threadIdx.x;
     const int chunk = blockIdx.y, chunks = gridDim.y, b = blockIdx.z;
     const int r = m / s, q = r + 3;
@@ -60,6 +61,7 @@ __global__ void k_block_norms_partial(const double* __restrict__ pw, long long p
 // norms[b*q + t] = max_col sum_chunk partial[b][chunk][t][col]  (fixed summation order).
 __global__ void k_norms_finalize(const double* __restrict__ partial, int n, int chunks, int q,
                                  double* __restrict__ norms) {
+    pdl_wait();
     const int t = blockIdx.x, b = blockIdx.y;
     double best = 0.0;
     for (int col = threadIdx.x; col < n; col += blockDim.x) {
@@ -74,6 +76,7 @@ __global__ void k_norms_finalize(const double* __restrict__ partial, int n, int 
 
 __global__ void k_colsum_partial(const double* __restrict__ M, long long bs, int n,
                                  double* __restrict__ partial) {
+    pdl_wait();
     const int col = blockIdx.x * kColsPerBlock + threadIdx.x;
     const int chunk = blockIdx.y, chunks = gridDim.y, b = blockIdx.z;
     if (col >= n) return;
@@ -95,6 +98,7 @@ __global__ void k_colsum_partial(const double* __restrict__ M, long long bs, int
 // it by the max of the sequential (row 0..n-1) column sums, the order a plain loop uses.
 __global__ void k_norm1_exact_near_pow2(const double* __restrict__ M, long long bs, int n,
                                         double* __restrict__ norms) {
+    pdl_wait();
     const int b = blockIdx.x;
     const double a = norms[b];
     if (!(a > 0.0) || !isfinite(a)) return;
@@ -134,6 +138,7 @@ struct NormCoefs {
 __global__ void k_block_norms_partial_f32(const double* __restrict__ pw, long long pw_bs, int n,
                                           int s, int m, NormCoefs cf,
                                           double* __restrict__ partial) {
+    pdl_wait();
     const int col = blockIdx.x * kColsPerBlock + threadIdx.x;
     const int chunk = blockIdx.y, chunks = gridDim.y, b = blockIdx.z;
     const int r = m / s, q = r + 3;
@@ -167,6 +172,7 @@ constexpr int kRegS = 8, kRegR = 8;
 __global__ void k_block_norms_partial_f32_reg(const double* __restrict__ pw, long long pw_bs,
                                               int n, int s, int m, NormCoefs cf,
                                               double* __restrict__ partial) {
+    pdl_wait();
     const int col = blockIdx.x * kColsPerBlock + threadIdx.x;
     const int chunk = blockIdx.y, chunks = gridDim.y, b = blockIdx.z;
     const int r = m / s, q = r + 3;
@@ -228,6 +234,7 @@ struct BlockScales {
 // atomic max over column blocks (norms must be zeroed first).
 __global__ void k_norms_finalize_scaled(const double* __restrict__ partial, int n, int chunks,
                                         int q, BlockScales sc, double* __restrict__ norms) {
+    pdl_wait();
     const int t = blockIdx.x, b = blockIdx.z;
     const int col = blockIdx.y * blockDim.x + threadIdx.x;
     double sum = 0.0;
@@ -244,6 +251,7 @@ __global__ void k_norms_finalize_scaled(const double* __restrict__ partial, int 
 
 __global__ void k_scale_copy(const double* __restrict__ A, long long a_bs, double* __restrict__ X,
                              long long x_bs, long long nn, const int* __restrict__ sigma) {
+    pdl_wait();
     const int b = blockIdx.y;
     const int e = sigma ? -sigma[b] : 0;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
@@ -254,6 +262,7 @@ __global__ void k_scale_copy(const double* __restrict__ A, long long a_bs, doubl
 // Gather items of different orders into a zero-padded batch (row-major n_pad x n_pad each)
 // and scatter the leading n x n blocks back.
 __global__ void k_gather_pad(const PadItem* __restrict__ list, int n_pad, double* __restrict__ dst) {
+    pdl_wait();
     const PadItem it = list[blockIdx.y];
     const long long nn = (long long)n_pad * n_pad;
     double* d = dst + (long long)blockIdx.y * nn;
@@ -266,6 +275,7 @@ __global__ void k_gather_pad(const PadItem* __restrict__ list, int n_pad, double
 
 __global__ void k_scatter_unpad(const PadItem* __restrict__ list, int n_pad,
                                 const double* __restrict__ src) {
+    pdl_wait();
     const PadItem it = list[blockIdx.y];
     const long long nn = (long long)it.n * it.n;
     const double* sp = src + (long long)blockIdx.y * n_pad * n_pad;
@@ -278,6 +288,7 @@ __global__ void k_scatter_unpad(const PadItem* __restrict__ list, int n_pad,
 
 // sigma[b] = max(0, ceil(log2 norms[b])) (0 for a non-finite norm), exactly as the host rule.
 __global__ void k_sigma(const double* __restrict__ norms, int batch, int* __restrict__ sigma) {
+    pdl_wait();
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= batch) return;
     const double a = norms[b];
@@ -292,6 +303,7 @@ __global__ void k_sigma(const double* __restrict__ norms, int batch, int* __rest
 __global__ void k_select_copy(const double* __restrict__ q0, const double* __restrict__ q1,
                               const int* __restrict__ sigma, double* __restrict__ out, int n,
                               double diag) {
+    pdl_wait();
     const int b = blockIdx.y;
     const long long nn = (long long)n * n;
     const double* src = (sigma[b] & 1) ? q1 : q0;
@@ -302,6 +314,7 @@ __global__ void k_select_copy(const double* __restrict__ q0, const double* __res
 
 __global__ void k_combine(int n, const double* __restrict__ extra, long long extra_bs,
                           Epilogue ep) {
+    pdl_wait();
     const int b = blockIdx.y;
     const long long nn = (long long)n * n;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
@@ -314,6 +327,7 @@ __global__ void k_combine(int n, const double* __restrict__ extra, long long ext
 
 __global__ void k_convert(int fmt, const double* __restrict__ M, long long bs, int n, void* hi,
                           void* lo, long long low_bs, int lld, const double* __restrict__ scale) {
+    pdl_wait();
     const int b = blockIdx.y;
     const double sc = scale ? scale[b] : 1.0;
     const long long nn = (long long)n * n;
@@ -328,6 +342,7 @@ __global__ void k_convert(int fmt, const double* __restrict__ M, long long bs, i
 __global__ void k_convert_t(int fmt, const double* __restrict__ M, long long bs, int n, void* hi,
                             void* lo, long long low_bs, int lld,
                             const double* __restrict__ scale) {
+    pdl_wait();
     __shared__ double tile[32][33];
     const int b = blockIdx.z;
     const double sc = scale ? scale[b] : 1.0;
@@ -352,6 +367,7 @@ struct BlockCoefs {
 
 __global__ void k_axpy_blocks(double* __restrict__ xbar, long long xbar_bs, int n, int t,
                               BlockCoefs c, const double* __restrict__ G, long long g_bs) {
+    pdl_wait();
     const int b = blockIdx.y;
     const long long nn = (long long)n * n;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nn;
@@ -363,6 +379,7 @@ __global__ void k_axpy_blocks(double* __restrict__ xbar, long long xbar_bs, int 
 
 __global__ void k_transpose(const double* __restrict__ A, long long a_bs, double* __restrict__ At,
                             int n) {
+    pdl_wait();
     __shared__ double tile[32][33];
     const int b = blockIdx.z;
     const long long nn = (long long)n * n;
@@ -380,6 +397,7 @@ __global__ void k_transpose(const double* __restrict__ A, long long a_bs, double
 
 __global__ void k_maxabs(const double* __restrict__ M, long long bs, long long nn,
                          double* __restrict__ out) {
+    pdl_wait();
     const int b = blockIdx.y;
     double v = 0.0;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
@@ -401,6 +419,7 @@ __device__ __forceinline__ int pow2_exp_above(double mx) {
 
 __global__ void k_pow2_scales(const double* __restrict__ ma, const double* __restrict__ mb,
                               int batch, int target, double* sa, double* sb, double* unscale) {
+    pdl_wait();
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= batch) return;
     const int ea = pow2_exp_above(ma[b]), eb = pow2_exp_above(mb[b]);
@@ -452,12 +471,12 @@ mpps_status launch_block_norms_f32(const double* pw, long long pw_bs, int n, int
     dim3 g((n + kColsPerBlock - 1) / kColsPerBlock, chunks, batch);
     MPPS_CUDA_TRY(cudaMemsetAsync(norms, 0, sizeof(double) * (size_t)batch * q, st));
     if (s <= kRegS && m / s <= kRegR)
-        k_block_norms_partial_f32_reg<<<g, kColsPerBlock, 0, st>>>(pw, pw_bs, n, s, m, cf, partial);
+        MPPS_CUDA_TRY(launch_pdl(k_block_norms_partial_f32_reg, dim3(g), dim3(kColsPerBlock), 0, st, pw, pw_bs, n, s, m, cf, partial));
     else
-        k_block_norms_partial_f32<<<g, kColsPerBlock, 0, st>>>(pw, pw_bs, n, s, m, cf, partial);
+        MPPS_CUDA_TRY(launch_pdl(k_block_norms_partial_f32, dim3(g), dim3(kColsPerBlock), 0, st, pw, pw_bs, n, s, m, cf, partial));
     MPPS_LAUNCH_CHECK();
-    k_norms_finalize_scaled<<<dim3(q, (n + 127) / 128, batch), 128, 0, st>>>(partial, n, chunks, q,
-                                                                              sc, norms);
+    MPPS_CUDA_TRY(launch_pdl(k_norms_finalize_scaled, dim3(dim3(q, (n + 127) / 128, batch)), dim3(128), 0, st, partial, n, chunks, q,
+                                                                              sc, norms));
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }
@@ -469,9 +488,9 @@ mpps_status launch_block_norms(const double* pw, long long pw_bs, int n, int bat
     const int chunks = (n + kRowsPerChunk - 1) / kRowsPerChunk;
     const int q = block_norms_count(m, s);
     dim3 g((n + kColsPerBlock - 1) / kColsPerBlock, chunks, batch);
-    k_block_norms_partial<<<g, kColsPerBlock, 0, st>>>(pw, pw_bs, n, s, m, d_coeffs, partial);
+    MPPS_CUDA_TRY(launch_pdl(k_block_norms_partial, dim3(g), dim3(kColsPerBlock), 0, st, pw, pw_bs, n, s, m, d_coeffs, partial));
     MPPS_LAUNCH_CHECK();
-    k_norms_finalize<<<dim3(q, batch), 256, 0, st>>>(partial, n, chunks, q, norms);
+    MPPS_CUDA_TRY(launch_pdl(k_norms_finalize, dim3(dim3(q, batch)), dim3(256), 0, st, partial, n, chunks, q, norms));
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }
@@ -482,17 +501,17 @@ mpps_status launch_norm1(const double* M, long long bs, int n, int batch, double
     // fast chunked sums (64-row partials, summed in chunk order) ...
     const int chunks = (n + kRowsPerChunk - 1) / kRowsPerChunk;
     dim3 g((n + kColsPerBlock - 1) / kColsPerBlock, chunks, batch);
-    k_colsum_partial<<<g, kColsPerBlock, 0, st>>>(M, bs, n, partial);
+    MPPS_CUDA_TRY(launch_pdl(k_colsum_partial, dim3(g), dim3(kColsPerBlock), 0, st, M, bs, n, partial));
     MPPS_LAUNCH_CHECK();
     MPPS_CUDA_TRY(cudaMemsetAsync(norms, 0, sizeof(double) * (size_t)batch, st));
     BlockScales one;
     one.c[0] = 1.0;
-    k_norms_finalize_scaled<<<dim3(1, (n + 127) / 128, batch), 128, 0, st>>>(partial, n, chunks, 1,
-                                                                             one, norms);
+    MPPS_CUDA_TRY(launch_pdl(k_norms_finalize_scaled, dim3(dim3(1, (n + 127) / 128, batch)), dim3(128), 0, st, partial, n, chunks, 1,
+                                                                             one, norms));
     MPPS_LAUNCH_CHECK();
     // ... and, only for a matrix whose norm lies within 2^-44 of a power of two (where the
     // summation order could move ceil(log2 ||A||_1)), the plain sequential column sums
-    k_norm1_exact_near_pow2<<<batch, 256, 0, st>>>(M, bs, n, norms);
+    MPPS_CUDA_TRY(launch_pdl(k_norm1_exact_near_pow2, dim3(batch), dim3(256), 0, st, M, bs, n, norms));
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }
@@ -501,7 +520,7 @@ mpps_status launch_scale_copy(const double* A, long long a_bs, double* X, long l
                               int batch, const int* d_sigma, cudaStream_t st) {
     ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
     const long long nn = (long long)n * n;
-    k_scale_copy<<<dim3(grid1d(nn, 256), batch), 256, 0, st>>>(A, a_bs, X, x_bs, nn, d_sigma);
+    MPPS_CUDA_TRY(launch_pdl(k_scale_copy, dim3(dim3(grid1d(nn, 256), batch)), dim3(256), 0, st, A, a_bs, X, x_bs, nn, d_sigma));
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }
@@ -510,7 +529,7 @@ mpps_status launch_gather_pad(const PadItem* d_list, int count, int n_pad, doubl
                               cudaStream_t st) {
     ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
     const long long nn = (long long)n_pad * n_pad;
-    k_gather_pad<<<dim3(grid1d(nn, 256, 64), count), 256, 0, st>>>(d_list, n_pad, dst);
+    MPPS_CUDA_TRY(launch_pdl(k_gather_pad, dim3(dim3(grid1d(nn, 256, 64), count)), dim3(256), 0, st, d_list, n_pad, dst));
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }
@@ -519,14 +538,14 @@ mpps_status launch_scatter_unpad(const PadItem* d_list, int count, int n_pad, co
                                  cudaStream_t st) {
     ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
     const long long nn = (long long)n_pad * n_pad;
-    k_scatter_unpad<<<dim3(grid1d(nn, 256, 64), count), 256, 0, st>>>(d_list, n_pad, src);
+    MPPS_CUDA_TRY(launch_pdl(k_scatter_unpad, dim3(dim3(grid1d(nn, 256, 64), count)), dim3(256), 0, st, d_list, n_pad, src));
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }
 
 mpps_status launch_sigma(const double* norms, int batch, int* sigma, cudaStream_t st) {
     ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
-    k_sigma<<<(batch + 127) / 128, 128, 0, st>>>(norms, batch, sigma);
+    MPPS_CUDA_TRY(launch_pdl(k_sigma, dim3((batch + 127) / 128), dim3(128), 0, st, norms, batch, sigma));
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }
@@ -535,7 +554,7 @@ mpps_status launch_select_copy(const double* q0, const double* q1, const int* d_
                                int n, int batch, double diag, cudaStream_t st) {
     ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
     const long long nn = (long long)n * n;
-    k_select_copy<<<dim3(grid1d(nn, 256), batch), 256, 0, st>>>(q0, q1, d_sigma, out, n, diag);
+    MPPS_CUDA_TRY(launch_pdl(k_select_copy, dim3(dim3(grid1d(nn, 256), batch)), dim3(256), 0, st, q0, q1, d_sigma, out, n, diag));
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }
@@ -544,7 +563,7 @@ mpps_status launch_combine(int n, int batch, const double* extra, long long extr
                            const Epilogue& ep, cudaStream_t st) {
     ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
     const long long nn = (long long)n * n;
-    k_combine<<<dim3(grid1d(nn, 256), batch), 256, 0, st>>>(n, extra, extra_bs, ep);
+    MPPS_CUDA_TRY(launch_pdl(k_combine, dim3(dim3(grid1d(nn, 256), batch)), dim3(256), 0, st, n, extra, extra_bs, ep));
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }
@@ -555,11 +574,11 @@ mpps_status launch_convert(int fmt, const double* M, long long bs, int n, int ba
     ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
     if (transpose) {
         dim3 g((n + 31) / 32, (n + 31) / 32, batch);
-        k_convert_t<<<g, dim3(32, 8), 0, st>>>(fmt, M, bs, n, hi, lo, low_bs, lld, d_scale);
+        MPPS_CUDA_TRY(launch_pdl(k_convert_t, dim3(g), dim3(dim3(32, 8)), 0, st, fmt, M, bs, n, hi, lo, low_bs, lld, d_scale));
     } else {
         const long long nn = (long long)n * n;
-        k_convert<<<dim3(grid1d(nn, 256), batch), 256, 0, st>>>(fmt, M, bs, n, hi, lo, low_bs,
-                                                                  lld, d_scale);
+        MPPS_CUDA_TRY(launch_pdl(k_convert, dim3(dim3(grid1d(nn, 256), batch)), dim3(256), 0, st, fmt, M, bs, n, hi, lo, low_bs,
+                                                                  lld, d_scale));
     }
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
@@ -569,7 +588,7 @@ mpps_status launch_maxabs(const double* M, long long bs, int n, int batch, doubl
                           cudaStream_t st) {
     ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
     const long long nn = (long long)n * n;
-    k_maxabs<<<dim3(grid1d(nn, 256, 1024), batch), 256, 0, st>>>(M, bs, nn, out);
+    MPPS_CUDA_TRY(launch_pdl(k_maxabs, dim3(dim3(grid1d(nn, 256, 1024), batch)), dim3(256), 0, st, M, bs, nn, out));
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }
@@ -578,8 +597,8 @@ mpps_status launch_pow2_scales(const double* maxabs_a, const double* maxabs_b, i
                                int target_exp, double* scale_a, double* scale_b, double* unscale,
                                cudaStream_t st) {
     ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
-    k_pow2_scales<<<(batch + 127) / 128, 128, 0, st>>>(maxabs_a, maxabs_b, batch, target_exp,
-                                                         scale_a, scale_b, unscale);
+    MPPS_CUDA_TRY(launch_pdl(k_pow2_scales, dim3((batch + 127) / 128), dim3(128), 0, st, maxabs_a, maxabs_b, batch, target_exp,
+                                                         scale_a, scale_b, unscale));
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }
@@ -592,7 +611,7 @@ mpps_status launch_axpy_blocks(double* xbar, long long xbar_bs, int n, int batch
     BlockCoefs bc;
     for (int j = 0; j <= MPPS_MAX_S; ++j) bc.c[j] = (j <= t) ? c[j] : 0.0;
     const long long nn = (long long)n * n;
-    k_axpy_blocks<<<dim3(grid1d(nn, 256), batch), 256, 0, st>>>(xbar, xbar_bs, n, t, bc, G, g_bs);
+    MPPS_CUDA_TRY(launch_pdl(k_axpy_blocks, dim3(dim3(grid1d(nn, 256), batch)), dim3(256), 0, st, xbar, xbar_bs, n, t, bc, G, g_bs));
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }
@@ -601,7 +620,7 @@ mpps_status launch_transpose(const double* A, long long a_bs, double* At, int n,
                              cudaStream_t st) {
     ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
     dim3 g((n + 31) / 32, (n + 31) / 32, batch);
-    k_transpose<<<g, dim3(32, 8), 0, st>>>(A, a_bs, At, n);
+    MPPS_CUDA_TRY(launch_pdl(k_transpose, dim3(g), dim3(dim3(32, 8)), 0, st, A, a_bs, At, n));
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }

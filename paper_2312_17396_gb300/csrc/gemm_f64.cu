@@ -39,6 +39,7 @@ template <int BM, int BN, int WM, int WN>
 __global__ void __launch_bounds__(32 * WM * WN)
     k_gemm_f64(const double* __restrict__ A, long long a_bs, const double* __restrict__ B,
                long long b_bs, int n, Epilogue ep, const int* __restrict__ bidx) {
+    pdl_wait();
     constexpr int NT = 32 * WM * WN;
     constexpr int WTM = BM / WM, WTN = BN / WN;   // warp tile
     constexpr int MI = WTM / 16, NI = WTN / 8;    // fragments per warp
@@ -155,10 +156,10 @@ mpps_status launch_gemm_f64(const double* A, long long a_bs, const double* B, lo
     const long long load64 = (t64 + sms - 1) / sms * 4096, load32 = (t32 + sms - 1) / sms * 1024;
     if (load32 < load64) {
         dim3 grid((n + 31) / 32, (n + 31) / 32, batch);
-        k_gemm_f64<32, 32, 2, 2><<<grid, 128, 0, st>>>(A, a_bs, B, b_bs, n, ep, bidx);
+        MPPS_CUDA_TRY(launch_pdl(k_gemm_f64<32, 32, 2, 2>, dim3(grid), dim3(128), 0, st, A, a_bs, B, b_bs, n, ep, bidx));
     } else {
         dim3 grid((n + 63) / 64, (n + 63) / 64, batch);
-        k_gemm_f64<64, 64, 2, 4><<<grid, 256, 0, st>>>(A, a_bs, B, b_bs, n, ep, bidx);
+        MPPS_CUDA_TRY(launch_pdl(k_gemm_f64<64, 64, 2, 4>, dim3(grid), dim3(256), 0, st, A, a_bs, B, b_bs, n, ep, bidx));
     }
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;

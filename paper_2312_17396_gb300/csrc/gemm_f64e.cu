@@ -153,6 +153,7 @@ __device__ __forceinline__ int exp_above(double mx) {
 __global__ void k_slice_rows(const double* __restrict__ M, long long bs, int n, int k,
                              long long goff, __nv_bfloat16* __restrict__ planes,
                              long long plane_bs, int lld, int* __restrict__ exps) {
+    pdl_wait();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row = blockIdx.x * (blockDim.x >> 5) + warp, b = blockIdx.y;
     if (row >= n) return;
@@ -176,6 +177,7 @@ __global__ void __launch_bounds__(256) k_slice_rows_blk(const double* __restrict
                                                         __nv_bfloat16* __restrict__ planes,
                                                         long long plane_bs, int lld,
                                                         int* __restrict__ exps) {
+    pdl_wait();
     __shared__ unsigned long long red[8];
     const int row = blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
     const double* src = M + (long long)b * bs + (long long)row * n;
@@ -216,6 +218,7 @@ __global__ void __launch_bounds__(256) k_slice_rows_blk4(const double* __restric
                                                          __nv_bfloat16* __restrict__ planes,
                                                          long long plane_bs, int lld,
                                                          int* __restrict__ exps) {
+    pdl_wait();
     __shared__ unsigned long long red[8];
     const int row = blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
     const double* src = M + (long long)b * bs + (long long)row * n;
@@ -269,6 +272,7 @@ __global__ void __launch_bounds__(256) k_slice_rows_blk4(const double* __restric
 
 // Row maxima of |M| -> exponents e_i (one warp per row), for rows too long for the above.
 __global__ void k_rowexp(const double* __restrict__ M, long long bs, int n, int* __restrict__ exps) {
+    pdl_wait();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row = blockIdx.x * (blockDim.x >> 5) + warp, b = blockIdx.y;
     if (row >= n) return;
@@ -283,6 +287,7 @@ __global__ void k_rowexp(const double* __restrict__ M, long long bs, int n, int*
 __global__ void k_slice_rows_elem(const double* __restrict__ M, long long bs, int n, int k,
                                   long long goff, const int* __restrict__ exps,
                                   __nv_bfloat16* __restrict__ planes, long long plane_bs, int lld) {
+    pdl_wait();
     const int col = blockIdx.x * blockDim.x + threadIdx.x, row = blockIdx.y, b = blockIdx.z;
     if (col >= n) return;
     const int e = exps[(long long)b * n + row];
@@ -294,6 +299,7 @@ __global__ void k_slice_rows_elem(const double* __restrict__ M, long long bs, in
 // thread per column over a 16-row chunk, all 16 loads in flight.
 __global__ void k_colmax(const double* __restrict__ M, long long bs, int n,
                          unsigned long long* __restrict__ out) {
+    pdl_wait();
     const int col = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.z;
     if (col >= n) return;
     const int r0 = blockIdx.y * 16;
@@ -316,6 +322,7 @@ __global__ void k_slice_cols(const double* __restrict__ M, long long bs, int n, 
                              long long goff, const unsigned long long* __restrict__ colmax,
                              __nv_bfloat16* __restrict__ planes, long long plane_bs, int lld,
                              int* __restrict__ exps) {
+    pdl_wait();
     __shared__ double tile[32][33];
     const int b = blockIdx.z, r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
     const double* src = M + (long long)b * bs;
@@ -441,6 +448,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    pdl_wait();   // barrier init, TMEM allocation and tensor-map prefetch overlap the previous kernel
 
     if (warp == EPI_WARPS) {
         if (lane == 0) {   // TMA producer
@@ -669,7 +677,7 @@ mpps_status launch_k(int dev, int grid, const CUtensorMap& ta, const CUtensorMap
                                            smem));
         attr_done[dev] = true;
     }
-    k_gemm_f64e<K><<<grid, THREADS, smem, st>>>(ta, tb, n, ksA, ksB, batch, eA, eB, ep, d_err, bidx);
+    MPPS_CUDA_TRY(launch_pdl(k_gemm_f64e<K>, dim3(grid), dim3(THREADS), smem, st, ta, tb, n, ksA, ksB, batch, eA, eB, ep, d_err, bidx));
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }
@@ -692,31 +700,31 @@ mpps_status launch_slice_rows(const double* M, long long bs, int n, int batch, i
         return MPPS_EINVAL;
     }
     if (n < 256) {
-        k_slice_rows<<<dim3((n + 7) / 8, batch), 256, 0, st>>>(M, bs, n, k, goff, pl, pbs, lld, exps);
+        MPPS_CUDA_TRY(launch_pdl(k_slice_rows, dim3(dim3((n + 7) / 8, batch)), dim3(256), 0, st, M, bs, n, k, goff, pl, pbs, lld, exps));
     } else if (n <= 4096 && n % 4 == 0 && ((uintptr_t)M & 15) == 0 && bs % 2 == 0) {
         const dim3 g(n, batch);
         if (n <= 1024)
-            k_slice_rows_blk4<1><<<g, 256, 0, st>>>(M, bs, n, k, goff, pl, pbs, lld, exps);
+            MPPS_CUDA_TRY(launch_pdl(k_slice_rows_blk4<1>, dim3(g), dim3(256), 0, st, M, bs, n, k, goff, pl, pbs, lld, exps));
         else if (n <= 2048)
-            k_slice_rows_blk4<2><<<g, 256, 0, st>>>(M, bs, n, k, goff, pl, pbs, lld, exps);
+            MPPS_CUDA_TRY(launch_pdl(k_slice_rows_blk4<2>, dim3(g), dim3(256), 0, st, M, bs, n, k, goff, pl, pbs, lld, exps));
         else
-            k_slice_rows_blk4<4><<<g, 256, 0, st>>>(M, bs, n, k, goff, pl, pbs, lld, exps);
+            MPPS_CUDA_TRY(launch_pdl(k_slice_rows_blk4<4>, dim3(g), dim3(256), 0, st, M, bs, n, k, goff, pl, pbs, lld, exps));
     } else if (n <= 4096) {
         const dim3 g(n, batch);
         if (n <= 512)
-            k_slice_rows_blk<2><<<g, 256, 0, st>>>(M, bs, n, k, goff, pl, pbs, lld, exps);
+            MPPS_CUDA_TRY(launch_pdl(k_slice_rows_blk<2>, dim3(g), dim3(256), 0, st, M, bs, n, k, goff, pl, pbs, lld, exps));
         else if (n <= 1024)
-            k_slice_rows_blk<4><<<g, 256, 0, st>>>(M, bs, n, k, goff, pl, pbs, lld, exps);
+            MPPS_CUDA_TRY(launch_pdl(k_slice_rows_blk<4>, dim3(g), dim3(256), 0, st, M, bs, n, k, goff, pl, pbs, lld, exps));
         else if (n <= 2048)
-            k_slice_rows_blk<8><<<g, 256, 0, st>>>(M, bs, n, k, goff, pl, pbs, lld, exps);
+            MPPS_CUDA_TRY(launch_pdl(k_slice_rows_blk<8>, dim3(g), dim3(256), 0, st, M, bs, n, k, goff, pl, pbs, lld, exps));
         else
-            k_slice_rows_blk<16><<<g, 256, 0, st>>>(M, bs, n, k, goff, pl, pbs, lld, exps);
+            MPPS_CUDA_TRY(launch_pdl(k_slice_rows_blk<16>, dim3(g), dim3(256), 0, st, M, bs, n, k, goff, pl, pbs, lld, exps));
     } else {
         // long rows: a row-maximum pass, then one thread per element
-        k_rowexp<<<dim3((n + 7) / 8, batch), 256, 0, st>>>(M, bs, n, exps);
+        MPPS_CUDA_TRY(launch_pdl(k_rowexp, dim3(dim3((n + 7) / 8, batch)), dim3(256), 0, st, M, bs, n, exps));
         MPPS_LAUNCH_CHECK();
-        k_slice_rows_elem<<<dim3((n + 127) / 128, n, batch), 128, 0, st>>>(M, bs, n, k, goff, exps, pl,
-                                                                          pbs, lld);
+        MPPS_CUDA_TRY(launch_pdl(k_slice_rows_elem, dim3(dim3((n + 127) / 128, n, batch)), dim3(128), 0, st, M, bs, n, k, goff, exps, pl,
+                                                                          pbs, lld));
     }
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
@@ -728,11 +736,10 @@ mpps_status launch_slice_cols(const double* M, long long bs, int n, int batch, i
     ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
     const int lld = low_ld(n);
     MPPS_CUDA_TRY(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * (size_t)batch * n, st));
-    k_colmax<<<dim3((n + 127) / 128, (n + 15) / 16, batch), 128, 0, st>>>(M, bs, n, colmax);
+    MPPS_CUDA_TRY(launch_pdl(k_colmax, dim3(dim3((n + 127) / 128, (n + 15) / 16, batch)), dim3(128), 0, st, M, bs, n, colmax));
     MPPS_LAUNCH_CHECK();
-    k_slice_cols<<<dim3((n + 31) / 32, (n + 31) / 32, batch), dim3(32, 8), 0, st>>>(
-        M, bs, n, k, digit_offset(k), colmax, (__nv_bfloat16*)planes, (long long)k * n * lld, lld,
-        exps);
+    MPPS_CUDA_TRY(launch_pdl(k_slice_cols, dim3(dim3((n + 31) / 32, (n + 31) / 32, batch)), dim3(dim3(32, 8)), 0, st, M, bs, n, k, digit_offset(k), colmax, (__nv_bfloat16*)planes, (long long)k * n * lld, lld,
+        exps));
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }

@@ -131,6 +131,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    pdl_wait();   // barrier init, TMEM allocation and tensor-map prefetch overlap the previous kernel
 
     if (warp == 0 && lane == 0) {
         // TMA producer
@@ -292,7 +293,7 @@ mpps_status launch_fmt(const void* A_hi, const void* A_lo, const void* Bt_hi, co
     dim3 grid((n + TN - 1) / TN, (n + TM - 1) / TM, batch);
     ProfScope prof(MPPS_PROF_GEMM_TC, st,
                    2.0 * n * (double)n * n * batch * (FMT == MPPS_FMT_BF16X3 ? 3 : 1));
-    k_gemm_tc<FMT, TN><<<grid, TC_THREADS, smem, st>>>(ta, tb, ta2, tb2, n, ep, d_err);
+    MPPS_CUDA_TRY(launch_pdl(k_gemm_tc<FMT, TN>, dim3(grid), dim3(TC_THREADS), smem, st, ta, tb, ta2, tb2, n, ep, d_err));
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }
