@@ -63,12 +63,12 @@ constexpr int EPI_COLS = ON / (EPI_WARPS / 4);
 constexpr int THREADS = (EPI_WARPS + 2) * 32;
 static_assert(EPI_COLS == 16, "the drain loads 16 TMEM columns per thread");
 constexpr int MAX_STAGES = 8;
-constexpr int NFULL = MAX_STAGES * (8 + 1);
+constexpr int NFULL = MAX_STAGES;       // one fill barrier per stage
 constexpr int BAR_BYTES = 1024;
 constexpr int SMEM_MAX = 232448;        // 227 KB of opt-in dynamic shared memory
 constexpr int SMEM_BUDGET = SMEM_MAX - 1024 - BAR_BYTES;
 constexpr int RASTER_G = 8;             // row blocks per raster group (L2 reuse of B)
-// barrier block after the ring: full[MAX_STAGES][k+1] | empty[MAX_STAGES] | chunk_done |
+// barrier block after the ring: full[MAX_STAGES] | empty[MAX_STAGES] | chunk_done |
 // tmem_free | mma_done | TMEM address slot
 static_assert((NFULL + MAX_STAGES + 3) * 8 + 4 <= BAR_BYTES, "barrier block exceeds its bytes");
 static_assert(NREG * ON <= 512, "TMEM regions exceed 512 columns");
@@ -399,6 +399,39 @@ struct TileMap {
     }
 };
 
+// One K=16 step of the split product into the TMEM regions: slice t of A times the stacked
+// slices b'_0..b'_{NR-1-t} of B lands in regions t..NR-1 (one instruction per 256 columns),
+// then the pairs of order NREG..K-1 (K = 9: t + q = 8) in the last region.  Every operand
+// offset and shape is a compile-time constant, so the instructions issue back to back: the
+// tensor pipe queues little, and any other work between them leaves it idle.  ASC walks the
+// slices upwards with slice 0 first, whose instruction covers every region and may start the
+// accumulation (acc0 = 0); otherwise the walk runs downwards and ends with slice 0's two wide
+// instructions, behind which the wait for the next stage hides.
+template <int K, int KK, bool ASC>
+__device__ __forceinline__ void issue_k16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t acc0) {
+    constexpr int NP = K < MAX_PLANES ? K : MAX_PLANES;
+    constexpr int NR = NP < NREG ? NP : NREG;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        const int t = ASC ? i : NP - 1 - i;
+        const uint64_t ad = da + (uint64_t)((t * A_TILE + KK * 32) >> 4);
+        if (t < NR) {
+            const int N = ON * (NR - t);
+            const uint32_t acc = (ASC && t == 0) ? acc0 : 1u;
+            mma_bf16(tmem + (uint32_t)(ON * t), ad, db + (uint64_t)((KK * 32) >> 4),
+                     make_idesc(1, OM, N > 256 ? 256 : N), acc);
+            if (N > 256)   // B rows 256..: 32 atoms of 512 B further
+                mma_bf16(tmem + (uint32_t)(ON * t + 256), ad,
+                         db + (uint64_t)((256 * 64 + KK * 32) >> 4),
+                         make_idesc(1, OM, N > 256 ? N - 256 : ON), acc);
+        }
+#pragma unroll
+        for (int q = (NREG - t > 0 ? NREG - t : 0); q <= K - 1 - t && q < NP; ++q)
+            mma_bf16(tmem + (uint32_t)(ON * (NREG - 1)), ad,
+                     db + (uint64_t)((q * B_TILE + KK * 32) >> 4), make_idesc(1, OM, ON), 1u);
+    }
+}
+
 template <int K>
 __global__ void __launch_bounds__(THREADS, 1)
     k_gemm_f64e(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -414,7 +447,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t* full = (uint64_t*)(smem + S * SB);     // [stage][0: B slices, 1 + t: A slice t]
+    uint64_t* full = (uint64_t*)(smem + S * SB);     // [stage]: all slices of A and B landed
     uint64_t* empty = full + NFULL;
     uint64_t* chunk_done = empty + MAX_STAGES;
     uint64_t* tmem_free = chunk_done + 1;
@@ -433,7 +466,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
-            for (int i = 0; i <= NP; ++i) mbar_init(&full[s * (NP + 1) + i], 1);
+            mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
         mbar_init(chunk_done, 1);
@@ -463,15 +496,12 @@ __global__ void __launch_bounds__(THREADS, 1)
                 for (int kb = 0; kb < nkb; ++kb, ++g) {
                     if (g >= (uint32_t)S && !(ok = mbar_wait(&empty[s], ph ^ 1, err))) break;
                     uint8_t* st = smem + s * SB;
-                    uint64_t* f = full + s * (NP + 1);
                     const int kc = kb * KB;
-                    mbar_expect_tx(&f[0], (uint32_t)(NP * B_TILE));
-                    tma_load_3d(st + NP * A_TILE, &tmB, kc, n0, b * ksB, &f[0]);
+                    mbar_expect_tx(&full[s], (uint32_t)SB);
+                    tma_load_3d(st + NP * A_TILE, &tmB, kc, n0, b * ksB, &full[s]);
 #pragma unroll
-                    for (int t = 0; t < NP; ++t) {
-                        mbar_expect_tx(&f[1 + t], (uint32_t)A_TILE);
-                        tma_load_3d(st + t * A_TILE, &tmA, kc, m0, b * ksA + t, &f[1 + t]);
-                    }
+                    for (int t = 0; t < NP; ++t)
+                        tma_load_3d(st + t * A_TILE, &tmA, kc, m0, b * ksA + t, &full[s]);
                     if (++s == S) { s = 0; ph ^= 1; }
                 }
             }
@@ -479,11 +509,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             // unless this loop or the MMA issuer gave up early)
             const uint32_t lo = g > (uint32_t)S ? g - (uint32_t)S : 0u;
             bool landed = true;
-            for (uint32_t gg = lo; gg < g && landed; ++gg) {
-                const int s = (int)(gg % (uint32_t)S);
-                for (int i = 0; i <= NP && landed; ++i)
-                    landed = mbar_wait_quiet(&full[s * (NP + 1) + i], (gg / S) & 1);
-            }
+            for (uint32_t gg = lo; gg < g && landed; ++gg)
+                landed = mbar_wait_quiet(&full[gg % (uint32_t)S], (gg / S) & 1);
             if (!landed) atomicExch(err, 1);
         }
     } else if (warp == EPI_WARPS + 1) {
@@ -500,35 +527,16 @@ __global__ void __launch_bounds__(THREADS, 1)
                         if (!(ok = mbar_wait(tmem_free, (gc - 1) & 1, err))) break;
                         tc_fence_after();
                     }
-                    uint64_t* f = full + s * (NP + 1);
-                    if (!(ok = mbar_wait(&f[0], ph, err))) break;
+                    if (!(ok = mbar_wait(&full[s], ph, err))) break;
+                    tc_fence_after();
                     const uint32_t abase = ring + (uint32_t)(s * SB);
                     const uint64_t da = sw64_desc(abase), db = sw64_desc(abase + NP * A_TILE);
-                    const uint32_t acc0 = kin == 0 ? 0u : 1u;
-#pragma unroll
-                    for (int t = 0; t < NP; ++t) {
-                        if (!(ok = mbar_wait(&f[1 + t], ph, err))) break;
-                        tc_fence_after();
-#pragma unroll
-                        for (int kk = 0; kk < 2; ++kk) {        // two K=16 steps per 64-byte row
-                            const uint64_t ad = da + (uint64_t)((t * A_TILE + kk * 32) >> 4);
-                            if (t < NR) {   // stacked b'_0..b'_{NR-1-t} -> regions t..NR-1
-                                const int N = ON * (NR - t);
-                                const uint32_t acc = (t == 0 && kk == 0) ? acc0 : 1u;
-                                mma_bf16(tmem + (uint32_t)(ON * t), ad, db + (uint64_t)((kk * 32) >> 4),
-                                         make_idesc(1, OM, N > 256 ? 256 : N), acc);
-                                if (N > 256)   // B rows 256..: 32 atoms of 512 B further
-                                    mma_bf16(tmem + (uint32_t)(ON * t + 256), ad,
-                                             db + (uint64_t)((256 * 64 + kk * 32) >> 4),
-                                             make_idesc(1, OM, N - 256), acc);
-                            }
-                            // pairs of order NREG..K-1 (K = 9: t + q = 8) -> last region
-#pragma unroll
-                            for (int q = (NREG - t > 0 ? NREG - t : 0); q <= K - 1 - t && q < NP; ++q)
-                                mma_bf16(tmem + (uint32_t)(ON * (NREG - 1)), ad,
-                                         db + (uint64_t)((q * B_TILE + kk * 32) >> 4),
-                                         make_idesc(1, OM, ON), 1u);
-                        }
+                    if (kin == 0) {   // the chunk's first step starts the accumulation
+                        issue_k16<K, 0, true>(tmem, da, db, 0u);
+                        issue_k16<K, 1, false>(tmem, da, db, 1u);
+                    } else {
+                        issue_k16<K, 0, false>(tmem, da, db, 1u);
+                        issue_k16<K, 1, false>(tmem, da, db, 1u);
                     }
                     if (!ok) break;
                     tc_commit(&empty[s]);
