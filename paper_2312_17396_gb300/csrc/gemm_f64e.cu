@@ -26,15 +26,22 @@
 // chunk, each chunk's W is added to an FP64 accumulator, so W never overflows.  The FP64
 // pipe only adds and does the fused epilogue: product = 2^{e-49} W + 2^{e-14} T.
 //
+// Slice layouts.  A (row slices): slices 2p and 2p+1 of a row share row r of "pair" p,
+// alternating 32-element K blocks, [pair][row][K block][slice 2p | slice 2p+1][32], so one TMA
+// box row carries 128 bytes (the copy engine's rate grows with the row length: about 150 GB/s
+// per SM for 128-byte rows against 96 for 64-byte ones) and lands in the 128-byte swizzle,
+// where slice 2p+1 is the same tile read 64 bytes further along K.  B^T (column slices):
+// plane q is [row][K] on its own ([plane][row][K]), 64-byte swizzle, so that the planes of
+// one tile stack along N.
+//
 // Kernel: persistent, one CTA per SM, 128 x 64 output tiles, 18 warps (0-15 epilogue: TMEM
 // lane quarter = warp % 4, 16-column group = warp / 4; 16 TMA producer; 17 MMA issuer).  Per
-// K block of 32 the producer loads the k slices of the B^T tile (one 3-D box) and the k
-// slices of the A tile (one box and one mbarrier each, so the MMAs of slice t start when
-// slice t lands).  The MMA of slice t uses the stacked B operand b'_0..b'_{7-t}
-// (N = 64 (8 - t)) and writes regions t..7 in one instruction (two when N > 256); with
-// k = 8 that covers all 36 pairs in 12 instructions per K step.  Operands are K-major with
-// the 64-byte swizzle.  The epilogue drains TMEM into registers and releases it at once, so
-// the FP64 epilogue of a tile overlaps the MMAs of the next.  All mbarrier waits are bounded.
+// K block of 32 the producer loads the pairs of the A tile (one box each) and the k planes of
+// the B^T tile (one 3-D box) on one mbarrier.  The MMA of slice t uses the stacked B operand
+// b'_0..b'_{7-t} (N = 64 (8 - t)) and writes regions t..7 in one instruction (two when
+// N > 256); with k = 8 that covers all 36 pairs in 12 instructions per K step.  The epilogue
+// drains TMEM into registers and releases it at once, so the FP64 epilogue of a tile overlaps
+// the MMAs of the next.  All mbarrier waits are bounded.
 #include "common.cuh"
 #include "tcgen05.cuh"
 
@@ -56,8 +63,8 @@ constexpr int DIGIT = 7;                // bits per slice
 constexpr int FLUSH = 8;                // chunks the 64-bit W may sum before an FP64 flush
 constexpr int NEXACT = 6;               // diagonals accumulated exactly
 constexpr int NREG = 8;                 // TMEM regions: D_0..D_5, d = 6, and d = 7
-constexpr int A_TILE = OM * KB * 2;     // 8 KB
-constexpr int B_TILE = ON * KB * 2;     // 4 KB
+constexpr int A_PAIR = OM * 4 * KB;     // 16 KB: a pair of A slices, 128-byte rows
+constexpr int B_TILE = ON * 2 * KB;     // 4 KB: one B plane, 64-byte rows
 constexpr int EPI_WARPS = 16;            // 4 per TMEM lane quarter, 16 columns each
 constexpr int EPI_COLS = ON / (EPI_WARPS / 4);
 constexpr int THREADS = (EPI_WARPS + 2) * 32;
@@ -76,7 +83,8 @@ constexpr int MAX_PLANES = 8;           // slices per operand (F64E(9) adds pair
 static_assert(MAX_PLANES <= NREG, "every slice must start a TMEM region");
 static_assert(55 - DIGIT * (MAX_PLANES - 1) >= 1, "the last digit needs a rounding bit");
 
-__host__ __device__ constexpr int stage_bytes(int k) { return k * (A_TILE + B_TILE); }
+__host__ __device__ constexpr int num_pairs(int k) { return (k + 1) / 2; }
+__host__ __device__ constexpr int stage_bytes(int k) { return num_pairs(k) * A_PAIR + k * B_TILE; }
 __host__ __device__ constexpr int num_stages(int k) {
     int s = SMEM_BUDGET / stage_bytes(k);
     return s > MAX_STAGES ? MAX_STAGES : s;
@@ -134,12 +142,20 @@ __device__ __forceinline__ unsigned digit_bits(long long G, int t) {
     return __float_as_uint(f) >> 16;
 }
 
+// Pair layout (see the top of the file): K index j of a row sits at kpos(j) in its pair row,
+// slice t at slice_off(t) from its pair's origin; pstride = n 2 lld elements per pair.
+__device__ __forceinline__ long long kpos(int j) { return (long long)j + (j & ~(KB - 1)); }
+__device__ __forceinline__ long long slice_off(int t, long long pstride) {
+    return (long long)(t >> 1) * pstride + (t & 1) * KB;
+}
+
+// The k digits of x (dst = the row's origin + kpos(j)); x = 0 gives k zero digits.
 __device__ __forceinline__ void put_digits(double x, int e, int k, long long goff,
                                            __nv_bfloat16* dst, long long pstride) {
     const long long G = scaled_int(x, e) + goff;
 #pragma unroll 1
     for (int t = 0; t < k; ++t)
-        dst[(long long)t * pstride] = __ushort_as_bfloat16((unsigned short)digit_bits(G, t));
+        dst[slice_off(t, pstride)] = __ushort_as_bfloat16((unsigned short)digit_bits(G, t));
 }
 
 __device__ __forceinline__ int exp_above(double mx) {
@@ -163,9 +179,10 @@ __global__ void k_slice_rows(const double* __restrict__ M, long long bs, int n, 
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     const int e = exp_above(mx);
     if (lane == 0) exps[(long long)b * n + row] = e;
-    __nv_bfloat16* dst = planes + (long long)b * plane_bs + (long long)row * lld;
-    const long long pstride = (long long)n * lld;
-    for (int j = lane; j < n; j += 32) put_digits(src[j], e, k, goff, dst + j, pstride);
+    __nv_bfloat16* dst = planes + (long long)b * plane_bs + (long long)row * 2 * lld;
+    const long long pstride = (long long)n * 2 * lld;
+    const int n32 = (n + KB - 1) / KB * KB;   // the K tail up to n32 is written as zeros
+    for (int j = lane; j < n32; j += 32) put_digits(j < n ? src[j] : 0.0, e, k, goff, dst + kpos(j), pstride);
 }
 
 // Row slices for rows of up to 256 VPT elements: one 256-thread block per row holds the row
@@ -201,12 +218,13 @@ __global__ void __launch_bounds__(256) k_slice_rows_blk(const double* __restrict
     for (int w = 1; w < 8; ++w) mx = red[w] > mx ? red[w] : mx;
     const int e = exp_above(__longlong_as_double((long long)mx));
     if (tid == 0) exps[(long long)b * n + row] = e;
-    __nv_bfloat16* dst = planes + (long long)b * plane_bs + (long long)row * lld;
-    const long long pstride = (long long)n * lld;
+    __nv_bfloat16* dst = planes + (long long)b * plane_bs + (long long)row * 2 * lld;
+    const long long pstride = (long long)n * 2 * lld;
+    const int n32 = (n + KB - 1) / KB * KB;   // v = 0 on the K tail n..n32-1
 #pragma unroll
     for (int i = 0; i < VPT; ++i) {
         const int j = tid + 256 * i;
-        if (j < n) put_digits(v[i], e, k, goff, dst + j, pstride);
+        if (j < n32) put_digits(v[i], e, k, goff, dst + kpos(j), pstride);
     }
 }
 
@@ -251,12 +269,13 @@ __global__ void __launch_bounds__(256) k_slice_rows_blk4(const double* __restric
     for (int w = 1; w < 8; ++w) mx = red[w] > mx ? red[w] : mx;
     const int e = exp_above(__longlong_as_double((long long)mx));
     if (tid == 0) exps[(long long)b * n + row] = e;
-    __nv_bfloat16* dst = planes + (long long)b * plane_bs + (long long)row * lld;
-    const long long pstride = (long long)n * lld;
+    __nv_bfloat16* dst = planes + (long long)b * plane_bs + (long long)row * 2 * lld;
+    const long long pstride = (long long)n * 2 * lld;
+    const int n32 = (n + KB - 1) / KB * KB;   // v = 0 on the K tail n..n32-1
 #pragma unroll
     for (int g = 0; g < NG; ++g) {
         const int j = 4 * (tid + 256 * g);
-        if (j >= n) continue;
+        if (j >= n32) continue;
         long long G[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) G[u] = scaled_int(v[g][u], e) + goff;
@@ -265,7 +284,7 @@ __global__ void __launch_bounds__(256) k_slice_rows_blk4(const double* __restric
             uint2 w;
             w.x = digit_bits(G[0], t) | (digit_bits(G[1], t) << 16);
             w.y = digit_bits(G[2], t) | (digit_bits(G[3], t) << 16);
-            *reinterpret_cast<uint2*>(dst + (long long)t * pstride + j) = w;
+            *reinterpret_cast<uint2*>(dst + slice_off(t, pstride) + kpos(j)) = w;
         }
     }
 }
@@ -289,10 +308,11 @@ __global__ void k_slice_rows_elem(const double* __restrict__ M, long long bs, in
                                   __nv_bfloat16* __restrict__ planes, long long plane_bs, int lld) {
     pdl_wait();
     const int col = blockIdx.x * blockDim.x + threadIdx.x, row = blockIdx.y, b = blockIdx.z;
-    if (col >= n) return;
+    if (col >= (n + KB - 1) / KB * KB) return;   // the K tail n..n32-1 is written as zeros
     const int e = exps[(long long)b * n + row];
-    put_digits(M[(long long)b * bs + (long long)row * n + col], e, k, goff,
-               planes + (long long)b * plane_bs + (long long)row * lld + col, (long long)n * lld);
+    put_digits(col < n ? M[(long long)b * bs + (long long)row * n + col] : 0.0, e, k, goff,
+               planes + (long long)b * plane_bs + (long long)row * 2 * lld + kpos(col),
+               (long long)n * 2 * lld);
 }
 
 // Column maxima of |M| (as the bit pattern of a non-negative double; out zeroed first): one
@@ -337,38 +357,32 @@ __global__ void k_slice_cols(const double* __restrict__ M, long long bs, int n, 
         if (col >= n || row >= n) continue;
         const int e = exp_above(__longlong_as_double((long long)colmax[(long long)b * n + col]));
         if (blockIdx.y == 0 && threadIdx.x == 0) exps[(long long)b * n + col] = e;
-        put_digits(tile[threadIdx.x][i], e, k, goff,
-                   planes + (long long)b * plane_bs + (long long)col * lld + row, pstride);
+        const long long G = scaled_int(tile[threadIdx.x][i], e) + goff;
+        __nv_bfloat16* dst = planes + (long long)b * plane_bs + (long long)col * lld + row;
+#pragma unroll 1
+        for (int t = 0; t < k; ++t)
+            dst[(long long)t * pstride] = __ushort_as_bfloat16((unsigned short)digit_bits(G, t));
     }
 }
 
-// w 2^s rounded to the nearest double (ties to even) on the integer pipe; false (and *out
-// untouched) when the result would not be a normal double.
+// w 2^s rounded to the nearest double (ties to even) on the integer pipe, for |w| < 2^62;
+// false (and *out untouched) when the result would not be a normal double.  The magnitude is
+// normalised so that its top bit sits at bit 62 (bit 0 is then zero: |w| < 2^62 shifts by at
+// least one), 0x1FF plus the kept bit's parity rounds the ten dropped bits half to even, and
+// adding the 53-bit significand (implicit bit included) to (exponent - 1) << 52 carries into
+// the exponent when the rounding reaches the next power of two.
 __device__ __forceinline__ bool i64_to_f64_scaled(long long w, int s, double* out) {
     if (w == 0) { *out = 0.0; return true; }
-    const unsigned long long sgn = w < 0 ? 0x8000000000000000ULL : 0ULL;
+    const unsigned long long sgn = (unsigned long long)w & 0x8000000000000000ULL;
     const unsigned long long a = w < 0 ? 0ULL - (unsigned long long)w : (unsigned long long)w;
-    const int msb = 63 - __clzll((long long)a);
-    int ed = msb + 1023 + s;
-    unsigned long long m;
-    if (msb <= 52) {
-        m = a << (52 - msb);
-    } else {
-        const int sh = msb - 52;
-        const unsigned long long rem = a & ((1ULL << sh) - 1), half = 1ULL << (sh - 1);
-        m = a >> sh;
-        if (rem > half || (rem == half && (m & 1))) {
-            ++m;
-            if (m >> 53) { m >>= 1; ++ed; }
-        }
-    }
-    if (ed <= 0 || ed >= 2047) return false;
-    *out = __longlong_as_double((long long)(sgn | ((unsigned long long)ed << 52) | (m & 0xFFFFFFFFFFFFFULL)));
+    const int lz = __clzll((long long)a);
+    const unsigned long long h = (a << lz) >> 1;
+    const unsigned long long r = h + 0x1FFULL + ((h >> 10) & 1ULL);
+    const int ed = (63 - lz) + 1023 + s;
+    if ((unsigned)(ed - 1) >= 2045u) return false;
+    *out = __longlong_as_double((long long)(sgn | (((unsigned long long)(ed - 1) << 52) + (r >> 10))));
     return true;
 }
-
-// f 2^s as a double (exact) on the integer pipe; false for subnormal, non-finite or
-// out-of-range results.
 __device__ __forceinline__ bool f32_to_f64_scaled(float f, int s, double* out) {
     const unsigned u = __float_as_uint(f);
     if ((u << 1) == 0) { *out = __longlong_as_double((long long)(u >> 31) << 63); return true; }
@@ -380,6 +394,20 @@ __device__ __forceinline__ bool f32_to_f64_scaled(float f, int s, double* out) {
                                             ((unsigned long long)ed << 52) |
                                             ((unsigned long long)(u & 0x7fffff) << 29)));
     return true;
+}
+
+// 2^(e-49) W + 2^(e-14) T through the FP64 pipe, for the rare values that leave the range
+// of the integer-pipe conversions (and, when the chunks were flushed, from the FP64 partial
+// sum acc = 2^35 W instead of W).  Kept out of line: its code would otherwise crowd the
+// unrolled fast path.
+__device__ __noinline__ double f64e_slow_value(bool flushed, double acc, long long W, float T,
+                                               int e) {
+    return flushed ? ldexp(fma(acc, 0x1p-35, (double)T), e - 14)
+                   : ldexp(fma((double)W, 0x1p-35, (double)T), e - 14);
+}
+__device__ __noinline__ void f64e_store(const Epilogue& ep, int b, int row, int col, int n,
+                                        double v) {
+    epilogue_store(ep, b, row, col, n, epilogue_value(ep, b, row, col, n, v));
 }
 
 // Tile `id` -> (matrix slot z, first row, first column); row blocks are walked in groups of
@@ -399,14 +427,15 @@ struct TileMap {
     }
 };
 
-// One K=16 step of the split product into the TMEM regions: slice t of A times the stacked
-// slices b'_0..b'_{NR-1-t} of B lands in regions t..NR-1 (one instruction per 256 columns),
-// then the pairs of order NREG..K-1 (K = 9: t + q = 8) in the last region.  Every operand
-// offset and shape is a compile-time constant, so the instructions issue back to back: the
-// tensor pipe queues little, and any other work between them leaves it idle.  ASC walks the
-// slices upwards with slice 0 first, whose instruction covers every region and may start the
-// accumulation (acc0 = 0); otherwise the walk runs downwards and ends with slice 0's two wide
-// instructions, behind which the wait for the next stage hides.
+// One K=16 step of the split product into the TMEM regions: slice t of A (pair t/2, K offset
+// 64 (t & 1) bytes) times the stacked planes b'_0..b'_{NR-1-t} lands in regions t..NR-1 (one
+// instruction per 256 columns), then the pairs of order NREG..K-1 (K = 9: t + q = 8) in the
+// last region.  Every operand offset and shape is a compile-time constant, so the
+// instructions issue back to back: the tensor pipe queues little, and any other work between
+// them leaves it idle.  ASC walks the slices upwards with slice 0 first, whose instruction
+// covers every region and may start the accumulation (acc0 = 0); otherwise the walk runs
+// downwards and ends with slice 0's wide instructions, behind which the wait for the next
+// stage hides.
 template <int K, int KK, bool ASC>
 __device__ __forceinline__ void issue_k16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t acc0) {
     constexpr int NP = K < MAX_PLANES ? K : MAX_PLANES;
@@ -414,7 +443,7 @@ __device__ __forceinline__ void issue_k16(uint32_t tmem, uint64_t da, uint64_t d
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
         const int t = ASC ? i : NP - 1 - i;
-        const uint64_t ad = da + (uint64_t)((t * A_TILE + KK * 32) >> 4);
+        const uint64_t ad = da + (uint64_t)(((t >> 1) * A_PAIR + (t & 1) * 64 + KK * 32) >> 4);
         if (t < NR) {
             const int N = ON * (NR - t);
             const uint32_t acc = (ASC && t == 0) ? acc0 : 1u;
@@ -435,9 +464,10 @@ __device__ __forceinline__ void issue_k16(uint32_t tmem, uint64_t da, uint64_t d
 template <int K>
 __global__ void __launch_bounds__(THREADS, 1)
     k_gemm_f64e(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                int n, int ksA, int ksB, int batch, const int* __restrict__ eA,
+                int n, int kpA, int ksB, int batch, const int* __restrict__ eA,
                 const int* __restrict__ eB, Epilogue ep, int* err, const int* __restrict__ bidx) {
     constexpr int NP = K < MAX_PLANES ? K : MAX_PLANES;   // slices per operand
+    constexpr int NPA = num_pairs(NP);                    // slice pairs of A
     constexpr int S = num_stages(NP);
     constexpr int SB = stage_bytes(NP);
     constexpr int NR = NP < NREG ? NP : NREG;         // TMEM regions in use
@@ -496,12 +526,11 @@ __global__ void __launch_bounds__(THREADS, 1)
                 for (int kb = 0; kb < nkb; ++kb, ++g) {
                     if (g >= (uint32_t)S && !(ok = mbar_wait(&empty[s], ph ^ 1, err))) break;
                     uint8_t* st = smem + s * SB;
-                    const int kc = kb * KB;
                     mbar_expect_tx(&full[s], (uint32_t)SB);
-                    tma_load_3d(st + NP * A_TILE, &tmB, kc, n0, b * ksB, &full[s]);
+                    tma_load_3d(st + NPA * A_PAIR, &tmB, kb * KB, n0, b * ksB, &full[s]);
 #pragma unroll
-                    for (int t = 0; t < NP; ++t)
-                        tma_load_3d(st + t * A_TILE, &tmA, kc, m0, b * ksA + t, &full[s]);
+                    for (int p = 0; p < NPA; ++p)   // pair rows hold 2 KB elements per K block
+                        tma_load_3d(st + p * A_PAIR, &tmA, kb * 2 * KB, m0, b * kpA + p, &full[s]);
                     if (++s == S) { s = 0; ph ^= 1; }
                 }
             }
@@ -530,7 +559,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     if (!(ok = mbar_wait(&full[s], ph, err))) break;
                     tc_fence_after();
                     const uint32_t abase = ring + (uint32_t)(s * SB);
-                    const uint64_t da = sw64_desc(abase), db = sw64_desc(abase + NP * A_TILE);
+                    const uint64_t da = sw128_desc(abase), db = sw64_desc(abase + NPA * A_PAIR);
                     if (kin == 0) {   // the chunk's first step starts the accumulation
                         issue_k16<K, 0, true>(tmem, da, db, 0u);
                         issue_k16<K, 1, false>(tmem, da, db, 1u);
@@ -553,6 +582,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
     } else {
         // epilogue warps: row = m0 + 32 (warp % 4) + lane, columns n0 + 16 (warp / 4) + j
+        // (a plain epilogue stores the product alone, four doubles at a time where aligned)
+        const bool ep_plain = ep.nt < 0 && ep.add == nullptr && ep.low_fmt == MPPS_FMT_NONE &&
+                              ep.alpha_b == nullptr &&
+                              __double_as_longlong(ep.alpha) == 0x3FF0000000000000LL;
         const int q4 = warp & 3, h = warp >> 2;   // lane quarter, column group
         const uint32_t lane_base = (uint32_t)(q4 * 32) << 16;
         uint32_t gc = 0;
@@ -568,6 +601,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             const int row = m0 + q4 * 32 + lane;
             const int cb = n0 + EPI_COLS * h;
             double* orow = ep.out + (long long)b * ep.out_bstride + (long long)row * n + cb;
+            const bool vec4 = ((uintptr_t)orow & 31) == 0;
             for (int c = 0; c < nchunks; ++c, ++gc) {
                 ok = __all_sync(0xffffffffu, mbar_wait(chunk_done, gc & 1, err));
                 if (!ok) break;
@@ -605,21 +639,33 @@ __global__ void __launch_bounds__(THREADS, 1)
             // product = 2^{eA+eB-49} W + 2^{eA+eB-14} T, then the fused epilogue
             if (row < n) {
                 const int er = eA[(long long)b * n + row];
+                const bool plain = ep_plain && cb + EPI_COLS <= n && nchunks <= FLUSH;
 #pragma unroll
-                for (int j = 0; j < EPI_COLS; ++j) {
-                    const int col = cb + j;
-                    if (col < n) {
-                        const int e = er + __ldg(eB + (long long)b * n + col);
+                for (int g = 0; g < EPI_COLS; g += 4) {
+                    double val[4];
+                    bool fast = nchunks <= FLUSH;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int j = g + u;
+                        const int e = er + __ldg(eB + (long long)b * n + min(cb + j, n - 1));
+                        double wd = 0.0, td = 0.0;
                         // 2^(e-49) W and 2^(e-14) T formed on the integer pipe, one FP64 add
-                        double wd, td, val;
-                        if (nchunks > FLUSH)
-                            val = ldexp(fma(orow[j], 0x1p-35, (double)T[j]), e - 14);
-                        else if (i64_to_f64_scaled(W[j], e - 49, &wd) &&
-                                 f32_to_f64_scaled(T[j], e - 14, &td))
-                            val = wd + td;
-                        else
-                            val = ldexp(fma((double)W[j], 0x1p-35, (double)T[j]), e - 14);
-                        epilogue_store(ep, b, row, col, n, epilogue_value(ep, b, row, col, n, val));
+                        fast = fast && i64_to_f64_scaled(W[j], e - 49, &wd) &&
+                               f32_to_f64_scaled(T[j], e - 14, &td);
+                        val[u] = wd + td;
+                    }
+                    if (plain && fast && vec4) {   // four consecutive doubles, 32-byte aligned
+                        asm volatile("st.global.v4.f64 [%0], {%1, %2, %3, %4};" ::"l"(orow + g),
+                                     "d"(val[0]), "d"(val[1]), "d"(val[2]), "d"(val[3]) : "memory");
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int col = cb + g + u;
+                            if (col < n)
+                                f64e_store(ep, b, row, col, n, fast ? val[u] : f64e_slow_value(
+                                    nchunks > FLUSH, orow[g + u], W[g + u], T[g + u],
+                                    er + __ldg(eB + (long long)b * n + col)));
+                        }
                     }
                 }
             }
@@ -646,14 +692,29 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// planes: [nplanes][n][lld] bf16 -> 3-D map (K = n, rows = n, planes), box 32 x rows x planes
-bool make_plane_map(CUtensorMap* tm, const void* ptr, int n, int nplanes, int lld, int box_rows,
-                    int box_planes) {
+// A pairs: [npairs][n][2 lld] bf16 -> 3-D map (pair row, rows = n, pairs), box 2 KB x 128 x 1,
+// 128-byte swizzle.  The row is read only below 2 round_up(n, KB), whose K tail the row
+// slicers write as zeros.
+bool make_pair_map(CUtensorMap* tm, const void* ptr, int n, int npairs, int lld) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)2 * lld, (cuuint64_t)n, (cuuint64_t)npairs};
+    cuuint64_t strides[2] = {(cuuint64_t)lld * 4, (cuuint64_t)n * lld * 4};
+    cuuint32_t box[3] = {(cuuint32_t)(2 * KB), (cuuint32_t)OM, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(ptr), dims, strides, box,
+              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// B^T planes: [nplanes][n][lld] bf16 -> 3-D map (K = n, rows = n, planes), box KB x 64 x
+// planes, 64-byte swizzle; the K tail past n reads as zeros.
+bool make_plane_map(CUtensorMap* tm, const void* ptr, int n, int nplanes, int lld, int box_planes) {
     auto fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)nplanes};
     cuuint64_t strides[2] = {(cuuint64_t)lld * 2, (cuuint64_t)n * lld * 2};
-    cuuint32_t box[3] = {(cuuint32_t)KB, (cuuint32_t)box_rows, (cuuint32_t)box_planes};
+    cuuint32_t box[3] = {(cuuint32_t)KB, (cuuint32_t)ON, (cuuint32_t)box_planes};
     cuuint32_t estr[3] = {1, 1, 1};
     return fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(ptr), dims, strides, box,
               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
@@ -674,7 +735,7 @@ int sm_count(int dev) {
 
 template <int K>
 mpps_status launch_k(int dev, int grid, const CUtensorMap& ta, const CUtensorMap& tb, int n,
-                     int ksA, int ksB, int batch, const int* eA, const int* eB, const Epilogue& ep,
+                     int kpA, int ksB, int batch, const int* eA, const int* eB, const Epilogue& ep,
                      int* d_err, cudaStream_t st, const int* bidx) {
     constexpr int NP = K < MAX_PLANES ? K : MAX_PLANES;
     constexpr int smem = num_stages(NP) * stage_bytes(NP) + 1024 + BAR_BYTES;
@@ -685,7 +746,7 @@ mpps_status launch_k(int dev, int grid, const CUtensorMap& ta, const CUtensorMap
                                            smem));
         attr_done[dev] = true;
     }
-    MPPS_CUDA_TRY(launch_pdl(k_gemm_f64e<K>, dim3(grid), dim3(THREADS), smem, st, ta, tb, n, ksA, ksB, batch, eA, eB, ep, d_err, bidx));
+    MPPS_CUDA_TRY(launch_pdl(k_gemm_f64e<K>, dim3(grid), dim3(THREADS), smem, st, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, bidx));
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }
@@ -693,7 +754,7 @@ mpps_status launch_k(int dev, int grid, const CUtensorMap& ta, const CUtensorMap
 }  // namespace
 
 size_t f64e_plane_elems(int n, int batch, int k) {
-    return (size_t)batch * f64e_planes(k) * n * low_ld(n);
+    return (size_t)batch * num_pairs(f64e_planes(k)) * n * 2 * low_ld(n);
 }
 
 mpps_status launch_slice_rows(const double* M, long long bs, int n, int batch, int k, void* planes,
@@ -701,7 +762,7 @@ mpps_status launch_slice_rows(const double* M, long long bs, int n, int batch, i
     k = f64e_planes(k);
     ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
     const int lld = low_ld(n);
-    const long long goff = digit_offset(k), pbs = (long long)k * n * lld;
+    const long long goff = digit_offset(k), pbs = (long long)num_pairs(k) * n * 2 * lld;
     __nv_bfloat16* pl = (__nv_bfloat16*)planes;
     if (batch > 65535) {
         set_error("slice_rows: batch %d exceeds the grid limit", batch);
@@ -731,7 +792,7 @@ mpps_status launch_slice_rows(const double* M, long long bs, int n, int batch, i
         // long rows: a row-maximum pass, then one thread per element
         MPPS_CUDA_TRY(launch_pdl(k_rowexp, dim3(dim3((n + 7) / 8, batch)), dim3(256), 0, st, M, bs, n, exps));
         MPPS_LAUNCH_CHECK();
-        MPPS_CUDA_TRY(launch_pdl(k_slice_rows_elem, dim3(dim3((n + 127) / 128, n, batch)), dim3(128), 0, st, M, bs, n, k, goff, exps, pl,
+        MPPS_CUDA_TRY(launch_pdl(k_slice_rows_elem, dim3(dim3((n + KB + 127) / 128, n, batch)), dim3(128), 0, st, M, bs, n, k, goff, exps, pl,
                                                                           pbs, lld));
     }
     MPPS_LAUNCH_CHECK();
@@ -764,9 +825,10 @@ mpps_status launch_gemm_f64e(int k, const void* slicesA, int ksA, const int* eA,
         return MPPS_EINVAL;
     }
     const int lld = low_ld(n);
+    const int kpA = num_pairs(ksA);   // slice pairs of A stored per matrix
     CUtensorMap ta, tb;
-    if (!make_plane_map(&ta, slicesA, n, nmat * ksA, lld, OM, 1) ||
-        !make_plane_map(&tb, slicesBt, n, nmat * ksB, lld, ON, f64e_planes(k))) {
+    if (!make_pair_map(&ta, slicesA, n, nmat * kpA, lld) ||
+        !make_plane_map(&tb, slicesBt, n, nmat * ksB, lld, f64e_planes(k))) {
         set_error("cuTensorMapEncodeTiled failed for slice planes (n=%d)", n);
         return MPPS_ECUDA;
     }
@@ -782,15 +844,15 @@ mpps_status launch_gemm_f64e(int k, const void* slicesA, int ksA, const int* eA,
     const int pairs = k <= 8 ? k * (k + 1) / 2 : 43;
     ProfScope prof(MPPS_PROF_GEMM_F64E, st, 2.0 * n * (double)n * n * batch * pairs);
     switch (k) {
-        case 1: return launch_k<1>(dev, grid, ta, tb, n, ksA, ksB, batch, eA, eB, ep, d_err, st, bidx);
-        case 2: return launch_k<2>(dev, grid, ta, tb, n, ksA, ksB, batch, eA, eB, ep, d_err, st, bidx);
-        case 3: return launch_k<3>(dev, grid, ta, tb, n, ksA, ksB, batch, eA, eB, ep, d_err, st, bidx);
-        case 4: return launch_k<4>(dev, grid, ta, tb, n, ksA, ksB, batch, eA, eB, ep, d_err, st, bidx);
-        case 5: return launch_k<5>(dev, grid, ta, tb, n, ksA, ksB, batch, eA, eB, ep, d_err, st, bidx);
-        case 6: return launch_k<6>(dev, grid, ta, tb, n, ksA, ksB, batch, eA, eB, ep, d_err, st, bidx);
-        case 7: return launch_k<7>(dev, grid, ta, tb, n, ksA, ksB, batch, eA, eB, ep, d_err, st, bidx);
-        case 8: return launch_k<8>(dev, grid, ta, tb, n, ksA, ksB, batch, eA, eB, ep, d_err, st, bidx);
-        default: return launch_k<9>(dev, grid, ta, tb, n, ksA, ksB, batch, eA, eB, ep, d_err, st, bidx);
+        case 1: return launch_k<1>(dev, grid, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx);
+        case 2: return launch_k<2>(dev, grid, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx);
+        case 3: return launch_k<3>(dev, grid, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx);
+        case 4: return launch_k<4>(dev, grid, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx);
+        case 5: return launch_k<5>(dev, grid, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx);
+        case 6: return launch_k<6>(dev, grid, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx);
+        case 7: return launch_k<7>(dev, grid, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx);
+        case 8: return launch_k<8>(dev, grid, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx);
+        default: return launch_k<9>(dev, grid, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx);
     }
 }
 
