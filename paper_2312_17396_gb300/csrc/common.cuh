@@ -144,7 +144,9 @@ __device__ __forceinline__ double epilogue_value(const Epilogue& ep, int b, int 
                                                  int n, double acc) {
     const double al = ep.alpha_b ? ep.alpha_b[b] : ep.alpha;
     double v = acc;
-    if (__double_as_longlong(al) != 0x3FF0000000000000LL) v = al * acc;   // no multiply by 1
+    const long long alb = __double_as_longlong(al);
+    if (alb == 0) v = 0.0;                                 // alpha = 0: no product term
+    else if (alb != 0x3FF0000000000000LL) v = al * acc;   // no multiply by 1
     if (ep.nt >= 0) {
         if (row == col) v += ep.coef[0];
         const double* base = ep.pw + (long long)b * ep.pw_bstride + (long long)row * n + col;

@@ -249,6 +249,17 @@ __global__ void k_norms_finalize_scaled(const double* __restrict__ partial, int 
                   (unsigned long long)__double_as_longlong(best));
 }
 
+// x 2^e, exact: the exponent field moves on the integer pipe whenever x and the result are
+// normal doubles (zero stays zero); subnormal or non-finite values take ldexp.
+__device__ __forceinline__ double scale_pow2(double x, int e) {
+    const long long bits = __double_as_longlong(x);
+    if ((bits << 1) == 0) return x;
+    const int ef = (int)((bits >> 52) & 0x7ff);
+    if (ef > 0 && ef < 0x7ff && ef + e > 0 && ef + e < 0x7ff)
+        return __longlong_as_double(bits + ((long long)e << 52));
+    return ldexp(x, e);
+}
+
 __global__ void k_scale_copy(const double* __restrict__ A, long long a_bs, double* __restrict__ X,
                              long long x_bs, long long nn, const int* __restrict__ sigma) {
     pdl_wait();
@@ -256,34 +267,29 @@ __global__ void k_scale_copy(const double* __restrict__ A, long long a_bs, doubl
     const int e = sigma ? -sigma[b] : 0;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
          t += (long long)gridDim.x * blockDim.x)
-        X[b * x_bs + t] = ldexp(A[b * a_bs + t], e);
+        X[b * x_bs + t] = scale_pow2(A[b * a_bs + t], e);
 }
 
 // Gather items of different orders into a zero-padded batch (row-major n_pad x n_pad each)
 // and scatter the leading n x n blocks back.
+// (Row, column) loops over a 2-D grid: x covers columns, y rows, z the matrices.
 __global__ void k_gather_pad(const PadItem* __restrict__ list, int n_pad, double* __restrict__ dst) {
     pdl_wait();
-    const PadItem it = list[blockIdx.y];
-    const long long nn = (long long)n_pad * n_pad;
-    double* d = dst + (long long)blockIdx.y * nn;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
-         t += (long long)gridDim.x * blockDim.x) {
-        const int r = (int)(t / n_pad), c = (int)(t % n_pad);
-        d[t] = (r < it.n && c < it.n) ? it.A[(long long)r * it.n + c] : 0.0;
-    }
+    const PadItem it = list[blockIdx.z];
+    double* d = dst + (long long)blockIdx.z * n_pad * n_pad;
+    for (int r = blockIdx.y; r < n_pad; r += gridDim.y)
+        for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n_pad; c += gridDim.x * blockDim.x)
+            d[(long long)r * n_pad + c] = (r < it.n && c < it.n) ? it.A[(long long)r * it.n + c] : 0.0;
 }
 
 __global__ void k_scatter_unpad(const PadItem* __restrict__ list, int n_pad,
                                 const double* __restrict__ src) {
     pdl_wait();
-    const PadItem it = list[blockIdx.y];
-    const long long nn = (long long)it.n * it.n;
-    const double* sp = src + (long long)blockIdx.y * n_pad * n_pad;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
-         t += (long long)gridDim.x * blockDim.x) {
-        const int r = (int)(t / it.n), c = (int)(t % it.n);
-        it.out[t] = sp[(long long)r * n_pad + c];
-    }
+    const PadItem it = list[blockIdx.z];
+    const double* sp = src + (long long)blockIdx.z * n_pad * n_pad;
+    for (int r = blockIdx.y; r < it.n; r += gridDim.y)
+        for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < it.n; c += gridDim.x * blockDim.x)
+            it.out[(long long)r * it.n + c] = sp[(long long)r * n_pad + c];
 }
 
 // sigma[b] = max(0, ceil(log2 norms[b])) (0 for a non-finite norm), exactly as the host rule.
@@ -304,38 +310,38 @@ __global__ void k_select_copy(const double* __restrict__ q0, const double* __res
                               const int* __restrict__ sigma, double* __restrict__ out, int n,
                               double diag) {
     pdl_wait();
-    const int b = blockIdx.y;
+    const int b = blockIdx.z;
     const long long nn = (long long)n * n;
-    const double* src = (sigma[b] & 1) ? q1 : q0;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
-         t += (long long)gridDim.x * blockDim.x)
-        out[b * nn + t] = src[b * nn + t] + ((t / n == t % n) ? diag : 0.0);
+    const double* src = ((sigma[b] & 1) ? q1 : q0) + b * nn;
+    for (int r = blockIdx.y; r < n; r += gridDim.y)
+        for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+            const long long t = (long long)r * n + c;
+            double v = src[t];
+            if (r == c) v += diag;
+            out[b * nn + t] = v;
+        }
 }
 
 __global__ void k_combine(int n, const double* __restrict__ extra, long long extra_bs,
                           Epilogue ep) {
     pdl_wait();
-    const int b = blockIdx.y;
-    const long long nn = (long long)n * n;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
-         t += (long long)gridDim.x * blockDim.x) {
-        const int row = (int)(t / n), col = (int)(t % n);
-        const double e = extra ? extra[b * extra_bs + t] : 0.0;
-        epilogue_store(ep, b, row, col, n, epilogue_value(ep, b, row, col, n, e));
-    }
+    const int b = blockIdx.z;
+    for (int row = blockIdx.y; row < n; row += gridDim.y)
+        for (int col = blockIdx.x * blockDim.x + threadIdx.x; col < n; col += gridDim.x * blockDim.x) {
+            const double e = extra ? extra[b * extra_bs + (long long)row * n + col] : 0.0;
+            epilogue_store(ep, b, row, col, n, epilogue_value(ep, b, row, col, n, e));
+        }
 }
 
 __global__ void k_convert(int fmt, const double* __restrict__ M, long long bs, int n, void* hi,
                           void* lo, long long low_bs, int lld, const double* __restrict__ scale) {
     pdl_wait();
-    const int b = blockIdx.y;
+    const int b = blockIdx.z;
     const double sc = scale ? scale[b] : 1.0;
-    const long long nn = (long long)n * n;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
-         t += (long long)gridDim.x * blockDim.x) {
-        const int row = (int)(t / n), col = (int)(t % n);
-        store_low(fmt, hi, lo, b * low_bs + (long long)row * lld + col, M[b * bs + t] * sc);
-    }
+    for (int row = blockIdx.y; row < n; row += gridDim.y)
+        for (int col = blockIdx.x * blockDim.x + threadIdx.x; col < n; col += gridDim.x * blockDim.x)
+            store_low(fmt, hi, lo, b * low_bs + (long long)row * lld + col,
+                      M[b * bs + (long long)row * n + col] * sc);
 }
 
 // Transposed copy through a 32 x 33 shared tile: out[col][row] = round(M[row][col] * scale).
@@ -426,6 +432,14 @@ __global__ void k_pow2_scales(const double* __restrict__ ma, const double* __res
     sa[b] = ldexp(1.0, target - ea);
     sb[b] = ldexp(1.0, target - eb);
     unscale[b] = ldexp(1.0, ea + eb - 2 * target);
+}
+
+// 256-thread blocks over an n x n matrix per z: x spans the columns, y up to 4096 rows
+// (each block row strides by gridDim.y), z the matrices.
+inline dim3 grid2d(int n, int nmat) {
+    const int gx = (n + 255) / 256;
+    const int gy = n < 4096 ? (n > 0 ? n : 1) : 4096;
+    return dim3(gx > 0 ? gx : 1, gy, nmat > 0 ? nmat : 1);
 }
 
 inline int grid1d(long long work, int threads, int cap = 4096) {
@@ -528,8 +542,7 @@ mpps_status launch_scale_copy(const double* A, long long a_bs, double* X, long l
 mpps_status launch_gather_pad(const PadItem* d_list, int count, int n_pad, double* dst,
                               cudaStream_t st) {
     ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
-    const long long nn = (long long)n_pad * n_pad;
-    MPPS_CUDA_TRY(launch_pdl(k_gather_pad, dim3(dim3(grid1d(nn, 256, 64), count)), dim3(256), 0, st, d_list, n_pad, dst));
+    MPPS_CUDA_TRY(launch_pdl(k_gather_pad, grid2d(n_pad, count), dim3(256), 0, st, d_list, n_pad, dst));
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }
@@ -537,8 +550,7 @@ mpps_status launch_gather_pad(const PadItem* d_list, int count, int n_pad, doubl
 mpps_status launch_scatter_unpad(const PadItem* d_list, int count, int n_pad, const double* src,
                                  cudaStream_t st) {
     ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
-    const long long nn = (long long)n_pad * n_pad;
-    MPPS_CUDA_TRY(launch_pdl(k_scatter_unpad, dim3(dim3(grid1d(nn, 256, 64), count)), dim3(256), 0, st, d_list, n_pad, src));
+    MPPS_CUDA_TRY(launch_pdl(k_scatter_unpad, grid2d(n_pad, count), dim3(256), 0, st, d_list, n_pad, src));
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }
@@ -553,8 +565,7 @@ mpps_status launch_sigma(const double* norms, int batch, int* sigma, cudaStream_
 mpps_status launch_select_copy(const double* q0, const double* q1, const int* d_sigma, double* out,
                                int n, int batch, double diag, cudaStream_t st) {
     ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
-    const long long nn = (long long)n * n;
-    MPPS_CUDA_TRY(launch_pdl(k_select_copy, dim3(dim3(grid1d(nn, 256), batch)), dim3(256), 0, st, q0, q1, d_sigma, out, n, diag));
+    MPPS_CUDA_TRY(launch_pdl(k_select_copy, grid2d(n, batch), dim3(256), 0, st, q0, q1, d_sigma, out, n, diag));
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }
@@ -562,8 +573,7 @@ mpps_status launch_select_copy(const double* q0, const double* q1, const int* d_
 mpps_status launch_combine(int n, int batch, const double* extra, long long extra_bs,
                            const Epilogue& ep, cudaStream_t st) {
     ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
-    const long long nn = (long long)n * n;
-    MPPS_CUDA_TRY(launch_pdl(k_combine, dim3(dim3(grid1d(nn, 256), batch)), dim3(256), 0, st, n, extra, extra_bs, ep));
+    MPPS_CUDA_TRY(launch_pdl(k_combine, grid2d(n, batch), dim3(256), 0, st, n, extra, extra_bs, ep));
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }
@@ -576,9 +586,8 @@ mpps_status launch_convert(int fmt, const double* M, long long bs, int n, int ba
         dim3 g((n + 31) / 32, (n + 31) / 32, batch);
         MPPS_CUDA_TRY(launch_pdl(k_convert_t, dim3(g), dim3(dim3(32, 8)), 0, st, fmt, M, bs, n, hi, lo, low_bs, lld, d_scale));
     } else {
-        const long long nn = (long long)n * n;
-        MPPS_CUDA_TRY(launch_pdl(k_convert, dim3(dim3(grid1d(nn, 256), batch)), dim3(256), 0, st, fmt, M, bs, n, hi, lo, low_bs,
-                                                                  lld, d_scale));
+        MPPS_CUDA_TRY(launch_pdl(k_convert, grid2d(n, batch), dim3(256), 0, st, fmt, M, bs, n, hi, lo, low_bs,
+                                 lld, d_scale));
     }
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;

@@ -149,48 +149,64 @@ __device__ __forceinline__ long long slice_off(int t, long long pstride) {
     return (long long)(t >> 1) * pstride + (t & 1) * KB;
 }
 
-// The k digits of x (dst = the row's origin + kpos(j)); x = 0 gives k zero digits.
-__device__ __forceinline__ void put_digits(double x, int e, int k, long long goff,
-                                           __nv_bfloat16* dst, long long pstride) {
+// The KS digits of x (dst = the row's origin + kpos(j)); x = 0 gives KS zero digits.  The
+// slice count is a template parameter in every slicing kernel: with the digit positions
+// known at compile time each digit is a constant shift and mask of G.
+template <int KS>
+__device__ __forceinline__ void put_digits(double x, int e, long long goff, __nv_bfloat16* dst,
+                                           long long pstride) {
     const long long G = scaled_int(x, e) + goff;
-#pragma unroll 1
-    for (int t = 0; t < k; ++t)
+#pragma unroll
+    for (int t = 0; t < KS; ++t)
         dst[slice_off(t, pstride)] = __ushort_as_bfloat16((unsigned short)digit_bits(G, t));
 }
 
-__device__ __forceinline__ int exp_above(double mx) {
-    int e = 0;
-    if (mx > 0.0 && isfinite(mx)) frexp(mx, &e);
-    return e;
+// |x| as the bit pattern of a non-negative double, a NaN as 0: the maximum of these bit
+// patterns is the bit pattern of the maximum magnitude, NaNs ignored (as fmax does).
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+    const unsigned long long a = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffULL;
+    return a > 0x7ff0000000000000ULL ? 0ULL : a;
+}
+
+// The frexp exponent e of a non-negative double given by its bits (value in [2^(e-1), 2^e));
+// 0 for zero and for infinity.  Integer pipe only.
+__device__ __forceinline__ int exp_above(unsigned long long a) {
+    const int ef = (int)(a >> 52);
+    if (a == 0 || ef == 0x7ff) return 0;
+    return ef != 0 ? ef - 1022 : (64 - __clzll((long long)a)) - 1074;
+}
+
+__device__ __forceinline__ unsigned long long max_bits(unsigned long long a, unsigned long long b) {
+    return a > b ? a : b;
 }
 
 // Row slices (A operand) for short rows (n < 256): one warp per row; e_i from the row
 // maximum.
-__global__ void k_slice_rows(const double* __restrict__ M, long long bs, int n, int k,
-                             long long goff, __nv_bfloat16* __restrict__ planes,
+template <int KS>
+__global__ void k_slice_rows(const double* __restrict__ M, long long bs, int n, long long goff, __nv_bfloat16* __restrict__ planes,
                              long long plane_bs, int lld, int* __restrict__ exps) {
     pdl_wait();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row = blockIdx.x * (blockDim.x >> 5) + warp, b = blockIdx.y;
     if (row >= n) return;
     const double* src = M + (long long)b * bs + (long long)row * n;
-    double mx = 0.0;
-    for (int j = lane; j < n; j += 32) mx = fmax(mx, fabs(src[j]));
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    unsigned long long mx = 0;
+    for (int j = lane; j < n; j += 32) mx = max_bits(mx, abs_bits(src[j]));
+    for (int o = 16; o > 0; o >>= 1) mx = max_bits(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     const int e = exp_above(mx);
     if (lane == 0) exps[(long long)b * n + row] = e;
     __nv_bfloat16* dst = planes + (long long)b * plane_bs + (long long)row * 2 * lld;
     const long long pstride = (long long)n * 2 * lld;
     const int n32 = (n + KB - 1) / KB * KB;   // the K tail up to n32 is written as zeros
-    for (int j = lane; j < n32; j += 32) put_digits(j < n ? src[j] : 0.0, e, k, goff, dst + kpos(j), pstride);
+    for (int j = lane; j < n32; j += 32) put_digits<KS>(j < n ? src[j] : 0.0, e, goff, dst + kpos(j), pstride);
 }
 
 // Row slices for rows of up to 256 VPT elements: one 256-thread block per row holds the row
 // in registers (VPT values per thread), reduces its maximum (as the bit pattern of a
 // non-negative double) and writes the k planes: the row is read once.
-template <int VPT>
+template <int KS, int VPT>
 __global__ void __launch_bounds__(256) k_slice_rows_blk(const double* __restrict__ M, long long bs,
-                                                        int n, int k, long long goff,
+                                                        int n, long long goff,
                                                         __nv_bfloat16* __restrict__ planes,
                                                         long long plane_bs, int lld,
                                                         int* __restrict__ exps) {
@@ -204,8 +220,7 @@ __global__ void __launch_bounds__(256) k_slice_rows_blk(const double* __restrict
     for (int i = 0; i < VPT; ++i) {
         const int j = tid + 256 * i;
         v[i] = j < n ? src[j] : 0.0;
-        const unsigned long long a = (unsigned long long)__double_as_longlong(v[i]) & 0x7fffffffffffffffULL;
-        mx = a > mx ? a : mx;
+        mx = max_bits(mx, abs_bits(v[i]));
     }
     for (int o = 16; o > 0; o >>= 1) {
         const unsigned long long t = __shfl_xor_sync(0xffffffffu, mx, o);
@@ -216,7 +231,7 @@ __global__ void __launch_bounds__(256) k_slice_rows_blk(const double* __restrict
     mx = red[0];
 #pragma unroll
     for (int w = 1; w < 8; ++w) mx = red[w] > mx ? red[w] : mx;
-    const int e = exp_above(__longlong_as_double((long long)mx));
+    const int e = exp_above(mx);
     if (tid == 0) exps[(long long)b * n + row] = e;
     __nv_bfloat16* dst = planes + (long long)b * plane_bs + (long long)row * 2 * lld;
     const long long pstride = (long long)n * 2 * lld;
@@ -224,15 +239,15 @@ __global__ void __launch_bounds__(256) k_slice_rows_blk(const double* __restrict
 #pragma unroll
     for (int i = 0; i < VPT; ++i) {
         const int j = tid + 256 * i;
-        if (j < n32) put_digits(v[i], e, k, goff, dst + kpos(j), pstride);
+        if (j < n32) put_digits<KS>(v[i], e, goff, dst + kpos(j), pstride);
     }
 }
 
 // The same with four consecutive columns per thread (n a multiple of 4): two 16-byte loads
 // and one 8-byte store per plane for each group.  NG groups per thread, n <= 1024 NG.
-template <int NG>
+template <int KS, int NG>
 __global__ void __launch_bounds__(256) k_slice_rows_blk4(const double* __restrict__ M, long long bs,
-                                                         int n, int k, long long goff,
+                                                         int n, long long goff,
                                                          __nv_bfloat16* __restrict__ planes,
                                                          long long plane_bs, int lld,
                                                          int* __restrict__ exps) {
@@ -254,8 +269,7 @@ __global__ void __launch_bounds__(256) k_slice_rows_blk4(const double* __restric
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const unsigned long long a = (unsigned long long)__double_as_longlong(v[g][u]) & 0x7fffffffffffffffULL;
-            mx = a > mx ? a : mx;
+            mx = max_bits(mx, abs_bits(v[g][u]));
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -267,7 +281,7 @@ __global__ void __launch_bounds__(256) k_slice_rows_blk4(const double* __restric
     mx = red[0];
 #pragma unroll
     for (int w = 1; w < 8; ++w) mx = red[w] > mx ? red[w] : mx;
-    const int e = exp_above(__longlong_as_double((long long)mx));
+    const int e = exp_above(mx);
     if (tid == 0) exps[(long long)b * n + row] = e;
     __nv_bfloat16* dst = planes + (long long)b * plane_bs + (long long)row * 2 * lld;
     const long long pstride = (long long)n * 2 * lld;
@@ -279,8 +293,8 @@ __global__ void __launch_bounds__(256) k_slice_rows_blk4(const double* __restric
         long long G[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) G[u] = scaled_int(v[g][u], e) + goff;
-#pragma unroll 1
-        for (int t = 0; t < k; ++t) {
+#pragma unroll
+        for (int t = 0; t < KS; ++t) {
             uint2 w;
             w.x = digit_bits(G[0], t) | (digit_bits(G[1], t) << 16);
             w.y = digit_bits(G[2], t) | (digit_bits(G[3], t) << 16);
@@ -296,21 +310,21 @@ __global__ void k_rowexp(const double* __restrict__ M, long long bs, int n, int*
     const int row = blockIdx.x * (blockDim.x >> 5) + warp, b = blockIdx.y;
     if (row >= n) return;
     const double* src = M + (long long)b * bs + (long long)row * n;
-    double mx = 0.0;
-    for (int j = lane; j < n; j += 32) mx = fmax(mx, fabs(src[j]));
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    unsigned long long mx = 0;
+    for (int j = lane; j < n; j += 32) mx = max_bits(mx, abs_bits(src[j]));
+    for (int o = 16; o > 0; o >>= 1) mx = max_bits(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (lane == 0) exps[(long long)b * n + row] = exp_above(mx);
 }
 
 // Row slices, one thread per element (the exponents come from k_rowexp).
-__global__ void k_slice_rows_elem(const double* __restrict__ M, long long bs, int n, int k,
-                                  long long goff, const int* __restrict__ exps,
+template <int KS>
+__global__ void k_slice_rows_elem(const double* __restrict__ M, long long bs, int n, long long goff, const int* __restrict__ exps,
                                   __nv_bfloat16* __restrict__ planes, long long plane_bs, int lld) {
     pdl_wait();
     const int col = blockIdx.x * blockDim.x + threadIdx.x, row = blockIdx.y, b = blockIdx.z;
     if (col >= (n + KB - 1) / KB * KB) return;   // the K tail n..n32-1 is written as zeros
     const int e = exps[(long long)b * n + row];
-    put_digits(col < n ? M[(long long)b * bs + (long long)row * n + col] : 0.0, e, k, goff,
+    put_digits<KS>(col < n ? M[(long long)b * bs + (long long)row * n + col] : 0.0, e, goff,
                planes + (long long)b * plane_bs + (long long)row * 2 * lld + kpos(col),
                (long long)n * 2 * lld);
 }
@@ -328,9 +342,7 @@ __global__ void k_colmax(const double* __restrict__ M, long long bs, int n,
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
         if (r0 + i < n) {
-            const unsigned long long a =
-                (unsigned long long)__double_as_longlong(__ldg(src + (long long)i * n)) & 0x7fffffffffffffffULL;
-            mx = a > mx ? a : mx;
+            mx = max_bits(mx, abs_bits(__ldg(src + (long long)i * n)));
         }
     }
     atomicMax(out + (long long)b * n + col, mx);
@@ -338,8 +350,8 @@ __global__ void k_colmax(const double* __restrict__ M, long long bs, int n,
 
 // Column slices (B operand, written transposed: plane row j = column j of M), 32 x 32 tiles
 // through shared memory; e_j from the column maxima.
-__global__ void k_slice_cols(const double* __restrict__ M, long long bs, int n, int k,
-                             long long goff, const unsigned long long* __restrict__ colmax,
+template <int KS>
+__global__ void k_slice_cols(const double* __restrict__ M, long long bs, int n, long long goff, const unsigned long long* __restrict__ colmax,
                              __nv_bfloat16* __restrict__ planes, long long plane_bs, int lld,
                              int* __restrict__ exps) {
     pdl_wait();
@@ -355,12 +367,12 @@ __global__ void k_slice_cols(const double* __restrict__ M, long long bs, int n, 
     for (int i = threadIdx.y; i < 32; i += blockDim.y) {
         const int col = c0 + i, row = r0 + threadIdx.x;     // output row = column of M
         if (col >= n || row >= n) continue;
-        const int e = exp_above(__longlong_as_double((long long)colmax[(long long)b * n + col]));
+        const int e = exp_above(colmax[(long long)b * n + col]);
         if (blockIdx.y == 0 && threadIdx.x == 0) exps[(long long)b * n + col] = e;
         const long long G = scaled_int(tile[threadIdx.x][i], e) + goff;
         __nv_bfloat16* dst = planes + (long long)b * plane_bs + (long long)col * lld + row;
-#pragma unroll 1
-        for (int t = 0; t < k; ++t)
+#pragma unroll
+        for (int t = 0; t < KS; ++t)
             dst[(long long)t * pstride] = __ushort_as_bfloat16((unsigned short)digit_bits(G, t));
     }
 }
@@ -757,60 +769,95 @@ size_t f64e_plane_elems(int n, int batch, int k) {
     return (size_t)batch * num_pairs(f64e_planes(k)) * n * 2 * low_ld(n);
 }
 
-mpps_status launch_slice_rows(const double* M, long long bs, int n, int batch, int k, void* planes,
-                              int* exps, cudaStream_t st) {
-    k = f64e_planes(k);
-    ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
+namespace {
+
+template <int KS>
+mpps_status slice_rows_k(const double* M, long long bs, int n, int batch, __nv_bfloat16* pl,
+                         int* exps, cudaStream_t st) {
     const int lld = low_ld(n);
-    const long long goff = digit_offset(k), pbs = (long long)num_pairs(k) * n * 2 * lld;
-    __nv_bfloat16* pl = (__nv_bfloat16*)planes;
-    if (batch > 65535) {
-        set_error("slice_rows: batch %d exceeds the grid limit", batch);
-        return MPPS_EINVAL;
-    }
+    const long long goff = digit_offset(KS), pbs = (long long)num_pairs(KS) * n * 2 * lld;
     if (n < 256) {
-        MPPS_CUDA_TRY(launch_pdl(k_slice_rows, dim3(dim3((n + 7) / 8, batch)), dim3(256), 0, st, M, bs, n, k, goff, pl, pbs, lld, exps));
+        MPPS_CUDA_TRY(launch_pdl(k_slice_rows<KS>, dim3(dim3((n + 7) / 8, batch)), dim3(256), 0, st, M, bs, n, goff, pl, pbs, lld, exps));
     } else if (n <= 4096 && n % 4 == 0 && ((uintptr_t)M & 15) == 0 && bs % 2 == 0) {
         const dim3 g(n, batch);
         if (n <= 1024)
-            MPPS_CUDA_TRY(launch_pdl(k_slice_rows_blk4<1>, dim3(g), dim3(256), 0, st, M, bs, n, k, goff, pl, pbs, lld, exps));
+            MPPS_CUDA_TRY(launch_pdl(k_slice_rows_blk4<KS, 1>, dim3(g), dim3(256), 0, st, M, bs, n, goff, pl, pbs, lld, exps));
         else if (n <= 2048)
-            MPPS_CUDA_TRY(launch_pdl(k_slice_rows_blk4<2>, dim3(g), dim3(256), 0, st, M, bs, n, k, goff, pl, pbs, lld, exps));
+            MPPS_CUDA_TRY(launch_pdl(k_slice_rows_blk4<KS, 2>, dim3(g), dim3(256), 0, st, M, bs, n, goff, pl, pbs, lld, exps));
         else
-            MPPS_CUDA_TRY(launch_pdl(k_slice_rows_blk4<4>, dim3(g), dim3(256), 0, st, M, bs, n, k, goff, pl, pbs, lld, exps));
+            MPPS_CUDA_TRY(launch_pdl(k_slice_rows_blk4<KS, 4>, dim3(g), dim3(256), 0, st, M, bs, n, goff, pl, pbs, lld, exps));
     } else if (n <= 4096) {
         const dim3 g(n, batch);
         if (n <= 512)
-            MPPS_CUDA_TRY(launch_pdl(k_slice_rows_blk<2>, dim3(g), dim3(256), 0, st, M, bs, n, k, goff, pl, pbs, lld, exps));
+            MPPS_CUDA_TRY(launch_pdl(k_slice_rows_blk<KS, 2>, dim3(g), dim3(256), 0, st, M, bs, n, goff, pl, pbs, lld, exps));
         else if (n <= 1024)
-            MPPS_CUDA_TRY(launch_pdl(k_slice_rows_blk<4>, dim3(g), dim3(256), 0, st, M, bs, n, k, goff, pl, pbs, lld, exps));
+            MPPS_CUDA_TRY(launch_pdl(k_slice_rows_blk<KS, 4>, dim3(g), dim3(256), 0, st, M, bs, n, goff, pl, pbs, lld, exps));
         else if (n <= 2048)
-            MPPS_CUDA_TRY(launch_pdl(k_slice_rows_blk<8>, dim3(g), dim3(256), 0, st, M, bs, n, k, goff, pl, pbs, lld, exps));
+            MPPS_CUDA_TRY(launch_pdl(k_slice_rows_blk<KS, 8>, dim3(g), dim3(256), 0, st, M, bs, n, goff, pl, pbs, lld, exps));
         else
-            MPPS_CUDA_TRY(launch_pdl(k_slice_rows_blk<16>, dim3(g), dim3(256), 0, st, M, bs, n, k, goff, pl, pbs, lld, exps));
+            MPPS_CUDA_TRY(launch_pdl(k_slice_rows_blk<KS, 16>, dim3(g), dim3(256), 0, st, M, bs, n, goff, pl, pbs, lld, exps));
     } else {
         // long rows: a row-maximum pass, then one thread per element
         MPPS_CUDA_TRY(launch_pdl(k_rowexp, dim3(dim3((n + 7) / 8, batch)), dim3(256), 0, st, M, bs, n, exps));
         MPPS_LAUNCH_CHECK();
-        MPPS_CUDA_TRY(launch_pdl(k_slice_rows_elem, dim3(dim3((n + KB + 127) / 128, n, batch)), dim3(128), 0, st, M, bs, n, k, goff, exps, pl,
-                                                                          pbs, lld));
+        MPPS_CUDA_TRY(launch_pdl(k_slice_rows_elem<KS>, dim3(dim3((n + KB + 127) / 128, n, batch)), dim3(128), 0, st, M, bs, n, goff, exps, pl,
+                                 pbs, lld));
     }
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
+}
+
+template <int KS>
+mpps_status slice_cols_k(const double* M, long long bs, int n, int batch, __nv_bfloat16* pl,
+                         int* exps, unsigned long long* colmax, cudaStream_t st) {
+    const int lld = low_ld(n);
+    MPPS_CUDA_TRY(launch_pdl(k_slice_cols<KS>, dim3(dim3((n + 31) / 32, (n + 31) / 32, batch)), dim3(dim3(32, 8)), 0, st, M, bs, n, digit_offset(KS), colmax, pl, (long long)KS * n * lld, lld,
+        exps));
+    MPPS_LAUNCH_CHECK();
+    return MPPS_OK;
+}
+
+}  // namespace
+
+mpps_status launch_slice_rows(const double* M, long long bs, int n, int batch, int k, void* planes,
+                              int* exps, cudaStream_t st) {
+    k = f64e_planes(k);
+    ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
+    if (batch > 65535) {
+        set_error("slice_rows: batch %d exceeds the grid limit", batch);
+        return MPPS_EINVAL;
+    }
+    __nv_bfloat16* pl = (__nv_bfloat16*)planes;
+    switch (k) {
+        case 1: return slice_rows_k<1>(M, bs, n, batch, pl, exps, st);
+        case 2: return slice_rows_k<2>(M, bs, n, batch, pl, exps, st);
+        case 3: return slice_rows_k<3>(M, bs, n, batch, pl, exps, st);
+        case 4: return slice_rows_k<4>(M, bs, n, batch, pl, exps, st);
+        case 5: return slice_rows_k<5>(M, bs, n, batch, pl, exps, st);
+        case 6: return slice_rows_k<6>(M, bs, n, batch, pl, exps, st);
+        case 7: return slice_rows_k<7>(M, bs, n, batch, pl, exps, st);
+        default: return slice_rows_k<8>(M, bs, n, batch, pl, exps, st);
+    }
 }
 
 mpps_status launch_slice_cols(const double* M, long long bs, int n, int batch, int k, void* planes,
                               int* exps, unsigned long long* colmax, cudaStream_t st) {
     k = f64e_planes(k);
     ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
-    const int lld = low_ld(n);
     MPPS_CUDA_TRY(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * (size_t)batch * n, st));
     MPPS_CUDA_TRY(launch_pdl(k_colmax, dim3(dim3((n + 127) / 128, (n + 15) / 16, batch)), dim3(128), 0, st, M, bs, n, colmax));
     MPPS_LAUNCH_CHECK();
-    MPPS_CUDA_TRY(launch_pdl(k_slice_cols, dim3(dim3((n + 31) / 32, (n + 31) / 32, batch)), dim3(dim3(32, 8)), 0, st, M, bs, n, k, digit_offset(k), colmax, (__nv_bfloat16*)planes, (long long)k * n * lld, lld,
-        exps));
-    MPPS_LAUNCH_CHECK();
-    return MPPS_OK;
+    __nv_bfloat16* pl = (__nv_bfloat16*)planes;
+    switch (k) {
+        case 1: return slice_cols_k<1>(M, bs, n, batch, pl, exps, colmax, st);
+        case 2: return slice_cols_k<2>(M, bs, n, batch, pl, exps, colmax, st);
+        case 3: return slice_cols_k<3>(M, bs, n, batch, pl, exps, colmax, st);
+        case 4: return slice_cols_k<4>(M, bs, n, batch, pl, exps, colmax, st);
+        case 5: return slice_cols_k<5>(M, bs, n, batch, pl, exps, colmax, st);
+        case 6: return slice_cols_k<6>(M, bs, n, batch, pl, exps, colmax, st);
+        case 7: return slice_cols_k<7>(M, bs, n, batch, pl, exps, colmax, st);
+        default: return slice_cols_k<8>(M, bs, n, batch, pl, exps, colmax, st);
+    }
 }
 
 mpps_status launch_gemm_f64e(int k, const void* slicesA, int ksA, const int* eA,
