@@ -125,9 +125,33 @@ __device__ __forceinline__ float to_tf32(double v) {
     return __uint_as_float(u);
 }
 
+// FP64 rounded to nearest even at KEEP significand bits (7: bf16, 10: tf32) on the integer
+// pipe, returned as the FP32 bit pattern of the result (bf16 = its upper half); false for
+// values outside the normal FP32 range (zero keeps its sign and succeeds).  Adding
+// 2^(drop-1) - 1 plus the kept bit's parity rounds the dropped bits half to even; a carry
+// moves into the exponent, up to infinity.
+template <int KEEP>
+__device__ __forceinline__ bool f64_round_bits(double x, unsigned* out) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const unsigned sgn = (unsigned)(u >> 63) << 31;
+    if ((u << 1) == 0) { *out = sgn; return true; }
+    const int e = (int)((u >> 52) & 0x7ff) - 1023 + 127;
+    if (e < 1 || e >= 255) return false;
+    constexpr int DROP = 52 - KEEP;
+    const unsigned long long m = u & 0xFFFFFFFFFFFFFULL;
+    const unsigned long long r = m + ((1ULL << (DROP - 1)) - 1ULL) + ((m >> DROP) & 1ULL);
+    *out = sgn | ((((unsigned)e << KEEP) + (unsigned)(r >> DROP)) << (23 - KEEP));
+    return true;
+}
+
 __device__ __forceinline__ void store_low(int fmt, void* hi, void* lo, long long idx, double v) {
+    unsigned bits;
     if (fmt == MPPS_FMT_BF16) {
-        ((__nv_bfloat16*)hi)[idx] = __double2bfloat16(v);
+        ((__nv_bfloat16*)hi)[idx] = f64_round_bits<7>(v, &bits)
+                                        ? __ushort_as_bfloat16((unsigned short)(bits >> 16))
+                                        : __double2bfloat16(v);
+    } else if (fmt == MPPS_FMT_TF32 && f64_round_bits<10>(v, &bits)) {
+        ((float*)hi)[idx] = __uint_as_float(bits);
     } else if (fmt == MPPS_FMT_BF16X3) {
         __nv_bfloat16 h = __double2bfloat16(v);
         ((__nv_bfloat16*)hi)[idx] = h;
@@ -139,6 +163,29 @@ __device__ __forceinline__ void store_low(int fmt, void* hi, void* lo, long long
     }
 }
 
+// v p for p = +2^k: the exponent field moves on the integer pipe when v and the result are
+// normal; otherwise (or for any other p) one FP64 multiply.
+__device__ __forceinline__ double mul_pow2(double v, double p) {
+    const long long pb = __double_as_longlong(p), vb = __double_as_longlong(v);
+    const int pe = (int)((pb >> 52) & 0x7ff), ve = (int)((vb >> 52) & 0x7ff);
+    if ((pb & (long long)0x800FFFFFFFFFFFFFULL) == 0 && pe > 0 && pe < 0x7ff && ve > 0 && ve < 0x7ff) {
+        const int r = ve + pe - 1023;
+        if (r > 0 && r < 0x7ff) return __longlong_as_double(vb + ((long long)(pe - 1023) << 52));
+    }
+    return v * p;
+}
+
+// FP32 -> FP64 (exact) by assembling the bits; zero, subnormal and non-finite values take the
+// conversion instruction (an FP64-pipe operation).
+__device__ __forceinline__ double f32_to_f64(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned ef = (u >> 23) & 0xffu;
+    if (ef - 1u < 254u)
+        return __hiloint2double((int)((u & 0x80000000u) | ((ef + 896u) << 20) | ((u >> 3) & 0xFFFFFu)),
+                                (int)(u << 29));
+    return (double)f;
+}
+
 // Epilogue value for element (row, col) of batch element b, given the product acc.
 __device__ __forceinline__ double epilogue_value(const Epilogue& ep, int b, int row, int col,
                                                  int n, double acc) {
@@ -146,7 +193,7 @@ __device__ __forceinline__ double epilogue_value(const Epilogue& ep, int b, int 
     double v = acc;
     const long long alb = __double_as_longlong(al);
     if (alb == 0) v = 0.0;                                 // alpha = 0: no product term
-    else if (alb != 0x3FF0000000000000LL) v = al * acc;   // no multiply by 1
+    else if (alb != 0x3FF0000000000000LL) v = mul_pow2(acc, al);   // no multiply by 1
     if (ep.nt >= 0) {
         if (row == col) v += ep.coef[0];
         const double* base = ep.pw + (long long)b * ep.pw_bstride + (long long)row * n + col;
@@ -163,7 +210,7 @@ __device__ __forceinline__ void epilogue_store(const Epilogue& ep, int b, int ro
     if (ep.low_fmt != MPPS_FMT_NONE)
         store_low(ep.low_fmt, ep.low_hi, ep.low_lo,
                   (long long)b * ep.low_bstride + (long long)row * ep.lld + col,
-                  v * (ep.low_scale_b ? ep.low_scale_b[b] : ep.low_scale));
+                  mul_pow2(v, ep.low_scale_b ? ep.low_scale_b[b] : ep.low_scale));
 }
 
 // ---- launchers (defined in the .cu files) ----------------------------------------

@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int e = e0 + u * TC_THREADS;
             const int r = e / TN, c = e % TN, row = m0 + r, col = n0 + c;
             val[u] = (e < TM * TN && row < n && col < n)
-                         ? epilogue_value(ep, b, row, col, n, (double)stile[r * PITCH + c])
+                         ? epilogue_value(ep, b, row, col, n, f32_to_f64(stile[r * PITCH + c]))
                          : 0.0;
         }
 #pragma unroll
