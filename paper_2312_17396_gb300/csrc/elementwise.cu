@@ -12,6 +12,9 @@ namespace {
 constexpr int kColsPerBlock = 128;   // one thread per column (coalesced row reads)
 constexpr int kRowsPerChunk = 64;    // rows summed by one thread before writing a partial
 constexpr int kRowsF32 = 16;         // the same for the FP32 norms: many short chains
+constexpr int kNormCols = 32;        // 2-D norm blocks: 32 columns (lanes) x 8 row slots (warps)
+constexpr int kNormSlots = 8;
+constexpr int kChunkRows = 64;       // rows of one chunk: 8 per row slot
 
 __device__ __forceinline__ double block_max(double v) {
     __shared__ double red[32];
@@ -74,24 +77,38 @@ __global__ void k_norms_finalize(const double* __restrict__ partial, int n, int 
     if (threadIdx.x == 0) norms[(long long)b * q + t] = best;
 }
 
-__global__ void k_colsum_partial(const double* __restrict__ M, long long bs, int n,
-                                 double* __restrict__ partial) {
+// Column sums of |M| over 64-row chunks: 256-thread blocks of 32 columns (the lanes) x 8 row
+// slots (the warps); slot w sums rows w, w+8, ..., w+56 of the chunk (8 loads in flight),
+// then the 8 slot sums are added in slot order.  The chunk partials are summed in chunk
+// order by the finalize kernel: a fixed summation order.
+__global__ void __launch_bounds__(256) k_colsum_partial(const double* __restrict__ M, long long bs,
+                                                        int n, double* __restrict__ partial) {
     pdl_wait();
-    const int col = blockIdx.x * kColsPerBlock + threadIdx.x;
+    __shared__ double red[kNormSlots][kNormCols];
+    const int lane = threadIdx.x & 31, slot = threadIdx.x >> 5;
+    const int col = blockIdx.x * kNormCols + lane;
     const int chunk = blockIdx.y, chunks = gridDim.y, b = blockIdx.z;
-    if (col >= n) return;
-    const double* base = M + (long long)b * bs;
-    const int r0 = chunk * kRowsPerChunk, r1 = min(n, r0 + kRowsPerChunk);
+    const int r0 = chunk * kChunkRows + slot;
     double acc = 0.0;
-    for (int row = r0; row < r1; row += 16) {   // 16 loads in flight, summed in row order
-        double v[16];
+    if (col < n) {
+        const double* base = M + (long long)b * bs + col;
+        double v[kChunkRows / kNormSlots];
 #pragma unroll
-        for (int i = 0; i < 16; ++i)
-            v[i] = row + i < r1 ? __ldg(base + (long long)(row + i) * n + col) : 0.0;
+        for (int k = 0; k < kChunkRows / kNormSlots; ++k) {
+            const int row = r0 + kNormSlots * k;
+            v[k] = row < n ? __ldg(base + (long long)row * n) : 0.0;
+        }
 #pragma unroll
-        for (int i = 0; i < 16; ++i) acc += fabs(v[i]);
+        for (int k = 0; k < kChunkRows / kNormSlots; ++k) acc += fabs(v[k]);
     }
-    partial[((long long)b * chunks + chunk) * n + col] = acc;
+    red[slot][lane] = acc;
+    __syncthreads();
+    if (slot == 0 && col < n) {
+        double sum = red[0][lane];
+#pragma unroll
+        for (int w = 1; w < kNormSlots; ++w) sum += red[w][lane];
+        partial[((long long)b * chunks + chunk) * n + col] = sum;
+    }
 }
 
 // One block per matrix: if norms[b] is within 2^-44 (relative) of a power of two, replace
@@ -169,61 +186,76 @@ __global__ void k_block_norms_partial_f32(const double* __restrict__ pw, long lo
 // The same sums with compile-time bounds (s <= 8, r <= 8, the exp degrees up to 72):
 // the power values and the block accumulators stay in registers.
 constexpr int kRegS = 8, kRegR = 8;
-__global__ void k_block_norms_partial_f32_reg(const double* __restrict__ pw, long long pw_bs,
-                                              int n, int s, int m, NormCoefs cf,
-                                              double* __restrict__ partial) {
+template <int S>
+__global__ void __launch_bounds__(256) k_block_norms_partial_f32_reg(const double* __restrict__ pw,
+                                                                     long long pw_bs, int n, int m,
+                                                                     NormCoefs cf,
+                                                                     double* __restrict__ partial) {
     pdl_wait();
-    const int col = blockIdx.x * kColsPerBlock + threadIdx.x;
+    // 2-D blocks as in k_colsum_partial: 32 columns x 8 row slots over a 64-row chunk, the slot
+    // sums added in slot order.  S (the block size s) is a compile-time constant: the r full
+    // blocks take S FMAs each without predicates, the last block its top + 1.
+    __shared__ float red[kNormSlots][kRegR + 3][kNormCols];
+    const int lane = threadIdx.x & 31, slot = threadIdx.x >> 5;
+    const int col = blockIdx.x * kNormCols + lane;
     const int chunk = blockIdx.y, chunks = gridDim.y, b = blockIdx.z;
-    const int r = m / s, q = r + 3;
-    if (col >= n) return;
+    const int r = m / S, q = r + 3, top = m - S * r;
     float acc[kRegR + 3];
-    float x[kRegS + 1];
+    float x[S + 1];
 #pragma unroll
     for (int t = 0; t < kRegR + 3; ++t) acc[t] = 0.f;
-    const long long nn = (long long)n * n;
-    const double* base = pw + (long long)b * pw_bs + col;
-    const int r0 = chunk * kRowsF32, r1 = min(n, r0 + kRowsF32);
-    for (int row4 = r0; row4 < r1; row4 += 4) {
-      double ld[4][kRegS];   // the powers of four rows: 4 s loads in flight
+    if (col < n) {
+        const long long nn = (long long)n * n;
+        const double* base = pw + (long long)b * pw_bs + col;
+        const int r0 = chunk * kChunkRows + slot;
+#pragma unroll 1
+        for (int k4 = 0; k4 < kChunkRows / kNormSlots; k4 += 4) {
+            double ld[4][S];   // the powers of four rows: 4 S loads in flight
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 4; ++u) {
+                const int row = r0 + kNormSlots * (k4 + u);
 #pragma unroll
-        for (int j = 1; j <= kRegS; ++j)
-            ld[u][j - 1] = (j <= s && row4 + u < r1)
-                               ? __ldg(base + (long long)(row4 + u) * n + (long long)(j - 1) * nn)
-                               : 0.0;
+                for (int j = 0; j < S; ++j)
+                    ld[u][j] = row < n ? __ldg(base + (long long)row * n + (long long)j * nn) : 0.0;
+            }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int row = row4 + u;
-        if (row >= r1) break;
-        x[0] = (row == col) ? 1.f : 0.f;
+            for (int u = 0; u < 4; ++u) {
+                const int row = r0 + kNormSlots * (k4 + u);
+                if (row >= n) break;
+                x[0] = (row == col) ? 1.f : 0.f;
 #pragma unroll
-        for (int j = 1; j <= kRegS; ++j) x[j] = narrow(ld[u][j - 1]);
+                for (int j = 1; j <= S; ++j) x[j] = narrow(ld[u][j - 1]);
 #pragma unroll
-        for (int i = 0; i <= kRegR; ++i) {
-            if (i <= r) {
-                const int top = (i < r) ? s - 1 : m - s * r;
-                float v = 0.f;
+                for (int i = 0; i < kRegR; ++i) {   // full blocks B_0..B_{r-1}
+                    if (i >= r) break;
+                    float v = 0.f;
 #pragma unroll
-                for (int j = 0; j < kRegS; ++j)
-                    if (j <= top) v = fmaf(cf.c[s * i + j], x[j], v);
-                acc[i] += fabsf(v);
+                    for (int j = 0; j < S; ++j) v = fmaf(cf.c[S * i + j], x[j], v);
+                    acc[i] += fabsf(v);
+                }
+                float v = 0.f;                       // B_r: terms j <= top
+#pragma unroll
+                for (int j = 0; j < S; ++j)
+                    if (j <= top) v = fmaf(cf.c[S * r + j], x[j], v);
+                acc[kRegR] += fabsf(v);
+                acc[kRegR + 1] += fabsf(x[S]);
+                acc[kRegR + 2] += fabsf(x[1]);
             }
         }
-        float xs = 0.f;
-#pragma unroll
-        for (int j = 1; j <= kRegS; ++j) if (j == s) xs = x[j];
-        acc[kRegR + 1] += fabsf(xs);
-        acc[kRegR + 2] += fabsf(x[1]);
-      }
     }
-    double* out = partial + ((long long)b * chunks + chunk) * q * n + col;
 #pragma unroll
-    for (int t = 0; t <= kRegR; ++t)
-        if (t <= r) out[(long long)t * n] = (double)acc[t];
-    out[(long long)(r + 1) * n] = (double)acc[kRegR + 1];
-    out[(long long)(r + 2) * n] = (double)acc[kRegR + 2];
+    for (int t = 0; t < kRegR + 3; ++t) red[slot][t][lane] = acc[t];
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < q * kNormCols; idx += blockDim.x) {
+        const int t = idx / kNormCols, l = idx % kNormCols, c = blockIdx.x * kNormCols + l;
+        // accumulator of output t: B_0..B_{r-1}, then B_r, |X_s|, |X_1| in the last three
+        const int ti = t < r ? t : kRegR + (t - r);
+        if (c >= n) continue;
+        float sum = red[0][ti][l];
+#pragma unroll
+        for (int w = 1; w < kNormSlots; ++w) sum += red[w][ti][l];
+        partial[(((long long)b * chunks + chunk) * q + t) * n + c] = (double)sum;
+    }
 }
 
 struct BlockScales {
@@ -249,6 +281,9 @@ __global__ void k_norms_finalize_scaled(const double* __restrict__ partial, int 
                   (unsigned long long)__double_as_longlong(best));
 }
 
+// Out of line, so that the rare case does not get predicated into the fast path.
+__device__ __noinline__ double ldexp_slow(double x, int e) { return ldexp(x, e); }
+
 // x 2^e, exact: the exponent field moves on the integer pipe whenever x and the result are
 // normal doubles (zero stays zero); subnormal or non-finite values take ldexp.
 __device__ __forceinline__ double scale_pow2(double x, int e) {
@@ -257,7 +292,7 @@ __device__ __forceinline__ double scale_pow2(double x, int e) {
     const int ef = (int)((bits >> 52) & 0x7ff);
     if (ef > 0 && ef < 0x7ff && ef + e > 0 && ef + e < 0x7ff)
         return __longlong_as_double(bits + ((long long)e << 52));
-    return ldexp(x, e);
+    return ldexp_slow(x, e);
 }
 
 __global__ void k_scale_copy(const double* __restrict__ A, long long a_bs, double* __restrict__ X,
@@ -458,7 +493,9 @@ size_t block_norms_partial_elems(int n, int batch, int m, int s) {
     return (size_t)batch * chunks * block_norms_count(m, s) * n;
 }
 
-size_t norm1_partial_elems(int n, int batch) { return (size_t)batch * n; }
+size_t norm1_partial_elems(int n, int batch) {
+    return (size_t)batch * ((n + kChunkRows - 1) / kChunkRows) * n;
+}
 
 size_t block_norms_f32_partial_elems(int n, int batch, int m, int s) {
     return (size_t)batch * ((n + kRowsF32 - 1) / kRowsF32) * block_norms_count(m, s) * n;
@@ -481,13 +518,22 @@ mpps_status launch_block_norms_f32(const double* pw, long long pw_bs, int n, int
     }
     sc.c[r + 1] = 1.0;
     sc.c[r + 2] = 1.0;
-    const int chunks = (n + kRowsF32 - 1) / kRowsF32;
-    dim3 g((n + kColsPerBlock - 1) / kColsPerBlock, chunks, batch);
+    const bool reg = s <= kRegS && m / s <= kRegR;
+    const int chunks = reg ? (n + kChunkRows - 1) / kChunkRows : (n + kRowsF32 - 1) / kRowsF32;
     MPPS_CUDA_TRY(cudaMemsetAsync(norms, 0, sizeof(double) * (size_t)batch * q, st));
-    if (s <= kRegS && m / s <= kRegR)
-        MPPS_CUDA_TRY(launch_pdl(k_block_norms_partial_f32_reg, dim3(g), dim3(kColsPerBlock), 0, st, pw, pw_bs, n, s, m, cf, partial));
-    else
-        MPPS_CUDA_TRY(launch_pdl(k_block_norms_partial_f32, dim3(g), dim3(kColsPerBlock), 0, st, pw, pw_bs, n, s, m, cf, partial));
+    const dim3 g2((n + kNormCols - 1) / kNormCols, chunks, batch);
+    if (reg) {
+        switch (s) {
+#define MPPS_BN_CASE(S)                                                                            \
+            case S:                                                                                \
+                MPPS_CUDA_TRY(launch_pdl(k_block_norms_partial_f32_reg<S>, g2, dim3(256), 0, st, pw, pw_bs, n, m, cf, partial)); \
+                break;
+            MPPS_BN_CASE(1) MPPS_BN_CASE(2) MPPS_BN_CASE(3) MPPS_BN_CASE(4)
+            MPPS_BN_CASE(5) MPPS_BN_CASE(6) MPPS_BN_CASE(7) MPPS_BN_CASE(8)
+#undef MPPS_BN_CASE
+        }
+    } else
+        MPPS_CUDA_TRY(launch_pdl(k_block_norms_partial_f32, dim3((n + kColsPerBlock - 1) / kColsPerBlock, chunks, batch), dim3(kColsPerBlock), 0, st, pw, pw_bs, n, s, m, cf, partial));
     MPPS_LAUNCH_CHECK();
     MPPS_CUDA_TRY(launch_pdl(k_norms_finalize_scaled, dim3(dim3(q, (n + 127) / 128, batch)), dim3(128), 0, st, partial, n, chunks, q,
                                                                               sc, norms));
@@ -513,9 +559,9 @@ mpps_status launch_norm1(const double* M, long long bs, int n, int batch, double
                          double* norms, cudaStream_t st) {
     ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
     // fast chunked sums (64-row partials, summed in chunk order) ...
-    const int chunks = (n + kRowsPerChunk - 1) / kRowsPerChunk;
-    dim3 g((n + kColsPerBlock - 1) / kColsPerBlock, chunks, batch);
-    MPPS_CUDA_TRY(launch_pdl(k_colsum_partial, dim3(g), dim3(kColsPerBlock), 0, st, M, bs, n, partial));
+    const int chunks = (n + kChunkRows - 1) / kChunkRows;
+    dim3 g((n + kNormCols - 1) / kNormCols, chunks, batch);
+    MPPS_CUDA_TRY(launch_pdl(k_colsum_partial, dim3(g), dim3(256), 0, st, M, bs, n, partial));
     MPPS_LAUNCH_CHECK();
     MPPS_CUDA_TRY(cudaMemsetAsync(norms, 0, sizeof(double) * (size_t)batch, st));
     BlockScales one;
