@@ -414,9 +414,11 @@ def main():
     outs = {p: [torch.empty_like(a) for a in dA] for p in order}
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
     stream = torch.cuda.current_stream(dev)
-    classes = (mpps.PROF_GEMM_F64, mpps.PROF_GEMM_F64E, mpps.PROF_GEMM_TC, mpps.PROF_ELEMENTWISE)
+    classes = (mpps.PROF_GEMM_F64, mpps.PROF_GEMM_F64E, mpps.PROF_GEMM_TC, mpps.PROF_SLICE,
+               mpps.PROF_ELEMENTWISE)
     cname = {mpps.PROF_GEMM_F64: "gemm_f64", mpps.PROF_GEMM_F64E: "gemm_f64e",
-             mpps.PROF_GEMM_TC: "gemm_tc", mpps.PROF_ELEMENTWISE: "elementwise"}
+             mpps.PROF_GEMM_TC: "gemm_tc", mpps.PROF_SLICE: "slice",
+             mpps.PROF_ELEMENTWISE: "elementwise"}
 
     def step(p, reports=None):
         for k in range(len(dA)):

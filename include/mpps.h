@@ -231,8 +231,9 @@ mpps_status mpps_matmul_noalloc(const double* A, const double* B, double* C, int
 /* Benchmark instrumentation (off by default).  When enabled, every kernel launch of the
  * library is bracketed by two CUDA events recorded on the launch stream and tagged with a
  * kernel class: MPPS_PROF_GEMM_F64 (FP64-pipe products), MPPS_PROF_GEMM_TC (low-precision
- * tensor-core products), MPPS_PROF_ELEMENTWISE (block sums, norms, conversions, slicing,
- * copies), MPPS_PROF_GEMM_F64E (emulated FP64 products).  mpps_profile_read waits for the
+ * tensor-core products), MPPS_PROF_ELEMENTWISE (block sums, norms, conversions, copies),
+ * MPPS_PROF_GEMM_F64E (emulated FP64 products), MPPS_PROF_SLICE (the exact bf16 slicing of
+ * the emulated products' operands, with its column maxima).  mpps_profile_read waits for the
  * recorded events and returns, for one class since the last reset, the number of launches,
  * their summed durations (ms) and their summed executed flops (products: 2 n^3 per matrix
  * times the number of tensor-core products issued; total_work may be NULL).  Do not enable
@@ -241,7 +242,8 @@ mpps_status mpps_matmul_noalloc(const double* A, const double* B, double* C, int
 #define MPPS_PROF_GEMM_TC 1
 #define MPPS_PROF_ELEMENTWISE 2
 #define MPPS_PROF_GEMM_F64E 3
-#define MPPS_PROF_NUM_CLASSES 4
+#define MPPS_PROF_SLICE 4
+#define MPPS_PROF_NUM_CLASSES 5
 void mpps_profile_enable(int on);
 void mpps_profile_reset(void);
 mpps_status mpps_profile_read(int kernel_class, long long* launches, double* total_ms,

@@ -80,7 +80,7 @@ EXPORTS = ("mpps_policy_default", "mpps_plan", "ps_eval", "expm_taylor_ss", "ps_
            "mpps_matmul", "mpps_last_error", "mpps_version", "mpps_profile_enable",
            "mpps_profile_reset", "mpps_profile_read", "mpps_matmul_noalloc",
            "mpps_selftest_bounded_wait", "expm_taylor_ss_grouped", "mpps_release_workspace")
-PROF_GEMM_F64, PROF_GEMM_TC, PROF_ELEMENTWISE, PROF_GEMM_F64E = 0, 1, 2, 3
+PROF_GEMM_F64, PROF_GEMM_TC, PROF_ELEMENTWISE, PROF_GEMM_F64E, PROF_SLICE = 0, 1, 2, 3, 4
 
 
 def lib():

@@ -51,10 +51,14 @@ struct ProfScope {
 // Every kernel of the library is launched with programmatic stream serialization: it may be
 // scheduled while the previous kernel on the stream drains, and it calls pdl_wait() before
 // it touches memory that an earlier kernel writes (griddepcontrol.wait returns when every
-// prerequisite grid has completed and its writes are visible) and lets its own dependents
-// launch at once (their CTAs then wait in pdl_wait()).
-__device__ __forceinline__ void pdl_wait() {
-    asm volatile("griddepcontrol.wait;" ::: "memory");
+// prerequisite grid has completed and its writes are visible).  Kernels whose grid runs in
+// one wave (the persistent products, the slicing kernels, the small reductions) then call
+// pdl_trigger(), which lets their dependents launch at once (those CTAs wait in pdl_wait()
+// on the SMs the grid leaves free).  Multi-wave grids do not: a dependent launched early would
+// hold registers and shared memory on SMs that the grid's later waves still need, so their
+// dependents launch as their last blocks exit.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 

@@ -65,6 +65,7 @@ __global__ void k_block_norms_partial(const double* __restrict__ pw, long long p
 __global__ void k_norms_finalize(const double* __restrict__ partial, int n, int chunks, int q,
                                  double* __restrict__ norms) {
     pdl_wait();
+    pdl_trigger();
     const int t = blockIdx.x, b = blockIdx.y;
     double best = 0.0;
     for (int col = threadIdx.x; col < n; col += blockDim.x) {
@@ -84,6 +85,7 @@ __global__ void k_norms_finalize(const double* __restrict__ partial, int n, int 
 __global__ void __launch_bounds__(256) k_colsum_partial(const double* __restrict__ M, long long bs,
                                                         int n, double* __restrict__ partial) {
     pdl_wait();
+    pdl_trigger();
     __shared__ double red[kNormSlots][kNormCols];
     const int lane = threadIdx.x & 31, slot = threadIdx.x >> 5;
     const int col = blockIdx.x * kNormCols + lane;
@@ -116,6 +118,7 @@ __global__ void __launch_bounds__(256) k_colsum_partial(const double* __restrict
 __global__ void k_norm1_exact_near_pow2(const double* __restrict__ M, long long bs, int n,
                                         double* __restrict__ norms) {
     pdl_wait();
+    pdl_trigger();
     const int b = blockIdx.x;
     const double a = norms[b];
     if (!(a > 0.0) || !isfinite(a)) return;
@@ -267,6 +270,7 @@ struct BlockScales {
 __global__ void k_norms_finalize_scaled(const double* __restrict__ partial, int n, int chunks,
                                         int q, BlockScales sc, double* __restrict__ norms) {
     pdl_wait();
+    pdl_trigger();
     const int t = blockIdx.x, b = blockIdx.z;
     const int col = blockIdx.y * blockDim.x + threadIdx.x;
     double sum = 0.0;
@@ -330,6 +334,7 @@ __global__ void k_scatter_unpad(const PadItem* __restrict__ list, int n_pad,
 // sigma[b] = max(0, ceil(log2 norms[b])) (0 for a non-finite norm), exactly as the host rule.
 __global__ void k_sigma(const double* __restrict__ norms, int batch, int* __restrict__ sigma) {
     pdl_wait();
+    pdl_trigger();
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= batch) return;
     const double a = norms[b];

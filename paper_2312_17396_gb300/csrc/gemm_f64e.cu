@@ -135,11 +135,21 @@ __host__ __device__ inline long long digit_offset(int k) {
 }
 
 // bf16 bits of digit t of G (see above).
-__device__ __forceinline__ unsigned digit_bits(long long G, int t) {
-    const int p = 55 - DIGIT * t;
-    const int v = t == 0 ? (int)(G >> 55) : (int)((G >> p) & 127) - 64;
-    const float f = (__int_as_float(0x4B400000 + v) - 12582912.0f) * __int_as_float((127 - DIGIT * t) << 23);
-    return __float_as_uint(f) >> 16;
+// FP32 bit pattern of v_t 2^-7t (its low 16 bits are zero: the value is exact in bf16).
+// M_t = 1.5 2^(23-7t) has an ulp of 2^-7t, so the float whose bits are bits(M_t) + v_t is
+// M_t + v_t 2^-7t, and subtracting M_t leaves v_t 2^-7t exactly: one integer add and one
+// FP32 subtraction per digit (t is a compile-time constant in every caller).
+__device__ __forceinline__ unsigned digit_f32(long long G, int t) {
+    const int v = t == 0 ? (int)(G >> 55) : (int)((G >> (55 - DIGIT * t)) & 127) - 64;
+    const unsigned mb = 0x4B400000u - ((unsigned)(DIGIT * t) << 23);
+    return __float_as_uint(__uint_as_float(mb + (unsigned)v) - __uint_as_float(mb));
+}
+// bf16 bits of digit t of G (see above).
+__device__ __forceinline__ unsigned digit_bits(long long G, int t) { return digit_f32(G, t) >> 16; }
+// Two digits' bf16 bits packed in one word (a in the low half): the upper halves of the two
+// FP32 patterns, one byte permutation.
+__device__ __forceinline__ unsigned digit_pair(long long Ga, long long Gb, int t) {
+    return __byte_perm(digit_f32(Ga, t), digit_f32(Gb, t), 0x7632);
 }
 
 // Pair layout (see the top of the file): K index j of a row sits at kpos(j) in its pair row,
@@ -186,6 +196,7 @@ template <int KS>
 __global__ void k_slice_rows(const double* __restrict__ M, long long bs, int n, long long goff, __nv_bfloat16* __restrict__ planes,
                              long long plane_bs, int lld, int* __restrict__ exps) {
     pdl_wait();
+    pdl_trigger();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row = blockIdx.x * (blockDim.x >> 5) + warp, b = blockIdx.y;
     if (row >= n) return;
@@ -211,6 +222,7 @@ __global__ void __launch_bounds__(256) k_slice_rows_blk(const double* __restrict
                                                         long long plane_bs, int lld,
                                                         int* __restrict__ exps) {
     pdl_wait();
+    pdl_trigger();
     __shared__ unsigned long long red[8];
     const int row = blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
     const double* src = M + (long long)b * bs + (long long)row * n;
@@ -252,6 +264,7 @@ __global__ void __launch_bounds__(256) k_slice_rows_blk4(const double* __restric
                                                          long long plane_bs, int lld,
                                                          int* __restrict__ exps) {
     pdl_wait();
+    pdl_trigger();
     __shared__ unsigned long long red[8];
     const int row = blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
     const double* src = M + (long long)b * bs + (long long)row * n;
@@ -296,8 +309,8 @@ __global__ void __launch_bounds__(256) k_slice_rows_blk4(const double* __restric
 #pragma unroll
         for (int t = 0; t < KS; ++t) {
             uint2 w;
-            w.x = digit_bits(G[0], t) | (digit_bits(G[1], t) << 16);
-            w.y = digit_bits(G[2], t) | (digit_bits(G[3], t) << 16);
+            w.x = digit_pair(G[0], G[1], t);
+            w.y = digit_pair(G[2], G[3], t);
             *reinterpret_cast<uint2*>(dst + slice_off(t, pstride) + kpos(j)) = w;
         }
     }
@@ -306,6 +319,7 @@ __global__ void __launch_bounds__(256) k_slice_rows_blk4(const double* __restric
 // Row maxima of |M| -> exponents e_i (one warp per row), for rows too long for the above.
 __global__ void k_rowexp(const double* __restrict__ M, long long bs, int n, int* __restrict__ exps) {
     pdl_wait();
+    pdl_trigger();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row = blockIdx.x * (blockDim.x >> 5) + warp, b = blockIdx.y;
     if (row >= n) return;
@@ -321,6 +335,7 @@ template <int KS>
 __global__ void k_slice_rows_elem(const double* __restrict__ M, long long bs, int n, long long goff, const int* __restrict__ exps,
                                   __nv_bfloat16* __restrict__ planes, long long plane_bs, int lld) {
     pdl_wait();
+    pdl_trigger();
     const int col = blockIdx.x * blockDim.x + threadIdx.x, row = blockIdx.y, b = blockIdx.z;
     if (col >= (n + KB - 1) / KB * KB) return;   // the K tail n..n32-1 is written as zeros
     const int e = exps[(long long)b * n + row];
@@ -334,6 +349,7 @@ __global__ void k_slice_rows_elem(const double* __restrict__ M, long long bs, in
 __global__ void k_colmax(const double* __restrict__ M, long long bs, int n,
                          unsigned long long* __restrict__ out) {
     pdl_wait();
+    pdl_trigger();
     const int col = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.z;
     if (col >= n) return;
     const int r0 = blockIdx.y * 16;
@@ -348,32 +364,39 @@ __global__ void k_colmax(const double* __restrict__ M, long long bs, int n,
     atomicMax(out + (long long)b * n + col, mx);
 }
 
-// Column slices (B operand, written transposed: plane row j = column j of M), 32 x 32 tiles
-// through shared memory; e_j from the column maxima.
+// Column slices (B operand, written transposed: plane row j = column j of M) through a
+// shared 64-row x 32-column block of M (stored column-major, pitch 65); e_j from the column
+// maxima.  Each thread turns two consecutive rows of one column (two consecutive K of the
+// plane row) into digits and stores both per plane in one 4-byte word.
 template <int KS>
-__global__ void k_slice_cols(const double* __restrict__ M, long long bs, int n, long long goff, const unsigned long long* __restrict__ colmax,
-                             __nv_bfloat16* __restrict__ planes, long long plane_bs, int lld,
-                             int* __restrict__ exps) {
+__global__ void __launch_bounds__(256) k_slice_cols(const double* __restrict__ M, long long bs,
+                                                    int n, long long goff,
+                                                    const unsigned long long* __restrict__ colmax,
+                                                    __nv_bfloat16* __restrict__ planes,
+                                                    long long plane_bs, int lld,
+                                                    int* __restrict__ exps) {
     pdl_wait();
-    __shared__ double tile[32][33];
-    const int b = blockIdx.z, r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    pdl_trigger();
+    __shared__ double tile[32][65];
+    const int b = blockIdx.z, r0 = blockIdx.y * 64, c0 = blockIdx.x * 32;
     const double* src = M + (long long)b * bs;
-    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    for (int i = threadIdx.y; i < 64; i += blockDim.y) {
         const int row = r0 + i, col = c0 + threadIdx.x;
-        tile[i][threadIdx.x] = (row < n && col < n) ? src[(long long)row * n + col] : 0.0;
+        tile[threadIdx.x][i] = (row < n && col < n) ? src[(long long)row * n + col] : 0.0;
     }
     __syncthreads();
     const long long pstride = (long long)n * lld;
     for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-        const int col = c0 + i, row = r0 + threadIdx.x;     // output row = column of M
-        if (col >= n || row >= n) continue;
+        const int col = c0 + i, k0 = r0 + 2 * threadIdx.x;   // plane row col, K k0 and k0 + 1
+        if (col >= n || k0 >= n) continue;
         const int e = exp_above(colmax[(long long)b * n + col]);
         if (blockIdx.y == 0 && threadIdx.x == 0) exps[(long long)b * n + col] = e;
-        const long long G = scaled_int(tile[threadIdx.x][i], e) + goff;
-        __nv_bfloat16* dst = planes + (long long)b * plane_bs + (long long)col * lld + row;
+        const long long G0 = scaled_int(tile[i][2 * threadIdx.x], e) + goff;
+        const long long G1 = scaled_int(tile[i][2 * threadIdx.x + 1], e) + goff;   // 0 past n
+        unsigned* dst = reinterpret_cast<unsigned*>(planes + (long long)b * plane_bs +
+                                                    (long long)col * lld + k0);
 #pragma unroll
-        for (int t = 0; t < KS; ++t)
-            dst[(long long)t * pstride] = __ushort_as_bfloat16((unsigned short)digit_bits(G, t));
+        for (int t = 0; t < KS; ++t) dst[(long long)t * (pstride / 2)] = digit_pair(G0, G1, t);
     }
 }
 
@@ -524,6 +547,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     pdl_wait();   // barrier init, TMEM allocation and tensor-map prefetch overlap the previous kernel
+    pdl_trigger();
 
     if (warp == EPI_WARPS) {
         if (lane == 0) {   // TMA producer
@@ -811,7 +835,7 @@ template <int KS>
 mpps_status slice_cols_k(const double* M, long long bs, int n, int batch, __nv_bfloat16* pl,
                          int* exps, unsigned long long* colmax, cudaStream_t st) {
     const int lld = low_ld(n);
-    MPPS_CUDA_TRY(launch_pdl(k_slice_cols<KS>, dim3(dim3((n + 31) / 32, (n + 31) / 32, batch)), dim3(dim3(32, 8)), 0, st, M, bs, n, digit_offset(KS), colmax, pl, (long long)KS * n * lld, lld,
+    MPPS_CUDA_TRY(launch_pdl(k_slice_cols<KS>, dim3(dim3((n + 31) / 32, (n + 63) / 64, batch)), dim3(dim3(32, 8)), 0, st, M, bs, n, digit_offset(KS), colmax, pl, (long long)KS * n * lld, lld,
         exps));
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
@@ -822,7 +846,7 @@ mpps_status slice_cols_k(const double* M, long long bs, int n, int batch, __nv_b
 mpps_status launch_slice_rows(const double* M, long long bs, int n, int batch, int k, void* planes,
                               int* exps, cudaStream_t st) {
     k = f64e_planes(k);
-    ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
+    ProfScope prof(MPPS_PROF_SLICE, st);
     if (batch > 65535) {
         set_error("slice_rows: batch %d exceeds the grid limit", batch);
         return MPPS_EINVAL;
@@ -843,7 +867,7 @@ mpps_status launch_slice_rows(const double* M, long long bs, int n, int batch, i
 mpps_status launch_slice_cols(const double* M, long long bs, int n, int batch, int k, void* planes,
                               int* exps, unsigned long long* colmax, cudaStream_t st) {
     k = f64e_planes(k);
-    ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
+    ProfScope prof(MPPS_PROF_SLICE, st);
     MPPS_CUDA_TRY(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * (size_t)batch * n, st));
     MPPS_CUDA_TRY(launch_pdl(k_colmax, dim3(dim3((n + 127) / 128, (n + 15) / 16, batch)), dim3(128), 0, st, M, bs, n, colmax));
     MPPS_LAUNCH_CHECK();

@@ -132,6 +132,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     pdl_wait();   // barrier init, TMEM allocation and tensor-map prefetch overlap the previous kernel
+    pdl_trigger();
 
     if (warp == 0 && lane == 0) {
         // TMA producer
