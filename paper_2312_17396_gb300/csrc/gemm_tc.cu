@@ -88,7 +88,8 @@ __host__ __device__ constexpr int smem_bytes() {
     return Tc<FMT>::kStages * Tc<FMT>::kOps * TILE_BYTES + 1024 + 256;
 }
 
-constexpr int TC_THREADS = 256;           // 8 warps: all of them run the epilogue
+constexpr int TC_THREADS = 512;           // 16 warps: all of them run the epilogue
+constexpr int TC_COLGROUPS = TC_THREADS / 128;   // warps per TMEM lane quarter
 
 template <int FMT, int TN>
 __global__ void __launch_bounds__(TC_THREADS, 1)
@@ -187,10 +188,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     mbar_wait(done, 0, err);
     tc_fence_after();
 
-    // Epilogue: the FP32 tile goes from TMEM to shared memory (the ring is idle now; warps w
-    // and w + 4 share TMEM lanes 32 (w % 4).. and split the columns), then all 256 threads
-    // walk it row-major, so that the reads of the power table and the stores are coalesced
-    // along rows, with four elements' loads in flight per thread.
+    // Epilogue: the FP32 tile goes from TMEM to shared memory (the ring is idle now; warps w,
+    // w + 4, w + 8, w + 12 share TMEM lanes 32 (w % 4).. and split the columns), then all 512
+    // threads walk it row-major, so that the reads of the power table and the stores are
+    // coalesced along rows, with four elements' loads in flight per thread: the FP64 block
+    // sums of the fused Horner add are latency-bound, and 16 warps hide twice as much.
     constexpr int PITCH = TN + 1;
     float* stile = (float*)smem;
     {
@@ -198,7 +200,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const uint32_t lane_base = (uint32_t)(q4 * 32) << 16;
         const int row = q4 * 32 + lane;
 #pragma unroll
-        for (int c0 = 32 * h; c0 < TN; c0 += 64) {
+        for (int c0 = 32 * h; c0 < TN; c0 += 32 * TC_COLGROUPS) {
             uint32_t v[32];
             tmem_ld32(tmem + lane_base + (uint32_t)c0, v);
 #pragma unroll
