@@ -119,6 +119,19 @@ __device__ __forceinline__ long long scaled_int(double x, int e) {
     return bits < 0 ? -F : F;
 }
 
+// The same value through the FP64 pipe, which the slicing kernels otherwise leave idle: x 2^(62-e)
+// is formed exactly by moving the exponent field, and the conversion instruction rounds it to
+// the nearest integer, ties to even.  Zero, subnormal and non-finite x, and products below
+// the normal range, take the integer path above.
+__device__ __noinline__ long long scaled_int_slow(double x, int e) { return scaled_int(x, e); }
+__device__ __forceinline__ long long scaled_int_fp64(double x, int e) {
+    const long long bits = __double_as_longlong(x);
+    const int ef = (int)((bits >> 52) & 0x7ff);
+    if (ef != 0 && ef != 0x7ff && ef + 62 - e > 0)
+        return __double2ll_rn(__longlong_as_double(bits + ((long long)(62 - e) << 52)));
+    return scaled_int_slow(x, e);
+}
+
 // Signed base-128 digits of x / 2^e (|x| < 2^e), in offset form: with F = round(x 2^(62-e))
 // (|F| < 2^62), p_t = 55 - 7t and G = F + 2^(p_{k-1} - 1) + sum_{t=1}^{k-1} 64 2^(p_t),
 //   v_0 = floor(G / 2^55),   v_t = ((G >> p_t) mod 128) - 64   (t >= 1),
@@ -165,7 +178,7 @@ __device__ __forceinline__ long long slice_off(int t, long long pstride) {
 template <int KS>
 __device__ __forceinline__ void put_digits(double x, int e, long long goff, __nv_bfloat16* dst,
                                            long long pstride) {
-    const long long G = scaled_int(x, e) + goff;
+    const long long G = scaled_int_fp64(x, e) + goff;
 #pragma unroll
     for (int t = 0; t < KS; ++t)
         dst[slice_off(t, pstride)] = __ushort_as_bfloat16((unsigned short)digit_bits(G, t));
@@ -305,7 +318,7 @@ __global__ void __launch_bounds__(256) k_slice_rows_blk4(const double* __restric
         if (j >= n32) continue;
         long long G[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) G[u] = scaled_int(v[g][u], e) + goff;
+        for (int u = 0; u < 4; ++u) G[u] = scaled_int_fp64(v[g][u], e) + goff;
 #pragma unroll
         for (int t = 0; t < KS; ++t) {
             uint2 w;
@@ -391,8 +404,8 @@ __global__ void __launch_bounds__(256) k_slice_cols(const double* __restrict__ M
         if (col >= n || k0 >= n) continue;
         const int e = exp_above(colmax[(long long)b * n + col]);
         if (blockIdx.y == 0 && threadIdx.x == 0) exps[(long long)b * n + col] = e;
-        const long long G0 = scaled_int(tile[i][2 * threadIdx.x], e) + goff;
-        const long long G1 = scaled_int(tile[i][2 * threadIdx.x + 1], e) + goff;   // 0 past n
+        const long long G0 = scaled_int_fp64(tile[i][2 * threadIdx.x], e) + goff;
+        const long long G1 = scaled_int_fp64(tile[i][2 * threadIdx.x + 1], e) + goff;   // 0 past n
         unsigned* dst = reinterpret_cast<unsigned*>(planes + (long long)b * plane_bs +
                                                     (long long)col * lld + k0);
 #pragma unroll
