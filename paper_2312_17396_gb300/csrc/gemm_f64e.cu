@@ -184,18 +184,26 @@ __device__ __forceinline__ void put_digits(double x, int e, long long goff, __nv
         dst[slice_off(t, pstride)] = __ushort_as_bfloat16((unsigned short)digit_bits(G, t));
 }
 
-// |x| as the bit pattern of a non-negative double, a NaN as 0: the maximum of these bit
-// patterns is the bit pattern of the maximum magnitude, NaNs ignored (as fmax does).
+// |x| as the bit pattern of a non-negative double, infinity for a NaN: the maximum of these
+// bit patterns is the bit pattern of the maximum magnitude, infinity when any entry is not
+// finite.
 __device__ __forceinline__ unsigned long long abs_bits(double x) {
     const unsigned long long a = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffULL;
-    return a > 0x7ff0000000000000ULL ? 0ULL : a;
+    return a > 0x7ff0000000000000ULL ? 0x7ff0000000000000ULL : a;
 }
 
+// Exponent recorded for a row or column with a non-finite entry.  Its digits are all zero
+// (scaled_int turns every entry into 0 at this exponent) and the epilogue writes NaN for
+// every product entry that involves it, as the FP64 product would have (up to inf vs NaN).
+constexpr int kNonFinite = 1 << 29;
+constexpr int kExpLimit = 1 << 20;   // e_A + e_B at or above it: a non-finite row or column
+
 // The frexp exponent e of a non-negative double given by its bits (value in [2^(e-1), 2^e));
-// 0 for zero and for infinity.  Integer pipe only.
+// 0 for zero, kNonFinite for infinity.  Integer pipe only.
 __device__ __forceinline__ int exp_above(unsigned long long a) {
     const int ef = (int)(a >> 52);
-    if (a == 0 || ef == 0x7ff) return 0;
+    if (a == 0) return 0;
+    if (ef == 0x7ff) return kNonFinite;
     return ef != 0 ? ef - 1022 : (64 - __clzll((long long)a)) - 1074;
 }
 
@@ -450,6 +458,7 @@ __device__ __forceinline__ bool f32_to_f64_scaled(float f, int s, double* out) {
 // unrolled fast path.
 __device__ __noinline__ double f64e_slow_value(bool flushed, double acc, long long W, float T,
                                                int e) {
+    if (e >= kExpLimit) return __longlong_as_double(0x7ff8000000000000LL);   // non-finite input
     return flushed ? ldexp(fma(acc, 0x1p-35, (double)T), e - 14)
                    : ldexp(fma((double)W, 0x1p-35, (double)T), e - 14);
 }
@@ -699,7 +708,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                         const int e = er + __ldg(eB + (long long)b * n + min(cb + j, n - 1));
                         double wd = 0.0, td = 0.0;
                         // 2^(e-49) W and 2^(e-14) T formed on the integer pipe, one FP64 add
-                        fast = fast && i64_to_f64_scaled(W[j], e - 49, &wd) &&
+                        fast = fast && e < kExpLimit && i64_to_f64_scaled(W[j], e - 49, &wd) &&
                                f32_to_f64_scaled(T[j], e - 14, &td);
                         val[u] = wd + td;
                     }

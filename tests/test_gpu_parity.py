@@ -319,6 +319,42 @@ def test_matmul_f64e_extreme_magnitudes(mpps, shift):
     assert np.all(err <= bound)
 
 
+@pytest.mark.parametrize("bad", [np.nan, np.inf, -np.inf])
+@pytest.mark.parametrize("n", [130, 1024, 4200])
+def test_matmul_f64e_nonfinite_entries(mpps, bad, n):
+    """A non-finite entry of A poisons its row of the product and one of B its column, as in
+    the FP64 product (the emulated path writes NaN there, where FP64 may give +-inf); every
+    other entry keeps the emulated product's accuracy.  n = 4200 also takes the path that
+    flushes the integer accumulator to FP64."""
+    rng = np.random.default_rng(11)
+    A = rng.standard_normal((n, n)); B = rng.standard_normal((n, n))
+    ia, ka = 3, n // 2
+    kb, jb = n - 2, n // 3
+    A[ia, ka] = bad; B[kb, jb] = bad
+    C = host(mpps.matmul(dev(A[None]), dev(B[None]), "f64e8"))[0]
+    assert np.all(np.isnan(C[ia, :])) and np.all(np.isnan(C[:, jb]))
+    rows = [0, n - 1, ia + 1]; cols = [0, n - 1, jb + 1]
+    assert np.all(np.isfinite(C[np.ix_(rows, cols)]))
+    Ac = np.where(np.isfinite(A), A, 0.0); Bc = np.where(np.isfinite(B), B, 0.0)
+    ref = Ac[rows, :] @ Bc[:, cols]
+    bound = 1e-12 * (np.abs(Ac[rows, :]) @ np.abs(Bc[:, cols]))
+    # rows and columns without a non-finite entry (A's column ka and B's row kb hold finite
+    # values elsewhere, so the sampled rows and columns are unaffected)
+    assert np.all(np.abs(C[np.ix_(rows, cols)] - ref) <= bound)
+
+
+def test_expm_nonfinite_input_propagates(mpps):
+    """A NaN entry makes every entry of exp(A) NaN on the FP64 pipe (the powers spread it);
+    the emulated path must not drop it: its slicing records the row and column and the
+    product writes NaN there, so the powers spread it the same way."""
+    n = 96
+    A = inputs.gaussian_matrix(n, seed=5, norm1=2.0)
+    A[7, 40] = np.nan
+    for pol in (mpps.FIXED, mpps.FIXED_E, mpps.NS_E):
+        E = host(mpps.expm(dev(A), m=18, policy=pol))
+        assert np.all(np.isnan(E)), pol
+
+
 def test_matmul_f64e_multichunk_sampled(mpps):
     """n = 2100 crosses the 2048-long exact-accumulation chunk (the exact diagonals are
     drained into the 64-bit integer accumulator twice); 8 sampled columns against an
