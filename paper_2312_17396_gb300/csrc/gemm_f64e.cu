@@ -467,6 +467,34 @@ __device__ __noinline__ void f64e_store(const Epilogue& ep, int b, int row, int 
     epilogue_store(ep, b, row, col, n, epilogue_value(ep, b, row, col, n, v));
 }
 
+// The fused Horner add (block sum from the power table), alpha = 1, for four products v0..v3
+// at columns col0..col0+3 of row `row` (inside the matrix, every row pointer 32-byte aligned):
+// the same operations in the same order as epilogue_value, with the power-table rows read
+// and the results stored four consecutive doubles at a time.
+__device__ __noinline__ void f64e_sum_store4(const Epilogue& ep, int b, int row, int col0, int n,
+                                             double v0, double v1, double v2, double v3) {
+    const long long off = (long long)row * n + col0;
+    double v[4] = {v0, v1, v2, v3};
+    const int dc = row - col0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        if (dc == u) v[u] += ep.coef[0];
+    const long long nn = (long long)n * n;
+    const double* pwrow = ep.pw + (long long)b * ep.pw_bstride + off;
+    for (int j = 1; j <= ep.nt; ++j) {
+        const double* pp = pwrow + (long long)(j - 1) * nn;
+        const double2 p01 = __ldg(reinterpret_cast<const double2*>(pp));
+        const double2 p23 = __ldg(reinterpret_cast<const double2*>(pp + 2));
+        const double c = ep.coef[j];
+        v[0] = fma(c, p01.x, v[0]);
+        v[1] = fma(c, p01.y, v[1]);
+        v[2] = fma(c, p23.x, v[2]);
+        v[3] = fma(c, p23.y, v[3]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) epilogue_store(ep, b, row, col0 + u, n, v[u]);
+}
+
 // Tile `id` -> (matrix slot z, first row, first column); row blocks are walked in groups of
 // RASTER_G with the column index outermost inside a group, so that the CTAs working at the
 // same time share few B column blocks and few A row blocks.
@@ -641,9 +669,14 @@ __global__ void __launch_bounds__(THREADS, 1)
     } else {
         // epilogue warps: row = m0 + 32 (warp % 4) + lane, columns n0 + 16 (warp / 4) + j
         // (a plain epilogue stores the product alone, four doubles at a time where aligned)
-        const bool ep_plain = ep.nt < 0 && ep.add == nullptr && ep.low_fmt == MPPS_FMT_NONE &&
-                              ep.alpha_b == nullptr &&
-                              __double_as_longlong(ep.alpha) == 0x3FF0000000000000LL;
+        const bool alpha1 = ep.alpha_b == nullptr &&
+                            __double_as_longlong(ep.alpha) == 0x3FF0000000000000LL;
+        const bool ep_plain = ep.nt < 0 && ep.add == nullptr && ep.low_fmt == MPPS_FMT_NONE && alpha1;
+        // fused Horner add, alpha = 1, with 32-byte aligned power-table rows (n a multiple of
+        // 4, aligned bases and batch strides)
+        const bool ep_sum = alpha1 && ep.nt >= 0 && ep.add == nullptr && (n & 3) == 0 &&
+                            ((((uintptr_t)ep.pw | (uintptr_t)ep.out) & 31) == 0) &&
+                            ((ep.pw_bstride | ep.out_bstride) & 3) == 0;
         const int q4 = warp & 3, h = warp >> 2;   // lane quarter, column group
         const uint32_t lane_base = (uint32_t)(q4 * 32) << 16;
         uint32_t gc = 0;
@@ -715,6 +748,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                     if (plain && fast && vec4) {   // four consecutive doubles, 32-byte aligned
                         asm volatile("st.global.v4.f64 [%0], {%1, %2, %3, %4};" ::"l"(orow + g),
                                      "d"(val[0]), "d"(val[1]), "d"(val[2]), "d"(val[3]) : "memory");
+                    } else if (fast && ep_sum && cb + EPI_COLS <= n && nchunks <= FLUSH) {
+                        f64e_sum_store4(ep, b, row, cb + g, n, val[0], val[1], val[2], val[3]);
                     } else {
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
