@@ -467,29 +467,40 @@ __device__ __noinline__ void f64e_store(const Epilogue& ep, int b, int row, int 
     epilogue_store(ep, b, row, col, n, epilogue_value(ep, b, row, col, n, v));
 }
 
-// The fused Horner add (block sum from the power table), alpha = 1, for four products v0..v3
-// at columns col0..col0+3 of row `row` (inside the matrix, every row pointer 32-byte aligned):
-// the same operations in the same order as epilogue_value, with the power-table rows read
-// and the results stored four consecutive doubles at a time.
+// The fused Horner add (block sum from the power table) and/or addend, alpha = 1, for four
+// products v0..v3 at columns col0..col0+3 of row `row` (inside the matrix, the power-table
+// and addend rows 16-byte aligned): the same operations in the same order as
+// epilogue_value, with those rows read two doubles at a time.
 __device__ __noinline__ void f64e_sum_store4(const Epilogue& ep, int b, int row, int col0, int n,
                                              double v0, double v1, double v2, double v3) {
     const long long off = (long long)row * n + col0;
     double v[4] = {v0, v1, v2, v3};
-    const int dc = row - col0;
+    if (ep.nt >= 0) {
+        const int dc = row - col0;
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
-        if (dc == u) v[u] += ep.coef[0];
-    const long long nn = (long long)n * n;
-    const double* pwrow = ep.pw + (long long)b * ep.pw_bstride + off;
-    for (int j = 1; j <= ep.nt; ++j) {
-        const double* pp = pwrow + (long long)(j - 1) * nn;
-        const double2 p01 = __ldg(reinterpret_cast<const double2*>(pp));
-        const double2 p23 = __ldg(reinterpret_cast<const double2*>(pp + 2));
-        const double c = ep.coef[j];
-        v[0] = fma(c, p01.x, v[0]);
-        v[1] = fma(c, p01.y, v[1]);
-        v[2] = fma(c, p23.x, v[2]);
-        v[3] = fma(c, p23.y, v[3]);
+        for (int u = 0; u < 4; ++u)
+            if (dc == u) v[u] += ep.coef[0];
+        const long long nn = (long long)n * n;
+        const double* pwrow = ep.pw + (long long)b * ep.pw_bstride + off;
+        for (int j = 1; j <= ep.nt; ++j) {
+            const double* pp = pwrow + (long long)(j - 1) * nn;
+            const double2 p01 = __ldg(reinterpret_cast<const double2*>(pp));
+            const double2 p23 = __ldg(reinterpret_cast<const double2*>(pp + 2));
+            const double c = ep.coef[j];
+            v[0] = fma(c, p01.x, v[0]);
+            v[1] = fma(c, p01.y, v[1]);
+            v[2] = fma(c, p23.x, v[2]);
+            v[3] = fma(c, p23.y, v[3]);
+        }
+    }
+    if (ep.add) {
+        const double* ap = ep.add + (long long)b * ep.add_bstride + off;
+        const double2 a01 = *reinterpret_cast<const double2*>(ap);
+        const double2 a23 = *reinterpret_cast<const double2*>(ap + 2);
+        v[0] = fma(ep.add_coef, a01.x, v[0]);
+        v[1] = fma(ep.add_coef, a01.y, v[1]);
+        v[2] = fma(ep.add_coef, a23.x, v[2]);
+        v[3] = fma(ep.add_coef, a23.y, v[3]);
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) epilogue_store(ep, b, row, col0 + u, n, v[u]);
@@ -672,11 +683,11 @@ __global__ void __launch_bounds__(THREADS, 1)
         const bool alpha1 = ep.alpha_b == nullptr &&
                             __double_as_longlong(ep.alpha) == 0x3FF0000000000000LL;
         const bool ep_plain = ep.nt < 0 && ep.add == nullptr && ep.low_fmt == MPPS_FMT_NONE && alpha1;
-        // fused Horner add, alpha = 1, with 32-byte aligned power-table rows (n a multiple of
-        // 4, aligned bases and batch strides)
-        const bool ep_sum = alpha1 && ep.nt >= 0 && ep.add == nullptr && (n & 3) == 0 &&
-                            ((((uintptr_t)ep.pw | (uintptr_t)ep.out) & 31) == 0) &&
-                            ((ep.pw_bstride | ep.out_bstride) & 3) == 0;
+        // fused Horner add and/or addend, alpha = 1, with 16-byte aligned power-table and
+        // addend rows (n a multiple of 4, aligned bases and even batch strides)
+        const bool ep_sum = alpha1 && (ep.nt >= 0 || ep.add != nullptr) && (n & 3) == 0 &&
+                            ((((uintptr_t)ep.pw | (uintptr_t)ep.add) & 15) == 0) &&
+                            ((ep.pw_bstride | ep.add_bstride) & 1) == 0;
         const int q4 = warp & 3, h = warp >> 2;   // lane quarter, column group
         const uint32_t lane_base = (uint32_t)(q4 * 32) << 16;
         uint32_t gc = 0;
