@@ -208,6 +208,47 @@ __device__ __forceinline__ double epilogue_value(const Epilogue& ep, int b, int 
     return v;
 }
 
+// epilogue_value for the four products v[0..3] at columns col0..col0+3 of one row (all inside
+// the matrix; power-table and addend rows 16-byte aligned): the same operations in the same
+// order, with each power-table and addend row read two doubles at a time.
+__device__ __forceinline__ void epilogue_value4(const Epilogue& ep, int b, int row, int col0, int n,
+                                                double (&v)[4]) {
+    const double al = ep.alpha_b ? ep.alpha_b[b] : ep.alpha;
+    const long long alb = __double_as_longlong(al);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        if (alb == 0) v[u] = 0.0;
+        else if (alb != 0x3FF0000000000000LL) v[u] = mul_pow2(v[u], al);
+    }
+    const long long off = (long long)row * n + col0;
+    if (ep.nt >= 0) {
+        const int dc = row - col0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (dc == u) v[u] += ep.coef[0];
+        const double* base = ep.pw + (long long)b * ep.pw_bstride + off;
+        const long long nn = (long long)n * n;
+        for (int j = 1; j <= ep.nt; ++j) {
+            const double* pp = base + (long long)(j - 1) * nn;
+            const double2 p01 = __ldg(reinterpret_cast<const double2*>(pp));
+            const double2 p23 = __ldg(reinterpret_cast<const double2*>(pp + 2));
+            v[0] += ep.coef[j] * p01.x;
+            v[1] += ep.coef[j] * p01.y;
+            v[2] += ep.coef[j] * p23.x;
+            v[3] += ep.coef[j] * p23.y;
+        }
+    }
+    if (ep.add) {
+        const double* ap = ep.add + (long long)b * ep.add_bstride + off;
+        const double2 a01 = *reinterpret_cast<const double2*>(ap);
+        const double2 a23 = *reinterpret_cast<const double2*>(ap + 2);
+        v[0] += ep.add_coef * a01.x;
+        v[1] += ep.add_coef * a01.y;
+        v[2] += ep.add_coef * a23.x;
+        v[3] += ep.add_coef * a23.y;
+    }
+}
+
 __device__ __forceinline__ void epilogue_store(const Epilogue& ep, int b, int row, int col, int n,
                                                double v) {
     ep.out[(long long)b * ep.out_bstride + (long long)row * n + col] = v;

@@ -190,9 +190,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
     // Epilogue: the FP32 tile goes from TMEM to shared memory (the ring is idle now; warps w,
     // w + 4, w + 8, w + 12 share TMEM lanes 32 (w % 4).. and split the columns), then all 512
-    // threads walk it row-major, so that the reads of the power table and the stores are
-    // coalesced along rows, with four elements' loads in flight per thread: the FP64 block
-    // sums of the fused Horner add are latency-bound, and 16 warps hide twice as much.
+    // threads walk it row-major, four consecutive columns each, so that the reads of the power
+    // table and the stores are coalesced along rows: the FP64 block sums of the fused Horner
+    // add are latency-bound, and 16 warps hide twice as much as 8.
     constexpr int PITCH = TN + 1;
     float* stile = (float*)smem;
     {
@@ -208,23 +208,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     }
     __syncthreads();
-    constexpr int U = 4;
+    // four consecutive columns per thread: the power-table and addend rows are read two
+    // doubles at a time where they are 16-byte aligned
+    const bool vep = (n & 3) == 0 && ((((uintptr_t)ep.pw | (uintptr_t)ep.add) & 15) == 0) &&
+                     ((ep.pw_bstride | ep.add_bstride) & 1) == 0;
 #pragma unroll 1
-    for (int e0 = threadIdx.x; e0 < TM * TN; e0 += TC_THREADS * U) {
-        double val[U];
+    for (int e0 = 4 * threadIdx.x; e0 < TM * TN; e0 += 4 * TC_THREADS) {
+        const int r = e0 / TN, c = e0 % TN, row = m0 + r, col = n0 + c;
+        if (row >= n) continue;
+        double v[4];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int e = e0 + u * TC_THREADS;
-            const int r = e / TN, c = e % TN, row = m0 + r, col = n0 + c;
-            val[u] = (e < TM * TN && row < n && col < n)
-                         ? epilogue_value(ep, b, row, col, n, f32_to_f64(stile[r * PITCH + c]))
-                         : 0.0;
-        }
+        for (int u = 0; u < 4; ++u) v[u] = f32_to_f64(stile[r * PITCH + c + u]);
+        if (vep && col + 3 < n) {
+            epilogue_value4(ep, b, row, col, n, v);
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int e = e0 + u * TC_THREADS;
-            const int r = e / TN, c = e % TN, row = m0 + r, col = n0 + c;
-            if (e < TM * TN && row < n && col < n) epilogue_store(ep, b, row, col, n, val[u]);
+            for (int u = 0; u < 4; ++u) epilogue_store(ep, b, row, col + u, n, v[u]);
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (col + u < n)
+                    epilogue_store(ep, b, row, col + u, n, epilogue_value(ep, b, row, col + u, n, v[u]));
         }
     }
     tc_fence_before();
