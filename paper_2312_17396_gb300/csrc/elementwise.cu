@@ -366,10 +366,30 @@ __global__ void k_combine(int n, const double* __restrict__ extra, long long ext
                           Epilogue ep) {
     pdl_wait();
     const int b = blockIdx.z;
+    // four consecutive columns per thread; the operand rows are read two doubles at a time
+    // when n is a multiple of 4 and every base and batch stride keeps them 16-byte aligned
+    const bool vec = (n & 3) == 0 &&
+                     ((((uintptr_t)extra | (uintptr_t)ep.pw | (uintptr_t)ep.add) & 15) == 0) &&
+                     ((extra_bs | ep.pw_bstride | ep.add_bstride) & 1) == 0;
     for (int row = blockIdx.y; row < n; row += gridDim.y)
-        for (int col = blockIdx.x * blockDim.x + threadIdx.x; col < n; col += gridDim.x * blockDim.x) {
-            const double e = extra ? extra[b * extra_bs + (long long)row * n + col] : 0.0;
-            epilogue_store(ep, b, row, col, n, epilogue_value(ep, b, row, col, n, e));
+        for (int col = 4 * (blockIdx.x * blockDim.x + threadIdx.x); col < n;
+             col += 4 * gridDim.x * blockDim.x) {
+            const double* xr = extra ? extra + b * extra_bs + (long long)row * n + col : nullptr;
+            if (vec && col + 3 < n) {
+                double v[4] = {0.0, 0.0, 0.0, 0.0};
+                if (xr) {
+                    const double2 x01 = *reinterpret_cast<const double2*>(xr);
+                    const double2 x23 = *reinterpret_cast<const double2*>(xr + 2);
+                    v[0] = x01.x; v[1] = x01.y; v[2] = x23.x; v[3] = x23.y;
+                }
+                epilogue_value4(ep, b, row, col, n, v);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) epilogue_store(ep, b, row, col + u, n, v[u]);
+            } else {
+                for (int u = 0; u < 4 && col + u < n; ++u)
+                    epilogue_store(ep, b, row, col + u, n,
+                                   epilogue_value(ep, b, row, col + u, n, xr ? xr[u] : 0.0));
+            }
         }
 }
 
@@ -474,11 +494,12 @@ __global__ void k_pow2_scales(const double* __restrict__ ma, const double* __res
     unscale[b] = ldexp(1.0, ea + eb - 2 * target);
 }
 
-// 256-thread blocks over an n x n matrix per z: x spans the columns, y up to 4096 rows
-// (each block row strides by gridDim.y), z the matrices.
-inline dim3 grid2d(int n, int nmat) {
-    const int gx = (n + 255) / 256;
-    const int gy = n < 4096 ? (n > 0 ? n : 1) : 4096;
+// 256-thread blocks over an n x n matrix per z: x spans ncol column units (columns, or groups
+// of columns), y up to 4096 rows (each block row strides by gridDim.y), z the matrices.
+inline dim3 grid2d(int ncol, int nmat, int nrow = -1) {
+    if (nrow < 0) nrow = ncol;
+    const int gx = (ncol + 255) / 256;
+    const int gy = nrow < 4096 ? (nrow > 0 ? nrow : 1) : 4096;
     return dim3(gx > 0 ? gx : 1, gy, nmat > 0 ? nmat : 1);
 }
 
@@ -624,7 +645,7 @@ mpps_status launch_select_copy(const double* q0, const double* q1, const int* d_
 mpps_status launch_combine(int n, int batch, const double* extra, long long extra_bs,
                            const Epilogue& ep, cudaStream_t st) {
     ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
-    MPPS_CUDA_TRY(launch_pdl(k_combine, grid2d(n, batch), dim3(256), 0, st, n, extra, extra_bs, ep));
+    MPPS_CUDA_TRY(launch_pdl(k_combine, grid2d((n + 3) / 4, batch, n), dim3(256), 0, st, n, extra, extra_bs, ep));
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }
