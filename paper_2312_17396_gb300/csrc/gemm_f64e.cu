@@ -506,6 +506,49 @@ __device__ __noinline__ void f64e_sum_store4(const Epilogue& ep, int b, int row,
     for (int u = 0; u < 4; ++u) epilogue_store(ep, b, row, col0 + u, n, v[u]);
 }
 
+// The block sum B_{i-1} = coef[0] I + sum_j coef[j] X^j of one thread's 16 products (row
+// `row`, columns cb..cb+15, all inside the matrix, 16-byte aligned rows), written into their
+// own output entries.  Called while the tile's MMAs run (the epilogue warps are idle then and
+// the FP64 pipe is not otherwise busy), so the final epilogue only adds the product to it.
+__device__ __noinline__ void f64e_block_sum16(const Epilogue& ep, int b, int row, int cb, int n,
+                                              double* __restrict__ orow) {
+    const long long nn = (long long)n * n;
+    const double* pwrow = ep.pw + (long long)b * ep.pw_bstride + (long long)row * n + cb;
+#pragma unroll 1
+    for (int g = 0; g < EPI_COLS; g += 4) {
+        double v[4] = {0.0, 0.0, 0.0, 0.0};
+        const int dc = row - (cb + g);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (dc == u) v[u] = ep.coef[0];
+        for (int j = 1; j <= ep.nt; ++j) {
+            const double* pp = pwrow + (long long)(j - 1) * nn + g;
+            const double2 p01 = __ldg(reinterpret_cast<const double2*>(pp));
+            const double2 p23 = __ldg(reinterpret_cast<const double2*>(pp + 2));
+            const double c = ep.coef[j];
+            v[0] = fma(c, p01.x, v[0]);
+            v[1] = fma(c, p01.y, v[1]);
+            v[2] = fma(c, p23.x, v[2]);
+            v[3] = fma(c, p23.y, v[3]);
+        }
+        *reinterpret_cast<double2*>(orow + g) = make_double2(v[0], v[1]);
+        *reinterpret_cast<double2*>(orow + g + 2) = make_double2(v[2], v[3]);
+    }
+}
+
+// Product plus the block sum stored by f64e_block_sum16, for four products at columns
+// col0..col0+3, then the store (and the rounded copy for the next step).
+__device__ __noinline__ void f64e_add_stored4(const Epilogue& ep, int b, int row, int col0, int n,
+                                              double v0, double v1, double v2, double v3) {
+    const double* op = ep.out + (long long)b * ep.out_bstride + (long long)row * n + col0;
+    const double2 s01 = *reinterpret_cast<const double2*>(op);
+    const double2 s23 = *reinterpret_cast<const double2*>(op + 2);
+    epilogue_store(ep, b, row, col0, n, v0 + s01.x);
+    epilogue_store(ep, b, row, col0 + 1, n, v1 + s01.y);
+    epilogue_store(ep, b, row, col0 + 2, n, v2 + s23.x);
+    epilogue_store(ep, b, row, col0 + 3, n, v3 + s23.y);
+}
+
 // Tile `id` -> (matrix slot z, first row, first column); row blocks are walked in groups of
 // RASTER_G with the column index outermost inside a group, so that the CTAs working at the
 // same time share few B column blocks and few A row blocks.
@@ -688,6 +731,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         const bool ep_sum = alpha1 && (ep.nt >= 0 || ep.add != nullptr) && (n & 3) == 0 &&
                             ((((uintptr_t)ep.pw | (uintptr_t)ep.add) & 15) == 0) &&
                             ((ep.pw_bstride | ep.add_bstride) & 1) == 0;
+        // a Horner block sum without addend, computed ahead into the output entries while the
+        // MMAs run (not when the chunks are flushed: the entries then hold the FP64 partials)
+        const bool ep_pre = ep_sum && ep.nt >= 0 && ep.add == nullptr && nchunks <= FLUSH &&
+                            ((((uintptr_t)ep.out) & 15) == 0) && (ep.out_bstride & 1) == 0;
         const int q4 = warp & 3, h = warp >> 2;   // lane quarter, column group
         const uint32_t lane_base = (uint32_t)(q4 * 32) << 16;
         uint32_t gc = 0;
@@ -704,6 +751,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             const int cb = n0 + EPI_COLS * h;
             double* orow = ep.out + (long long)b * ep.out_bstride + (long long)row * n + cb;
             const bool vec4 = ((uintptr_t)orow & 31) == 0;
+            const bool pre = ep_pre && row < n && cb + EPI_COLS <= n;
+            if (pre) f64e_block_sum16(ep, b, row, cb, n, orow);
             for (int c = 0; c < nchunks; ++c, ++gc) {
                 ok = __all_sync(0xffffffffu, mbar_wait(chunk_done, gc & 1, err));
                 if (!ok) break;
@@ -759,6 +808,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                     if (plain && fast && vec4) {   // four consecutive doubles, 32-byte aligned
                         asm volatile("st.global.v4.f64 [%0], {%1, %2, %3, %4};" ::"l"(orow + g),
                                      "d"(val[0]), "d"(val[1]), "d"(val[2]), "d"(val[3]) : "memory");
+                    } else if (fast && pre) {
+                        f64e_add_stored4(ep, b, row, cb + g, n, val[0], val[1], val[2], val[3]);
                     } else if (fast && ep_sum && cb + EPI_COLS <= n && nchunks <= FLUSH) {
                         f64e_sum_store4(ep, b, row, cb + g, n, val[0], val[1], val[2], val[3]);
                     } else {
