@@ -480,6 +480,10 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
     void *Ylo_hi[MPPS_NUM_FORMATS] = {}, *Ylo_lo[MPPS_NUM_FORMATS] = {};
     void *Pl_hi[2] = {}, *Pl_lo[2] = {};
     double *d_sY, *d_sP, *d_alpha;
+    // FP8 operands get one power-of-two scale per row of P_i and per column of Y (the
+    // exponents that undo them, and column-maximum scratch)
+    int *xrowP = nullptr, *xcolY = nullptr;
+    unsigned long long* cmax8 = nullptr;
     auto layout2 = [&](Arena& a) {
         for (int f = 1; f < MPPS_NUM_FORMATS; ++f)
             if (used[f]) {
@@ -489,6 +493,11 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
         for (int k = 0; k < 2; ++k) {
             Pl_hi[k] = a.take<char>(any_low ? (size_t)batch * low_bs * max_es : 0);
             Pl_lo[k] = a.take<char>(used[MPPS_FMT_BF16X3] ? (size_t)batch * low_bs * 2 : 0);
+        }
+        if (used[MPPS_FMT_FP8]) {
+            xrowP = a.take<int>((size_t)batch * n);
+            xcolY = a.take<int>((size_t)batch * n);
+            cmax8 = a.take<unsigned long long>((size_t)batch * n);
         }
         // one contiguous block (filled by a single copy): sY | sP | alpha
         d_sY = a.take<double>((size_t)(MPPS_NUM_FORMATS + 2 * (r + 1)) * batch);
@@ -529,8 +538,12 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
                                       cudaMemcpyHostToDevice, st));
         for (int f = 1; f < MPPS_NUM_FORMATS; ++f)
             if (used[f]) {
-                rc = launch_convert(f, pw + (long long)(s - 1) * nn, pw_bs, n, batch, Ylo_hi[f],
-                                    Ylo_lo[f], low_bs, lld, d_sY + (size_t)f * batch, true, st);
+                rc = f == MPPS_FMT_FP8
+                         ? launch_convert_scaled(f, pw + (long long)(s - 1) * nn, pw_bs, n, batch,
+                                                 Ylo_hi[f], nullptr, low_bs, lld, low_target_exp(f),
+                                                 true, xcolY, cmax8, st)
+                         : launch_convert(f, pw + (long long)(s - 1) * nn, pw_bs, n, batch, Ylo_hi[f],
+                                          Ylo_lo[f], low_bs, lld, d_sY + (size_t)f * batch, true, st);
                 if (rc) return rc;
             }
     }
@@ -558,7 +571,7 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
         if (i - 1 == 0 && qform) ep.coef[0] -= 1.0;
         ep.pw = pw;
         ep.pw_bstride = pw_bs;
-        if (i - 1 >= 1 && is_low(fmt[i - 1])) {
+        if (i - 1 >= 1 && is_low(fmt[i - 1]) && fmt[i - 1] != MPPS_FMT_FP8) {
             ep.low_fmt = fmt[i - 1];
             ep.low_hi = Pl_hi[(i - 1) & 1];
             ep.low_lo = Pl_lo[(i - 1) & 1];
@@ -584,7 +597,7 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
         ep.pw = pw;
         ep.pw_bstride = pw_bs;
         ep.alpha = 0.0;
-        if (is_low(fmt[r])) {
+        if (is_low(fmt[r]) && fmt[r] != MPPS_FMT_FP8) {
             ep.low_fmt = fmt[r];
             ep.low_hi = Pl_hi[r & 1];
             ep.low_lo = Pl_lo[r & 1];
@@ -605,6 +618,16 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
             rc = launch_slice_rows(Pbuf[i & 1], nn, n, batch, k, slA, eA, st);
             if (!rc)
                 rc = launch_gemm_f64e(k, slA, k, eA, slY, K, eY, n, batch, batch, ep, d_err, st);
+        } else if (fmt[i] == MPPS_FMT_FP8) {
+            // per-row scales of P_i, per-column scales of Y (the paper's scaled low-precision
+            // products, with the scales as fine as a row / a column)
+            rc = launch_convert_scaled(fmt[i], Pbuf[i & 1], nn, n, batch, Pl_hi[i & 1], nullptr,
+                                       low_bs, lld, low_target_exp(fmt[i]), false, xrowP, nullptr, st);
+            ep.row_exp = xrowP;
+            ep.col_exp = xcolY;
+            if (!rc)
+                rc = launch_gemm_tc(fmt[i], Pl_hi[i & 1], Pl_lo[i & 1], Ylo_hi[fmt[i]], Ylo_lo[fmt[i]],
+                                    low_bs, low_bs, lld, n, batch, ep, d_err, st);
         } else {
             ep.alpha_b = d_alpha + (size_t)i * batch;
             rc = launch_gemm_tc(fmt[i], Pl_hi[i & 1], Pl_lo[i & 1], Ylo_hi[fmt[i]], Ylo_lo[fmt[i]],

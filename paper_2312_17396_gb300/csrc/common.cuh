@@ -90,6 +90,10 @@ struct Epilogue {
     long long pw_bstride;
     double alpha;                 // used when alpha_b is null
     const double* alpha_b;        // per batch element (device), or null
+    // per-row / per-column power-of-two unscaling of a product of scaled operands (device,
+    // [batch][n] each, or null): the product term is multiplied by 2^(row_exp + col_exp)
+    const int* row_exp;
+    const int* col_exp;
     const double* add;            // optional addend: v += add_coef * add[b][row][col]
     long long add_bstride;
     double add_coef;
@@ -109,6 +113,7 @@ inline Epilogue epilogue_plain(double* out, long long out_bstride) {
     e.nt = -1;
     for (int j = 0; j <= MPPS_MAX_S; ++j) e.coef[j] = 0.0;
     e.pw = nullptr; e.pw_bstride = 0; e.alpha = 1.0; e.alpha_b = nullptr;
+    e.row_exp = nullptr; e.col_exp = nullptr;
     e.add = nullptr; e.add_bstride = 0; e.add_coef = 0.0;
     e.out = out; e.out_bstride = out_bstride;
     e.low_fmt = MPPS_FMT_NONE; e.low_hi = nullptr; e.low_lo = nullptr;
@@ -179,6 +184,17 @@ __device__ __forceinline__ double mul_pow2(double v, double p) {
     return v * p;
 }
 
+// v 2^k, exact when v and the result are normal (the exponent field moves on the integer
+// pipe); otherwise one FP64 multiply by 2^k (k clamped to the normal range, then ldexp).
+static __device__ __noinline__ double ldexp_out_of_line(double v, int k) { return ldexp(v, k); }
+__device__ __forceinline__ double mul_exp2(double v, int k) {
+    const long long vb = __double_as_longlong(v);
+    const int ve = (int)((vb >> 52) & 0x7ff);
+    if (ve > 0 && ve < 0x7ff && ve + k > 0 && ve + k < 0x7ff)
+        return __longlong_as_double(vb + ((long long)k << 52));
+    return ldexp_out_of_line(v, k);
+}
+
 // FP32 -> FP64 (exact) by assembling the bits; zero, subnormal and non-finite values take the
 // conversion instruction (an FP64-pipe operation).
 __device__ __forceinline__ double f32_to_f64(float f) {
@@ -198,6 +214,8 @@ __device__ __forceinline__ double epilogue_value(const Epilogue& ep, int b, int 
     const long long alb = __double_as_longlong(al);
     if (alb == 0) v = 0.0;                                 // alpha = 0: no product term
     else if (alb != 0x3FF0000000000000LL) v = mul_pow2(acc, al);   // no multiply by 1
+    if (ep.row_exp)
+        v = mul_exp2(v, ep.row_exp[(long long)b * n + row] + ep.col_exp[(long long)b * n + col]);
     if (ep.nt >= 0) {
         if (row == col) v += ep.coef[0];
         const double* base = ep.pw + (long long)b * ep.pw_bstride + (long long)row * n + col;
@@ -219,6 +237,12 @@ __device__ __forceinline__ void epilogue_value4(const Epilogue& ep, int b, int r
     for (int u = 0; u < 4; ++u) {
         if (alb == 0) v[u] = 0.0;
         else if (alb != 0x3FF0000000000000LL) v[u] = mul_pow2(v[u], al);
+    }
+    if (ep.row_exp) {
+        const int re = ep.row_exp[(long long)b * n + row];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            v[u] = mul_exp2(v[u], re + ep.col_exp[(long long)b * n + col0 + u]);
     }
     const long long off = (long long)row * n + col0;
     if (ep.nt >= 0) {
@@ -354,6 +378,15 @@ mpps_status launch_convert(int fmt, const double* M, long long bs, int n, int ba
                            void* lo, long long low_bs, int lld, const double* d_scale,
                            bool transpose, cudaStream_t st);
 // max_ij |M_ij| per matrix, written to out[b] (out must be zeroed first).
+// Rounded copy in format fmt with one power-of-two scale per row (transpose = false: rows of
+// M, the A operand) or per column (transpose = true: written transposed, row j = column j of
+// M, the B^T operand): the row or column maximum is brought below 2^target, and its unscaling
+// exponent (e - target, max < 2^e) goes to out_exp[batch][n].  colmax: batch * n scratch
+// words (transpose only).
+mpps_status launch_convert_scaled(int fmt, const double* M, long long bs, int n, int batch,
+                                  void* hi, void* lo, long long low_bs, int lld, int target,
+                                  bool transpose, int* out_exp, unsigned long long* colmax,
+                                  cudaStream_t st);
 mpps_status launch_maxabs(const double* M, long long bs, int n, int batch, double* out,
                           cudaStream_t st);
 // For each matrix b: scale[b] = 2^(target - e) and unscale... (power-of-two operand scales)

@@ -461,6 +461,94 @@ __global__ void k_transpose(const double* __restrict__ A, long long a_bs, double
     }
 }
 
+// |x| as the bit pattern of a non-negative double (NaN as 0); the frexp exponent of such a
+// pattern (value in [2^(e-1), 2^e)), 0 for zero and infinity.
+__device__ __forceinline__ unsigned long long absbits(double x) {
+    const unsigned long long a = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffULL;
+    return a > 0x7ff0000000000000ULL ? 0ULL : a;
+}
+__device__ __forceinline__ int frexp_exp_bits(unsigned long long a) {
+    const int ef = (int)(a >> 52);
+    if (a == 0 || ef == 0x7ff) return 0;
+    return ef != 0 ? ef - 1022 : (64 - __clzll((long long)a)) - 1074;
+}
+
+// Rounded copy of each row of M with its own power-of-two scale: the row maximum is brought
+// below 2^target (scale 2^(target - e)), and e - target, the exponent that undoes it, goes to
+// out_exp.  One 256-thread block per row.
+__global__ void __launch_bounds__(256) k_convert_rows_scaled(int fmt, const double* __restrict__ M,
+                                                             long long bs, int n, void* hi, void* lo,
+                                                             long long low_bs, int lld, int target,
+                                                             int* __restrict__ out_exp) {
+    pdl_wait();
+    __shared__ unsigned long long red[8];
+    const int row = blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
+    const double* src = M + (long long)b * bs + (long long)row * n;
+    unsigned long long mx = 0;
+    for (int j = tid; j < n; j += blockDim.x) {
+        const unsigned long long a = absbits(src[j]);
+        mx = a > mx ? a : mx;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = t > mx ? t : mx;
+    }
+    if ((tid & 31) == 0) red[tid >> 5] = mx;
+    __syncthreads();
+    mx = red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = red[w] > mx ? red[w] : mx;
+    const int e = frexp_exp_bits(mx);
+    if (tid == 0) out_exp[(long long)b * n + row] = e - target;
+    for (int j = tid; j < n; j += blockDim.x)
+        store_low(fmt, hi, lo, (long long)b * low_bs + (long long)row * lld + j,
+                  mul_exp2(src[j], target - e));
+}
+
+// Column maxima of |M| as bit patterns (out zeroed first), one thread per column over a
+// 16-row chunk.
+__global__ void k_colmax_bits(const double* __restrict__ M, long long bs, int n,
+                              unsigned long long* __restrict__ out) {
+    pdl_wait();
+    const int col = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.z;
+    if (col >= n) return;
+    const int r0 = blockIdx.y * 16;
+    const double* src = M + (long long)b * bs + (long long)r0 * n + col;
+    unsigned long long mx = 0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+        if (r0 + i < n) {
+            const unsigned long long a = absbits(__ldg(src + (long long)i * n));
+            mx = a > mx ? a : mx;
+        }
+    atomicMax(out + (long long)b * n + col, mx);
+}
+
+// Transposed rounded copy (row j = column j of M) with one power-of-two scale per column of M
+// from its maximum (colmax); e - target per column to out_exp.
+__global__ void k_convert_t_scaled(int fmt, const double* __restrict__ M, long long bs, int n,
+                                   void* hi, void* lo, long long low_bs, int lld, int target,
+                                   const unsigned long long* __restrict__ colmax,
+                                   int* __restrict__ out_exp) {
+    pdl_wait();
+    __shared__ double tile[32][33];
+    const int b = blockIdx.z;
+    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    const double* base = M + (long long)b * bs;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int row = r0 + i, col = c0 + threadIdx.x;
+        tile[i][threadIdx.x] = (row < n && col < n) ? base[(long long)row * n + col] : 0.0;
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int orow = c0 + i, ocol = r0 + threadIdx.x;   // out row = source column
+        if (orow >= n || ocol >= n) continue;
+        const int e = frexp_exp_bits(colmax[(long long)b * n + orow]);
+        if (blockIdx.y == 0 && threadIdx.x == 0) out_exp[(long long)b * n + orow] = e - target;
+        store_low(fmt, hi, lo, (long long)b * low_bs + (long long)orow * lld + ocol,
+                  mul_exp2(tile[threadIdx.x][i], target - e));
+    }
+}
+
 __global__ void k_maxabs(const double* __restrict__ M, long long bs, long long nn,
                          double* __restrict__ out) {
     pdl_wait();
@@ -660,6 +748,30 @@ mpps_status launch_convert(int fmt, const double* M, long long bs, int n, int ba
     } else {
         MPPS_CUDA_TRY(launch_pdl(k_convert, grid2d(n, batch), dim3(256), 0, st, fmt, M, bs, n, hi, lo, low_bs,
                                  lld, d_scale));
+    }
+    MPPS_LAUNCH_CHECK();
+    return MPPS_OK;
+}
+
+mpps_status launch_convert_scaled(int fmt, const double* M, long long bs, int n, int batch,
+                                  void* hi, void* lo, long long low_bs, int lld, int target,
+                                  bool transpose, int* out_exp, unsigned long long* colmax,
+                                  cudaStream_t st) {
+    ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
+    if (batch > 65535) {
+        set_error("convert_scaled: batch %d exceeds the grid limit", batch);
+        return MPPS_EINVAL;
+    }
+    if (!transpose) {
+        MPPS_CUDA_TRY(launch_pdl(k_convert_rows_scaled, dim3(n, batch), dim3(256), 0, st, fmt, M, bs, n, hi, lo,
+                                 low_bs, lld, target, out_exp));
+    } else {
+        MPPS_CUDA_TRY(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * (size_t)batch * n, st));
+        MPPS_CUDA_TRY(launch_pdl(k_colmax_bits, dim3((n + 127) / 128, (n + 15) / 16, batch), dim3(128), 0, st, M, bs, n,
+                                 colmax));
+        MPPS_LAUNCH_CHECK();
+        MPPS_CUDA_TRY(launch_pdl(k_convert_t_scaled, dim3((n + 31) / 32, (n + 31) / 32, batch), dim3(32, 8), 0, st, fmt, M,
+                                 bs, n, hi, lo, low_bs, lld, target, colmax, out_exp));
     }
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;

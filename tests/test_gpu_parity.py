@@ -118,6 +118,27 @@ def test_ps_eval_mixed_vs_fixed(mpps, n, norm):
         assert em <= 2 * ef + n * U, (pol.mode, em, ef, rep[0]["fmt"])
 
 
+@pytest.mark.parametrize("n", [64, 130, 257])
+@pytest.mark.parametrize("graded", [False, True])
+def test_ps_eval_fp8_steps_row_column_scaled(mpps, n, graded):
+    # A loose target lets the planner put the high-order Horner steps in FP8; those products
+    # scale each row of P_i and each column of Y by its own power of two.  A diagonally
+    # similar matrix D G D^-1 (D spanning 2^12) gives rows and columns of very different
+    # magnitude.  The normwise result must stay within the target's bound.
+    m, tol = 30, 2.0 ** -30
+    A = inputs.gaussian_matrix(n, seed=7100 + n, norm1=0.5)
+    if graded:
+        d = 2.0 ** np.round(np.linspace(0.0, 12.0, n))
+        A = (d[:, None] * A) / d[None, :]
+    coef = mpps.taylor_exp_coeffs(m)
+    ph, pl, _ = oracle.ps_dd(oracle.taylor_exp_rational(m), A)
+    pol = mpps.Policy(mode=mpps.MIXED_NS, tol=tol, formats=["fp64", "fp8"])
+    P, rep = mpps.ps_eval(coef, dev(A), policy=pol, report=True)
+    assert "fp8" in rep[0]["fmt"], rep[0]["fmt"]
+    err = oracle.rel_err_1norm(host(P), ph, pl)
+    assert err <= 50 * n * tol, (err, rep[0]["fmt"])
+
+
 def test_ps_eval_general_coefficients(mpps):
     n = 96
     A = inputs.gaussian_matrix(n, seed=5, norm1=2.0)
