@@ -359,6 +359,7 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
     double *d_coef, *pw, *Pb0, *Pb1, *partial, *norms, *d_anorm, *tmpT = nullptr;
     int *d_sigma, *d_err, *d_bidx, *eA = nullptr, *eB = nullptr, *eY = nullptr;
     __nv_bfloat16 *slA = nullptr, *slB = nullptr, *slY = nullptr;
+    char* split = nullptr;   // split-K scratch of the emulated products
     auto layout1 = [&](Arena& a) {
         d_coef = a.take<double>(m + 1);
         pw = a.take<double>((size_t)batch * pw_bs);
@@ -379,6 +380,7 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
             eB = a.take<int>((size_t)batch * n);
             eY = a.take<int>((size_t)batch * n);
             tmpT = a.take<double>((size_t)batch * nn);
+            split = a.take<char>(f64e_split_bytes());
         }
     };
     layout1(L);
@@ -388,6 +390,7 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
     L.base = (char*)ws1.p;
     L.off = 0;
     layout1(L);
+    if (split) MPPS_CUDA_TRY(cudaMemsetAsync(split, 0, f64e_split_flag_bytes(), st));
     MPPS_CUDA_TRY(cudaMemcpyAsync(d_coef, coeffs, sizeof(double) * (m + 1), cudaMemcpyHostToDevice, st));
     DevErr* derr = nullptr;
     if ((rc = dev_err_get(&derr))) return rc;
@@ -421,7 +424,9 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
         Epilogue ep = epilogue_plain(pw + (long long)(j - 1) * nn, pw_bs);
         if (K > 0) {
             rc = launch_slice_rows(pw + (long long)(j - 2) * nn, pw_bs, n, batch, K, slA, eA, st);
-            if (!rc) rc = launch_gemm_f64e(K, slA, K, eA, slB, K, eB, n, batch, batch, ep, d_err, st);
+            if (!rc)
+                rc = launch_gemm_f64e(K, slA, K, eA, slB, K, eB, n, batch, batch, ep, d_err, st,
+                                      nullptr, split);
         } else {
             rc = launch_gemm_f64(pw + (long long)(j - 2) * nn, pw_bs, pw, pw_bs, n, batch, ep, st);
         }
@@ -617,7 +622,8 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
             const int k = MPPS_F64E_SLICES(fmt[i]);
             rc = launch_slice_rows(Pbuf[i & 1], nn, n, batch, k, slA, eA, st);
             if (!rc)
-                rc = launch_gemm_f64e(k, slA, k, eA, slY, K, eY, n, batch, batch, ep, d_err, st);
+                rc = launch_gemm_f64e(k, slA, k, eA, slY, K, eY, n, batch, batch, ep, d_err, st,
+                                      nullptr, split);
         } else if (fmt[i] == MPPS_FMT_FP8) {
             // per-row scales of P_i, per-column scales of Y (the paper's scaled low-precision
             // products, with the scales as fine as a row / a column)
@@ -664,7 +670,7 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
                 if (!rc) rc = slice_cols(Pbuf[k & 1], nn, K, slB, eB);
                 if (!rc)
                     rc = launch_gemm_f64e(K, slA, K, eA, slB, K, eB, n, counts[k], batch, ep, d_err,
-                                          st, d_lists + (size_t)k * batch);
+                                          st, d_lists + (size_t)k * batch, split);
             } else {
                 rc = launch_gemm_f64(Pbuf[k & 1], nn, Pbuf[k & 1], nn, n, counts[k], ep, st,
                                      d_lists + (size_t)k * batch);
@@ -947,6 +953,7 @@ mpps_status mpps_matmul(const double* A, const double* B, double* C, int n, int 
         __nv_bfloat16 *sa, *sb;
         int *ea, *eb, *err;
         double* bt;
+        char* split;
         auto lay = [&](Arena& z) {
             sa = z.take<__nv_bfloat16>(f64e_plane_elems(n, batch, k));
             sb = z.take<__nv_bfloat16>(f64e_plane_elems(n, batch, k));
@@ -954,6 +961,7 @@ mpps_status mpps_matmul(const double* A, const double* B, double* C, int n, int 
             eb = z.take<int>((size_t)batch * n);
             bt = z.take<double>(elems);
             err = z.take<int>(1);
+            split = z.take<char>(f64e_split_bytes());
         };
         lay(L);
         DevBuf ws;
@@ -962,10 +970,13 @@ mpps_status mpps_matmul(const double* A, const double* B, double* C, int n, int 
         L.off = 0;
         lay(L);
         MPPS_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+        MPPS_CUDA_TRY(cudaMemsetAsync(split, 0, f64e_split_flag_bytes(), st));
         if ((rc = launch_slice_rows(a.dev, nn, n, batch, k, sa, ea, st))) return rc;
         if ((rc = launch_slice_cols(b.dev, nn, n, batch, k, sb, eb, (unsigned long long*)bt, st)))
             return rc;
-        if ((rc = launch_gemm_f64e(k, sa, k, ea, sb, k, eb, n, batch, batch, ep, err, st))) return rc;
+        if ((rc = launch_gemm_f64e(k, sa, k, ea, sb, k, eb, n, batch, batch, ep, err, st, nullptr,
+                                   split)))
+            return rc;
         int h_err = 0;
         MPPS_CUDA_TRY(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st));
         MPPS_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1082,6 +1093,7 @@ mpps_status ps_eval_adjoint(const double* coeffs, int m, const double* A, const 
         __nv_bfloat16 *slA = nullptr, *slB = nullptr;
         int *eA = nullptr, *eB = nullptr;
         unsigned long long* cmx = nullptr;
+        char* split = nullptr;
         auto lay = [&](Arena& z) {
             pw = z.take<double>((size_t)batch * pw_bs);
             xbar = z.take<double>((size_t)batch * pw_bs);
@@ -1098,6 +1110,7 @@ mpps_status ps_eval_adjoint(const double* coeffs, int m, const double* A, const 
                 eA = z.take<int>((size_t)batch * n);
                 eB = z.take<int>((size_t)batch * n);
                 cmx = z.take<unsigned long long>((size_t)batch * n);
+                split = z.take<char>(f64e_split_bytes());
             }
         };
         lay(L);
@@ -1106,6 +1119,7 @@ mpps_status ps_eval_adjoint(const double* coeffs, int m, const double* A, const 
         L.base = (char*)ws.p;
         L.off = 0;
         lay(L);
+        if (split) MPPS_CUDA_TRY(cudaMemsetAsync(split, 0, f64e_split_flag_bytes(), st));
         auto P_at = [&](int i) { return Pst + (size_t)i * batch * nn; };
         DevErr* derr = nullptr;
         if (K > 0) {
@@ -1118,7 +1132,9 @@ mpps_status ps_eval_adjoint(const double* coeffs, int m, const double* A, const 
             if (K == 0) return launch_gemm_f64(Am, a_bs, Bm, b_bs, n, batch, ep, st);
             mpps_status r1 = launch_slice_rows(Am, a_bs, n, batch, K, slA, eA, st);
             if (!r1) r1 = launch_slice_cols(Bm, b_bs, n, batch, K, slB, eB, cmx, st);
-            if (!r1) r1 = launch_gemm_f64e(K, slA, K, eA, slB, K, eB, n, batch, batch, ep, derr->d, st);
+            if (!r1)
+                r1 = launch_gemm_f64e(K, slA, K, eA, slB, K, eB, n, batch, batch, ep, derr->d, st,
+                                      nullptr, split);
             return r1;
         };
         // forward

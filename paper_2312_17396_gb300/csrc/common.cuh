@@ -306,12 +306,18 @@ mpps_status launch_slice_rows(const double* M, long long bs, int n, int batch, i
 // Column slices of M written as rows of the B^T planes; colmax: batch * n scratch words.
 mpps_status launch_slice_cols(const double* M, long long bs, int n, int batch, int k, void* planes,
                               int* exps, unsigned long long* colmax, cudaStream_t st);
+// Scratch that lets the emulated product split the K range of output tiles between CTAs
+// (f64e_split_bytes() bytes, 256-byte aligned; its first f64e_split_flag_bytes() bytes
+// zeroed by the caller before the first product that uses it, on the same stream).  Without
+// it every CTA works on whole tiles.
+size_t f64e_split_bytes();
+size_t f64e_split_flag_bytes();
 // k slices are used; ksA / ksB planes are stored per matrix (>= k); nmat matrices are
 // stored, `batch` of them are processed (all, or those listed in bidx).
 mpps_status launch_gemm_f64e(int k, const void* slicesA, int ksA, const int* eA,
                              const void* slicesBt, int ksB, const int* eB, int n, int batch,
                              int nmat, const Epilogue& ep, int* d_err, cudaStream_t st,
-                             const int* bidx = nullptr);
+                             const int* bidx = nullptr, void* split = nullptr);
 
 // Slice planes per operand of an emulated product MPPS_FMT_F64E(k): k, at most 8 (k = 9
 // adds slice pairs, not slices).

@@ -47,6 +47,7 @@
 
 #include <cudaTypedefs.h>
 
+#include <atomic>
 #include <mutex>
 
 namespace mpps {
@@ -566,6 +567,87 @@ struct TileMap {
     }
 };
 
+// Split K (stream-K).  The work is the tile-major sequence of U = tiles x nkb units (one
+// output tile, one K block of 32); CTA c of G takes the units [c U / G, (c + 1) U / G), so
+// that every CTA gets the same number of K blocks whatever the tile count.  A CTA's work
+// is then a list of segments (tile, K blocks kb0..kb1-1): possibly the end of a tile that
+// an earlier CTA started, whole tiles, possibly the start of a tile that later CTAs finish.
+// The CTA that holds a tile's first K block owns it: every other piece of the tile drains
+// its sums (the exact integer W and the FP32 tails T) to the piece's slot of `part` and sets
+// its flag to the launch's epoch; the owner adds those pieces in CTA order (W exactly, T in
+// a fixed order) and runs the epilogue.  A contributor's piece is its first segment and the
+// owner's piece its last, so the owner waits only at the end of its own work, for pieces
+// that were computed first.  W of a whole tile sums at most FLUSH chunks, so split launches
+// are limited to K <= FLUSH x 512.  U = 0: whole tiles, blockIdx.x + i gridDim.x.
+struct Split {
+    long long U;            // units; 0: no split
+    long long* partW;       // [G][EPI_WARPS][EPI_COLS][32]
+    float* partT;           // [G][EPI_WARPS][EPI_COLS][32]
+    unsigned* flags;        // [G][EPI_WARPS]
+    unsigned epoch;         // this launch's flag value (never 0)
+};
+
+__device__ __forceinline__ long long split_start(int c, long long U) {
+    return (long long)c * U / gridDim.x;
+}
+
+struct Segments {
+    long long u, ue;        // split: units left
+    int id, total, nkb;     // whole tiles: next tile
+    bool split;
+    __device__ Segments(const Split& sp, int total_, int nkb_) {
+        split = sp.U > 0;
+        total = total_;
+        nkb = nkb_;
+        id = blockIdx.x;
+        u = split ? split_start(blockIdx.x, sp.U) : 0;
+        ue = split ? split_start(blockIdx.x + 1, sp.U) : 0;
+    }
+    __device__ bool next(int& tile, int& kb0, int& kb1) {
+        if (!split) {
+            if (id >= total) return false;
+            tile = id;
+            kb0 = 0;
+            kb1 = nkb;
+            id += gridDim.x;
+            return true;
+        }
+        if (u >= ue) return false;
+        tile = (int)(u / nkb);
+        kb0 = (int)(u - (long long)tile * nkb);
+        kb1 = ue - u < (long long)(nkb - kb0) ? kb0 + (int)(ue - u) : nkb;
+        u += kb1 - kb0;
+        return true;
+    }
+};
+
+__device__ __forceinline__ void flag_release(unsigned* f, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(f), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned flag_acquire(const unsigned* f) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
+    return v;
+}
+// Bounded wait until *f == v (false and *err set after the time limit or when another
+// thread gave up).
+__device__ __forceinline__ bool flag_wait(const unsigned* f, unsigned v, int* err) {
+    unsigned long long t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        if (flag_acquire(f) == v) return true;
+        if ((it & 15) == 0) {
+            if (*(volatile int*)err != 0) return false;
+            const unsigned long long now = globaltimer();
+            if (t0 == 0) t0 = now;
+            else if (now - t0 > kWaitNs) {
+                atomicExch(err, 1);
+                return false;
+            }
+        }
+        __nanosleep(128);
+    }
+}
+
 // One K=16 step of the split product into the TMEM regions: slice t of A (pair t/2, K offset
 // 64 (t & 1) bytes) times the stacked planes b'_0..b'_{NR-1-t} lands in regions t..NR-1 (one
 // instruction per 256 columns), then the pairs of order NREG..K-1 (K = 9: t + q = 8) in the
@@ -604,7 +686,8 @@ template <int K>
 __global__ void __launch_bounds__(THREADS, 1)
     k_gemm_f64e(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 int n, int kpA, int ksB, int batch, const int* __restrict__ eA,
-                const int* __restrict__ eB, Epilogue ep, int* err, const int* __restrict__ bidx) {
+                const int* __restrict__ eB, Epilogue ep, int* err, const int* __restrict__ bidx,
+                Split sp) {
     constexpr int NP = K < MAX_PLANES ? K : MAX_PLANES;   // slices per operand
     constexpr int NPA = num_pairs(NP);                    // slice pairs of A
     constexpr int S = num_stages(NP);
@@ -659,11 +742,13 @@ __global__ void __launch_bounds__(THREADS, 1)
             int s = 0;                                        // stage of K block g
             uint32_t ph = 0;                                  // its fill parity
             bool ok = true;
-            for (int id = blockIdx.x; id < total && ok; id += gridDim.x) {
+            Segments sg(sp, total, nkb);
+            int id, kb0, kb1;
+            while (ok && sg.next(id, kb0, kb1)) {
                 int z, m0, n0;
                 tm.decode(id, z, m0, n0);
                 const int b = bidx ? bidx[z] : z;
-                for (int kb = 0; kb < nkb; ++kb, ++g) {
+                for (int kb = kb0; kb < kb1; ++kb, ++g) {
                     if (g >= (uint32_t)S && !(ok = mbar_wait(&empty[s], ph ^ 1, err))) break;
                     uint8_t* st = smem + s * SB;
                     mbar_expect_tx(&full[s], (uint32_t)SB);
@@ -689,10 +774,13 @@ __global__ void __launch_bounds__(THREADS, 1)
             uint32_t ph = 0;
             bool ok = true;
             const uint32_t ring = smem_u32(smem);
-            for (int id = blockIdx.x; id < total && ok; id += gridDim.x) {
-                for (int kb = 0; kb < nkb && ok; ++kb) {
+            Segments sg(sp, total, nkb);
+            int id, kb0, kb1;
+            while (ok && sg.next(id, kb0, kb1)) {
+                for (int kb = kb0; kb < kb1 && ok; ++kb) {
                     const int kin = kb % kb_per_chunk;
-                    if (kin == 0 && gc > 0) {   // the epilogue must have drained the last chunk
+                    const bool first = kin == 0 || kb == kb0;   // starts an accumulation
+                    if (first && gc > 0) {   // the epilogue must have drained the last one
                         if (!(ok = mbar_wait(tmem_free, (gc - 1) & 1, err))) break;
                         tc_fence_after();
                     }
@@ -700,7 +788,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     tc_fence_after();
                     const uint32_t abase = ring + (uint32_t)(s * SB);
                     const uint64_t da = sw128_desc(abase), db = sw64_desc(abase + NPA * A_PAIR);
-                    if (kin == 0) {   // the chunk's first step starts the accumulation
+                    if (first) {
                         issue_k16<K, 0, true>(tmem, da, db, 0u);
                         issue_k16<K, 1, false>(tmem, da, db, 1u);
                     } else {
@@ -709,7 +797,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     }
                     if (!ok) break;
                     tc_commit(&empty[s]);
-                    if (kin == kb_per_chunk - 1 || kb == nkb - 1) {
+                    if (kin == kb_per_chunk - 1 || kb == kb1 - 1) {
                         tc_commit(chunk_done);
                         ++gc;
                     }
@@ -738,7 +826,9 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int q4 = warp & 3, h = warp >> 2;   // lane quarter, column group
         const uint32_t lane_base = (uint32_t)(q4 * 32) << 16;
         uint32_t gc = 0;
-        for (int id = blockIdx.x; id < total; id += gridDim.x) {
+        Segments sg(sp, total, nkb);
+        int id, kb0, kb1;
+        while (sg.next(id, kb0, kb1)) {
             int z, m0, n0;
             tm.decode(id, z, m0, n0);
             const int b = bidx ? bidx[z] : z;
@@ -751,9 +841,11 @@ __global__ void __launch_bounds__(THREADS, 1)
             const int cb = n0 + EPI_COLS * h;
             double* orow = ep.out + (long long)b * ep.out_bstride + (long long)row * n + cb;
             const bool vec4 = ((uintptr_t)orow & 31) == 0;
-            const bool pre = ep_pre && row < n && cb + EPI_COLS <= n;
+            const bool head = kb0 == 0;   // this CTA owns the tile
+            const bool pre = ep_pre && head && row < n && cb + EPI_COLS <= n;
             if (pre) f64e_block_sum16(ep, b, row, cb, n, orow);
-            for (int c = 0; c < nchunks; ++c, ++gc) {
+            const int c_end = (kb1 - 1) / kb_per_chunk;
+            for (int c = kb0 / kb_per_chunk; c <= c_end; ++c, ++gc) {
                 ok = __all_sync(0xffffffffu, mbar_wait(chunk_done, gc & 1, err));
                 if (!ok) break;
                 tc_fence_after();
@@ -787,6 +879,36 @@ __global__ void __launch_bounds__(THREADS, 1)
                 }
             }
             if (!ok) break;
+            if (!head) {   // a later piece of a split tile: hand the sums to the owner
+                const size_t slot = ((size_t)blockIdx.x * EPI_WARPS + warp) * EPI_COLS * 32 + lane;
+#pragma unroll
+                for (int j = 0; j < EPI_COLS; ++j) {
+                    __stcg(sp.partW + slot + 32 * j, W[j]);
+                    __stcg(sp.partT + slot + 32 * j, T[j]);
+                }
+                __threadfence();
+                __syncwarp();
+                if (lane == 0) flag_release(sp.flags + (size_t)blockIdx.x * EPI_WARPS + warp, sp.epoch);
+                continue;
+            }
+            if (kb1 < nkb) {   // the owner of a split tile adds the later pieces, in CTA order
+                const long long tend = (long long)(id + 1) * nkb;
+                for (int c2 = blockIdx.x + 1; c2 < (int)gridDim.x && split_start(c2, sp.U) < tend; ++c2) {
+                    const unsigned* f = sp.flags + (size_t)c2 * EPI_WARPS + warp;
+                    bool got = true;
+                    if (lane == 0) got = flag_wait(f, sp.epoch, err);
+                    got = __shfl_sync(0xffffffffu, got, 0);
+                    if (!got) { ok = false; break; }
+                    (void)flag_acquire(f);   // every lane reads the pieces after an acquire
+                    const size_t slot = ((size_t)c2 * EPI_WARPS + warp) * EPI_COLS * 32 + lane;
+#pragma unroll
+                    for (int j = 0; j < EPI_COLS; ++j) {
+                        W[j] += __ldcg(sp.partW + slot + 32 * j);
+                        T[j] += __ldcg(sp.partT + slot + 32 * j);
+                    }
+                }
+                if (!ok) break;
+            }
             // product = 2^{eA+eB-49} W + 2^{eA+eB-14} T, then the fused epilogue
             if (row < n) {
                 const int er = eA[(long long)b * n + row];
@@ -891,7 +1013,7 @@ int sm_count(int dev) {
 template <int K>
 mpps_status launch_k(int dev, int grid, const CUtensorMap& ta, const CUtensorMap& tb, int n,
                      int kpA, int ksB, int batch, const int* eA, const int* eB, const Epilogue& ep,
-                     int* d_err, cudaStream_t st, const int* bidx) {
+                     int* d_err, cudaStream_t st, const int* bidx, const Split& sp) {
     constexpr int NP = K < MAX_PLANES ? K : MAX_PLANES;
     constexpr int smem = num_stages(NP) * stage_bytes(NP) + 1024 + BAR_BYTES;
     static_assert(smem <= SMEM_MAX, "shared memory budget exceeded");
@@ -901,12 +1023,25 @@ mpps_status launch_k(int dev, int grid, const CUtensorMap& ta, const CUtensorMap
                                            smem));
         attr_done[dev] = true;
     }
-    MPPS_CUDA_TRY(launch_pdl(k_gemm_f64e<K>, dim3(grid), dim3(THREADS), smem, st, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, bidx));
+    MPPS_CUDA_TRY(launch_pdl(k_gemm_f64e<K>, dim3(grid), dim3(THREADS), smem, st, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, bidx, sp));
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }
 
 }  // namespace
+
+static int current_sm_count() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return sm_count(dev);
+}
+size_t f64e_split_flag_bytes() {
+    return ((size_t)current_sm_count() * EPI_WARPS * sizeof(unsigned) + 255) / 256 * 256;
+}
+size_t f64e_split_bytes() {
+    return f64e_split_flag_bytes() +
+           (size_t)current_sm_count() * EPI_WARPS * EPI_COLS * 32 * (sizeof(long long) + sizeof(float));
+}
 
 size_t f64e_plane_elems(int n, int batch, int k) {
     return (size_t)batch * num_pairs(f64e_planes(k)) * n * 2 * low_ld(n);
@@ -1006,7 +1141,7 @@ mpps_status launch_slice_cols(const double* M, long long bs, int n, int batch, i
 mpps_status launch_gemm_f64e(int k, const void* slicesA, int ksA, const int* eA,
                              const void* slicesBt, int ksB, const int* eB, int n, int batch,
                              int nmat, const Epilogue& ep, int* d_err, cudaStream_t st,
-                             const int* bidx) {
+                             const int* bidx, void* split) {
     if (batch <= 0) return MPPS_OK;
     ksA = f64e_planes(ksA);    // planes stored per matrix
     ksB = f64e_planes(ksB);
@@ -1030,19 +1165,41 @@ mpps_status launch_gemm_f64e(int k, const void* slicesA, int ksA, const int* eA,
         set_error("emulated FP64 product: %lld tiles exceed the index range", tiles);
         return MPPS_EINVAL;
     }
-    const int grid = (int)(tiles < sm_count(dev) ? tiles : sm_count(dev));
+    const int G = sm_count(dev);
+    int grid = (int)(tiles < G ? tiles : G);
+    // Split K between CTAs when there are several waves of whole tiles and the last would
+    // leave at least a tenth of the SMs' time idle, every CTA keeps at least 16 K blocks and
+    // W needs no flush.  (With a single partial wave the split costs more than it saves:
+    // each piece adds a TMEM drain during which the tensor pipe waits.)
+    Split sp{0, nullptr, nullptr, nullptr, 0u};
+    const int nkb = (n + KB - 1) / KB;
+    const long long waves = (tiles + G - 1) / G;
+    if (split && waves >= 2 && (nkb + KCHUNK / KB - 1) / (KCHUNK / KB) <= FLUSH && tiles * nkb / G >= 16 &&
+        (waves * G - tiles) * 10 >= waves * G) {
+        static std::atomic<unsigned> epoch{0};
+        unsigned e = epoch.fetch_add(1u) + 1u;
+        if (e == 0u) e = epoch.fetch_add(1u) + 1u;
+        char* base = (char*)split;
+        const size_t nslot = (size_t)G * EPI_WARPS * EPI_COLS * 32;
+        sp.U = tiles * nkb;
+        sp.flags = (unsigned*)base;
+        sp.partW = (long long*)(base + f64e_split_flag_bytes());
+        sp.partT = (float*)(sp.partW + nslot);
+        sp.epoch = e;
+        grid = G;
+    }
     const int pairs = k <= 8 ? k * (k + 1) / 2 : 43;
     ProfScope prof(MPPS_PROF_GEMM_F64E, st, 2.0 * n * (double)n * n * batch * pairs);
     switch (k) {
-        case 1: return launch_k<1>(dev, grid, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx);
-        case 2: return launch_k<2>(dev, grid, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx);
-        case 3: return launch_k<3>(dev, grid, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx);
-        case 4: return launch_k<4>(dev, grid, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx);
-        case 5: return launch_k<5>(dev, grid, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx);
-        case 6: return launch_k<6>(dev, grid, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx);
-        case 7: return launch_k<7>(dev, grid, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx);
-        case 8: return launch_k<8>(dev, grid, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx);
-        default: return launch_k<9>(dev, grid, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx);
+        case 1: return launch_k<1>(dev, grid, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx, sp);
+        case 2: return launch_k<2>(dev, grid, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx, sp);
+        case 3: return launch_k<3>(dev, grid, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx, sp);
+        case 4: return launch_k<4>(dev, grid, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx, sp);
+        case 5: return launch_k<5>(dev, grid, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx, sp);
+        case 6: return launch_k<6>(dev, grid, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx, sp);
+        case 7: return launch_k<7>(dev, grid, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx, sp);
+        case 8: return launch_k<8>(dev, grid, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx, sp);
+        default: return launch_k<9>(dev, grid, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx, sp);
     }
 }
 

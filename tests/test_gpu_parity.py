@@ -292,9 +292,11 @@ def test_expm_n1024_sampled_columns(mpps, norm):
 # ------------------------------------------------------------------------------------
 # FP64 products emulated by exact bf16 slices on the tensor cores
 # ------------------------------------------------------------------------------------
-@pytest.mark.parametrize("n", [8, 64, 130, 257])
+@pytest.mark.parametrize("n", [8, 64, 130, 257, 1024, 1100])
 def test_matmul_f64e_exact_on_small_integers(mpps, n):
-    """Integers below 64 in magnitude are one exact slice; their products sum exactly."""
+    """Integers below 64 in magnitude are one exact slice; their products sum exactly.  At
+    n = 1024 and 1100 the tiles are fewer than two per SM, and CTAs split the K range of
+    tiles (up to three pieces per tile) and add the pieces' integer sums."""
     rng = np.random.default_rng(300 + n)
     A = rng.integers(-63, 64, size=(2, n, n)).astype(np.float64)
     B = rng.integers(-63, 64, size=(2, n, n)).astype(np.float64)
