@@ -579,6 +579,8 @@ struct TileMap {
 // owner's piece its last, so the owner waits only at the end of its own work, for pieces
 // that were computed first.  W of a whole tile sums at most FLUSH chunks, so split launches
 // are limited to K <= FLUSH x 512.  U = 0: whole tiles, blockIdx.x + i gridDim.x.
+constexpr int kMinSplitSlices = 7;
+
 struct Split {
     long long U;            // units; 0: no split
     long long* partW;       // [G][EPI_WARPS][EPI_COLS][32]
@@ -591,20 +593,19 @@ __device__ __forceinline__ long long split_start(int c, long long U) {
     return (long long)c * U / gridDim.x;
 }
 
+template <bool SPLIT>
 struct Segments {
     long long u, ue;        // split: units left
     int id, total, nkb;     // whole tiles: next tile
-    bool split;
     __device__ Segments(const Split& sp, int total_, int nkb_) {
-        split = sp.U > 0;
         total = total_;
         nkb = nkb_;
         id = blockIdx.x;
-        u = split ? split_start(blockIdx.x, sp.U) : 0;
-        ue = split ? split_start(blockIdx.x + 1, sp.U) : 0;
+        u = SPLIT ? split_start(blockIdx.x, sp.U) : 0;
+        ue = SPLIT ? split_start(blockIdx.x + 1, sp.U) : 0;
     }
     __device__ bool next(int& tile, int& kb0, int& kb1) {
-        if (!split) {
+        if (!SPLIT) {
             if (id >= total) return false;
             tile = id;
             kb0 = 0;
@@ -682,7 +683,7 @@ __device__ __forceinline__ void issue_k16(uint32_t tmem, uint64_t da, uint64_t d
     }
 }
 
-template <int K>
+template <int K, bool SPLIT>
 __global__ void __launch_bounds__(THREADS, 1)
     k_gemm_f64e(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 int n, int kpA, int ksB, int batch, const int* __restrict__ eA,
@@ -742,7 +743,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             int s = 0;                                        // stage of K block g
             uint32_t ph = 0;                                  // its fill parity
             bool ok = true;
-            Segments sg(sp, total, nkb);
+            Segments<SPLIT> sg(sp, total, nkb);
             int id, kb0, kb1;
             while (ok && sg.next(id, kb0, kb1)) {
                 int z, m0, n0;
@@ -774,12 +775,12 @@ __global__ void __launch_bounds__(THREADS, 1)
             uint32_t ph = 0;
             bool ok = true;
             const uint32_t ring = smem_u32(smem);
-            Segments sg(sp, total, nkb);
+            Segments<SPLIT> sg(sp, total, nkb);
             int id, kb0, kb1;
             while (ok && sg.next(id, kb0, kb1)) {
                 for (int kb = kb0; kb < kb1 && ok; ++kb) {
                     const int kin = kb % kb_per_chunk;
-                    const bool first = kin == 0 || kb == kb0;   // starts an accumulation
+                    const bool first = kin == 0 || (SPLIT && kb == kb0);   // starts an accumulation
                     if (first && gc > 0) {   // the epilogue must have drained the last one
                         if (!(ok = mbar_wait(tmem_free, (gc - 1) & 1, err))) break;
                         tc_fence_after();
@@ -826,7 +827,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int q4 = warp & 3, h = warp >> 2;   // lane quarter, column group
         const uint32_t lane_base = (uint32_t)(q4 * 32) << 16;
         uint32_t gc = 0;
-        Segments sg(sp, total, nkb);
+        Segments<SPLIT> sg(sp, total, nkb);
         int id, kb0, kb1;
         while (sg.next(id, kb0, kb1)) {
             int z, m0, n0;
@@ -841,7 +842,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             const int cb = n0 + EPI_COLS * h;
             double* orow = ep.out + (long long)b * ep.out_bstride + (long long)row * n + cb;
             const bool vec4 = ((uintptr_t)orow & 31) == 0;
-            const bool head = kb0 == 0;   // this CTA owns the tile
+            const bool head = !SPLIT || kb0 == 0;   // this CTA owns the tile
             const bool pre = ep_pre && head && row < n && cb + EPI_COLS <= n;
             if (pre) f64e_block_sum16(ep, b, row, cb, n, orow);
             const int c_end = (kb1 - 1) / kb_per_chunk;
@@ -879,6 +880,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 }
             }
             if (!ok) break;
+            if constexpr (SPLIT) {
             if (!head) {   // a later piece of a split tile: hand the sums to the owner
                 const size_t slot = ((size_t)blockIdx.x * EPI_WARPS + warp) * EPI_COLS * 32 + lane;
 #pragma unroll
@@ -908,6 +910,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     }
                 }
                 if (!ok) break;
+            }
             }
             // product = 2^{eA+eB-49} W + 2^{eA+eB-14} T, then the fused epilogue
             if (row < n) {
@@ -1017,13 +1020,22 @@ mpps_status launch_k(int dev, int grid, const CUtensorMap& ta, const CUtensorMap
     constexpr int NP = K < MAX_PLANES ? K : MAX_PLANES;
     constexpr int smem = num_stages(NP) * stage_bytes(NP) + 1024 + BAR_BYTES;
     static_assert(smem <= SMEM_MAX, "shared memory budget exceeded");
+    // split K only for the slice counts of working-precision products (7..9); the split
+    // kernel is a separate instantiation so that the whole-tile kernel keeps its code
+    constexpr bool kSplit = K >= kMinSplitSlices;
     static bool attr_done[64] = {false};
     if (!attr_done[dev]) {
-        MPPS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_f64e<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        MPPS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_f64e<K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            smem));
+        if (kSplit)
+            MPPS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_f64e<K, kSplit>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         attr_done[dev] = true;
     }
-    MPPS_CUDA_TRY(launch_pdl(k_gemm_f64e<K>, dim3(grid), dim3(THREADS), smem, st, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, bidx, sp));
+    if (kSplit && sp.U > 0)
+        MPPS_CUDA_TRY(launch_pdl(k_gemm_f64e<K, kSplit>, dim3(grid), dim3(THREADS), smem, st, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, bidx, sp));
+    else
+        MPPS_CUDA_TRY(launch_pdl(k_gemm_f64e<K, false>, dim3(grid), dim3(THREADS), smem, st, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, bidx, sp));
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }
@@ -1174,7 +1186,7 @@ mpps_status launch_gemm_f64e(int k, const void* slicesA, int ksA, const int* eA,
     Split sp{0, nullptr, nullptr, nullptr, 0u};
     const int nkb = (n + KB - 1) / KB;
     const long long waves = (tiles + G - 1) / G;
-    if (split && waves >= 2 && (nkb + KCHUNK / KB - 1) / (KCHUNK / KB) <= FLUSH && tiles * nkb / G >= 16 &&
+    if (split && k >= kMinSplitSlices && waves >= 2 && (nkb + KCHUNK / KB - 1) / (KCHUNK / KB) <= FLUSH && tiles * nkb / G >= 16 &&
         (waves * G - tiles) * 10 >= waves * G) {
         static std::atomic<unsigned> epoch{0};
         unsigned e = epoch.fetch_add(1u) + 1u;
