@@ -468,6 +468,26 @@ def test_expm_emulated_batch_mixed_sigma(mpps):
         assert oracle.rel_err_1norm(E[b], eh, el) <= 50 * n * U * max(1, 2 ** sg)
 
 
+def test_expm_emulated_batch_split_k_squarings(mpps):
+    """Two 1152 x 1152 matrices (162 tiles each, more than one wave on the SMs): the emulated
+    powers and Horner products split K between CTAs, and so do the squarings of both
+    matrices (sigma 3 and 1), whose last two run on one matrix through the index list.
+    Sampled columns against the oracle's Horner applied to unit vectors."""
+    n = 1152
+    A = inputs.gaussian_batch(2, n, seed=31, norm1=[6.0, 1.5])
+    E = host(mpps.expm(dev(A), m=30, policy=mpps.NS_E))
+    cols = [0, 577, n - 1]
+    V = np.zeros((n, len(cols)))
+    for t, j in enumerate(cols):
+        V[j, t] = 1.0
+    for b in range(2):
+        sg = oracle.sigma_for(A[b])
+        wh, wl = oracle.ps_apply_dd(oracle.taylor_exp_rational(30), np.ldexp(A[b], -sg), V,
+                                    reps=2 ** sg)
+        err = np.abs(E[b][:, cols] - wh - wl).sum(axis=0) / np.abs(wh).sum(axis=0)
+        assert np.all(err <= 50 * n * U * max(1, 2 ** sg)), (b, sg, err)
+
+
 # ------------------------------------------------------------------------------------
 # failure path of the bounded waits (no fault: a wait that nothing completes gives up)
 # ------------------------------------------------------------------------------------
