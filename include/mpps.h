@@ -190,6 +190,25 @@ mpps_status ps_eval_adjoint(const double* coeffs, int m, const double* A, const 
                             void* stream);
 
 /*
+ * Gradient of f(A) = <G, r(A)> for the scaling-and-squaring approximant of exp,
+ * r(A) = p_m(2^-sigma A)^(2^sigma) of eq. (3.6) with b_i = 1/i! and sigma = max(0,
+ * ceil(log2 ||A||_1)) per matrix (the paper states no adjoint; this is reverse mode through
+ * the squarings, then through the PS evaluation as in ps_eval_adjoint):
+ *   S_0 = p_m(X), X = 2^-sigma A;  S_{k+1} = S_k^2;
+ *   Sbar_sigma = G;  Sbar_k = Sbar_{k+1} S_k^T + S_k^T Sbar_{k+1};
+ *   gradA = 2^-sigma L_p(X^T, Sbar_0).
+ * The squarings S_0..S_{sigma-1} are stored (sigma n^2 doubles per matrix).
+ *   A, G   : batch x n x n (host or device).     m : Taylor degree (0 -> 30).
+ *   policy : NULL or a policy whose f64_slices selects the products (0 = FP64 pipe, k =
+ *            emulated with k exact bf16 slices); every product, the forward polynomial
+ *            included, is in that working precision; other fields unused.
+ *   gradA  : batch x n x n output (host or device).
+ * Synchronises `stream` (sigma is read back; the forward polynomial plans on the host).
+ */
+mpps_status expm_taylor_ss_adjoint(const double* A, const double* G, int n, int batch, int m,
+                                   const mpps_policy* policy, double* gradA, void* stream);
+
+/*
  * C = A B for a batch of n x n FP64 matrices, the product computed in `format`
  * (an mpps_format other than NONE, or MPPS_FMT_F64E(k)): the building block of every step
  * above.  MPPS_FMT_F64E(k) splits the rows of A and the columns of B into k exact bf16

@@ -9,7 +9,8 @@ Contents
 * ``mpps_oracle.c`` (built here with gcc into ``_liboracle.so``): Algorithm 2.1 literally
   in double-double and plain double, Horner, explicit powers, scaling and squaring
   (eq. (3.6)), column-block application p(X)^k V, the adjoint as the defining double sum
-  of the Frechet derivative, and the 1-norm.
+  of the Frechet derivative, the adjoint of the scaling-and-squaring approximant (chain
+  rule through the squarings), and the 1-norm.
 * Coefficient sequences as exact rationals (``fractions.Fraction``), converted to
   double-double: Taylor exp b_i = 1/i! (Section 3), the [q/q] Pade numerator and
   denominator of exp (Section 4.1; the Ward example of Section 2 prints the first eight
@@ -64,6 +65,7 @@ def lib():
         L.orc_expm_ss_dd.argtypes = [dp, dp, i, i, dp, i, i, dp, dp]
         L.orc_ps_apply_dd.argtypes = [dp, dp, i, dp, i, dp, i, ctypes.c_long, dp, dp]
         L.orc_adjoint_dd.argtypes = [dp, dp, i, dp, dp, i, dp, dp]
+        L.orc_expm_ss_adjoint_dd.argtypes = [dp, dp, i, dp, dp, i, i, dp, dp]
         L.orc_matmul_dd.argtypes = [dp, dp, dp, dp, i, dp, dp]
         L.orc_ps_d.argtypes = [dp, i, i, dp, i, dp, lp]
         L.orc_expm_ss_d.argtypes = [dp, i, i, dp, i, i, dp]
@@ -71,8 +73,8 @@ def lib():
         L.orc_norm1.restype = ctypes.c_double
         L.orc_num_threads.restype = ctypes.c_int
         for name in ("orc_ps_dd", "orc_horner_dd", "orc_powers_dd", "orc_expm_ss_dd",
-                     "orc_ps_apply_dd", "orc_adjoint_dd", "orc_matmul_dd", "orc_ps_d",
-                     "orc_expm_ss_d"):
+                     "orc_ps_apply_dd", "orc_adjoint_dd", "orc_expm_ss_adjoint_dd",
+                     "orc_matmul_dd", "orc_ps_d", "orc_expm_ss_d"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -208,6 +210,19 @@ def adjoint_dd(coefs, A, G):
     dh = np.empty((n, n)); dl = np.empty((n, n))
     if lib().orc_adjoint_dd(_p(ch), _p(cl), m, _p(A), _p(G), n, _p(dh), _p(dl)):
         raise ValueError("orc_adjoint_dd: bad arguments")
+    return dh, dl
+
+
+def expm_ss_adjoint_dd(A, G, m: int, sigma: int, coefs=None):
+    """Gradient of <G, p_m(2^-sigma A)^(2^sigma)> with respect to A (sigma fixed): the chain
+    rule through the squarings of eq. (3.6) and the defining double sum of the polynomial's
+    Frechet derivative, in double-double."""
+    ch, cl = _coef_arrays(coefs if coefs is not None else taylor_exp_rational(m))
+    m = len(ch) - 1
+    A = _f64(A); G = _f64(G); n = A.shape[0]
+    dh = np.empty((n, n)); dl = np.empty((n, n))
+    if lib().orc_expm_ss_adjoint_dd(_p(ch), _p(cl), m, _p(A), _p(G), n, int(sigma), _p(dh), _p(dl)):
+        raise ValueError("orc_expm_ss_adjoint_dd: bad arguments")
     return dh, dl
 
 

@@ -287,17 +287,16 @@ int orc_ps_apply_dd(const double* coef_hi, const double* coef_lo, int m,
  * the definition of the derivative of a matrix polynomial).  Written as the double sum,
  * with the powers Q_j = (A^T)^j formed once by repeated multiplication.  Double-double.
  */
-int orc_adjoint_dd(const double* coef_hi, const double* coef_lo, int m,
-                   const double* A, const double* G, int n, double* D_hi, double* D_lo) {
-    if (m < 0 || n <= 0) return -1;
+/* D = sum_k c_k sum_{j<k} (A^T)^j Gm (A^T)^(k-1-j) for a double-double Gm. */
+static void adjoint_sum_dd(const double* coef_hi, const double* coef_lo, int m,
+                           const double* A, ddmat Gm, ddmat D) {
+    int n = Gm.n;
     int nq = m > 0 ? m : 1;
     ddmat* Q = (ddmat*)malloc(sizeof(ddmat) * (size_t)nq);
     for (int j = 0; j < nq; ++j) Q[j] = ddm_alloc(n);
-    ddmat At = ddm_alloc(n), Gm = ddm_alloc(n), T = ddm_alloc(n), U = ddm_alloc(n),
-          D = ddm_alloc(n);
+    ddmat At = ddm_alloc(n), T = ddm_alloc(n), U = ddm_alloc(n);
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < n; ++j) At.v[(size_t)i * n + j] = dd_from(A[(size_t)j * n + i]);
-    ddm_load(Gm, G);
     ddm_identity(Q[0]);
     for (int j = 1; j < nq; ++j) ddm_mul(Q[j], Q[j - 1], At);
     ddm_zero(D);
@@ -309,11 +308,67 @@ int orc_adjoint_dd(const double* coef_hi, const double* coef_lo, int m,
             ddm_axpy(D, c, U);
         }
     }
-    ddm_store(D, D_hi, D_lo);
     for (int j = 0; j < nq; ++j) ddm_free(&Q[j]);
     free(Q);
-    ddm_free(&At); ddm_free(&Gm); ddm_free(&T); ddm_free(&U); ddm_free(&D);
+    ddm_free(&At); ddm_free(&T); ddm_free(&U);
+}
+
+int orc_adjoint_dd(const double* coef_hi, const double* coef_lo, int m,
+                   const double* A, const double* G, int n, double* D_hi, double* D_lo) {
+    if (m < 0 || n <= 0) return -1;
+    ddmat Gm = ddm_alloc(n), D = ddm_alloc(n);
+    ddm_load(Gm, G);
+    adjoint_sum_dd(coef_hi, coef_lo, m, A, Gm, D);
+    ddm_store(D, D_hi, D_lo);
+    ddm_free(&Gm); ddm_free(&D);
     return 0;
+}
+
+/*
+ * Gradient of A -> <G, r(A)> for the scaling-and-squaring approximant of eq. (3.6),
+ * r(A) = p(X)^(2^sigma), X = 2^-sigma A, sigma given: the chain rule through each step.
+ *   S_0 = p(X), S_{k+1} = S_k S_k                      (k < sigma)
+ *   d<G, S_sigma> : Sbar_sigma = G,  Sbar_k = Sbar_{k+1} S_k^T + S_k^T Sbar_{k+1}
+ *   Xbar = sum_k c_k sum_{j<k} (X^T)^j Sbar_0 (X^T)^(k-1-j),   Abar = 2^-sigma Xbar.
+ * All in double-double; S_0 from Algorithm 2.1 (orc_ps_dd).
+ */
+int orc_expm_ss_adjoint_dd(const double* coef_hi, const double* coef_lo, int m,
+                           const double* A, const double* G, int n, int sigma,
+                           double* D_hi, double* D_lo) {
+    if (m < 0 || n <= 0 || sigma < 0) return -1;
+    size_t N = (size_t)n * n;
+    double* X = (double*)malloc(sizeof(double) * N);
+    double* ph = (double*)malloc(sizeof(double) * N);
+    double* pl = (double*)malloc(sizeof(double) * N);
+    for (size_t t = 0; t < N; ++t) X[t] = ldexp(A[t], -sigma);
+    int rc = orc_ps_dd(coef_hi, coef_lo, m, 0, X, n, ph, pl, NULL);
+    if (rc == 0) {
+        int ns = sigma > 0 ? sigma : 1;
+        ddmat* S = (ddmat*)malloc(sizeof(ddmat) * (size_t)ns);
+        for (int k = 0; k < ns; ++k) S[k] = ddm_alloc(n);
+        for (size_t t = 0; t < N; ++t) { S[0].v[t].hi = ph[t]; S[0].v[t].lo = pl[t]; }
+        for (int k = 1; k < sigma; ++k) ddm_mul(S[k], S[k - 1], S[k - 1]);
+        ddmat Sb = ddm_alloc(n), St = ddm_alloc(n), T1 = ddm_alloc(n), T2 = ddm_alloc(n),
+              D = ddm_alloc(n);
+        ddm_load(Sb, G);
+        for (int k = sigma - 1; k >= 0; --k) {
+            for (int i = 0; i < n; ++i)          /* St = S_k^T */
+                for (int j = 0; j < n; ++j) St.v[(size_t)i * n + j] = S[k].v[(size_t)j * n + i];
+            ddm_mul(T1, Sb, St);
+            ddm_mul(T2, St, Sb);
+            for (size_t t = 0; t < N; ++t) Sb.v[t] = dd_add(T1.v[t], T2.v[t]);
+        }
+        adjoint_sum_dd(coef_hi, coef_lo, m, X, Sb, D);
+        for (size_t t = 0; t < N; ++t) {   /* exact power-of-two scaling of both words */
+            D_hi[t] = ldexp(D.v[t].hi, -sigma);
+            D_lo[t] = ldexp(D.v[t].lo, -sigma);
+        }
+        for (int k = 0; k < ns; ++k) ddm_free(&S[k]);
+        free(S);
+        ddm_free(&Sb); ddm_free(&St); ddm_free(&T1); ddm_free(&T2); ddm_free(&D);
+    }
+    free(X); free(ph); free(pl);
+    return rc;
 }
 
 /* Product of two double-double matrices (hi/lo pairs), C = A B; used by the tests to

@@ -79,7 +79,8 @@ class _Report(ctypes.Structure):
 EXPORTS = ("mpps_policy_default", "mpps_plan", "ps_eval", "expm_taylor_ss", "ps_eval_adjoint",
            "mpps_matmul", "mpps_last_error", "mpps_version", "mpps_profile_enable",
            "mpps_profile_reset", "mpps_profile_read", "mpps_matmul_noalloc",
-           "mpps_selftest_bounded_wait", "expm_taylor_ss_grouped", "mpps_release_workspace")
+           "mpps_selftest_bounded_wait", "expm_taylor_ss_grouped", "mpps_release_workspace",
+           "expm_taylor_ss_adjoint")
 PROF_GEMM_F64, PROF_GEMM_TC, PROF_ELEMENTWISE, PROF_GEMM_F64E, PROF_SLICE = 0, 1, 2, 3, 4
 
 
@@ -101,6 +102,7 @@ def lib():
         L.expm_taylor_ss.argtypes = [vp, ip, ip, ip, ctypes.POINTER(_Policy), vp,
                                      ctypes.POINTER(_Report), vp]
         L.ps_eval_adjoint.argtypes = [dp, ip, vp, vp, ip, ip, ctypes.POINTER(_Policy), vp, vp]
+        L.expm_taylor_ss_adjoint.argtypes = [vp, vp, ip, ip, ip, ctypes.POINTER(_Policy), vp, vp]
         L.mpps_matmul.argtypes = [vp, vp, vp, ip, ip, ip, vp]
         L.mpps_matmul_noalloc.argtypes = [vp, vp, vp, ip, ip, ip, vp]
         L.mpps_matmul_noalloc.restype = ctypes.c_int
@@ -111,7 +113,8 @@ def lib():
         L.mpps_selftest_bounded_wait.restype = ctypes.c_int
         L.mpps_release_workspace.argtypes = []
         L.mpps_release_workspace.restype = ctypes.c_int
-        for f in ("mpps_plan", "ps_eval", "expm_taylor_ss", "ps_eval_adjoint", "mpps_matmul"):
+        for f in ("mpps_plan", "ps_eval", "expm_taylor_ss", "ps_eval_adjoint",
+                  "expm_taylor_ss_adjoint", "mpps_matmul"):
             getattr(L, f).restype = ctypes.c_int
         L.mpps_profile_enable.argtypes = [ctypes.c_int]
         L.mpps_profile_enable.restype = None
@@ -358,6 +361,24 @@ def ps_eval_adjoint(coeffs, A, G, out=None, policy: Policy | None = None, stream
     return out
 
 
+def expm_adjoint(A, G, m: int = 30, out=None, policy: Policy | None = None, stream=None):
+    """Gradient of <G, r(A)> with respect to A for the scaling-and-squaring approximant
+    r(A) = p_m(2^-sigma A)^(2^sigma) (reverse mode through the squarings and the PS steps;
+    products on the FP64 pipe, or emulated when policy.f64_slices > 0)."""
+    ptr, batch, n, kind, keep = _prep(A, "A")
+    gptr, gb, gn, _, _ = _prep(G, "G")
+    if (gb, gn) != (batch, n):
+        raise ValueError("G must have the shape of A")
+    if out is None:
+        out = _empty_like(A, keep)
+    optr, _, _, _, _ = _prep(out, "out")
+    pol = (policy or Policy(f64_slices=0))._c()
+    _check(lib().expm_taylor_ss_adjoint(ctypes.c_void_p(ptr), ctypes.c_void_p(gptr), n, batch,
+                                        int(m), ctypes.byref(pol), ctypes.c_void_p(optr),
+                                        _stream_for(kind, stream)))
+    return out
+
+
 def matmul(A, B, fmt="fp64", out=None, stream=None):
     """C = A B with the product computed in format `fmt` (name or FMT_* code)."""
     f = _FMT_BY_NAME[fmt] if isinstance(fmt, str) else int(fmt)
@@ -420,7 +441,7 @@ def release_workspace() -> None:
 def _make_autograd():
     torch = _torch()
     if torch is None:  # pragma: no cover
-        return None
+        return None, None
 
     class PolyFn(torch.autograd.Function):
         """p(A) with a hand-written reverse mode: forward ps_eval, backward ps_eval_adjoint.
@@ -444,12 +465,39 @@ def _make_autograd():
             gA = ps_eval_adjoint(ctx.coeffs, A64, G, policy=ctx.policy)
             return gA.to(ctx.in_dtype), None, None
 
-    return PolyFn
+    class ExpmFn(torch.autograd.Function):
+        """exp(A) by scaling and squaring (expm) with a hand-written reverse mode
+        (expm_adjoint).  FP32 inputs are evaluated in FP64 and returned in the input dtype."""
+
+        @staticmethod
+        def forward(ctx, A, m=30, policy=None):
+            A64 = A.detach().to(torch.float64).contiguous()
+            E = expm(A64, m=m, policy=policy)
+            ctx.save_for_backward(A64)
+            ctx.m = m
+            ctx.policy = policy
+            ctx.in_dtype = A.dtype
+            return E.to(A.dtype)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (A64,) = ctx.saved_tensors
+            G = grad_out.detach().to(torch.float64).contiguous()
+            gA = expm_adjoint(A64, G, m=ctx.m, policy=ctx.policy)
+            return gA.to(ctx.in_dtype), None, None
+
+    return PolyFn, ExpmFn
 
 
-PolyFn = _make_autograd()
+PolyFn, ExpmFn = _make_autograd()
 
 
 def poly(A, coeffs, policy: Policy | None = None):
     """Differentiable p(A) (torch): ``PolyFn.apply`` with a default policy."""
     return PolyFn.apply(A, coeffs, policy)
+
+
+def expm_differentiable(A, m: int = 30, policy: Policy | None = None):
+    """Differentiable exp(A) (torch): ``ExpmFn.apply``; the backward pass differentiates the
+    scaling-and-squaring approximant with the same products (policy.f64_slices)."""
+    return ExpmFn.apply(A, m, policy)

@@ -1251,4 +1251,176 @@ mpps_status ps_eval_adjoint(const double* coeffs, int m, const double* A, const 
     return MPPS_OK;
 }
 
+mpps_status expm_taylor_ss_adjoint(const double* A, const double* G, int n, int batch, int m,
+                                   const mpps_policy* policy, double* gradA, void* stream) {
+    clear_error();
+    mpps_status rc = check_sizes(n, batch);
+    if (rc) return rc;
+    if (m <= 0) m = 30;
+    if (m > 170) {
+        set_error("expm_taylor_ss_adjoint: degree m=%d too large", m);
+        return MPPS_EINVAL;
+    }
+    if (batch == 0) return MPPS_OK;
+    if (!A || !G || !gradA) {
+        set_error("expm_taylor_ss_adjoint: null matrix pointer");
+        return MPPS_EINVAL;
+    }
+    const Pol pol = resolve(policy);
+    if (pol.f64k < 0 || pol.f64k > MPPS_F64E_MAX_SLICES) {
+        set_error("f64_slices=%d outside 0..%d", pol.f64k, MPPS_F64E_MAX_SLICES);
+        return MPPS_EINVAL;
+    }
+    const int K = pol.f64k;
+    // the forward polynomial and the PS adjoint in the working precision (FP64 pipe or
+    // emulated with K slices), like every product below
+    mpps_policy fpol;
+    mpps_policy_default(&fpol);
+    fpol.mode = MPPS_FIXED_FP64;
+    fpol.f64_slices = K;
+    std::vector<double> c(m + 1);   // b_i = 1/i!, as in expm_taylor_ss
+    {
+        long double f = 1.0L;
+        for (int i = 0; i <= m; ++i) {
+            if (i > 0) f /= (long double)i;
+            c[i] = (double)f;
+        }
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long nn = (long long)n * n;
+    const size_t elems = (size_t)batch * nn;
+    Staged a, g;
+    if ((rc = stage_in(A, elems, st, a))) return rc;
+    if ((rc = stage_in(G, elems, st, g))) return rc;
+    const bool o_dev = is_device_ptr(gradA);
+
+    // ---- sigma per matrix (eq. (3.6)), X = 2^-sigma A
+    Arena L1;
+    double *X, *partial, *anorm;
+    int* d_sigma;
+    auto lay1 = [&](Arena& z) {
+        X = z.take<double>(elems);
+        partial = z.take<double>(norm1_partial_elems(n, batch));
+        anorm = z.take<double>(batch);
+        d_sigma = z.take<int>(batch);
+    };
+    lay1(L1);
+    DevBuf ws1;
+    if ((rc = ws1.alloc(L1.off, st))) return rc;
+    L1.base = (char*)ws1.p;
+    L1.off = 0;
+    lay1(L1);
+    if ((rc = launch_norm1(a.dev, nn, n, batch, partial, anorm, st))) return rc;
+    if ((rc = launch_sigma(anorm, batch, d_sigma, st))) return rc;
+    if ((rc = launch_scale_copy(a.dev, nn, X, nn, n, batch, d_sigma, st))) return rc;
+    std::vector<int> sigma(batch);
+    MPPS_CUDA_TRY(cudaMemcpyAsync(sigma.data(), d_sigma, sizeof(int) * batch,
+                                  cudaMemcpyDeviceToHost, st));
+    MPPS_CUDA_TRY(cudaStreamSynchronize(st));
+    int sig_max = 0;
+    for (int b = 0; b < batch; ++b) sig_max = std::max(sig_max, sigma[b]);
+
+    // ---- workspace: the squarings S_0..S_{sigma-1}, two upstream buffers, scratch
+    Arena L2;
+    double *S, *Sb0, *Sb1, *T, *tmp, *Xbar, *dGrad = gradA;
+    int* d_lists;
+    __nv_bfloat16 *slA = nullptr, *slB = nullptr;
+    int *eA = nullptr, *eB = nullptr;
+    unsigned long long* cmx = nullptr;
+    char* split = nullptr;
+    auto lay2 = [&](Arena& z) {
+        S = z.take<double>((size_t)std::max(sig_max, 1) * elems);
+        Sb0 = z.take<double>(elems);
+        Sb1 = z.take<double>(elems);
+        T = z.take<double>(elems);
+        tmp = z.take<double>(elems);
+        Xbar = z.take<double>(elems);
+        d_lists = z.take<int>((size_t)std::max(sig_max, 1) * batch);
+        if (!o_dev) dGrad = z.take<double>(elems);
+        if (K > 0) {
+            slA = z.take<__nv_bfloat16>(f64e_plane_elems(n, batch, K));
+            slB = z.take<__nv_bfloat16>(f64e_plane_elems(n, batch, K));
+            eA = z.take<int>((size_t)batch * n);
+            eB = z.take<int>((size_t)batch * n);
+            cmx = z.take<unsigned long long>((size_t)batch * n);
+            split = z.take<char>(f64e_split_bytes());
+        }
+    };
+    lay2(L2);
+    DevBuf ws2;
+    if ((rc = ws2.alloc(L2.off, st))) return rc;
+    L2.base = (char*)ws2.p;
+    L2.off = 0;
+    lay2(L2);
+    if (split) MPPS_CUDA_TRY(cudaMemsetAsync(split, 0, f64e_split_flag_bytes(), st));
+    DevErr* derr = nullptr;
+    if (K > 0) {
+        if ((rc = dev_err_get(&derr))) return rc;
+        if ((rc = dev_err_check(derr, false))) return rc;
+    }
+    // C = Am Bm (+ add) for the `cnt` matrices listed in `list` (all when null)
+    auto product = [&](const double* Am, const double* Bm, int cnt, const int* list,
+                       const Epilogue& ep) -> mpps_status {
+        if (K == 0) return launch_gemm_f64(Am, nn, Bm, nn, n, cnt, ep, st, list);
+        mpps_status r1 = launch_slice_rows(Am, nn, n, batch, K, slA, eA, st);
+        if (!r1) r1 = launch_slice_cols(Bm, nn, n, batch, K, slB, eB, cmx, st);
+        if (!r1)
+            r1 = launch_gemm_f64e(K, slA, K, eA, slB, K, eB, n, cnt, batch, ep, derr->d, st, list,
+                                  split);
+        return r1;
+    };
+
+    // ---- forward: S_0 = p(X), S_{k+1} = S_k^2 for the matrices with sigma > k + 1
+    if ((rc = ps_eval(c.data(), m, X, n, batch, &fpol, S, nullptr, stream))) return rc;
+    std::vector<int> lists((size_t)std::max(sig_max, 1) * batch);
+    std::vector<int> counts(std::max(sig_max, 1), 0);
+    for (int k = 0; k < sig_max; ++k)
+        for (int b = 0; b < batch; ++b)
+            if (sigma[b] > k) lists[(size_t)k * batch + counts[k]++] = b;
+    MPPS_CUDA_TRY(cudaMemcpyAsync(d_lists, lists.data(), sizeof(int) * lists.size(),
+                                  cudaMemcpyHostToDevice, st));
+    for (int k = 0; k + 1 < sig_max; ++k) {
+        // S_{k+1} is needed by the matrices with sigma > k + 1: list k + 1
+        Epilogue ep = epilogue_plain(S + (size_t)(k + 1) * elems, nn);
+        const double* Sk = S + (size_t)k * elems;
+        if ((rc = product(Sk, Sk, counts[k + 1], d_lists + (size_t)(k + 1) * batch, ep))) return rc;
+    }
+
+    // ---- backward through the squarings: Sbar_k = Sbar_{k+1} S_k^T + S_k^T Sbar_{k+1}.
+    // Step k reads buffer k mod 2 and writes buffer (k + 1) mod 2, so matrix b starts with
+    // G in buffer (sigma_b + 1) mod 2 and every matrix ends in buffer 1.
+    double* Sb[2] = {Sb0, Sb1};
+    for (int b = 0; b < batch; ++b)
+        MPPS_CUDA_TRY(cudaMemcpyAsync(Sb[(sigma[b] + 1) & 1] + (size_t)b * nn,
+                                      g.dev + (size_t)b * nn, sizeof(double) * nn,
+                                      cudaMemcpyDeviceToDevice, st));
+    for (int k = sig_max - 1; k >= 0; --k) {
+        const int* lk = d_lists + (size_t)k * batch;
+        if ((rc = launch_transpose(S + (size_t)k * elems, nn, T, n, batch, st))) return rc;
+        Epilogue e1 = epilogue_plain(tmp, nn);   // Sbar_{k+1} S_k^T
+        if ((rc = product(Sb[k & 1], T, counts[k], lk, e1))) return rc;
+        Epilogue e2 = epilogue_plain(Sb[(k + 1) & 1], nn);   // S_k^T Sbar_{k+1} + that
+        e2.add = tmp;
+        e2.add_bstride = nn;
+        e2.add_coef = 1.0;
+        if ((rc = product(T, Sb[k & 1], counts[k], lk, e2))) return rc;
+    }
+    // ---- through p: Xbar = L_p(X^T, Sbar_0); then Abar = 2^-sigma Xbar
+    if ((rc = ps_eval_adjoint(c.data(), m, X, Sb[1], n, batch, &fpol, Xbar, stream))) return rc;
+    if ((rc = launch_scale_copy(Xbar, nn, dGrad, nn, n, batch, d_sigma, st))) return rc;
+    if (K > 0) {
+        if ((rc = dev_err_enqueue(derr, st))) return rc;
+        if (!o_dev && (rc = dev_err_check(derr, true))) return rc;
+    }
+    if (!o_dev) {
+        MPPS_CUDA_TRY(cudaMemcpyAsync(gradA, dGrad, elems * sizeof(double), cudaMemcpyDeviceToHost, st));
+        MPPS_CUDA_TRY(cudaStreamSynchronize(st));
+        if (K > 0 && (rc = dev_err_check(derr, true))) return rc;
+    } else {
+        // the workspace above is released stream-ordered; the staged inputs too
+        if (!is_device_ptr(A) || !is_device_ptr(G)) MPPS_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    return MPPS_OK;
+}
+
 }  // extern "C"

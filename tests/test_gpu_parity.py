@@ -535,6 +535,49 @@ def test_adjoint_emulated_vs_oracle(mpps, n, m):
     assert oracle.norm1(g - gh - gl) / oracle.norm1(gh) <= 100 * n * U
 
 
+@pytest.mark.parametrize("n,m,norms", [(16, 30, (0.5, 3.0, 7.0)), (33, 18, (5.0, 0.2)),
+                                         (64, 12, (2.5,))])
+@pytest.mark.parametrize("k", [0, 8])
+def test_expm_adjoint_vs_oracle(mpps, n, m, norms, k):
+    """Reverse mode through scaling and squaring (one sigma per matrix, a batch of mixed
+    sigma) against the oracle's chain rule in double-double; k = 0: FP64 pipe, k = 8:
+    emulated products."""
+    batch = len(norms)
+    A = inputs.gaussian_batch(batch, n, seed=900 + n, norm1=list(norms))
+    rng = np.random.default_rng(n + m)
+    G = rng.standard_normal((batch, n, n))
+    g = host(mpps.expm_adjoint(dev(A), dev(G), m=m,
+                               policy=mpps.Policy(mode=mpps.FIXED_FP64, f64_slices=k)))
+    for b in range(batch):
+        sg = oracle.sigma_for(A[b])
+        gh, gl = oracle.expm_ss_adjoint_dd(A[b], G[b], m, sg)
+        err = oracle.norm1(g[b] - gh - gl) / oracle.norm1(gh)
+        assert err <= 100 * n * U * max(1, 2 ** sg), (b, sg, err)
+
+
+def test_expm_autograd_central_differences(mpps):
+    """torch autograd through ExpmFn: the backward pass equals expm_adjoint and matches FP64
+    central differences of the forward expm."""
+    n = 24
+    A0 = inputs.gaussian_matrix(n, seed=77, norm1=3.0)
+    A = torch.tensor(A0, device="cuda:0", requires_grad=True)
+    G = torch.randn((n, n), generator=torch.Generator(device="cuda:0").manual_seed(8),
+                    device="cuda:0", dtype=torch.float64)
+    E = mpps.expm_differentiable(A)
+    (E * G).sum().backward()
+    grad = A.grad.cpu().numpy()
+    direct = host(mpps.expm_adjoint(dev(A0[None]), G[None].contiguous()))[0]
+    assert np.array_equal(grad, direct)
+    h = 1e-6
+    Gn = G.cpu().numpy()
+    for (i, j) in [(0, 0), (3, 17), (20, 5)]:
+        D = np.zeros((n, n)); D[i, j] = h
+        fp = host(mpps.expm(dev(A0 + D)))
+        fm = host(mpps.expm(dev(A0 - D)))
+        fd = float(np.sum(Gn * (fp - fm))) / (2 * h)
+        assert abs(fd - grad[i, j]) <= 1e-7 * max(1.0, abs(grad[i, j])), (i, j, fd, grad[i, j])
+
+
 def test_adjoint_fp32_batch_config_shape(mpps):
     """Batch of FP32-stored 128 x 128 matrices, N(0,1)/sqrt(n) entries, Taylor exp m = 18,
     through the autograd Function with emulated products: the gradient agrees with the

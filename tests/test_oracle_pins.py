@@ -334,6 +334,67 @@ def test_adjoint_central_differences():
         assert abs(fd - gh[i, j]) < 1e-9 * max(1.0, abs(gh[i, j]))
 
 
+@pytest.mark.parametrize("sigma", [0, 1, 3])
+def test_expm_ss_adjoint_block_identity(sigma):
+    """The scaling-and-squaring approximant r(A) = p(2^-sigma A)^(2^sigma) is a polynomial in
+    A for fixed sigma, so <grad, E> = <G, r([[A, E], [0, A]])_12> with r evaluated by the
+    independent forward routine (Algorithm 2.1 then sigma squarings on the 2n matrix)."""
+    n, m = 6, 12
+    A = RNG.standard_normal((n, n)) * 0.5
+    G = RNG.standard_normal((n, n))
+    E = RNG.standard_normal((n, n))
+    gh, gl = oracle.expm_ss_adjoint_dd(A, G, m, sigma)
+    M = np.zeros((2 * n, 2 * n))
+    M[:n, :n] = A; M[n:, n:] = A; M[:n, n:] = E
+    eh, el = oracle.expm_ss_dd(M, m, sigma)
+    lhs = math.fsum((gh * E).ravel()) + math.fsum((gl * E).ravel())
+    rhs = math.fsum((G * eh[:n, n:]).ravel()) + math.fsum((G * el[:n, n:]).ravel())
+    scale = math.fsum(np.abs(G * eh[:n, n:]).ravel())
+    assert abs(lhs - rhs) < 1e-14 * scale
+    # entrywise: grad = L_r(A^T, G) = r([[A^T, G], [0, A^T]])_12
+    Mt = np.zeros((2 * n, 2 * n))
+    Mt[:n, :n] = A.T; Mt[n:, n:] = A.T; Mt[:n, n:] = G
+    th, tl = oracle.expm_ss_dd(Mt, m, sigma)
+    assert np.max(np.abs((gh - th[:n, n:]) + (gl - tl[:n, n:]))) < 1e-26 * np.max(np.abs(gh))
+
+
+def test_expm_ss_adjoint_diagonal_closed_form():
+    """For A = diag(d) the gradient is G_ij r[d_i, d_j] (divided differences of the scalar
+    r(x) = p(2^-sigma x)^(2^sigma), r'(d_i) on the diagonal), here in 40-digit arithmetic."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    d = np.array([-1.75, -0.5, 0.25, 1.5, 3.0])
+    n, m, sigma = len(d), 16, 2
+    c = [mpmath.mpf(x.numerator) / x.denominator for x in oracle.taylor_exp_rational(m)]
+    p = lambda y: sum(cj * y ** j for j, cj in enumerate(c))
+    dp = lambda y: sum(j * cj * y ** (j - 1) for j, cj in enumerate(c) if j > 0)
+    q = 2 ** sigma
+    r = lambda x: p(mpmath.mpf(x) / q) ** q
+    dr = lambda x: p(mpmath.mpf(x) / q) ** (q - 1) * dp(mpmath.mpf(x) / q)
+    G = RNG.standard_normal((n, n))
+    gh, gl = oracle.expm_ss_adjoint_dd(np.diag(d), G, m, sigma)
+    for i in range(n):
+        for j in range(n):
+            dd_ = dr(d[i]) if i == j else (r(d[i]) - r(d[j])) / (mpmath.mpf(d[i]) - mpmath.mpf(d[j]))
+            ref = mpmath.mpf(G[i, j]) * dd_
+            got = mpmath.mpf(gh[i, j]) + mpmath.mpf(gl[i, j])
+            assert abs(got - ref) <= mpmath.mpf(1e-28) * max(1, abs(ref))
+
+
+def test_expm_ss_adjoint_central_differences():
+    n, m, sigma = 5, 10, 2
+    A = RNG.standard_normal((n, n)) * 0.8
+    G = RNG.standard_normal((n, n))
+    gh, gl = oracle.expm_ss_adjoint_dd(A, G, m, sigma)
+    h = 1e-6
+    for (i, j) in [(0, 0), (2, 4), (3, 1)]:
+        E = np.zeros((n, n)); E[i, j] = h
+        ph, pl = oracle.expm_ss_dd(A + E, m, sigma)
+        mh, ml = oracle.expm_ss_dd(A - E, m, sigma)
+        fd = (np.sum(G * (ph - mh)) + np.sum(G * (pl - ml))) / (2 * h)
+        assert abs(fd - gh[i, j]) < 1e-8 * max(1.0, abs(gh[i, j]))
+
+
 # --------------------------------------------------------------------------------
 # 9. the paper's printed worked example and tables
 # --------------------------------------------------------------------------------
