@@ -92,6 +92,8 @@ typedef struct {
     int f64_slices;         /* 0: working-precision products on the FP64 pipe (DMMA);
                                k in 1..MPPS_F64E_MAX_SLICES: emulate them as MPPS_FMT_F64E(k),
                                and let mixed steps use F64E(k') for k' < k as well */
+    int variable_s;         /* 1 (mixed modes, s = 0): the variable-s branch of Algorithm 3.1
+                               (mpps_choose_s); 0: s = ceil(sqrt(m)) */
 } mpps_policy;
 
 /* Per-matrix description of what a call did (filled when `rep` is non-NULL). */
@@ -109,8 +111,19 @@ typedef struct {
 } mpps_report;
 
 /* Fill *p with the defaults: MIXED_NS, tol 2^-53, delta 10, s 0, all formats, floor 2,
- * f64_slices 0 (working-precision products on the FP64 pipe). */
+ * f64_slices 0 (working-precision products on the FP64 pipe), variable_s 0. */
 void mpps_policy_default(mpps_policy* p);
+
+/*
+ * Host-only rule of the variable-s branch of Algorithm 3.1 (no GPU work).  Starting from
+ * s0 = ceil(sqrt(m)), and only when ||X||_1 <= s0/e, s grows by one while
+ *   ||Y||_1 > ||B_0||_1 ||X||_1^s   and   s < m   (and s < MPPS_MAX_S),
+ * Y = X^s and B_0 = sum_{j<s} b_j X^j for the current s (||X||^s by repeated
+ * multiplication).  normB0[k] and normY[k] are the norms for s = s0 + k, k < len.
+ * Returns the chosen s (at most s0 + len - 1: the caller supplies norms as s grows), or -1
+ * for m < 1, len < 1 or a NULL pointer.
+ */
+int mpps_choose_s(int m, double normX, const double* normB0, const double* normY, int len);
 
 /*
  * Host-only precision planner (no GPU work): eq. (2.8) at nu = 1,

@@ -308,6 +308,31 @@ def block_norms_dd(coefs, X, s: int = 0):
     return norms, norm1(pw[s])
 
 
+def choose_s(m: int, normX: float, normB0, normY):
+    """The variable-s branch of Algorithm 3.1 (fix_params false), step by step.
+
+    Start from s = ceil(sqrt(m)).  The branch is taken only when ||X||_1 <= s/e; then, while
+    ||Y||_1 > ||B_0||_1 ||X||_1^s and s < m, the algorithm adds Y/s! to B_0 (B_0 becomes the
+    first block for s+1), increments s and forms the next power as Y.  normB0[k] and
+    normY[k] are ||B_0|| and ||Y|| = ||X^s|| for s = s0 + k, k < len(normB0); the result is
+    at most s0 + len(normB0).  ||X||^s is formed by repeated multiplication.  (The library
+    also stops at s = 32, its largest block size.)"""
+    s0 = ceil_sqrt(m)
+    if not (normX <= s0 / math.e):
+        return s0
+    s = s0
+    for k in range(len(normB0)):
+        if s >= m or s >= 32:
+            break
+        xs = 1.0
+        for _ in range(s):
+            xs *= normX
+        if not (normY[k] > normB0[k] * xs):
+            break
+        s += 1
+    return s
+
+
 # ---------------------------------------------------------------------------------
 # precision rule (eq. (2.8); Algorithm 3.1 fix_params branch; Algorithm 4.1)
 # ---------------------------------------------------------------------------------

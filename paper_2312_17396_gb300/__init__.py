@@ -59,7 +59,7 @@ class MppsError(RuntimeError):
 class _Policy(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("tol", ctypes.c_double), ("delta", ctypes.c_double),
                 ("s", ctypes.c_int), ("formats", ctypes.c_uint), ("fp64_floor_steps", ctypes.c_int),
-                ("f64_slices", ctypes.c_int)]
+                ("f64_slices", ctypes.c_int), ("variable_s", ctypes.c_int)]
 
 
 class _GroupItem(ctypes.Structure):
@@ -80,7 +80,7 @@ EXPORTS = ("mpps_policy_default", "mpps_plan", "ps_eval", "expm_taylor_ss", "ps_
            "mpps_matmul", "mpps_last_error", "mpps_version", "mpps_profile_enable",
            "mpps_profile_reset", "mpps_profile_read", "mpps_matmul_noalloc",
            "mpps_selftest_bounded_wait", "expm_taylor_ss_grouped", "mpps_release_workspace",
-           "expm_taylor_ss_adjoint")
+           "expm_taylor_ss_adjoint", "mpps_choose_s")
 PROF_GEMM_F64, PROF_GEMM_TC, PROF_ELEMENTWISE, PROF_GEMM_F64E, PROF_SLICE = 0, 1, 2, 3, 4
 
 
@@ -103,6 +103,8 @@ def lib():
                                      ctypes.POINTER(_Report), vp]
         L.ps_eval_adjoint.argtypes = [dp, ip, vp, vp, ip, ip, ctypes.POINTER(_Policy), vp, vp]
         L.expm_taylor_ss_adjoint.argtypes = [vp, vp, ip, ip, ip, ctypes.POINTER(_Policy), vp, vp]
+        L.mpps_choose_s.argtypes = [ip, ctypes.c_double, dp, dp, ip]
+        L.mpps_choose_s.restype = ctypes.c_int
         L.mpps_matmul.argtypes = [vp, vp, vp, ip, ip, ip, vp]
         L.mpps_matmul_noalloc.argtypes = [vp, vp, vp, ip, ip, ip, vp]
         L.mpps_matmul_noalloc.restype = ctypes.c_int
@@ -148,6 +150,7 @@ class Policy:
     formats: object = 0x1F          # bitmask or iterable of format names
     fp64_floor_steps: int = 2
     f64_slices: int = 0             # 0: FP64 pipe; k: emulate FP64 products with k slices
+    variable_s: bool = False        # the variable-s branch of Algorithm 3.1 (mixed modes)
 
     def _c(self):
         fm = self.formats
@@ -157,7 +160,8 @@ class Policy:
                 mask |= 1 << _FMT_BY_NAME[name]
             fm = mask
         return _Policy(int(self.mode), float(self.tol), float(self.delta), int(self.s),
-                       int(fm), int(self.fp64_floor_steps), int(self.f64_slices))
+                       int(fm), int(self.fp64_floor_steps), int(self.f64_slices),
+                       int(bool(self.variable_s)))
 
 
 FIXED = Policy(mode=FIXED_FP64)
@@ -377,6 +381,18 @@ def expm_adjoint(A, G, m: int = 30, out=None, policy: Policy | None = None, stre
                                         int(m), ctypes.byref(pol), ctypes.c_void_p(optr),
                                         _stream_for(kind, stream)))
     return out
+
+
+def choose_s(m: int, normX: float, normB0, normY) -> int:
+    """The library's variable-s rule (mpps_choose_s) on given norms: normB0[k], normY[k] are
+    ||B_0||_1 and ||X^s||_1 for s = ceil(sqrt(m)) + k."""
+    b0 = np.ascontiguousarray(normB0, dtype=np.float64)
+    y = np.ascontiguousarray(normY, dtype=np.float64)
+    if b0.shape != y.shape or b0.size < 1:
+        raise ValueError("normB0 and normY need the same non-zero length")
+    dp = ctypes.POINTER(ctypes.c_double)
+    return int(lib().mpps_choose_s(int(m), float(normX), b0.ctypes.data_as(dp),
+                                   y.ctypes.data_as(dp), int(b0.size)))
 
 
 def matmul(A, B, fmt="fp64", out=None, stream=None):

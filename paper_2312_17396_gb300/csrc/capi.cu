@@ -33,6 +33,7 @@ struct Pol {
     unsigned formats;
     int floor_steps;
     int f64k;   // 0: FP64 pipe; k > 0: working-precision products emulated with k slices
+    int var_s;  // variable-s branch of Algorithm 3.1
 };
 
 static Pol resolve(const mpps_policy* p) {
@@ -47,6 +48,7 @@ static Pol resolve(const mpps_policy* p) {
     r.formats = (p->formats ? p->formats : 0x1Fu) | 1u;
     r.floor_steps = p->fp64_floor_steps < 0 ? 2 : p->fp64_floor_steps;
     r.f64k = p->f64_slices;
+    r.var_s = p->variable_s != 0;
     return r;
 }
 
@@ -56,6 +58,26 @@ static int ceil_sqrt_int(int m) {
     while (s * s < m) ++s;
     while (s > 1 && (s - 1) * (s - 1) >= m) --s;
     return s;
+}
+
+// Variable-s branch of Algorithm 3.1: entered when ||X||_1 <= s0/e (s0 = ceil(sqrt(m)));
+// s then grows while ||Y|| > ||B_0|| ||X||^s and s < m (||X||^s by repeated multiplication).
+static bool var_s_grow(int m, int s, double normX, double normB0, double normY) {
+    if (s >= m || s >= MPPS_MAX_S) return false;
+    double xs = 1.0;
+    for (int j = 0; j < s; ++j) xs *= normX;
+    return normY > normB0 * xs;
+}
+
+extern "C" int mpps_choose_s(int m, double normX, const double* normB0, const double* normY,
+                             int len) {
+    if (m < 1 || len < 1 || !normB0 || !normY) return -1;
+    const int s0 = ceil_sqrt_int(m);
+    const double kE = 2.718281828459045;   // e
+    if (!(normX <= (double)s0 / kE)) return s0;
+    int k = 0;
+    while (k < len && var_s_grow(m, s0 + k, normX, normB0[k], normY[k])) ++k;
+    return s0 + k;
 }
 
 // unit roundoff of the rounded inputs of each format, and the FP32 accumulation unit
@@ -342,16 +364,27 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
             }
         return MPPS_OK;
     }
-    const int s = pol.s > 0 ? std::min(pol.s, m) : ceil_sqrt_int(m);
+    int s = pol.s > 0 ? std::min(pol.s, m) : ceil_sqrt_int(m);
     if (s > MPPS_MAX_S || m / s > MPPS_MAX_R) {
         set_error("m=%d with s=%d is outside the supported range (s<=%d, r<=%d)", m, s, MPPS_MAX_S,
                   MPPS_MAX_R);
         return MPPS_EINVAL;
     }
-    const int r = m / s;
-    const bool fold = (m % s) == 0;
-    const int q = block_norms_count(m, s);
-    const long long pw_bs = (long long)s * nn;
+    // Variable s (Algorithm 3.1, fix_params false): s may grow after the powers, so the
+    // power table has room for s_cap powers and the norm buffers for every s up to it.
+    const bool var_s = pol.var_s && pol.s <= 0 && pol.mode != MPPS_FIXED_FP64 && m >= 2;
+    const int s0 = s;
+    const int s_cap = var_s ? std::min(std::min(m, MPPS_MAX_S), 2 * s0) : s;
+    int r = m / s;
+    bool fold = (m % s) == 0;
+    int q = block_norms_count(m, s);   // largest at the smallest s
+    const int q_alloc = q;
+    size_t partial_elems = norm1_partial_elems(n, batch);
+    for (int t = s0; t <= s_cap; ++t)
+        partial_elems = std::max(partial_elems,
+                                 std::max(block_norms_partial_elems(n, batch, m, t),
+                                          block_norms_f32_partial_elems(n, batch, m, t)));
+    const long long pw_bs = (long long)s_cap * nn;
 
     // ---- phase-1 workspace (FP64 part, and slice planes when FP64 is emulated)
     const int K = pol.f64k;                      // slices of an emulated working-precision product
@@ -365,10 +398,8 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
         pw = a.take<double>((size_t)batch * pw_bs);
         Pb0 = a.take<double>((size_t)batch * nn);
         Pb1 = a.take<double>((size_t)batch * nn);
-        partial = a.take<double>(std::max(std::max(block_norms_partial_elems(n, batch, m, s),
-                                                   block_norms_f32_partial_elems(n, batch, m, s)),
-                                          norm1_partial_elems(n, batch)));
-        norms = a.take<double>((size_t)batch * q);
+        partial = a.take<double>(partial_elems);
+        norms = a.take<double>((size_t)batch * q_alloc);
         d_anorm = a.take<double>(batch);
         d_sigma = a.take<int>(batch);
         d_bidx = a.take<int>((size_t)batch * 64);
@@ -420,17 +451,54 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
         rc = slice_cols(pw, pw_bs, K, slB, eB);
         if (rc) return rc;
     }
-    for (int j = 2; j <= s; ++j) {
+    auto power = [&](int j) -> mpps_status {   // X_j = X_{j-1} X_1
         Epilogue ep = epilogue_plain(pw + (long long)(j - 1) * nn, pw_bs);
         if (K > 0) {
-            rc = launch_slice_rows(pw + (long long)(j - 2) * nn, pw_bs, n, batch, K, slA, eA, st);
-            if (!rc)
-                rc = launch_gemm_f64e(K, slA, K, eA, slB, K, eB, n, batch, batch, ep, d_err, st,
+            mpps_status r1 = launch_slice_rows(pw + (long long)(j - 2) * nn, pw_bs, n, batch, K,
+                                               slA, eA, st);
+            if (!r1)
+                r1 = launch_gemm_f64e(K, slA, K, eA, slB, K, eB, n, batch, batch, ep, d_err, st,
                                       nullptr, split);
-        } else {
-            rc = launch_gemm_f64(pw + (long long)(j - 2) * nn, pw_bs, pw, pw_bs, n, batch, ep, st);
+            return r1;
         }
-        if (rc) return rc;
+        return launch_gemm_f64(pw + (long long)(j - 2) * nn, pw_bs, pw, pw_bs, n, batch, ep, st);
+    };
+    for (int j = 2; j <= s; ++j)
+        if ((rc = power(j))) return rc;
+
+    // ---- variable s (Algorithm 3.1): while a matrix's rule asks for it (mpps_choose_s on
+    // ||X||, and ||B_0||, ||Y|| for each s so far), s grows by one and X_s = X_{s-1} X_1 is
+    // formed; a batch takes the largest s any of its matrices asks for
+    if (var_s) {
+        std::vector<std::vector<double>> nb0(batch), ny(batch);
+        std::vector<double> nx(batch, 0.0);
+        for (;;) {
+            q = block_norms_count(m, s);
+            r = m / s;
+            if (expm)
+                rc = launch_block_norms_f32(pw, pw_bs, n, batch, s, m, coeffs, partial, norms, st);
+            else
+                rc = launch_block_norms(pw, pw_bs, n, batch, s, m, d_coef, partial, norms, st);
+            if (rc) return rc;
+            std::vector<double> h((size_t)batch * q);
+            MPPS_CUDA_TRY(cudaMemcpyAsync(h.data(), norms, sizeof(double) * h.size(),
+                                          cudaMemcpyDeviceToHost, st));
+            MPPS_CUDA_TRY(cudaStreamSynchronize(st));
+            bool grow = false;
+            for (int b = 0; b < batch; ++b) {
+                if (s == s0) nx[b] = h[(size_t)b * q + r + 2];
+                nb0[b].push_back(h[(size_t)b * q]);
+                ny[b].push_back(h[(size_t)b * q + r + 1]);
+                if (mpps_choose_s(m, nx[b], nb0[b].data(), ny[b].data(), (int)nb0[b].size()) > s)
+                    grow = true;
+            }
+            if (!grow || s >= s_cap) break;
+            ++s;
+            if ((rc = power(s))) return rc;
+        }
+        r = m / s;
+        fold = (m % s) == 0;
+        q = block_norms_count(m, s);
     }
 
     // ---- a3: ||B_i||_1, ||Y||_1, ||X||_1
@@ -738,6 +806,7 @@ void mpps_policy_default(mpps_policy* p) {
     p->formats = 0x1Fu;
     p->fp64_floor_steps = 2;
     p->f64_slices = 0;
+    p->variable_s = 0;
 }
 
 mpps_status mpps_release_workspace(void) {

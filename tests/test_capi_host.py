@@ -109,3 +109,18 @@ def test_planner_emulated_ladder(mpps):
     assert f["fmt"][1:] == ["f64e8", "f64e8", "none"]
     with pytest.raises(mpps.MppsError):
         mpps.plan(9, 64, norms, 1.0, mpps.Policy(f64_slices=10))
+
+
+def test_variable_s_rule_matches_oracle(mpps):
+    """The library's variable-s rule (Algorithm 3.1, fix_params false) against the oracle's
+    statement of it, on random norm sequences around the growth condition."""
+    rng = np.random.default_rng(31)
+    for _ in range(500):
+        m = int(rng.integers(1, 80))
+        s0 = oracle.ceil_sqrt(m)
+        normX = float(rng.choice([s0 / np.e, s0 / np.e * (1 + 1e-12), 10.0 ** rng.uniform(-3, 0.5)]))
+        ln = int(rng.integers(1, 12))
+        b0 = 10.0 ** rng.uniform(-2, 1, size=ln)
+        # ||Y|| near ||B_0|| ||X||^s, on either side
+        y = np.array([b0[k] * normX ** (s0 + k) * 10.0 ** rng.uniform(-1, 1) for k in range(ln)])
+        assert mpps.choose_s(m, normX, b0, y) == oracle.choose_s(m, normX, list(b0), list(y))

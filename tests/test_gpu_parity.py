@@ -139,6 +139,59 @@ def test_ps_eval_fp8_steps_row_column_scaled(mpps, n, graded):
     assert err <= 50 * n * tol, (err, rep[0]["fmt"])
 
 
+def _var_s_expected(coefq, X, m, s_cap):
+    """The oracle's variable-s choice from double-double norms, and the smallest relative
+    margin of the growth tests it made (a decision closer than that to the threshold could
+    flip under the library's own norm rounding)."""
+    s0 = oracle.ceil_sqrt(m)
+    nx = oracle.norm1(X)
+    b0, ys = [], []
+    for s in range(s0, s_cap + 1):
+        nb, ny = oracle.block_norms_dd(coefq, X, s)
+        b0.append(nb[0]); ys.append(ny)
+    got = min(oracle.choose_s(m, nx, b0, ys), s_cap)
+    margin = min(abs(ys[k] - b0[k] * nx ** (s0 + k)) / ys[k] for k in range(got - s0 + 1 if got < s_cap else got - s0))
+    return got, margin
+
+
+@pytest.mark.parametrize("k", [0, 8])
+def test_ps_eval_variable_s(mpps, k):
+    """The variable-s branch of Algorithm 3.1: for X = -0.9 I + small noise ||B_0|| < 1, so
+    ||Y|| > ||B_0|| ||X||^s and s grows; the chosen s matches the oracle's rule on
+    double-double norms and the result keeps the fixed-FP64 accuracy.  A matrix with
+    ||B_0|| >= 1 keeps s = ceil(sqrt(m)) and gives the same bits as without the branch."""
+    n, m = 64, 30
+    rng = np.random.default_rng(55)
+    X = -0.9 * np.eye(n) + 0.02 * rng.standard_normal((n, n)) / np.sqrt(n)
+    coefq = oracle.taylor_exp_rational(m)
+    coef = mpps.taylor_exp_coeffs(m)
+    pol = mpps.Policy(mode=mpps.MIXED_NS, variable_s=True, f64_slices=k)
+    P, rep = mpps.ps_eval(coef, dev(X), policy=pol, report=True)
+    s_cap = min(m, 32, 2 * oracle.ceil_sqrt(m))
+    want, margin = _var_s_expected(coefq, X, m, s_cap)
+    assert margin > 1e-6
+    assert want > oracle.ceil_sqrt(m)
+    assert rep[0]["s"] == want, (rep[0]["s"], want)
+    ph, pl, _ = oracle.ps_dd(coefq, X)
+    assert oracle.rel_err_1norm(host(P), ph, pl) <= 50 * n * U
+    # expm takes the branch too; with ||X||_1 < 1 (sigma = 0) and this X the rule would grow
+    # s past the library's cap of 2 ceil(sqrt(m)) = 12
+    X2 = -0.85 * np.eye(n) + 0.01 * rng.standard_normal((n, n)) / np.sqrt(n)
+    assert oracle.sigma_for(X2) == 0
+    want2, margin2 = _var_s_expected(coefq, X2, m, s_cap)
+    assert margin2 > 1e-6 and want2 == s_cap
+    E, erep = mpps.expm(dev(X2), m=m, policy=pol, report=True)
+    assert erep[0]["s"] == want2
+    eh, el = oracle.expm_ss_dd(X2, m, 0)
+    assert oracle.rel_err_1norm(host(E), eh, el) <= 50 * n * U
+    # no growth for a Gaussian matrix: identical to the fixed-s evaluation
+    G = inputs.gaussian_matrix(n, seed=56, norm1=0.5)
+    P1, r1 = mpps.ps_eval(coef, dev(G), policy=pol, report=True)
+    P0 = mpps.ps_eval(coef, dev(G), policy=mpps.Policy(mode=mpps.MIXED_NS, f64_slices=k))
+    assert r1[0]["s"] == oracle.ceil_sqrt(m)
+    assert np.array_equal(host(P1), host(P0))
+
+
 def test_ps_eval_general_coefficients(mpps):
     n = 96
     A = inputs.gaussian_matrix(n, seed=5, norm1=2.0)

@@ -395,6 +395,24 @@ def test_expm_ss_adjoint_central_differences():
         assert abs(fd - gh[i, j]) < 1e-8 * max(1.0, abs(gh[i, j]))
 
 
+def test_choose_s_variable_branch_by_hand():
+    """Algorithm 3.1's variable-s loop on norms worked out by hand (m = 30, s0 = 6)."""
+    # ||X|| = 3 > 6/e: the branch is not taken
+    assert oracle.choose_s(30, 3.0, [0.5], [10.0]) == 6
+    # ||X|| = 1/2: ||X||^6 = 1/64, ^7 = 1/128, ^8 = 1/256
+    #   s = 6: 0.02 > 0.5/64 = 0.0078 -> 7;  s = 7: 0.015 > 0.0039 -> 8;
+    #   s = 8: 0.001 > 0.00195 fails -> stop at 8
+    assert oracle.choose_s(30, 0.5, [0.5, 0.5, 0.5], [0.02, 0.015, 0.001]) == 8
+    # the first test fails: s stays 6
+    assert oracle.choose_s(30, 0.5, [0.5], [0.007]) == 6
+    # growth stops at s = m (m = 5, s0 = 3)
+    assert oracle.choose_s(5, 0.1, [1e-9] * 5, [1.0] * 5) == 5
+    # and after the norms supplied (two of them)
+    assert oracle.choose_s(30, 0.5, [1e-9, 1e-9], [1.0, 1.0]) == 8
+    # ||X|| exactly at s0/e takes the branch
+    assert oracle.choose_s(30, 6 / math.e, [1e-9], [1.0]) == 7
+
+
 # --------------------------------------------------------------------------------
 # 9. the paper's printed worked example and tables
 # --------------------------------------------------------------------------------
