@@ -295,6 +295,28 @@ mpps_status mpps_selftest_bounded_wait(int limit_us, void* stream);
  * MPPS_ECUDA if a synchronisation or the trim fails. */
 mpps_status mpps_release_workspace(void);
 
+/*
+ * Measured choice of product schedules.  Two products have more than one valid schedule:
+ * the emulated FP64 product with 7..9 slices (whole output tiles per CTA, or the K range of
+ * tiles split between CTAs) and the tensor-core low-precision product (128 x 64 or
+ * 128 x 128 tiles).  By default a rule measured on GB300 chooses.  With tuning on, the first
+ * launch of each (kind, n, batch, variant) times every candidate on its own operands (CUDA
+ * events on the call's stream; the call then waits for those launches), keeps the fastest
+ * for the rest of the process and leaves that candidate's output.  Launches whose epilogue
+ * accumulates into their own output are not tuned.  Host-only calls.
+ *   mpps_autotune_enable : 1 = on, 0 = off (initially MPPS_AUTOTUNE=1 in the environment).
+ *   mpps_autotune_clear  : forget every measured choice.
+ *   mpps_autotune_entries: the table: kind (0 = emulated-product split, 1 = tensor-core tile
+ *                          width), n, batch, variant (slice count or format), choice (index
+ *                          of the fastest candidate) and the mean time of each of up to 4
+ *                          candidates in ms (ms[4 i + c]); fills at most `cap` rows (any
+ *                          pointer may be NULL) and returns the number of entries.
+ */
+void mpps_autotune_enable(int on);
+void mpps_autotune_clear(void);
+int mpps_autotune_entries(int* kind, int* n, int* batch, int* variant, int* choice, float* ms,
+                          int cap);
+
 /* Description of the last failure on this thread ("" if none). */
 const char* mpps_last_error(void);
 

@@ -80,7 +80,8 @@ EXPORTS = ("mpps_policy_default", "mpps_plan", "ps_eval", "expm_taylor_ss", "ps_
            "mpps_matmul", "mpps_last_error", "mpps_version", "mpps_profile_enable",
            "mpps_profile_reset", "mpps_profile_read", "mpps_matmul_noalloc",
            "mpps_selftest_bounded_wait", "expm_taylor_ss_grouped", "mpps_release_workspace",
-           "expm_taylor_ss_adjoint", "mpps_choose_s")
+           "expm_taylor_ss_adjoint", "mpps_choose_s", "mpps_autotune_enable",
+           "mpps_autotune_clear", "mpps_autotune_entries")
 PROF_GEMM_F64, PROF_GEMM_TC, PROF_ELEMENTWISE, PROF_GEMM_F64E, PROF_SLICE = 0, 1, 2, 3, 4
 
 
@@ -105,6 +106,12 @@ def lib():
         L.expm_taylor_ss_adjoint.argtypes = [vp, vp, ip, ip, ip, ctypes.POINTER(_Policy), vp, vp]
         L.mpps_choose_s.argtypes = [ip, ctypes.c_double, dp, dp, ip]
         L.mpps_choose_s.restype = ctypes.c_int
+        L.mpps_autotune_enable.argtypes = [ctypes.c_int]
+        L.mpps_autotune_enable.restype = None
+        L.mpps_autotune_clear.argtypes = []
+        L.mpps_autotune_clear.restype = None
+        L.mpps_autotune_entries.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.c_int]
+        L.mpps_autotune_entries.restype = ctypes.c_int
         L.mpps_matmul.argtypes = [vp, vp, vp, ip, ip, ip, vp]
         L.mpps_matmul_noalloc.argtypes = [vp, vp, vp, ip, ip, ip, vp]
         L.mpps_matmul_noalloc.restype = ctypes.c_int
@@ -393,6 +400,32 @@ def choose_s(m: int, normX: float, normB0, normY) -> int:
     dp = ctypes.POINTER(ctypes.c_double)
     return int(lib().mpps_choose_s(int(m), float(normX), b0.ctypes.data_as(dp),
                                    y.ctypes.data_as(dp), int(b0.size)))
+
+
+def autotune(on: bool = True) -> None:
+    """Switch measured schedule choice on or off (see mpps_autotune_enable)."""
+    lib().mpps_autotune_enable(1 if on else 0)
+
+
+def autotune_clear() -> None:
+    lib().mpps_autotune_clear()
+
+
+def autotune_entries() -> list:
+    """The measured choices: dicts with kind ('f64e_split' or 'tc_width'), n, batch,
+    variant, choice and the candidates' mean times in ms."""
+    L = lib()
+    cnt = L.mpps_autotune_entries(None, None, None, None, None, None, 0)
+    if cnt == 0:
+        return []
+    cols = [np.zeros(cnt, dtype=np.int32) for _ in range(5)]
+    ms = np.zeros(4 * cnt, dtype=np.float32)
+    L.mpps_autotune_entries(*[ctypes.c_void_p(c.ctypes.data) for c in cols],
+                            ctypes.c_void_p(ms.ctypes.data), cnt)
+    kinds = {0: "f64e_split", 1: "tc_width"}
+    return [dict(kind=kinds.get(int(cols[0][i]), int(cols[0][i])), n=int(cols[1][i]),
+                 batch=int(cols[2][i]), variant=int(cols[3][i]), choice=int(cols[4][i]),
+                 ms=[float(x) for x in ms[4 * i:4 * i + 4]]) for i in range(cnt)]
 
 
 def matmul(A, B, fmt="fp64", out=None, stream=None):

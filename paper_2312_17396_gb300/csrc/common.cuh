@@ -6,6 +6,8 @@
 #include <cuda_fp8.h>
 #include <stdint.h>
 
+#include <functional>
+
 #include "../../include/mpps.h"
 
 namespace mpps {
@@ -318,6 +320,17 @@ mpps_status launch_gemm_f64e(int k, const void* slicesA, int ksA, const int* eA,
                              const void* slicesBt, int ksB, const int* eB, int n, int batch,
                              int nmat, const Epilogue& ep, int* d_err, cudaStream_t st,
                              const int* bidx = nullptr, void* split = nullptr);
+
+// ---- measured choice of product schedules (autotune.cu) ---------------------------
+constexpr int kTuneMaxCandidates = 4;
+enum { TUNE_F64E_SPLIT = 0, TUNE_TC_WIDTH = 1 };
+// Whether tuning is on (mpps_autotune_enable, or MPPS_AUTOTUNE=1).
+bool tune_enabled();
+// The tuned candidate for (kind, n, batch, variant) on the current device, or -1.
+int tune_lookup(int kind, int n, int batch, int variant);
+// Time launch(c) for c < ncand on stream st, record the fastest, leave its output.
+mpps_status tune_run(int kind, int n, int batch, int variant, int ncand, cudaStream_t st,
+                     const std::function<mpps_status(int)>& launch);
 
 // Slice planes per operand of an emulated product MPPS_FMT_F64E(k): k, at most 8 (k = 9
 // adds slice pairs, not slices).

@@ -1183,36 +1183,50 @@ mpps_status launch_gemm_f64e(int k, const void* slicesA, int ksA, const int* eA,
     // leave at least a tenth of the SMs' time idle, every CTA keeps at least 16 K blocks and
     // W needs no flush.  (With a single partial wave the split costs more than it saves:
     // each piece adds a TMEM drain during which the tensor pipe waits.)
-    Split sp{0, nullptr, nullptr, nullptr, 0u};
     const int nkb = (n + KB - 1) / KB;
     const long long waves = (tiles + G - 1) / G;
-    if (split && k >= kMinSplitSlices && waves >= 2 && (nkb + KCHUNK / KB - 1) / (KCHUNK / KB) <= FLUSH && tiles * nkb / G >= 16 &&
-        (waves * G - tiles) * 10 >= waves * G) {
-        static std::atomic<unsigned> epoch{0};
-        unsigned e = epoch.fetch_add(1u) + 1u;
-        if (e == 0u) e = epoch.fetch_add(1u) + 1u;
-        char* base = (char*)split;
-        const size_t nslot = (size_t)G * EPI_WARPS * EPI_COLS * 32;
-        sp.U = tiles * nkb;
-        sp.flags = (unsigned*)base;
-        sp.partW = (long long*)(base + f64e_split_flag_bytes());
-        sp.partT = (float*)(sp.partW + nslot);
-        sp.epoch = e;
-        grid = G;
-    }
+    const bool can_split = split && k >= kMinSplitSlices &&
+                           (nkb + KCHUNK / KB - 1) / (KCHUNK / KB) <= FLUSH && tiles * nkb / G >= 16;
+    const int tuned = can_split ? tune_lookup(TUNE_F64E_SPLIT, n, batch, k) : -1;
+    const bool rule = can_split && waves >= 2 && (waves * G - tiles) * 10 >= waves * G;
+    const int grid_tiles = grid;
+    auto run = [&](bool use_split) -> mpps_status {
+        Split sp{0, nullptr, nullptr, nullptr, 0u};
+        int g = grid_tiles;
+        if (use_split) {
+            static std::atomic<unsigned> epoch{0};
+            unsigned e = epoch.fetch_add(1u) + 1u;
+            if (e == 0u) e = epoch.fetch_add(1u) + 1u;
+            char* base = (char*)split;
+            const size_t nslot = (size_t)G * EPI_WARPS * EPI_COLS * 32;
+            sp.U = tiles * nkb;
+            sp.flags = (unsigned*)base;
+            sp.partW = (long long*)(base + f64e_split_flag_bytes());
+            sp.partT = (float*)(sp.partW + nslot);
+            sp.epoch = e;
+            g = G;
+        }
+        switch (k) {
+            case 1: return launch_k<1>(dev, g, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx, sp);
+            case 2: return launch_k<2>(dev, g, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx, sp);
+            case 3: return launch_k<3>(dev, g, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx, sp);
+            case 4: return launch_k<4>(dev, g, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx, sp);
+            case 5: return launch_k<5>(dev, g, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx, sp);
+            case 6: return launch_k<6>(dev, g, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx, sp);
+            case 7: return launch_k<7>(dev, g, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx, sp);
+            case 8: return launch_k<8>(dev, g, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx, sp);
+            default: return launch_k<9>(dev, g, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx, sp);
+        }
+    };
     const int pairs = k <= 8 ? k * (k + 1) / 2 : 43;
     ProfScope prof(MPPS_PROF_GEMM_F64E, st, 2.0 * n * (double)n * n * batch * pairs);
-    switch (k) {
-        case 1: return launch_k<1>(dev, grid, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx, sp);
-        case 2: return launch_k<2>(dev, grid, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx, sp);
-        case 3: return launch_k<3>(dev, grid, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx, sp);
-        case 4: return launch_k<4>(dev, grid, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx, sp);
-        case 5: return launch_k<5>(dev, grid, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx, sp);
-        case 6: return launch_k<6>(dev, grid, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx, sp);
-        case 7: return launch_k<7>(dev, grid, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx, sp);
-        case 8: return launch_k<8>(dev, grid, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx, sp);
-        default: return launch_k<9>(dev, grid, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, st, bidx, sp);
-    }
+    // with tuning on, the first launch of an eligible shape times both schedules (not when
+    // the epilogue accumulates into its own output: a re-run would add twice)
+    const bool inplace = ep.add != nullptr && ep.add == ep.out;
+    if (can_split && tuned < 0 && !inplace && tune_enabled())
+        return tune_run(TUNE_F64E_SPLIT, n, batch, k, 2, st,
+                        [&](int c) { return run(c == 1); });
+    return run(tuned >= 0 ? tuned == 1 : rule);
 }
 
 }  // namespace mpps

@@ -313,22 +313,30 @@ mpps_status launch_gemm_tc(int fmt, const void* A_hi, const void* A_lo, const vo
     // block sums) then spreads over twice as many SMs
     const long long tiles128 = (long long)((n + 127) / 128) * ((n + 127) / 128) * batch;
     const bool narrow = tiles128 < 2 * 148;
+    // candidate 0: 128 x 64 tiles, 1: 128 x 128 (the rule above, or the tuned choice)
+    auto run = [&](int c) -> mpps_status {
 #define MPPS_TC_CASE(F)                                                                         \
     case F:                                                                                     \
-        return narrow ? launch_fmt<F, 64>(A_hi, A_lo, Bt_hi, Bt_lo, a_bs, b_bs, lld, n, batch, ep, \
+        return c == 0 ? launch_fmt<F, 64>(A_hi, A_lo, Bt_hi, Bt_lo, a_bs, b_bs, lld, n, batch, ep, \
                                           d_err, st)                                            \
                       : launch_fmt<F, 128>(A_hi, A_lo, Bt_hi, Bt_lo, a_bs, b_bs, lld, n, batch, ep, \
                                            d_err, st);
-    switch (fmt) {
-        MPPS_TC_CASE(MPPS_FMT_BF16)
-        MPPS_TC_CASE(MPPS_FMT_BF16X3)
-        MPPS_TC_CASE(MPPS_FMT_TF32)
-        MPPS_TC_CASE(MPPS_FMT_FP8)
+        switch (fmt) {
+            MPPS_TC_CASE(MPPS_FMT_BF16)
+            MPPS_TC_CASE(MPPS_FMT_BF16X3)
+            MPPS_TC_CASE(MPPS_FMT_TF32)
+            MPPS_TC_CASE(MPPS_FMT_FP8)
 #undef MPPS_TC_CASE
-        default:
-            set_error("launch_gemm_tc: unsupported format %d", fmt);
-            return MPPS_EINVAL;
-    }
+            default:
+                set_error("launch_gemm_tc: unsupported format %d", fmt);
+                return MPPS_EINVAL;
+        }
+    };
+    const int tuned = tune_lookup(TUNE_TC_WIDTH, n, batch, fmt);
+    const bool inplace = ep.add != nullptr && ep.add == ep.out;   // a re-run would add twice
+    if (tuned < 0 && !inplace && tune_enabled())
+        return tune_run(TUNE_TC_WIDTH, n, batch, fmt, 2, st, run);
+    return run(tuned >= 0 ? tuned : (narrow ? 0 : 1));
 }
 
 }  // namespace mpps

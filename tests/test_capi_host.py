@@ -124,3 +124,13 @@ def test_variable_s_rule_matches_oracle(mpps):
         # ||Y|| near ||B_0|| ||X||^s, on either side
         y = np.array([b0[k] * normX ** (s0 + k) * 10.0 ** rng.uniform(-1, 1) for k in range(ln)])
         assert mpps.choose_s(m, normX, b0, y) == oracle.choose_s(m, normX, list(b0), list(y))
+
+
+def test_autotune_table_host_calls(mpps):
+    """Switching measured schedule choice on and off and clearing its table need no GPU."""
+    mpps.autotune_clear()
+    assert mpps.autotune_entries() == []
+    mpps.autotune(True)
+    mpps.autotune(False)
+    mpps.autotune_clear()
+    assert mpps.autotune_entries() == []

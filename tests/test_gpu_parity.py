@@ -542,6 +542,35 @@ def test_expm_emulated_batch_split_k_squarings(mpps):
         assert np.all(err <= 50 * n * U * max(1, 2 ** sg)), (b, sg, err)
 
 
+def test_autotune_picks_a_schedule_and_keeps_its_output(mpps):
+    """With tuning on, the first product of a shape times both schedules and records the
+    fastest; the output is that schedule's, and the next call (from the table) gives the
+    same bits.  Small-integer inputs make every schedule exact (A B in FP64)."""
+    rng = np.random.default_rng(12)
+    A = rng.integers(-63, 64, size=(2, 1024, 1024)).astype(np.float64)
+    B = rng.integers(-63, 64, size=(2, 1024, 1024)).astype(np.float64)
+    A2 = rng.integers(-63, 64, size=(1, 512, 512)).astype(np.float64)
+    B2 = rng.integers(-63, 64, size=(1, 512, 512)).astype(np.float64)
+    mpps.autotune_clear()
+    mpps.autotune(True)
+    try:
+        C1 = host(mpps.matmul(dev(A), dev(B), "f64e8"))
+        C2 = host(mpps.matmul(dev(A), dev(B), "f64e8"))
+        L1 = host(mpps.matmul(dev(A2), dev(B2), "bf16"))
+        L2 = host(mpps.matmul(dev(A2), dev(B2), "bf16"))
+        ent = {(e["kind"], e["n"], e["batch"], e["variant"]): e for e in mpps.autotune_entries()}
+    finally:
+        mpps.autotune(False)
+        mpps.autotune_clear()
+    exact = np.einsum("bij,bjk->bik", A, B)
+    assert np.array_equal(C1, exact) and np.array_equal(C2, C1)
+    assert np.array_equal(L1[0], A2[0] @ B2[0]) and np.array_equal(L2, L1)
+    e = ent[("f64e_split", 1024, 2, 8)]
+    assert e["choice"] in (0, 1) and e["ms"][0] > 0 and e["ms"][1] > 0
+    t = ent[("tc_width", 512, 1, 3)]
+    assert t["choice"] in (0, 1) and t["ms"][0] > 0 and t["ms"][1] > 0
+
+
 # ------------------------------------------------------------------------------------
 # failure path of the bounded waits (no fault: a wait that nothing completes gives up)
 # ------------------------------------------------------------------------------------
