@@ -203,6 +203,23 @@ mpps_status ps_eval_adjoint(const double* coeffs, int m, const double* A, const 
                             void* stream);
 
 /*
+ * exp(A) by the [13/13] Pade approximant r = q^-1 p with scaling and squaring (the Pade
+ * numerator and denominator of Section 4.1 evaluated from one power chain, then a linear
+ * solve): sigma = smallest integer >= 0 with 2^-sigma ||A||_1 <= theta_13 = 5.3719...
+ * (the bound of the [13/13] approximant's backward error by the working precision),
+ * X = 2^-sigma A, V = sum_k c_{2k} X^{2k} and W = sum_k c_{2k+1} X^{2k} (degree-6 polynomials
+ * in X^2, each by the PS evaluation of ps_eval under `policy`), U = X W, p = V + U,
+ * q = p(-X) = V - U, R = q^-1 p by an LU factorisation with partial pivoting (cuSOLVER,
+ * loaded at the first call; MPPS_ENOTSUP if it cannot be), then sigma squarings.  The
+ * products X^2, X W and the squarings run in the working precision of `policy`
+ * (f64_slices: FP64 pipe or emulated).
+ *   A, out : batch x n x n (host or device); out may not alias A.
+ * Synchronises `stream`.
+ */
+mpps_status expm_pade13(const double* A, int n, int batch, const mpps_policy* policy, double* out,
+                        void* stream);
+
+/*
  * Gradient of f(A) = <G, r(A)> for the scaling-and-squaring approximant of exp,
  * r(A) = p_m(2^-sigma A)^(2^sigma) of eq. (3.6) with b_i = 1/i! and sigma = max(0,
  * ceil(log2 ||A||_1)) per matrix (the paper states no adjoint; this is reverse mode through

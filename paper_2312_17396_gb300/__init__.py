@@ -81,7 +81,7 @@ EXPORTS = ("mpps_policy_default", "mpps_plan", "ps_eval", "expm_taylor_ss", "ps_
            "mpps_profile_reset", "mpps_profile_read", "mpps_matmul_noalloc",
            "mpps_selftest_bounded_wait", "expm_taylor_ss_grouped", "mpps_release_workspace",
            "expm_taylor_ss_adjoint", "mpps_choose_s", "mpps_autotune_enable",
-           "mpps_autotune_clear", "mpps_autotune_entries")
+           "mpps_autotune_clear", "mpps_autotune_entries", "expm_pade13")
 PROF_GEMM_F64, PROF_GEMM_TC, PROF_ELEMENTWISE, PROF_GEMM_F64E, PROF_SLICE = 0, 1, 2, 3, 4
 
 
@@ -106,6 +106,8 @@ def lib():
         L.expm_taylor_ss_adjoint.argtypes = [vp, vp, ip, ip, ip, ctypes.POINTER(_Policy), vp, vp]
         L.mpps_choose_s.argtypes = [ip, ctypes.c_double, dp, dp, ip]
         L.mpps_choose_s.restype = ctypes.c_int
+        L.expm_pade13.argtypes = [vp, ip, ip, ctypes.POINTER(_Policy), vp, vp]
+        L.expm_pade13.restype = ctypes.c_int
         L.mpps_autotune_enable.argtypes = [ctypes.c_int]
         L.mpps_autotune_enable.restype = None
         L.mpps_autotune_clear.argtypes = []
@@ -369,6 +371,21 @@ def ps_eval_adjoint(coeffs, A, G, out=None, policy: Policy | None = None, stream
     pol = (policy or Policy(f64_slices=0))._c()
     _check(lib().ps_eval_adjoint(cp, m, ctypes.c_void_p(ptr), ctypes.c_void_p(gptr), n, batch,
                                  ctypes.byref(pol), ctypes.c_void_p(optr), _stream_for(kind, stream)))
+    return out
+
+
+def expm_pade(A, policy: Policy | None = None, out=None, stream=None):
+    """exp(A) by the [13/13] Pade approximant with scaling and squaring (numerator and
+    denominator from one power chain, LU solve, squarings)."""
+    ptr, batch, n, kind, keep = _prep(A, "A")
+    if out is None:
+        out = _empty_like(A, keep)
+    optr, ob, on, _, _ = _prep(out, "out")
+    if (ob, on) != (batch, n):
+        raise ValueError("out has the wrong shape")
+    pol = (policy or Policy())._c()
+    _check(lib().expm_pade13(ctypes.c_void_p(ptr), n, batch, ctypes.byref(pol),
+                             ctypes.c_void_p(optr), _stream_for(kind, stream)))
     return out
 
 

@@ -58,7 +58,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         objs = list(ex.map(compile_one, srcs))
     if force or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [nvcc, *ARCH, "-shared", "-cudart", "static", *objs, "-o", tmp]
+        cmd = [nvcc, *ARCH, "-shared", "-cudart", "static", *objs, "-ldl", "-o", tmp]
         if verbose:
             print(" ".join(cmd))
         subprocess.check_call(cmd)

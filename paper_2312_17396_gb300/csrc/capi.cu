@@ -8,6 +8,9 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <cusolverDn.h>
+#include <dlfcn.h>
+
 #include <algorithm>
 #include <mutex>
 #include <vector>
@@ -1488,6 +1491,266 @@ mpps_status expm_taylor_ss_adjoint(const double* A, const double* G, int n, int 
     } else {
         // the workspace above is released stream-ordered; the staged inputs too
         if (!is_device_ptr(A) || !is_device_ptr(G)) MPPS_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    return MPPS_OK;
+}
+
+}  // extern "C"
+
+// ---- LU solve for the Pade approximant: cuSOLVER, loaded at first use -----------------
+namespace {
+struct Solver {
+    bool tried = false;
+    void* so = nullptr;
+    cusolverStatus_t (*create)(cusolverDnHandle_t*) = nullptr;
+    cusolverStatus_t (*set_stream)(cusolverDnHandle_t, cudaStream_t) = nullptr;
+    cusolverStatus_t (*getrf_ws)(cusolverDnHandle_t, int, int, double*, int, int*) = nullptr;
+    cusolverStatus_t (*getrf)(cusolverDnHandle_t, int, int, double*, int, double*, int*, int*) = nullptr;
+    cusolverStatus_t (*getrs)(cusolverDnHandle_t, cublasOperation_t, int, int, const double*, int,
+                              const int*, double*, int, int*) = nullptr;
+    cusolverDnHandle_t handle[64] = {};
+};
+std::mutex g_solvermu;
+Solver g_solver;
+
+// The solver library is opened only by the Pade entry point, so that the rest of the
+// library does not depend on it.
+mpps_status solver_get(cudaStream_t st, Solver** out, cusolverDnHandle_t* h) {
+    std::lock_guard<std::mutex> lk(g_solvermu);
+    Solver& S = g_solver;
+    if (!S.tried) {
+        S.tried = true;
+        const char* names[] = {"libcusolver.so.12", "libcusolver.so.11", "libcusolver.so",
+                               "/usr/local/cuda/lib64/libcusolver.so.12"};
+        for (const char* nm : names)
+            if ((S.so = dlopen(nm, RTLD_NOW | RTLD_LOCAL))) break;
+        if (S.so) {
+            S.create = (decltype(S.create))dlsym(S.so, "cusolverDnCreate");
+            S.set_stream = (decltype(S.set_stream))dlsym(S.so, "cusolverDnSetStream");
+            S.getrf_ws = (decltype(S.getrf_ws))dlsym(S.so, "cusolverDnDgetrf_bufferSize");
+            S.getrf = (decltype(S.getrf))dlsym(S.so, "cusolverDnDgetrf");
+            S.getrs = (decltype(S.getrs))dlsym(S.so, "cusolverDnDgetrs");
+        }
+    }
+    if (!S.create || !S.set_stream || !S.getrf_ws || !S.getrf || !S.getrs) {
+        set_error("expm_pade13: the LU solver (libcusolver) could not be loaded");
+        return MPPS_ENOTSUP;
+    }
+    int dev = 0;
+    MPPS_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) {
+        set_error("device index %d out of range", dev);
+        return MPPS_ENOTSUP;
+    }
+    if (!S.handle[dev] && S.create(&S.handle[dev]) != CUSOLVER_STATUS_SUCCESS) {
+        S.handle[dev] = nullptr;
+        set_error("cusolverDnCreate failed");
+        return MPPS_ECUDA;
+    }
+    if (S.set_stream(S.handle[dev], st) != CUSOLVER_STATUS_SUCCESS) {
+        set_error("cusolverDnSetStream failed");
+        return MPPS_ECUDA;
+    }
+    *out = &S;
+    *h = S.handle[dev];
+    return MPPS_OK;
+}
+}  // namespace
+
+extern "C" {
+
+mpps_status expm_pade13(const double* A, int n, int batch, const mpps_policy* policy, double* out,
+                        void* stream) {
+    clear_error();
+    mpps_status rc = check_sizes(n, batch);
+    if (rc) return rc;
+    if (batch == 0) return MPPS_OK;
+    if (!A || !out) {
+        set_error("expm_pade13: null matrix pointer");
+        return MPPS_EINVAL;
+    }
+    const Pol pol = resolve(policy);
+    if (pol.f64k < 0 || pol.f64k > MPPS_F64E_MAX_SLICES) {
+        set_error("f64_slices=%d outside 0..%d", pol.f64k, MPPS_F64E_MAX_SLICES);
+        return MPPS_EINVAL;
+    }
+    const int K = pol.f64k;
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long nn = (long long)n * n;
+    const size_t elems = (size_t)batch * nn;
+    Staged a;
+    if ((rc = stage_in(A, elems, st, a))) return rc;
+    const bool o_dev = is_device_ptr(out);
+    Solver* S = nullptr;
+    cusolverDnHandle_t sh = nullptr;
+    if ((rc = solver_get(st, &S, &sh))) return rc;
+
+    // [13/13] Pade coefficients c_j = (26-j)! 13! / (26! j! (13-j)!), by the ratio
+    // c_{j+1} / c_j = (13 - j) / ((26 - j)(j + 1)); even and odd parts as polynomials in X^2
+    double c[14];
+    {
+        long double v = 1.0L;
+        for (int j = 0; j <= 13; ++j) {
+            c[j] = (double)v;
+            v = v * (long double)(13 - j) / ((long double)(26 - j) * (long double)(j + 1));
+        }
+    }
+    double ce[7], co[7];
+    for (int k = 0; k <= 6; ++k) {
+        ce[k] = c[2 * k];
+        co[k] = c[2 * k + 1];
+    }
+
+    // ---- sigma = max(0, ceil(log2(||A||_1 / theta_13))), theta_13 = 5.371920351148152
+    Arena L;
+    double *X, *X2, *V, *W, *U, *P, *Q, *Rb1, *partial, *anorm, *work = nullptr, *dOut = out;
+    int *d_sigma, *d_lists, *ipiv, *info;
+    __nv_bfloat16 *slA = nullptr, *slB = nullptr;
+    int *eA = nullptr, *eB = nullptr;
+    unsigned long long* cmx = nullptr;
+    char* split = nullptr;
+    int lwork = 0;
+    auto lay = [&](Arena& z) {
+        X = z.take<double>(elems);
+        X2 = z.take<double>(elems);
+        V = z.take<double>(elems);
+        W = z.take<double>(elems);
+        U = z.take<double>(elems);
+        P = z.take<double>(elems);
+        Q = z.take<double>(elems);
+        Rb1 = z.take<double>(elems);
+        partial = z.take<double>(norm1_partial_elems(n, batch));
+        anorm = z.take<double>(batch);
+        d_sigma = z.take<int>(batch);
+        d_lists = z.take<int>((size_t)batch * 64);
+        ipiv = z.take<int>((size_t)n);
+        info = z.take<int>(1);
+        if (!o_dev) dOut = z.take<double>(elems);
+        if (K > 0) {
+            slA = z.take<__nv_bfloat16>(f64e_plane_elems(n, batch, K));
+            slB = z.take<__nv_bfloat16>(f64e_plane_elems(n, batch, K));
+            eA = z.take<int>((size_t)batch * n);
+            eB = z.take<int>((size_t)batch * n);
+            cmx = z.take<unsigned long long>((size_t)batch * n);
+            split = z.take<char>(f64e_split_bytes());
+        }
+    };
+    lay(L);
+    DevBuf ws;
+    if ((rc = ws.alloc(L.off, st))) return rc;
+    L.base = (char*)ws.p;
+    L.off = 0;
+    lay(L);
+    if (S->getrf_ws(sh, n, n, Q, n, &lwork) != CUSOLVER_STATUS_SUCCESS) {
+        set_error("cusolverDnDgetrf_bufferSize failed");
+        return MPPS_ECUDA;
+    }
+    DevBuf wbuf;
+    if ((rc = wbuf.alloc(sizeof(double) * (size_t)std::max(lwork, 1), st))) return rc;
+    work = (double*)wbuf.p;
+    if (split) MPPS_CUDA_TRY(cudaMemsetAsync(split, 0, f64e_split_flag_bytes(), st));
+    DevErr* derr = nullptr;
+    if (K > 0) {
+        if ((rc = dev_err_get(&derr))) return rc;
+        if ((rc = dev_err_check(derr, false))) return rc;
+    }
+    auto product = [&](const double* Am, const double* Bm, int cnt, const int* list,
+                       const Epilogue& ep) -> mpps_status {
+        if (K == 0) return launch_gemm_f64(Am, nn, Bm, nn, n, cnt, ep, st, list);
+        mpps_status r1 = launch_slice_rows(Am, nn, n, batch, K, slA, eA, st);
+        if (!r1) r1 = launch_slice_cols(Bm, nn, n, batch, K, slB, eB, cmx, st);
+        if (!r1)
+            r1 = launch_gemm_f64e(K, slA, K, eA, slB, K, eB, n, cnt, batch, ep, derr->d, st, list,
+                                  split);
+        return r1;
+    };
+
+    if ((rc = launch_norm1(a.dev, nn, n, batch, partial, anorm, st))) return rc;
+    std::vector<double> hnorm(batch);
+    MPPS_CUDA_TRY(cudaMemcpyAsync(hnorm.data(), anorm, sizeof(double) * batch,
+                                  cudaMemcpyDeviceToHost, st));
+    MPPS_CUDA_TRY(cudaStreamSynchronize(st));
+    const double theta13 = 5.371920351148152;
+    std::vector<int> sigma(batch, 0);
+    int sig_max = 0;
+    for (int b = 0; b < batch; ++b) {
+        int sg = 0;
+        if (!(hnorm[b] <= theta13)) {     // smallest sigma with ||A|| 2^-sigma <= theta_13
+            if (!std::isfinite(hnorm[b])) sg = 0;
+            else
+                while (ldexp(hnorm[b], -sg) > theta13 && sg < 1000) ++sg;
+        }
+        sigma[b] = sg;
+        sig_max = std::max(sig_max, sg);
+    }
+    if (sig_max > 64) {
+        set_error("expm_pade13: ||A||_1 needs %d squarings (at most 64)", sig_max);
+        return MPPS_EINVAL;
+    }
+    MPPS_CUDA_TRY(cudaMemcpyAsync(d_sigma, sigma.data(), sizeof(int) * batch,
+                                  cudaMemcpyHostToDevice, st));
+    if ((rc = launch_scale_copy(a.dev, nn, X, nn, n, batch, d_sigma, st))) return rc;
+
+    // ---- numerator and denominator from one power chain: with V = even part and
+    // U = X (odd part / X), both polynomials in X^2,  p = V + U,  q = p(-X) = V - U
+    {
+        Epilogue ep = epilogue_plain(X2, nn);
+        if ((rc = product(X, X, batch, nullptr, ep))) return rc;
+    }
+    if ((rc = ps_eval(ce, 6, X2, n, batch, policy, V, nullptr, stream))) return rc;
+    if ((rc = ps_eval(co, 6, X2, n, batch, policy, W, nullptr, stream))) return rc;
+    {
+        Epilogue ep = epilogue_plain(U, nn);
+        if ((rc = product(X, W, batch, nullptr, ep))) return rc;
+    }
+    for (int sgn = 0; sgn < 2; ++sgn) {   // P = V + U, Q = V - U
+        Epilogue ep = epilogue_plain(sgn == 0 ? P : Q, nn);
+        ep.alpha = sgn == 0 ? 1.0 : -1.0;
+        ep.add = V;
+        ep.add_bstride = nn;
+        ep.add_coef = 1.0;
+        if ((rc = launch_combine(n, batch, U, nn, ep, st))) return rc;
+    }
+    // ---- R = q^-1 p.  p and q commute (both polynomials in X), so R^T = (Q^T)^-1 P^T: the
+    // row-major Q and P, read column-major, are Q^T and P^T, and the column-major solution
+    // written over P is R in row-major order
+    for (int b = 0; b < batch; ++b) {
+        double* Qb = Q + (size_t)b * nn;
+        double* Pb = P + (size_t)b * nn;
+        if (S->getrf(sh, n, n, Qb, n, work, ipiv, info) != CUSOLVER_STATUS_SUCCESS ||
+            S->getrs(sh, CUBLAS_OP_N, n, n, Qb, n, ipiv, Pb, n, info) != CUSOLVER_STATUS_SUCCESS) {
+            set_error("expm_pade13: LU solve failed for matrix %d", b);
+            return MPPS_ECUDA;
+        }
+    }
+    // ---- sigma squarings per matrix (index lists), then each result from its buffer
+    std::vector<int> lists((size_t)std::max(sig_max, 1) * batch);
+    std::vector<int> counts(std::max(sig_max, 1), 0);
+    for (int k = 0; k < sig_max; ++k)
+        for (int b = 0; b < batch; ++b)
+            if (sigma[b] > k) lists[(size_t)k * batch + counts[k]++] = b;
+    int* dl = d_lists;
+    DevBuf extra;
+    if ((size_t)sig_max * batch > (size_t)batch * 64) {
+        if ((rc = extra.alloc(sizeof(int) * lists.size(), st))) return rc;
+        dl = (int*)extra.p;
+    }
+    MPPS_CUDA_TRY(cudaMemcpyAsync(dl, lists.data(), sizeof(int) * lists.size(),
+                                  cudaMemcpyHostToDevice, st));
+    double* buf[2] = {P, Rb1};
+    for (int k = 0; k < sig_max; ++k) {
+        Epilogue ep = epilogue_plain(buf[(k + 1) & 1], nn);
+        if ((rc = product(buf[k & 1], buf[k & 1], counts[k], dl + (size_t)k * batch, ep))) return rc;
+    }
+    if ((rc = launch_select_copy(buf[0], buf[1], d_sigma, dOut, n, batch, 0.0, st))) return rc;
+    if (K > 0 && (rc = dev_err_enqueue(derr, st))) return rc;
+    if (!o_dev) {
+        MPPS_CUDA_TRY(cudaMemcpyAsync(out, dOut, elems * sizeof(double), cudaMemcpyDeviceToHost, st));
+        MPPS_CUDA_TRY(cudaStreamSynchronize(st));
+        if (K > 0 && (rc = dev_err_check(derr, true))) return rc;
+    } else {
+        MPPS_CUDA_TRY(cudaStreamSynchronize(st));   // the LU pivots and info live in this call's workspace
+        if (K > 0 && (rc = dev_err_check(derr, true))) return rc;
     }
     return MPPS_OK;
 }

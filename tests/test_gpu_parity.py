@@ -660,6 +660,29 @@ def test_expm_autograd_central_differences(mpps):
         assert abs(fd - grad[i, j]) <= 1e-7 * max(1.0, abs(grad[i, j])), (i, j, fd, grad[i, j])
 
 
+@pytest.mark.parametrize("n,norms", [(16, (0.5, 3.0)), (100, (20.0, 60.0)), (257, (4.0,))])
+@pytest.mark.parametrize("pol", ["fixed", "ns_e"])
+def test_expm_pade13_vs_oracle(mpps, n, norms, pol):
+    """exp by the [13/13] Pade approximant (scaling to theta_13, numerator and denominator
+    from one power chain, LU solve, squarings) against the oracle's exp (Taylor degree 30
+    with its own scaling, exact to double-double level): the same 50 n u 2^sigma bound as
+    the Taylor path (an FP64 numpy model of the algorithm stays below 0.25 n u 2^sigma on
+    these inputs)."""
+    policy = {"fixed": mpps.FIXED, "ns_e": mpps.NS_E}[pol]
+    batch = len(norms)
+    A = inputs.gaussian_batch(batch, n, seed=1300 + n, norm1=list(norms))
+    E = host(mpps.expm_pade(dev(A), policy=policy))
+    theta = 5.371920351148152
+    for b in range(batch):
+        nrm = np.abs(A[b]).sum(axis=0).max()
+        sg = 0
+        while nrm * 2.0 ** -sg > theta:
+            sg += 1
+        eh, el = oracle.expm_ss_dd(A[b], 30, oracle.sigma_for(A[b]))
+        err = oracle.rel_err_1norm(E[b], eh, el)
+        assert err <= 50 * n * U * max(1, 2 ** sg), (b, sg, err)
+
+
 def test_adjoint_fp32_batch_config_shape(mpps):
     """Batch of FP32-stored 128 x 128 matrices, N(0,1)/sqrt(n) entries, Taylor exp m = 18,
     through the autograd Function with emulated products: the gradient agrees with the
