@@ -94,6 +94,8 @@ typedef struct {
                                and let mixed steps use F64E(k') for k' < k as well */
     int variable_s;         /* 1 (mixed modes, s = 0): the variable-s branch of Algorithm 3.1
                                (mpps_choose_s); 0: s = ceil(sqrt(m)) */
+    int adjoint_recompute;  /* 1: the adjoints keep every ceil(sqrt(r))-th Horner iterate and
+                               recompute the others (same products, same result); 0: keep all */
 } mpps_policy;
 
 /* Per-matrix description of what a call did (filled when `rep` is non-NULL). */
@@ -111,7 +113,8 @@ typedef struct {
 } mpps_report;
 
 /* Fill *p with the defaults: MIXED_NS, tol 2^-53, delta 10, s 0, all formats, floor 2,
- * f64_slices 0 (working-precision products on the FP64 pipe), variable_s 0. */
+ * f64_slices 0 (working-precision products on the FP64 pipe), variable_s 0,
+ * adjoint_recompute 0. */
 void mpps_policy_default(mpps_policy* p);
 
 /*

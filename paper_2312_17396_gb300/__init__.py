@@ -59,7 +59,8 @@ class MppsError(RuntimeError):
 class _Policy(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("tol", ctypes.c_double), ("delta", ctypes.c_double),
                 ("s", ctypes.c_int), ("formats", ctypes.c_uint), ("fp64_floor_steps", ctypes.c_int),
-                ("f64_slices", ctypes.c_int), ("variable_s", ctypes.c_int)]
+                ("f64_slices", ctypes.c_int), ("variable_s", ctypes.c_int),
+                ("adjoint_recompute", ctypes.c_int)]
 
 
 class _GroupItem(ctypes.Structure):
@@ -160,6 +161,7 @@ class Policy:
     fp64_floor_steps: int = 2
     f64_slices: int = 0             # 0: FP64 pipe; k: emulate FP64 products with k slices
     variable_s: bool = False        # the variable-s branch of Algorithm 3.1 (mixed modes)
+    adjoint_recompute: bool = False  # adjoints: keep ceil(sqrt(r)) iterates, recompute the rest
 
     def _c(self):
         fm = self.formats
@@ -170,7 +172,7 @@ class Policy:
             fm = mask
         return _Policy(int(self.mode), float(self.tol), float(self.delta), int(self.s),
                        int(fm), int(self.fp64_floor_steps), int(self.f64_slices),
-                       int(bool(self.variable_s)))
+                       int(bool(self.variable_s)), int(bool(self.adjoint_recompute)))
 
 
 FIXED = Policy(mode=FIXED_FP64)

@@ -37,6 +37,7 @@ struct Pol {
     int floor_steps;
     int f64k;   // 0: FP64 pipe; k > 0: working-precision products emulated with k slices
     int var_s;  // variable-s branch of Algorithm 3.1
+    int recompute;  // adjoints: checkpoint the Horner iterates, recompute the rest
 };
 
 static Pol resolve(const mpps_policy* p) {
@@ -52,6 +53,7 @@ static Pol resolve(const mpps_policy* p) {
     r.floor_steps = p->fp64_floor_steps < 0 ? 2 : p->fp64_floor_steps;
     r.f64k = p->f64_slices;
     r.var_s = p->variable_s != 0;
+    r.recompute = p->adjoint_recompute != 0;
     return r;
 }
 
@@ -810,6 +812,7 @@ void mpps_policy_default(mpps_policy* p) {
     p->fp64_floor_steps = 2;
     p->f64_slices = 0;
     p->variable_s = 0;
+    p->adjoint_recompute = 0;
 }
 
 mpps_status mpps_release_workspace(void) {
@@ -1160,6 +1163,15 @@ mpps_status ps_eval_adjoint(const double* coeffs, int m, const double* A, const 
             return MPPS_EINVAL;
         }
         const int K = pol.f64k;      // products on the FP64 pipe (0) or emulated with K slices
+        // Horner iterates P_i kept for the reverse pass: all of them, or (recompute) only
+        // every c-th with c = ceil(sqrt(r)) and the top one, the others recomputed a segment
+        // at a time from the checkpoint above by the same products (so bit for bit the same)
+        const int i_top = fold ? r - 1 : r;   // highest Horner iterate that is a real matrix
+        const bool recompute = pol.recompute && r >= 3;
+        const int cseg = recompute ? ceil_sqrt_int(r) : 1;
+        const int ck_top = r / cseg + 1;                  // slot of the top checkpoint
+        const int seg0 = r / cseg + 2;                    // first segment slot
+        const int nslots = recompute ? seg0 + std::max(2, cseg) : r + 1;
         Arena L;
         double *pw, *xbar, *Pst, *Ybar, *Pbar0, *Pbar1, *Yt, *X1t, *T;
         __nv_bfloat16 *slA = nullptr, *slB = nullptr;
@@ -1169,7 +1181,7 @@ mpps_status ps_eval_adjoint(const double* coeffs, int m, const double* A, const 
         auto lay = [&](Arena& z) {
             pw = z.take<double>((size_t)batch * pw_bs);
             xbar = z.take<double>((size_t)batch * pw_bs);
-            Pst = z.take<double>((size_t)batch * nn * (r + 1));   // P_i at slot i
+            Pst = z.take<double>((size_t)batch * nn * nslots);
             Ybar = z.take<double>(elems);
             Pbar0 = z.take<double>(elems);
             Pbar1 = z.take<double>(elems);
@@ -1192,7 +1204,10 @@ mpps_status ps_eval_adjoint(const double* coeffs, int m, const double* A, const 
         L.off = 0;
         lay(L);
         if (split) MPPS_CUDA_TRY(cudaMemsetAsync(split, 0, f64e_split_flag_bytes(), st));
-        auto P_at = [&](int i) { return Pst + (size_t)i * batch * nn; };
+        auto slotp = [&](int k) { return Pst + (size_t)k * batch * nn; };
+        auto is_ckpt = [&](int j) { return !recompute || j % cseg == 0 || j == i_top; };
+        auto ck_slot = [&](int j) { return !recompute ? j : (j == i_top ? ck_top : j / cseg); };
+        std::vector<double*> loc(r + 1, nullptr);   // where P_j is held now
         DevErr* derr = nullptr;
         if (K > 0) {
             if ((rc = dev_err_get(&derr))) return rc;
@@ -1216,29 +1231,50 @@ mpps_status ps_eval_adjoint(const double* coeffs, int m, const double* A, const 
             if ((rc = product(pw + (long long)(j - 2) * nn, pw_bs, pw, pw_bs, ep))) return rc;
         }
         const double* Y = pw + (long long)(s - 1) * nn;
-        int i_top;   // highest Horner iterate that is a real matrix
+        // P_{i-1} = B_{i-1} + P_i Y into dst
+        auto horner_step = [&](int i, double* dst) -> mpps_status {
+            Epilogue ep = epilogue_plain(dst, nn);
+            ep.nt = s - 1;
+            for (int j = 0; j < s; ++j) ep.coef[j] = coeffs[(i - 1) * s + j];
+            ep.pw = pw; ep.pw_bstride = pw_bs;
+            return product(loc[i], nn, Y, pw_bs, ep);
+        };
+        // where the forward pass puts P_j: its checkpoint slot, else one of two rolling slots
+        auto fwd_dst = [&](int j) { return is_ckpt(j) ? slotp(ck_slot(j)) : slotp(seg0 + (j & 1)); };
+        loc[i_top] = fwd_dst(i_top);
         if (fold) {
-            Epilogue ep = epilogue_plain(P_at(r - 1), nn);
+            Epilogue ep = epilogue_plain(loc[r - 1], nn);
             ep.nt = s - 1;
             for (int j = 0; j < s; ++j) ep.coef[j] = coeffs[(r - 1) * s + j];
             ep.pw = pw; ep.pw_bstride = pw_bs; ep.alpha = coeffs[m];
             if ((rc = launch_combine(n, batch, Y, pw_bs, ep, st))) return rc;
-            i_top = r - 1;
         } else {
-            Epilogue ep = epilogue_plain(P_at(r), nn);
+            Epilogue ep = epilogue_plain(loc[r], nn);
             ep.nt = m - s * r;
             for (int j = 0; j <= ep.nt; ++j) ep.coef[j] = coeffs[s * r + j];
             ep.pw = pw; ep.pw_bstride = pw_bs; ep.alpha = 0.0;
             if ((rc = launch_combine(n, batch, nullptr, 0, ep, st))) return rc;
-            i_top = r;
         }
         for (int i = i_top; i >= 2; --i) {   // P_{i-1} = B_{i-1} + P_i Y (P_0 not needed)
-            Epilogue ep = epilogue_plain(P_at(i - 1), nn);
-            ep.nt = s - 1;
-            for (int j = 0; j < s; ++j) ep.coef[j] = coeffs[(i - 1) * s + j];
-            ep.pw = pw; ep.pw_bstride = pw_bs;
-            if ((rc = product(P_at(i), nn, Y, pw_bs, ep))) return rc;
+            loc[i - 1] = fwd_dst(i - 1);
+            if ((rc = horner_step(i, loc[i - 1]))) return rc;
         }
+        for (int j = 1; j <= r; ++j)
+            if (!is_ckpt(j)) loc[j] = nullptr;   // rolling slots: overwritten
+        // P_i for the reverse pass (ascending i): a missing one is recomputed with the rest of
+        // its segment, P_{k-1} .. P_{i0} from the checkpoint k above
+        auto P_at = [&](int i, mpps_status* err) -> double* {
+            if (loc[i]) return loc[i];
+            const int k = std::min((i / cseg + 1) * cseg, i_top);
+            const int i0 = (i / cseg) * cseg + 1;
+            for (int j = 1; j <= r; ++j)
+                if (!is_ckpt(j)) loc[j] = nullptr;
+            for (int j = k; j > i0; --j) {
+                loc[j - 1] = slotp(seg0 + (j - 1 - i0));
+                if ((*err = horner_step(j, loc[j - 1]))) return nullptr;
+            }
+            return loc[i];
+        };
         // backward
         MPPS_CUDA_TRY(cudaMemsetAsync(xbar, 0, sizeof(double) * batch * pw_bs, st));
         MPPS_CUDA_TRY(cudaMemsetAsync(Ybar, 0, elems * sizeof(double), st));
@@ -1265,7 +1301,9 @@ mpps_status ps_eval_adjoint(const double* coeffs, int m, const double* A, const 
                 break;
             }
             // Ybar += P_i^T Pbar_{i-1}
-            if ((rc = launch_transpose(P_at(i), nn, T, n, batch, st))) return rc;
+            double* Pi = P_at(i, &rc);
+            if (rc) return rc;
+            if ((rc = launch_transpose(Pi, nn, T, n, batch, st))) return rc;
             {
                 Epilogue ep = epilogue_plain(Ybar, nn);
                 ep.add = Ybar; ep.add_bstride = nn; ep.add_coef = 1.0;
@@ -1350,6 +1388,7 @@ mpps_status expm_taylor_ss_adjoint(const double* A, const double* G, int n, int 
     mpps_policy_default(&fpol);
     fpol.mode = MPPS_FIXED_FP64;
     fpol.f64_slices = K;
+    fpol.adjoint_recompute = pol.recompute;
     std::vector<double> c(m + 1);   // b_i = 1/i!, as in expm_taylor_ss
     {
         long double f = 1.0L;

@@ -683,6 +683,29 @@ def test_expm_pade13_vs_oracle(mpps, n, norms, pol):
         assert err <= 50 * n * U * max(1, 2 ** sg), (b, sg, err)
 
 
+@pytest.mark.parametrize("m", [50, 64])
+@pytest.mark.parametrize("k", [0, 8])
+def test_adjoint_recompute_same_bits(mpps, m, k):
+    """Recompute mode keeps every ceil(sqrt(r))-th Horner iterate (and the top one) and
+    recomputes the others a segment at a time with the same products: the gradient is the
+    stored mode's, bit for bit.  m = 50 (s = 8, r = 6) and m = 64 (r = 8, s | m, top
+    iterate r - 1), batch 2; also through scaling and squaring."""
+    n = 64
+    A = inputs.gaussian_batch(2, n, seed=m + k, norm1=[0.7, 3.0])
+    G = np.random.default_rng(m).standard_normal((2, n, n))
+    coef = mpps.taylor_exp_coeffs(m)
+    keep = mpps.Policy(mode=mpps.FIXED_FP64, f64_slices=k)
+    rec = mpps.Policy(mode=mpps.FIXED_FP64, f64_slices=k, adjoint_recompute=True)
+    g0 = host(mpps.ps_eval_adjoint(coef, dev(A), dev(G), policy=keep))
+    g1 = host(mpps.ps_eval_adjoint(coef, dev(A), dev(G), policy=rec))
+    assert np.array_equal(g0, g1)
+    gh, gl = oracle.adjoint_dd(oracle.taylor_exp_rational(m), A[0], G[0])
+    assert oracle.norm1(g1[0] - gh - gl) / oracle.norm1(gh) <= 100 * n * U
+    e0 = host(mpps.expm_adjoint(dev(A), dev(G), m=m, policy=keep))
+    e1 = host(mpps.expm_adjoint(dev(A), dev(G), m=m, policy=rec))
+    assert np.array_equal(e0, e1)
+
+
 def test_adjoint_fp32_batch_config_shape(mpps):
     """Batch of FP32-stored 128 x 128 matrices, N(0,1)/sqrt(n) entries, Taylor exp m = 18,
     through the autograd Function with emulated products: the gradient agrees with the
