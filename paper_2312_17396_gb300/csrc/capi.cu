@@ -1550,6 +1550,7 @@ struct Solver {
     cusolverDnHandle_t handle[64] = {};
 };
 std::mutex g_solvermu;
+std::mutex g_solvecall;   // one handle per device: its stream is set for each call's solves
 Solver g_solver;
 
 // The solver library is opened only by the Pade entry point, so that the rest of the
@@ -1753,13 +1754,22 @@ mpps_status expm_pade13(const double* A, int n, int batch, const mpps_policy* po
     // ---- R = q^-1 p.  p and q commute (both polynomials in X), so R^T = (Q^T)^-1 P^T: the
     // row-major Q and P, read column-major, are Q^T and P^T, and the column-major solution
     // written over P is R in row-major order
-    for (int b = 0; b < batch; ++b) {
-        double* Qb = Q + (size_t)b * nn;
-        double* Pb = P + (size_t)b * nn;
-        if (S->getrf(sh, n, n, Qb, n, work, ipiv, info) != CUSOLVER_STATUS_SUCCESS ||
-            S->getrs(sh, CUBLAS_OP_N, n, n, Qb, n, ipiv, Pb, n, info) != CUSOLVER_STATUS_SUCCESS) {
-            set_error("expm_pade13: LU solve failed for matrix %d", b);
+    // (q_13 has no zeros in the disc |x| <= theta_13, so q(X) is nonsingular there and the
+    // factorisation's info word is not read back)
+    {
+        std::lock_guard<std::mutex> lk(g_solvecall);
+        if (S->set_stream(sh, st) != CUSOLVER_STATUS_SUCCESS) {
+            set_error("cusolverDnSetStream failed");
             return MPPS_ECUDA;
+        }
+        for (int b = 0; b < batch; ++b) {
+            double* Qb = Q + (size_t)b * nn;
+            double* Pb = P + (size_t)b * nn;
+            if (S->getrf(sh, n, n, Qb, n, work, ipiv, info) != CUSOLVER_STATUS_SUCCESS ||
+                S->getrs(sh, CUBLAS_OP_N, n, n, Qb, n, ipiv, Pb, n, info) != CUSOLVER_STATUS_SUCCESS) {
+                set_error("expm_pade13: LU solve failed for matrix %d", b);
+                return MPPS_ECUDA;
+            }
         }
     }
     // ---- sigma squarings per matrix (index lists), then each result from its buffer
