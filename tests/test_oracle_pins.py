@@ -395,6 +395,39 @@ def test_expm_ss_adjoint_central_differences():
         assert abs(fd - gh[i, j]) < 1e-8 * max(1.0, abs(gh[i, j]))
 
 
+def test_expm_ss_adjoint_pin_catches_planted_mistakes():
+    """The block-identity pin above separates the chain rule from plausible slips: the same
+    chain in plain double passes it, and the chain with the transposes dropped from the
+    squarings' reverse step, or without the final 2^-sigma, fails it."""
+    n, m, sigma = 6, 12, 2
+    A = RNG.standard_normal((n, n)) * 0.5
+    G = RNG.standard_normal((n, n))
+    c = oracle.taylor_exp_rational(m)
+    Mt = np.zeros((2 * n, 2 * n))
+    Mt[:n, :n] = A.T; Mt[n:, n:] = A.T; Mt[:n, n:] = G
+    th, tl = oracle.expm_ss_dd(Mt, m, sigma)
+    ref = th[:n, n:] + tl[:n, n:]
+
+    def chain(transpose=True, scale=True):
+        X = np.ldexp(A, -sigma)
+        ph, pl, _ = oracle.ps_dd(c, X)
+        S = [ph + pl]
+        for _ in range(sigma - 1):
+            S.append(S[-1] @ S[-1])
+        Sb = G.copy()
+        for k in range(sigma - 1, -1, -1):
+            T = S[k].T if transpose else S[k]
+            Sb = Sb @ T + T @ Sb
+        dh, dl = oracle.adjoint_dd(c, X, Sb)
+        D = dh + dl
+        return np.ldexp(D, -sigma) if scale else D
+
+    rel = lambda D: np.max(np.abs(D - ref)) / np.max(np.abs(ref))
+    assert rel(chain()) < 1e-13
+    assert rel(chain(transpose=False)) > 1e-3
+    assert rel(chain(scale=False)) > 1e-1
+
+
 def test_choose_s_variable_branch_by_hand():
     """Algorithm 3.1's variable-s loop on norms worked out by hand (m = 30, s0 = 6)."""
     # ||X|| = 3 > 6/e: the branch is not taken
