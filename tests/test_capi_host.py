@@ -134,3 +134,31 @@ def test_autotune_table_host_calls(mpps):
     mpps.autotune(False)
     mpps.autotune_clear()
     assert mpps.autotune_entries() == []
+
+
+def test_new_bindings_validate_shapes_before_any_gpu_work(mpps):
+    """Shape errors of the Pade, adjoint and variable-s bindings are raised on the host."""
+    A = np.zeros((2, 4, 4)); G = np.zeros((2, 5, 5))
+    with pytest.raises(ValueError):
+        mpps.expm_adjoint(A, G)
+    with pytest.raises(ValueError):
+        mpps.expm_pade(np.zeros((3, 4)))
+    with pytest.raises(ValueError):
+        mpps.expm_pade(A, out=np.zeros((1, 4, 4)))
+    with pytest.raises(ValueError):
+        mpps.choose_s(30, 0.5, [1.0, 2.0], [1.0])
+    # m < 1 is rejected by the C rule itself
+    assert mpps.choose_s(0, 0.5, [1.0], [1.0]) == -1
+
+
+def test_policy_struct_round_trip(mpps):
+    """Every Policy field reaches the C struct in order (the struct has no padding surprises:
+    its fields are read back through ctypes)."""
+    p = mpps.Policy(mode=mpps.MIXED_PAPER, tol=1e-12, delta=7.0, s=5, formats=["fp64", "bf16"],
+                    fp64_floor_steps=3, f64_slices=9, variable_s=True, adjoint_recompute=True)
+    c = p._c()
+    assert (c.mode, c.tol, c.delta, c.s, c.formats, c.fp64_floor_steps, c.f64_slices,
+            c.variable_s, c.adjoint_recompute) == (mpps.MIXED_PAPER, 1e-12, 7.0, 5, 0b1001, 3, 9, 1, 1)
+    d = mpps._Policy()
+    mpps.lib().mpps_policy_default(d)
+    assert (d.variable_s, d.adjoint_recompute, d.f64_slices, d.s) == (0, 0, 0, 0)
