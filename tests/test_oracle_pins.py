@@ -560,3 +560,134 @@ def test_plan_degenerate():
     assert F.plan(0, 8, [1.0], 0.0)["r"] == 0
     p1 = F.plan(1, 8, [1.0, 1.0], 1.0)      # s = 1, r = 1, folded (b_1 I)
     assert (p1["s"], p1["r"], p1["fold"]) == (1, 1, True)
+
+
+# --------------------------------------------------------------------------------
+# 12. the plain-double oracle (the timed CPU baseline): exact on dyadic inputs, and within
+#     the rounding-error bound of Algorithm 2.1 (Lemma 2.2 / Theorem 2.1 with every u_i = u)
+#     of the double-double oracle
+# --------------------------------------------------------------------------------
+def _ps_d_bound(coefs, X, s):
+    """Normwise form of the fixed-precision bound: the computed P differs from p(X) by at
+    most (s - 1 + r + 1) n u sum_k |b_k| || |X| ||_1^k (first order in u)."""
+    m = len(coefs) - 1
+    r = m // s
+    nx = oracle.norm1(np.abs(X))
+    tail = sum(abs(float(c)) * nx ** k for k, c in enumerate(coefs))
+    return (s + r) * X.shape[0] * 2.0 ** -53 * tail
+
+
+@pytest.mark.parametrize("n,m", [(3, 9), (4, 16), (2, 7)])
+def test_ps_d_exact_on_dyadic_inputs(n, m):
+    # dyadic X and coefficients 2^-k: every product and sum of Algorithm 2.1 is exact in
+    # double, so the plain-double result equals the exact rational value bit for bit
+    Xf, Xq = dyadic_matrix(n, denom=2, lo=-1, hi=2)
+    coefs = [Fraction(1, 2 ** k) for k in range(m + 1)]
+    exact = fr_poly(coefs, Xq)
+    for s in (0, 1, 2, m):
+        P, _ = oracle.ps_d([float(c) for c in coefs], Xf, s=s)
+        assert all(Fraction(float(P[i, j])) == exact[i][j] for i in range(n) for j in range(n)), s
+
+
+@pytest.mark.parametrize("n,m", [(5, 7), (33, 16), (64, 30)])
+def test_ps_d_within_bound_of_dd(n, m):
+    # order-one signed coefficients so that every term of p carries weight
+    rng = np.random.default_rng(900 + n + m)
+    coefs = list(rng.standard_normal(m + 1) / np.arange(1, m + 2))
+    X = rng.standard_normal((n, n))
+    X /= oracle.norm1(X)
+    s = oracle.ceil_sqrt(m)
+    ph, pl, _ = oracle.ps_dd(coefs, X)
+    P, cnt = oracle.ps_d(coefs, X)
+    assert cnt == s - 1 + m // s
+    err = oracle.norm1(P - ph - pl)
+    assert err <= _ps_d_bound(coefs, X, s)
+    assert err > 0.0          # plain double does round (the comparison is not vacuous)
+
+
+def test_ps_d_bound_catches_planted_mistakes():
+    """Oracle-side slips in a plain-double PS (a dropped block coefficient, one Horner
+    step too few) leave the bound by more than two orders of magnitude."""
+    n, m = 33, 16
+    rng = np.random.default_rng(77)
+    coefs = list(rng.standard_normal(m + 1) / np.arange(1, m + 2))
+    X = rng.standard_normal((n, n))
+    X /= oracle.norm1(X)
+    ph, pl, _ = oracle.ps_dd(coefs, X)
+    bound = _ps_d_bound(coefs, X, 4)
+    dropped = list(coefs); dropped[9] = 0.0
+    P1, _ = oracle.ps_d(dropped, X)
+    assert oracle.norm1(P1 - ph - pl) > 100 * bound
+    short = coefs[:-4]                      # the top block B_r missing
+    P2, _ = oracle.ps_d(short, X)
+    assert oracle.norm1(P2 - ph - pl) > 100 * bound
+
+
+@pytest.mark.parametrize("n,norm", [(8, 0.5), (24, 4.0), (40, 32.0)])
+def test_expm_ss_d_within_bound_of_dd(n, norm):
+    A = RNG.standard_normal((n, n))
+    A *= norm / oracle.norm1(A)
+    sg = oracle.sigma_for(A)
+    eh, el = oracle.expm_ss_dd(A, 30, sg)
+    E = oracle.expm_ss_d(A, 30, sg)
+    err = oracle.rel_err_1norm(E, eh, el)
+    # the polynomial's bound, amplified by 2^sigma through the squarings (Section 3.2)
+    assert err <= 50 * n * 2.0 ** -53 * 2 ** sg
+    # the result of one squaring too many, p(2^-sigma A)^(2^(sigma+1)) = E^2, and of one too
+    # few, p(2^-sigma A)^(2^(sigma-1)) (the oracle run on A/2 with sigma-1), are far outside it
+    assert oracle.rel_err_1norm(E @ E, eh, el) > 1e-3
+    if sg > 0:
+        assert oracle.rel_err_1norm(oracle.expm_ss_d(A / 2, 30, sg - 1), eh, el) > 1e-3
+
+
+# --------------------------------------------------------------------------------
+# 13. the cosine and Pade coefficient sequences against the functions they approximate
+# --------------------------------------------------------------------------------
+@pytest.mark.parametrize("m", [8, 16])
+def test_cos_taylor_coefficients_reproduce_cos(m):
+    # c_m(B) with B = D^2, D diagonal: diag(sum_k (-1)^k d^(2k) / (2k)!) = diag(cos d) up to
+    # the truncation term |d|^(2m+2) / (2m+2)!
+    d = np.linspace(-4.0, 4.0, 13)
+    B = np.diag(d * d)
+    ph, pl, _ = oracle.ps_dd(oracle.cos_taylor_rational(m), B)
+    for i, di in enumerate(d):
+        trunc = abs(di) ** (2 * m + 2) / math.factorial(2 * m + 2)
+        assert abs(ph[i, i] + pl[i, i] - math.cos(di)) <= trunc + 4e-16, (m, di)
+    off = ph - np.diag(np.diag(ph))
+    assert np.all(off == 0.0)
+
+
+def test_cos_pin_catches_planted_mistake():
+    # odd factorials in the denominators (the sine's sequence) do not reproduce cos
+    wrong = [Fraction((-1) ** k, math.factorial(2 * k + 1)) for k in range(17)]
+    B = np.diag([1.0, 2.0, 3.0])
+    ph, pl, _ = oracle.ps_dd(wrong, B)
+    assert max(abs(ph[i, i] - math.cos(math.sqrt(B[i, i]))) for i in range(3)) > 1e-2
+
+
+def test_pade_coefficients_approximate_exp():
+    # the [13/13] Pade approximant p(x)/q(x) agrees with e^x to order x^27: at |x| <= 1/2 the
+    # difference is far below an FP64 ulp; p(-x) is q(x) exactly
+    num, den = oracle.pade_exp_num_rational(13), oracle.pade_exp_den_rational(13)
+    assert all(d == n * (-1) ** j for j, (n, d) in enumerate(zip(num, den)))
+    for x in (Fraction(1, 2), Fraction(-1, 3), Fraction(1, 8)):
+        p = sum(c * x ** j for j, c in enumerate(num))
+        q = sum(c * x ** j for j, c in enumerate(den))
+        assert abs(float(p / q) - math.exp(float(x))) <= 2.0 ** -52 * math.exp(float(x))
+
+
+# --------------------------------------------------------------------------------
+# 14. the 1-norm: maximum column sum, on a non-square matrix whose row and column maxima
+#     differ (a row/column swap gives 6 instead of 7)
+# --------------------------------------------------------------------------------
+def test_norm1_hand_worked_3x4():
+    M = np.array([[1.0, -2.0, 0.0, 3.0],
+                  [4.0, 0.0, -1.0, 0.0],
+                  [0.0, 5.0, 0.0, -1.0]])
+    # column sums of |M|: 5, 7, 1, 4 ; row sums: 6, 5, 6
+    assert oracle.norm1(M) == 7.0
+    assert oracle.norm1(M.T) == 6.0
+    assert oracle.norm1(np.array([[-3.0, 2.0, 1.0]])) == 3.0      # one row: max |entry|
+    assert oracle.norm1(np.array([[-3.0], [2.0], [1.0]])) == 6.0  # one column: its sum
+    R = RNG.standard_normal((7, 5))
+    assert oracle.norm1(R) == np.abs(R).sum(axis=0).max()
