@@ -12,6 +12,7 @@
 #include <dlfcn.h>
 
 #include <algorithm>
+#include <initializer_list>
 #include <mutex>
 #include <vector>
 
@@ -270,6 +271,27 @@ static bool is_device_ptr(const void* p) {
         return false;
     }
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Every kernel of a call runs on the current device, so a device pointer that lives on
+// another GPU would make them touch that GPU's memory: rejected before any work.
+static mpps_status check_same_device(const char* fn, std::initializer_list<const void*> ptrs) {
+    int cur = 0;
+    MPPS_CUDA_TRY(cudaGetDevice(&cur));
+    for (const void* p : ptrs) {
+        if (!p) continue;
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (a.type == cudaMemoryTypeDevice && a.device != cur) {
+            set_error("%s: a matrix pointer lives on device %d but device %d is current", fn,
+                      a.device, cur);
+            return MPPS_EINVAL;
+        }
+    }
+    return MPPS_OK;
 }
 
 static int low_target_exp(int f) { return f == MPPS_FMT_FP8 ? 8 : 0; }
@@ -874,6 +896,7 @@ static mpps_status run_eval(const double* coeffs, int m, const double* A, int n,
         set_error("invalid argument: null matrix pointer");
         return MPPS_EINVAL;
     }
+    if ((rc = check_same_device(expm ? "expm_taylor_ss" : "ps_eval", {A, out}))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t elems = (size_t)batch * n * n;
     Staged a;
@@ -938,6 +961,8 @@ mpps_status expm_taylor_ss_grouped(const mpps_group_item* items, int count,
                       "required)", i, items[i].n, items[i].m);
             return MPPS_EINVAL;
         }
+        mpps_status rc = check_same_device("expm_taylor_ss_grouped", {items[i].A, items[i].out});
+        if (rc) return rc;
     }
     cudaStream_t st = (cudaStream_t)stream;
     Pol P = resolve(policy);
@@ -1005,6 +1030,7 @@ mpps_status mpps_matmul(const double* A, const double* B, double* C, int n, int 
         set_error("mpps_matmul: null matrix pointer");
         return MPPS_EINVAL;
     }
+    if ((rc = check_same_device("mpps_matmul", {A, B, C}))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     const long long nn = (long long)n * n;
     const size_t elems = (size_t)batch * nn;
@@ -1137,6 +1163,7 @@ mpps_status ps_eval_adjoint(const double* coeffs, int m, const double* A, const 
         set_error("ps_eval_adjoint: null matrix pointer");
         return MPPS_EINVAL;
     }
+    if ((rc = check_same_device("ps_eval_adjoint", {A, G, gradA}))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     const long long nn = (long long)n * n;
     const size_t elems = (size_t)batch * nn;
@@ -1376,6 +1403,7 @@ mpps_status expm_taylor_ss_adjoint(const double* A, const double* G, int n, int 
         set_error("expm_taylor_ss_adjoint: null matrix pointer");
         return MPPS_EINVAL;
     }
+    if ((rc = check_same_device("expm_taylor_ss_adjoint", {A, G, gradA}))) return rc;
     const Pol pol = resolve(policy);
     if (pol.f64k < 0 || pol.f64k > MPPS_F64E_MAX_SLICES) {
         set_error("f64_slices=%d outside 0..%d", pol.f64k, MPPS_F64E_MAX_SLICES);
@@ -1609,6 +1637,7 @@ mpps_status expm_pade13(const double* A, int n, int batch, const mpps_policy* po
         set_error("expm_pade13: null matrix pointer");
         return MPPS_EINVAL;
     }
+    if ((rc = check_same_device("expm_pade13", {A, out}))) return rc;
     const Pol pol = resolve(policy);
     if (pol.f64k < 0 || pol.f64k > MPPS_F64E_MAX_SLICES) {
         set_error("f64_slices=%d outside 0..%d", pol.f64k, MPPS_F64E_MAX_SLICES);
@@ -1715,11 +1744,12 @@ mpps_status expm_pade13(const double* A, int n, int batch, const mpps_policy* po
     int sig_max = 0;
     for (int b = 0; b < batch; ++b) {
         int sg = 0;
-        if (!(hnorm[b] <= theta13)) {     // smallest sigma with ||A|| 2^-sigma <= theta_13
-            if (!std::isfinite(hnorm[b])) sg = 0;
-            else
-                while (ldexp(hnorm[b], -sg) > theta13 && sg < 1000) ++sg;
+        if (!std::isfinite(hnorm[b])) {   // no sigma brings it into range; the solve would
+            set_error("expm_pade13: ||A||_1 of matrix %d is not finite", b);   // be garbage
+            return MPPS_EINVAL;
         }
+        if (!(hnorm[b] <= theta13))       // smallest sigma with ||A|| 2^-sigma <= theta_13
+            while (ldexp(hnorm[b], -sg) > theta13 && sg < 1000) ++sg;
         sigma[b] = sg;
         sig_max = std::max(sig_max, sg);
     }

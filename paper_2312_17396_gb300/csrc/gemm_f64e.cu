@@ -1023,7 +1023,9 @@ mpps_status launch_k(int dev, int grid, const CUtensorMap& ta, const CUtensorMap
     // split K only for the slice counts of working-precision products (7..9); the split
     // kernel is a separate instantiation so that the whole-tile kernel keeps its code
     constexpr bool kSplit = K >= kMinSplitSlices;
+    static std::mutex attr_mu;
     static bool attr_done[64] = {false};
+    std::unique_lock<std::mutex> attr_lk(attr_mu);
     if (!attr_done[dev]) {
         MPPS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_f64e<K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            smem));
@@ -1032,6 +1034,7 @@ mpps_status launch_k(int dev, int grid, const CUtensorMap& ta, const CUtensorMap
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         attr_done[dev] = true;
     }
+    attr_lk.unlock();
     if (kSplit && sp.U > 0)
         MPPS_CUDA_TRY(launch_pdl(k_gemm_f64e<K, kSplit>, dim3(grid), dim3(THREADS), smem, st, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, bidx, sp));
     else

@@ -290,11 +290,22 @@ mpps_status launch_fmt(const void* A_hi, const void* A_lo, const void* Bt_hi, co
         return MPPS_ECUDA;
     }
     constexpr int smem = smem_bytes<FMT>();
-    static bool attr_set = false;
-    if (!attr_set) {
-        MPPS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<FMT, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           smem));
-        attr_set = true;
+    // the attribute is a property of the kernel on the current device: set once per device
+    static std::mutex attr_mu;
+    static bool attr_set[64] = {false};
+    {
+        int dev = 0;
+        MPPS_CUDA_TRY(cudaGetDevice(&dev));
+        if (dev < 0 || dev >= 64) {
+            set_error("device index %d out of range", dev);
+            return MPPS_ENOTSUP;
+        }
+        std::lock_guard<std::mutex> lk(attr_mu);
+        if (!attr_set[dev]) {
+            MPPS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<FMT, TN>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            attr_set[dev] = true;
+        }
     }
     dim3 grid((n + TN - 1) / TN, (n + TM - 1) / TM, batch);
     ProfScope prof(MPPS_PROF_GEMM_TC, st,

@@ -44,13 +44,21 @@ mpps_status scratch_address(unsigned char** out) {
     return MPPS_OK;
 }
 
+// Device (or managed) memory that the current device's kernels may touch: a device pointer
+// of another GPU is refused, since the kernels and the scratch address belong to this one.
 bool on_device(const void* p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice && a.device == cur;
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }

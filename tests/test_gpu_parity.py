@@ -5,9 +5,12 @@ Tolerances
   bound used throughout; Section 3.4 reports errors of order r n u).
 * Low-precision products: normwise |C - AB| <= k u_F |A||B| with u_F the format's unit
   roundoff, plus exactness on integer inputs that every format represents exactly.
-* Mixed PS: the same 50 n 2^-53 bound, and within 2x of the fixed-FP64 error up to an
-  absolute floor of n u (both are measured against the double-double oracle).
+* Mixed PS: the same 50 n 2^-53 bound, and within 2x of the fixed-FP64 error up to a
+  floor of 4 ulps of ||P|| (4 u relative), both measured against the double-double oracle.
+  The floor only covers inputs on which the fixed path happens to round almost exactly.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -18,6 +21,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 U = 2.0 ** -53
+FLOOR = 4 * U   # "mixed within 2x of fixed" floor: a few ulps of ||P||
 
 
 @pytest.fixture(scope="module")
@@ -115,7 +119,7 @@ def test_ps_eval_mixed_vs_fixed(mpps, n, norm):
         Pm, rep = mpps.ps_eval(coef, dev(A), policy=pol, report=True)
         em = oracle.rel_err_1norm(host(Pm), ph, pl)
         assert em <= 50 * n * U
-        assert em <= 2 * ef + n * U, (pol.mode, em, ef, rep[0]["fmt"])
+        assert em <= 2 * ef + FLOOR, (pol.mode, em, ef, rep[0]["fmt"])
 
 
 @pytest.mark.parametrize("n", [64, 130, 257])
@@ -265,7 +269,7 @@ def test_expm_vs_oracle(mpps, n, norm):
     for pol in (mpps.PAPER, mpps.NS):
         Em = host(mpps.expm(dev(A), m=30, policy=pol))
         em = oracle.rel_err_1norm(Em, eh, el)
-        assert em <= tol and em <= 2 * ef + n * U * 2 ** sg
+        assert em <= tol and em <= 2 * ef + FLOOR, (pol.mode, em, ef)
 
 
 def test_expm_batch_mixed_sigma(mpps):
@@ -337,10 +341,17 @@ def test_expm_n1024_sampled_columns(mpps, norm):
         V[j, t] = 1.0
     wh, wl = oracle.ps_apply_dd(oracle.taylor_exp_rational(30), X, V, reps=2 ** sg)
     ref_norm = np.abs(wh).sum(axis=0)
-    for pol in (mpps.FIXED, mpps.NS, mpps.PAPER, mpps.FIXED_E, mpps.NS_E):
+    # the benchmarked mixed policy: emulated working precision, FP64/3xBF16/TF32/BF16 ladder
+    c2 = dataclasses.replace(mpps.NS_E, formats=("fp64", "bf16x3", "tf32", "bf16"))
+    errs = {}
+    for name, pol in (("fixed", mpps.FIXED), ("ns", mpps.NS), ("paper", mpps.PAPER),
+                      ("fixed_e", mpps.FIXED_E), ("ns_e", mpps.NS_E), ("c2", c2)):
         E = host(mpps.expm(dev(A), m=30, policy=pol))
         err = np.abs(E[:, cols] - wh - wl).sum(axis=0) / ref_norm
-        assert np.all(err <= 50 * n * U * max(1, 2 ** sg)), (pol.mode, err)
+        assert np.all(err <= 50 * n * U * max(1, 2 ** sg)), (name, err)
+        errs[name] = err
+    for name in ("ns", "paper", "ns_e", "c2"):
+        assert np.all(errs[name] <= 2 * errs["fixed"] + FLOOR), (name, errs[name], errs["fixed"])
 
 
 # ------------------------------------------------------------------------------------
@@ -495,7 +506,7 @@ def test_ps_eval_emulated_vs_oracle(mpps, n):
         P, rep = mpps.ps_eval(coef, dev(A), policy=pol, report=True)
         e = oracle.rel_err_1norm(host(P), ph, pl)
         assert e <= 50 * n * U, (pol.mode, e, rep[0]["fmt"])
-        assert e <= 2 * ef + n * U, (pol.mode, e, ef, rep[0]["fmt"])
+        assert e <= 2 * ef + FLOOR, (pol.mode, e, ef, rep[0]["fmt"])
 
 
 @pytest.mark.parametrize("norm", [0.5, 4.0, 32.0])
@@ -508,7 +519,7 @@ def test_expm_emulated_vs_oracle(mpps, norm):
     for pol in (mpps.FIXED_E, mpps.NS_E, mpps.PAPER_E):
         E = host(mpps.expm(dev(A), policy=pol))
         e = oracle.rel_err_1norm(E, eh, el)
-        assert e <= 50 * n * U * max(1, 2 ** sg) and e <= 2 * ef + n * U * 2 ** sg, (pol.mode, e, ef)
+        assert e <= 50 * n * U * max(1, 2 ** sg) and e <= 2 * ef + FLOOR, (pol.mode, e, ef)
 
 
 def test_expm_emulated_batch_mixed_sigma(mpps):
