@@ -194,16 +194,71 @@ mpps_status expm_taylor_ss_grouped(const mpps_group_item* items, int count,
 /*
  * Gradient of f(A) = <G, p_m(A)> = sum_ij G_ij p_m(A)_ij with respect to A, i.e. the
  * Frechet derivative L_p(A^T, G) (the paper states no adjoint; this is the derivative of
- * the PS evaluation, computed by reverse mode through its steps, every product in the
- * working precision).
+ * the PS evaluation of Algorithm 2.1 / 4.1, computed by reverse mode through its steps):
+ *   forward: the powers X_2..X_s and the Horner iterates P_r..P_1 under `policy` (eq. (2.8));
+ *   reverse: Pbar_0 = G; for i = 1..r: Ybar += P_i^T Pbar_{i-1}, Pbar_i = Pbar_{i-1} Y^T,
+ *            Xbar_j += b_{(i-1)s+j} Pbar_{i-1};  then Xbar_s += Ybar and the power chain
+ *            Xbar_{j-1} += Xbar_j X^T, Xbar_1 += X_{j-1}^T Xbar_j (j = s..2); gradA = Xbar_1.
+ * The two products of reverse step i run in the format the forward rule of each matrix picks
+ * for u_i / d, d = m / min(1, ||X||_1) (the high-order blocks weigh up to m/||X|| times more
+ * in the gradient than in p(X)), the batch taking the most precise; the power chain runs in
+ * the working precision.  FIXED_FP64 keeps every product in the working precision.
+ * Equivalent to ps_eval_forward_tape into a private tape followed by ps_eval_adjoint_tape.
  *   coeffs : host, m+1 doubles.   A, G : batch x n x n (host or device).
- *   policy : NULL or a policy whose f64_slices selects the products: 0 = FP64 pipe,
- *            k = emulated with k exact bf16 slices (MPPS_FMT_F64E(k)); other fields unused.
+ *   policy : NULL -> defaults; f64_slices selects the working-precision products (0 = FP64
+ *            pipe, k = MPPS_FMT_F64E(k)); adjoint_recompute keeps ceil(sqrt(r)) iterates.
  *   gradA  : batch x n x n output (host or device).
+ * Synchronises `stream` (the forward plans on the host; the reverse pass reads the tape's
+ * header).
  */
 mpps_status ps_eval_adjoint(const double* coeffs, int m, const double* A, const double* G,
                             int n, int batch, const mpps_policy* policy, double* gradA,
                             void* stream);
+
+/* Element type of the matrices of the tape entry points: FP64, or FP32 storage (evaluated
+ * in FP64: inputs widened exactly, results rounded to nearest FP32). */
+#define MPPS_STORAGE_F64 0
+#define MPPS_STORAGE_F32 1
+
+/* Host planner of the reverse pass (no GPU work): mpps_plan with every u_i of eq. (2.8)
+ * divided by d = m / min(1, normX) before nu and the formats are chosen (see
+ * ps_eval_adjoint).  normX = ||X||_1.  Errors as mpps_plan. */
+mpps_status mpps_plan_adjoint(int m, int n, const double* normB, double normY, double normX,
+                              const mpps_policy* policy, mpps_report* out);
+
+/* Bytes of the tape of ps_eval_forward_tape for this call shape and policy (s and
+ * adjoint_recompute fix its layout): the power table, the kept Horner iterates and a header
+ * with the formats of both passes.  0 for invalid arguments (see mpps_last_error). */
+size_t ps_eval_tape_bytes(int m, int n, int batch, const mpps_policy* policy);
+
+/*
+ * p_m(A) as in ps_eval, keeping what the reverse pass needs in `tape` (caller-owned device
+ * memory of at least ps_eval_tape_bytes(m, n, batch, policy) bytes): the powers, the Horner
+ * iterates (all, or with adjoint_recompute every ceil(sqrt(r))-th and the top one) and the
+ * planned formats.  policy.variable_s is ignored (s = policy.s or ceil(sqrt(m))).
+ *   A, out  : batch x n x n device matrices of `storage` (MPPS_STORAGE_F64 or _F32).
+ * Synchronises `stream` once (the planner reads the block norms).
+ */
+mpps_status ps_eval_forward_tape(const double* coeffs, int m, const void* A, int storage, int n,
+                                 int batch, const mpps_policy* policy, void* out, void* tape,
+                                 size_t tape_bytes, void* stream);
+
+/*
+ * Gradient of <G, p_m(A)> from the tape of an earlier ps_eval_forward_tape call with the
+ * same coeffs, m, storage, n, batch and policy (checked against the tape's header:
+ * MPPS_EINVAL if they differ).  The tape is read (in recompute mode its rolling slots are
+ * overwritten, so a tape serves one reverse pass at a time).  G, gradA: batch x n x n device
+ * matrices of `storage`.  Synchronises `stream` (reads the tape's header).
+ */
+mpps_status ps_eval_adjoint_tape(const double* coeffs, int m, const void* tape, size_t tape_bytes,
+                                 const void* G, int storage, int n, int batch,
+                                 const mpps_policy* policy, void* gradA, void* stream);
+
+/* ps_eval_adjoint for FP32-stored matrices (device pointers only): A and G widened exactly,
+ * both passes in FP64 under `policy`, the gradient rounded to FP32. */
+mpps_status ps_eval_adjoint_f32(const double* coeffs, int m, const float* A, const float* G,
+                                int n, int batch, const mpps_policy* policy, float* gradA,
+                                void* stream);
 
 /*
  * exp(A) by the [13/13] Pade approximant r = q^-1 p with scaling and squaring (the Pade
@@ -230,11 +285,12 @@ mpps_status expm_pade13(const double* A, int n, int batch, const mpps_policy* po
  *   S_0 = p_m(X), X = 2^-sigma A;  S_{k+1} = S_k^2;
  *   Sbar_sigma = G;  Sbar_k = Sbar_{k+1} S_k^T + S_k^T Sbar_{k+1};
  *   gradA = 2^-sigma L_p(X^T, Sbar_0).
- * The squarings S_0..S_{sigma-1} are stored (sigma n^2 doubles per matrix).
+ * The squarings S_0..S_{sigma-1} are stored (sigma n^2 doubles per matrix), and the
+ * polynomial's powers and iterates on a tape as in ps_eval_forward_tape.
  *   A, G   : batch x n x n (host or device).     m : Taylor degree (0 -> 30).
- *   policy : NULL or a policy whose f64_slices selects the products (0 = FP64 pipe, k =
- *            emulated with k exact bf16 slices); every product, the forward polynomial
- *            included, is in that working precision; other fields unused.
+ *   policy : NULL -> defaults.  The polynomial and its reverse pass follow the policy as in
+ *            ps_eval_adjoint; the squarings and their reverse pass run in its working
+ *            precision (f64_slices: 0 = FP64 pipe, k = emulated).
  *   gradA  : batch x n x n output (host or device).
  * Synchronises `stream` (sigma is read back; the forward polynomial plans on the host).
  */

@@ -350,9 +350,18 @@ def FMT_F64E(k):
     return 16 + k
 
 
+def adjoint_divisor(m: int, normX: float) -> float:
+    """Tightening of eq. (2.8) for the reverse pass (the paper states no adjoint; this is the
+    reading used): the gradient of b_k X^k is a sum of k products X^j E X^(k-1-j), so the
+    blocks of degree up to m weigh up to m / ||X|| times more in the gradient than in p(X).
+    Divisor d = m / min(1, ||X||_1) (||X||_1 = 0 or >= 1 counts as 1)."""
+    x = normX if 0.0 < normX < 1.0 else 1.0
+    return m / x
+
+
 def plan(m: int, n: int, norms, normY: float, mode: int = MODE_PAPER, tol: float = 2.0 ** -53,
          delta: float = 10.0, s: int = 0, formats: int = 0x1F, floor_steps: int = 2,
-         f64_slices: int = 0):
+         f64_slices: int = 0, divisor: float = 1.0):
     """Per-step precisions for the Horner products P_i Y, i = r..1.
 
     1. s = ceil(sqrt(m)) unless given; r = floor(m/s).
@@ -371,6 +380,8 @@ def plan(m: int, n: int, norms, normY: float, mode: int = MODE_PAPER, tol: float
     5. mode NS: steps i <= floor_steps stay in the working precision.  FIXED: every step.
     6. When s divides m, B_r = b_m I and step r is a scalar multiple of Y: no product
        (format NONE).
+    divisor != 1 (the reverse pass, see adjoint_divisor): each u_i of step 2 is divided by it
+    before the clamp of step 2 and before steps 3-6.
     Returns dict(s, r, nu, u (list, index 1..r), fmt (index 1..r), fold).
     """
     if m <= 0:
@@ -387,6 +398,8 @@ def plan(m: int, n: int, norms, normY: float, mode: int = MODE_PAPER, tol: float
             yi = yi * float(normY)
         den = eta * yi
         ui = math.inf if den == 0.0 else (eta0 * tol) / den
+        if divisor != 1.0:
+            ui = ui / divisor
         u[i] = max(tol, ui)
     nu = r + 1
     for i in range(1, r + 1):

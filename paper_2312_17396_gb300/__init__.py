@@ -82,7 +82,10 @@ EXPORTS = ("mpps_policy_default", "mpps_plan", "ps_eval", "expm_taylor_ss", "ps_
            "mpps_profile_reset", "mpps_profile_read", "mpps_matmul_noalloc",
            "mpps_selftest_bounded_wait", "expm_taylor_ss_grouped", "mpps_release_workspace",
            "expm_taylor_ss_adjoint", "mpps_choose_s", "mpps_autotune_enable",
-           "mpps_autotune_clear", "mpps_autotune_entries", "expm_pade13")
+           "mpps_autotune_clear", "mpps_autotune_entries", "expm_pade13", "mpps_plan_adjoint",
+           "ps_eval_tape_bytes", "ps_eval_forward_tape", "ps_eval_adjoint_tape",
+           "ps_eval_adjoint_f32")
+STORAGE_F64, STORAGE_F32 = 0, 1
 PROF_GEMM_F64, PROF_GEMM_TC, PROF_ELEMENTWISE, PROF_GEMM_F64E, PROF_SLICE = 0, 1, 2, 3, 4
 
 
@@ -105,6 +108,19 @@ def lib():
                                      ctypes.POINTER(_Report), vp]
         L.ps_eval_adjoint.argtypes = [dp, ip, vp, vp, ip, ip, ctypes.POINTER(_Policy), vp, vp]
         L.expm_taylor_ss_adjoint.argtypes = [vp, vp, ip, ip, ip, ctypes.POINTER(_Policy), vp, vp]
+        L.mpps_plan_adjoint.argtypes = [ip, ip, dp, ctypes.c_double, ctypes.c_double,
+                                        ctypes.POINTER(_Policy), ctypes.POINTER(_Report)]
+        L.mpps_plan_adjoint.restype = ctypes.c_int
+        L.ps_eval_tape_bytes.argtypes = [ip, ip, ip, ctypes.POINTER(_Policy)]
+        L.ps_eval_tape_bytes.restype = ctypes.c_size_t
+        L.ps_eval_forward_tape.argtypes = [dp, ip, vp, ip, ip, ip, ctypes.POINTER(_Policy), vp, vp,
+                                           ctypes.c_size_t, vp]
+        L.ps_eval_forward_tape.restype = ctypes.c_int
+        L.ps_eval_adjoint_tape.argtypes = [dp, ip, vp, ctypes.c_size_t, vp, ip, ip, ip,
+                                           ctypes.POINTER(_Policy), vp, vp]
+        L.ps_eval_adjoint_tape.restype = ctypes.c_int
+        L.ps_eval_adjoint_f32.argtypes = [dp, ip, vp, vp, ip, ip, ctypes.POINTER(_Policy), vp, vp]
+        L.ps_eval_adjoint_f32.restype = ctypes.c_int
         L.mpps_choose_s.argtypes = [ip, ctypes.c_double, dp, dp, ip]
         L.mpps_choose_s.restype = ctypes.c_int
         L.expm_pade13.argtypes = [vp, ip, ip, ctypes.POINTER(_Policy), vp, vp]
@@ -202,6 +218,18 @@ def plan(m: int, n: int, normB, normY: float, policy: Policy | None = None) -> d
     pol = (policy or Policy())._c()
     _check(lib().mpps_plan(int(m), int(n), nb.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                            float(normY), ctypes.byref(pol), ctypes.byref(R)))
+    return _report_dict(R)
+
+
+def plan_adjoint(m: int, n: int, normB, normY: float, normX: float,
+                 policy: Policy | None = None) -> dict:
+    """Host-only planner of the reverse pass: the forward rule with every u_i divided by
+    m / min(1, ||X||_1) (mpps_plan_adjoint; no GPU needed)."""
+    nb = np.ascontiguousarray(normB, dtype=np.float64)
+    R = _Report()
+    pol = (policy or Policy())._c()
+    _check(lib().mpps_plan_adjoint(int(m), int(n), nb.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   float(normY), float(normX), ctypes.byref(pol), ctypes.byref(R)))
     return _report_dict(R)
 
 
@@ -376,6 +404,88 @@ def ps_eval_adjoint(coeffs, A, G, out=None, policy: Policy | None = None, stream
     return out
 
 
+def _storage_of(t):
+    torch = _torch()
+    if not (_is_torch(t) and t.is_cuda and t.is_contiguous()):
+        raise ValueError("tape calls take contiguous CUDA tensors")
+    if t.dtype == torch.float64:
+        return STORAGE_F64
+    if t.dtype == torch.float32:
+        return STORAGE_F32
+    raise TypeError(f"tape calls take float64 or float32 tensors (got {t.dtype})")
+
+
+def _shape(t):
+    if t.dim() == 2:
+        return 1, t.shape[0]
+    if t.dim() == 3 and t.shape[1] == t.shape[2]:
+        return t.shape[0], t.shape[1]
+    raise ValueError("expected (n, n) or (batch, n, n)")
+
+
+def tape_bytes(m: int, n: int, batch: int, policy: Policy | None = None) -> int:
+    pol = (policy or Policy())._c()
+    nbytes = int(lib().ps_eval_tape_bytes(int(m), int(n), int(batch), ctypes.byref(pol)))
+    if nbytes == 0:
+        raise MppsError(1, lib().mpps_last_error().decode(errors="replace"))
+    return nbytes
+
+
+def ps_eval_forward_tape(coeffs, A, policy: Policy | None = None, out=None, stream=None):
+    """p(A) (float64 or float32 CUDA tensor) and the tape its reverse pass reads: returns
+    (out, tape), tape a uint8 CUDA tensor of ps_eval_tape_bytes bytes."""
+    torch = _torch()
+    storage = _storage_of(A)
+    batch, n = _shape(A)
+    c, cp, m = _coef_ptr(coeffs)
+    pol = (policy or Policy())._c()
+    nbytes = tape_bytes(m, n, batch, policy)
+    tape = torch.empty(nbytes, dtype=torch.uint8, device=A.device)
+    if out is None:
+        out = torch.empty_like(A)
+    _check(lib().ps_eval_forward_tape(cp, m, ctypes.c_void_p(A.data_ptr()), storage, n, batch,
+                                      ctypes.byref(pol), ctypes.c_void_p(out.data_ptr()),
+                                      ctypes.c_void_p(tape.data_ptr()), nbytes,
+                                      _stream_for("cuda", stream)))
+    return out, tape
+
+
+def ps_eval_adjoint_tape(coeffs, tape, G, policy: Policy | None = None, out=None, stream=None):
+    """Gradient of <G, p(A)> from the tape of ps_eval_forward_tape (same coeffs, policy,
+    shape and dtype)."""
+    torch = _torch()
+    storage = _storage_of(G)
+    batch, n = _shape(G)
+    c, cp, m = _coef_ptr(coeffs)
+    pol = (policy or Policy())._c()
+    if out is None:
+        out = torch.empty_like(G)
+    _check(lib().ps_eval_adjoint_tape(cp, m, ctypes.c_void_p(tape.data_ptr()), tape.numel(),
+                                      ctypes.c_void_p(G.data_ptr()), storage, n, batch,
+                                      ctypes.byref(pol), ctypes.c_void_p(out.data_ptr()),
+                                      _stream_for("cuda", stream)))
+    return out
+
+
+def ps_eval_adjoint_f32(coeffs, A, G, out=None, policy: Policy | None = None, stream=None):
+    """ps_eval_adjoint for float32 CUDA tensors (evaluated in FP64, gradient rounded to FP32)."""
+    torch = _torch()
+    for t, nm in ((A, "A"), (G, "G")):
+        if not (_is_torch(t) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+            raise ValueError(f"{nm} must be a contiguous float32 CUDA tensor")
+    batch, n = _shape(A)
+    if tuple(G.shape) != tuple(A.shape):
+        raise ValueError("G must have the shape of A")
+    c, cp, m = _coef_ptr(coeffs)
+    pol = (policy or Policy())._c()
+    if out is None:
+        out = torch.empty_like(A)
+    _check(lib().ps_eval_adjoint_f32(cp, m, ctypes.c_void_p(A.data_ptr()),
+                                     ctypes.c_void_p(G.data_ptr()), n, batch, ctypes.byref(pol),
+                                     ctypes.c_void_p(out.data_ptr()), _stream_for("cuda", stream)))
+    return out
+
+
 def expm_pade(A, policy: Policy | None = None, out=None, stream=None):
     """exp(A) by the [13/13] Pade approximant with scaling and squaring (numerator and
     denominator from one power chain, LU solve, squarings)."""
@@ -512,25 +622,32 @@ def _make_autograd():
         return None, None
 
     class PolyFn(torch.autograd.Function):
-        """p(A) with a hand-written reverse mode: forward ps_eval, backward ps_eval_adjoint.
-        FP32 inputs are evaluated in FP64 and the result is returned in the input dtype."""
+        """p(A) with a hand-written reverse mode that reuses the forward pass: forward
+        ps_eval_forward_tape keeps the powers and Horner iterates on a tape (all of them, or
+        with policy.adjoint_recompute every ceil(sqrt(r))-th), backward ps_eval_adjoint_tape
+        reads it.  float64 and float32 CUDA tensors go through the library as they are (FP32
+        storage is widened and narrowed by its kernels); other dtypes are cast to float64."""
 
         @staticmethod
         def forward(ctx, A, coeffs, policy=None):
             c = np.asarray(coeffs, dtype=np.float64)
-            A64 = A.detach().to(torch.float64).contiguous()
-            P = ps_eval(c, A64, policy=policy)
-            ctx.save_for_backward(A64)
+            x = A.detach()
+            if x.dtype not in (torch.float64, torch.float32):
+                x = x.to(torch.float64)
+            x = x.contiguous()
+            P, tape = ps_eval_forward_tape(c, x, policy=policy)
+            ctx.save_for_backward(tape)
             ctx.coeffs = c
             ctx.policy = policy
+            ctx.work_dtype = x.dtype
             ctx.in_dtype = A.dtype
             return P.to(A.dtype)
 
         @staticmethod
         def backward(ctx, grad_out):
-            (A64,) = ctx.saved_tensors
-            G = grad_out.detach().to(torch.float64).contiguous()
-            gA = ps_eval_adjoint(ctx.coeffs, A64, G, policy=ctx.policy)
+            (tape,) = ctx.saved_tensors
+            G = grad_out.detach().to(ctx.work_dtype).contiguous()
+            gA = ps_eval_adjoint_tape(ctx.coeffs, tape, G, policy=ctx.policy)
             return gA.to(ctx.in_dtype), None, None
 
     class ExpmFn(torch.autograd.Function):

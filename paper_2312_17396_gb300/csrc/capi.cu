@@ -120,8 +120,28 @@ static int prec_rank(int f) {
 static const int kF64eMinRung = 4;
 
 // Planner for one matrix.  normB: r+1 norms ||B_0||..||B_r||; normY = ||X^s||.
+// div > 1 tightens every u_i of eq. (2.8) by that factor before nu and the formats are chosen
+// (the rule of the reverse pass, see plan_adjoint_divisor); div = 1 is the forward rule.
+static mpps_status plan_steps(int m, int n, const double* normB, double normY, const Pol& P,
+                              double div, mpps_report* out);
 static mpps_status plan_one(int m, int n, const double* normB, double normY, const Pol& P,
                             mpps_report* out) {
+    return plan_steps(m, n, normB, normY, P, 1.0, out);
+}
+
+// Reverse pass (the paper states no adjoint).  The gradient of a degree-k term b_k X^k is a
+// sum of k products X^j E X^(k-1-j), each as large as the term itself times ||E||/||X||, so
+// relative to the value the high-order blocks weigh up to m/||X|| times more in the gradient
+// than in p(X), while the reference (the low-order block) keeps its weight.  The products of
+// reverse step i therefore run in the format the forward rule picks for u_i / d with
+// d = m / min(1, ||X||_1).
+static double plan_adjoint_divisor(int m, double normX) {
+    const double x = (normX > 0.0 && normX < 1.0) ? normX : 1.0;
+    return (double)m / x;
+}
+
+static mpps_status plan_steps(int m, int n, const double* normB, double normY, const Pol& P,
+                              double div, mpps_report* out) {
     memset(out, 0, sizeof(*out));
     for (int i = 0; i <= MPPS_MAX_R; ++i) out->fmt[i] = MPPS_FMT_NONE;
     if (m == 0) {
@@ -155,7 +175,8 @@ static mpps_status plan_one(int m, int n, const double* normB, double normY, con
         double yi = 1.0;
         for (int k = 0; k < i; ++k) yi = yi * normY;
         const double den = normB[i] * yi;
-        const double ui = (den == 0.0) ? INFINITY : (normB[0] * tol) / den;
+        double ui = (den == 0.0) ? INFINITY : (normB[0] * tol) / den;
+        if (div != 1.0) ui = ui / div;
         out->u[i] = (ui > tol) ? ui : tol;
     }
     // nu: first step allowed below the working precision; earlier steps get u
@@ -370,11 +391,43 @@ static mpps_status dev_err_enqueue(DevErr* e, cudaStream_t st) {
     return MPPS_OK;
 }
 
+// ---- forward state kept for a reverse pass (the adjoint's tape) -----------------------
+// Where the forward pass leaves the power table and the Horner iterates P_1..P_top
+// (top = r, or r - 1 when s divides m).  All iterates are kept, or (recompute) every c-th
+// with c = ceil(sqrt(r)) and the top one; the others go to two rolling slots and are
+// recomputed a segment at a time by the reverse pass.
+struct TapeLayout {
+    int s = 0, r = 0, fold = 0, i_top = 0;
+    int recompute = 0, cseg = 1, ck_top = 0, seg0 = 0, nslots = 0;
+    size_t pw_off = 0, slot_off = 0, hdr_off = 0, bytes = 0;
+    bool is_ckpt(int j) const { return !recompute || j % cseg == 0 || j == i_top; }
+    int ck_slot(int j) const { return !recompute ? j : (j == i_top ? ck_top : j / cseg); }
+    int fwd_slot(int j) const { return is_ckpt(j) ? ck_slot(j) : seg0 + (j & 1); }
+};
+
+// Per-step formats of the forward and of the reverse Horner products, and the checks that
+// tie a tape to its call.
+struct TapeHeader {
+    int magic, m, n, batch, s, r, storage, pad_;
+    int fmt[MPPS_MAX_R + 1];
+    int fmt_adj[MPPS_MAX_R + 1];
+};
+static const int kTapeMagic = 0x6d707073;
+
+struct Keep {
+    const TapeLayout* L;
+    double* pw;                      // power table [batch][s][n][n]
+    double* slots;                   // iterate slots [nslots][batch][n][n]
+    int fmt[MPPS_MAX_R + 1];         // out: the batch's format of each Horner step
+    std::vector<mpps_report> plans;  // out: per-matrix plans (u_i, norms)
+};
+
 // ---- the PS evaluation --------------------------------------------------------------
 // Evaluates p(X) for a device batch; for expm, X = 2^-sigma A and sigma squarings follow.
+// keep (not for expm): the power table and the Horner iterates go where *keep says.
 static mpps_status eval_device(const double* coeffs, int m, const double* dA, int n, int batch,
                                const Pol& pol, double* dOut, mpps_report* rep, cudaStream_t st,
-                               bool expm, bool sync_at_end) {
+                               bool expm, bool sync_at_end, Keep* keep = nullptr) {
     const long long nn = (long long)n * n;
     // ---- m == 0: p = b_0 I
     if (m == 0) {
@@ -399,7 +452,7 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
     }
     // Variable s (Algorithm 3.1, fix_params false): s may grow after the powers, so the
     // power table has room for s_cap powers and the norm buffers for every s up to it.
-    const bool var_s = pol.var_s && pol.s <= 0 && pol.mode != MPPS_FIXED_FP64 && m >= 2;
+    const bool var_s = pol.var_s && pol.s <= 0 && pol.mode != MPPS_FIXED_FP64 && m >= 2 && !keep;
     const int s0 = s;
     const int s_cap = var_s ? std::min(std::min(m, MPPS_MAX_S), 2 * s0) : s;
     int r = m / s;
@@ -422,7 +475,7 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
     char* split = nullptr;   // split-K scratch of the emulated products
     auto layout1 = [&](Arena& a) {
         d_coef = a.take<double>(m + 1);
-        pw = a.take<double>((size_t)batch * pw_bs);
+        pw = keep ? keep->pw : a.take<double>((size_t)batch * pw_bs);
         Pb0 = a.take<double>((size_t)batch * nn);
         Pb1 = a.take<double>((size_t)batch * nn);
         partial = a.take<double>(partial_elems);
@@ -658,6 +711,12 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
     for (int b = 0; b < batch; ++b) sig_max = std::max(sig_max, sigma[b]);
     double* Pbuf[2] = {Pb0, Pb1};
     double* dst0 = (expm && sig_max > 0) ? Pb0 : dOut;
+    // where each Horner iterate P_j is written (and read by step j): ping-pong buffers, or the
+    // tape's slots
+    double* Pdst[MPPS_MAX_R + 1];
+    Pdst[0] = dst0;
+    for (int j = 1; j <= r; ++j)
+        Pdst[j] = keep ? keep->slots + (size_t)keep->L->fwd_slot(j) * batch * nn : Pbuf[j & 1];
     const double* Y = pw + (long long)(s - 1) * nn;
     // Emulated squarings work on Q = P - I (Q <- Q Q + 2 Q, exact algebra): the slices of a
     // matrix close to I would be aligned to its unit diagonal and lose the small entries'
@@ -665,7 +724,7 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
     const bool qform = expm && sig_max > 0 && K > 0;
 
     auto make_ep = [&](int i) {   // epilogue producing P_{i-1} = B_{i-1} + (...)
-        Epilogue ep = epilogue_plain((i - 1 == 0) ? dst0 : Pbuf[(i - 1) & 1], nn);
+        Epilogue ep = epilogue_plain(Pdst[i - 1], nn);
         ep.nt = s - 1;
         for (int j = 0; j < s; ++j) ep.coef[j] = coeffs[(i - 1) * s + j];
         if (i - 1 == 0 && qform) ep.coef[0] -= 1.0;
@@ -691,7 +750,7 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
         i_start = r - 1;
     } else {
         // P_r = B_r = sum_{j<=m-sr} b_{sr+j} X_j
-        Epilogue ep = epilogue_plain(Pbuf[r & 1], nn);
+        Epilogue ep = epilogue_plain(Pdst[r], nn);
         ep.nt = m - s * r;
         for (int j = 0; j <= ep.nt; ++j) ep.coef[j] = coeffs[s * r + j];
         ep.pw = pw;
@@ -712,17 +771,17 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
     for (int i = i_start; i >= 1; --i) {
         Epilogue ep = make_ep(i);
         if (fmt[i] == MPPS_FMT_FP64) {
-            rc = launch_gemm_f64(Pbuf[i & 1], nn, Y, pw_bs, n, batch, ep, st);
+            rc = launch_gemm_f64(Pdst[i], nn, Y, pw_bs, n, batch, ep, st);
         } else if (MPPS_FMT_IS_F64E(fmt[i])) {
             const int k = MPPS_F64E_SLICES(fmt[i]);
-            rc = launch_slice_rows(Pbuf[i & 1], nn, n, batch, k, slA, eA, st);
+            rc = launch_slice_rows(Pdst[i], nn, n, batch, k, slA, eA, st);
             if (!rc)
                 rc = launch_gemm_f64e(k, slA, k, eA, slY, K, eY, n, batch, batch, ep, d_err, st,
                                       nullptr, split);
         } else if (fmt[i] == MPPS_FMT_FP8) {
             // per-row scales of P_i, per-column scales of Y (the paper's scaled low-precision
             // products, with the scales as fine as a row / a column)
-            rc = launch_convert_scaled(fmt[i], Pbuf[i & 1], nn, n, batch, Pl_hi[i & 1], nullptr,
+            rc = launch_convert_scaled(fmt[i], Pdst[i], nn, n, batch, Pl_hi[i & 1], nullptr,
                                        low_bs, lld, low_target_exp(fmt[i]), false, xrowP, nullptr, st);
             ep.row_exp = xrowP;
             ep.col_exp = xcolY;
@@ -781,6 +840,10 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
         if (sync_at_end && (rc = dev_err_check(derr, true))) return rc;
     }
 
+    if (keep) {
+        for (int i = 0; i <= MPPS_MAX_R; ++i) keep->fmt[i] = (i >= 1 && i <= r) ? fmt[i] : MPPS_FMT_NONE;
+        keep->plans = rp;
+    }
     if (rep) {
         for (int b = 0; b < batch; ++b) {
             mpps_report& R = rp[b];
@@ -870,6 +933,23 @@ mpps_status mpps_plan(int m, int n, const double* normB, double normY, const mpp
     Pol P = resolve(policy);
     mpps_status rc = plan_one(m, n, normB, normY, P, out);
     if (rc == MPPS_OK) out->cost_ratio = cost_ratio(*out, P.tol);
+    return rc;
+}
+
+mpps_status mpps_plan_adjoint(int m, int n, const double* normB, double normY, double normX,
+                              const mpps_policy* policy, mpps_report* out) {
+    clear_error();
+    if (m < 0 || n <= 0 || !normB || !out) {
+        set_error("mpps_plan_adjoint: invalid argument");
+        return MPPS_EINVAL;
+    }
+    Pol P = resolve(policy);
+    mpps_status rc = plan_steps(m, n, normB, normY, P, m > 0 ? plan_adjoint_divisor(m, normX) : 1.0,
+                                out);
+    if (rc == MPPS_OK) {
+        out->normX = normX;
+        out->cost_ratio = cost_ratio(*out, P.tol);
+    }
     return rc;
 }
 
@@ -1142,250 +1222,522 @@ mpps_status mpps_matmul(const double* A, const double* B, double* C, int n, int 
     return MPPS_OK;
 }
 
-// Reverse mode through the PS steps (FP64).  Forward: powers X_1..X_s and Horner iterates
-// P_r..P_1 are kept.  Backward (f = <G, P_0>):
+}  // extern "C"
+
+namespace mpps {
+
+// ---- tape of the reverse pass ----------------------------------------------------------
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static mpps_status tape_layout(int m, int n, int batch, const Pol& pol, TapeLayout* L) {
+    *L = TapeLayout();
+    if (m < 1) {
+        L->hdr_off = 0;
+        L->bytes = sizeof(TapeHeader);
+        return MPPS_OK;
+    }
+    const int s = pol.s > 0 ? std::min(pol.s, m) : ceil_sqrt_int(m);
+    const int r = m / s;
+    if (s > MPPS_MAX_S || r > MPPS_MAX_R) {
+        set_error("m=%d with s=%d is outside the supported range (s<=%d, r<=%d)", m, s, MPPS_MAX_S,
+                  MPPS_MAX_R);
+        return MPPS_EINVAL;
+    }
+    L->s = s;
+    L->r = r;
+    L->fold = (m % s) == 0;
+    L->i_top = L->fold ? r - 1 : r;
+    L->recompute = pol.recompute && r >= 3;
+    L->cseg = L->recompute ? ceil_sqrt_int(r) : 1;
+    L->ck_top = r / L->cseg + 1;
+    L->seg0 = r / L->cseg + 2;
+    L->nslots = L->recompute ? L->seg0 + std::max(2, L->cseg) : r + 1;
+    const size_t nn = (size_t)n * n;
+    L->pw_off = 0;
+    L->slot_off = align256(sizeof(double) * (size_t)batch * s * nn);
+    L->hdr_off = align256(L->slot_off + sizeof(double) * (size_t)L->nslots * batch * nn);
+    L->bytes = L->hdr_off + sizeof(TapeHeader);
+    return MPPS_OK;
+}
+
+// Scratch of a product in any format (product_fmt): slice planes for the emulated products,
+// rounded copies and power-of-two scales for the low-precision ones.
+struct ProductWs {
+    __nv_bfloat16 *slA = nullptr, *slB = nullptr;
+    int *eA = nullptr, *eB = nullptr;
+    unsigned long long* cmx = nullptr;
+    char* split = nullptr;
+    char *ahi = nullptr, *alo = nullptr, *bhi = nullptr, *blo = nullptr;
+    double *ma = nullptr, *mb = nullptr, *sa = nullptr, *sb = nullptr, *un = nullptr;
+    void take(Arena& z, int n, int batch, int kmax, bool low) {
+        if (kmax > 0) {
+            slA = z.take<__nv_bfloat16>(f64e_plane_elems(n, batch, kmax));
+            slB = z.take<__nv_bfloat16>(f64e_plane_elems(n, batch, kmax));
+            eA = z.take<int>((size_t)batch * n);
+            eB = z.take<int>((size_t)batch * n);
+            cmx = z.take<unsigned long long>((size_t)batch * n);
+            split = z.take<char>(f64e_split_bytes());
+        }
+        if (low) {
+            const size_t lb = (size_t)batch * n * low_ld(n) * 4;   // widest low element: 4 bytes
+            ahi = z.take<char>(lb);
+            alo = z.take<char>(lb);
+            bhi = z.take<char>(lb);
+            blo = z.take<char>(lb);
+            ma = z.take<double>(batch);
+            mb = z.take<double>(batch);
+            sa = z.take<double>(batch);
+            sb = z.take<double>(batch);
+            un = z.take<double>(batch);
+        }
+    }
+};
+
+// C = A B in format fmt with the fused epilogue ep (alpha = 1): FP64 pipe, emulated
+// F64E(k) from exact slices of the rows of A and the columns of B, or a low-precision
+// tensor-core product of A and B each scaled by a power of two from its largest entry
+// (the building block mpps_matmul offers, used here with an epilogue).
+static mpps_status product_fmt(int fmt, const double* A, long long a_bs, const double* B,
+                               long long b_bs, int n, int batch, Epilogue ep, ProductWs& w,
+                               int* d_err, cudaStream_t st) {
+    const long long nn = (long long)n * n;
+    if (fmt == MPPS_FMT_FP64) return launch_gemm_f64(A, a_bs, B, b_bs, n, batch, ep, st);
+    if (MPPS_FMT_IS_F64E(fmt)) {
+        const int k = MPPS_F64E_SLICES(fmt);
+        mpps_status rc = launch_slice_rows(A, a_bs, n, batch, k, w.slA, w.eA, st);
+        if (!rc) rc = launch_slice_cols(B, b_bs, n, batch, k, w.slB, w.eB, w.cmx, st);
+        if (!rc)
+            rc = launch_gemm_f64e(k, w.slA, k, w.eA, w.slB, k, w.eB, n, batch, batch, ep, d_err, st,
+                                  nullptr, w.split);
+        return rc;
+    }
+    if (!is_low(fmt) || !w.ahi) {
+        set_error("product_fmt: format %d has no workspace", fmt);
+        return MPPS_EINVAL;
+    }
+    const int lld = low_ld(n);
+    const long long low_bs = (long long)n * lld;
+    MPPS_CUDA_TRY(cudaMemsetAsync(w.ma, 0, sizeof(double) * batch, st));
+    MPPS_CUDA_TRY(cudaMemsetAsync(w.mb, 0, sizeof(double) * batch, st));
+    mpps_status rc = launch_maxabs(A, a_bs, n, batch, w.ma, st);
+    if (!rc) rc = launch_maxabs(B, b_bs, n, batch, w.mb, st);
+    if (!rc) rc = launch_pow2_scales(w.ma, w.mb, batch, low_target_exp(fmt), w.sa, w.sb, w.un, st);
+    if (!rc) rc = launch_convert(fmt, A, a_bs, n, batch, w.ahi, w.alo, low_bs, lld, w.sa, false, st);
+    if (!rc) rc = launch_convert(fmt, B, b_bs, n, batch, w.bhi, w.blo, low_bs, lld, w.sb, true, st);
+    if (rc) return rc;
+    (void)nn;
+    ep.alpha_b = w.un;
+    return launch_gemm_tc(fmt, w.ahi, w.alo, w.bhi, w.blo, low_bs, low_bs, lld, n, batch, ep, d_err, st);
+}
+
+// The reverse pass's per-step formats: the forward rule of each matrix with u_i tightened by
+// plan_adjoint_divisor, the batch taking the most precise format any matrix asks for.
+static void adjoint_formats(int m, int n, int r, const Keep& k, const Pol& pol, int* fmt_adj) {
+    for (int i = 0; i <= MPPS_MAX_R; ++i) fmt_adj[i] = MPPS_FMT_NONE;
+    for (size_t b = 0; b < k.plans.size(); ++b) {
+        const mpps_report& R = k.plans[b];
+        mpps_report A;
+        if (plan_steps(m, n, R.normB, R.normY, pol, plan_adjoint_divisor(m, R.normX), &A)) continue;
+        for (int i = 1; i <= r; ++i)
+            if (fmt_adj[i] == MPPS_FMT_NONE || prec_rank(A.fmt[i]) > prec_rank(fmt_adj[i]))
+                fmt_adj[i] = A.fmt[i];
+    }
+    const int wp = pol.f64k > 0 ? MPPS_FMT_F64E(pol.f64k) : MPPS_FMT_FP64;
+    for (int i = 1; i <= r; ++i)
+        if (fmt_adj[i] == MPPS_FMT_NONE) fmt_adj[i] = wp;   // folded step: no product to run
+}
+
+// Forward pass into a tape: P_0 = p(X) into dOut, the power table and the Horner iterates
+// into the tape, the formats of both passes into its header.  All pointers on the device.
+static mpps_status forward_tape_dev(const double* coeffs, int m, const double* dA, int n, int batch,
+                                    const Pol& pol, double* dOut, char* tape, const TapeLayout& L,
+                                    int storage, cudaStream_t st) {
+    TapeHeader h;
+    memset(&h, 0, sizeof(h));
+    h.magic = kTapeMagic;
+    h.m = m;
+    h.n = n;
+    h.batch = batch;
+    h.storage = storage;
+    for (int i = 0; i <= MPPS_MAX_R; ++i) h.fmt[i] = h.fmt_adj[i] = MPPS_FMT_NONE;
+    if (m >= 1) {
+        Keep k;
+        k.L = &L;
+        k.pw = (double*)(tape + L.pw_off);
+        k.slots = (double*)(tape + L.slot_off);
+        Pol p = pol;
+        p.var_s = 0;
+        mpps_status rc = eval_device(coeffs, m, dA, n, batch, p, dOut, nullptr, st, false, false, &k);
+        if (rc) return rc;
+        h.s = L.s;
+        h.r = L.r;
+        for (int i = 0; i <= MPPS_MAX_R; ++i) h.fmt[i] = k.fmt[i];
+        adjoint_formats(m, n, L.r, k, p, h.fmt_adj);
+    } else {
+        mpps_status rc = eval_device(coeffs, m, dA, n, batch, pol, dOut, nullptr, st, false, false);
+        if (rc) return rc;
+    }
+    MPPS_CUDA_TRY(cudaMemcpyAsync(tape + L.hdr_off, &h, sizeof(h), cudaMemcpyHostToDevice, st));
+    return MPPS_OK;
+}
+
+// Reverse mode through the PS steps.  Forward: powers X_1..X_s and Horner iterates P_r..P_1
+// on the tape.  Backward (f = <G, P_0>):
 //   Pbar_0 = G;  for i = 1..r: Bbar_{i-1} = Pbar_{i-1};  Ybar += P_i^T Pbar_{i-1};
 //                              Pbar_i = Pbar_{i-1} Y^T;   (fold: step r has P_r = b_m I,
 //                              so Ybar += b_m Pbar_{r-1} and the loop stops)
 //   Bbar_r = Pbar_r;  Xbar_j += sum_i b_{si+j} Bbar_i;  Xbar_s += Ybar;
 //   for j = s..2: Xbar_{j-1} += Xbar_j X_1^T;  Xbar_1 += X_{j-1}^T Xbar_j;   grad = Xbar_1.
-mpps_status ps_eval_adjoint(const double* coeffs, int m, const double* A, const double* G, int n,
-                            int batch, const mpps_policy* policy, double* gradA, void* stream) {
-    clear_error();
-    mpps_status rc = check_sizes(n, batch);
-    if (rc) return rc;
-    if (m < 0 || !coeffs) {
-        set_error("ps_eval_adjoint: invalid argument (m=%d)", m);
-        return MPPS_EINVAL;
-    }
-    if (batch == 0) return MPPS_OK;
-    if (!A || !G || !gradA) {
-        set_error("ps_eval_adjoint: null matrix pointer");
-        return MPPS_EINVAL;
-    }
-    if ((rc = check_same_device("ps_eval_adjoint", {A, G, gradA}))) return rc;
-    cudaStream_t st = (cudaStream_t)stream;
+// The two products of reverse step i run in the header's fmt_adj[i]; the power chain in the
+// working precision.  All pointers on the device.
+static mpps_status adjoint_tape_dev(const double* coeffs, int m, const char* tape,
+                                    const TapeLayout& L, const double* dG, int n, int batch,
+                                    const Pol& pol, double* dGrad, int storage, cudaStream_t st) {
     const long long nn = (long long)n * n;
     const size_t elems = (size_t)batch * nn;
-    Staged a, g;
-    if ((rc = stage_in(A, elems, st, a))) return rc;
-    if ((rc = stage_in(G, elems, st, g))) return rc;
-    const bool o_dev = is_device_ptr(gradA);
-    DevBuf ob;
-    double* dGrad = gradA;
-    if (!o_dev) {
-        if ((rc = ob.alloc(elems * sizeof(double), st))) return rc;
-        dGrad = (double*)ob.p;
+    TapeHeader h;
+    MPPS_CUDA_TRY(cudaMemcpyAsync(&h, tape + L.hdr_off, sizeof(h), cudaMemcpyDeviceToHost, st));
+    MPPS_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h.magic != kTapeMagic || h.m != m || h.n != n || h.batch != batch || h.storage != storage ||
+        (m >= 1 && (h.s != L.s || h.r != L.r))) {
+        set_error("adjoint: the tape was not written by a forward call of this size and policy");
+        return MPPS_EINVAL;
     }
     if (m == 0) {
         MPPS_CUDA_TRY(cudaMemsetAsync(dGrad, 0, elems * sizeof(double), st));
-    } else {
-        const int s = ceil_sqrt_int(m);
-        const int r = m / s;
-        const bool fold = (m % s) == 0;
-        const long long pw_bs = (long long)s * nn;
-        const Pol pol = resolve(policy);
-        if (pol.f64k < 0 || pol.f64k > MPPS_F64E_MAX_SLICES) {
-            set_error("f64_slices=%d outside 0..%d", pol.f64k, MPPS_F64E_MAX_SLICES);
+        return MPPS_OK;
+    }
+    const int s = L.s, r = L.r;
+    const bool fold = L.fold;
+    const int i_top = L.i_top;
+    const long long pw_bs = (long long)s * nn;
+    const double* pw = (const double*)(tape + L.pw_off);
+    double* Pst = (double*)(tape + L.slot_off);   // recompute mode writes its rolling slots
+    const int K = pol.f64k;
+    const int wp = K > 0 ? MPPS_FMT_F64E(K) : MPPS_FMT_FP64;
+    bool any_low = false;
+    int kmax = K;
+    for (int i = 1; i <= r; ++i) {
+        for (int f : {h.fmt[i], h.fmt_adj[i]}) {
+            if (is_low(f)) any_low = true;
+            if (MPPS_FMT_IS_F64E(f)) kmax = std::max(kmax, MPPS_F64E_SLICES(f));
+        }
+    }
+    Arena Z;
+    double *xbar, *Ybar, *Pbar0, *Pbar1, *Yt, *X1t, *T;
+    ProductWs w;
+    auto lay = [&](Arena& z) {
+        xbar = z.take<double>((size_t)batch * pw_bs);
+        Ybar = z.take<double>(elems);
+        Pbar0 = z.take<double>(elems);
+        Pbar1 = z.take<double>(elems);
+        Yt = z.take<double>(elems);
+        X1t = z.take<double>(elems);
+        T = z.take<double>(elems);
+        w = ProductWs();
+        w.take(z, n, batch, kmax, any_low);
+    };
+    lay(Z);
+    DevBuf ws;
+    mpps_status rc = ws.alloc(Z.off, st);
+    if (rc) return rc;
+    Z.base = (char*)ws.p;
+    Z.off = 0;
+    lay(Z);
+    if (w.split) MPPS_CUDA_TRY(cudaMemsetAsync(w.split, 0, f64e_split_flag_bytes(), st));
+    DevErr* derr = nullptr;
+    if ((rc = dev_err_get(&derr))) return rc;
+    if ((rc = dev_err_check(derr, false))) return rc;
+    auto product = [&](int fmt, const double* Am, long long a_bs, const double* Bm, long long b_bs,
+                       const Epilogue& ep) -> mpps_status {
+        return product_fmt(fmt, Am, a_bs, Bm, b_bs, n, batch, ep, w, derr->d, st);
+    };
+    auto slotp = [&](int k) { return Pst + (size_t)k * batch * nn; };
+    std::vector<double*> loc(r + 1, nullptr);   // where P_j is held now
+    for (int j = 1; j <= i_top; ++j)
+        if (L.is_ckpt(j)) loc[j] = slotp(L.ck_slot(j));
+    const double* Y = pw + (long long)(s - 1) * nn;
+    // P_{i-1} = B_{i-1} + P_i Y into dst, in the forward step's format
+    auto horner_step = [&](int i, double* dst) -> mpps_status {
+        Epilogue ep = epilogue_plain(dst, nn);
+        ep.nt = s - 1;
+        for (int j = 0; j < s; ++j) ep.coef[j] = coeffs[(i - 1) * s + j];
+        ep.pw = pw; ep.pw_bstride = pw_bs;
+        return product(h.fmt[i] >= 0 ? h.fmt[i] : wp, loc[i], nn, Y, pw_bs, ep);
+    };
+    // P_i for the reverse pass (ascending i): a missing one is recomputed with the rest of
+    // its segment, P_{k-1} .. P_{i0} from the checkpoint k above
+    auto P_at = [&](int i, mpps_status* err) -> double* {
+        if (loc[i]) return loc[i];
+        const int k = std::min((i / L.cseg + 1) * L.cseg, i_top);
+        const int i0 = (i / L.cseg) * L.cseg + 1;
+        for (int j = 1; j <= r; ++j)
+            if (!L.is_ckpt(j)) loc[j] = nullptr;
+        for (int j = k; j > i0; --j) {
+            loc[j - 1] = slotp(L.seg0 + (j - 1 - i0));
+            if ((*err = horner_step(j, loc[j - 1]))) return nullptr;
+        }
+        return loc[i];
+    };
+    MPPS_CUDA_TRY(cudaMemsetAsync(xbar, 0, sizeof(double) * batch * pw_bs, st));
+    MPPS_CUDA_TRY(cudaMemsetAsync(Ybar, 0, elems * sizeof(double), st));
+    // Y^T and X_1^T (strided power table -> contiguous copies first)
+    if ((rc = launch_scale_copy(Y, pw_bs, T, nn, n, batch, nullptr, st))) return rc;
+    if ((rc = launch_transpose(T, nn, Yt, n, batch, st))) return rc;
+    if ((rc = launch_scale_copy(pw, pw_bs, T, nn, n, batch, nullptr, st))) return rc;
+    if ((rc = launch_transpose(T, nn, X1t, n, batch, st))) return rc;
+    double* Pbar[2] = {Pbar0, Pbar1};
+    if ((rc = launch_scale_copy(dG, nn, Pbar[0], nn, n, batch, nullptr, st))) return rc;
+    int cur = 0;
+    for (int i = 1; i <= r; ++i) {
+        // Bbar_{i-1} = Pbar_{i-1}: Xbar_j += b_{(i-1)s+j} Pbar for j = 1..s-1
+        double c[MPPS_MAX_S + 1];
+        for (int j = 0; j < s; ++j) c[j] = coeffs[(i - 1) * s + j];
+        if ((rc = launch_axpy_blocks(xbar, pw_bs, n, batch, s - 1, c, Pbar[cur], nn, st))) return rc;
+        if (fold && i == r) {
+            // P_r = b_m I: Ybar += b_m Pbar_{r-1}
+            Epilogue ep = epilogue_plain(Ybar, nn);
+            ep.alpha = coeffs[m];
+            ep.add = Ybar; ep.add_bstride = nn; ep.add_coef = 1.0;
+            if ((rc = launch_combine(n, batch, Pbar[cur], nn, ep, st))) return rc;
+            cur = -1;
+            break;
+        }
+        // Ybar += P_i^T Pbar_{i-1}
+        double* Pi = P_at(i, &rc);
+        if (rc) return rc;
+        if ((rc = launch_transpose(Pi, nn, T, n, batch, st))) return rc;
+        {
+            Epilogue ep = epilogue_plain(Ybar, nn);
+            ep.add = Ybar; ep.add_bstride = nn; ep.add_coef = 1.0;
+            if ((rc = product(h.fmt_adj[i], T, nn, Pbar[cur], nn, ep))) return rc;
+        }
+        // Pbar_i = Pbar_{i-1} Y^T
+        {
+            Epilogue ep = epilogue_plain(Pbar[cur ^ 1], nn);
+            if ((rc = product(h.fmt_adj[i], Pbar[cur], nn, Yt, nn, ep))) return rc;
+        }
+        cur ^= 1;
+    }
+    if (cur >= 0) {   // not folded: Bbar_r = Pbar_r, B_r = sum_{j<=m-sr} b_{sr+j} X_j
+        double c[MPPS_MAX_S + 1];
+        const int t = m - s * r;
+        for (int j = 0; j <= t; ++j) c[j] = coeffs[s * r + j];
+        if ((rc = launch_axpy_blocks(xbar, pw_bs, n, batch, t, c, Pbar[cur], nn, st))) return rc;
+    }
+    // Xbar_s += Ybar
+    {
+        double c[MPPS_MAX_S + 1] = {0};
+        double* xs = xbar + (long long)(s - 1) * nn;
+        c[1] = 1.0;
+        if ((rc = launch_axpy_blocks(xs, pw_bs, n, batch, 1, c, Ybar, nn, st))) return rc;
+    }
+    // powers: X_j = X_{j-1} X_1, j = s..2 (working precision: they feed the low-order blocks)
+    for (int j = s; j >= 2; --j) {
+        double* xj = xbar + (long long)(j - 1) * nn;
+        double* xjm = xbar + (long long)(j - 2) * nn;
+        // Xbar_{j-1} += Xbar_j X_1^T
+        Epilogue e1 = epilogue_plain(xjm, pw_bs);
+        e1.add = xjm; e1.add_bstride = pw_bs; e1.add_coef = 1.0;
+        if ((rc = product(wp, xj, pw_bs, X1t, nn, e1))) return rc;
+        // Xbar_1 += X_{j-1}^T Xbar_j
+        if ((rc = launch_scale_copy(pw + (long long)(j - 2) * nn, pw_bs, T, nn, n, batch, nullptr, st)))
+            return rc;
+        if ((rc = launch_transpose(T, nn, Pbar0, n, batch, st))) return rc;
+        Epilogue e2 = epilogue_plain(xbar, pw_bs);
+        e2.add = xbar; e2.add_bstride = pw_bs; e2.add_coef = 1.0;
+        if ((rc = product(wp, Pbar0, nn, xj, pw_bs, e2))) return rc;
+    }
+    if ((rc = launch_scale_copy(xbar, pw_bs, dGrad, nn, n, batch, nullptr, st))) return rc;
+    return dev_err_enqueue(derr, st);
+}
+
+// The entry points' shared checks; resolves the policy and the tape layout.
+static mpps_status tape_args(const char* fn, const double* coeffs, int m, int n, int batch,
+                             const mpps_policy* policy, Pol* pol, TapeLayout* L) {
+    mpps_status rc = check_sizes(n, batch);
+    if (rc) return rc;
+    if (m < 0 || !coeffs) {
+        set_error("%s: invalid argument (m=%d)", fn, m);
+        return MPPS_EINVAL;
+    }
+    *pol = resolve(policy);
+    if (pol->f64k < 0 || pol->f64k > MPPS_F64E_MAX_SLICES) {
+        set_error("f64_slices=%d outside 0..%d", pol->f64k, MPPS_F64E_MAX_SLICES);
+        return MPPS_EINVAL;
+    }
+    return tape_layout(m, n, batch, *pol, L);
+}
+
+}  // namespace mpps
+
+extern "C" {
+
+size_t ps_eval_tape_bytes(int m, int n, int batch, const mpps_policy* policy) {
+    clear_error();
+    Pol pol;
+    TapeLayout L;
+    const double one = 1.0;
+    if (tape_args("ps_eval_tape_bytes", &one, m, n, batch, policy, &pol, &L)) return 0;
+    return L.bytes;
+}
+
+// FP32 storage: widen into a workspace copy (exact); results narrowed to nearest.
+static mpps_status widen_in(const void* p, int storage, size_t elems, cudaStream_t st, DevBuf& buf,
+                            const double** out) {
+    if (storage == MPPS_STORAGE_F64) {
+        *out = (const double*)p;
+        return MPPS_OK;
+    }
+    mpps_status rc = buf.alloc(elems * sizeof(double), st);
+    if (rc) return rc;
+    if ((rc = launch_widen_f32((const float*)p, (double*)buf.p, (long long)elems, st))) return rc;
+    *out = (const double*)buf.p;
+    return MPPS_OK;
+}
+
+static mpps_status storage_args(const char* fn, int storage, std::initializer_list<const void*> ptrs) {
+    if (storage != MPPS_STORAGE_F64 && storage != MPPS_STORAGE_F32) {
+        set_error("%s: storage %d is neither MPPS_STORAGE_F64 nor MPPS_STORAGE_F32", fn, storage);
+        return MPPS_EINVAL;
+    }
+    for (const void* p : ptrs)
+        if (!p || !is_device_ptr(p)) {
+            set_error("%s: matrix and tape pointers must be device pointers", fn);
             return MPPS_EINVAL;
         }
-        const int K = pol.f64k;      // products on the FP64 pipe (0) or emulated with K slices
-        // Horner iterates P_i kept for the reverse pass: all of them, or (recompute) only
-        // every c-th with c = ceil(sqrt(r)) and the top one, the others recomputed a segment
-        // at a time from the checkpoint above by the same products (so bit for bit the same)
-        const int i_top = fold ? r - 1 : r;   // highest Horner iterate that is a real matrix
-        const bool recompute = pol.recompute && r >= 3;
-        const int cseg = recompute ? ceil_sqrt_int(r) : 1;
-        const int ck_top = r / cseg + 1;                  // slot of the top checkpoint
-        const int seg0 = r / cseg + 2;                    // first segment slot
-        const int nslots = recompute ? seg0 + std::max(2, cseg) : r + 1;
-        Arena L;
-        double *pw, *xbar, *Pst, *Ybar, *Pbar0, *Pbar1, *Yt, *X1t, *T;
-        __nv_bfloat16 *slA = nullptr, *slB = nullptr;
-        int *eA = nullptr, *eB = nullptr;
-        unsigned long long* cmx = nullptr;
-        char* split = nullptr;
-        auto lay = [&](Arena& z) {
-            pw = z.take<double>((size_t)batch * pw_bs);
-            xbar = z.take<double>((size_t)batch * pw_bs);
-            Pst = z.take<double>((size_t)batch * nn * nslots);
-            Ybar = z.take<double>(elems);
-            Pbar0 = z.take<double>(elems);
-            Pbar1 = z.take<double>(elems);
-            Yt = z.take<double>(elems);
-            X1t = z.take<double>(elems);
-            T = z.take<double>(elems);
-            if (K > 0) {
-                slA = z.take<__nv_bfloat16>(f64e_plane_elems(n, batch, K));
-                slB = z.take<__nv_bfloat16>(f64e_plane_elems(n, batch, K));
-                eA = z.take<int>((size_t)batch * n);
-                eB = z.take<int>((size_t)batch * n);
-                cmx = z.take<unsigned long long>((size_t)batch * n);
-                split = z.take<char>(f64e_split_bytes());
-            }
-        };
-        lay(L);
-        DevBuf ws;
-        if ((rc = ws.alloc(L.off, st))) return rc;
-        L.base = (char*)ws.p;
-        L.off = 0;
-        lay(L);
-        if (split) MPPS_CUDA_TRY(cudaMemsetAsync(split, 0, f64e_split_flag_bytes(), st));
-        auto slotp = [&](int k) { return Pst + (size_t)k * batch * nn; };
-        auto is_ckpt = [&](int j) { return !recompute || j % cseg == 0 || j == i_top; };
-        auto ck_slot = [&](int j) { return !recompute ? j : (j == i_top ? ck_top : j / cseg); };
-        std::vector<double*> loc(r + 1, nullptr);   // where P_j is held now
-        DevErr* derr = nullptr;
-        if (K > 0) {
-            if ((rc = dev_err_get(&derr))) return rc;
-            if ((rc = dev_err_check(derr, false))) return rc;
-        }
-        // every product of the adjoint in the working precision: FP64 pipe or emulated
-        auto product = [&](const double* Am, long long a_bs, const double* Bm, long long b_bs,
-                           const Epilogue& ep) -> mpps_status {
-            if (K == 0) return launch_gemm_f64(Am, a_bs, Bm, b_bs, n, batch, ep, st);
-            mpps_status r1 = launch_slice_rows(Am, a_bs, n, batch, K, slA, eA, st);
-            if (!r1) r1 = launch_slice_cols(Bm, b_bs, n, batch, K, slB, eB, cmx, st);
-            if (!r1)
-                r1 = launch_gemm_f64e(K, slA, K, eA, slB, K, eB, n, batch, batch, ep, derr->d, st,
-                                      nullptr, split);
-            return r1;
-        };
-        // forward
-        if ((rc = launch_scale_copy(a.dev, nn, pw, pw_bs, n, batch, nullptr, st))) return rc;
-        for (int j = 2; j <= s; ++j) {
-            Epilogue ep = epilogue_plain(pw + (long long)(j - 1) * nn, pw_bs);
-            if ((rc = product(pw + (long long)(j - 2) * nn, pw_bs, pw, pw_bs, ep))) return rc;
-        }
-        const double* Y = pw + (long long)(s - 1) * nn;
-        // P_{i-1} = B_{i-1} + P_i Y into dst
-        auto horner_step = [&](int i, double* dst) -> mpps_status {
-            Epilogue ep = epilogue_plain(dst, nn);
-            ep.nt = s - 1;
-            for (int j = 0; j < s; ++j) ep.coef[j] = coeffs[(i - 1) * s + j];
-            ep.pw = pw; ep.pw_bstride = pw_bs;
-            return product(loc[i], nn, Y, pw_bs, ep);
-        };
-        // where the forward pass puts P_j: its checkpoint slot, else one of two rolling slots
-        auto fwd_dst = [&](int j) { return is_ckpt(j) ? slotp(ck_slot(j)) : slotp(seg0 + (j & 1)); };
-        loc[i_top] = fwd_dst(i_top);
-        if (fold) {
-            Epilogue ep = epilogue_plain(loc[r - 1], nn);
-            ep.nt = s - 1;
-            for (int j = 0; j < s; ++j) ep.coef[j] = coeffs[(r - 1) * s + j];
-            ep.pw = pw; ep.pw_bstride = pw_bs; ep.alpha = coeffs[m];
-            if ((rc = launch_combine(n, batch, Y, pw_bs, ep, st))) return rc;
-        } else {
-            Epilogue ep = epilogue_plain(loc[r], nn);
-            ep.nt = m - s * r;
-            for (int j = 0; j <= ep.nt; ++j) ep.coef[j] = coeffs[s * r + j];
-            ep.pw = pw; ep.pw_bstride = pw_bs; ep.alpha = 0.0;
-            if ((rc = launch_combine(n, batch, nullptr, 0, ep, st))) return rc;
-        }
-        for (int i = i_top; i >= 2; --i) {   // P_{i-1} = B_{i-1} + P_i Y (P_0 not needed)
-            loc[i - 1] = fwd_dst(i - 1);
-            if ((rc = horner_step(i, loc[i - 1]))) return rc;
-        }
-        for (int j = 1; j <= r; ++j)
-            if (!is_ckpt(j)) loc[j] = nullptr;   // rolling slots: overwritten
-        // P_i for the reverse pass (ascending i): a missing one is recomputed with the rest of
-        // its segment, P_{k-1} .. P_{i0} from the checkpoint k above
-        auto P_at = [&](int i, mpps_status* err) -> double* {
-            if (loc[i]) return loc[i];
-            const int k = std::min((i / cseg + 1) * cseg, i_top);
-            const int i0 = (i / cseg) * cseg + 1;
-            for (int j = 1; j <= r; ++j)
-                if (!is_ckpt(j)) loc[j] = nullptr;
-            for (int j = k; j > i0; --j) {
-                loc[j - 1] = slotp(seg0 + (j - 1 - i0));
-                if ((*err = horner_step(j, loc[j - 1]))) return nullptr;
-            }
-            return loc[i];
-        };
-        // backward
-        MPPS_CUDA_TRY(cudaMemsetAsync(xbar, 0, sizeof(double) * batch * pw_bs, st));
-        MPPS_CUDA_TRY(cudaMemsetAsync(Ybar, 0, elems * sizeof(double), st));
-        // Y^T and X_1^T (strided power table -> contiguous copies first)
-        if ((rc = launch_scale_copy(Y, pw_bs, T, nn, n, batch, nullptr, st))) return rc;
-        if ((rc = launch_transpose(T, nn, Yt, n, batch, st))) return rc;
-        if ((rc = launch_scale_copy(pw, pw_bs, T, nn, n, batch, nullptr, st))) return rc;
-        if ((rc = launch_transpose(T, nn, X1t, n, batch, st))) return rc;
-        double* Pbar[2] = {Pbar0, Pbar1};
-        if ((rc = launch_scale_copy(g.dev, nn, Pbar[0], nn, n, batch, nullptr, st))) return rc;
-        int cur = 0;
-        for (int i = 1; i <= r; ++i) {
-            // Bbar_{i-1} = Pbar_{i-1}: Xbar_j += b_{(i-1)s+j} Pbar for j = 1..s-1
-            double c[MPPS_MAX_S + 1];
-            for (int j = 0; j < s; ++j) c[j] = coeffs[(i - 1) * s + j];
-            if ((rc = launch_axpy_blocks(xbar, pw_bs, n, batch, s - 1, c, Pbar[cur], nn, st))) return rc;
-            if (fold && i == r) {
-                // P_r = b_m I: Ybar += b_m Pbar_{r-1}
-                Epilogue ep = epilogue_plain(Ybar, nn);
-                ep.alpha = coeffs[m];
-                ep.add = Ybar; ep.add_bstride = nn; ep.add_coef = 1.0;
-                if ((rc = launch_combine(n, batch, Pbar[cur], nn, ep, st))) return rc;
-                cur = -1;
-                break;
-            }
-            // Ybar += P_i^T Pbar_{i-1}
-            double* Pi = P_at(i, &rc);
-            if (rc) return rc;
-            if ((rc = launch_transpose(Pi, nn, T, n, batch, st))) return rc;
-            {
-                Epilogue ep = epilogue_plain(Ybar, nn);
-                ep.add = Ybar; ep.add_bstride = nn; ep.add_coef = 1.0;
-                if ((rc = product(T, nn, Pbar[cur], nn, ep))) return rc;
-            }
-            // Pbar_i = Pbar_{i-1} Y^T
-            {
-                Epilogue ep = epilogue_plain(Pbar[cur ^ 1], nn);
-                if ((rc = product(Pbar[cur], nn, Yt, nn, ep))) return rc;
-            }
-            cur ^= 1;
-        }
-        if (cur >= 0) {   // not folded: Bbar_r = Pbar_r, B_r = sum_{j<=m-sr} b_{sr+j} X_j
-            double c[MPPS_MAX_S + 1];
-            const int t = m - s * r;
-            for (int j = 0; j <= t; ++j) c[j] = coeffs[s * r + j];
-            if ((rc = launch_axpy_blocks(xbar, pw_bs, n, batch, t, c, Pbar[cur], nn, st))) return rc;
-        }
-        // Xbar_s += Ybar
-        {
-            double c[MPPS_MAX_S + 1] = {0};
-            double* xs = xbar + (long long)(s - 1) * nn;
-            c[1] = 1.0;
-            if ((rc = launch_axpy_blocks(xs, pw_bs, n, batch, 1, c, Ybar, nn, st))) return rc;
-        }
-        // powers: X_j = X_{j-1} X_1, j = s..2
-        for (int j = s; j >= 2; --j) {
-            double* xj = xbar + (long long)(j - 1) * nn;
-            double* xjm = xbar + (long long)(j - 2) * nn;
-            // Xbar_{j-1} += Xbar_j X_1^T
-            Epilogue e1 = epilogue_plain(xjm, pw_bs);
-            e1.add = xjm; e1.add_bstride = pw_bs; e1.add_coef = 1.0;
-            if ((rc = product(xj, pw_bs, X1t, nn, e1))) return rc;
-            // Xbar_1 += X_{j-1}^T Xbar_j
-            if ((rc = launch_scale_copy(pw + (long long)(j - 2) * nn, pw_bs, T, nn, n, batch, nullptr, st)))
-                return rc;
-            if ((rc = launch_transpose(T, nn, Pbar0, n, batch, st))) return rc;
-            Epilogue e2 = epilogue_plain(xbar, pw_bs);
-            e2.add = xbar; e2.add_bstride = pw_bs; e2.add_coef = 1.0;
-            if ((rc = product(Pbar0, nn, xj, pw_bs, e2))) return rc;
-        }
-        if ((rc = launch_scale_copy(xbar, pw_bs, dGrad, nn, n, batch, nullptr, st))) return rc;
-        if (K > 0) {
-            if ((rc = dev_err_enqueue(derr, st))) return rc;
-            if ((!o_dev || !is_device_ptr(A) || !is_device_ptr(G)) && (rc = dev_err_check(derr, true)))
-                return rc;
-        }
+    return check_same_device(fn, ptrs);
+}
+
+mpps_status ps_eval_forward_tape(const double* coeffs, int m, const void* A, int storage, int n,
+                                 int batch, const mpps_policy* policy, void* out, void* tape,
+                                 size_t tape_bytes, void* stream) {
+    clear_error();
+    Pol pol;
+    TapeLayout L;
+    mpps_status rc = tape_args("ps_eval_forward_tape", coeffs, m, n, batch, policy, &pol, &L);
+    if (rc) return rc;
+    if (batch == 0) return MPPS_OK;
+    if ((rc = storage_args("ps_eval_forward_tape", storage, {A, out, tape}))) return rc;
+    if (tape_bytes < L.bytes) {
+        set_error("ps_eval_forward_tape: the tape holds %zu bytes, %zu needed (ps_eval_tape_bytes)",
+                  tape_bytes, L.bytes);
+        return MPPS_EINVAL;
     }
-    if (!o_dev) {
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t elems = (size_t)batch * n * n;
+    DevBuf ain, obuf;
+    const double* dA = nullptr;
+    if ((rc = widen_in(A, storage, elems, st, ain, &dA))) return rc;
+    double* dOut = (double*)out;
+    if (storage == MPPS_STORAGE_F32) {
+        if ((rc = obuf.alloc(elems * sizeof(double), st))) return rc;
+        dOut = (double*)obuf.p;
+    }
+    if ((rc = forward_tape_dev(coeffs, m, dA, n, batch, pol, dOut, (char*)tape, L, storage, st)))
+        return rc;
+    if (storage == MPPS_STORAGE_F32)
+        return launch_narrow_f64(dOut, (float*)out, (long long)elems, st);
+    return MPPS_OK;
+}
+
+mpps_status ps_eval_adjoint_tape(const double* coeffs, int m, const void* tape, size_t tape_bytes,
+                                 const void* G, int storage, int n, int batch,
+                                 const mpps_policy* policy, void* gradA, void* stream) {
+    clear_error();
+    Pol pol;
+    TapeLayout L;
+    mpps_status rc = tape_args("ps_eval_adjoint_tape", coeffs, m, n, batch, policy, &pol, &L);
+    if (rc) return rc;
+    if (batch == 0) return MPPS_OK;
+    if ((rc = storage_args("ps_eval_adjoint_tape", storage, {tape, G, gradA}))) return rc;
+    if (tape_bytes < L.bytes) {
+        set_error("ps_eval_adjoint_tape: the tape holds %zu bytes, %zu needed", tape_bytes, L.bytes);
+        return MPPS_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t elems = (size_t)batch * n * n;
+    DevBuf gin, gbuf;
+    const double* dG = nullptr;
+    if ((rc = widen_in(G, storage, elems, st, gin, &dG))) return rc;
+    double* dGrad = (double*)gradA;
+    if (storage == MPPS_STORAGE_F32) {
+        if ((rc = gbuf.alloc(elems * sizeof(double), st))) return rc;
+        dGrad = (double*)gbuf.p;
+    }
+    if ((rc = adjoint_tape_dev(coeffs, m, (const char*)tape, L, dG, n, batch, pol, dGrad, storage, st)))
+        return rc;
+    if (storage == MPPS_STORAGE_F32)
+        return launch_narrow_f64(dGrad, (float*)gradA, (long long)elems, st);
+    return MPPS_OK;
+}
+
+// Forward into a private tape, then the reverse pass.
+static mpps_status adjoint_private(const char* fn, const double* coeffs, int m, const void* A,
+                                   const void* G, int storage, int n, int batch,
+                                   const mpps_policy* policy, void* gradA, void* stream) {
+    clear_error();
+    Pol pol;
+    TapeLayout L;
+    mpps_status rc = tape_args(fn, coeffs, m, n, batch, policy, &pol, &L);
+    if (rc) return rc;
+    if (batch == 0) return MPPS_OK;
+    if (!A || !G || !gradA) {
+        set_error("%s: null matrix pointer", fn);
+        return MPPS_EINVAL;
+    }
+    if ((rc = check_same_device(fn, {A, G, gradA}))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t elems = (size_t)batch * n * n;
+    const size_t es = storage == MPPS_STORAGE_F32 ? sizeof(float) : sizeof(double);
+    // host matrices are staged in and out (FP64 only; the FP32 variant takes device pointers)
+    const bool host_io = !is_device_ptr(A) || !is_device_ptr(G) || !is_device_ptr(gradA);
+    if (host_io && storage == MPPS_STORAGE_F32) {
+        set_error("%s: device pointers required", fn);
+        return MPPS_EINVAL;
+    }
+    Staged a, g;
+    const void *dA = A, *dG = G;
+    if (host_io) {
+        if ((rc = stage_in((const double*)A, elems, st, a))) return rc;
+        if ((rc = stage_in((const double*)G, elems, st, g))) return rc;
+        dA = a.dev;
+        dG = g.dev;
+    }
+    DevBuf tb, ob, gb;
+    if ((rc = tb.alloc(L.bytes, st))) return rc;
+    if ((rc = ob.alloc(elems * es, st))) return rc;
+    void* dGrad = gradA;
+    if (!is_device_ptr(gradA)) {
+        if ((rc = gb.alloc(elems * sizeof(double), st))) return rc;
+        dGrad = gb.p;
+    }
+    if ((rc = ps_eval_forward_tape(coeffs, m, dA, storage, n, batch, policy, ob.p, tb.p, L.bytes, stream)))
+        return rc;
+    if ((rc = ps_eval_adjoint_tape(coeffs, m, tb.p, L.bytes, dG, storage, n, batch, policy, dGrad,
+                                   stream)))
+        return rc;
+    if (dGrad != gradA) {
         MPPS_CUDA_TRY(cudaMemcpyAsync(gradA, dGrad, elems * sizeof(double), cudaMemcpyDeviceToHost, st));
         MPPS_CUDA_TRY(cudaStreamSynchronize(st));
-    } else if (!is_device_ptr(A) || !is_device_ptr(G)) {
+    } else if (host_io) {
         MPPS_CUDA_TRY(cudaStreamSynchronize(st));
     }
-    return MPPS_OK;
+    DevErr* derr = nullptr;
+    if ((rc = dev_err_get(&derr))) return rc;
+    return dev_err_check(derr, host_io);
+}
+
+mpps_status ps_eval_adjoint(const double* coeffs, int m, const double* A, const double* G, int n,
+                            int batch, const mpps_policy* policy, double* gradA, void* stream) {
+    return adjoint_private("ps_eval_adjoint", coeffs, m, A, G, MPPS_STORAGE_F64, n, batch, policy,
+                           gradA, stream);
+}
+
+mpps_status ps_eval_adjoint_f32(const double* coeffs, int m, const float* A, const float* G, int n,
+                                int batch, const mpps_policy* policy, float* gradA, void* stream) {
+    return adjoint_private("ps_eval_adjoint_f32", coeffs, m, A, G, MPPS_STORAGE_F32, n, batch,
+                           policy, gradA, stream);
 }
 
 mpps_status expm_taylor_ss_adjoint(const double* A, const double* G, int n, int batch, int m,
@@ -1410,13 +1762,13 @@ mpps_status expm_taylor_ss_adjoint(const double* A, const double* G, int n, int 
         return MPPS_EINVAL;
     }
     const int K = pol.f64k;
-    // the forward polynomial and the PS adjoint in the working precision (FP64 pipe or
-    // emulated with K slices), like every product below
+    // the polynomial and its reverse pass under the caller's precision rule (the Horner
+    // steps of both passes by eq. (2.8), the reverse one tightened as in ps_eval_adjoint);
+    // the squarings and their reverse pass in the working precision (FP64 pipe or emulated
+    // with K slices): their errors are amplified
     mpps_policy fpol;
-    mpps_policy_default(&fpol);
-    fpol.mode = MPPS_FIXED_FP64;
-    fpol.f64_slices = K;
-    fpol.adjoint_recompute = pol.recompute;
+    if (policy) fpol = *policy; else mpps_policy_default(&fpol);
+    fpol.variable_s = 0;
     std::vector<double> c(m + 1);   // b_i = 1/i!, as in expm_taylor_ss
     {
         long double f = 1.0L;
@@ -1509,8 +1861,16 @@ mpps_status expm_taylor_ss_adjoint(const double* A, const double* G, int n, int 
         return r1;
     };
 
-    // ---- forward: S_0 = p(X), S_{k+1} = S_k^2 for the matrices with sigma > k + 1
-    if ((rc = ps_eval(c.data(), m, X, n, batch, &fpol, S, nullptr, stream))) return rc;
+    // ---- forward: S_0 = p(X) (its powers and Horner iterates kept on a tape for the reverse
+    // pass), S_{k+1} = S_k^2 for the matrices with sigma > k + 1
+    const Pol tpol = resolve(&fpol);
+    TapeLayout TL;
+    if ((rc = tape_layout(m, n, batch, tpol, &TL))) return rc;
+    DevBuf tape;
+    if ((rc = tape.alloc(TL.bytes, st))) return rc;
+    if ((rc = forward_tape_dev(c.data(), m, X, n, batch, tpol, S, (char*)tape.p, TL, MPPS_STORAGE_F64,
+                               st)))
+        return rc;
     std::vector<int> lists((size_t)std::max(sig_max, 1) * batch);
     std::vector<int> counts(std::max(sig_max, 1), 0);
     for (int k = 0; k < sig_max; ++k)
@@ -1545,7 +1905,9 @@ mpps_status expm_taylor_ss_adjoint(const double* A, const double* G, int n, int 
         if ((rc = product(T, Sb[k & 1], counts[k], lk, e2))) return rc;
     }
     // ---- through p: Xbar = L_p(X^T, Sbar_0); then Abar = 2^-sigma Xbar
-    if ((rc = ps_eval_adjoint(c.data(), m, X, Sb[1], n, batch, &fpol, Xbar, stream))) return rc;
+    if ((rc = adjoint_tape_dev(c.data(), m, (const char*)tape.p, TL, Sb[1], n, batch, tpol, Xbar,
+                               MPPS_STORAGE_F64, st)))
+        return rc;
     if ((rc = launch_scale_copy(Xbar, nn, dGrad, nn, n, batch, d_sigma, st))) return rc;
     if (K > 0) {
         if ((rc = dev_err_enqueue(derr, st))) return rc;

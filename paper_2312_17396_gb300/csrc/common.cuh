@@ -375,6 +375,9 @@ mpps_status launch_norm1(const double* M, long long bs, int n, int batch, double
 // X = 2^-sigma[b] A (exact power-of-two scaling; d_sigma null -> plain copy).
 mpps_status launch_scale_copy(const double* A, long long a_bs, double* X, long long x_bs, int n,
                               int batch, const int* d_sigma, cudaStream_t st);
+// FP32 storage: x = (double)a (exact) and a = (float)x (round to nearest), count elements.
+mpps_status launch_widen_f32(const float* a, double* x, long long count, cudaStream_t st);
+mpps_status launch_narrow_f64(const double* x, float* a, long long count, cudaStream_t st);
 // One member of an uneven batch (device pointers), for the padded gather / scatter.
 struct PadItem {
     const double* A;

@@ -309,6 +309,20 @@ __global__ void k_scale_copy(const double* __restrict__ A, long long a_bs, doubl
         X[b * x_bs + t] = scale_pow2(A[b * a_bs + t], e);
 }
 
+// FP32 storage <-> FP64 evaluation (exact widening; narrowing rounds to nearest).
+__global__ void k_widen_f32(const float* __restrict__ a, double* __restrict__ x, long long count) {
+    pdl_wait();
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count;
+         t += (long long)gridDim.x * blockDim.x)
+        x[t] = (double)a[t];
+}
+__global__ void k_narrow_f64(const double* __restrict__ x, float* __restrict__ a, long long count) {
+    pdl_wait();
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count;
+         t += (long long)gridDim.x * blockDim.x)
+        a[t] = (float)x[t];
+}
+
 // Gather items of different orders into a zero-padded batch (row-major n_pad x n_pad each)
 // and scatter the leading n x n blocks back.
 // (Row, column) loops over a 2-D grid: x covers columns, y rows, z the matrices.
@@ -695,6 +709,20 @@ mpps_status launch_scale_copy(const double* A, long long a_bs, double* X, long l
     ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
     const long long nn = (long long)n * n;
     MPPS_CUDA_TRY(launch_pdl(k_scale_copy, dim3(dim3(grid1d(nn, 256), batch)), dim3(256), 0, st, A, a_bs, X, x_bs, nn, d_sigma));
+    MPPS_LAUNCH_CHECK();
+    return MPPS_OK;
+}
+
+mpps_status launch_widen_f32(const float* a, double* x, long long count, cudaStream_t st) {
+    ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
+    MPPS_CUDA_TRY(launch_pdl(k_widen_f32, dim3(grid1d(count, 256)), dim3(256), 0, st, a, x, count));
+    MPPS_LAUNCH_CHECK();
+    return MPPS_OK;
+}
+
+mpps_status launch_narrow_f64(const double* x, float* a, long long count, cudaStream_t st) {
+    ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
+    MPPS_CUDA_TRY(launch_pdl(k_narrow_f64, dim3(grid1d(count, 256)), dim3(256), 0, st, x, a, count));
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }

@@ -162,3 +162,34 @@ def test_policy_struct_round_trip(mpps):
     d = mpps._Policy()
     mpps.lib().mpps_policy_default(d)
     assert (d.variable_s, d.adjoint_recompute, d.f64_slices, d.s) == (0, 0, 0, 0)
+
+
+@pytest.mark.parametrize("mode", [oracle.MODE_FIXED, oracle.MODE_PAPER, oracle.MODE_NS])
+def test_adjoint_planner_matches_oracle_rule(mpps, mode):
+    """The reverse pass's rule (eq. (2.8) with u_i divided by m / min(1, ||X||_1)) agrees bit
+    for bit with the oracle's statement."""
+    rng = np.random.default_rng(70 + mode)
+    for _ in range(300):
+        m, n, norms, y = _rand_case(rng)
+        x = float(10.0 ** rng.uniform(-3, 1))
+        k = int(rng.choice([0, 8]))
+        d = oracle.adjoint_divisor(m, x)
+        ref = oracle.plan(m, n, norms, y, mode=mode, formats=0x1F, floor_steps=2, f64_slices=k,
+                          divisor=d)
+        got = mpps.plan_adjoint(m, n, norms, y, x, mpps.Policy(mode=mode, formats=0x1F,
+                                                               fp64_floor_steps=2, f64_slices=k))
+        assert got["nu"] == ref["nu"]
+        for i in range(1, ref["r"] + 1):
+            assert got["u"][i] == ref["u"][i], (m, i)
+            want = ref["fmt"][i]
+            assert got["fmt"][i] == (mpps.FORMAT_NAMES[want] if want is not None else None), (m, i)
+        # tightening never asks for less precision than the forward rule
+        fwd = oracle.plan(m, n, norms, y, mode=mode, formats=0x1F, floor_steps=2, f64_slices=k)
+        for i in range(1, ref["r"] + 1):
+            assert ref["u"][i] <= fwd["u"][i]
+
+
+def test_adjoint_divisor_reading():
+    assert oracle.adjoint_divisor(18, 9.0) == 18.0
+    assert oracle.adjoint_divisor(18, 0.5) == 36.0
+    assert oracle.adjoint_divisor(30, 0.0) == 30.0
