@@ -44,7 +44,9 @@ typedef enum {
     MPPS_ENOMEM = 2,    /* device allocation failed */
     MPPS_ECUDA = 3,     /* a CUDA runtime/driver call or kernel launch failed */
     MPPS_ETIMEOUT = 4,  /* a bounded wait inside a kernel gave up (device error word set) */
-    MPPS_ENOTSUP = 5    /* not supported on this device / build */
+    MPPS_ENOTSUP = 5,   /* not supported on this device / build */
+    MPPS_ECHECK = 6     /* a check made on the GPU failed (e.g. a matrix needed more squarings
+                           than policy.max_squarings; its result is NaN) */
 } mpps_status;
 
 /* Precision modes.  FIXED: every product in FP64 (Algorithm 2.1).  MIXED_PAPER: eq. (2.8)
@@ -96,6 +98,18 @@ typedef struct {
                                (mpps_choose_s); 0: s = ceil(sqrt(m)) */
     int adjoint_recompute;  /* 1: the adjoints keep every ceil(sqrt(r))-th Horner iterate and
                                recompute the others (same products, same result); 0: keep all */
+    int device_plan;        /* 1: the precision rule runs on the GPU (ps_eval, expm_taylor_ss):
+                               no read-back of the norms; every format the rule may pick for a
+                               step is launched and all but the chosen one return at once.
+                               Same formats, scales and results as the host planner.  0: the
+                               host plans after one read-back of the norms */
+    int max_squarings;      /* expm with device_plan: k > 0 launches k squaring steps, each on
+                               the matrices whose sigma exceeds its index (lists built on the
+                               GPU), so the call reads nothing back and can be captured in a
+                               CUDA graph; a matrix needing more than k squarings gets NaN and
+                               MPPS_ECHECK is reported (at once, or by the next call that finds
+                               the error word).  0: sigma is read back early in the call (the
+                               GPU does not wait for it) and exactly max sigma steps run */
 } mpps_policy;
 
 /* Per-matrix description of what a call did (filled when `rep` is non-NULL). */
@@ -114,7 +128,7 @@ typedef struct {
 
 /* Fill *p with the defaults: MIXED_NS, tol 2^-53, delta 10, s 0, all formats, floor 2,
  * f64_slices 0 (working-precision products on the FP64 pipe), variable_s 0,
- * adjoint_recompute 0. */
+ * adjoint_recompute 0, device_plan 0, max_squarings 0. */
 void mpps_policy_default(mpps_policy* p);
 
 /*

@@ -47,7 +47,7 @@ MAX_S = 32
 NUM_FORMATS = 5
 
 STATUS = {0: "MPPS_OK", 1: "MPPS_EINVAL", 2: "MPPS_ENOMEM", 3: "MPPS_ECUDA", 4: "MPPS_ETIMEOUT",
-          5: "MPPS_ENOTSUP"}
+          5: "MPPS_ENOTSUP", 6: "MPPS_ECHECK"}
 
 
 class MppsError(RuntimeError):
@@ -60,7 +60,8 @@ class _Policy(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("tol", ctypes.c_double), ("delta", ctypes.c_double),
                 ("s", ctypes.c_int), ("formats", ctypes.c_uint), ("fp64_floor_steps", ctypes.c_int),
                 ("f64_slices", ctypes.c_int), ("variable_s", ctypes.c_int),
-                ("adjoint_recompute", ctypes.c_int)]
+                ("adjoint_recompute", ctypes.c_int), ("device_plan", ctypes.c_int),
+                ("max_squarings", ctypes.c_int)]
 
 
 class _GroupItem(ctypes.Structure):
@@ -178,6 +179,8 @@ class Policy:
     f64_slices: int = 0             # 0: FP64 pipe; k: emulate FP64 products with k slices
     variable_s: bool = False        # the variable-s branch of Algorithm 3.1 (mixed modes)
     adjoint_recompute: bool = False  # adjoints: keep ceil(sqrt(r)) iterates, recompute the rest
+    device_plan: bool = False       # the precision rule on the GPU: no read-back of the norms
+    max_squarings: int = 0          # expm with device_plan: squaring steps launched (0: read sigma)
 
     def _c(self):
         fm = self.formats
@@ -188,7 +191,8 @@ class Policy:
             fm = mask
         return _Policy(int(self.mode), float(self.tol), float(self.delta), int(self.s),
                        int(fm), int(self.fp64_floor_steps), int(self.f64_slices),
-                       int(bool(self.variable_s)), int(bool(self.adjoint_recompute)))
+                       int(bool(self.variable_s)), int(bool(self.adjoint_recompute)),
+                       int(bool(self.device_plan)), int(self.max_squarings))
 
 
 FIXED = Policy(mode=FIXED_FP64)

@@ -39,6 +39,8 @@ struct Pol {
     int f64k;   // 0: FP64 pipe; k > 0: working-precision products emulated with k slices
     int var_s;  // variable-s branch of Algorithm 3.1
     int recompute;  // adjoints: checkpoint the Horner iterates, recompute the rest
+    int dplan;      // precision rule on the device
+    int max_sq;     // expm, device plan: squaring steps launched (0: sigma read back)
 };
 
 static Pol resolve(const mpps_policy* p) {
@@ -55,6 +57,8 @@ static Pol resolve(const mpps_policy* p) {
     r.f64k = p->f64_slices;
     r.var_s = p->variable_s != 0;
     r.recompute = p->adjoint_recompute != 0;
+    r.dplan = p->device_plan != 0;
+    r.max_sq = p->max_squarings > 0 ? p->max_squarings : 0;
     return r;
 }
 
@@ -87,24 +91,32 @@ extern "C" int mpps_choose_s(int m, double normX, const double* normB0, const do
 }
 
 // unit roundoff of the rounded inputs of each format, and the FP32 accumulation unit
-static const double kUFmt[MPPS_NUM_FORMATS] = {0x1p-53, 0x1p-16, 0x1p-11, 0x1p-8, 0x1p-4};
-static const double kAcc = 0x1p-24;
+__host__ __device__ inline double u_fmt(int f) {
+    switch (f) {
+        case MPPS_FMT_FP64: return 0x1p-53;
+        case MPPS_FMT_BF16X3: return 0x1p-16;
+        case MPPS_FMT_TF32: return 0x1p-11;
+        case MPPS_FMT_BF16: return 0x1p-8;
+        case MPPS_FMT_FP8: return 0x1p-4;
+        default: return 1.0;
+    }
+}
 
-static bool is_low(int f) { return f >= MPPS_FMT_BF16X3 && f <= MPPS_FMT_FP8; }
+__host__ __device__ inline bool is_low(int f) { return f >= MPPS_FMT_BF16X3 && f <= MPPS_FMT_FP8; }
 
 // Unit roundoff assigned to an emulated product F64E(k): 2^(2-7k) for k <= 8 slices of 7 bits
 // (the slices keep 7k bits below the row/column maxima; the constant covers the dropped pairs
 // t + q >= k); 2^-55 for k = 9 (8 slices, pairs up to order 8: the 2^-57 residual of each
 // operand dominates).
-static double u_f64e(int k) { return k <= 8 ? ldexp(1.0, 2 - 7 * k) : 0x1p-55; }
+__host__ __device__ inline double u_f64e(int k) { return k <= 8 ? ldexp(1.0, 2 - 7 * k) : 0x1p-55; }
 
 static double unit_roundoff(int f) {
     if (MPPS_FMT_IS_F64E(f)) return u_f64e(MPPS_F64E_SLICES(f));
-    return (f >= 0 && f < MPPS_NUM_FORMATS) ? kUFmt[f] : 1.0;
+    return (f >= 0 && f < MPPS_NUM_FORMATS) ? u_fmt(f) : 1.0;
 }
 
 // Precision rank: larger = more precise (used to run a batch step at its most precise ask).
-static int prec_rank(int f) {
+__host__ __device__ inline int prec_rank(int f) {
     if (f == MPPS_FMT_FP64) return 1000;
     if (MPPS_FMT_IS_F64E(f)) return 100 + MPPS_F64E_SLICES(f);
     switch (f) {
@@ -117,7 +129,7 @@ static int prec_rank(int f) {
 }
 
 // Smallest emulated slice count that always counts as "cheaper than the working precision".
-static const int kF64eMinRung = 4;
+constexpr int kF64eMinRung = 4;
 
 // Planner for one matrix.  normB: r+1 norms ||B_0||..||B_r||; normY = ||X^s||.
 // div > 1 tightens every u_i of eq. (2.8) by that factor before nu and the formats are chosen
@@ -139,6 +151,9 @@ static double plan_adjoint_divisor(int m, double normX) {
     const double x = (normX > 0.0 && normX < 1.0) ? normX : 1.0;
     return (double)m / x;
 }
+
+__host__ __device__ void plan_core(int n, int r, int fold, const double* normB, double normY,
+                                   const Pol& P, double div, double* u, int* fmt, int* nu_out);
 
 static mpps_status plan_steps(int m, int n, const double* normB, double normY, const Pol& P,
                               double div, mpps_report* out) {
@@ -169,26 +184,35 @@ static mpps_status plan_steps(int m, int n, const double* normB, double normY, c
     out->fold = (m % s == 0) ? 1 : 0;
     out->normY = normY;
     for (int i = 0; i <= r; ++i) out->normB[i] = normB[i];
+    plan_core(n, r, out->fold, normB, normY, P, div, out->u, out->fmt, &out->nu);
+    return MPPS_OK;
+}
+
+// eq. (2.8), nu and the format ladder for one matrix, shared by the host planner and the
+// device planner (the same operations in the same order: the plans agree bit for bit).
+// u and fmt: MPPS_MAX_R + 1 entries, steps 1..r written (fmt[r] = NONE when s | m).
+__host__ __device__ void plan_core(int n, int r, int fold, const double* normB, double normY,
+                                   const Pol& P, double div, double* u, int* fmt, int* nu_out) {
     const double tol = P.tol;
     // eq. (2.8) with nu = 1, clamped at the working precision
     for (int i = 1; i <= r; ++i) {
         double yi = 1.0;
         for (int k = 0; k < i; ++k) yi = yi * normY;
         const double den = normB[i] * yi;
-        double ui = (den == 0.0) ? INFINITY : (normB[0] * tol) / den;
+        double ui = (den == 0.0) ? (double)INFINITY : (normB[0] * tol) / den;
         if (div != 1.0) ui = ui / div;
-        out->u[i] = (ui > tol) ? ui : tol;
+        u[i] = (ui > tol) ? ui : tol;
     }
     // nu: first step allowed below the working precision; earlier steps get u
     int nu = r + 1;
     for (int i = 1; i <= r; ++i)
-        if (out->u[i] >= P.delta * tol) { nu = i; break; }
-    for (int i = 1; i < nu; ++i) out->u[i] = tol;
-    out->nu = nu;
+        if (u[i] >= P.delta * tol) { nu = i; break; }
+    for (int i = 1; i < nu; ++i) u[i] = tol;
+    *nu_out = nu;
     // formats: cheapest allowed with unit roundoff <= u_i (and FP32 accumulation <= u_i for
     // the hardware formats); with emulation on, the slice counts 4..k-1 sit between BF16X3
     // and the working precision (their accumulation is exact)
-    static const int order[4] = {MPPS_FMT_FP8, MPPS_FMT_BF16, MPPS_FMT_TF32, MPPS_FMT_BF16X3};
+    const int order[4] = {MPPS_FMT_FP8, MPPS_FMT_BF16, MPPS_FMT_TF32, MPPS_FMT_BF16X3};
     const int wp = P.f64k > 0 ? MPPS_FMT_F64E(P.f64k) : MPPS_FMT_FP64;
     for (int i = 1; i <= r; ++i) {
         int f = wp;
@@ -198,15 +222,136 @@ static mpps_status plan_steps(int m, int n, const double* normB, double normY, c
             for (int k = 0; k < 4 && !found; ++k) {
                 const int F = order[k];
                 if (!((P.formats >> F) & 1u)) continue;
-                if (kUFmt[F] <= out->u[i] && (double)n * kAcc <= out->u[i]) { f = F; found = true; }
+                if (u_fmt(F) <= u[i] && (double)n * 0x1p-24 <= u[i]) { f = F; found = true; }
             }
             for (int k = kF64eMinRung; k < P.f64k && !found; ++k)
-                if (u_f64e(k) <= out->u[i]) { f = MPPS_FMT_F64E(k); found = true; }
+                if (u_f64e(k) <= u[i]) { f = MPPS_FMT_F64E(k); found = true; }
         }
-        out->fmt[i] = f;
+        fmt[i] = f;
     }
-    if (out->fold) out->fmt[r] = MPPS_FMT_NONE;
-    return MPPS_OK;
+    if (fold) fmt[r] = MPPS_FMT_NONE;
+}
+
+// ---- the precision rule on the device ------------------------------------------------
+// The call's plan in device memory: the batch's format of each Horner step and, for every
+// format code, the number of matrices a launch of that format processes (the batch size if
+// the step runs in it, else 0: the gated candidate launches read these counts).
+constexpr int kSlots = 32;   // format codes: 0..4, MPPS_FMT_F64E(k) = 16 + k
+__host__ __device__ inline int fmt_slot(int f) { return f >= 0 && f < kSlots ? f : kSlots - 1; }
+constexpr int kYAnyF64e = 5;  // ycnt slot: some step runs an emulated product
+struct DevPlan {
+    int fmt[MPPS_MAX_R + 1];
+    int cnt[MPPS_MAX_R + 1][kSlots];
+    int ycnt[8];   // [f], f = 1..4: some step uses low format f (Y's rounded copy); [5]: F64E
+};
+
+__device__ __forceinline__ int exp_above_dev(double x) {   // e with x < 2^e (x > 0), else 0
+    if (!(x > 0.0) || !isfinite(x)) return 0;
+    int e;
+    frexp(x, &e);
+    return e;
+}
+
+// One block.  Per matrix: plan_core on its norms (eta_0..eta_r, ||Y||, ||X|| at stride q),
+// the report fields, and the power-of-two operand scales of its low-precision steps (the
+// host planner's arithmetic: beta_i = eta_i + ||Y|| beta_{i+1} with the multiply and the add
+// rounded separately).
+__global__ void k_plan(const double* __restrict__ norms, int q, int batch, int n, int r, int fold,
+                       Pol P, DevPlan* __restrict__ dp, int* __restrict__ rep_fmt,
+                       double* __restrict__ rep_u, int* __restrict__ rep_nu, double* __restrict__ sY,
+                       double* __restrict__ sP, double* __restrict__ al) {
+    pdl_wait();
+    __shared__ int key[MPPS_MAX_R + 1];
+    __shared__ int sfmt[MPPS_MAX_R + 1];
+    for (int i = threadIdx.x; i <= MPPS_MAX_R; i += blockDim.x) key[i] = 0;
+    __syncthreads();
+    for (int b = threadIdx.x; b < batch; b += blockDim.x) {
+        const double* eta = norms + (size_t)b * q;
+        double u[MPPS_MAX_R + 1];
+        int f[MPPS_MAX_R + 1];
+        int nu = 1;
+        for (int i = 0; i <= MPPS_MAX_R; ++i) { u[i] = 0.0; f[i] = MPPS_FMT_NONE; }
+        plan_core(n, r, fold, eta, eta[r + 1], P, 1.0, u, f, &nu);
+        rep_nu[b] = nu;
+        for (int i = 0; i <= r; ++i) {
+            rep_fmt[(size_t)b * (MPPS_MAX_R + 1) + i] = f[i];
+            rep_u[(size_t)b * (MPPS_MAX_R + 1) + i] = u[i];
+        }
+        for (int i = 1; i <= r; ++i) atomicMax(&key[i], prec_rank(f[i]) * 64 + (f[i] + 1));
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i <= MPPS_MAX_R; i += blockDim.x) {
+        int fi = (i >= 1 && i <= r && key[i] > 0) ? (key[i] & 63) - 1 : MPPS_FMT_NONE;
+        if (fold && i == r) fi = MPPS_FMT_NONE;
+        sfmt[i] = fi;
+        dp->fmt[i] = fi;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < (MPPS_MAX_R + 1) * kSlots; t += blockDim.x) {
+        const int i = t / kSlots, c = t % kSlots;
+        dp->cnt[i][c] = (sfmt[i] != MPPS_FMT_NONE && fmt_slot(sfmt[i]) == c) ? batch : 0;
+    }
+    if (threadIdx.x < 8) {
+        const int f = threadIdx.x;
+        bool used = false;
+        for (int i = 1; i <= r; ++i)
+            used = used || (f >= 1 && f <= 4 && sfmt[i] == f) ||
+                   (f == kYAnyF64e && MPPS_FMT_IS_F64E(sfmt[i]));
+        dp->ycnt[f] = used ? batch : 0;
+    }
+    for (int b = threadIdx.x; b < batch; b += blockDim.x) {
+        const double* eta = norms + (size_t)b * q;
+        const double y = eta[r + 1];
+        const int eY = exp_above_dev(y);
+        for (int f = 0; f < MPPS_NUM_FORMATS; ++f)
+            sY[(size_t)f * batch + b] = f == 0 ? 1.0 : ldexp(1.0, (f == MPPS_FMT_FP8 ? 8 : 0) - eY);
+        double beta = 0.0;
+        sP[b] = 1.0;
+        al[b] = 1.0;
+        for (int i = r; i >= 1; --i) {
+            beta = __dadd_rn(eta[i], __dmul_rn(y, beta));
+            double p = 1.0, a = 1.0;
+            if (is_low(sfmt[i])) {
+                const int T = sfmt[i] == MPPS_FMT_FP8 ? 8 : 0;
+                const int eP = exp_above_dev(beta);
+                p = ldexp(1.0, T - eP);
+                a = ldexp(1.0, eP + eY - 2 * T);
+            }
+            sP[(size_t)i * batch + b] = p;
+            al[(size_t)i * batch + b] = a;
+        }
+    }
+}
+
+// Squaring lists on the device (max_squarings steps): list k holds, in ascending order, the
+// matrices with sigma > k, and count k their number.  A matrix with sigma above the number of
+// steps sets bit 1 of the error word.  One block.
+__global__ void k_sq_lists(const int* __restrict__ sigma, int batch, int steps, int* __restrict__ lists,
+                           int* __restrict__ counts, int* __restrict__ err) {
+    pdl_wait();
+    __shared__ int part[1024];
+    for (int k = 0; k < steps; ++k) {
+        int base = 0;
+        for (int b0 = 0; b0 < batch; b0 += blockDim.x) {
+            const int b = b0 + threadIdx.x;
+            const int on = (b < batch && sigma[b] > k) ? 1 : 0;
+            part[threadIdx.x] = on;
+            __syncthreads();
+            for (int o = 1; o < (int)blockDim.x; o <<= 1) {   // inclusive scan
+                const int v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
+                __syncthreads();
+                part[threadIdx.x] += v;
+                __syncthreads();
+            }
+            if (on) lists[(size_t)k * batch + base + part[threadIdx.x] - 1] = b;
+            const int tot = part[blockDim.x - 1];
+            __syncthreads();
+            base += tot;
+        }
+        if (threadIdx.x == 0) counts[k] = base;
+    }
+    for (int b = threadIdx.x; b < batch; b += blockDim.x)
+        if (sigma[b] > steps) atomicOr(err, 2);
 }
 
 // eq. (3.8): ((s-1) D + sum d_i) / ((s+r-1) D), D = digits of u, d_i = digits of the
@@ -262,6 +407,15 @@ static mpps_status workspace_pool(cudaMemPool_t* out) {
     return MPPS_OK;
 }
 
+static bool is_capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return cs != cudaStreamCaptureStatusNone;
+}
+
 struct DevBuf {
     void* p = nullptr;
     cudaStream_t st = nullptr;
@@ -271,10 +425,17 @@ struct DevBuf {
     mpps_status alloc(size_t bytes, cudaStream_t s) {
         st = s;
         if (bytes == 0) bytes = 256;
-        cudaMemPool_t pool = nullptr;
-        mpps_status rc = workspace_pool(&pool);
-        if (rc) return rc;
-        cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, pool, s);
+        // while the stream is captured into a CUDA graph the allocation becomes a graph
+        // memory node of the device's default pool (its address is fixed for the graph)
+        cudaError_t e;
+        if (is_capturing(s)) {
+            e = cudaMallocAsync(&p, bytes, s);
+        } else {
+            cudaMemPool_t pool = nullptr;
+            mpps_status rc = workspace_pool(&pool);
+            if (rc) return rc;
+            e = cudaMallocFromPoolAsync(&p, bytes, pool, s);
+        }
         if (e != cudaSuccess) {
             p = nullptr;
             cudaGetLastError();
@@ -375,15 +536,23 @@ static mpps_status dev_err_check(DevErr* e, bool wait) {
     }
     e->pending = false;
     if (*e->h) {
+        const int v = *e->h;
         *e->h = 0;
         MPPS_CUDA_TRY(cudaMemset(e->d, 0, sizeof(int)));
-        set_error("a bounded wait in a tensor-core product timed out (device error word set)");
-        return MPPS_ETIMEOUT;
+        if (v & 1) {
+            set_error("a bounded wait in a tensor-core product timed out (device error word set)");
+            return MPPS_ETIMEOUT;
+        }
+        set_error("a matrix needed more squarings than policy.max_squarings (its result is NaN)");
+        return MPPS_ECHECK;
     }
     return MPPS_OK;
 }
 
 static mpps_status dev_err_enqueue(DevErr* e, cudaStream_t st) {
+    // under stream capture the word stays on the device; the next call outside a capture
+    // copies and reports it
+    if (is_capturing(st)) return MPPS_OK;
     std::lock_guard<std::mutex> lk(g_errmu);
     MPPS_CUDA_TRY(cudaMemcpyAsync(e->h, e->d, sizeof(int), cudaMemcpyDeviceToHost, st));
     MPPS_CUDA_TRY(cudaEventRecord(e->ev, st));
@@ -422,12 +591,85 @@ struct Keep {
     std::vector<mpps_report> plans;  // out: per-matrix plans (u_i, norms)
 };
 
+// Formats the rule may pick for Horner step i, before the norms are known (device plan):
+// the working precision first, then, unless the step is fixed to it, every allowed
+// low-precision format and the emulated slice counts below the working precision.
+static std::vector<int> step_candidates(const Pol& P, int r, bool fold, int i) {
+    std::vector<int> c;
+    if (fold && i == r) return c;
+    c.push_back(P.f64k > 0 ? MPPS_FMT_F64E(P.f64k) : MPPS_FMT_FP64);
+    if (P.mode == MPPS_FIXED_FP64 || (P.mode == MPPS_MIXED_NS && i <= P.floor_steps)) return c;
+    for (int F : {MPPS_FMT_BF16X3, MPPS_FMT_TF32, MPPS_FMT_BF16, MPPS_FMT_FP8})
+        if ((P.formats >> F) & 1u) c.push_back(F);
+    for (int k = kF64eMinRung; k < P.f64k; ++k) c.push_back(MPPS_FMT_F64E(k));
+    return c;
+}
+
+// Page-locked staging for the early read of sigma (device plan), one per host thread and
+// device, with the event that marks its copy.
+struct SigmaStage {
+    int* h = nullptr;
+    size_t cap = 0;
+    cudaEvent_t ev = nullptr;
+    ~SigmaStage() {
+        if (h) cudaFreeHost(h);
+        if (ev) cudaEventDestroy(ev);
+    }
+};
+static thread_local SigmaStage t_sig[64];
+
+// Streams of a grouped call's buckets: created once per device (non-blocking), shared by
+// the calls on that device; every use forks from and joins the caller's stream.
+constexpr int kAuxStreams = 8;
+static std::mutex g_auxmu;
+static cudaStream_t g_aux[64][kAuxStreams];
+
+static mpps_status aux_streams(int k, std::vector<cudaStream_t>* out) {
+    int dev = 0;
+    MPPS_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) {
+        set_error("device index %d out of range", dev);
+        return MPPS_ENOTSUP;
+    }
+    std::lock_guard<std::mutex> lk(g_auxmu);
+    out->clear();
+    for (int j = 0; j < k && j < kAuxStreams; ++j) {
+        if (!g_aux[dev][j]) MPPS_CUDA_TRY(cudaStreamCreateWithFlags(&g_aux[dev][j], cudaStreamNonBlocking));
+        out->push_back(g_aux[dev][j]);
+    }
+    if (out->empty()) {
+        set_error("no stream for the grouped call");
+        return MPPS_ECUDA;
+    }
+    return MPPS_OK;
+}
+
+static mpps_status sigma_stage(int batch, SigmaStage** out) {
+    int dev = 0;
+    MPPS_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) {
+        set_error("device index %d out of range", dev);
+        return MPPS_ENOTSUP;
+    }
+    SigmaStage& S = t_sig[dev];
+    if (S.cap < (size_t)batch) {
+        if (S.h) MPPS_CUDA_TRY(cudaFreeHost(S.h));
+        S.h = nullptr;
+        MPPS_CUDA_TRY(cudaHostAlloc(&S.h, sizeof(int) * (size_t)batch, cudaHostAllocDefault));
+        S.cap = (size_t)batch;
+    }
+    if (!S.ev) MPPS_CUDA_TRY(cudaEventCreateWithFlags(&S.ev, cudaEventDisableTiming));
+    *out = &S;
+    return MPPS_OK;
+}
+
 // ---- the PS evaluation --------------------------------------------------------------
 // Evaluates p(X) for a device batch; for expm, X = 2^-sigma A and sigma squarings follow.
 // keep (not for expm): the power table and the Horner iterates go where *keep says.
 static mpps_status eval_device(const double* coeffs, int m, const double* dA, int n, int batch,
                                const Pol& pol, double* dOut, mpps_report* rep, cudaStream_t st,
-                               bool expm, bool sync_at_end, Keep* keep = nullptr) {
+                               bool expm, bool sync_at_end, Keep* keep = nullptr,
+                               const int* sig_dev = nullptr, const int* sig_host = nullptr) {
     const long long nn = (long long)n * n;
     // ---- m == 0: p = b_0 I
     if (m == 0) {
@@ -453,6 +695,9 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
     // Variable s (Algorithm 3.1, fix_params false): s may grow after the powers, so the
     // power table has room for s_cap powers and the norm buffers for every s up to it.
     const bool var_s = pol.var_s && pol.s <= 0 && pol.mode != MPPS_FIXED_FP64 && m >= 2 && !keep;
+    // Device plan: the rule runs on the GPU (k_plan); not with variable s or a tape
+    const bool dp = pol.dplan && !var_s && !keep;
+    const int sq_steps = (dp && expm) ? pol.max_sq : 0;   // squarings launched blind (0: read)
     const int s0 = s;
     const int s_cap = var_s ? std::min(std::min(m, MPPS_MAX_S), 2 * s0) : s;
     int r = m / s;
@@ -473,6 +718,15 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
     int *d_sigma, *d_err, *d_bidx, *eA = nullptr, *eB = nullptr, *eY = nullptr;
     __nv_bfloat16 *slA = nullptr, *slB = nullptr, *slY = nullptr;
     char* split = nullptr;   // split-K scratch of the emulated products
+    DevPlan* d_plan = nullptr;                      // device plan (dp)
+    int *d_rfmt = nullptr, *d_rnu = nullptr, *d_sql = nullptr, *d_sqc = nullptr;
+    double *d_ru = nullptr, *d_sc = nullptr;
+    // Row / column maxima recorded by the emulated products' epilogues for the slicing of
+    // the matrices they write (one buffer per matrix written, zeroed once): powers X_2..X_s
+    // (rows), Y (columns), Horner iterates P_0..P_r (rows).  Not with variable s.
+    const bool pre = K > 0 && !var_s;
+    int* mxbuf = nullptr;
+    const size_t mx_count = pre ? (size_t)(s + 1 + r + 1 + 1) * batch * n : 0;
     auto layout1 = [&](Arena& a) {
         d_coef = a.take<double>(m + 1);
         pw = keep ? keep->pw : a.take<double>((size_t)batch * pw_bs);
@@ -492,6 +746,18 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
             eY = a.take<int>((size_t)batch * n);
             tmpT = a.take<double>((size_t)batch * nn);
             split = a.take<char>(f64e_split_bytes());
+            if (pre) mxbuf = a.take<int>(mx_count);
+        }
+        if (dp) {
+            d_plan = (DevPlan*)a.take<char>(sizeof(DevPlan));
+            d_rfmt = a.take<int>((size_t)batch * (MPPS_MAX_R + 1));
+            d_ru = a.take<double>((size_t)batch * (MPPS_MAX_R + 1));
+            d_rnu = a.take<int>(batch);
+            d_sc = a.take<double>((size_t)(MPPS_NUM_FORMATS + 2 * (r + 1)) * batch);
+            if (sq_steps > 0) {
+                d_sql = a.take<int>((size_t)sq_steps * batch);
+                d_sqc = a.take<int>(sq_steps);
+            }
         }
     };
     layout1(L);
@@ -502,7 +768,12 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
     L.off = 0;
     layout1(L);
     if (split) MPPS_CUDA_TRY(cudaMemsetAsync(split, 0, f64e_split_flag_bytes(), st));
-    MPPS_CUDA_TRY(cudaMemcpyAsync(d_coef, coeffs, sizeof(double) * (m + 1), cudaMemcpyHostToDevice, st));
+    if (mxbuf) MPPS_CUDA_TRY(cudaMemsetAsync(mxbuf, 0, sizeof(int) * mx_count, st));
+    const size_t bn = (size_t)batch * n;
+    auto mx_pow = [&](int j) { return mxbuf + (size_t)j * bn; };                // rows of X_j
+    auto mx_iter = [&](int i) { return mxbuf + (size_t)(s + 1 + i) * bn; };     // rows of P_i
+    int* mx_ycol = mxbuf ? mxbuf + (size_t)(s + 1 + r + 1) * bn : nullptr;
+    if ((rc = launch_fill(d_coef, coeffs, m + 1, st))) return rc;
     DevErr* derr = nullptr;
     if ((rc = dev_err_get(&derr))) return rc;
     if ((rc = dev_err_check(derr, false))) return rc;
@@ -516,10 +787,24 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
 
     // ---- a1: scaling (expm) or plain copy into X_1
     std::vector<int> sigma(batch, 0);
-    if (expm) {
+    SigmaStage* sgs = nullptr;
+    if (expm && sig_dev) {   // sigma computed by the caller (device copy, and host copy)
+        MPPS_CUDA_TRY(cudaMemcpyAsync(d_sigma, sig_dev, sizeof(int) * batch, cudaMemcpyDeviceToDevice, st));
+        if (sig_host) sigma.assign(sig_host, sig_host + batch);
+        rc = launch_scale_copy(dA, nn, pw, pw_bs, n, batch, d_sigma, st);
+    } else if (expm) {
         // sigma = max(0, ceil(log2 ||A||_1)) on the device; read back with the block norms
+        // (device plan: copied to page-locked memory now and waited for before the Horner
+        // steps, by which time the GPU has long passed it; or not read at all)
         rc = launch_norm1(dA, nn, n, batch, partial, d_anorm, st);
         if (!rc) rc = launch_sigma(d_anorm, batch, d_sigma, st);
+        if (!rc && dp && sq_steps == 0) {
+            if (!(rc = sigma_stage(batch, &sgs)) && sgs) {
+                MPPS_CUDA_TRY(cudaMemcpyAsync(sgs->h, d_sigma, sizeof(int) * batch,
+                                              cudaMemcpyDeviceToHost, st));
+                MPPS_CUDA_TRY(cudaEventRecord(sgs->ev, st));
+            }
+        }
         if (!rc) rc = launch_scale_copy(dA, nn, pw, pw_bs, n, batch, d_sigma, st);
     } else {
         rc = launch_scale_copy(dA, nn, pw, pw_bs, n, batch, nullptr, st);
@@ -534,8 +819,15 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
     auto power = [&](int j) -> mpps_status {   // X_j = X_{j-1} X_1
         Epilogue ep = epilogue_plain(pw + (long long)(j - 1) * nn, pw_bs);
         if (K > 0) {
-            mpps_status r1 = launch_slice_rows(pw + (long long)(j - 2) * nn, pw_bs, n, batch, K,
-                                               slA, eA, st);
+            if (pre) {   // X_j's rows feed the next power, Y's columns the Horner steps
+                if (j < s) ep.rmax = mx_pow(j);
+                else ep.cmax = mx_ycol;
+            }
+            const double* Xa = pw + (long long)(j - 2) * nn;
+            mpps_status r1 = (pre && j > 2)
+                                 ? launch_slice_rows_pre(Xa, pw_bs, n, batch, K, slA, eA,
+                                                         mx_pow(j - 1), nullptr, st)
+                                 : launch_slice_rows(Xa, pw_bs, n, batch, K, slA, eA, st);
             if (!r1)
                 r1 = launch_gemm_f64e(K, slA, K, eA, slB, K, eB, n, batch, batch, ep, d_err, st,
                                       nullptr, split);
@@ -589,42 +881,76 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
     else
         rc = launch_block_norms(pw, pw_bs, n, batch, s, m, d_coef, partial, norms, st);
     if (rc) return rc;
-    std::vector<double> hn((size_t)batch * q);
-    MPPS_CUDA_TRY(cudaMemcpyAsync(hn.data(), norms, sizeof(double) * hn.size(),
-                                  cudaMemcpyDeviceToHost, st));
-    if (expm)
-        MPPS_CUDA_TRY(cudaMemcpyAsync(sigma.data(), d_sigma, sizeof(int) * batch,
-                                      cudaMemcpyDeviceToHost, st));
-    MPPS_CUDA_TRY(cudaStreamSynchronize(st));
-
-    // ---- a4: plan per matrix; a batch runs each step in the most precise format any of
-    // its matrices asks for
+    std::vector<double> hn;
     std::vector<mpps_report> rp(batch);
     Pol pol_s = pol;
     pol_s.s = s;
-    for (int b = 0; b < batch; ++b) {
-        rc = plan_one(m, n, &hn[(size_t)b * q], hn[(size_t)b * q + r + 1], pol_s, &rp[b]);
-        if (rc) return rc;
-        rp[b].normX = hn[(size_t)b * q + r + 2];
-        rp[b].sigma = sigma[b];
-    }
     int fmt[MPPS_MAX_R + 1];
     bool any_f64e = false;
-    for (int i = 1; i <= r; ++i) {
-        int f = rp[0].fmt[i];
-        for (int b = 1; b < batch; ++b)
-            if (prec_rank(rp[b].fmt[i]) > prec_rank(f)) f = rp[b].fmt[i];
-        fmt[i] = (fold && i == r) ? MPPS_FMT_NONE : f;
-        if (MPPS_FMT_IS_F64E(fmt[i])) any_f64e = true;
-    }
     bool used[MPPS_NUM_FORMATS] = {false, false, false, false, false};
-    int max_es = 1;
-    for (int i = 1; i <= r; ++i)
-        if (is_low(fmt[i])) {
-            used[fmt[i]] = true;
-            max_es = std::max(max_es, low_elem_bytes(fmt[i]));
+    // device plan: the formats each step may take (fmt[i] is MPPS_FMT_DEVICE unless one)
+    std::vector<std::vector<int>> cand(r + 1);
+    if (!dp) {
+        hn.resize((size_t)batch * q);
+        MPPS_CUDA_TRY(cudaMemcpyAsync(hn.data(), norms, sizeof(double) * hn.size(),
+                                      cudaMemcpyDeviceToHost, st));
+        if (expm)
+            MPPS_CUDA_TRY(cudaMemcpyAsync(sigma.data(), d_sigma, sizeof(int) * batch,
+                                          cudaMemcpyDeviceToHost, st));
+        MPPS_CUDA_TRY(cudaStreamSynchronize(st));
+
+        // ---- a4: plan per matrix; a batch runs each step in the most precise format any
+        // of its matrices asks for
+        for (int b = 0; b < batch; ++b) {
+            rc = plan_one(m, n, &hn[(size_t)b * q], hn[(size_t)b * q + r + 1], pol_s, &rp[b]);
+            if (rc) return rc;
+            rp[b].normX = hn[(size_t)b * q + r + 2];
+            rp[b].sigma = sigma[b];
         }
+        for (int i = 1; i <= r; ++i) {
+            int f = rp[0].fmt[i];
+            for (int b = 1; b < batch; ++b)
+                if (prec_rank(rp[b].fmt[i]) > prec_rank(f)) f = rp[b].fmt[i];
+            fmt[i] = (fold && i == r) ? MPPS_FMT_NONE : f;
+            if (MPPS_FMT_IS_F64E(fmt[i])) any_f64e = true;
+            if (fmt[i] != MPPS_FMT_NONE) cand[i].assign(1, fmt[i]);
+        }
+    } else {
+        // ---- a4 on the device: the same rule (plan_core) per matrix, the batch's formats,
+        // the gate counts and the operand scales; nothing is read back
+        {
+            mpps_report probe;   // validates s, r and f64_slices as the host planner does
+            std::vector<double> ones(r + 1, 1.0);
+            if ((rc = plan_one(m, n, ones.data(), 1.0, pol_s, &probe))) return rc;
+        }
+        ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
+        MPPS_CUDA_TRY(launch_pdl(k_plan, dim3(1), dim3(256), 0, st, (const double*)norms, q, batch, n,
+                                 r, (int)fold, pol_s, d_plan, d_rfmt, d_ru, d_rnu, d_sc,
+                                 d_sc + (size_t)MPPS_NUM_FORMATS * batch,
+                                 d_sc + (size_t)(MPPS_NUM_FORMATS + r + 1) * batch));
+        MPPS_LAUNCH_CHECK();
+        for (int i = 1; i <= r; ++i) {
+            cand[i] = step_candidates(pol_s, r, fold, i);
+            fmt[i] = cand[i].empty() ? MPPS_FMT_NONE
+                                     : (cand[i].size() == 1 ? cand[i][0] : MPPS_FMT_DEVICE);
+            for (int f : cand[i]) if (MPPS_FMT_IS_F64E(f)) any_f64e = true;
+        }
+    }
+    for (int i = 1; i <= r; ++i)
+        for (int f : cand[i]) if (is_low(f)) used[f] = true;
+    int max_es = 1;
+    for (int f = 1; f < MPPS_NUM_FORMATS; ++f)
+        if (used[f]) max_es = std::max(max_es, low_elem_bytes(f));
     const bool any_low = used[1] || used[2] || used[3] || used[4];
+    // gate of candidate f of step i (null when the step has a single format)
+    auto gate = [&](int i, int f) -> const int* {
+        if (!dp || cand[i].size() <= 1) return nullptr;
+        return &d_plan->cnt[i][fmt_slot(f)];
+    };
+    auto has_low_copy = [&](int i) {   // P_i may need a rounded copy from its producer
+        for (int f : cand[i]) if (is_low(f) && f != MPPS_FMT_FP8) return true;
+        return false;
+    };
 
     // ---- phase-2 workspace: rounded copies and their power-of-two scales
     const int lld = low_ld(n);
@@ -652,8 +978,9 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
             xcolY = a.take<int>((size_t)batch * n);
             cmax8 = a.take<unsigned long long>((size_t)batch * n);
         }
-        // one contiguous block (filled by a single copy): sY | sP | alpha
-        d_sY = a.take<double>((size_t)(MPPS_NUM_FORMATS + 2 * (r + 1)) * batch);
+        // one contiguous block (filled by a single copy, or by the device plan): sY | sP |
+        // alpha
+        d_sY = dp ? d_sc : a.take<double>((size_t)(MPPS_NUM_FORMATS + 2 * (r + 1)) * batch);
         d_sP = d_sY ? d_sY + (size_t)MPPS_NUM_FORMATS * batch : nullptr;
         d_alpha = d_sP ? d_sP + (size_t)(r + 1) * batch : nullptr;
     };
@@ -665,6 +992,8 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
         L2.base = (char*)ws2.p;
         L2.off = 0;
         layout2(L2);
+    }
+    if (any_low && !dp) {
         std::vector<double> hs((size_t)(MPPS_NUM_FORMATS + 2 * (r + 1)) * batch, 1.0);
         double* h_sY = hs.data();
         double* h_sP = h_sY + (size_t)MPPS_NUM_FORMATS * batch;
@@ -689,26 +1018,58 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
         }
         MPPS_CUDA_TRY(cudaMemcpyAsync(d_sY, hs.data(), sizeof(double) * hs.size(),
                                       cudaMemcpyHostToDevice, st));
+    }
+    if (any_low) {   // Y's rounded copies (device plan: each only if a step uses its format)
+        const int* yg[MPPS_NUM_FORMATS] = {};
+        if (dp)
+            for (int f = 1; f < MPPS_NUM_FORMATS; ++f) yg[f] = &d_plan->ycnt[f];
         for (int f = 1; f < MPPS_NUM_FORMATS; ++f)
             if (used[f]) {
                 rc = f == MPPS_FMT_FP8
                          ? launch_convert_scaled(f, pw + (long long)(s - 1) * nn, pw_bs, n, batch,
                                                  Ylo_hi[f], nullptr, low_bs, lld, low_target_exp(f),
-                                                 true, xcolY, cmax8, st)
+                                                 true, xcolY, cmax8, st, yg[f])
                          : launch_convert(f, pw + (long long)(s - 1) * nn, pw_bs, n, batch, Ylo_hi[f],
-                                          Ylo_lo[f], low_bs, lld, d_sY + (size_t)f * batch, true, st);
+                                          Ylo_lo[f], low_bs, lld, d_sY + (size_t)f * batch, true, st,
+                                          yg[f]);
                 if (rc) return rc;
             }
     }
 
     if (any_f64e) {   // Y^T slices for every emulated Horner step (first k planes used)
-        rc = slice_cols(pw + (long long)(s - 1) * nn, pw_bs, K, slY, eY);
+        // (device plan: gated unless some step runs an emulated product whatever the norms)
+        bool fixed_f64e = !dp;
+        for (int i = 1; i <= r && !fixed_f64e; ++i)
+            fixed_f64e = cand[i].size() == 1 && MPPS_FMT_IS_F64E(cand[i][0]);
+        const int* yg = fixed_f64e ? nullptr : &d_plan->ycnt[kYAnyF64e];
+        rc = (pre && s >= 2) ? launch_slice_cols_pre(pw + (long long)(s - 1) * nn, pw_bs, n, batch, K,
+                                                     slY, eY, mx_ycol, st, yg)
+                             : launch_slice_cols(pw + (long long)(s - 1) * nn, pw_bs, n, batch, K, slY, eY,
+                                                 (unsigned long long*)tmpT, st, yg);
         if (rc) return rc;
     }
 
     // ---- a5/a6: Horner in Y with the block sums fused into the product epilogues
     int sig_max = 0;
-    for (int b = 0; b < batch; ++b) sig_max = std::max(sig_max, sigma[b]);
+    if (sgs) {   // device plan: the early copy of sigma (the GPU is well past it by now)
+        MPPS_CUDA_TRY(cudaEventSynchronize(sgs->ev));
+        for (int b = 0; b < batch; ++b) sigma[b] = sgs->h[b];
+    }
+    const bool blind = sq_steps > 0 && !(sig_dev && sig_host);
+    if (blind) sig_max = sq_steps;   // squarings launched blind, per-matrix on the GPU
+    else
+        for (int b = 0; b < batch; ++b) sig_max = std::max(sig_max, sigma[b]);
+    // row and column maxima of Q_0 .. Q_{sigma-1}, recorded for the squarings' slicing
+    DevBuf wsq;
+    int* sqmx = nullptr;
+    if (pre && expm && sig_max > 0) {
+        const size_t cnt = (size_t)2 * sig_max * bn;
+        if ((rc = wsq.alloc(sizeof(int) * cnt, st))) return rc;
+        sqmx = (int*)wsq.p;
+        MPPS_CUDA_TRY(cudaMemsetAsync(sqmx, 0, sizeof(int) * cnt, st));
+    }
+    auto mx_sq_row = [&](int k) { return sqmx + (size_t)(2 * k) * bn; };
+    auto mx_sq_col = [&](int k) { return sqmx + (size_t)(2 * k + 1) * bn; };
     double* Pbuf[2] = {Pb0, Pb1};
     double* dst0 = (expm && sig_max > 0) ? Pb0 : dOut;
     // where each Horner iterate P_j is written (and read by step j): ping-pong buffers, or the
@@ -730,8 +1091,10 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
         if (i - 1 == 0 && qform) ep.coef[0] -= 1.0;
         ep.pw = pw;
         ep.pw_bstride = pw_bs;
-        if (i - 1 >= 1 && is_low(fmt[i - 1]) && fmt[i - 1] != MPPS_FMT_FP8) {
+        const bool dev_copy = i - 1 >= 1 && fmt[i - 1] == MPPS_FMT_DEVICE && has_low_copy(i - 1);
+        if (dev_copy || (i - 1 >= 1 && is_low(fmt[i - 1]) && fmt[i - 1] != MPPS_FMT_FP8)) {
             ep.low_fmt = fmt[i - 1];
+            if (dev_copy) ep.low_fmt_dev = &d_plan->fmt[i - 1];
             ep.low_hi = Pl_hi[(i - 1) & 1];
             ep.low_lo = Pl_lo[(i - 1) & 1];
             ep.low_bstride = low_bs;
@@ -741,6 +1104,8 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
         return ep;
     };
 
+    // which Horner iterates had their row maxima recorded by the product that wrote them
+    bool iter_mx[MPPS_MAX_R + 2] = {false};
     int i_start;
     if (fold) {
         // B_r = b_m I: P_{r-1} = B_{r-1} + b_m Y, no product
@@ -756,8 +1121,10 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
         ep.pw = pw;
         ep.pw_bstride = pw_bs;
         ep.alpha = 0.0;
-        if (is_low(fmt[r]) && fmt[r] != MPPS_FMT_FP8) {
+        const bool dev_copy = fmt[r] == MPPS_FMT_DEVICE && has_low_copy(r);
+        if (dev_copy || (is_low(fmt[r]) && fmt[r] != MPPS_FMT_FP8)) {
             ep.low_fmt = fmt[r];
+            if (dev_copy) ep.low_fmt_dev = &d_plan->fmt[r];
             ep.low_hi = Pl_hi[r & 1];
             ep.low_lo = Pl_lo[r & 1];
             ep.low_bstride = low_bs;
@@ -769,59 +1136,101 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
     }
     if (rc) return rc;
     for (int i = i_start; i >= 1; --i) {
-        Epilogue ep = make_ep(i);
-        if (fmt[i] == MPPS_FMT_FP64) {
-            rc = launch_gemm_f64(Pdst[i], nn, Y, pw_bs, n, batch, ep, st);
-        } else if (MPPS_FMT_IS_F64E(fmt[i])) {
-            const int k = MPPS_F64E_SLICES(fmt[i]);
-            rc = launch_slice_rows(Pdst[i], nn, n, batch, k, slA, eA, st);
-            if (!rc)
-                rc = launch_gemm_f64e(k, slA, k, eA, slY, K, eY, n, batch, batch, ep, d_err, st,
-                                      nullptr, split);
-        } else if (fmt[i] == MPPS_FMT_FP8) {
-            // per-row scales of P_i, per-column scales of Y (the paper's scaled low-precision
-            // products, with the scales as fine as a row / a column)
-            rc = launch_convert_scaled(fmt[i], Pdst[i], nn, n, batch, Pl_hi[i & 1], nullptr,
-                                       low_bs, lld, low_target_exp(fmt[i]), false, xrowP, nullptr, st);
-            ep.row_exp = xrowP;
-            ep.col_exp = xcolY;
-            if (!rc)
-                rc = launch_gemm_tc(fmt[i], Pl_hi[i & 1], Pl_lo[i & 1], Ylo_hi[fmt[i]], Ylo_lo[fmt[i]],
-                                    low_bs, low_bs, lld, n, batch, ep, d_err, st);
-        } else {
-            ep.alpha_b = d_alpha + (size_t)i * batch;
-            rc = launch_gemm_tc(fmt[i], Pl_hi[i & 1], Pl_lo[i & 1], Ylo_hi[fmt[i]], Ylo_lo[fmt[i]],
-                                low_bs, low_bs, lld, n, batch, ep, d_err, st);
+        // one launch per format the step may take; with the device plan all but the chosen
+        // one find a zero count and return at once
+        for (int f : cand[i]) {
+            Epilogue ep = make_ep(i);
+            const int* g = gate(i, f);
+            ep.dcount = g;
+            if (f == MPPS_FMT_FP64) {
+                rc = launch_gemm_f64(Pdst[i], nn, Y, pw_bs, n, batch, ep, st);
+            } else if (MPPS_FMT_IS_F64E(f)) {
+                const int k = MPPS_F64E_SLICES(f);
+                // P_{i-1} feeds an emulated step (or, as Q_0, the squarings): record its maxima
+                // (only when this step's format is certain, so that they are always written)
+                const bool certain = cand[i].size() == 1;
+                if (pre && certain &&
+                    ((i - 1 >= 1 && MPPS_FMT_IS_F64E(fmt[i - 1])) || (i == 1 && qform))) {
+                    if (i == 1) {        // Q_0 of the squarings: rows and columns
+                        ep.rmax = mx_sq_row(0);
+                        ep.cmax = mx_sq_col(0);
+                    } else {
+                        ep.rmax = mx_iter(i - 1);
+                    }
+                    iter_mx[i - 1] = true;
+                }
+                rc = iter_mx[i] ? launch_slice_rows_pre(Pdst[i], nn, n, batch, k, slA, eA, mx_iter(i),
+                                                        nullptr, st, g)
+                                : launch_slice_rows(Pdst[i], nn, n, batch, k, slA, eA, st, g);
+                if (!rc)
+                    rc = launch_gemm_f64e(k, slA, k, eA, slY, K, eY, n, batch, batch, ep, d_err, st,
+                                          nullptr, split);
+            } else if (f == MPPS_FMT_FP8) {
+                // per-row scales of P_i, per-column scales of Y (the paper's scaled low-precision
+                // products, with the scales as fine as a row / a column)
+                rc = launch_convert_scaled(f, Pdst[i], nn, n, batch, Pl_hi[i & 1], nullptr, low_bs,
+                                           lld, low_target_exp(f), false, xrowP, nullptr, st, g);
+                ep.row_exp = xrowP;
+                ep.col_exp = xcolY;
+                if (!rc)
+                    rc = launch_gemm_tc(f, Pl_hi[i & 1], Pl_lo[i & 1], Ylo_hi[f], Ylo_lo[f], low_bs,
+                                        low_bs, lld, n, batch, ep, d_err, st);
+            } else {
+                ep.alpha_b = d_alpha + (size_t)i * batch;
+                rc = launch_gemm_tc(f, Pl_hi[i & 1], Pl_lo[i & 1], Ylo_hi[f], Ylo_lo[f], low_bs,
+                                    low_bs, lld, n, batch, ep, d_err, st);
+            }
+            if (rc) return rc;
         }
-        if (rc) return rc;
     }
 
     // ---- a7: squarings (eq. (3.6)), FP64, per-matrix counts
     if (expm && sig_max > 0) {
-        std::vector<int> lists((size_t)sig_max * batch);
         std::vector<int> counts(sig_max, 0);
-        for (int k = 0; k < sig_max; ++k)
-            for (int b = 0; b < batch; ++b)
-                if (sigma[b] > k) lists[(size_t)k * batch + counts[k]++] = b;
         int* d_lists = d_bidx;
+        const int* d_counts = nullptr;   // device plan with blind squarings: counts on the GPU
         DevBuf extra;
-        if ((size_t)sig_max * batch > (size_t)batch * 64) {
-            rc = extra.alloc(sizeof(int) * lists.size(), st);
-            if (rc) return rc;
-            d_lists = (int*)extra.p;
+        if (blind) {
+            ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
+            MPPS_CUDA_TRY(launch_pdl(k_sq_lists, dim3(1), dim3(1024), 0, st, (const int*)d_sigma, batch,
+                                     sq_steps, d_sql, d_sqc, d_err));
+            MPPS_LAUNCH_CHECK();
+            d_lists = d_sql;
+            d_counts = d_sqc;
+            for (int k = 0; k < sig_max; ++k) counts[k] = batch;
+        } else {
+            std::vector<int> lists((size_t)sig_max * batch);
+            for (int k = 0; k < sig_max; ++k)
+                for (int b = 0; b < batch; ++b)
+                    if (sigma[b] > k) lists[(size_t)k * batch + counts[k]++] = b;
+            if ((size_t)sig_max * batch > (size_t)batch * 64) {
+                rc = extra.alloc(sizeof(int) * lists.size(), st);
+                if (rc) return rc;
+                d_lists = (int*)extra.p;
+            }
+            if ((rc = launch_fill_bytes(d_lists, lists.data(), sizeof(int) * lists.size(), st)))
+                return rc;
         }
-        MPPS_CUDA_TRY(cudaMemcpyAsync(d_lists, lists.data(), sizeof(int) * lists.size(),
-                                      cudaMemcpyHostToDevice, st));
         for (int k = 0; k < sig_max; ++k) {
             Epilogue ep = epilogue_plain(Pbuf[(k + 1) & 1], nn);
+            ep.dcount = d_counts ? d_counts + k : nullptr;
             if (qform) {   // Q_{k+1} = Q_k Q_k + 2 Q_k
                 ep.add = Pbuf[k & 1];
                 ep.add_bstride = nn;
                 ep.add_coef = 2.0;
             }
             if (K > 0) {
-                rc = launch_slice_rows(Pbuf[k & 1], nn, n, batch, K, slA, eA, st);
-                if (!rc) rc = slice_cols(Pbuf[k & 1], nn, K, slB, eB);
+                const bool have = pre && (k == 0 ? iter_mx[0] : true);
+                if (pre && k + 1 < sig_max) {   // Q_{k+1} is sliced for the next squaring
+                    ep.rmax = mx_sq_row(k + 1);
+                    ep.cmax = mx_sq_col(k + 1);
+                }
+                rc = have ? launch_slice_rows_pre(Pbuf[k & 1], nn, n, batch, K, slA, eA, mx_sq_row(k),
+                                                  nullptr, st)
+                          : launch_slice_rows(Pbuf[k & 1], nn, n, batch, K, slA, eA, st);
+                if (!rc)
+                    rc = have ? launch_slice_cols_pre(Pbuf[k & 1], nn, n, batch, K, slB, eB, mx_sq_col(k), st)
+                              : slice_cols(Pbuf[k & 1], nn, K, slB, eB);
                 if (!rc)
                     rc = launch_gemm_f64e(K, slA, K, eA, slB, K, eB, n, counts[k], batch, ep, d_err,
                                           st, d_lists + (size_t)k * batch, split);
@@ -831,13 +1240,48 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
             }
             if (rc) return rc;
         }
-        rc = launch_select_copy(Pb0, Pb1, d_sigma, dOut, n, batch, qform ? 1.0 : 0.0, st);
+        rc = launch_select_copy(Pb0, Pb1, d_sigma, dOut, n, batch, qform ? 1.0 : 0.0, st,
+                                blind ? sq_steps : -1);
         if (rc) return rc;
     }
 
-    if (any_low || K > 0) {
+    // device plan: what the GPU planned, read back only when a report is asked for
+    std::vector<int> dfmt;
+    if (dp && rep) {
+        std::vector<int> rf((size_t)batch * (MPPS_MAX_R + 1)), rnu(batch);
+        std::vector<double> ru((size_t)batch * (MPPS_MAX_R + 1));
+        hn.resize((size_t)batch * q);
+        dfmt.resize(MPPS_MAX_R + 1);
+        MPPS_CUDA_TRY(cudaMemcpyAsync(dfmt.data(), d_plan->fmt, sizeof(int) * dfmt.size(),
+                                      cudaMemcpyDeviceToHost, st));
+        MPPS_CUDA_TRY(cudaMemcpyAsync(rf.data(), d_rfmt, sizeof(int) * rf.size(), cudaMemcpyDeviceToHost, st));
+        MPPS_CUDA_TRY(cudaMemcpyAsync(ru.data(), d_ru, sizeof(double) * ru.size(), cudaMemcpyDeviceToHost, st));
+        MPPS_CUDA_TRY(cudaMemcpyAsync(rnu.data(), d_rnu, sizeof(int) * batch, cudaMemcpyDeviceToHost, st));
+        MPPS_CUDA_TRY(cudaMemcpyAsync(hn.data(), norms, sizeof(double) * hn.size(),
+                                      cudaMemcpyDeviceToHost, st));
+        if (expm)
+            MPPS_CUDA_TRY(cudaMemcpyAsync(sigma.data(), d_sigma, sizeof(int) * batch,
+                                          cudaMemcpyDeviceToHost, st));
+        MPPS_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int b = 0; b < batch; ++b) {
+            mpps_report& R = rp[b];
+            memset(&R, 0, sizeof(R));
+            R.s = s; R.r = r; R.fold = fold ? 1 : 0; R.nu = rnu[b];
+            for (int i = 0; i <= MPPS_MAX_R; ++i) R.fmt[i] = MPPS_FMT_NONE;
+            for (int i = 0; i <= r; ++i) {
+                R.normB[i] = hn[(size_t)b * q + i];
+                R.u[i] = i >= 1 ? ru[(size_t)b * (MPPS_MAX_R + 1) + i] : 0.0;
+            }
+            R.normY = hn[(size_t)b * q + r + 1];
+            R.normX = hn[(size_t)b * q + r + 2];
+            R.sigma = sigma[b];
+        }
+        for (int i = 1; i <= r; ++i) fmt[i] = dfmt[i];
+    }
+
+    if (any_low || K > 0 || sq_steps > 0) {
         if ((rc = dev_err_enqueue(derr, st))) return rc;
-        if (sync_at_end && (rc = dev_err_check(derr, true))) return rc;
+        if ((sync_at_end || (dp && rep)) && (rc = dev_err_check(derr, true))) return rc;
     }
 
     if (keep) {
@@ -898,6 +1342,8 @@ void mpps_policy_default(mpps_policy* p) {
     p->f64_slices = 0;
     p->variable_s = 0;
     p->adjoint_recompute = 0;
+    p->device_plan = 0;
+    p->max_squarings = 0;
 }
 
 mpps_status mpps_release_workspace(void) {
@@ -1046,6 +1492,8 @@ mpps_status expm_taylor_ss_grouped(const mpps_group_item* items, int count,
     }
     cudaStream_t st = (cudaStream_t)stream;
     Pol P = resolve(policy);
+    P.dplan = 1;   // every bucket planned on the device: no read-back between buckets
+    P.var_s = 0;
     // buckets keyed by (padded order, degree), in first-appearance order
     struct Bucket { int n_pad, m; std::vector<int> idx; };
     std::vector<Bucket> buckets;
@@ -1057,43 +1505,106 @@ mpps_status expm_taylor_ss_grouped(const mpps_group_item* items, int count,
         if (k == buckets.size()) buckets.push_back({np, m, {}});
         buckets[k].idx.push_back(i);
     }
-    for (const Bucket& bk : buckets) {
+    const int nb = (int)buckets.size();
+    struct Work {
+        DevBuf buf;
+        PadItem* d_list = nullptr;
+        double *dA = nullptr, *dO = nullptr, *partial = nullptr, *anorm = nullptr;
+        int* d_sig = nullptr;
+        std::vector<double> c;
+    };
+    std::vector<Work> wk(nb);
+    mpps_status rc = MPPS_OK;
+    // ---- phase A, on the caller's stream: every bucket gathered into its zero-padded batch,
+    // ||A||_1 and sigma per matrix (eq. (3.6))
+    for (int k = 0; k < nb; ++k) {
+        const Bucket& bk = buckets[k];
+        Work& w = wk[k];
         const int cnt = (int)bk.idx.size();
         if (cnt > 65535) {
             set_error("expm_taylor_ss_grouped: more than 65535 items of one size and degree");
             return MPPS_EINVAL;
         }
         const long long nn = (long long)bk.n_pad * bk.n_pad;
-        std::vector<double> c(bk.m + 1);
+        w.c.resize(bk.m + 1);
         long double f = 1.0L;
         for (int i = 0; i <= bk.m; ++i) {
             if (i > 0) f /= (long double)i;
-            c[i] = (double)f;
+            w.c[i] = (double)f;
         }
         std::vector<PadItem> list(cnt);
         for (int j = 0; j < cnt; ++j) {
             const mpps_group_item& it = items[bk.idx[j]];
             list[j] = PadItem{it.A, it.out, it.n, 0};
         }
-        DevBuf buf;
-        const size_t list_bytes = ((sizeof(PadItem) * cnt + 255) / 256) * 256;
-        mpps_status rc = buf.alloc(list_bytes + 2 * sizeof(double) * nn * cnt, st);
-        if (rc) return rc;
-        PadItem* d_list = (PadItem*)buf.p;
-        double* dA = (double*)((char*)buf.p + list_bytes);
-        double* dO = dA + nn * cnt;
-        MPPS_CUDA_TRY(cudaMemcpyAsync(d_list, list.data(), sizeof(PadItem) * cnt,
-                                      cudaMemcpyHostToDevice, st));
-        if ((rc = launch_gather_pad(d_list, cnt, bk.n_pad, dA, st))) return rc;
-        std::vector<mpps_report> brep(rep ? cnt : 0);
-        rc = eval_device(c.data(), bk.m, dA, bk.n_pad, cnt, P, dO, rep ? brep.data() : nullptr, st,
-                         true, false);
-        if (rc) return rc;
-        if ((rc = launch_scatter_unpad(d_list, cnt, bk.n_pad, dO, st))) return rc;
-        if (rep)
-            for (int j = 0; j < cnt; ++j) rep[bk.idx[j]] = brep[j];
+        Arena a;
+        auto lay = [&](Arena& z) {
+            w.d_list = (PadItem*)z.take<char>(sizeof(PadItem) * cnt);
+            w.dA = z.take<double>((size_t)nn * cnt);
+            w.dO = z.take<double>((size_t)nn * cnt);
+            w.partial = z.take<double>(norm1_partial_elems(bk.n_pad, cnt));
+            w.anorm = z.take<double>(cnt);
+            w.d_sig = z.take<int>(cnt);
+        };
+        lay(a);
+        if ((rc = w.buf.alloc(a.off, st))) return rc;
+        a.base = (char*)w.buf.p;
+        a.off = 0;
+        lay(a);
+        if ((rc = launch_fill_bytes(w.d_list, list.data(), sizeof(PadItem) * cnt, st))) return rc;
+        if ((rc = launch_gather_pad(w.d_list, cnt, bk.n_pad, w.dA, st))) return rc;
+        if ((rc = launch_norm1(w.dA, nn, bk.n_pad, cnt, w.partial, w.anorm, st))) return rc;
+        if ((rc = launch_sigma(w.anorm, cnt, w.d_sig, st))) return rc;
     }
-    return MPPS_OK;
+    // one read of every sigma (skipped with blind squarings: then nothing is read back)
+    std::vector<int> hsig;
+    if (P.max_sq == 0) {
+        hsig.resize(count);
+        SigmaStage* sgs = nullptr;
+        if ((rc = sigma_stage(count, &sgs))) return rc;
+        size_t off = 0;
+        for (int k = 0; k < nb; ++k) {
+            const size_t cnt = buckets[k].idx.size();
+            MPPS_CUDA_TRY(cudaMemcpyAsync(sgs->h + off, wk[k].d_sig, sizeof(int) * cnt,
+                                          cudaMemcpyDeviceToHost, st));
+            off += cnt;
+        }
+        MPPS_CUDA_TRY(cudaEventRecord(sgs->ev, st));
+        MPPS_CUDA_TRY(cudaEventSynchronize(sgs->ev));
+        std::copy(sgs->h, sgs->h + count, hsig.begin());
+    }
+    // ---- phase B: the buckets on up to kAuxStreams streams that fork from the caller's
+    // stream and join it again, so that small buckets run side by side
+    std::vector<cudaStream_t> aux;
+    if ((rc = aux_streams(std::min(nb, kAuxStreams), &aux))) return rc;
+    cudaEvent_t fork_ev;
+    MPPS_CUDA_TRY(cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming));
+    MPPS_CUDA_TRY(cudaEventRecord(fork_ev, st));
+    for (cudaStream_t sx : aux) MPPS_CUDA_TRY(cudaStreamWaitEvent(sx, fork_ev, 0));
+    MPPS_CUDA_TRY(cudaEventDestroy(fork_ev));
+    size_t off = 0;
+    for (int k = 0; k < nb && !rc; ++k) {
+        const Bucket& bk = buckets[k];
+        Work& w = wk[k];
+        const int cnt = (int)bk.idx.size();
+        cudaStream_t sb = aux[k % aux.size()];
+        std::vector<mpps_report> brep(rep ? cnt : 0);
+        rc = eval_device(w.c.data(), bk.m, w.dA, bk.n_pad, cnt, P, w.dO, rep ? brep.data() : nullptr,
+                         sb, true, false, nullptr, w.d_sig, hsig.empty() ? nullptr : hsig.data() + off);
+        if (!rc) rc = launch_scatter_unpad(w.d_list, cnt, bk.n_pad, w.dO, sb);
+        if (!rc && rep)
+            for (int j = 0; j < cnt; ++j) rep[bk.idx[j]] = brep[j];
+        off += cnt;
+    }
+    // join (also after a failure, so that the workspaces are released in stream order)
+    for (cudaStream_t sx : aux) {
+        cudaEvent_t jev;
+        MPPS_CUDA_TRY(cudaEventCreateWithFlags(&jev, cudaEventDisableTiming));
+        MPPS_CUDA_TRY(cudaEventRecord(jev, sx));
+        MPPS_CUDA_TRY(cudaStreamWaitEvent(st, jev, 0));
+        MPPS_CUDA_TRY(cudaEventDestroy(jev));
+    }
+    return rc;
 }
 
 mpps_status mpps_matmul(const double* A, const double* B, double* C, int n, int batch, int format,

@@ -108,7 +108,25 @@ struct Epilogue {
     int lld;
     double low_scale;             // used when low_scale_b is null
     const double* low_scale_b;    // per batch element (device), or null
+    // exponent codes of the largest |stored value| per row and per column ([batch][n] each,
+    // atomically combined with max; zeroed by the caller), or null: the exponents of the next
+    // product's slices, recorded here so that the slicing needs no reduction pass (emulated
+    // products only).  Code 0: every entry zero; otherwise 2048 + the frexp exponent of the
+    // largest magnitude (the exponent is monotone in |x|, so the maximum of the codes is the
+    // code of the maximum).
+    int* rmax;
+    int* cmax;
+    // device-side number of matrices to process (device plan), or null: a launch whose count
+    // is 0 does no work, a smaller count processes that prefix of the matrices (or of bidx)
+    const int* dcount;
+    // device plan: the format of the rounded copy (low_fmt = MPPS_FMT_DEVICE) is read from
+    // here; a copy is written only for BF16, TF32 and BF16X3 (FP8 copies are row-scaled by
+    // their own pass)
+    const int* low_fmt_dev;
 };
+
+// low_fmt value meaning "read the format from Epilogue::low_fmt_dev".
+constexpr int MPPS_FMT_DEVICE = 100;
 
 inline Epilogue epilogue_plain(double* out, long long out_bstride) {
     Epilogue e;
@@ -120,6 +138,9 @@ inline Epilogue epilogue_plain(double* out, long long out_bstride) {
     e.out = out; e.out_bstride = out_bstride;
     e.low_fmt = MPPS_FMT_NONE; e.low_hi = nullptr; e.low_lo = nullptr;
     e.low_bstride = 0; e.lld = 0; e.low_scale = 1.0; e.low_scale_b = nullptr;
+    e.rmax = nullptr; e.cmax = nullptr;
+    e.dcount = nullptr;
+    e.low_fmt_dev = nullptr;
     return e;
 }
 
@@ -278,10 +299,13 @@ __device__ __forceinline__ void epilogue_value4(const Epilogue& ep, int b, int r
 __device__ __forceinline__ void epilogue_store(const Epilogue& ep, int b, int row, int col, int n,
                                                double v) {
     ep.out[(long long)b * ep.out_bstride + (long long)row * n + col] = v;
-    if (ep.low_fmt != MPPS_FMT_NONE)
-        store_low(ep.low_fmt, ep.low_hi, ep.low_lo,
-                  (long long)b * ep.low_bstride + (long long)row * ep.lld + col,
-                  mul_pow2(v, ep.low_scale_b ? ep.low_scale_b[b] : ep.low_scale));
+    if (ep.low_fmt != MPPS_FMT_NONE) {
+        const int lf = ep.low_fmt == MPPS_FMT_DEVICE ? __ldg(ep.low_fmt_dev) : ep.low_fmt;
+        if (lf >= MPPS_FMT_BF16X3 && lf <= MPPS_FMT_BF16)
+            store_low(lf, ep.low_hi, ep.low_lo,
+                      (long long)b * ep.low_bstride + (long long)row * ep.lld + col,
+                      mul_pow2(v, ep.low_scale_b ? ep.low_scale_b[b] : ep.low_scale));
+    }
 }
 
 // ---- launchers (defined in the .cu files) ----------------------------------------
@@ -303,11 +327,22 @@ mpps_status launch_gemm_tc(int fmt, const void* A_hi, const void* A_lo, const vo
 // and of B^T (rows of B^T = columns of B) come from launch_slice_rows; eA/eB are the
 // per-row exponents it returns.  Planes: [batch][k][n][low_ld(n)] bf16.
 size_t f64e_plane_elems(int n, int batch, int k);
+// gate (device, optional): the device plan's count; 0 = the launch does nothing.
 mpps_status launch_slice_rows(const double* M, long long bs, int n, int batch, int k, void* planes,
-                              int* exps, cudaStream_t st);
+                              int* exps, cudaStream_t st, const int* gate = nullptr);
 // Column slices of M written as rows of the B^T planes; colmax: batch * n scratch words.
 mpps_status launch_slice_cols(const double* M, long long bs, int n, int batch, int k, void* planes,
-                              int* exps, unsigned long long* colmax, cudaStream_t st);
+                              int* exps, unsigned long long* colmax, cudaStream_t st,
+                              const int* gate = nullptr);
+// The same two with the row / column maxima of |M| already known (recorded by the epilogue
+// of the emulated product that wrote M, Epilogue::rmax / cmax): no reduction pass.  The row
+// variant also zeroes rmax_clear ([batch][n], may be null) for the next product to fill.
+mpps_status launch_slice_rows_pre(const double* M, long long bs, int n, int batch, int k,
+                                  void* planes, int* exps, const int* rmax, int* rmax_clear,
+                                  cudaStream_t st, const int* gate = nullptr);
+mpps_status launch_slice_cols_pre(const double* M, long long bs, int n, int batch, int k,
+                                  void* planes, int* exps, const int* cmax, cudaStream_t st,
+                                  const int* gate = nullptr);
 // Scratch that lets the emulated product split the K range of output tiles between CTAs
 // (f64e_split_bytes() bytes, 256-byte aligned; its first f64e_split_flag_bytes() bytes
 // zeroed by the caller before the first product that uses it, on the same stream).  Without
@@ -375,6 +410,11 @@ mpps_status launch_norm1(const double* M, long long bs, int n, int batch, double
 // X = 2^-sigma[b] A (exact power-of-two scaling; d_sigma null -> plain copy).
 mpps_status launch_scale_copy(const double* A, long long a_bs, double* X, long long x_bs, int n,
                               int batch, const int* d_sigma, cudaStream_t st);
+// bytes of host memory written to dst (16-byte aligned) by kernels that carry them as
+// parameters: no host memory is read by the stream (capturable), whatever its kind.
+mpps_status launch_fill_bytes(void* dst, const void* host, size_t bytes, cudaStream_t st);
+// dst[0..count) = host_vals (device write from kernel parameters; capturable).
+mpps_status launch_fill(double* dst, const double* host_vals, int count, cudaStream_t st);
 // FP32 storage: x = (double)a (exact) and a = (float)x (round to nearest), count elements.
 mpps_status launch_widen_f32(const float* a, double* x, long long count, cudaStream_t st);
 mpps_status launch_narrow_f64(const double* x, float* a, long long count, cudaStream_t st);
@@ -392,13 +432,14 @@ mpps_status launch_scatter_unpad(const PadItem* d_list, int count, int n_pad, co
 // sigma[b] = max(0, ceil(log2 norms[b])) on the device.
 mpps_status launch_sigma(const double* norms, int batch, int* sigma, cudaStream_t st);
 // out[b] = (sigma[b] odd ? q1 : q0)[b] + diag I  (all contiguous, stride n*n).
+// sigma_cap >= 0: matrices with sigma above it get NaN (squarings launched blind).
 mpps_status launch_select_copy(const double* q0, const double* q1, const int* d_sigma, double* out,
-                               int n, int batch, double diag, cudaStream_t st);
+                               int n, int batch, double diag, cudaStream_t st, int sigma_cap = -1);
 // Rounded copies (times scale[b], or 1 if scale is null) for the low-precision products:
 // convert keeps the layout, convert_t writes the transpose (row j = column j).
 mpps_status launch_convert(int fmt, const double* M, long long bs, int n, int batch, void* hi,
                            void* lo, long long low_bs, int lld, const double* d_scale,
-                           bool transpose, cudaStream_t st);
+                           bool transpose, cudaStream_t st, const int* gate = nullptr);
 // max_ij |M_ij| per matrix, written to out[b] (out must be zeroed first).
 // Rounded copy in format fmt with one power-of-two scale per row (transpose = false: rows of
 // M, the A operand) or per column (transpose = true: written transposed, row j = column j of
@@ -408,7 +449,7 @@ mpps_status launch_convert(int fmt, const double* M, long long bs, int n, int ba
 mpps_status launch_convert_scaled(int fmt, const double* M, long long bs, int n, int batch,
                                   void* hi, void* lo, long long low_bs, int lld, int target,
                                   bool transpose, int* out_exp, unsigned long long* colmax,
-                                  cudaStream_t st);
+                                  cudaStream_t st, const int* gate = nullptr);
 mpps_status launch_maxabs(const double* M, long long bs, int n, int batch, double* out,
                           cudaStream_t st);
 // For each matrix b: scale[b] = 2^(target - e) and unscale... (power-of-two operand scales)

@@ -3,6 +3,8 @@
 // rounded operand copies for the low-precision products, and small reductions.
 #include "common.cuh"
 
+#include <string.h>
+
 #include <math.h>
 
 namespace mpps {
@@ -309,6 +311,16 @@ __global__ void k_scale_copy(const double* __restrict__ A, long long a_bs, doubl
         X[b * x_bs + t] = scale_pow2(A[b * a_bs + t], e);
 }
 
+// Up to 64 values written from the launch's parameters (no host memory is read by the
+// stream, so the write is captured by value into a CUDA graph).
+struct Fill64 {
+    double v[64];
+};
+__global__ void k_fill(double* __restrict__ dst, Fill64 vals, int count) {
+    pdl_wait();
+    if ((int)threadIdx.x < count) dst[threadIdx.x] = vals.v[threadIdx.x];
+}
+
 // FP32 storage <-> FP64 evaluation (exact widening; narrowing rounds to nearest).
 __global__ void k_widen_f32(const float* __restrict__ a, double* __restrict__ x, long long count) {
     pdl_wait();
@@ -362,15 +374,17 @@ __global__ void k_sigma(const double* __restrict__ norms, int batch, int* __rest
 
 __global__ void k_select_copy(const double* __restrict__ q0, const double* __restrict__ q1,
                               const int* __restrict__ sigma, double* __restrict__ out, int n,
-                              double diag) {
+                              double diag, int sigma_cap) {
     pdl_wait();
     const int b = blockIdx.z;
     const long long nn = (long long)n * n;
     const double* src = ((sigma[b] & 1) ? q1 : q0) + b * nn;
+    // a matrix that needed more squarings than were run has no result: NaN
+    const bool bad = sigma_cap >= 0 && sigma[b] > sigma_cap;
     for (int r = blockIdx.y; r < n; r += gridDim.y)
         for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
             const long long t = (long long)r * n + c;
-            double v = src[t];
+            double v = bad ? __longlong_as_double(0x7ff8000000000000LL) : src[t];
             if (r == c) v += diag;
             out[b * nn + t] = v;
         }
@@ -408,8 +422,10 @@ __global__ void k_combine(int n, const double* __restrict__ extra, long long ext
 }
 
 __global__ void k_convert(int fmt, const double* __restrict__ M, long long bs, int n, void* hi,
-                          void* lo, long long low_bs, int lld, const double* __restrict__ scale) {
+                          void* lo, long long low_bs, int lld, const double* __restrict__ scale,
+        const int* __restrict__ gate) {
     pdl_wait();
+    if (gate && (int)blockIdx.z >= __ldg(gate)) return;   // device plan: not run
     const int b = blockIdx.z;
     const double sc = scale ? scale[b] : 1.0;
     for (int row = blockIdx.y; row < n; row += gridDim.y)
@@ -421,8 +437,10 @@ __global__ void k_convert(int fmt, const double* __restrict__ M, long long bs, i
 // Transposed copy through a 32 x 33 shared tile: out[col][row] = round(M[row][col] * scale).
 __global__ void k_convert_t(int fmt, const double* __restrict__ M, long long bs, int n, void* hi,
                             void* lo, long long low_bs, int lld,
-                            const double* __restrict__ scale) {
+                            const double* __restrict__ scale,
+        const int* __restrict__ gate) {
     pdl_wait();
+    if (gate && (int)blockIdx.z >= __ldg(gate)) return;   // device plan: not run
     __shared__ double tile[32][33];
     const int b = blockIdx.z;
     const double sc = scale ? scale[b] : 1.0;
@@ -493,8 +511,10 @@ __device__ __forceinline__ int frexp_exp_bits(unsigned long long a) {
 __global__ void __launch_bounds__(256) k_convert_rows_scaled(int fmt, const double* __restrict__ M,
                                                              long long bs, int n, void* hi, void* lo,
                                                              long long low_bs, int lld, int target,
-                                                             int* __restrict__ out_exp) {
+                                                             int* __restrict__ out_exp,
+        const int* __restrict__ gate) {
     pdl_wait();
+    if (gate && (int)blockIdx.y >= __ldg(gate)) return;   // device plan: not run
     __shared__ unsigned long long red[8];
     const int row = blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
     const double* src = M + (long long)b * bs + (long long)row * n;
@@ -521,8 +541,10 @@ __global__ void __launch_bounds__(256) k_convert_rows_scaled(int fmt, const doub
 // Column maxima of |M| as bit patterns (out zeroed first), one thread per column over a
 // 16-row chunk.
 __global__ void k_colmax_bits(const double* __restrict__ M, long long bs, int n,
-                              unsigned long long* __restrict__ out) {
+                              unsigned long long* __restrict__ out,
+        const int* __restrict__ gate) {
     pdl_wait();
+    if (gate && (int)blockIdx.z >= __ldg(gate)) return;   // device plan: not run
     const int col = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.z;
     if (col >= n) return;
     const int r0 = blockIdx.y * 16;
@@ -542,8 +564,10 @@ __global__ void k_colmax_bits(const double* __restrict__ M, long long bs, int n,
 __global__ void k_convert_t_scaled(int fmt, const double* __restrict__ M, long long bs, int n,
                                    void* hi, void* lo, long long low_bs, int lld, int target,
                                    const unsigned long long* __restrict__ colmax,
-                                   int* __restrict__ out_exp) {
+                                   int* __restrict__ out_exp,
+        const int* __restrict__ gate) {
     pdl_wait();
+    if (gate && (int)blockIdx.z >= __ldg(gate)) return;   // device plan: not run
     __shared__ double tile[32][33];
     const int b = blockIdx.z;
     const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
@@ -713,6 +737,46 @@ mpps_status launch_scale_copy(const double* A, long long a_bs, double* X, long l
     return MPPS_OK;
 }
 
+// Bytes copied from the launch's parameters, 2 KB per launch (see Fill64).
+struct Fill2K {
+    uint4 w[128];
+};
+__global__ void k_fill_bytes(uint4* __restrict__ dst, Fill2K vals, int words) {
+    pdl_wait();
+    if ((int)threadIdx.x < words) dst[threadIdx.x] = vals.w[threadIdx.x];
+}
+
+mpps_status launch_fill_bytes(void* dst, const void* host, size_t bytes, cudaStream_t st) {
+    ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
+    if ((uintptr_t)dst & 15) {
+        set_error("fill_bytes: destination not 16-byte aligned");
+        return MPPS_EINVAL;
+    }
+    const unsigned char* src = (const unsigned char*)host;
+    for (size_t o = 0; o < bytes; o += sizeof(Fill2K)) {
+        Fill2K f;
+        const size_t c = bytes - o < sizeof(Fill2K) ? bytes - o : sizeof(Fill2K);
+        memset(&f, 0, sizeof(f));
+        memcpy(&f, src + o, c);
+        MPPS_CUDA_TRY(launch_pdl(k_fill_bytes, dim3(1), dim3(128), 0, st, (uint4*)((char*)dst + o), f,
+                                 (int)((c + 15) / 16)));
+        MPPS_LAUNCH_CHECK();
+    }
+    return MPPS_OK;
+}
+
+mpps_status launch_fill(double* dst, const double* host_vals, int count, cudaStream_t st) {
+    ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
+    for (int o = 0; o < count; o += 64) {
+        Fill64 f;
+        const int c = count - o < 64 ? count - o : 64;
+        for (int i = 0; i < 64; ++i) f.v[i] = i < c ? host_vals[o + i] : 0.0;
+        MPPS_CUDA_TRY(launch_pdl(k_fill, dim3(1), dim3(64), 0, st, dst + o, f, c));
+        MPPS_LAUNCH_CHECK();
+    }
+    return MPPS_OK;
+}
+
 mpps_status launch_widen_f32(const float* a, double* x, long long count, cudaStream_t st) {
     ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
     MPPS_CUDA_TRY(launch_pdl(k_widen_f32, dim3(grid1d(count, 256)), dim3(256), 0, st, a, x, count));
@@ -751,9 +815,10 @@ mpps_status launch_sigma(const double* norms, int batch, int* sigma, cudaStream_
 }
 
 mpps_status launch_select_copy(const double* q0, const double* q1, const int* d_sigma, double* out,
-                               int n, int batch, double diag, cudaStream_t st) {
+                               int n, int batch, double diag, cudaStream_t st, int sigma_cap) {
     ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
-    MPPS_CUDA_TRY(launch_pdl(k_select_copy, grid2d(n, batch), dim3(256), 0, st, q0, q1, d_sigma, out, n, diag));
+    MPPS_CUDA_TRY(launch_pdl(k_select_copy, grid2d(n, batch), dim3(256), 0, st, q0, q1, d_sigma, out, n, diag,
+                             sigma_cap));
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }
@@ -768,14 +833,14 @@ mpps_status launch_combine(int n, int batch, const double* extra, long long extr
 
 mpps_status launch_convert(int fmt, const double* M, long long bs, int n, int batch, void* hi,
                            void* lo, long long low_bs, int lld, const double* d_scale,
-                           bool transpose, cudaStream_t st) {
+                           bool transpose, cudaStream_t st, const int* gate) {
     ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
     if (transpose) {
         dim3 g((n + 31) / 32, (n + 31) / 32, batch);
-        MPPS_CUDA_TRY(launch_pdl(k_convert_t, dim3(g), dim3(dim3(32, 8)), 0, st, fmt, M, bs, n, hi, lo, low_bs, lld, d_scale));
+        MPPS_CUDA_TRY(launch_pdl(k_convert_t, dim3(g), dim3(dim3(32, 8)), 0, st, fmt, M, bs, n, hi, lo, low_bs, lld, d_scale, gate));
     } else {
         MPPS_CUDA_TRY(launch_pdl(k_convert, grid2d(n, batch), dim3(256), 0, st, fmt, M, bs, n, hi, lo, low_bs,
-                                 lld, d_scale));
+                                 lld, d_scale, gate));
     }
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
@@ -784,7 +849,7 @@ mpps_status launch_convert(int fmt, const double* M, long long bs, int n, int ba
 mpps_status launch_convert_scaled(int fmt, const double* M, long long bs, int n, int batch,
                                   void* hi, void* lo, long long low_bs, int lld, int target,
                                   bool transpose, int* out_exp, unsigned long long* colmax,
-                                  cudaStream_t st) {
+                                  cudaStream_t st, const int* gate) {
     ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
     if (batch > 65535) {
         set_error("convert_scaled: batch %d exceeds the grid limit", batch);
@@ -792,14 +857,14 @@ mpps_status launch_convert_scaled(int fmt, const double* M, long long bs, int n,
     }
     if (!transpose) {
         MPPS_CUDA_TRY(launch_pdl(k_convert_rows_scaled, dim3(n, batch), dim3(256), 0, st, fmt, M, bs, n, hi, lo,
-                                 low_bs, lld, target, out_exp));
+                                 low_bs, lld, target, out_exp, gate));
     } else {
         MPPS_CUDA_TRY(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * (size_t)batch * n, st));
         MPPS_CUDA_TRY(launch_pdl(k_colmax_bits, dim3((n + 127) / 128, (n + 15) / 16, batch), dim3(128), 0, st, M, bs, n,
-                                 colmax));
+                                 colmax, gate));
         MPPS_LAUNCH_CHECK();
         MPPS_CUDA_TRY(launch_pdl(k_convert_t_scaled, dim3((n + 31) / 32, (n + 31) / 32, batch), dim3(32, 8), 0, st, fmt, M,
-                                 bs, n, hi, lo, low_bs, lld, target, colmax, out_exp));
+                                 bs, n, hi, lo, low_bs, lld, target, colmax, out_exp, gate));
     }
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;

@@ -40,6 +40,7 @@ __global__ void __launch_bounds__(32 * WM * WN)
     k_gemm_f64(const double* __restrict__ A, long long a_bs, const double* __restrict__ B,
                long long b_bs, int n, Epilogue ep, const int* __restrict__ bidx) {
     pdl_wait();
+    if (ep.dcount && (int)blockIdx.z >= __ldg(ep.dcount)) return;   // device plan: not run
     constexpr int NT = 32 * WM * WN;
     constexpr int WTM = BM / WM, WTN = BN / WN;   // warp tile
     constexpr int MI = WTM / 16, NI = WTN / 8;    // fragments per warp

@@ -212,12 +212,24 @@ __device__ __forceinline__ unsigned long long max_bits(unsigned long long a, uns
     return a > b ? a : b;
 }
 
+// Exponent code of |x| recorded by the epilogues (Epilogue::rmax / cmax): 0 for zero,
+// 2048 + exp_above(|x|) otherwise (always positive: exp_above >= -1073), kNonFinite + 2048
+// for a NaN or infinity; and its inverse for the slicers.
+constexpr int kExpCodeBias = 2048;
+__device__ __forceinline__ int exp_code(double x) {
+    const unsigned long long a = abs_bits(x);
+    return a == 0 ? 0 : exp_above(a) + kExpCodeBias;
+}
+__device__ __forceinline__ int exp_from_code(int c) { return c == 0 ? 0 : c - kExpCodeBias; }
+
 // Row slices (A operand) for short rows (n < 256): one warp per row; e_i from the row
 // maximum.
 template <int KS>
 __global__ void k_slice_rows(const double* __restrict__ M, long long bs, int n, long long goff, __nv_bfloat16* __restrict__ planes,
-                             long long plane_bs, int lld, int* __restrict__ exps) {
+                             long long plane_bs, int lld, int* __restrict__ exps,
+        const int* __restrict__ gate) {
     pdl_wait();
+    if (gate && (int)blockIdx.y >= __ldg(gate)) return;   // device plan: not run
     pdl_trigger();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row = blockIdx.x * (blockDim.x >> 5) + warp, b = blockIdx.y;
@@ -242,8 +254,10 @@ __global__ void __launch_bounds__(256) k_slice_rows_blk(const double* __restrict
                                                         int n, long long goff,
                                                         __nv_bfloat16* __restrict__ planes,
                                                         long long plane_bs, int lld,
-                                                        int* __restrict__ exps) {
+                                                        int* __restrict__ exps,
+        const int* __restrict__ gate) {
     pdl_wait();
+    if (gate && (int)blockIdx.y >= __ldg(gate)) return;   // device plan: not run
     pdl_trigger();
     __shared__ unsigned long long red[8];
     const int row = blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
@@ -284,8 +298,10 @@ __global__ void __launch_bounds__(256) k_slice_rows_blk4(const double* __restric
                                                          int n, long long goff,
                                                          __nv_bfloat16* __restrict__ planes,
                                                          long long plane_bs, int lld,
-                                                         int* __restrict__ exps) {
+                                                         int* __restrict__ exps,
+        const int* __restrict__ gate) {
     pdl_wait();
+    if (gate && (int)blockIdx.y >= __ldg(gate)) return;   // device plan: not run
     pdl_trigger();
     __shared__ unsigned long long red[8];
     const int row = blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
@@ -338,9 +354,65 @@ __global__ void __launch_bounds__(256) k_slice_rows_blk4(const double* __restric
     }
 }
 
-// Row maxima of |M| -> exponents e_i (one warp per row), for rows too long for the above.
-__global__ void k_rowexp(const double* __restrict__ M, long long bs, int n, int* __restrict__ exps) {
+// Row slices with the row maxima already known (recorded by the epilogue of the product that
+// wrote M): a streaming pass with no reduction.  V consecutive columns per thread (V = 4:
+// n a multiple of 4, 16-byte aligned rows), grid (column groups, rows, matrices); the K tail
+// up to round_up(n, KB) is written as zeros.  Column group 0 also writes the row's exponent
+// and zeroes the row's entry of rclear (the maxima buffer the next product fills).
+template <int KS, int V>
+__global__ void __launch_bounds__(256) k_slice_rows_pre(const double* __restrict__ M, long long bs, int n,
+                                                        long long goff,
+                                                        const int* __restrict__ rmax,
+                                                        int* __restrict__ rclear,
+                                                        __nv_bfloat16* __restrict__ planes,
+                                                        long long plane_bs, int lld,
+                                                        int* __restrict__ exps,
+        const int* __restrict__ gate) {
     pdl_wait();
+    if (gate && (int)blockIdx.z >= __ldg(gate)) return;   // device plan: not run
+    pdl_trigger();
+    const int b = blockIdx.z;
+    const int n32 = (n + KB - 1) / KB * KB;
+    const long long pstride = (long long)n * 2 * lld;
+    for (int row = blockIdx.y; row < n; row += gridDim.y) {
+        const long long ri = (long long)b * n + row;
+        const int e = exp_from_code(rmax[ri]);
+        const int j = V * (blockIdx.x * blockDim.x + threadIdx.x);
+        if (j == 0) {
+            exps[ri] = e;
+            if (rclear) rclear[ri] = 0;
+        }
+        if (j >= n32) continue;
+        const double* src = M + (long long)b * bs + (long long)row * n + j;
+        __nv_bfloat16* dst = planes + (long long)b * plane_bs + (long long)row * 2 * lld + kpos(j);
+        if constexpr (V == 4) {
+            double v[4] = {0.0, 0.0, 0.0, 0.0};
+            if (j < n) {
+                const double2 a = __ldg(reinterpret_cast<const double2*>(src));
+                const double2 c = __ldg(reinterpret_cast<const double2*>(src + 2));
+                v[0] = a.x; v[1] = a.y; v[2] = c.x; v[3] = c.y;
+            }
+            long long G[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) G[u] = scaled_int_fp64(v[u], e) + goff;
+#pragma unroll
+            for (int t = 0; t < KS; ++t) {
+                uint2 w;
+                w.x = digit_pair(G[0], G[1], t);
+                w.y = digit_pair(G[2], G[3], t);
+                *reinterpret_cast<uint2*>(dst + slice_off(t, pstride)) = w;
+            }
+        } else {
+            put_digits<KS>(j < n ? __ldg(src) : 0.0, e, goff, dst, pstride);
+        }
+    }
+}
+
+// Row maxima of |M| -> exponents e_i (one warp per row), for rows too long for the above.
+__global__ void k_rowexp(const double* __restrict__ M, long long bs, int n, int* __restrict__ exps,
+        const int* __restrict__ gate) {
+    pdl_wait();
+    if (gate && (int)blockIdx.y >= __ldg(gate)) return;   // device plan: not run
     pdl_trigger();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row = blockIdx.x * (blockDim.x >> 5) + warp, b = blockIdx.y;
@@ -355,8 +427,10 @@ __global__ void k_rowexp(const double* __restrict__ M, long long bs, int n, int*
 // Row slices, one thread per element (the exponents come from k_rowexp).
 template <int KS>
 __global__ void k_slice_rows_elem(const double* __restrict__ M, long long bs, int n, long long goff, const int* __restrict__ exps,
-                                  __nv_bfloat16* __restrict__ planes, long long plane_bs, int lld) {
+                                  __nv_bfloat16* __restrict__ planes, long long plane_bs, int lld,
+        const int* __restrict__ gate) {
     pdl_wait();
+    if (gate && (int)blockIdx.z >= __ldg(gate)) return;   // device plan: not run
     pdl_trigger();
     const int col = blockIdx.x * blockDim.x + threadIdx.x, row = blockIdx.y, b = blockIdx.z;
     if (col >= (n + KB - 1) / KB * KB) return;   // the K tail n..n32-1 is written as zeros
@@ -369,8 +443,10 @@ __global__ void k_slice_rows_elem(const double* __restrict__ M, long long bs, in
 // Column maxima of |M| (as the bit pattern of a non-negative double; out zeroed first): one
 // thread per column over a 16-row chunk, all 16 loads in flight.
 __global__ void k_colmax(const double* __restrict__ M, long long bs, int n,
-                         unsigned long long* __restrict__ out) {
+                         unsigned long long* __restrict__ out,
+        const int* __restrict__ gate) {
     pdl_wait();
+    if (gate && (int)blockIdx.z >= __ldg(gate)) return;   // device plan: not run
     pdl_trigger();
     const int col = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.z;
     if (col >= n) return;
@@ -388,16 +464,20 @@ __global__ void k_colmax(const double* __restrict__ M, long long bs, int n,
 
 // Column slices (B operand, written transposed: plane row j = column j of M) through a
 // shared 64-row x 32-column block of M (stored column-major, pitch 65); e_j from the column
-// maxima.  Each thread turns two consecutive rows of one column (two consecutive K of the
-// plane row) into digits and stores both per plane in one 4-byte word.
-template <int KS>
+// maxima (or, CODES, from the exponent codes an epilogue recorded).  Each thread turns two
+// consecutive rows of one column (two consecutive K of the plane row) into digits and stores
+// both per plane in one 4-byte word.
+template <int KS, bool CODES>
 __global__ void __launch_bounds__(256) k_slice_cols(const double* __restrict__ M, long long bs,
                                                     int n, long long goff,
                                                     const unsigned long long* __restrict__ colmax,
+                                                    const int* __restrict__ codes,
                                                     __nv_bfloat16* __restrict__ planes,
                                                     long long plane_bs, int lld,
-                                                    int* __restrict__ exps) {
+                                                    int* __restrict__ exps,
+        const int* __restrict__ gate) {
     pdl_wait();
+    if (gate && (int)blockIdx.z >= __ldg(gate)) return;   // device plan: not run
     pdl_trigger();
     __shared__ double tile[32][65];
     const int b = blockIdx.z, r0 = blockIdx.y * 64, c0 = blockIdx.x * 32;
@@ -411,7 +491,8 @@ __global__ void __launch_bounds__(256) k_slice_cols(const double* __restrict__ M
     for (int i = threadIdx.y; i < 32; i += blockDim.y) {
         const int col = c0 + i, k0 = r0 + 2 * threadIdx.x;   // plane row col, K k0 and k0 + 1
         if (col >= n || k0 >= n) continue;
-        const int e = exp_above(colmax[(long long)b * n + col]);
+        const int e = CODES ? exp_from_code(codes[(long long)b * n + col])
+                            : exp_above(colmax[(long long)b * n + col]);
         if (blockIdx.y == 0 && threadIdx.x == 0) exps[(long long)b * n + col] = e;
         const long long G0 = scaled_int_fp64(tile[i][2 * threadIdx.x], e) + goff;
         const long long G1 = scaled_int_fp64(tile[i][2 * threadIdx.x + 1], e) + goff;   // 0 past n
@@ -463,17 +544,24 @@ __device__ __noinline__ double f64e_slow_value(bool flushed, double acc, long lo
     return flushed ? ldexp(fma(acc, 0x1p-35, (double)T), e - 14)
                    : ldexp(fma((double)W, 0x1p-35, (double)T), e - 14);
 }
-__device__ __noinline__ void f64e_store(const Epilogue& ep, int b, int row, int col, int n,
-                                        double v) {
-    epilogue_store(ep, b, row, col, n, epilogue_value(ep, b, row, col, n, v));
+__device__ __noinline__ double f64e_store(const Epilogue& ep, int b, int row, int col, int n,
+                                          double v) {
+    const double r = epilogue_value(ep, b, row, col, n, v);
+    epilogue_store(ep, b, row, col, n, r);
+    return r;
 }
+
+// Four stored values handed back by the store helpers (for the epilogue's maxima).
+struct F64x4 {
+    double x, y, z, w;
+};
 
 // The fused Horner add (block sum from the power table) and/or addend, alpha = 1, for four
 // products v0..v3 at columns col0..col0+3 of row `row` (inside the matrix, the power-table
 // and addend rows 16-byte aligned): the same operations in the same order as
 // epilogue_value, with those rows read two doubles at a time.
-__device__ __noinline__ void f64e_sum_store4(const Epilogue& ep, int b, int row, int col0, int n,
-                                             double v0, double v1, double v2, double v3) {
+__device__ __noinline__ F64x4 f64e_sum_store4(const Epilogue& ep, int b, int row, int col0, int n,
+                                                double v0, double v1, double v2, double v3) {
     const long long off = (long long)row * n + col0;
     double v[4] = {v0, v1, v2, v3};
     if (ep.nt >= 0) {
@@ -505,6 +593,7 @@ __device__ __noinline__ void f64e_sum_store4(const Epilogue& ep, int b, int row,
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) epilogue_store(ep, b, row, col0 + u, n, v[u]);
+    return F64x4{v[0], v[1], v[2], v[3]};
 }
 
 // The block sum B_{i-1} = coef[0] I + sum_j coef[j] X^j of one thread's 16 products (row
@@ -539,15 +628,17 @@ __device__ __noinline__ void f64e_block_sum16(const Epilogue& ep, int b, int row
 
 // Product plus the block sum stored by f64e_block_sum16, for four products at columns
 // col0..col0+3, then the store (and the rounded copy for the next step).
-__device__ __noinline__ void f64e_add_stored4(const Epilogue& ep, int b, int row, int col0, int n,
-                                              double v0, double v1, double v2, double v3) {
+__device__ __noinline__ F64x4 f64e_add_stored4(const Epilogue& ep, int b, int row, int col0, int n,
+                                                 double v0, double v1, double v2, double v3) {
     const double* op = ep.out + (long long)b * ep.out_bstride + (long long)row * n + col0;
     const double2 s01 = *reinterpret_cast<const double2*>(op);
     const double2 s23 = *reinterpret_cast<const double2*>(op + 2);
-    epilogue_store(ep, b, row, col0, n, v0 + s01.x);
-    epilogue_store(ep, b, row, col0 + 1, n, v1 + s01.y);
-    epilogue_store(ep, b, row, col0 + 2, n, v2 + s23.x);
-    epilogue_store(ep, b, row, col0 + 3, n, v3 + s23.y);
+    const F64x4 r{v0 + s01.x, v1 + s01.y, v2 + s23.x, v3 + s23.y};
+    epilogue_store(ep, b, row, col0, n, r.x);
+    epilogue_store(ep, b, row, col0 + 1, n, r.y);
+    epilogue_store(ep, b, row, col0 + 2, n, r.z);
+    epilogue_store(ep, b, row, col0 + 3, n, r.w);
+    return r;
 }
 
 // Tile `id` -> (matrix slot z, first row, first column); row blocks are walked in groups of
@@ -712,7 +803,6 @@ __global__ void __launch_bounds__(THREADS, 1)
     tm.tcols = (n + ON - 1) / ON;
     tm.trows = (n + OM - 1) / OM;
     tm.per_mat = tm.tcols * tm.trows;
-    const int total = tm.per_mat * batch;
     const int nkb = (n + KB - 1) / KB;
     constexpr int kb_per_chunk = KCHUNK / KB;
     const int nchunks = (nkb + kb_per_chunk - 1) / kb_per_chunk;
@@ -736,6 +826,12 @@ __global__ void __launch_bounds__(THREADS, 1)
     const uint32_t tmem = *tmem_slot;
     pdl_wait();   // barrier init, TMEM allocation and tensor-map prefetch overlap the previous kernel
     pdl_trigger();
+    // matrices processed: all, or the device plan's count (0: the launch does nothing; the
+    // split schedule then covers the tiles of that many matrices)
+    const int nbat = ep.dcount ? min(__ldg(ep.dcount), batch) : batch;
+    const int total = tm.per_mat * nbat;
+    Split spl = sp;
+    if (ep.dcount && sp.U) spl.U = (long long)total * nkb;
 
     if (warp == EPI_WARPS) {
         if (lane == 0) {   // TMA producer
@@ -743,7 +839,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             int s = 0;                                        // stage of K block g
             uint32_t ph = 0;                                  // its fill parity
             bool ok = true;
-            Segments<SPLIT> sg(sp, total, nkb);
+            Segments<SPLIT> sg(spl, total, nkb);
             int id, kb0, kb1;
             while (ok && sg.next(id, kb0, kb1)) {
                 int z, m0, n0;
@@ -775,7 +871,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             uint32_t ph = 0;
             bool ok = true;
             const uint32_t ring = smem_u32(smem);
-            Segments<SPLIT> sg(sp, total, nkb);
+            Segments<SPLIT> sg(spl, total, nkb);
             int id, kb0, kb1;
             while (ok && sg.next(id, kb0, kb1)) {
                 for (int kb = kb0; kb < kb1 && ok; ++kb) {
@@ -827,7 +923,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int q4 = warp & 3, h = warp >> 2;   // lane quarter, column group
         const uint32_t lane_base = (uint32_t)(q4 * 32) << 16;
         uint32_t gc = 0;
-        Segments<SPLIT> sg(sp, total, nkb);
+        Segments<SPLIT> sg(spl, total, nkb);
         int id, kb0, kb1;
         while (sg.next(id, kb0, kb1)) {
             int z, m0, n0;
@@ -895,7 +991,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
             if (kb1 < nkb) {   // the owner of a split tile adds the later pieces, in CTA order
                 const long long tend = (long long)(id + 1) * nkb;
-                for (int c2 = blockIdx.x + 1; c2 < (int)gridDim.x && split_start(c2, sp.U) < tend; ++c2) {
+                for (int c2 = blockIdx.x + 1; c2 < (int)gridDim.x && split_start(c2, spl.U) < tend; ++c2) {
                     const unsigned* f = sp.flags + (size_t)c2 * EPI_WARPS + warp;
                     bool got = true;
                     if (lane == 0) got = flag_wait(f, sp.epoch, err);
@@ -912,13 +1008,17 @@ __global__ void __launch_bounds__(THREADS, 1)
                 if (!ok) break;
             }
             }
-            // product = 2^{eA+eB-49} W + 2^{eA+eB-14} T, then the fused epilogue
-            if (row < n) {
-                const int er = eA[(long long)b * n + row];
-                const bool plain = ep_plain && cb + EPI_COLS <= n && nchunks <= FLUSH;
+            // product = 2^{eA+eB-49} W + 2^{eA+eB-14} T, then the fused epilogue; with
+            // ep.rmax / ep.cmax the maxima of the stored values are recorded as well (every
+            // lane runs the group loop: the column maxima reduce across the warp's rows)
+            const bool inside = row < n;
+            const int er = inside ? eA[(long long)b * n + row] : 0;
+            const bool plain = ep_plain && cb + EPI_COLS <= n && nchunks <= FLUSH;
+            int mrow = 0;
 #pragma unroll
-                for (int g = 0; g < EPI_COLS; g += 4) {
-                    double val[4];
+            for (int g = 0; g < EPI_COLS; g += 4) {
+                double val[4] = {0.0, 0.0, 0.0, 0.0};
+                if (inside) {
                     bool fast = nchunks <= FLUSH;
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
@@ -934,21 +1034,38 @@ __global__ void __launch_bounds__(THREADS, 1)
                         asm volatile("st.global.v4.f64 [%0], {%1, %2, %3, %4};" ::"l"(orow + g),
                                      "d"(val[0]), "d"(val[1]), "d"(val[2]), "d"(val[3]) : "memory");
                     } else if (fast && pre) {
-                        f64e_add_stored4(ep, b, row, cb + g, n, val[0], val[1], val[2], val[3]);
+                        const F64x4 r = f64e_add_stored4(ep, b, row, cb + g, n, val[0], val[1],
+                                                         val[2], val[3]);
+                        val[0] = r.x; val[1] = r.y; val[2] = r.z; val[3] = r.w;
                     } else if (fast && ep_sum && cb + EPI_COLS <= n && nchunks <= FLUSH) {
-                        f64e_sum_store4(ep, b, row, cb + g, n, val[0], val[1], val[2], val[3]);
+                        const F64x4 r = f64e_sum_store4(ep, b, row, cb + g, n, val[0], val[1],
+                                                        val[2], val[3]);
+                        val[0] = r.x; val[1] = r.y; val[2] = r.z; val[3] = r.w;
                     } else {
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
                             const int col = cb + g + u;
-                            if (col < n)
-                                f64e_store(ep, b, row, col, n, fast ? val[u] : f64e_slow_value(
-                                    nchunks > FLUSH, orow[g + u], W[g + u], T[g + u],
-                                    er + __ldg(eB + (long long)b * n + col)));
+                            val[u] = col < n ? f64e_store(ep, b, row, col, n, fast ? val[u] : f64e_slow_value(
+                                                   nchunks > FLUSH, orow[g + u], W[g + u], T[g + u],
+                                                   er + __ldg(eB + (long long)b * n + col)))
+                                             : 0.0;
+                        }
+                    }
+                }
+                if (ep.rmax || ep.cmax) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int c = exp_code(val[u]);
+                        mrow = c > mrow ? c : mrow;
+                        if (ep.cmax) {   // column maximum over the warp's 32 rows
+                            const int cm = (int)__reduce_max_sync(0xffffffffu, (unsigned)c);
+                            if (lane == g + u && cb + g + u < n && cm)
+                                atomicMax(ep.cmax + (long long)b * n + cb + g + u, cm);
                         }
                     }
                 }
             }
+            if (ep.rmax && inside && mrow) atomicMax(ep.rmax + (long long)b * n + row, mrow);
         }
     }
     __syncwarp();
@@ -1066,35 +1183,35 @@ namespace {
 
 template <int KS>
 mpps_status slice_rows_k(const double* M, long long bs, int n, int batch, __nv_bfloat16* pl,
-                         int* exps, cudaStream_t st) {
+                         int* exps, cudaStream_t st, const int* gate) {
     const int lld = low_ld(n);
     const long long goff = digit_offset(KS), pbs = (long long)num_pairs(KS) * n * 2 * lld;
     if (n < 256) {
-        MPPS_CUDA_TRY(launch_pdl(k_slice_rows<KS>, dim3(dim3((n + 7) / 8, batch)), dim3(256), 0, st, M, bs, n, goff, pl, pbs, lld, exps));
+        MPPS_CUDA_TRY(launch_pdl(k_slice_rows<KS>, dim3(dim3((n + 7) / 8, batch)), dim3(256), 0, st, M, bs, n, goff, pl, pbs, lld, exps, gate));
     } else if (n <= 4096 && n % 4 == 0 && ((uintptr_t)M & 15) == 0 && bs % 2 == 0) {
         const dim3 g(n, batch);
         if (n <= 1024)
-            MPPS_CUDA_TRY(launch_pdl(k_slice_rows_blk4<KS, 1>, dim3(g), dim3(256), 0, st, M, bs, n, goff, pl, pbs, lld, exps));
+            MPPS_CUDA_TRY(launch_pdl(k_slice_rows_blk4<KS, 1>, dim3(g), dim3(256), 0, st, M, bs, n, goff, pl, pbs, lld, exps, gate));
         else if (n <= 2048)
-            MPPS_CUDA_TRY(launch_pdl(k_slice_rows_blk4<KS, 2>, dim3(g), dim3(256), 0, st, M, bs, n, goff, pl, pbs, lld, exps));
+            MPPS_CUDA_TRY(launch_pdl(k_slice_rows_blk4<KS, 2>, dim3(g), dim3(256), 0, st, M, bs, n, goff, pl, pbs, lld, exps, gate));
         else
-            MPPS_CUDA_TRY(launch_pdl(k_slice_rows_blk4<KS, 4>, dim3(g), dim3(256), 0, st, M, bs, n, goff, pl, pbs, lld, exps));
+            MPPS_CUDA_TRY(launch_pdl(k_slice_rows_blk4<KS, 4>, dim3(g), dim3(256), 0, st, M, bs, n, goff, pl, pbs, lld, exps, gate));
     } else if (n <= 4096) {
         const dim3 g(n, batch);
         if (n <= 512)
-            MPPS_CUDA_TRY(launch_pdl(k_slice_rows_blk<KS, 2>, dim3(g), dim3(256), 0, st, M, bs, n, goff, pl, pbs, lld, exps));
+            MPPS_CUDA_TRY(launch_pdl(k_slice_rows_blk<KS, 2>, dim3(g), dim3(256), 0, st, M, bs, n, goff, pl, pbs, lld, exps, gate));
         else if (n <= 1024)
-            MPPS_CUDA_TRY(launch_pdl(k_slice_rows_blk<KS, 4>, dim3(g), dim3(256), 0, st, M, bs, n, goff, pl, pbs, lld, exps));
+            MPPS_CUDA_TRY(launch_pdl(k_slice_rows_blk<KS, 4>, dim3(g), dim3(256), 0, st, M, bs, n, goff, pl, pbs, lld, exps, gate));
         else if (n <= 2048)
-            MPPS_CUDA_TRY(launch_pdl(k_slice_rows_blk<KS, 8>, dim3(g), dim3(256), 0, st, M, bs, n, goff, pl, pbs, lld, exps));
+            MPPS_CUDA_TRY(launch_pdl(k_slice_rows_blk<KS, 8>, dim3(g), dim3(256), 0, st, M, bs, n, goff, pl, pbs, lld, exps, gate));
         else
-            MPPS_CUDA_TRY(launch_pdl(k_slice_rows_blk<KS, 16>, dim3(g), dim3(256), 0, st, M, bs, n, goff, pl, pbs, lld, exps));
+            MPPS_CUDA_TRY(launch_pdl(k_slice_rows_blk<KS, 16>, dim3(g), dim3(256), 0, st, M, bs, n, goff, pl, pbs, lld, exps, gate));
     } else {
         // long rows: a row-maximum pass, then one thread per element
-        MPPS_CUDA_TRY(launch_pdl(k_rowexp, dim3(dim3((n + 7) / 8, batch)), dim3(256), 0, st, M, bs, n, exps));
+        MPPS_CUDA_TRY(launch_pdl(k_rowexp, dim3(dim3((n + 7) / 8, batch)), dim3(256), 0, st, M, bs, n, exps, gate));
         MPPS_LAUNCH_CHECK();
         MPPS_CUDA_TRY(launch_pdl(k_slice_rows_elem<KS>, dim3(dim3((n + KB + 127) / 128, n, batch)), dim3(128), 0, st, M, bs, n, goff, exps, pl,
-                                 pbs, lld));
+                                 pbs, lld, gate));
     }
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
@@ -1102,10 +1219,19 @@ mpps_status slice_rows_k(const double* M, long long bs, int n, int batch, __nv_b
 
 template <int KS>
 mpps_status slice_cols_k(const double* M, long long bs, int n, int batch, __nv_bfloat16* pl,
-                         int* exps, unsigned long long* colmax, cudaStream_t st) {
+                         int* exps, unsigned long long* colmax, cudaStream_t st,
+                         const int* codes, const int* gate) {
     const int lld = low_ld(n);
-    MPPS_CUDA_TRY(launch_pdl(k_slice_cols<KS>, dim3(dim3((n + 31) / 32, (n + 63) / 64, batch)), dim3(dim3(32, 8)), 0, st, M, bs, n, digit_offset(KS), colmax, pl, (long long)KS * n * lld, lld,
-        exps));
+    if (codes) {
+        MPPS_CUDA_TRY(launch_pdl(k_slice_cols<KS, true>, dim3(dim3((n + 31) / 32, (n + 63) / 64, batch)),
+                                 dim3(dim3(32, 8)), 0, st, M, bs, n, digit_offset(KS),
+                                 (const unsigned long long*)nullptr, codes, pl,
+                                 (long long)KS * n * lld, lld, exps, gate));
+        MPPS_LAUNCH_CHECK();
+        return MPPS_OK;
+    }
+    MPPS_CUDA_TRY(launch_pdl(k_slice_cols<KS, false>, dim3(dim3((n + 31) / 32, (n + 63) / 64, batch)), dim3(dim3(32, 8)), 0, st, M, bs, n, digit_offset(KS), (const unsigned long long*)colmax, (const int*)nullptr, pl, (long long)KS * n * lld, lld,
+        exps, gate));
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }
@@ -1113,7 +1239,7 @@ mpps_status slice_cols_k(const double* M, long long bs, int n, int batch, __nv_b
 }  // namespace
 
 mpps_status launch_slice_rows(const double* M, long long bs, int n, int batch, int k, void* planes,
-                              int* exps, cudaStream_t st) {
+                              int* exps, cudaStream_t st, const int* gate) {
     k = f64e_planes(k);
     ProfScope prof(MPPS_PROF_SLICE, st);
     if (batch > 65535) {
@@ -1122,34 +1248,98 @@ mpps_status launch_slice_rows(const double* M, long long bs, int n, int batch, i
     }
     __nv_bfloat16* pl = (__nv_bfloat16*)planes;
     switch (k) {
-        case 1: return slice_rows_k<1>(M, bs, n, batch, pl, exps, st);
-        case 2: return slice_rows_k<2>(M, bs, n, batch, pl, exps, st);
-        case 3: return slice_rows_k<3>(M, bs, n, batch, pl, exps, st);
-        case 4: return slice_rows_k<4>(M, bs, n, batch, pl, exps, st);
-        case 5: return slice_rows_k<5>(M, bs, n, batch, pl, exps, st);
-        case 6: return slice_rows_k<6>(M, bs, n, batch, pl, exps, st);
-        case 7: return slice_rows_k<7>(M, bs, n, batch, pl, exps, st);
-        default: return slice_rows_k<8>(M, bs, n, batch, pl, exps, st);
+        case 1: return slice_rows_k<1>(M, bs, n, batch, pl, exps, st, gate);
+        case 2: return slice_rows_k<2>(M, bs, n, batch, pl, exps, st, gate);
+        case 3: return slice_rows_k<3>(M, bs, n, batch, pl, exps, st, gate);
+        case 4: return slice_rows_k<4>(M, bs, n, batch, pl, exps, st, gate);
+        case 5: return slice_rows_k<5>(M, bs, n, batch, pl, exps, st, gate);
+        case 6: return slice_rows_k<6>(M, bs, n, batch, pl, exps, st, gate);
+        case 7: return slice_rows_k<7>(M, bs, n, batch, pl, exps, st, gate);
+        default: return slice_rows_k<8>(M, bs, n, batch, pl, exps, st, gate);
+    }
+}
+
+namespace {
+template <int KS>
+mpps_status slice_rows_pre_k(const double* M, long long bs, int n, int batch, __nv_bfloat16* pl,
+                             int* exps, const int* rmax, int* rclear, cudaStream_t st,
+                             const int* gate) {
+    const int lld = low_ld(n);
+    const long long goff = digit_offset(KS), pbs = (long long)num_pairs(KS) * n * 2 * lld;
+    const int n32 = (n + KB - 1) / KB * KB;
+    const int gy = n < 65535 ? n : 65535;
+    if (n % 4 == 0 && ((uintptr_t)M & 15) == 0 && bs % 2 == 0) {
+        const int gx = (n32 / 4 + 255) / 256;
+        MPPS_CUDA_TRY(launch_pdl(k_slice_rows_pre<KS, 4>, dim3(gx, gy, batch), dim3(256), 0, st, M, bs, n,
+                                 goff, rmax, rclear, pl, pbs, lld, exps, gate));
+    } else {
+        const int gx = (n32 + 255) / 256;
+        MPPS_CUDA_TRY(launch_pdl(k_slice_rows_pre<KS, 1>, dim3(gx, gy, batch), dim3(256), 0, st, M, bs, n,
+                                 goff, rmax, rclear, pl, pbs, lld, exps, gate));
+    }
+    MPPS_LAUNCH_CHECK();
+    return MPPS_OK;
+}
+}  // namespace
+
+mpps_status launch_slice_rows_pre(const double* M, long long bs, int n, int batch, int k,
+                                  void* planes, int* exps, const int* rmax, int* rmax_clear,
+                                  cudaStream_t st, const int* gate) {
+    k = f64e_planes(k);
+    ProfScope prof(MPPS_PROF_SLICE, st);
+    if (batch > 65535) {
+        set_error("slice_rows: batch %d exceeds the grid limit", batch);
+        return MPPS_EINVAL;
+    }
+    __nv_bfloat16* pl = (__nv_bfloat16*)planes;
+    switch (k) {
+        case 1: return slice_rows_pre_k<1>(M, bs, n, batch, pl, exps, rmax, rmax_clear, st, gate);
+        case 2: return slice_rows_pre_k<2>(M, bs, n, batch, pl, exps, rmax, rmax_clear, st, gate);
+        case 3: return slice_rows_pre_k<3>(M, bs, n, batch, pl, exps, rmax, rmax_clear, st, gate);
+        case 4: return slice_rows_pre_k<4>(M, bs, n, batch, pl, exps, rmax, rmax_clear, st, gate);
+        case 5: return slice_rows_pre_k<5>(M, bs, n, batch, pl, exps, rmax, rmax_clear, st, gate);
+        case 6: return slice_rows_pre_k<6>(M, bs, n, batch, pl, exps, rmax, rmax_clear, st, gate);
+        case 7: return slice_rows_pre_k<7>(M, bs, n, batch, pl, exps, rmax, rmax_clear, st, gate);
+        default: return slice_rows_pre_k<8>(M, bs, n, batch, pl, exps, rmax, rmax_clear, st, gate);
+    }
+}
+
+mpps_status launch_slice_cols_pre(const double* M, long long bs, int n, int batch, int k,
+                                  void* planes, int* exps, const int* cmax, cudaStream_t st,
+                                  const int* gate) {
+    k = f64e_planes(k);
+    ProfScope prof(MPPS_PROF_SLICE, st);
+    __nv_bfloat16* pl = (__nv_bfloat16*)planes;
+    switch (k) {
+        case 1: return slice_cols_k<1>(M, bs, n, batch, pl, exps, nullptr, st, cmax, gate);
+        case 2: return slice_cols_k<2>(M, bs, n, batch, pl, exps, nullptr, st, cmax, gate);
+        case 3: return slice_cols_k<3>(M, bs, n, batch, pl, exps, nullptr, st, cmax, gate);
+        case 4: return slice_cols_k<4>(M, bs, n, batch, pl, exps, nullptr, st, cmax, gate);
+        case 5: return slice_cols_k<5>(M, bs, n, batch, pl, exps, nullptr, st, cmax, gate);
+        case 6: return slice_cols_k<6>(M, bs, n, batch, pl, exps, nullptr, st, cmax, gate);
+        case 7: return slice_cols_k<7>(M, bs, n, batch, pl, exps, nullptr, st, cmax, gate);
+        default: return slice_cols_k<8>(M, bs, n, batch, pl, exps, nullptr, st, cmax, gate);
     }
 }
 
 mpps_status launch_slice_cols(const double* M, long long bs, int n, int batch, int k, void* planes,
-                              int* exps, unsigned long long* colmax, cudaStream_t st) {
+                              int* exps, unsigned long long* colmax, cudaStream_t st,
+                              const int* gate) {
     k = f64e_planes(k);
     ProfScope prof(MPPS_PROF_SLICE, st);
     MPPS_CUDA_TRY(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * (size_t)batch * n, st));
-    MPPS_CUDA_TRY(launch_pdl(k_colmax, dim3(dim3((n + 127) / 128, (n + 15) / 16, batch)), dim3(128), 0, st, M, bs, n, colmax));
+    MPPS_CUDA_TRY(launch_pdl(k_colmax, dim3(dim3((n + 127) / 128, (n + 15) / 16, batch)), dim3(128), 0, st, M, bs, n, colmax, gate));
     MPPS_LAUNCH_CHECK();
     __nv_bfloat16* pl = (__nv_bfloat16*)planes;
     switch (k) {
-        case 1: return slice_cols_k<1>(M, bs, n, batch, pl, exps, colmax, st);
-        case 2: return slice_cols_k<2>(M, bs, n, batch, pl, exps, colmax, st);
-        case 3: return slice_cols_k<3>(M, bs, n, batch, pl, exps, colmax, st);
-        case 4: return slice_cols_k<4>(M, bs, n, batch, pl, exps, colmax, st);
-        case 5: return slice_cols_k<5>(M, bs, n, batch, pl, exps, colmax, st);
-        case 6: return slice_cols_k<6>(M, bs, n, batch, pl, exps, colmax, st);
-        case 7: return slice_cols_k<7>(M, bs, n, batch, pl, exps, colmax, st);
-        default: return slice_cols_k<8>(M, bs, n, batch, pl, exps, colmax, st);
+        case 1: return slice_cols_k<1>(M, bs, n, batch, pl, exps, colmax, st, nullptr, gate);
+        case 2: return slice_cols_k<2>(M, bs, n, batch, pl, exps, colmax, st, nullptr, gate);
+        case 3: return slice_cols_k<3>(M, bs, n, batch, pl, exps, colmax, st, nullptr, gate);
+        case 4: return slice_cols_k<4>(M, bs, n, batch, pl, exps, colmax, st, nullptr, gate);
+        case 5: return slice_cols_k<5>(M, bs, n, batch, pl, exps, colmax, st, nullptr, gate);
+        case 6: return slice_cols_k<6>(M, bs, n, batch, pl, exps, colmax, st, nullptr, gate);
+        case 7: return slice_cols_k<7>(M, bs, n, batch, pl, exps, colmax, st, nullptr, gate);
+        default: return slice_cols_k<8>(M, bs, n, batch, pl, exps, colmax, st, nullptr, gate);
     }
 }
 
@@ -1226,7 +1416,7 @@ mpps_status launch_gemm_f64e(int k, const void* slicesA, int ksA, const int* eA,
     // with tuning on, the first launch of an eligible shape times both schedules (not when
     // the epilogue accumulates into its own output: a re-run would add twice)
     const bool inplace = ep.add != nullptr && ep.add == ep.out;
-    if (can_split && tuned < 0 && !inplace && tune_enabled())
+    if (can_split && tuned < 0 && !inplace && !ep.dcount && tune_enabled())
         return tune_run(TUNE_F64E_SPLIT, n, batch, k, 2, st,
                         [&](int c) { return run(c == 1); });
     return run(tuned >= 0 ? tuned == 1 : rule);

@@ -134,6 +134,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t tmem = *tmem_slot;
     pdl_wait();   // barrier init, TMEM allocation and tensor-map prefetch overlap the previous kernel
     pdl_trigger();
+    if (ep.dcount && b >= __ldg(ep.dcount)) {   // not this launch's matrix (device plan)
+        tc_fence_before();
+        __syncthreads();
+        if (warp == 0)
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TN));
+        return;
+    }
 
     if (warp == 0 && lane == 0) {
         // TMA producer
@@ -345,7 +352,7 @@ mpps_status launch_gemm_tc(int fmt, const void* A_hi, const void* A_lo, const vo
     };
     const int tuned = tune_lookup(TUNE_TC_WIDTH, n, batch, fmt);
     const bool inplace = ep.add != nullptr && ep.add == ep.out;   // a re-run would add twice
-    if (tuned < 0 && !inplace && tune_enabled())
+    if (tuned < 0 && !inplace && !ep.dcount && tune_enabled())   // gated launches: no tuning
         return tune_run(TUNE_TC_WIDTH, n, batch, fmt, 2, st, run);
     return run(tuned >= 0 ? tuned : (narrow ? 0 : 1));
 }
