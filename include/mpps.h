@@ -196,11 +196,15 @@ typedef struct {
  * expm_taylor_ss, one sigma per matrix).  Matrices are bucketed by (n rounded up to a
  * multiple of 32, m); each bucket is zero-padded block-diagonally -- exact, since
  * p(diag(A, 0)) = diag(p(A), b_0 I) and ||diag(A, 0)||_1 = ||A||_1 -- and evaluated as one
- * batch, with per-matrix plans and operand scales; the n x n results are scattered back.
+ * batch with the precision rule on the GPU (as with policy.device_plan), per-matrix plans
+ * and operand scales; the n x n results are scattered back.  The buckets run on up to 8
+ * library streams that fork from `stream` and join it again, so small buckets overlap.
  *   items : host array of `count` descriptors (device matrix pointers).
  *   rep   : NULL, or `count` reports (host), in item order (norms include the padding's
  *           b_{is} I part of each block).
- * Synchronises `stream` once per bucket.
+ * With policy.max_squarings = 0 the call reads every sigma back once, early (one host wait,
+ * before the heavy work is enqueued); with max_squarings = k > 0 it reads nothing back and
+ * can be captured in a CUDA graph (see mpps_policy).  A report synchronises per bucket.
  */
 mpps_status expm_taylor_ss_grouped(const mpps_group_item* items, int count,
                                    const mpps_policy* policy, mpps_report* rep, void* stream);
