@@ -1091,6 +1091,12 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
         if (i - 1 == 0 && qform) ep.coef[0] -= 1.0;
         ep.pw = pw;
         ep.pw_bstride = pw_bs;
+        // P_{i-1} only feeds a low-precision product: its block sum in FP32 (Epilogue::sum32)
+        if (i - 1 >= 1 && (is_low(fmt[i - 1]) || fmt[i - 1] == MPPS_FMT_DEVICE)) {
+            ep.sum32 = fmt[i - 1] == MPPS_FMT_DEVICE ? 2 : 1;
+            if (ep.sum32 == 2) ep.sum32_fmt = &d_plan->fmt[i - 1];
+            for (int j = 0; j < s; ++j) ep.coef32[j] = (float)ep.coef[j];
+        }
         const bool dev_copy = i - 1 >= 1 && fmt[i - 1] == MPPS_FMT_DEVICE && has_low_copy(i - 1);
         if (dev_copy || (i - 1 >= 1 && is_low(fmt[i - 1]) && fmt[i - 1] != MPPS_FMT_FP8)) {
             ep.low_fmt = fmt[i - 1];
@@ -1121,6 +1127,11 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
         ep.pw = pw;
         ep.pw_bstride = pw_bs;
         ep.alpha = 0.0;
+        if (is_low(fmt[r]) || fmt[r] == MPPS_FMT_DEVICE) {   // P_r only feeds a low product
+            ep.sum32 = fmt[r] == MPPS_FMT_DEVICE ? 2 : 1;
+            if (ep.sum32 == 2) ep.sum32_fmt = &d_plan->fmt[r];
+            for (int j = 0; j <= ep.nt; ++j) ep.coef32[j] = (float)ep.coef[j];
+        }
         const bool dev_copy = fmt[r] == MPPS_FMT_DEVICE && has_low_copy(r);
         if (dev_copy || (is_low(fmt[r]) && fmt[r] != MPPS_FMT_FP8)) {
             ep.low_fmt = fmt[r];
