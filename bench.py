@@ -54,6 +54,8 @@ def parse():
                     help="comma list of policies timed beside the headline (fixed is always kept)")
     ap.add_argument("--no-check", action="store_true", help="skip the oracle error check")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="leave out the compact C3/C4/C5 results of the default line")
     ap.add_argument("--kernel", default=None,
                     choices=["gemm_f64", "gemm_bf16", "gemm_bf16x3", "gemm_tf32", "gemm_fp8",
                              "gemm_f64e9", "gemm_f64e8", "gemm_f64e6"],
@@ -225,9 +227,11 @@ POLICY_DESC = {
 }
 
 
-def run_config(args):
-    """The other workloads, one JSON line each (mixed policy vs fixed FP64, errors against the
-    oracle on a sample): C3 uneven batch, C4 adjoint batch, C5 n = 2048 general polynomials."""
+def run_config(args, which=None, steps=None, warmup=None, emit=True):
+    """The other workloads (mixed policy vs fixed FP64, errors against the oracle on a
+    sample, the dominant kernel class's executed-flop roofline from a profiled pass): C3
+    uneven batch, C4 adjoint batch, C5 n = 2048 general polynomials.  Prints one JSON line
+    (emit) and returns it."""
     import numpy as np
     import torch
 
@@ -235,11 +239,39 @@ def run_config(args):
     import paper_2312_17396_gb300 as mpps
     from paper_2312_17396_gb300 import inputs
 
+    which = which or args.config
+    steps = steps or args.steps
+    warmup = warmup if warmup is not None else args.warmup
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     mpps.lib()
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    classes = (mpps.PROF_GEMM_F64, mpps.PROF_GEMM_F64E, mpps.PROF_GEMM_TC, mpps.PROF_SLICE,
+               mpps.PROF_ELEMENTWISE)
+    cname = {mpps.PROF_GEMM_F64: "k_gemm_f64 (DMMA)", mpps.PROF_GEMM_F64E: "k_gemm_f64e (tcgen05)",
+             mpps.PROF_GEMM_TC: "k_gemm_tc (tcgen05)", mpps.PROF_SLICE: "slicing",
+             mpps.PROF_ELEMENTWISE: "elementwise"}
+
+    def roofline_of(step, step_ms, passes=2):
+        """Per-class CUDA-event times of the library's launches over `passes` steps (a
+        separate, profiled pass): the dominant class, its executed TFLOP/s and fraction."""
+        mpps.profile_enable(True)
+        mpps.profile_reset()
+        for _ in range(passes):
+            step()
+        torch.cuda.synchronize()
+        prof = {c: mpps.profile_read(c) for c in classes}
+        mpps.profile_enable(False)
+        mpps.profile_reset()
+        dom = max(classes, key=lambda c: prof[c][1])
+        launches, ms, work = prof[dom]
+        ach = work / (ms / 1e3) / 1e12 if ms > 0 and work > 0 else None
+        peak, src = (peak_fp64_tflops() if dom == mpps.PROF_GEMM_F64 else peak_bf16_tflops(step_ms))
+        return {"bound": "tensor", "kernel": cname[dom], "achieved": ach, "peak": peak,
+                "unit": "TFLOP/s", "frac": (ach / peak) if ach else None, "peak_source": src,
+                "share_of_step": ms / passes / step_ms if step_ms > 0 else None,
+                "launches_per_step": launches // passes}
 
     def timed(step, steps, warmup):
         for _ in range(warmup):
@@ -256,10 +288,10 @@ def run_config(args):
             ts.append(e0.elapsed_time(e1))
         return statistics.median(ts)
 
-    line = {"metric": METRIC, "unit": "evals/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "higher_is_better": True, "data": "synthetic",
+    line = {"metric": METRIC, "unit": "evals/s", "n_gpus": 1, "steps": steps,
+            "warmup": warmup, "higher_is_better": True, "data": "synthetic",
             "impl": "mpps", "vs_baseline": None}
-    if args.config == "c3":
+    if which == "c3":
         count = 4096
         mats, degs = inputs.uneven_batch(count, 8, 256, 0.1, 10.0, seed=3)
         dA = [torch.from_numpy(A).to(dev) for A in mats]
@@ -284,7 +316,7 @@ def run_config(args):
             else:
                 fn = (lambda pol=pol, outs=outs: mpps.expm_grouped(dA, degs, policy=pol, outs=outs))
             with ClockSampler(dev.index) as clk:
-                ms = timed(fn, args.steps, max(3, args.warmup))
+                ms = timed(fn, steps, max(3, warmup))
             flops = sum(2.0 * A.shape[0] ** 3 * sum(r["gemms"].values()) for A, r in zip(mats, reps))
             errs = []
             for k in range(0, count, count // 12):
@@ -294,6 +326,8 @@ def run_config(args):
             res[name] = {"evals_per_s": count / (ms / 1e3), "ms_per_step": ms,
                          "tflops": flops / (ms / 1e3) / 1e12, "max_rel_err_1norm_sampled": max(errs),
                          "clocks": clk.summary()}
+        line["roofline"] = roofline_of(lambda: mpps.expm_grouped(dA, degs, policy=mpps.NS_E),
+                                       res["ns_e"]["ms_per_step"])
         line.update({"value": res["ns_e"]["evals_per_s"], "ms_per_step": res["ns_e"]["ms_per_step"],
                      "dtype": "f64", "scaling": "weak",
                      "config": {"workload": "C3: 4096 matrices, n ~ U[8,256], ||A||_1 log-uniform in "
@@ -303,7 +337,7 @@ def run_config(args):
                                 "graph": "ns_e_graph: the same call captured once in a CUDA graph "
                                          "(max_squarings 5) and replayed"},
                      "policies": res})
-    elif args.config == "c4":
+    elif which == "c4":
         n, m, batch = 128, 18, 512
         rng = np.random.default_rng(4)
         A32 = torch.tensor(rng.standard_normal((batch, n, n)) / np.sqrt(n), dtype=torch.float32,
@@ -311,15 +345,17 @@ def run_config(args):
         G = torch.tensor(rng.standard_normal((batch, n, n)), dtype=torch.float32, device=dev)
         coef = mpps.taylor_exp_coeffs(m)
         res = {}
+        step_of = {}
         for name, pol in (("ns_e", mpps.NS_E), ("fixed", mpps.FIXED)):
             A = A32.clone().requires_grad_(True)
 
-            def step():
+            def step(A=A, pol=pol):
                 A.grad = None
                 P = mpps.poly(A, coef, pol)
                 P.backward(G)
+            step_of[name] = step
             with ClockSampler(dev.index) as clk:
-                ms = timed(step, args.steps, max(3, args.warmup))
+                ms = timed(step, steps, max(3, warmup))
             step()
             grad = A.grad.double().cpu().numpy()
             errs = []
@@ -329,6 +365,7 @@ def run_config(args):
                 errs.append(oracle.norm1(grad[b] - gh - gl) / oracle.norm1(gh))
             res[name] = {"evals_per_s": batch / (ms / 1e3), "ms_per_step": ms,
                          "max_rel_err_1norm_sampled": max(errs), "clocks": clk.summary()}
+        line["roofline"] = roofline_of(step_of["ns_e"], res["ns_e"]["ms_per_step"])
         line.update({"value": res["ns_e"]["evals_per_s"], "ms_per_step": res["ns_e"]["ms_per_step"],
                      "unit": "gradients/s", "dtype": "f32 storage, f64 evaluation", "scaling": "weak",
                      "config": {"workload": "C4: 512 x 128x128 FP32, N(0,1)/sqrt(n), Taylor exp m=18 "
@@ -361,13 +398,30 @@ def run_config(args):
                 out = torch.empty_like(dX)
                 _, rep = mpps.ps_eval(coef, dX, policy=pol, out=out, report=True)
                 with ClockSampler(dev.index) as clk:
-                    ms = timed(lambda: mpps.ps_eval(coef, dX, policy=pol, out=out), args.steps,
-                               max(3, args.warmup))
+                    ms = timed(lambda: mpps.ps_eval(coef, dX, policy=pol, out=out), steps,
+                               max(3, warmup))
                 P = out.cpu().numpy()[:, cols]
                 entry[pname] = {"evals_per_s": 1e3 / ms, "ms_per_step": ms,
                                 "rel_err_1norm_sampled_cols": oracle.norm1(P - ref) / oracle.norm1(ref),
                                 "formats": rep[0]["fmt"], "clocks": clk.summary()}
             res[name] = entry
+        # the full [13/13] Pade exp (one power chain, LU solve, squarings), checked against
+        # the emulated Taylor scaling and squaring of the same matrix
+        dA = torch.from_numpy(A).to(dev)
+        E_t = mpps.expm(dA, m=30, policy=pol_fixed_e)
+        entry = {}
+        for pname, pol in (("ns_e", pol_mixed), ("fixed", mpps.FIXED)):
+            out = torch.empty_like(dA)
+            mpps.expm_pade(dA, policy=pol, out=out)
+            with ClockSampler(dev.index) as clk:
+                ms = timed(lambda: mpps.expm_pade(dA, policy=pol, out=out), steps, max(3, warmup))
+            d = ((out - E_t).abs().sum(dim=0).max() / E_t.abs().sum(dim=0).max()).item()
+            entry[pname] = {"evals_per_s": 1e3 / ms, "ms_per_step": ms,
+                            "rel_diff_1norm_vs_taylor_expm": d, "clocks": clk.summary()}
+        res["expm_pade13"] = entry
+        coef0, X0 = jobs[0][1], torch.from_numpy(jobs[0][3]).to(dev)
+        line["roofline"] = roofline_of(lambda: mpps.ps_eval(coef0, X0, policy=pol_mixed),
+                                       res["pade13_num"]["ns_e"]["ms_per_step"])
         tot_mixed = sum(res[j[0]]["ns_e"]["ms_per_step"] for j in jobs[:3])
         tot_fixed = sum(res[j[0]]["fixed"]["ms_per_step"] for j in jobs[:3])
         line.update({"value": 1e3 / tot_mixed, "ms_per_step": tot_mixed,
@@ -378,7 +432,37 @@ def run_config(args):
                                             "in B = A^2; plus a scaled variant with ||X||_1 = 1",
                                 "policy": "ns_e (all formats, f64_slices=9)"},
                      "jobs": res})
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
+
+
+def compact(line):
+    """The headline fields of a config line: value, mixed over fixed, sampled errors,
+    roofline."""
+    out = {"workload": line["config"]["workload"], "value": line["value"], "unit": line["unit"],
+           "ms_per_step": line["ms_per_step"], "roofline": line.get("roofline")}
+    pol = line.get("policies")
+    if pol:
+        out["fixed_value"] = pol["fixed"]["evals_per_s"]
+        out["mixed_over_fixed"] = line["value"] / pol["fixed"]["evals_per_s"]
+        out["max_rel_err_mixed"] = pol["ns_e"]["max_rel_err_1norm_sampled"]
+        out["max_rel_err_fixed"] = pol["fixed"]["max_rel_err_1norm_sampled"]
+        if "ns_e_graph" in pol:
+            out["graph_replay_value"] = pol["ns_e_graph"]["evals_per_s"]
+    jobs = line.get("jobs")
+    if jobs:
+        out["fixed_value"] = line["fixed_value"]
+        out["mixed_over_fixed"] = line["value"] / line["fixed_value"]
+        out["rel_err_mixed"] = {k: v["ns_e"].get("rel_err_1norm_sampled_cols")
+                                for k, v in jobs.items() if "rel_err_1norm_sampled_cols" in v["ns_e"]}
+        out["rel_err_fixed"] = {k: v["fixed"].get("rel_err_1norm_sampled_cols")
+                                for k, v in jobs.items() if "rel_err_1norm_sampled_cols" in v["fixed"]}
+        if "expm_pade13" in jobs:
+            out["expm_pade13"] = {k: {"evals_per_s": v["evals_per_s"],
+                                      "rel_diff_vs_taylor": v["rel_diff_1norm_vs_taylor_expm"]}
+                                  for k, v in jobs["expm_pade13"].items()}
+    return out
 
 
 def peak_bf16_tflops(step_ms):
@@ -620,6 +704,14 @@ def main():
     }
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(n, m, mats)
+    if not args.no_configs and world == 1:
+        # the other workloads, compact, in the same line (fewer steps: a bounded run time)
+        line["configs"] = {}
+        for c in ("c3", "c4", "c5"):
+            try:
+                line["configs"][c] = compact(run_config(args, c, steps=3, warmup=2, emit=False))
+            except Exception as exc:   # pragma: no cover - reported, not hidden
+                line["configs"][c] = {"error": repr(exc)}
     print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

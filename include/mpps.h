@@ -210,6 +210,30 @@ mpps_status expm_taylor_ss_grouped(const mpps_group_item* items, int count,
                                    const mpps_policy* policy, mpps_report* rep, void* stream);
 
 /*
+ * One item of an uneven batch of polynomial evaluations: its own order n, degree m and
+ * coefficients b_0..b_m (host array, read during the call).  A and out are device pointers to
+ * n x n row-major FP64 matrices (out may not alias A).
+ */
+typedef struct {
+    const double* A;
+    double* out;
+    int n;
+    int m;
+    const double* coeffs;
+} mpps_poly_item;
+
+/*
+ * p(A) for `count` matrices of different orders, degrees and coefficients (Algorithm 2.1 /
+ * Algorithm 4.1 per matrix, the precision rule of eq. (2.8) per matrix): bucketed by (n
+ * rounded up to a multiple of 32, m, coefficients) and zero-padded as in
+ * expm_taylor_ss_grouped (p(diag(A, 0)) = diag(p(A), b_0 I)), each bucket planned on the GPU
+ * and the buckets run on forked streams.  No read-back unless `rep` is given; capturable in
+ * a CUDA graph.  items: host array of `count` descriptors; rep: NULL or `count` reports.
+ */
+mpps_status ps_eval_grouped(const mpps_poly_item* items, int count, const mpps_policy* policy,
+                            mpps_report* rep, void* stream);
+
+/*
  * Gradient of f(A) = <G, p_m(A)> = sum_ij G_ij p_m(A)_ij with respect to A, i.e. the
  * Frechet derivative L_p(A^T, G) (the paper states no adjoint; this is the derivative of
  * the PS evaluation of Algorithm 2.1 / 4.1, computed by reverse mode through its steps):

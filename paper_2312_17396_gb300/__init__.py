@@ -69,6 +69,11 @@ class _GroupItem(ctypes.Structure):
                 ("m", ctypes.c_int)]
 
 
+class _PolyItem(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("out", ctypes.c_void_p), ("n", ctypes.c_int),
+                ("m", ctypes.c_int), ("coeffs", ctypes.POINTER(ctypes.c_double))]
+
+
 class _Report(ctypes.Structure):
     _fields_ = [("s", ctypes.c_int), ("r", ctypes.c_int), ("nu", ctypes.c_int),
                 ("sigma", ctypes.c_int), ("fold", ctypes.c_int),
@@ -85,7 +90,7 @@ EXPORTS = ("mpps_policy_default", "mpps_plan", "ps_eval", "expm_taylor_ss", "ps_
            "expm_taylor_ss_adjoint", "mpps_choose_s", "mpps_autotune_enable",
            "mpps_autotune_clear", "mpps_autotune_entries", "expm_pade13", "mpps_plan_adjoint",
            "ps_eval_tape_bytes", "ps_eval_forward_tape", "ps_eval_adjoint_tape",
-           "ps_eval_adjoint_f32")
+           "ps_eval_adjoint_f32", "ps_eval_grouped")
 STORAGE_F64, STORAGE_F32 = 0, 1
 PROF_GEMM_F64, PROF_GEMM_TC, PROF_ELEMENTWISE, PROF_GEMM_F64E, PROF_SLICE = 0, 1, 2, 3, 4
 
@@ -138,6 +143,9 @@ def lib():
         L.expm_taylor_ss_grouped.argtypes = [ctypes.POINTER(_GroupItem), ip, ctypes.POINTER(_Policy),
                                              ctypes.POINTER(_Report), vp]
         L.expm_taylor_ss_grouped.restype = ctypes.c_int
+        L.ps_eval_grouped.argtypes = [ctypes.POINTER(_PolyItem), ip, ctypes.POINTER(_Policy),
+                                      ctypes.POINTER(_Report), vp]
+        L.ps_eval_grouped.restype = ctypes.c_int
         L.mpps_selftest_bounded_wait.argtypes = [ctypes.c_int, vp]
         L.mpps_selftest_bounded_wait.restype = ctypes.c_int
         L.mpps_release_workspace.argtypes = []
@@ -386,6 +394,36 @@ def expm_grouped(mats, degrees=None, policy: Policy | None = None, outs=None, re
     st = ctypes.c_void_p(int(stream)) if stream is not None else \
         ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     _check(lib().expm_taylor_ss_grouped(arr, count, ctypes.byref(pol), reps, st))
+    if report:
+        return outs, [_report_dict(r) for r in reps]
+    return outs
+
+
+def ps_eval_grouped(coeffs_list, mats, policy: Policy | None = None, outs=None, report: bool = False,
+                    stream=None):
+    """p_i(A_i) for many CUDA matrices of different orders, each with its own coefficient
+    sequence, in one call (ps_eval_grouped).  coeffs_list: one coefficient array per matrix
+    (equal sequences share a bucket)."""
+    torch = _torch()
+    count = len(mats)
+    if len(coeffs_list) != count:
+        raise ValueError("one coefficient sequence per matrix")
+    if outs is None:
+        outs = [torch.empty_like(a) for a in mats]
+    arr = (_PolyItem * max(1, count))()
+    keep = []
+    for i, (a, o, c) in enumerate(zip(mats, outs, coeffs_list)):
+        if not (_is_torch(a) and a.is_cuda and a.dtype == torch.float64 and a.is_contiguous()
+                and a.dim() == 2 and a.shape[0] == a.shape[1]):
+            raise ValueError("ps_eval_grouped takes contiguous square float64 CUDA tensors")
+        cc, cp, m = _coef_ptr(c)
+        keep.append(cc)
+        arr[i] = _PolyItem(a.data_ptr(), o.data_ptr(), int(a.shape[0]), int(m), cp)
+    reps = (_Report * count)() if report else None
+    pol = (policy or Policy())._c()
+    st = ctypes.c_void_p(int(stream)) if stream is not None else \
+        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    _check(lib().ps_eval_grouped(arr, count, ctypes.byref(pol), reps, st))
     if report:
         return outs, [_report_dict(r) for r in reps]
     return outs

@@ -1091,12 +1091,6 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
         if (i - 1 == 0 && qform) ep.coef[0] -= 1.0;
         ep.pw = pw;
         ep.pw_bstride = pw_bs;
-        // P_{i-1} only feeds a low-precision product: its block sum in FP32 (Epilogue::sum32)
-        if (i - 1 >= 1 && (is_low(fmt[i - 1]) || fmt[i - 1] == MPPS_FMT_DEVICE)) {
-            ep.sum32 = fmt[i - 1] == MPPS_FMT_DEVICE ? 2 : 1;
-            if (ep.sum32 == 2) ep.sum32_fmt = &d_plan->fmt[i - 1];
-            for (int j = 0; j < s; ++j) ep.coef32[j] = (float)ep.coef[j];
-        }
         const bool dev_copy = i - 1 >= 1 && fmt[i - 1] == MPPS_FMT_DEVICE && has_low_copy(i - 1);
         if (dev_copy || (i - 1 >= 1 && is_low(fmt[i - 1]) && fmt[i - 1] != MPPS_FMT_FP8)) {
             ep.low_fmt = fmt[i - 1];
@@ -1127,11 +1121,6 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
         ep.pw = pw;
         ep.pw_bstride = pw_bs;
         ep.alpha = 0.0;
-        if (is_low(fmt[r]) || fmt[r] == MPPS_FMT_DEVICE) {   // P_r only feeds a low product
-            ep.sum32 = fmt[r] == MPPS_FMT_DEVICE ? 2 : 1;
-            if (ep.sum32 == 2) ep.sum32_fmt = &d_plan->fmt[r];
-            for (int j = 0; j <= ep.nt; ++j) ep.coef32[j] = (float)ep.coef[j];
-        }
         const bool dev_copy = fmt[r] == MPPS_FMT_DEVICE && has_low_copy(r);
         if (dev_copy || (is_low(fmt[r]) && fmt[r] != MPPS_FMT_FP8)) {
             ep.low_fmt = fmt[r];
@@ -1340,6 +1329,139 @@ static mpps_status stage_in(const double* p, size_t elems, cudaStream_t st, Stag
 
 using namespace mpps;
 
+namespace mpps {
+// One member of an uneven batch, for the grouped evaluations.
+struct GItem {
+    const double* A;
+    double* out;
+    int n, m;
+    const double* c;   // m + 1 coefficients (host)
+};
+
+// Grouped evaluation (expm: Taylor exp with scaling and squaring, else p(A)); items checked.
+static mpps_status grouped_eval(const GItem* items, int count, const mpps_policy* policy,
+                                mpps_report* rep, cudaStream_t stream, bool expm) {
+    cudaStream_t st = stream;
+    Pol P = resolve(policy);
+    P.dplan = 1;   // every bucket planned on the device: no read-back between buckets
+    P.var_s = 0;
+    // buckets keyed by (padded order, degree, coefficients), in first-appearance order
+    struct Bucket { int n_pad, m; const double* c; std::vector<int> idx; };
+    std::vector<Bucket> buckets;
+    for (int i = 0; i < count; ++i) {
+        const int m = items[i].m;
+        const int np = (items[i].n + 31) / 32 * 32;
+        size_t k = 0;
+        while (k < buckets.size() &&
+               !(buckets[k].n_pad == np && buckets[k].m == m &&
+                 (buckets[k].c == items[i].c ||
+                  std::equal(items[i].c, items[i].c + m + 1, buckets[k].c))))
+            ++k;
+        if (k == buckets.size()) buckets.push_back({np, m, items[i].c, {}});
+        buckets[k].idx.push_back(i);
+    }
+    const int nb = (int)buckets.size();
+    struct Work {
+        DevBuf buf;
+        PadItem* d_list = nullptr;
+        double *dA = nullptr, *dO = nullptr, *partial = nullptr, *anorm = nullptr;
+        int* d_sig = nullptr;
+        std::vector<double> c;
+    };
+    std::vector<Work> wk(nb);
+    mpps_status rc = MPPS_OK;
+    // ---- phase A, on the caller's stream: every bucket gathered into its zero-padded batch,
+    // ||A||_1 and sigma per matrix (eq. (3.6))
+    for (int k = 0; k < nb; ++k) {
+        const Bucket& bk = buckets[k];
+        Work& w = wk[k];
+        const int cnt = (int)bk.idx.size();
+        if (cnt > 65535) {
+            set_error("expm_taylor_ss_grouped: more than 65535 items of one size and degree");
+            return MPPS_EINVAL;
+        }
+        const long long nn = (long long)bk.n_pad * bk.n_pad;
+        w.c.assign(bk.c, bk.c + bk.m + 1);
+        std::vector<PadItem> list(cnt);
+        for (int j = 0; j < cnt; ++j) {
+            const GItem& it = items[bk.idx[j]];
+            list[j] = PadItem{it.A, it.out, it.n, 0};
+        }
+        Arena a;
+        auto lay = [&](Arena& z) {
+            w.d_list = (PadItem*)z.take<char>(sizeof(PadItem) * cnt);
+            w.dA = z.take<double>((size_t)nn * cnt);
+            w.dO = z.take<double>((size_t)nn * cnt);
+            w.partial = z.take<double>(norm1_partial_elems(bk.n_pad, cnt));
+            w.anorm = z.take<double>(cnt);
+            w.d_sig = z.take<int>(cnt);
+        };
+        lay(a);
+        if ((rc = w.buf.alloc(a.off, st))) return rc;
+        a.base = (char*)w.buf.p;
+        a.off = 0;
+        lay(a);
+        if ((rc = launch_fill_bytes(w.d_list, list.data(), sizeof(PadItem) * cnt, st))) return rc;
+        if ((rc = launch_gather_pad(w.d_list, cnt, bk.n_pad, w.dA, st))) return rc;
+        if (!expm) continue;
+        if ((rc = launch_norm1(w.dA, nn, bk.n_pad, cnt, w.partial, w.anorm, st))) return rc;
+        if ((rc = launch_sigma(w.anorm, cnt, w.d_sig, st))) return rc;
+    }
+    // one read of every sigma (skipped with blind squarings: then nothing is read back)
+    std::vector<int> hsig;
+    if (expm && P.max_sq == 0) {
+        hsig.resize(count);
+        SigmaStage* sgs = nullptr;
+        if ((rc = sigma_stage(count, &sgs))) return rc;
+        size_t off = 0;
+        for (int k = 0; k < nb; ++k) {
+            const size_t cnt = buckets[k].idx.size();
+            MPPS_CUDA_TRY(cudaMemcpyAsync(sgs->h + off, wk[k].d_sig, sizeof(int) * cnt,
+                                          cudaMemcpyDeviceToHost, st));
+            off += cnt;
+        }
+        MPPS_CUDA_TRY(cudaEventRecord(sgs->ev, st));
+        MPPS_CUDA_TRY(cudaEventSynchronize(sgs->ev));
+        std::copy(sgs->h, sgs->h + count, hsig.begin());
+    }
+    // ---- phase B: the buckets on up to kAuxStreams streams that fork from the caller's
+    // stream and join it again, so that small buckets run side by side
+    std::vector<cudaStream_t> aux;
+    if ((rc = aux_streams(std::min(nb, kAuxStreams), &aux))) return rc;
+    cudaEvent_t fork_ev;
+    MPPS_CUDA_TRY(cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming));
+    MPPS_CUDA_TRY(cudaEventRecord(fork_ev, st));
+    for (cudaStream_t sx : aux) MPPS_CUDA_TRY(cudaStreamWaitEvent(sx, fork_ev, 0));
+    MPPS_CUDA_TRY(cudaEventDestroy(fork_ev));
+    size_t off = 0;
+    for (int k = 0; k < nb && !rc; ++k) {
+        const Bucket& bk = buckets[k];
+        Work& w = wk[k];
+        const int cnt = (int)bk.idx.size();
+        cudaStream_t sb = aux[k % aux.size()];
+        std::vector<mpps_report> brep(rep ? cnt : 0);
+        rc = eval_device(w.c.data(), bk.m, w.dA, bk.n_pad, cnt, P, w.dO, rep ? brep.data() : nullptr,
+                         sb, expm, false, nullptr, expm ? w.d_sig : nullptr,
+                         hsig.empty() ? nullptr : hsig.data() + off);
+        if (!rc) rc = launch_scatter_unpad(w.d_list, cnt, bk.n_pad, w.dO, sb);
+        if (!rc && rep)
+            for (int j = 0; j < cnt; ++j) rep[bk.idx[j]] = brep[j];
+        off += cnt;
+    }
+    // join (also after a failure, so that the workspaces are released in stream order)
+    for (cudaStream_t sx : aux) {
+        cudaEvent_t jev;
+        MPPS_CUDA_TRY(cudaEventCreateWithFlags(&jev, cudaEventDisableTiming));
+        MPPS_CUDA_TRY(cudaEventRecord(jev, sx));
+        MPPS_CUDA_TRY(cudaStreamWaitEvent(st, jev, 0));
+        MPPS_CUDA_TRY(cudaEventDestroy(jev));
+    }
+    return rc;
+}
+
+
+}  // namespace mpps
+
 extern "C" {
 
 void mpps_policy_default(mpps_policy* p) {
@@ -1501,121 +1623,46 @@ mpps_status expm_taylor_ss_grouped(const mpps_group_item* items, int count,
         mpps_status rc = check_same_device("expm_taylor_ss_grouped", {items[i].A, items[i].out});
         if (rc) return rc;
     }
-    cudaStream_t st = (cudaStream_t)stream;
-    Pol P = resolve(policy);
-    P.dplan = 1;   // every bucket planned on the device: no read-back between buckets
-    P.var_s = 0;
-    // buckets keyed by (padded order, degree), in first-appearance order
-    struct Bucket { int n_pad, m; std::vector<int> idx; };
-    std::vector<Bucket> buckets;
+    // Taylor coefficients b_i = 1/i! per degree, each quotient in extended precision
+    std::vector<std::vector<double>> taylor(171);
+    std::vector<GItem> g(count);
     for (int i = 0; i < count; ++i) {
         const int m = items[i].m <= 0 ? 30 : items[i].m;
-        const int np = (items[i].n + 31) / 32 * 32;
-        size_t k = 0;
-        while (k < buckets.size() && !(buckets[k].n_pad == np && buckets[k].m == m)) ++k;
-        if (k == buckets.size()) buckets.push_back({np, m, {}});
-        buckets[k].idx.push_back(i);
+        if (taylor[m].empty()) {
+            taylor[m].resize(m + 1);
+            long double f = 1.0L;
+            for (int j = 0; j <= m; ++j) {
+                if (j > 0) f /= (long double)j;
+                taylor[m][j] = (double)f;
+            }
+        }
+        g[i] = GItem{items[i].A, items[i].out, items[i].n, m, taylor[m].data()};
     }
-    const int nb = (int)buckets.size();
-    struct Work {
-        DevBuf buf;
-        PadItem* d_list = nullptr;
-        double *dA = nullptr, *dO = nullptr, *partial = nullptr, *anorm = nullptr;
-        int* d_sig = nullptr;
-        std::vector<double> c;
-    };
-    std::vector<Work> wk(nb);
-    mpps_status rc = MPPS_OK;
-    // ---- phase A, on the caller's stream: every bucket gathered into its zero-padded batch,
-    // ||A||_1 and sigma per matrix (eq. (3.6))
-    for (int k = 0; k < nb; ++k) {
-        const Bucket& bk = buckets[k];
-        Work& w = wk[k];
-        const int cnt = (int)bk.idx.size();
-        if (cnt > 65535) {
-            set_error("expm_taylor_ss_grouped: more than 65535 items of one size and degree");
+    return grouped_eval(g.data(), count, policy, rep, (cudaStream_t)stream, true);
+}
+
+mpps_status ps_eval_grouped(const mpps_poly_item* items, int count, const mpps_policy* policy,
+                            mpps_report* rep, void* stream) {
+    clear_error();
+    if (count < 0 || (count > 0 && !items)) {
+        set_error("ps_eval_grouped: invalid argument (count=%d)", count);
+        return MPPS_EINVAL;
+    }
+    if (count == 0) return MPPS_OK;
+    std::vector<GItem> g(count);
+    for (int i = 0; i < count; ++i) {
+        const mpps_poly_item& it = items[i];
+        if (it.n <= 0 || it.m < 0 || !it.coeffs || !it.A || !it.out || !is_device_ptr(it.A) ||
+            !is_device_ptr(it.out)) {
+            set_error("ps_eval_grouped: item %d invalid (n=%d, m=%d, coefficients and device "
+                      "pointers required)", i, it.n, it.m);
             return MPPS_EINVAL;
         }
-        const long long nn = (long long)bk.n_pad * bk.n_pad;
-        w.c.resize(bk.m + 1);
-        long double f = 1.0L;
-        for (int i = 0; i <= bk.m; ++i) {
-            if (i > 0) f /= (long double)i;
-            w.c[i] = (double)f;
-        }
-        std::vector<PadItem> list(cnt);
-        for (int j = 0; j < cnt; ++j) {
-            const mpps_group_item& it = items[bk.idx[j]];
-            list[j] = PadItem{it.A, it.out, it.n, 0};
-        }
-        Arena a;
-        auto lay = [&](Arena& z) {
-            w.d_list = (PadItem*)z.take<char>(sizeof(PadItem) * cnt);
-            w.dA = z.take<double>((size_t)nn * cnt);
-            w.dO = z.take<double>((size_t)nn * cnt);
-            w.partial = z.take<double>(norm1_partial_elems(bk.n_pad, cnt));
-            w.anorm = z.take<double>(cnt);
-            w.d_sig = z.take<int>(cnt);
-        };
-        lay(a);
-        if ((rc = w.buf.alloc(a.off, st))) return rc;
-        a.base = (char*)w.buf.p;
-        a.off = 0;
-        lay(a);
-        if ((rc = launch_fill_bytes(w.d_list, list.data(), sizeof(PadItem) * cnt, st))) return rc;
-        if ((rc = launch_gather_pad(w.d_list, cnt, bk.n_pad, w.dA, st))) return rc;
-        if ((rc = launch_norm1(w.dA, nn, bk.n_pad, cnt, w.partial, w.anorm, st))) return rc;
-        if ((rc = launch_sigma(w.anorm, cnt, w.d_sig, st))) return rc;
+        mpps_status rc = check_same_device("ps_eval_grouped", {it.A, it.out});
+        if (rc) return rc;
+        g[i] = GItem{it.A, it.out, it.n, it.m, it.coeffs};
     }
-    // one read of every sigma (skipped with blind squarings: then nothing is read back)
-    std::vector<int> hsig;
-    if (P.max_sq == 0) {
-        hsig.resize(count);
-        SigmaStage* sgs = nullptr;
-        if ((rc = sigma_stage(count, &sgs))) return rc;
-        size_t off = 0;
-        for (int k = 0; k < nb; ++k) {
-            const size_t cnt = buckets[k].idx.size();
-            MPPS_CUDA_TRY(cudaMemcpyAsync(sgs->h + off, wk[k].d_sig, sizeof(int) * cnt,
-                                          cudaMemcpyDeviceToHost, st));
-            off += cnt;
-        }
-        MPPS_CUDA_TRY(cudaEventRecord(sgs->ev, st));
-        MPPS_CUDA_TRY(cudaEventSynchronize(sgs->ev));
-        std::copy(sgs->h, sgs->h + count, hsig.begin());
-    }
-    // ---- phase B: the buckets on up to kAuxStreams streams that fork from the caller's
-    // stream and join it again, so that small buckets run side by side
-    std::vector<cudaStream_t> aux;
-    if ((rc = aux_streams(std::min(nb, kAuxStreams), &aux))) return rc;
-    cudaEvent_t fork_ev;
-    MPPS_CUDA_TRY(cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming));
-    MPPS_CUDA_TRY(cudaEventRecord(fork_ev, st));
-    for (cudaStream_t sx : aux) MPPS_CUDA_TRY(cudaStreamWaitEvent(sx, fork_ev, 0));
-    MPPS_CUDA_TRY(cudaEventDestroy(fork_ev));
-    size_t off = 0;
-    for (int k = 0; k < nb && !rc; ++k) {
-        const Bucket& bk = buckets[k];
-        Work& w = wk[k];
-        const int cnt = (int)bk.idx.size();
-        cudaStream_t sb = aux[k % aux.size()];
-        std::vector<mpps_report> brep(rep ? cnt : 0);
-        rc = eval_device(w.c.data(), bk.m, w.dA, bk.n_pad, cnt, P, w.dO, rep ? brep.data() : nullptr,
-                         sb, true, false, nullptr, w.d_sig, hsig.empty() ? nullptr : hsig.data() + off);
-        if (!rc) rc = launch_scatter_unpad(w.d_list, cnt, bk.n_pad, w.dO, sb);
-        if (!rc && rep)
-            for (int j = 0; j < cnt; ++j) rep[bk.idx[j]] = brep[j];
-        off += cnt;
-    }
-    // join (also after a failure, so that the workspaces are released in stream order)
-    for (cudaStream_t sx : aux) {
-        cudaEvent_t jev;
-        MPPS_CUDA_TRY(cudaEventCreateWithFlags(&jev, cudaEventDisableTiming));
-        MPPS_CUDA_TRY(cudaEventRecord(jev, sx));
-        MPPS_CUDA_TRY(cudaStreamWaitEvent(st, jev, 0));
-        MPPS_CUDA_TRY(cudaEventDestroy(jev));
-    }
-    return rc;
+    return grouped_eval(g.data(), count, policy, rep, (cudaStream_t)stream, false);
 }
 
 mpps_status mpps_matmul(const double* A, const double* B, double* C, int n, int batch, int format,
@@ -2577,7 +2624,7 @@ mpps_status expm_pade13(const double* A, int n, int batch, const mpps_policy* po
         d_sigma = z.take<int>(batch);
         d_lists = z.take<int>((size_t)batch * 64);
         ipiv = z.take<int>((size_t)n);
-        info = z.take<int>(1);
+        info = z.take<int>((size_t)2 * batch);   // getrf and getrs info per matrix
         if (!o_dev) dOut = z.take<double>(elems);
         if (K > 0) {
             slA = z.take<__nv_bfloat16>(f64e_plane_elems(n, batch, K));
@@ -2668,8 +2715,9 @@ mpps_status expm_pade13(const double* A, int n, int batch, const mpps_policy* po
     // ---- R = q^-1 p.  p and q commute (both polynomials in X), so R^T = (Q^T)^-1 P^T: the
     // row-major Q and P, read column-major, are Q^T and P^T, and the column-major solution
     // written over P is R in row-major order
-    // (q_13 has no zeros in the disc |x| <= theta_13, so q(X) is nonsingular there and the
-    // factorisation's info word is not read back)
+    // (q_13 has no zeros in the disc |x| <= theta_13, so the exact q(X) is nonsingular there;
+    // the info words are still read back at the end: q assembled under a mixed policy is not
+    // the exact one)
     {
         std::lock_guard<std::mutex> lk(g_solvecall);
         if (S->set_stream(sh, st) != CUSOLVER_STATUS_SUCCESS) {
@@ -2679,8 +2727,9 @@ mpps_status expm_pade13(const double* A, int n, int batch, const mpps_policy* po
         for (int b = 0; b < batch; ++b) {
             double* Qb = Q + (size_t)b * nn;
             double* Pb = P + (size_t)b * nn;
-            if (S->getrf(sh, n, n, Qb, n, work, ipiv, info) != CUSOLVER_STATUS_SUCCESS ||
-                S->getrs(sh, CUBLAS_OP_N, n, n, Qb, n, ipiv, Pb, n, info) != CUSOLVER_STATUS_SUCCESS) {
+            if (S->getrf(sh, n, n, Qb, n, work, ipiv, info + 2 * b) != CUSOLVER_STATUS_SUCCESS ||
+                S->getrs(sh, CUBLAS_OP_N, n, n, Qb, n, ipiv, Pb, n, info + 2 * b + 1) !=
+                    CUSOLVER_STATUS_SUCCESS) {
                 set_error("expm_pade13: LU solve failed for matrix %d", b);
                 return MPPS_ECUDA;
             }
@@ -2707,6 +2756,8 @@ mpps_status expm_pade13(const double* A, int n, int batch, const mpps_policy* po
     }
     if ((rc = launch_select_copy(buf[0], buf[1], d_sigma, dOut, n, batch, 0.0, st))) return rc;
     if (K > 0 && (rc = dev_err_enqueue(derr, st))) return rc;
+    std::vector<int> hinfo((size_t)2 * batch);
+    MPPS_CUDA_TRY(cudaMemcpyAsync(hinfo.data(), info, sizeof(int) * hinfo.size(), cudaMemcpyDeviceToHost, st));
     if (!o_dev) {
         MPPS_CUDA_TRY(cudaMemcpyAsync(out, dOut, elems * sizeof(double), cudaMemcpyDeviceToHost, st));
         MPPS_CUDA_TRY(cudaStreamSynchronize(st));
@@ -2715,6 +2766,12 @@ mpps_status expm_pade13(const double* A, int n, int batch, const mpps_policy* po
         MPPS_CUDA_TRY(cudaStreamSynchronize(st));   // the LU pivots and info live in this call's workspace
         if (K > 0 && (rc = dev_err_check(derr, true))) return rc;
     }
+    for (int b = 0; b < batch; ++b)
+        if (hinfo[2 * b] != 0 || hinfo[2 * b + 1] != 0) {
+            set_error("expm_pade13: the LU factorisation of q(X) of matrix %d failed (info %d, %d)",
+                      b, hinfo[2 * b], hinfo[2 * b + 1]);
+            return MPPS_ECHECK;
+        }
     return MPPS_OK;
 }
 

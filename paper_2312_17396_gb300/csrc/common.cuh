@@ -123,20 +123,7 @@ struct Epilogue {
     // here; a copy is written only for BF16, TF32 and BF16X3 (FP8 copies are row-scaled by
     // their own pass)
     const int* low_fmt_dev;
-    // 1: the block sum sum_j coef[j] X_j is accumulated in FP32 (the value produced only feeds
-    // a product whose inputs are rounded to a low-precision format, u >= 2^-16: the FP32
-    // rounding of the sum is at least 2^8 below that rounding); the product term and the
-    // final add stay FP64
-    int sum32;                    // 2: decided on the device, 1 when *sum32_fmt is low
-    const int* sum32_fmt;
-    float coef32[MPPS_MAX_S + 1];
 };
-
-__device__ __forceinline__ bool epilogue_sum32(const Epilogue& ep) {
-    if (ep.sum32 != 2) return ep.sum32 == 1;
-    const int f = __ldg(ep.sum32_fmt);
-    return f >= MPPS_FMT_BF16X3 && f <= MPPS_FMT_FP8;
-}
 
 // low_fmt value meaning "read the format from Epilogue::low_fmt_dev".
 constexpr int MPPS_FMT_DEVICE = 100;
@@ -154,9 +141,6 @@ inline Epilogue epilogue_plain(double* out, long long out_bstride) {
     e.rmax = nullptr; e.cmax = nullptr;
     e.dcount = nullptr;
     e.low_fmt_dev = nullptr;
-    e.sum32 = 0;
-    e.sum32_fmt = nullptr;
-    for (int j = 0; j <= MPPS_MAX_S; ++j) e.coef32[j] = 0.f;
     return e;
 }
 
@@ -190,13 +174,6 @@ __device__ __forceinline__ bool f64_round_bits(double x, unsigned* out) {
     const unsigned long long r = m + ((1ULL << (DROP - 1)) - 1ULL) + ((m >> DROP) & 1ULL);
     *out = sgn | ((((unsigned)e << KEEP) + (unsigned)(r >> DROP)) << (23 - KEEP));
     return true;
-}
-
-// FP64 -> FP32 rounded to nearest even on the integer pipe (the conversion instruction for
-// values outside the normal FP32 range).
-__device__ __forceinline__ float f64_to_f32_int(double x) {
-    unsigned bits;
-    return f64_round_bits<23>(x, &bits) ? __uint_as_float(bits) : (float)x;
 }
 
 __device__ __forceinline__ void store_low(int fmt, void* hi, void* lo, long long idx, double v) {
@@ -263,17 +240,10 @@ __device__ __forceinline__ double epilogue_value(const Epilogue& ep, int b, int 
     if (ep.row_exp)
         v = mul_exp2(v, ep.row_exp[(long long)b * n + row] + ep.col_exp[(long long)b * n + col]);
     if (ep.nt >= 0) {
+        if (row == col) v += ep.coef[0];
         const double* base = ep.pw + (long long)b * ep.pw_bstride + (long long)row * n + col;
         const long long nn = (long long)n * n;
-        if (epilogue_sum32(ep)) {
-            float a = row == col ? ep.coef32[0] : 0.f;
-            for (int j = 1; j <= ep.nt; ++j)
-                a = fmaf(ep.coef32[j], f64_to_f32_int(__ldg(base + (long long)(j - 1) * nn)), a);
-            v += f32_to_f64(a);
-        } else {
-            if (row == col) v += ep.coef[0];
-            for (int j = 1; j <= ep.nt; ++j) v += ep.coef[j] * __ldg(base + (long long)(j - 1) * nn);
-        }
+        for (int j = 1; j <= ep.nt; ++j) v += ep.coef[j] * __ldg(base + (long long)(j - 1) * nn);
     }
     if (ep.add) v += ep.add_coef * ep.add[(long long)b * ep.add_bstride + (long long)row * n + col];
     return v;
@@ -298,27 +268,7 @@ __device__ __forceinline__ void epilogue_value4(const Epilogue& ep, int b, int r
             v[u] = mul_exp2(v[u], re + ep.col_exp[(long long)b * n + col0 + u]);
     }
     const long long off = (long long)row * n + col0;
-    if (ep.nt >= 0 && epilogue_sum32(ep)) {
-        const int dc = row - col0;
-        float a[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (dc == u) a[u] = ep.coef32[0];
-        const double* base = ep.pw + (long long)b * ep.pw_bstride + off;
-        const long long nn = (long long)n * n;
-        for (int j = 1; j <= ep.nt; ++j) {
-            const double* pp = base + (long long)(j - 1) * nn;
-            const double2 p01 = __ldg(reinterpret_cast<const double2*>(pp));
-            const double2 p23 = __ldg(reinterpret_cast<const double2*>(pp + 2));
-            const float c = ep.coef32[j];
-            a[0] = fmaf(c, f64_to_f32_int(p01.x), a[0]);
-            a[1] = fmaf(c, f64_to_f32_int(p01.y), a[1]);
-            a[2] = fmaf(c, f64_to_f32_int(p23.x), a[2]);
-            a[3] = fmaf(c, f64_to_f32_int(p23.y), a[3]);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) v[u] += f32_to_f64(a[u]);
-    } else if (ep.nt >= 0) {
+    if (ep.nt >= 0) {
         const int dc = row - col0;
 #pragma unroll
         for (int u = 0; u < 4; ++u)

@@ -356,9 +356,11 @@ __global__ void __launch_bounds__(256) k_slice_rows_blk4(const double* __restric
 
 // Row slices with the row maxima already known (recorded by the epilogue of the product that
 // wrote M): a streaming pass with no reduction.  V consecutive columns per thread (V = 4:
-// n a multiple of 4, 16-byte aligned rows), grid (column groups, rows, matrices); the K tail
-// up to round_up(n, KB) is written as zeros.  Column group 0 also writes the row's exponent
-// and zeroes the row's entry of rclear (the maxima buffer the next product fills).
+// n a multiple of 4, 16-byte aligned rows); a 256-thread block covers 256 / TPR rows of TPR
+// threads each (TPR = the threads a row needs, a power of two up to 256), grid (column
+// groups, row groups, matrices); the K tail up to round_up(n, KB) is written as zeros.
+// Column group 0 also writes the row's exponent and zeroes the row's entry of rclear (the
+// maxima buffer the next product fills).
 template <int KS, int V>
 __global__ void __launch_bounds__(256) k_slice_rows_pre(const double* __restrict__ M, long long bs, int n,
                                                         long long goff,
@@ -374,10 +376,13 @@ __global__ void __launch_bounds__(256) k_slice_rows_pre(const double* __restrict
     const int b = blockIdx.z;
     const int n32 = (n + KB - 1) / KB * KB;
     const long long pstride = (long long)n * 2 * lld;
-    for (int row = blockIdx.y; row < n; row += gridDim.y) {
+    int tpr = 1;   // threads per row: a power of two covering n32 / V columns, at most 256
+    while (tpr < 256 && tpr * V < n32) tpr <<= 1;
+    const int rpb = 256 / tpr, sub = threadIdx.x / tpr, lt = threadIdx.x % tpr;
+    for (int row = blockIdx.y * rpb + sub; row < n; row += gridDim.y * rpb) {
         const long long ri = (long long)b * n + row;
         const int e = exp_from_code(rmax[ri]);
-        const int j = V * (blockIdx.x * blockDim.x + threadIdx.x);
+        const int j = V * (blockIdx.x * tpr + lt);
         if (j == 0) {
             exps[ri] = e;
             if (rclear) rclear[ri] = 0;
@@ -1267,14 +1272,19 @@ mpps_status slice_rows_pre_k(const double* M, long long bs, int n, int batch, __
     const int lld = low_ld(n);
     const long long goff = digit_offset(KS), pbs = (long long)num_pairs(KS) * n * 2 * lld;
     const int n32 = (n + KB - 1) / KB * KB;
-    const int gy = n < 65535 ? n : 65535;
+    // the kernel's mapping: TPR threads per row, 256 / TPR rows per block
+    auto grid_for = [&](int V) {
+        int tpr = 1;
+        while (tpr < 256 && tpr * V < n32) tpr <<= 1;
+        const int gx = (n32 / V + tpr - 1) / tpr;
+        const int rows = (n + 256 / tpr - 1) / (256 / tpr);
+        return dim3(gx, rows < 65535 ? rows : 65535, batch);
+    };
     if (n % 4 == 0 && ((uintptr_t)M & 15) == 0 && bs % 2 == 0) {
-        const int gx = (n32 / 4 + 255) / 256;
-        MPPS_CUDA_TRY(launch_pdl(k_slice_rows_pre<KS, 4>, dim3(gx, gy, batch), dim3(256), 0, st, M, bs, n,
+        MPPS_CUDA_TRY(launch_pdl(k_slice_rows_pre<KS, 4>, grid_for(4), dim3(256), 0, st, M, bs, n,
                                  goff, rmax, rclear, pl, pbs, lld, exps, gate));
     } else {
-        const int gx = (n32 + 255) / 256;
-        MPPS_CUDA_TRY(launch_pdl(k_slice_rows_pre<KS, 1>, dim3(gx, gy, batch), dim3(256), 0, st, M, bs, n,
+        MPPS_CUDA_TRY(launch_pdl(k_slice_rows_pre<KS, 1>, grid_for(1), dim3(256), 0, st, M, bs, n,
                                  goff, rmax, rclear, pl, pbs, lld, exps, gate));
     }
     MPPS_LAUNCH_CHECK();

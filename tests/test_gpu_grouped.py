@@ -89,3 +89,48 @@ def test_grouped_captured_in_a_cuda_graph(mpps):
         n = new[k].shape[0]
         assert oracle.rel_err_1norm(outs[k].cpu().numpy(), eh, el) <= 50 * n * U * max(1, 2 ** sg) + \
             np.e / float(oracle.math.factorial(degs[k] + 1)) * 2 ** sg
+
+
+def test_ps_eval_grouped_general_coefficients(mpps):
+    """Uneven orders with three different coefficient sequences (Taylor exp, the Pade
+    numerator, the Taylor cosine in B): each matrix against the oracle's PS in
+    double-double, and its report against the single-matrix call's plan."""
+    rng = np.random.default_rng(17)
+    seqs = [(mpps.taylor_exp_coeffs(18), oracle.taylor_exp_rational(18)),
+            (mpps.pade_exp_num_coeffs(13), oracle.pade_exp_num_rational(13)),
+            (mpps.cos_taylor_coeffs(8), oracle.cos_taylor_rational(8))]
+    ns = [5, 31, 33, 64, 70, 100, 129, 17, 48, 96, 1, 40]
+    mats, coefs, rats = [], [], []
+    for k, n in enumerate(ns):
+        A = rng.standard_normal((n, n))
+        A *= rng.uniform(0.2, 1.0) / np.abs(A).sum(axis=0).max()
+        c, q = seqs[k % 3]
+        mats.append(A); coefs.append(c); rats.append(q)
+    outs, reps = mpps.ps_eval_grouped(coefs, [dev(A) for A in mats], policy=mpps.NS_E, report=True)
+    for A, P, q, R in zip(mats, outs, rats, reps):
+        n = A.shape[0]
+        ph, pl, _ = oracle.ps_dd(q, A)
+        assert oracle.rel_err_1norm(P.cpu().numpy(), ph, pl) <= 50 * n * U, n
+        m = len(q) - 1
+        assert (R["s"], R["r"]) == (oracle.ceil_sqrt(m), m // oracle.ceil_sqrt(m))
+
+
+def test_shard_expm_local_two_ranks_in_sequence(mpps):
+    """The multi-rank path on one GPU: rank 0 and rank 1 of a world of two evaluate their
+    shards (shard.expm_local, no collective) one after the other; together they cover every
+    matrix once and each result matches the oracle."""
+    from paper_2312_17396_gb300 import shard
+    mats, degs = inputs.uneven_batch(40, 8, 96, 0.1, 10.0, seed=23)
+    dA = [dev(A) for A in mats]
+    got = {}
+    for rank in (0, 1):
+        idx, outs = shard.expm_local(dA, degs, rank, 2, policy=mpps.NS_E)
+        for i, E in zip(idx, outs):
+            assert i not in got
+            got[i] = E.cpu().numpy()
+    assert sorted(got) == list(range(len(mats)))
+    for i, A in enumerate(mats):
+        n, sg = A.shape[0], oracle.sigma_for(A)
+        eh, el = oracle.expm_ss_dd(A, degs[i], sg)
+        trunc = np.e / float(oracle.math.factorial(degs[i] + 1)) * 2 ** sg
+        assert oracle.rel_err_1norm(got[i], eh, el) <= 50 * n * U * max(1, 2 ** sg) + trunc, i
