@@ -32,10 +32,10 @@ sys.path.insert(0, ROOT)
 METRIC = "p(A) evals/s and TFLOP/s, mixed vs fixed FP64 PS, at equal 1-norm rel. error"
 NORMS = (0.5, 4.0, 32.0)
 C2_FORMATS = ("fp64", "bf16x3", "tf32", "bf16")
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_gemm_f64e<8> launch at n = 1024 from the
-# ncu capture summarised in profiles/gemm_f64e_n1024_bench.md (None until the current kernel
-# has been captured)
-F64E_N1024_DRAM_BYTES = 33.96e6
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_gemm_f64e<8> power-product launch at
+# n = 1024 from the ncu capture summarised in profiles/gemm_f64e_n1024_bench.md (None until
+# the current kernel has been captured)
+F64E_N1024_DRAM_BYTES = 33.98e6
 SEED = 2
 
 
@@ -299,6 +299,8 @@ def run_config(args, which=None, steps=None, warmup=None, emit=True):
         # ||A||_1 <= 10: sigma <= 4, so five blind squaring steps cover every matrix and the
         # whole grouped call can be captured in a CUDA graph (nothing is read back)
         graph_pol = dataclasses.replace(mpps.NS_E, max_squarings=5)
+        refs = {k: oracle.expm_ss_dd(mats[k], int(degs[k]), oracle.sigma_for(mats[k]))
+                for k in range(0, count, count // 12)}   # the oracle on a sample, once
         for name, pol in (("ns_e", mpps.NS_E), ("ns_e_graph", graph_pol), ("fixed", mpps.FIXED)):
             outs = [torch.empty_like(a) for a in dA]
             _, reps = mpps.expm_grouped(dA, degs, policy=pol, outs=outs, report=True)
@@ -318,11 +320,7 @@ def run_config(args, which=None, steps=None, warmup=None, emit=True):
             with ClockSampler(dev.index) as clk:
                 ms = timed(fn, steps, max(3, warmup))
             flops = sum(2.0 * A.shape[0] ** 3 * sum(r["gemms"].values()) for A, r in zip(mats, reps))
-            errs = []
-            for k in range(0, count, count // 12):
-                sig = oracle.sigma_for(mats[k])
-                eh, el = oracle.expm_ss_dd(mats[k], int(degs[k]), sig)
-                errs.append(oracle.rel_err_1norm(outs[k].cpu().numpy(), eh, el))
+            errs = [oracle.rel_err_1norm(outs[k].cpu().numpy(), eh, el) for k, (eh, el) in refs.items()]
             res[name] = {"evals_per_s": count / (ms / 1e3), "ms_per_step": ms,
                          "tflops": flops / (ms / 1e3) / 1e12, "max_rel_err_1norm_sampled": max(errs),
                          "clocks": clk.summary()}
@@ -346,6 +344,8 @@ def run_config(args, which=None, steps=None, warmup=None, emit=True):
         coef = mpps.taylor_exp_coeffs(m)
         res = {}
         step_of = {}
+        grefs = {b: oracle.adjoint_dd(oracle.taylor_exp_rational(m), A32[b].double().cpu().numpy(),
+                                      G[b].double().cpu().numpy()) for b in (0, batch // 2, batch - 1)}
         for name, pol in (("ns_e", mpps.NS_E), ("fixed", mpps.FIXED)):
             A = A32.clone().requires_grad_(True)
 
@@ -358,11 +358,7 @@ def run_config(args, which=None, steps=None, warmup=None, emit=True):
                 ms = timed(step, steps, max(3, warmup))
             step()
             grad = A.grad.double().cpu().numpy()
-            errs = []
-            for b in (0, batch // 2, batch - 1):
-                gh, gl = oracle.adjoint_dd(oracle.taylor_exp_rational(m),
-                                           A32[b].double().cpu().numpy(), G[b].double().cpu().numpy())
-                errs.append(oracle.norm1(grad[b] - gh - gl) / oracle.norm1(gh))
+            errs = [oracle.norm1(grad[b] - gh - gl) / oracle.norm1(gh) for b, (gh, gl) in grefs.items()]
             res[name] = {"evals_per_s": batch / (ms / 1e3), "ms_per_step": ms,
                          "max_rel_err_1norm_sampled": max(errs), "clocks": clk.summary()}
         line["roofline"] = roofline_of(step_of["ns_e"], res["ns_e"]["ms_per_step"])
@@ -594,6 +590,42 @@ def main():
                       "formats": [R["fmt"][1:] for R in reps[p]],
                       "policy": POLICY_DESC[p], "_prof": prof}
 
+    # the same three evaluations on three streams (independent problems overlap; the device
+    # plan keeps the host from waiting between them): reported beside the headline
+    conc = None
+    if world == 1:
+        dpol = dataclasses.replace(pols[head], device_plan=True)
+        side = [torch.cuda.Stream(dev) for _ in dA]
+        couts = [torch.empty_like(a) for a in dA]
+
+        def step_streams():
+            ev = torch.cuda.Event()
+            ev.record(stream)
+            for k in range(len(dA)):
+                side[k].wait_event(ev)
+                with torch.cuda.stream(side[k]):
+                    mpps.expm(dA[k], m=m, policy=dpol, out=couts[k])
+            for k in range(len(dA)):
+                stream.wait_stream(side[k])
+
+        for _ in range(max(3, args.warmup)):
+            step_streams()
+        torch.cuda.synchronize()
+        ct = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step_streams()
+            e1.record(stream)
+            e1.synchronize()
+            ct.append(e0.elapsed_time(e1))
+        cms = sum(ct) / len(ct)
+        same = all(torch.equal(couts[k], outs[head][k]) for k in range(len(dA)))
+        conc = {"value": len(dA) / (cms / 1e3), "unit": "evals/s", "ms_per_step": cms,
+                "policy": head + " with device_plan, one stream per matrix",
+                "same_bits_as_headline": bool(same)}
+
     # e2e: pinned host buffers through the C ABI (H2D + D2H inside the timed region), headline
     # policy; the torch tensors own the page-locked memory the numpy views point at
     pinned = [torch.empty(A.shape, dtype=torch.float64, pin_memory=True) for A in mats for _ in (0, 1)]
@@ -695,6 +727,7 @@ def main():
             if "ns" in results else None},
         "mixed_within_2x_fixed_error": within2x,
         "policies": results,
+        "concurrent_streams": conc,
         "roofline": roofline,
         "gpu_launches": int(gpu_launches),
         "e2e": {"value": e2e_value, "unit": "evals/s",
