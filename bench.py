@@ -264,14 +264,17 @@ def run_config(args, which=None, steps=None, warmup=None, emit=True):
         prof = {c: mpps.profile_read(c) for c in classes}
         mpps.profile_enable(False)
         mpps.profile_reset()
-        dom = max(classes, key=lambda c: prof[c][1])
+        products = (mpps.PROF_GEMM_F64, mpps.PROF_GEMM_F64E, mpps.PROF_GEMM_TC)
+        dom = max(products, key=lambda c: prof[c][1])   # the dominant product class
         launches, ms, work = prof[dom]
         ach = work / (ms / 1e3) / 1e12 if ms > 0 and work > 0 else None
         peak, src = (peak_fp64_tflops() if dom == mpps.PROF_GEMM_F64 else peak_bf16_tflops(step_ms))
+        # per-class event time per step (the classes overlap when launches run on several
+        # streams, so the sum may exceed the step)
         return {"bound": "tensor", "kernel": cname[dom], "achieved": ach, "peak": peak,
                 "unit": "TFLOP/s", "frac": (ach / peak) if ach else None, "peak_source": src,
-                "share_of_step": ms / passes / step_ms if step_ms > 0 else None,
-                "launches_per_step": launches // passes}
+                "launches_per_step": launches // passes,
+                "class_ms_per_step": {cname[c]: prof[c][1] / passes for c in classes}}
 
     def timed(step, steps, warmup):
         for _ in range(warmup):
