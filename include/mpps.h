@@ -309,15 +309,30 @@ mpps_status ps_eval_adjoint_f32(const double* coeffs, int m, const float* A, con
  * (the bound of the [13/13] approximant's backward error by the working precision),
  * X = 2^-sigma A, V = sum_k c_{2k} X^{2k} and W = sum_k c_{2k+1} X^{2k} (degree-6 polynomials
  * in X^2, each by the PS evaluation of ps_eval under `policy`), U = X W, p = V + U,
- * q = p(-X) = V - U, R = q^-1 p by an LU factorisation with partial pivoting (cuSOLVER,
- * loaded at the first call; MPPS_ENOTSUP if it cannot be), then sigma squarings.  The
- * products X^2, X W and the squarings run in the working precision of `policy`
- * (f64_slices: FP64 pipe or emulated).
+ * q = p(-X) = V - U, R = q^-1 p by lu_solve (below), then sigma squarings.  The
+ * products X^2, X W, those of the solve and the squarings run in the working precision of
+ * `policy` (f64_slices: FP64 pipe or emulated).
  *   A, out : batch x n x n (host or device); out may not alias A.
- * Synchronises `stream`.
+ * Synchronises `stream`.  MPPS_ECHECK when q(X) has a zero pivot (not for the exact q on
+ * the scaled argument, whose zeros lie outside |x| <= theta_13).
  */
 mpps_status expm_pade13(const double* A, int n, int batch, const mpps_policy* policy, double* out,
                         void* stream);
+
+/*
+ * R = Q^-1 P for each of `batch` systems: the q(X)^-1 p(X) solve of the Pade approximant
+ * (Section 4.1), by LU factorisation with partial pivoting (row interchanges chosen by the
+ * first largest magnitude in the pivot column), blocked in 64 x 64 tiles: every panel is
+ * factored on the FP64 pipe by one thread-block cluster, every block update and the block
+ * forward and back substitutions run as tile products in the working precision of
+ * `policy` (f64_slices = 0: FP64 pipe; k > 0: emulated FP64 with k slices; the other policy
+ * fields are not used), the diagonal blocks through their inverses.
+ *   Q, P, R : batch x n x n row-major (host or device); R may alias P or Q.
+ * Synchronises `stream`.  MPPS_ECHECK when a pivot is exactly zero (Q singular in the
+ * arithmetic of the factorisation); R then holds non-finite values.
+ */
+mpps_status lu_solve(const double* Q, const double* P, int n, int batch, const mpps_policy* policy,
+                     double* R, void* stream);
 
 /*
  * Gradient of f(A) = <G, r(A)> for the scaling-and-squaring approximant of exp,

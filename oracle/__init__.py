@@ -20,6 +20,8 @@ Contents
   ``fix_params`` branch of Algorithm 3.1 / Algorithm 4.1, with the format ladder of
   Section 4.1.1 generalised to the GPU formats.
 * ``cost_ratio``: eq. (3.8).
+* ``lu_solve``: R = Q^-1 P by Gaussian elimination with partial pivoting (the q^-1 p solve of
+  the Pade approximant, Section 4.1), unblocked, in plain double.
 """
 from __future__ import annotations
 
@@ -280,6 +282,46 @@ def sigma_for(A) -> int:
         return 0
     m, e = math.frexp(nrm)          # nrm = m * 2^e, 0.5 <= m < 1
     return e - 1 if m == 0.5 else e
+
+
+# ---------------------------------------------------------------------------------
+# the linear solve of the Pade approximant (Section 4.1: r = q^-1 p)
+# ---------------------------------------------------------------------------------
+def lu_solve(Q, P):
+    """R = Q^-1 P by Gaussian elimination with partial pivoting, unblocked, in plain double.
+
+    Column j: the pivot is the first row i >= j of largest |Q_ij|; rows j and i are
+    interchanged (in Q and in the right-hand sides), the multipliers l_ij = Q_ij / Q_jj of
+    the rows below are stored in place and those rows lose l_ij times row j.  Then forward
+    substitution with the unit lower triangle and back substitution with the upper one.
+    Returns (R, piv, info): piv[j] = the row interchanged with row j, info = 0 or the first
+    1-based column with a zero pivot (elimination skips that column, as the usual LAPACK
+    convention does, and R is then not a solution)."""
+    A = np.array(Q, dtype=np.float64, copy=True)
+    B = np.array(P, dtype=np.float64, copy=True)
+    n = A.shape[0]
+    piv = np.zeros(n, dtype=np.int64)
+    info = 0
+    for j in range(n):
+        col = np.abs(A[j:, j])
+        i = j + int(np.argmax(col))          # argmax returns the first maximum
+        piv[j] = i
+        if not (A[i, j] != 0.0):
+            if info == 0:
+                info = j + 1
+            continue
+        if i != j:
+            A[[j, i], :] = A[[i, j], :]
+            B[[j, i], :] = B[[i, j], :]
+        A[j + 1:, j] /= A[j, j]
+        A[j + 1:, j + 1:] -= np.outer(A[j + 1:, j], A[j, j + 1:])
+    Y = B
+    for j in range(n):                        # L Y = B (unit diagonal)
+        Y[j + 1:, :] -= np.outer(A[j + 1:, j], Y[j, :])
+    for j in range(n - 1, -1, -1):            # U R = Y
+        Y[j, :] /= A[j, j]
+        Y[:j, :] -= np.outer(A[:j, j], Y[j, :])
+    return Y, piv, info
 
 
 # ---------------------------------------------------------------------------------

@@ -90,7 +90,7 @@ EXPORTS = ("mpps_policy_default", "mpps_plan", "ps_eval", "expm_taylor_ss", "ps_
            "expm_taylor_ss_adjoint", "mpps_choose_s", "mpps_autotune_enable",
            "mpps_autotune_clear", "mpps_autotune_entries", "expm_pade13", "mpps_plan_adjoint",
            "ps_eval_tape_bytes", "ps_eval_forward_tape", "ps_eval_adjoint_tape",
-           "ps_eval_adjoint_f32", "ps_eval_grouped")
+           "ps_eval_adjoint_f32", "ps_eval_grouped", "lu_solve")
 STORAGE_F64, STORAGE_F32 = 0, 1
 PROF_GEMM_F64, PROF_GEMM_TC, PROF_ELEMENTWISE, PROF_GEMM_F64E, PROF_SLICE = 0, 1, 2, 3, 4
 
@@ -131,6 +131,8 @@ def lib():
         L.mpps_choose_s.restype = ctypes.c_int
         L.expm_pade13.argtypes = [vp, ip, ip, ctypes.POINTER(_Policy), vp, vp]
         L.expm_pade13.restype = ctypes.c_int
+        L.lu_solve.argtypes = [vp, vp, ip, ip, ctypes.POINTER(_Policy), vp, vp]
+        L.lu_solve.restype = ctypes.c_int
         L.mpps_autotune_enable.argtypes = [ctypes.c_int]
         L.mpps_autotune_enable.restype = None
         L.mpps_autotune_clear.argtypes = []
@@ -540,6 +542,26 @@ def expm_pade(A, policy: Policy | None = None, out=None, stream=None):
     pol = (policy or Policy())._c()
     _check(lib().expm_pade13(ctypes.c_void_p(ptr), n, batch, ctypes.byref(pol),
                              ctypes.c_void_p(optr), _stream_for(kind, stream)))
+    return out
+
+
+def lu_solve(Q, P, policy: Policy | None = None, out=None, stream=None):
+    """R = Q^-1 P per matrix by LU with partial pivoting (the q^-1 p solve of the Pade
+    approximant): panels on the FP64 pipe, block updates and substitutions as tile products
+    in the policy's working precision (f64_slices)."""
+    qptr, batch, n, kind, keep = _prep(Q, "Q")
+    pptr, pb, pn, pkind, pkeep = _prep(P, "P")   # pkeep: P's (possibly converted) array
+    if (pb, pn) != (batch, n) or pkind != kind:
+        raise ValueError("P must have the shape and placement of Q")
+    if out is None:
+        out = _empty_like(Q, keep)
+    optr, ob, on, _, _ = _prep(out, "out")
+    if (ob, on) != (batch, n):
+        raise ValueError("out has the wrong shape")
+    pol = (policy or Policy())._c()
+    _check(lib().lu_solve(ctypes.c_void_p(qptr), ctypes.c_void_p(pptr), n, batch,
+                          ctypes.byref(pol), ctypes.c_void_p(optr), _stream_for(kind, stream)))
+    del pkeep
     return out
 
 

@@ -8,8 +8,6 @@
 #include <stdio.h>
 #include <string.h>
 
-#include <cusolverDn.h>
-#include <dlfcn.h>
 
 #include <algorithm>
 #include <initializer_list>
@@ -2495,67 +2493,6 @@ mpps_status expm_taylor_ss_adjoint(const double* A, const double* G, int n, int 
 
 }  // extern "C"
 
-// ---- LU solve for the Pade approximant: cuSOLVER, loaded at first use -----------------
-namespace {
-struct Solver {
-    bool tried = false;
-    void* so = nullptr;
-    cusolverStatus_t (*create)(cusolverDnHandle_t*) = nullptr;
-    cusolverStatus_t (*set_stream)(cusolverDnHandle_t, cudaStream_t) = nullptr;
-    cusolverStatus_t (*getrf_ws)(cusolverDnHandle_t, int, int, double*, int, int*) = nullptr;
-    cusolverStatus_t (*getrf)(cusolverDnHandle_t, int, int, double*, int, double*, int*, int*) = nullptr;
-    cusolverStatus_t (*getrs)(cusolverDnHandle_t, cublasOperation_t, int, int, const double*, int,
-                              const int*, double*, int, int*) = nullptr;
-    cusolverDnHandle_t handle[64] = {};
-};
-std::mutex g_solvermu;
-std::mutex g_solvecall;   // one handle per device: its stream is set for each call's solves
-Solver g_solver;
-
-// The solver library is opened only by the Pade entry point, so that the rest of the
-// library does not depend on it.
-mpps_status solver_get(cudaStream_t st, Solver** out, cusolverDnHandle_t* h) {
-    std::lock_guard<std::mutex> lk(g_solvermu);
-    Solver& S = g_solver;
-    if (!S.tried) {
-        S.tried = true;
-        const char* names[] = {"libcusolver.so.12", "libcusolver.so.11", "libcusolver.so",
-                               "/usr/local/cuda/lib64/libcusolver.so.12"};
-        for (const char* nm : names)
-            if ((S.so = dlopen(nm, RTLD_NOW | RTLD_LOCAL))) break;
-        if (S.so) {
-            S.create = (decltype(S.create))dlsym(S.so, "cusolverDnCreate");
-            S.set_stream = (decltype(S.set_stream))dlsym(S.so, "cusolverDnSetStream");
-            S.getrf_ws = (decltype(S.getrf_ws))dlsym(S.so, "cusolverDnDgetrf_bufferSize");
-            S.getrf = (decltype(S.getrf))dlsym(S.so, "cusolverDnDgetrf");
-            S.getrs = (decltype(S.getrs))dlsym(S.so, "cusolverDnDgetrs");
-        }
-    }
-    if (!S.create || !S.set_stream || !S.getrf_ws || !S.getrf || !S.getrs) {
-        set_error("expm_pade13: the LU solver (libcusolver) could not be loaded");
-        return MPPS_ENOTSUP;
-    }
-    int dev = 0;
-    MPPS_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) {
-        set_error("device index %d out of range", dev);
-        return MPPS_ENOTSUP;
-    }
-    if (!S.handle[dev] && S.create(&S.handle[dev]) != CUSOLVER_STATUS_SUCCESS) {
-        S.handle[dev] = nullptr;
-        set_error("cusolverDnCreate failed");
-        return MPPS_ECUDA;
-    }
-    if (S.set_stream(S.handle[dev], st) != CUSOLVER_STATUS_SUCCESS) {
-        set_error("cusolverDnSetStream failed");
-        return MPPS_ECUDA;
-    }
-    *out = &S;
-    *h = S.handle[dev];
-    return MPPS_OK;
-}
-}  // namespace
-
 extern "C" {
 
 mpps_status expm_pade13(const double* A, int n, int batch, const mpps_policy* policy, double* out,
@@ -2581,9 +2518,6 @@ mpps_status expm_pade13(const double* A, int n, int batch, const mpps_policy* po
     Staged a;
     if ((rc = stage_in(A, elems, st, a))) return rc;
     const bool o_dev = is_device_ptr(out);
-    Solver* S = nullptr;
-    cusolverDnHandle_t sh = nullptr;
-    if ((rc = solver_get(st, &S, &sh))) return rc;
 
     // [13/13] Pade coefficients c_j = (26-j)! 13! / (26! j! (13-j)!), by the ratio
     // c_{j+1} / c_j = (13 - j) / ((26 - j)(j + 1)); even and odd parts as polynomials in X^2
@@ -2603,13 +2537,13 @@ mpps_status expm_pade13(const double* A, int n, int batch, const mpps_policy* po
 
     // ---- sigma = max(0, ceil(log2(||A||_1 / theta_13))), theta_13 = 5.371920351148152
     Arena L;
-    double *X, *X2, *V, *W, *U, *P, *Q, *Rb1, *partial, *anorm, *work = nullptr, *dOut = out;
-    int *d_sigma, *d_lists, *ipiv, *info;
+    double *X, *X2, *V, *W, *U, *P, *Q, *Rb1, *partial, *anorm, *dOut = out;
+    int *d_sigma, *d_lists, *info;
     __nv_bfloat16 *slA = nullptr, *slB = nullptr;
     int *eA = nullptr, *eB = nullptr;
     unsigned long long* cmx = nullptr;
     char* split = nullptr;
-    int lwork = 0;
+    void* luws = nullptr;
     auto lay = [&](Arena& z) {
         X = z.take<double>(elems);
         X2 = z.take<double>(elems);
@@ -2623,8 +2557,8 @@ mpps_status expm_pade13(const double* A, int n, int batch, const mpps_policy* po
         anorm = z.take<double>(batch);
         d_sigma = z.take<int>(batch);
         d_lists = z.take<int>((size_t)batch * 64);
-        ipiv = z.take<int>((size_t)n);
-        info = z.take<int>((size_t)2 * batch);   // getrf and getrs info per matrix
+        info = z.take<int>((size_t)batch);   // first zero pivot of the LU, per matrix
+        luws = z.take<char>(lu_workspace_bytes(n, K));
         if (!o_dev) dOut = z.take<double>(elems);
         if (K > 0) {
             slA = z.take<__nv_bfloat16>(f64e_plane_elems(n, batch, K));
@@ -2641,13 +2575,6 @@ mpps_status expm_pade13(const double* A, int n, int batch, const mpps_policy* po
     L.base = (char*)ws.p;
     L.off = 0;
     lay(L);
-    if (S->getrf_ws(sh, n, n, Q, n, &lwork) != CUSOLVER_STATUS_SUCCESS) {
-        set_error("cusolverDnDgetrf_bufferSize failed");
-        return MPPS_ECUDA;
-    }
-    DevBuf wbuf;
-    if ((rc = wbuf.alloc(sizeof(double) * (size_t)std::max(lwork, 1), st))) return rc;
-    work = (double*)wbuf.p;
     if (split) MPPS_CUDA_TRY(cudaMemsetAsync(split, 0, f64e_split_flag_bytes(), st));
     DevErr* derr = nullptr;
     if (K > 0) {
@@ -2712,29 +2639,11 @@ mpps_status expm_pade13(const double* A, int n, int batch, const mpps_policy* po
         ep.add_coef = 1.0;
         if ((rc = launch_combine(n, batch, U, nn, ep, st))) return rc;
     }
-    // ---- R = q^-1 p.  p and q commute (both polynomials in X), so R^T = (Q^T)^-1 P^T: the
-    // row-major Q and P, read column-major, are Q^T and P^T, and the column-major solution
-    // written over P is R in row-major order
+    // ---- R = q^-1 p by LU with partial pivoting, in the products of the working precision
     // (q_13 has no zeros in the disc |x| <= theta_13, so the exact q(X) is nonsingular there;
-    // the info words are still read back at the end: q assembled under a mixed policy is not
-    // the exact one)
-    {
-        std::lock_guard<std::mutex> lk(g_solvecall);
-        if (S->set_stream(sh, st) != CUSOLVER_STATUS_SUCCESS) {
-            set_error("cusolverDnSetStream failed");
-            return MPPS_ECUDA;
-        }
-        for (int b = 0; b < batch; ++b) {
-            double* Qb = Q + (size_t)b * nn;
-            double* Pb = P + (size_t)b * nn;
-            if (S->getrf(sh, n, n, Qb, n, work, ipiv, info + 2 * b) != CUSOLVER_STATUS_SUCCESS ||
-                S->getrs(sh, CUBLAS_OP_N, n, n, Qb, n, ipiv, Pb, n, info + 2 * b + 1) !=
-                    CUSOLVER_STATUS_SUCCESS) {
-                set_error("expm_pade13: LU solve failed for matrix %d", b);
-                return MPPS_ECUDA;
-            }
-        }
-    }
+    // the first zero pivot is still read back at the end: q assembled under a mixed policy is
+    // not the exact one)
+    if ((rc = lu_solve_dev(Q, P, P, n, batch, K, luws, info, K > 0 ? derr->d : nullptr, st))) return rc;
     // ---- sigma squarings per matrix (index lists), then each result from its buffer
     std::vector<int> lists((size_t)std::max(sig_max, 1) * batch);
     std::vector<int> counts(std::max(sig_max, 1), 0);
@@ -2756,20 +2665,79 @@ mpps_status expm_pade13(const double* A, int n, int batch, const mpps_policy* po
     }
     if ((rc = launch_select_copy(buf[0], buf[1], d_sigma, dOut, n, batch, 0.0, st))) return rc;
     if (K > 0 && (rc = dev_err_enqueue(derr, st))) return rc;
-    std::vector<int> hinfo((size_t)2 * batch);
+    std::vector<int> hinfo((size_t)batch);
     MPPS_CUDA_TRY(cudaMemcpyAsync(hinfo.data(), info, sizeof(int) * hinfo.size(), cudaMemcpyDeviceToHost, st));
     if (!o_dev) {
         MPPS_CUDA_TRY(cudaMemcpyAsync(out, dOut, elems * sizeof(double), cudaMemcpyDeviceToHost, st));
         MPPS_CUDA_TRY(cudaStreamSynchronize(st));
         if (K > 0 && (rc = dev_err_check(derr, true))) return rc;
     } else {
-        MPPS_CUDA_TRY(cudaStreamSynchronize(st));   // the LU pivots and info live in this call's workspace
+        MPPS_CUDA_TRY(cudaStreamSynchronize(st));   // the LU info lives in this call's workspace
         if (K > 0 && (rc = dev_err_check(derr, true))) return rc;
     }
     for (int b = 0; b < batch; ++b)
-        if (hinfo[2 * b] != 0 || hinfo[2 * b + 1] != 0) {
-            set_error("expm_pade13: the LU factorisation of q(X) of matrix %d failed (info %d, %d)",
-                      b, hinfo[2 * b], hinfo[2 * b + 1]);
+        if (hinfo[b] != 0) {
+            set_error("expm_pade13: q(X) of matrix %d is singular (zero pivot in column %d)", b,
+                      hinfo[b] - 1);
+            return MPPS_ECHECK;
+        }
+    return MPPS_OK;
+}
+
+mpps_status lu_solve(const double* Q, const double* P, int n, int batch, const mpps_policy* policy,
+                     double* R, void* stream) {
+    clear_error();
+    mpps_status rc = check_sizes(n, batch);
+    if (rc) return rc;
+    if (batch == 0) return MPPS_OK;
+    if (!Q || !P || !R) {
+        set_error("lu_solve: null matrix pointer");
+        return MPPS_EINVAL;
+    }
+    if ((rc = check_same_device("lu_solve", {Q, P, R}))) return rc;
+    const Pol pol = resolve(policy);
+    if (pol.f64k < 0 || pol.f64k > MPPS_F64E_MAX_SLICES) {
+        set_error("f64_slices=%d outside 0..%d", pol.f64k, MPPS_F64E_MAX_SLICES);
+        return MPPS_EINVAL;
+    }
+    const int K = pol.f64k;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t elems = (size_t)batch * n * n;
+    Staged q, p;
+    if ((rc = stage_in(Q, elems, st, q)) || (rc = stage_in(P, elems, st, p))) return rc;
+    const bool o_dev = is_device_ptr(R);
+    Arena L;
+    int* info = nullptr;
+    void* luws = nullptr;
+    double* dR = R;
+    auto lay = [&](Arena& z) {
+        info = z.take<int>((size_t)batch);
+        luws = z.take<char>(lu_workspace_bytes(n, K));
+        if (!o_dev) dR = z.take<double>(elems);
+    };
+    lay(L);
+    DevBuf ws;
+    if ((rc = ws.alloc(L.off, st))) return rc;
+    L.base = (char*)ws.p;
+    L.off = 0;
+    lay(L);
+    DevErr* derr = nullptr;
+    if (K > 0) {
+        if ((rc = dev_err_get(&derr))) return rc;
+        if ((rc = dev_err_check(derr, false))) return rc;
+    }
+    if ((rc = lu_solve_dev(q.dev, p.dev, dR, n, batch, K, luws, info, K > 0 ? derr->d : nullptr, st)))
+        return rc;
+    if (K > 0 && (rc = dev_err_enqueue(derr, st))) return rc;
+    std::vector<int> hinfo((size_t)batch);
+    MPPS_CUDA_TRY(cudaMemcpyAsync(hinfo.data(), info, sizeof(int) * hinfo.size(), cudaMemcpyDeviceToHost, st));
+    if (!o_dev)
+        MPPS_CUDA_TRY(cudaMemcpyAsync(R, dR, elems * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MPPS_CUDA_TRY(cudaStreamSynchronize(st));
+    if (K > 0 && (rc = dev_err_check(derr, true))) return rc;
+    for (int b = 0; b < batch; ++b)
+        if (hinfo[b] != 0) {
+            set_error("lu_solve: Q of system %d is singular (zero pivot in column %d)", b, hinfo[b] - 1);
             return MPPS_ECHECK;
         }
     return MPPS_OK;

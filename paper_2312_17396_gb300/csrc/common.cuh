@@ -123,7 +123,26 @@ struct Epilogue {
     // here; a copy is written only for BF16, TF32 and BF16X3 (FP8 copies are row-scaled by
     // their own pass)
     const int* low_fmt_dev;
+    // grid mode (gnj > 0): product z multiplies matrix z / gnj of the A operand with matrix
+    // z % gnj of the B operand and writes (and reads its addend at) matrix
+    // (z / gnj) gci + (z % gnj) gcj of the output; the products of a blocked factorisation
+    // or triangular solve, whose tiles are the matrices (gnj = 0: A, B and the output all
+    // take matrix z, or bidx[z])
+    int gnj;
+    int gci, gcj;
 };
+
+// The operand and output matrices of product z (see Epilogue::gnj).
+__host__ __device__ __forceinline__ void grid_index(const Epilogue& ep, int z, int b, int& ba,
+                                                    int& bb, int& bo) {
+    if (ep.gnj > 0) {
+        ba = z / ep.gnj;
+        bb = z - ba * ep.gnj;
+        bo = ba * ep.gci + bb * ep.gcj;
+    } else {
+        ba = bb = bo = b;
+    }
+}
 
 // low_fmt value meaning "read the format from Epilogue::low_fmt_dev".
 constexpr int MPPS_FMT_DEVICE = 100;
@@ -141,6 +160,7 @@ inline Epilogue epilogue_plain(double* out, long long out_bstride) {
     e.rmax = nullptr; e.cmax = nullptr;
     e.dcount = nullptr;
     e.low_fmt_dev = nullptr;
+    e.gnj = 0; e.gci = 0; e.gcj = 0;
     return e;
 }
 
@@ -355,6 +375,21 @@ mpps_status launch_gemm_f64e(int k, const void* slicesA, int ksA, const int* eA,
                              const void* slicesBt, int ksB, const int* eB, int n, int batch,
                              int nmat, const Epilogue& ep, int* d_err, cudaStream_t st,
                              const int* bidx = nullptr, void* split = nullptr);
+// Grid mode (Epilogue::gnj = nmatB): the nmatA x nmatB products of every stored A matrix
+// with every stored B matrix (k slices stored per matrix), whole tiles, no split.
+mpps_status launch_gemm_f64e_grid(int k, const void* slicesA, const int* eA, int nmatA,
+                                  const void* slicesBt, const int* eB, int nmatB, int n,
+                                  const Epilogue& ep, int* d_err, cudaStream_t st);
+
+// ---- LU factorisation with partial pivoting and the solve Q R = P (lu.cu) -----------
+// Device workspace bytes of lu_solve_dev for one n x n system with k-slice products (k = 0:
+// FP64 pipe).
+size_t lu_workspace_bytes(int n, int k);
+// R_b = Q_b^-1 P_b for b < batch (row-major, batch stride n^2, device pointers; R may be
+// P).  info[b] (device) gets 0, or j + 1 for the first column j whose pivot is zero.
+// d_err: the emulated products' error word (k > 0).
+mpps_status lu_solve_dev(const double* Q, const double* P, double* R, int n, int batch, int k,
+                         void* ws, int* info, int* d_err, cudaStream_t st);
 
 // ---- measured choice of product schedules (autotune.cu) ---------------------------
 constexpr int kTuneMaxCandidates = 4;

@@ -49,10 +49,11 @@ __global__ void __launch_bounds__(32 * WM * WN)
     __shared__ __align__(16) double As[2][BM][BK + APAD];
     __shared__ __align__(16) double Bs[2][BK][BN + BPAD];
 
-    const int b = bidx ? bidx[blockIdx.z] : blockIdx.z;
+    int ba, bb, b;   // A and B operand matrices, output matrix (grid mode: Epilogue::gnj)
+    grid_index(ep, (int)blockIdx.z, bidx ? bidx[blockIdx.z] : (int)blockIdx.z, ba, bb, b);
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    const double* Ab = A + (long long)b * a_bs;
-    const double* Bb = B + (long long)b * b_bs;
+    const double* Ab = A + (long long)ba * a_bs;
+    const double* Bb = B + (long long)bb * b_bs;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int g = lane >> 2, t = lane & 3;
     const int wm = warp / WN, wn = warp % WN;

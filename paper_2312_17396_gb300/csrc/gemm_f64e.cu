@@ -849,15 +849,17 @@ __global__ void __launch_bounds__(THREADS, 1)
             while (ok && sg.next(id, kb0, kb1)) {
                 int z, m0, n0;
                 tm.decode(id, z, m0, n0);
-                const int b = bidx ? bidx[z] : z;
+                int ba, bb, bo;
+                grid_index(ep, z, bidx ? bidx[z] : z, ba, bb, bo);
+                (void)bo;
                 for (int kb = kb0; kb < kb1; ++kb, ++g) {
                     if (g >= (uint32_t)S && !(ok = mbar_wait(&empty[s], ph ^ 1, err))) break;
                     uint8_t* st = smem + s * SB;
                     mbar_expect_tx(&full[s], (uint32_t)SB);
-                    tma_load_3d(st + NPA * A_PAIR, &tmB, kb * KB, n0, b * ksB, &full[s]);
+                    tma_load_3d(st + NPA * A_PAIR, &tmB, kb * KB, n0, bb * ksB, &full[s]);
 #pragma unroll
                     for (int p = 0; p < NPA; ++p)   // pair rows hold 2 KB elements per K block
-                        tma_load_3d(st + p * A_PAIR, &tmA, kb * 2 * KB, m0, b * kpA + p, &full[s]);
+                        tma_load_3d(st + p * A_PAIR, &tmA, kb * 2 * KB, m0, ba * kpA + p, &full[s]);
                     if (++s == S) { s = 0; ph ^= 1; }
                 }
             }
@@ -933,7 +935,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         while (sg.next(id, kb0, kb1)) {
             int z, m0, n0;
             tm.decode(id, z, m0, n0);
-            const int b = bidx ? bidx[z] : z;
+            int ba, bb, b;   // A and B operand matrices, output matrix
+            grid_index(ep, z, bidx ? bidx[z] : z, ba, bb, b);
             long long W[EPI_COLS];
             float T[EPI_COLS];
 #pragma unroll
@@ -1017,7 +1020,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             // ep.rmax / ep.cmax the maxima of the stored values are recorded as well (every
             // lane runs the group loop: the column maxima reduce across the warp's rows)
             const bool inside = row < n;
-            const int er = inside ? eA[(long long)b * n + row] : 0;
+            const int er = inside ? eA[(long long)ba * n + row] : 0;
             const bool plain = ep_plain && cb + EPI_COLS <= n && nchunks <= FLUSH;
             int mrow = 0;
 #pragma unroll
@@ -1028,7 +1031,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         const int j = g + u;
-                        const int e = er + __ldg(eB + (long long)b * n + min(cb + j, n - 1));
+                        const int e = er + __ldg(eB + (long long)bb * n + min(cb + j, n - 1));
                         double wd = 0.0, td = 0.0;
                         // 2^(e-49) W and 2^(e-14) T formed on the integer pipe, one FP64 add
                         fast = fast && e < kExpLimit && i64_to_f64_scaled(W[j], e - 49, &wd) &&
@@ -1052,7 +1055,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                             const int col = cb + g + u;
                             val[u] = col < n ? f64e_store(ep, b, row, col, n, fast ? val[u] : f64e_slow_value(
                                                    nchunks > FLUSH, orow[g + u], W[g + u], T[g + u],
-                                                   er + __ldg(eB + (long long)b * n + col)))
+                                                   er + __ldg(eB + (long long)bb * n + col)))
                                              : 0.0;
                         }
                     }
@@ -1430,6 +1433,52 @@ mpps_status launch_gemm_f64e(int k, const void* slicesA, int ksA, const int* eA,
         return tune_run(TUNE_F64E_SPLIT, n, batch, k, 2, st,
                         [&](int c) { return run(c == 1); });
     return run(tuned >= 0 ? tuned == 1 : rule);
+}
+
+mpps_status launch_gemm_f64e_grid(int k, const void* slicesA, const int* eA, int nmatA,
+                                  const void* slicesBt, const int* eB, int nmatB, int n,
+                                  const Epilogue& ep, int* d_err, cudaStream_t st) {
+    if (nmatA <= 0 || nmatB <= 0) return MPPS_OK;
+    if (k < 1 || k > MPPS_F64E_MAX_SLICES || ep.gnj != nmatB) {
+        set_error("emulated FP64 grid product: slice count %d or grid width %d (need %d)", k,
+                  ep.gnj, nmatB);
+        return MPPS_EINVAL;
+    }
+    const int kp = f64e_planes(k);
+    const int lld = low_ld(n);
+    const int kpA = num_pairs(kp);
+    CUtensorMap ta, tb;
+    if (!make_pair_map(&ta, slicesA, n, nmatA * kpA, lld) ||
+        !make_plane_map(&tb, slicesBt, n, nmatB * kp, lld, kp)) {
+        set_error("cuTensorMapEncodeTiled failed for slice planes (n=%d)", n);
+        return MPPS_ECUDA;
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    const long long batch = (long long)nmatA * nmatB;
+    const long long tiles = (long long)((n + ON - 1) / ON) * ((n + OM - 1) / OM) * batch;
+    if (tiles > 0x7fffffffLL) {
+        set_error("emulated FP64 grid product: %lld tiles exceed the index range", tiles);
+        return MPPS_EINVAL;
+    }
+    const int G = sm_count(dev);
+    const int grid = (int)(tiles < G ? tiles : G);
+    const int pairs = k <= 8 ? k * (k + 1) / 2 : 43;
+    ProfScope prof(MPPS_PROF_GEMM_F64E, st, 2.0 * n * (double)n * n * (double)batch * pairs);
+    const Split sp{0, nullptr, nullptr, nullptr, 0u};
+    const int nb = (int)batch;
+    switch (k) {
+        case 1: return launch_k<1>(dev, grid, ta, tb, n, kpA, kp, nb, eA, eB, ep, d_err, st, nullptr, sp);
+        case 2: return launch_k<2>(dev, grid, ta, tb, n, kpA, kp, nb, eA, eB, ep, d_err, st, nullptr, sp);
+        case 3: return launch_k<3>(dev, grid, ta, tb, n, kpA, kp, nb, eA, eB, ep, d_err, st, nullptr, sp);
+        case 4: return launch_k<4>(dev, grid, ta, tb, n, kpA, kp, nb, eA, eB, ep, d_err, st, nullptr, sp);
+        case 5: return launch_k<5>(dev, grid, ta, tb, n, kpA, kp, nb, eA, eB, ep, d_err, st, nullptr, sp);
+        case 6: return launch_k<6>(dev, grid, ta, tb, n, kpA, kp, nb, eA, eB, ep, d_err, st, nullptr, sp);
+        case 7: return launch_k<7>(dev, grid, ta, tb, n, kpA, kp, nb, eA, eB, ep, d_err, st, nullptr, sp);
+        case 8: return launch_k<8>(dev, grid, ta, tb, n, kpA, kp, nb, eA, eB, ep, d_err, st, nullptr, sp);
+        default: return launch_k<9>(dev, grid, ta, tb, n, kpA, kp, nb, eA, eB, ep, d_err, st, nullptr, sp);
+    }
 }
 
 }  // namespace mpps

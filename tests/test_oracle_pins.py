@@ -691,3 +691,75 @@ def test_norm1_hand_worked_3x4():
     assert oracle.norm1(np.array([[-3.0], [2.0], [1.0]])) == 6.0  # one column: its sum
     R = RNG.standard_normal((7, 5))
     assert oracle.norm1(R) == np.abs(R).sum(axis=0).max()
+
+
+# --------------------------------------------------------------------------------
+# 15. the linear solve of the Pade approximant (Section 4.1: r = q^-1 p)
+# --------------------------------------------------------------------------------
+def _fr_inverse(A):
+    """Gauss-Jordan in exact rationals (no pivoting choice matters for exactness)."""
+    n = len(A)
+    M = [[Fraction(v) for v in row] + [Fraction(int(i == j)) for j in range(n)]
+         for i, row in enumerate(A)]
+    for j in range(n):
+        p = next(i for i in range(j, n) if M[i][j] != 0)
+        M[j], M[p] = M[p], M[j]
+        pv = M[j][j]
+        M[j] = [v / pv for v in M[j]]
+        for i in range(n):
+            if i != j and M[i][j] != 0:
+                f = M[i][j]
+                M[i] = [a - f * b for a, b in zip(M[i], M[j])]
+    return [row[n:] for row in M]
+
+
+def test_lu_solve_hand_worked_3x3():
+    # column 0: |4| at row 2 is the largest -> rows 0, 2 swap; the remaining rows read
+    # [0, .5, .5] and [0, 1, 2]: column 1's pivot 1 is again in row 2 -> rows 1, 2 swap;
+    # U = [[4, 7, 9], [0, 1, 2], [0, 0, -1/2]], det = -2: every step and the inverse are dyadic,
+    # so the plain-double result is exact
+    Q = [[0.0, 1.0, 2.0], [2.0, 4.0, 5.0], [4.0, 7.0, 9.0]]
+    R, piv, info = oracle.lu_solve(np.array(Q), np.eye(3))
+    assert info == 0 and list(piv) == [2, 2, 2]
+    exact = _fr_inverse(Q)
+    assert all(R[i, j] == float(exact[i][j]) for i in range(3) for j in range(3))
+
+
+def test_lu_solve_exact_on_dyadic_factors():
+    # Q = L0 U0 with |l_ij| <= 1/2 (so partial pivoting keeps the diagonal) and small dyadic
+    # entries: elimination recovers the factors exactly and R = X0 for P = Q X0
+    n = 6
+    rng = np.random.default_rng(7)
+    L0 = np.tril(rng.integers(-2, 3, (n, n)) / 4.0, -1) + np.eye(n)
+    U0 = np.triu(rng.integers(-3, 4, (n, n)).astype(float), 1) + np.diag([2.0, -4, 1, 8, -2, 4])
+    X0 = rng.integers(-5, 6, (n, n)).astype(float)
+    Q, P = L0 @ U0, L0 @ U0 @ X0
+    R, piv, info = oracle.lu_solve(Q, P)
+    assert info == 0 and list(piv) == list(range(n))
+    assert np.array_equal(R, X0)
+
+
+def test_lu_solve_pivots_and_solution_match_lapack():
+    # the pivot sequence is the one of LAPACK's getrf (first largest magnitude), the
+    # solution agrees with getrs to rounding, and the residual is at rounding level
+    sl = pytest.importorskip("scipy.linalg")
+    rng = np.random.default_rng(11)
+    for n in (1, 2, 5, 33, 80):
+        Q, P = rng.standard_normal((n, n)), rng.standard_normal((n, n))
+        R, piv, info = oracle.lu_solve(Q, P)
+        lu, pv = sl.lu_factor(Q)
+        assert info == 0 and np.array_equal(piv, pv)
+        ref = sl.lu_solve((lu, pv), P)
+        kappa = np.linalg.cond(Q, 1)
+        assert np.abs(R - ref).max() <= 8 * n * kappa * 2.0 ** -53 * np.abs(ref).max()
+        assert np.abs(Q @ R - P).max() <= 8 * n * 2.0 ** -53 * np.abs(Q).sum(1).max() * np.abs(R).max()
+
+
+def test_lu_solve_zero_pivot_info():
+    # rows 0 and 2 equal: column 2 loses its pivot (info = 3); a 0 leading entry is not a
+    # zero pivot (an interchange cures it): the inverse of a swap is the swap
+    Q = np.array([[1.0, 2.0, 3.0], [0.0, 1.0, 4.0], [1.0, 2.0, 3.0]])
+    assert oracle.lu_solve(Q, np.eye(3))[2] == 3
+    Z = np.array([[0.0, 1.0], [1.0, 0.0]])
+    R, piv, info = oracle.lu_solve(Z, np.eye(2))
+    assert info == 0 and list(piv) == [1, 1] and np.array_equal(R, Z)
