@@ -375,6 +375,11 @@ mpps_status launch_gemm_f64e(int k, const void* slicesA, int ksA, const int* eA,
                              const void* slicesBt, int ksB, const int* eB, int n, int batch,
                              int nmat, const Epilogue& ep, int* d_err, cudaStream_t st,
                              const int* bidx = nullptr, void* split = nullptr);
+// Row slices of nI and column slices of nJ small tiles (n <= 64, even) in one launch, for
+// a grid product (the planes and exponents of launch_slice_rows / launch_slice_cols).
+mpps_status launch_slice_tiles(int k, const double* A, long long a_bs, int nI, const double* B,
+                               long long b_bs, int nJ, int n, void* planesA, int* eA,
+                               void* planesB, int* eB, cudaStream_t st);
 // Grid mode (Epilogue::gnj = nmatB): the nmatA x nmatB products of every stored A matrix
 // with every stored B matrix (k slices stored per matrix), whole tiles, no split.
 mpps_status launch_gemm_f64e_grid(int k, const void* slicesA, const int* eA, int nmatA,

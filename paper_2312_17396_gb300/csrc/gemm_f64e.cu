@@ -467,6 +467,69 @@ __global__ void k_colmax(const double* __restrict__ M, long long bs, int n,
     atomicMax(out + (long long)b * n + col, mx);
 }
 
+// Slices of small square tiles (n <= 64, even) for a grid product, in one launch: block
+// b < nI takes the rows of A tile b (A operand, pair layout), block nI + j the columns of B
+// tile j (B^T planes).  The tile is staged in shared memory; a row's (column's) exponent
+// comes from its maximum magnitude, as in the separate slicers, and the digits are the same.
+template <int KS>
+__global__ void __launch_bounds__(256) k_slice_tiles(const double* __restrict__ A, long long a_bs,
+                                                     int nI, const double* __restrict__ B,
+                                                     long long b_bs, int n, long long goff,
+                                                     __nv_bfloat16* __restrict__ plA,
+                                                     __nv_bfloat16* __restrict__ plB, int lld,
+                                                     int* __restrict__ eA, int* __restrict__ eB) {
+    pdl_wait();
+    pdl_trigger();
+    __shared__ double t[64][65];
+    __shared__ unsigned long long part[4][64];
+    const bool rows = (int)blockIdx.x < nI;
+    const int b = rows ? (int)blockIdx.x : (int)blockIdx.x - nI;
+    const double* src = rows ? A + (long long)b * a_bs : B + (long long)b * b_bs;
+    for (int e = threadIdx.x; e < 64 * 64; e += 256) {
+        const int r = e >> 6, c = e & 63;
+        t[r][c] = (r < n && c < n) ? src[(long long)r * n + c] : 0.0;
+    }
+    __syncthreads();
+    const int q = threadIdx.x >> 6, x = threadIdx.x & 63;   // quarter, row (column) index
+    __shared__ int es[64];
+    unsigned long long mx = 0;
+#pragma unroll
+    for (int u = 0; u < 16; ++u)
+        mx = max_bits(mx, abs_bits(rows ? t[x][q * 16 + u] : t[q * 16 + u][x]));
+    part[q][x] = mx;
+    __syncthreads();
+    if (q == 0) {
+        const int e = exp_above(max_bits(max_bits(part[0][x], part[1][x]), max_bits(part[2][x], part[3][x])));
+        es[x] = e;
+        if (x < n) (rows ? eA : eB)[(long long)b * n + x] = e;
+    }
+    __syncthreads();
+    if (rows) {   // a warp writes 32 consecutive K of one row per slice
+        const long long pstride = (long long)n * 2 * lld;
+        __nv_bfloat16* dst = plA + (long long)b * num_pairs(KS) * pstride;
+        const int n32 = (n + KB - 1) / KB * KB;   // the K tail up to n32 is written as zeros
+        for (int idx = threadIdx.x; idx < 64 * 64; idx += 256) {
+            const int r = idx >> 6, j = idx & 63;
+            if (r < n && j < n32)
+                put_digits<KS>(j < n ? t[r][j] : 0.0, es[r], goff, dst + (long long)r * 2 * lld + kpos(j),
+                               pstride);
+        }
+    } else {      // a warp writes 32 consecutive K pairs of one plane row (tile column)
+        const long long pstride = (long long)n * lld;
+        __nv_bfloat16* dst = plB + (long long)b * KS * pstride;
+        for (int idx = threadIdx.x; idx < 64 * 32; idx += 256) {
+            const int xc = idx >> 5, k0 = 2 * (idx & 31);
+            if (xc >= n || k0 >= n) continue;
+            const int e = es[xc];
+            const long long G0 = scaled_int_fp64(t[k0][xc], e) + goff;
+            const long long G1 = scaled_int_fp64(t[k0 + 1][xc], e) + goff;   // 0 past n
+            unsigned* d = reinterpret_cast<unsigned*>(dst + (long long)xc * lld + k0);
+#pragma unroll
+            for (int tt = 0; tt < KS; ++tt) d[(long long)tt * (pstride / 2)] = digit_pair(G0, G1, tt);
+        }
+    }
+}
+
 // Column slices (B operand, written transposed: plane row j = column j of M) through a
 // shared 64-row x 32-column block of M (stored column-major, pitch 65); e_j from the column
 // maxima (or, CODES, from the exponent codes an epilogue recorded).  Each thread turns two
@@ -779,7 +842,7 @@ __device__ __forceinline__ void issue_k16(uint32_t tmem, uint64_t da, uint64_t d
     }
 }
 
-template <int K, bool SPLIT>
+template <int K, bool SPLIT, bool GRID>
 __global__ void __launch_bounds__(THREADS, 1)
     k_gemm_f64e(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 int n, int kpA, int ksB, int batch, const int* __restrict__ eA,
@@ -850,7 +913,11 @@ __global__ void __launch_bounds__(THREADS, 1)
                 int z, m0, n0;
                 tm.decode(id, z, m0, n0);
                 int ba, bb, bo;
-                grid_index(ep, z, bidx ? bidx[z] : z, ba, bb, bo);
+                if constexpr (GRID) {
+                    grid_index(ep, z, z, ba, bb, bo);
+                } else {
+                    ba = bb = bidx ? bidx[z] : z;
+                }
                 (void)bo;
                 for (int kb = kb0; kb < kb1; ++kb, ++g) {
                     if (g >= (uint32_t)S && !(ok = mbar_wait(&empty[s], ph ^ 1, err))) break;
@@ -917,15 +984,21 @@ __global__ void __launch_bounds__(THREADS, 1)
         // (a plain epilogue stores the product alone, four doubles at a time where aligned)
         const bool alpha1 = ep.alpha_b == nullptr &&
                             __double_as_longlong(ep.alpha) == 0x3FF0000000000000LL;
+        // grid products with alpha = -1 (block updates C - A B): the product is negated
+        // exactly and then takes the path of alpha = 1, whose sum has the same roundings
+        const bool alpham1 = GRID && ep.alpha_b == nullptr &&
+                             __double_as_longlong(ep.alpha) == (long long)0xBFF0000000000000ULL;
         const bool ep_plain = ep.nt < 0 && ep.add == nullptr && ep.low_fmt == MPPS_FMT_NONE && alpha1;
-        // fused Horner add and/or addend, alpha = 1, with 16-byte aligned power-table and
+        // fused Horner add and/or addend, alpha = +-1, with 16-byte aligned power-table and
         // addend rows (n a multiple of 4, aligned bases and even batch strides)
-        const bool ep_sum = alpha1 && (ep.nt >= 0 || ep.add != nullptr) && (n & 3) == 0 &&
+        const bool ep_sum = (alpha1 || alpham1) && (ep.nt >= 0 || ep.add != nullptr) &&
+                            (n & 3) == 0 &&
                             ((((uintptr_t)ep.pw | (uintptr_t)ep.add) & 15) == 0) &&
                             ((ep.pw_bstride | ep.add_bstride) & 1) == 0;
         // a Horner block sum without addend, computed ahead into the output entries while the
         // MMAs run (not when the chunks are flushed: the entries then hold the FP64 partials)
-        const bool ep_pre = ep_sum && ep.nt >= 0 && ep.add == nullptr && nchunks <= FLUSH &&
+        const bool ep_pre = ep_sum && alpha1 && ep.nt >= 0 && ep.add == nullptr &&
+                            nchunks <= FLUSH &&
                             ((((uintptr_t)ep.out) & 15) == 0) && (ep.out_bstride & 1) == 0;
         const int q4 = warp & 3, h = warp >> 2;   // lane quarter, column group
         const uint32_t lane_base = (uint32_t)(q4 * 32) << 16;
@@ -936,7 +1009,12 @@ __global__ void __launch_bounds__(THREADS, 1)
             int z, m0, n0;
             tm.decode(id, z, m0, n0);
             int ba, bb, b;   // A and B operand matrices, output matrix
-            grid_index(ep, z, bidx ? bidx[z] : z, ba, bb, b);
+            if constexpr (GRID) {
+                grid_index(ep, z, z, ba, bb, b);
+            } else {
+                b = bidx ? bidx[z] : z;
+                ba = bb = b;
+            }
             long long W[EPI_COLS];
             float T[EPI_COLS];
 #pragma unroll
@@ -947,7 +1025,10 @@ __global__ void __launch_bounds__(THREADS, 1)
             double* orow = ep.out + (long long)b * ep.out_bstride + (long long)row * n + cb;
             const bool vec4 = ((uintptr_t)orow & 31) == 0;
             const bool head = !SPLIT || kb0 == 0;   // this CTA owns the tile
-            const bool pre = ep_pre && head && row < n && cb + EPI_COLS <= n;
+            const bool pre = !GRID && ep_pre && head && row < n && cb + EPI_COLS <= n;
+            if (GRID && ep.add && row < n && cb < n)   // the addend's 16 entries: one line, early
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(ep.add + (long long)b * ep.add_bstride +
+                                                              (long long)row * n + cb));
             if (pre) f64e_block_sum16(ep, b, row, cb, n, orow);
             const int c_end = (kb1 - 1) / kb_per_chunk;
             for (int c = kb0 / kb_per_chunk; c <= c_end; ++c, ++gc) {
@@ -975,7 +1056,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 mbar_arrive_cta(tmem_free);
                 // |W| < 2^58.02 per chunk: every FLUSH chunks it is added, in FP64, to this
                 // tile's own output entries (used as scratch), so the integer never overflows
-                if (nchunks > FLUSH && (c % FLUSH == FLUSH - 1 || c == nchunks - 1) && row < n) {
+                if (!GRID && nchunks > FLUSH && (c % FLUSH == FLUSH - 1 || c == nchunks - 1) && row < n) {
 #pragma unroll
                     for (int j = 0; j < EPI_COLS; ++j) {
                         if (cb + j < n) orow[j] = (c < FLUSH ? 0.0 : orow[j]) + (double)W[j];
@@ -1046,6 +1127,10 @@ __global__ void __launch_bounds__(THREADS, 1)
                                                          val[2], val[3]);
                         val[0] = r.x; val[1] = r.y; val[2] = r.z; val[3] = r.w;
                     } else if (fast && ep_sum && cb + EPI_COLS <= n && nchunks <= FLUSH) {
+                        if (alpham1) {
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) val[u] = -val[u];
+                        }
                         const F64x4 r = f64e_sum_store4(ep, b, row, cb + g, n, val[0], val[1],
                                                         val[2], val[3]);
                         val[0] = r.x; val[1] = r.y; val[2] = r.z; val[3] = r.w;
@@ -1060,7 +1145,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                         }
                     }
                 }
-                if (ep.rmax || ep.cmax) {
+                if (!GRID && (ep.rmax || ep.cmax)) {
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         const int c = exp_code(val[u]);
@@ -1073,7 +1158,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     }
                 }
             }
-            if (ep.rmax && inside && mrow) atomicMax(ep.rmax + (long long)b * n + row, mrow);
+            if (!GRID && ep.rmax && inside && mrow) atomicMax(ep.rmax + (long long)b * n + row, mrow);
         }
     }
     __syncwarp();
@@ -1138,7 +1223,7 @@ int sm_count(int dev) {
     return cache[dev];
 }
 
-template <int K>
+template <int K, bool GRID = false>
 mpps_status launch_k(int dev, int grid, const CUtensorMap& ta, const CUtensorMap& tb, int n,
                      int kpA, int ksB, int batch, const int* eA, const int* eB, const Epilogue& ep,
                      int* d_err, cudaStream_t st, const int* bidx, const Split& sp) {
@@ -1147,23 +1232,23 @@ mpps_status launch_k(int dev, int grid, const CUtensorMap& ta, const CUtensorMap
     static_assert(smem <= SMEM_MAX, "shared memory budget exceeded");
     // split K only for the slice counts of working-precision products (7..9); the split
     // kernel is a separate instantiation so that the whole-tile kernel keeps its code
-    constexpr bool kSplit = K >= kMinSplitSlices;
+    constexpr bool kSplit = K >= kMinSplitSlices && !GRID;
     static std::mutex attr_mu;
     static bool attr_done[64] = {false};
     std::unique_lock<std::mutex> attr_lk(attr_mu);
     if (!attr_done[dev]) {
-        MPPS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_f64e<K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           smem));
+        MPPS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_f64e<K, false, GRID>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         if (kSplit)
-            MPPS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_f64e<K, kSplit>,
+            MPPS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_f64e<K, kSplit, false>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         attr_done[dev] = true;
     }
     attr_lk.unlock();
     if (kSplit && sp.U > 0)
-        MPPS_CUDA_TRY(launch_pdl(k_gemm_f64e<K, kSplit>, dim3(grid), dim3(THREADS), smem, st, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, bidx, sp));
+        MPPS_CUDA_TRY(launch_pdl(k_gemm_f64e<K, kSplit, false>, dim3(grid), dim3(THREADS), smem, st, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, bidx, sp));
     else
-        MPPS_CUDA_TRY(launch_pdl(k_gemm_f64e<K, false>, dim3(grid), dim3(THREADS), smem, st, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, bidx, sp));
+        MPPS_CUDA_TRY(launch_pdl(k_gemm_f64e<K, false, GRID>, dim3(grid), dim3(THREADS), smem, st, ta, tb, n, kpA, ksB, batch, eA, eB, ep, d_err, bidx, sp));
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }
@@ -1356,6 +1441,36 @@ mpps_status launch_slice_cols(const double* M, long long bs, int n, int batch, i
     }
 }
 
+mpps_status launch_slice_tiles(int k, const double* A, long long a_bs, int nI, const double* B,
+                               long long b_bs, int nJ, int n, void* planesA, int* eA,
+                               void* planesB, int* eB, cudaStream_t st) {
+    k = f64e_planes(k);
+    if (n > 64 || n < 2 || (n & 1)) {
+        set_error("slice_tiles: tile size %d outside 2..64 (even)", n);
+        return MPPS_EINVAL;
+    }
+    if (nI < 0 || nJ < 0 || nI + nJ <= 0) return MPPS_OK;
+    ProfScope prof(MPPS_PROF_SLICE, st);
+    const int lld = low_ld(n);
+    __nv_bfloat16* pa = (__nv_bfloat16*)planesA;
+    __nv_bfloat16* pb = (__nv_bfloat16*)planesB;
+    const dim3 g(nI + nJ);
+    switch (k) {
+#define MPPS_SLICE_TILES(KS)                                                                     \
+    case KS:                                                                                     \
+        MPPS_CUDA_TRY(launch_pdl(k_slice_tiles<KS>, g, dim3(256), 0, st, A, a_bs, nI, B, b_bs, n, \
+                                 digit_offset(KS), pa, pb, lld, eA, eB));                        \
+        break;
+        MPPS_SLICE_TILES(1) MPPS_SLICE_TILES(2) MPPS_SLICE_TILES(3) MPPS_SLICE_TILES(4)
+        MPPS_SLICE_TILES(5) MPPS_SLICE_TILES(6) MPPS_SLICE_TILES(7)
+        default:
+        MPPS_SLICE_TILES(8)
+#undef MPPS_SLICE_TILES
+    }
+    MPPS_LAUNCH_CHECK();
+    return MPPS_OK;
+}
+
 mpps_status launch_gemm_f64e(int k, const void* slicesA, int ksA, const int* eA,
                              const void* slicesBt, int ksB, const int* eB, int n, int batch,
                              int nmat, const Epilogue& ep, int* d_err, cudaStream_t st,
@@ -1439,9 +1554,10 @@ mpps_status launch_gemm_f64e_grid(int k, const void* slicesA, const int* eA, int
                                   const void* slicesBt, const int* eB, int nmatB, int n,
                                   const Epilogue& ep, int* d_err, cudaStream_t st) {
     if (nmatA <= 0 || nmatB <= 0) return MPPS_OK;
-    if (k < 1 || k > MPPS_F64E_MAX_SLICES || ep.gnj != nmatB) {
-        set_error("emulated FP64 grid product: slice count %d or grid width %d (need %d)", k,
-                  ep.gnj, nmatB);
+    if (k < 1 || k > MPPS_F64E_MAX_SLICES || ep.gnj != nmatB || n > KCHUNK || ep.rmax ||
+        ep.cmax || ep.nt >= 0) {
+        set_error("emulated FP64 grid product: slice count %d, grid width %d (need %d), tile %d "
+                  "(at most %d, no block sum or exponent codes)", k, ep.gnj, nmatB, n, KCHUNK);
         return MPPS_EINVAL;
     }
     const int kp = f64e_planes(k);
@@ -1469,15 +1585,15 @@ mpps_status launch_gemm_f64e_grid(int k, const void* slicesA, const int* eA, int
     const Split sp{0, nullptr, nullptr, nullptr, 0u};
     const int nb = (int)batch;
     switch (k) {
-        case 1: return launch_k<1>(dev, grid, ta, tb, n, kpA, kp, nb, eA, eB, ep, d_err, st, nullptr, sp);
-        case 2: return launch_k<2>(dev, grid, ta, tb, n, kpA, kp, nb, eA, eB, ep, d_err, st, nullptr, sp);
-        case 3: return launch_k<3>(dev, grid, ta, tb, n, kpA, kp, nb, eA, eB, ep, d_err, st, nullptr, sp);
-        case 4: return launch_k<4>(dev, grid, ta, tb, n, kpA, kp, nb, eA, eB, ep, d_err, st, nullptr, sp);
-        case 5: return launch_k<5>(dev, grid, ta, tb, n, kpA, kp, nb, eA, eB, ep, d_err, st, nullptr, sp);
-        case 6: return launch_k<6>(dev, grid, ta, tb, n, kpA, kp, nb, eA, eB, ep, d_err, st, nullptr, sp);
-        case 7: return launch_k<7>(dev, grid, ta, tb, n, kpA, kp, nb, eA, eB, ep, d_err, st, nullptr, sp);
-        case 8: return launch_k<8>(dev, grid, ta, tb, n, kpA, kp, nb, eA, eB, ep, d_err, st, nullptr, sp);
-        default: return launch_k<9>(dev, grid, ta, tb, n, kpA, kp, nb, eA, eB, ep, d_err, st, nullptr, sp);
+        case 1: return launch_k<1, true>(dev, grid, ta, tb, n, kpA, kp, nb, eA, eB, ep, d_err, st, nullptr, sp);
+        case 2: return launch_k<2, true>(dev, grid, ta, tb, n, kpA, kp, nb, eA, eB, ep, d_err, st, nullptr, sp);
+        case 3: return launch_k<3, true>(dev, grid, ta, tb, n, kpA, kp, nb, eA, eB, ep, d_err, st, nullptr, sp);
+        case 4: return launch_k<4, true>(dev, grid, ta, tb, n, kpA, kp, nb, eA, eB, ep, d_err, st, nullptr, sp);
+        case 5: return launch_k<5, true>(dev, grid, ta, tb, n, kpA, kp, nb, eA, eB, ep, d_err, st, nullptr, sp);
+        case 6: return launch_k<6, true>(dev, grid, ta, tb, n, kpA, kp, nb, eA, eB, ep, d_err, st, nullptr, sp);
+        case 7: return launch_k<7, true>(dev, grid, ta, tb, n, kpA, kp, nb, eA, eB, ep, d_err, st, nullptr, sp);
+        case 8: return launch_k<8, true>(dev, grid, ta, tb, n, kpA, kp, nb, eA, eB, ep, d_err, st, nullptr, sp);
+        default: return launch_k<9, true>(dev, grid, ta, tb, n, kpA, kp, nb, eA, eB, ep, d_err, st, nullptr, sp);
     }
 }
 

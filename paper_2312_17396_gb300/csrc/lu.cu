@@ -1,26 +1,28 @@
 // lu.cu -- R = Q^-1 P by LU factorisation with partial pivoting: the q(X)^-1 p(X) solve of
 // the [13/13] Pade approximant (Section 4.1, the diagonal Pade approximant r_m = q_m^-1 p_m).
 //
-// Blocked right-looking LU (Golub and Van Loan, Algorithm 3.4.2 with row interchanges), laid
-// out for a GPU whose FP64 pipe gives about 1 TFLOP/s while the emulated FP64 product on the
-// BF16 tensor cores gives tens of TFLOP/s:
+// Blocked right-looking LU (Golub and Van Loan, Algorithm 3.4.2 with row interchanges) of the
+// augmented matrix [Q | P], laid out for a GPU whose FP64 pipe gives about 1 TFLOP/s while
+// the emulated FP64 product on the BF16 tensor cores gives tens of TFLOP/s:
 //
-//   * Q and P are copied into a tile-major layout: T x T tiles of TB x TB doubles, each tile
+//   * [Q | P] is copied into a tile-major layout: T x 2T tiles of TB x TB doubles, each tile
 //     a contiguous row-major TB x TB matrix, n padded to N = T TB with Q = diag(Q, I) and
 //     P = diag(P, 0) (the padded unknowns are zero).  Every block operation below is then a
 //     batch of TB x TB products, run by the existing products in grid mode (product z takes
 //     A tile z / nJ and B tile z % nJ).
 //   * Panel k (tile column k, rows k TB .. N): one thread-block cluster.  CTA c holds rows
 //     [c R, (c + 1) R) of the panel in its shared memory (in place in the tiles when the
-//     panel is too tall); per column: local pivot candidates, a cluster barrier, the pivot
-//     row read from its owner's shared memory, a second barrier, the interchange, the
-//     multipliers and the rank-1 update of the panel's later columns (FP64 pipe).  The
-//     panel's interchanges leave as a list of (destination, source) rows.
-//   * The interchanges applied to the rest of Q and to P (one gather per panel); the
-//     diagonal tile's unit-lower and upper triangles inverted column by column (FP64).
-//   * U_kJ = L_kk^-1 A_kJ and the trailing update A_IJ -= L_Ik U_kJ as tile products.
-//   * The solve: block forward substitution Y_J = L_JJ^-1 (P_J - sum_{I<J} L_JI Y_I) and
-//     block back substitution X_J = U_JJ^-1 (Y_J - sum_{I>J} U_JI X_I), written
+//     panel is too tall); per column: local pivot candidates published with copies of their
+//     rows, one cluster barrier, the pivot row read from the winner's shared memory, the
+//     multipliers and the rank-1 update of the panel's later columns with the interchange
+//     folded in (FP64 pipe).  The panel's interchanges leave as a list of (destination,
+//     source) rows.
+//   * The interchanges applied to the rest of [Q | P] (one gather per panel); the diagonal
+//     tile's unit-lower and upper triangles inverted column by column (FP64).
+//   * U_kJ = L_kk^-1 A_kJ and the trailing update A_IJ -= L_Ik U_kJ as tile products, over
+//     the columns of Q and of P: on P's columns they are the block forward substitution
+//     L Y = P, so that P's tiles hold Y when the factorisation ends.
+//   * The block back substitution X_J = U_JJ^-1 (Y_J - sum_{I>J} U_JI X_I), written
 //     right-looking so that every update is again a batch of tile products.
 //
 // Products use the working precision of the caller's policy: emulated FP64 with k slices
@@ -45,62 +47,78 @@ constexpr int LDS = TB + 1;             // shared row pitch of the panel (double
 constexpr int MAXPAIRS = 2 * TB;        // rows one panel's interchanges can move
 constexpr int PAIR_INTS = 1 + 2 * MAXPAIRS;
 constexpr int SMEM_DYN_MAX = 216 * 1024;
-constexpr int ROWS_SMEM_MAX = (SMEM_DYN_MAX - 2 * TB * 8) / (LDS * 8);
+// panel rows a CTA keeps in shared memory: LDS doubles each plus one multiplier
+constexpr int ROWS_SMEM_MAX = (SMEM_DYN_MAX / 8 - 2 * TB) / (LDS + 1);
 
-__host__ __device__ __forceinline__ size_t tile_off(int T, int I, int J) {
-    return ((size_t)I * T + J) * TB * TB;
+// tile (I, J) of a tile-major array W tiles wide
+__host__ __device__ __forceinline__ size_t tile_off(int W, int I, int J) {
+    return ((size_t)I * W + J) * TB * TB;
 }
-__host__ __device__ __forceinline__ size_t elem_off(int T, int r, int c) {
-    return tile_off(T, r / TB, c / TB) + (size_t)(r % TB) * TB + (c % TB);
+__host__ __device__ __forceinline__ size_t elem_off(int W, int r, int c) {
+    return tile_off(W, r / TB, c / TB) + (size_t)(r % TB) * TB + (c % TB);
 }
 
-// dst (tile-major, N = T TB) from the row-major n x n src; the padding holds `diag` on the
-// diagonal and zeros elsewhere.  Block (64, 4): 64 consecutive columns of 4 rows.
-__global__ void k_lu_to_tiles(const double* __restrict__ src, int n, int T, double diag,
-                              double* __restrict__ dst) {
+// Columns c0 .. c0 + N - 1 of the tile-major array (W tiles wide, N = T TB) from the
+// row-major n x n src; the padding holds `diag` on the diagonal and zeros elsewhere.  Block
+// (64, 4): 64 consecutive columns of 4 rows.
+__global__ void k_lu_to_tiles(const double* __restrict__ src, int n, int T, int W, int c0,
+                              double diag, double* __restrict__ dst) {
     const int N = T * TB;
     const int c = blockIdx.x * 64 + threadIdx.x, r = blockIdx.y * 4 + threadIdx.y;
     if (r >= N || c >= N) return;
     const double v = (r < n && c < n) ? src[(size_t)r * n + c] : (r == c ? diag : 0.0);
-    dst[elem_off(T, r, c)] = v;
+    dst[elem_off(W, r, c0 + c)] = v;
 }
 
-// The leading n x n block of the tile-major src, row-major into dst.
-__global__ void k_lu_from_tiles(const double* __restrict__ src, int n, int T,
+// The leading n x n block of columns c0 .. of the tile-major src, row-major into dst.
+__global__ void k_lu_from_tiles(const double* __restrict__ src, int n, int W, int c0,
                                 double* __restrict__ dst) {
     const int c = blockIdx.x * 64 + threadIdx.x, r = blockIdx.y * 4 + threadIdx.y;
     if (r >= n || c >= n) return;
-    dst[(size_t)r * n + c] = src[elem_off(T, r, c)];
+    dst[(size_t)r * n + c] = src[elem_off(W, r, c0 + c)];
 }
 
-// The interchanges of panel k applied to every tile column of Q except column k (which the
-// panel kernel has already permuted) and to every tile column of P: new row dst_i = old row
-// src_i for the listed pairs (a permutation of the rows they name).  One warp per half tile
-// column (32 columns): each thread reads all source entries of its column, then writes.
-__global__ void __launch_bounds__(32) k_lu_swap(double* __restrict__ Qt, double* __restrict__ Pt,
-                                                int T, int k, const int* __restrict__ pairs) {
-    __shared__ double vals[MAXPAIRS][32];
-    const int tc = blockIdx.x >> 1;                  // 0 .. 2T-1: Q's tile columns, then P's
-    const bool isq = tc < T;
-    const int J = isq ? tc : tc - T;
-    if (isq && J == k) return;
-    double* M = isq ? Qt : Pt;
-    const int col = J * TB + (blockIdx.x & 1) * 32 + threadIdx.x;
+// The interchanges of panel k applied to every tile column of [Q | P] except column k
+// (which the panel kernel has already permuted): new row dst_i = old row src_i for the
+// listed pairs (a permutation of the rows they name).  A block takes 32 columns: its 8 warps
+// read every source entry of them into shared memory (four loads in flight per thread),
+// then write the destinations.
+__global__ void __launch_bounds__(256) k_lu_swap(double* __restrict__ M, int W, int k,
+                                                 const int* __restrict__ pairs) {
+    __shared__ double vals[MAXPAIRS][33];
+    const int J = blockIdx.x >> 1;
+    if (J == k) return;                              // the whole block
+    const int cx = threadIdx.x & 31, sy = threadIdx.x >> 5;
+    const int col = J * TB + (blockIdx.x & 1) * 32 + cx;
     const int cnt = min(__ldg(pairs), MAXPAIRS);
-    for (int i = 0; i < cnt; ++i) vals[i][threadIdx.x] = M[elem_off(T, __ldg(pairs + 2 + 2 * i), col)];
-    for (int i = 0; i < cnt; ++i) M[elem_off(T, __ldg(pairs + 1 + 2 * i), col)] = vals[i][threadIdx.x];
+    for (int i0 = sy; i0 < cnt; i0 += 32) {
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + 8 * u;
+            v[u] = i < cnt ? M[elem_off(W, __ldg(pairs + 2 + 2 * i), col)] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (i0 + 8 * u < cnt) vals[i0 + 8 * u][cx] = v[u];
+    }
+    __syncthreads();
+    for (int i = sy; i < cnt; i += 8) M[elem_off(W, __ldg(pairs + 1 + 2 * i), col)] = vals[i][cx];
 }
 
 // Column `blockIdx.x` of the inverses of the diagonal tile's unit lower triangle
 // (blockIdx.y = 0: L x = e_c by forward substitution, column-oriented) and of its upper
-// triangle (blockIdx.y = 1: U x = e_c by back substitution), thread i holding x_i.  The
-// tiles are written row-major into invL / invU at tile k.
-__global__ void __launch_bounds__(TB) k_lu_tri_inv(const double* __restrict__ Qt, int T, int k,
+// triangle (blockIdx.y = 1: U x = e_c by back substitution), thread i holding x_i; the tile
+// is staged in shared memory first.  The tiles are written row-major into invL / invU at
+// tile k.
+__global__ void __launch_bounds__(TB) k_lu_tri_inv(const double* __restrict__ M, int W, int k,
                                                    double* __restrict__ invL,
                                                    double* __restrict__ invU) {
     const int col = blockIdx.x, i = threadIdx.x;
-    const double* D = Qt + tile_off(T, k, k);
+    __shared__ double D[TB][TB + 1];
     __shared__ double x[TB];
+    const double* src = M + tile_off(W, k, k);
+    for (int e = i; e < TB * TB; e += TB) D[e / TB][e % TB] = src[e];
     double xi = i == col ? 1.0 : 0.0;
     x[i] = xi;
     if (blockIdx.y == 0) {
@@ -108,7 +126,7 @@ __global__ void __launch_bounds__(TB) k_lu_tri_inv(const double* __restrict__ Qt
             __syncthreads();
             const double xj = x[j];
             if (i > j) {
-                xi = fma(-D[i * TB + j], xj, xi);
+                xi = fma(-D[i][j], xj, xi);
                 x[i] = xi;
             }
         }
@@ -117,12 +135,12 @@ __global__ void __launch_bounds__(TB) k_lu_tri_inv(const double* __restrict__ Qt
         for (int j = col; j >= 0; --j) {
             __syncthreads();
             if (i == j) {
-                xi = xi / D[j * TB + j];
+                xi = xi / D[j][j];
                 x[j] = xi;
             }
             __syncthreads();
             const double xj = x[j];
-            if (i < j) xi = fma(-D[i * TB + j], xj, xi);
+            if (i < j) xi = fma(-D[i][j], xj, xi);
         }
         invU[(size_t)k * TB * TB + (size_t)i * TB + col] = xi;
     }
@@ -130,34 +148,39 @@ __global__ void __launch_bounds__(TB) k_lu_tri_inv(const double* __restrict__ Qt
 
 // ---- panel factorisation (one cluster) ---------------------------------------------------
 struct PanelArgs {
-    double* Qt;
-    int T, k;
+    double* M;
+    int T, W, k;
     int R;          // panel rows per CTA (CTA c: rows c R .. c R + R - 1, clipped)
     int in_smem;    // 1: rows held in shared memory; 0: worked on in place in the tiles
     int* pairs;     // out: count, then (destination, source) global row pairs
     int* info;      // first zero pivot (1-based global column), 0 if none
 };
 
-// The better of two pivot candidates: the larger magnitude, the smaller row on ties (the
-// first maximum, as the usual partial pivoting search takes).  A NaN never wins; v = -1
-// marks "no row".
-__device__ __forceinline__ void cand_max(double& v, int& i, double ov, int oi) {
+// Pivot candidates compare on the integer pipe: |x| as the bit pattern of a non-negative
+// double orders like |x| (a NaN maps to 0 and never wins).  The better of two candidates
+// has the larger magnitude, the smaller row on ties (the first maximum, as the usual partial
+// pivoting search takes); (0, INT_MAX) is "no row".
+__device__ __forceinline__ unsigned long long piv_key(double x) {
+    const unsigned long long a = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffULL;
+    return a > 0x7ff0000000000000ULL ? 0ULL : a;
+}
+__device__ __forceinline__ void cand_max(unsigned long long& v, int& i, unsigned long long ov, int oi) {
     if (ov > v || (ov == v && oi < i)) {
         v = ov;
         i = oi;
     }
 }
-__device__ __forceinline__ void cand_warp_max(double& v, int& i) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, i, o);
-        cand_max(v, i, ov, oi);
-    }
-}
 
 // Every thread of every CTA of the cluster runs the same sequence of barriers: no thread
-// leaves early, whatever its rows.
+// leaves early, whatever its rows.  Per column j, one cluster barrier: before it, each CTA
+// publishes its candidate (magnitude, row) and a copy of that row, and the owner of row j a
+// copy of row j, in the slot of the column's parity; after it, every warp finds the winner
+// and the CTA reads the copies it needs from the other CTAs' shared memory.  A CTA writes
+// only its own rows, and a slot is written again two columns later, after the next barrier,
+// when every read of it is done.  The multipliers use the reciprocal of the pivot (as the
+// unblocked LAPACK factorisation does), and the interchange is folded into the update: row
+// p is rebuilt from the copy of the old row j.
+template <bool SMEM>
 __global__ void __launch_bounds__(PT) k_lu_panel(PanelArgs a) {
     cg::cluster_group cl = cg::this_cluster();
     const int c = (int)cl.block_rank(), CL = (int)cl.num_blocks();
@@ -166,30 +189,29 @@ __global__ void __launch_bounds__(PT) k_lu_panel(PanelArgs a) {
     const int r0 = c * a.R;
     const int nr = max(0, min(a.R, Mk - r0));
     extern __shared__ __align__(16) double sm[];
-    double* rows = sm;                                          // [R][LDS] (in_smem)
-    double* urow = sm + (a.in_smem ? (size_t)a.R * LDS : 0);    // the pivot row
+    double* rows = sm;                                          // [R][LDS] (SMEM)
+    double* urow = sm + (SMEM ? (size_t)a.R * LDS : 0);         // the pivot row
     double* tmp = urow + TB;                                    // the old row j (owner of p)
-    __shared__ double cand_v;                                   // read by the other CTAs
-    __shared__ int cand_i;
-    __shared__ double red_v[PT / 32];
+    double* lmul = tmp + TB;                                    // this column's multipliers
+    __shared__ double pub_cand[2][TB];                          // published: candidate row
+    __shared__ double pub_rowj[2][TB];                          // published: row j (its owner)
+    __shared__ unsigned long long cand_v[2];
+    __shared__ int cand_i[2];
+    __shared__ double s_pinv;
+    __shared__ unsigned long long red_v[PT / 32];
     __shared__ int red_i[PT / 32];
-    __shared__ int s_p, s_sing, s_ns;
+    __shared__ int s_ns, s_p, s_w;
     __shared__ int sl_row[MAXPAIRS], sl_src[MAXPAIRS];          // CTA 0: the interchanges
 
     auto gptr = [&](int pr) -> double* {   // panel row pr in the tile storage
-        return a.Qt + tile_off(a.T, a.k + pr / TB, a.k) + (size_t)(pr % TB) * TB;
+        return a.M + tile_off(a.W, a.k + pr / TB, a.k) + (size_t)(pr % TB) * TB;
     };
     auto own = [&](int lr) -> double* {
-        return a.in_smem ? rows + (size_t)lr * LDS : gptr(r0 + lr);
-    };
-    // entry `col` of panel row pr, wherever its owner keeps it
-    auto rload = [&](int pr, int col) -> double {
-        const int o = pr / a.R;
-        if (a.in_smem) return cl.map_shared_rank(rows, o)[(size_t)(pr - o * a.R) * LDS + col];
-        return __ldcg(gptr(pr) + col);
+        if constexpr (SMEM) return rows + (size_t)lr * LDS;
+        else return gptr(r0 + lr);
     };
 
-    if (a.in_smem)
+    if (SMEM)
         for (int e = tid; e < nr * TB; e += PT) rows[(size_t)(e / TB) * LDS + e % TB] = gptr(r0 + e / TB)[e % TB];
     if (c == 0) {
         for (int s = tid; s < MAXPAIRS; s += PT) {
@@ -198,46 +220,63 @@ __global__ void __launch_bounds__(PT) k_lu_panel(PanelArgs a) {
         }
         if (tid == 0) s_ns = TB;
     }
-    cl.sync();   // every CTA of the cluster runs and holds its rows
+    __syncthreads();
 
     for (int j = 0; j < TB; ++j) {
+        const int slot = j & 1;
+        const bool own_j = j >= r0 && j < r0 + nr;
+        if (own_j && tid < TB) pub_rowj[slot][tid] = own(j - r0)[tid];
         // (1) this CTA's candidate for column j among its rows j, j+1, ...
-        double bv = -1.0;
+        unsigned long long bv = 0;
         int bi = 0x7fffffff;
         for (int lr = tid; lr < nr; lr += PT)
-            if (r0 + lr >= j) cand_max(bv, bi, fabs(own(lr)[j]), r0 + lr);
-        cand_warp_max(bv, bi);
+            if (r0 + lr >= j) cand_max(bv, bi, piv_key(own(lr)[j]), r0 + lr);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            cand_max(bv, bi, __shfl_xor_sync(0xffffffffu, bv, o), __shfl_xor_sync(0xffffffffu, bi, o));
         if (lane == 0) {
             red_v[warp] = bv;
             red_i[warp] = bi;
         }
         __syncthreads();
-        if (warp == 0) {
-            bv = lane < PT / 32 ? red_v[lane] : -1.0;
-            bi = lane < PT / 32 ? red_i[lane] : 0x7fffffff;
-            cand_warp_max(bv, bi);
-            if (lane == 0) {
-                cand_v = bv;
-                cand_i = bi;
-            }
+        bv = red_v[0];
+        bi = red_i[0];
+#pragma unroll
+        for (int w = 1; w < PT / 32; ++w) cand_max(bv, bi, red_v[w], red_i[w]);
+        if (tid == 0) {
+            cand_v[slot] = bv;
+            cand_i[slot] = bi;
         }
-        cl.sync();   // (2) every CTA's candidate is written
+        if (tid < TB && bi != 0x7fffffff) pub_cand[slot][tid] = own(bi - r0)[tid];
+        cl.sync();   // (2) every CTA's candidate and copies are published
+        // (3) the winner, found by warp 0 (one remote read per CTA) and broadcast
         if (warp == 0) {
-            double v = -1.0;
-            int i = 0x7fffffff;
+            unsigned long long v = 0;
+            int i = 0x7fffffff, w = lane;
             if (lane < CL) {
-                v = *cl.map_shared_rank(&cand_v, lane);
-                i = *cl.map_shared_rank(&cand_i, lane);
+                v = cl.map_shared_rank(cand_v, lane)[slot];
+                i = cl.map_shared_rank(cand_i, lane)[slot];
             }
-            cand_warp_max(v, i);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long ov = __shfl_xor_sync(0xffffffffu, v, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+                const int ow = __shfl_xor_sync(0xffffffffu, w, o);
+                if (ov > v || (ov == v && oi < i)) {
+                    v = ov;
+                    i = oi;
+                    w = ow;
+                }
+            }
             if (lane == 0) {
-                s_sing = !(v > 0.0);   // an exactly zero (or NaN) column: no interchange
-                s_p = s_sing ? j : i;
+                const bool zero = v == 0;   // an exactly zero (or NaN) column
+                s_p = zero ? -1 : i;
+                s_w = w;
             }
         }
         __syncthreads();
-        const int p = s_p;
-        const bool sing = s_sing != 0;
+        const bool sing = s_p < 0;
+        const int p = sing ? j : s_p, w = s_w;
         if (c == 0 && warp == 0) {   // the interchange list, and the first zero pivot
             if (sing && lane == 0) atomicCAS(a.info, 0, a.k * TB + j + 1);
             if (p != j) {
@@ -268,35 +307,44 @@ __global__ void __launch_bounds__(PT) k_lu_panel(PanelArgs a) {
                 __syncwarp();
             }
         }
-        // (3) the pivot row, and (at the owner of row p) the old row j
-        const int op = p / a.R;
-        if (tid < TB) {
-            urow[tid] = rload(p, tid);
-            if (op == c && p != j) tmp[tid] = rload(j, tid);
-        }
-        cl.sync();   // (4) every read of the rows j and p is done
-        if (tid < TB && p != j) {
-            if (j / a.R == c) own(j - r0)[tid] = urow[tid];
-            if (op == c) own(p - r0)[tid] = tmp[tid];
-        }
-        __syncthreads();
         if (!sing) {
-            const double piv = urow[j];
-            for (int lr = tid; lr < nr; lr += PT)
-                if (r0 + lr > j) own(lr)[j] = own(lr)[j] / piv;
+            const bool swap_p = p != j && p >= r0 && p < r0 + nr;   // this CTA rebuilds row p
+            if (tid < TB) {
+                const double x = cl.map_shared_rank(&pub_cand[0][0], w)[slot * TB + tid];
+                urow[tid] = x;
+                if (tid == j) s_pinv = 1.0 / x;   // once, on the FP64 pipe
+                if (swap_p) tmp[tid] = cl.map_shared_rank(&pub_rowj[0][0], j / a.R)[slot * TB + tid];
+            }
             __syncthreads();
+            // (4) the multipliers (row p's from the old row j) and the new row j
+            const double pinv = s_pinv;
+            for (int lr = tid; lr < nr; lr += PT) {
+                const int pr = r0 + lr;
+                if (pr > j) lmul[lr] = (pr == p && swap_p ? tmp[j] : own(lr)[j]) * pinv;
+            }
+            if (own_j && p != j && tid < TB) own(j - r0)[tid] = urow[tid];
+            __syncthreads();
+            // (5) the rank-1 update of the later columns; row p takes the old row j's entries
             const int col = tid % TB;
-            if (col > j)
+            const double u = urow[col];
+            if (col > j) {
+#pragma unroll 4
+                for (int lr = tid / TB; lr < nr; lr += PT / TB) {
+                    if (r0 + lr <= j) continue;
+                    double* rw = own(lr) + col;
+                    *rw = fma(-lmul[lr], u, (swap_p && r0 + lr == p) ? tmp[col] : *rw);
+                }
+            } else if (col == j) {
                 for (int lr = tid / TB; lr < nr; lr += PT / TB)
-                    if (r0 + lr > j) {
-                        double* rw = own(lr);
-                        rw[col] = fma(-rw[j], urow[col], rw[col]);
-                    }
+                    if (r0 + lr > j) own(lr)[j] = lmul[lr];
+            } else if (swap_p && (p - r0) % (PT / TB) == tid / TB) {
+                own(p - r0)[col] = tmp[col];
+            }
         }
         __syncthreads();
     }
 
-    if (a.in_smem)
+    if (SMEM)
         for (int e = tid; e < nr * TB; e += PT) gptr(r0 + e / TB)[e % TB] = rows[(size_t)(e / TB) * LDS + e % TB];
     if (c == 0 && tid == 0) {
         int cnt = 0;
@@ -317,15 +365,15 @@ __global__ void __launch_bounds__(PT) k_lu_panel(PanelArgs a) {
 namespace {
 
 struct LuLayout {
-    int T, N;
-    size_t off_Qt, off_Pt, off_invL, off_invU, off_pairs, off_slA, off_slB, off_eA, off_eB,
-        off_cmx, bytes;
+    int T, N, W;
+    size_t off_M, off_invL, off_invU, off_pairs, off_slA, off_slB, off_eA, off_eB, bytes;
 };
 
 LuLayout lu_layout(int n, int k) {
     LuLayout L;
     L.T = (n + TB - 1) / TB;
     L.N = L.T * TB;
+    L.W = 2 * L.T;
     size_t off = 0;
     auto take = [&](size_t bytes) {
         off = (off + 255) & ~(size_t)255;
@@ -333,18 +381,15 @@ LuLayout lu_layout(int n, int k) {
         off += bytes;
         return at;
     };
-    const size_t NN = (size_t)L.N * L.N;
-    L.off_Qt = take(NN * sizeof(double));
-    L.off_Pt = take(NN * sizeof(double));
+    L.off_M = take((size_t)L.T * L.W * TB * TB * sizeof(double));
     L.off_invL = take((size_t)L.T * TB * TB * sizeof(double));
     L.off_invU = take((size_t)L.T * TB * TB * sizeof(double));
     L.off_pairs = take(PAIR_INTS * sizeof(int));
-    const size_t planes = k > 0 ? f64e_plane_elems(TB, L.T, k) * sizeof(__nv_bfloat16) : 0;
-    L.off_slA = take(planes);
-    L.off_slB = take(planes);
+    // A operands: at most T tiles; B operands: at most W tiles (a tile row of [Q | P])
+    L.off_slA = take(k > 0 ? f64e_plane_elems(TB, L.T, k) * sizeof(__nv_bfloat16) : 0);
+    L.off_slB = take(k > 0 ? f64e_plane_elems(TB, L.W, k) * sizeof(__nv_bfloat16) : 0);
     L.off_eA = take(k > 0 ? (size_t)L.T * TB * sizeof(int) : 0);
-    L.off_eB = take(k > 0 ? (size_t)L.T * TB * sizeof(int) : 0);
-    L.off_cmx = take(k > 0 ? (size_t)L.T * TB * sizeof(unsigned long long) : 0);
+    L.off_eB = take(k > 0 ? (size_t)L.W * TB * sizeof(int) : 0);
     L.bytes = (off + 255) & ~(size_t)255;
     return L;
 }
@@ -358,9 +403,13 @@ int panel_cluster_max(int dev) {
     if (dev < 0 || dev >= 64) dev = 0;
     if (cache[dev]) return cache[dev];
     int best = 1;
-    if (cudaFuncSetAttribute(k_lu_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_DYN_MAX) ==
+    if (cudaFuncSetAttribute(k_lu_panel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_DYN_MAX) ==
             cudaSuccess &&
-        cudaFuncSetAttribute(k_lu_panel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+        cudaFuncSetAttribute(k_lu_panel<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+            cudaSuccess &&
+        cudaFuncSetAttribute(k_lu_panel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_DYN_MAX) ==
+            cudaSuccess &&
+        cudaFuncSetAttribute(k_lu_panel<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
             cudaSuccess) {
         for (int cl = 16; cl >= 2; cl >>= 1) {
             cudaLaunchConfig_t cfg = {};
@@ -375,7 +424,7 @@ int panel_cluster_max(int dev) {
             cfg.attrs = at;
             cfg.numAttrs = 1;
             int ncl = 0;
-            if (cudaOccupancyMaxActiveClusters(&ncl, k_lu_panel, &cfg) == cudaSuccess && ncl >= 1) {
+            if (cudaOccupancyMaxActiveClusters(&ncl, k_lu_panel<true>, &cfg) == cudaSuccess && ncl >= 1) {
                 best = cl;
                 break;
             }
@@ -388,12 +437,11 @@ int panel_cluster_max(int dev) {
 }
 
 struct LuRun {
-    int T, k;
-    double *Qt, *Pt, *invL, *invU;
+    int T, W, k;
+    double *M, *invL, *invU;
     int* pairs;
     void *slA, *slB;
     int *eA, *eB;
-    unsigned long long* cmx;
     int* d_err;
     cudaStream_t st;
     int cl_max;
@@ -426,8 +474,7 @@ struct LuRun {
             }
             return MPPS_OK;
         }
-        mpps_status rc = launch_slice_rows(A, a_bs, TB, nI, k, slA, eA, st);
-        if (!rc) rc = launch_slice_cols(B, b_bs, TB, nJ, k, slB, eB, cmx, st);
+        mpps_status rc = launch_slice_tiles(k, A, a_bs, nI, B, b_bs, nJ, TB, slA, eA, slB, eB, st);
         if (!rc) rc = launch_gemm_f64e_grid(k, slA, eA, nI, slB, eB, nJ, TB, ep, d_err, st);
         return rc;
     }
@@ -438,11 +485,11 @@ struct LuRun {
         while (cl * 2 <= cl_max && cl * 2 * 32 <= Mk) cl *= 2;
         const int R = (Mk + cl - 1) / cl;
         const bool in_smem = R <= ROWS_SMEM_MAX;
-        PanelArgs a{Qt, T, kk, R, in_smem ? 1 : 0, pairs, info};
+        PanelArgs a{M, T, W, kk, R, in_smem ? 1 : 0, pairs, info};
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(cl);
         cfg.blockDim = dim3(PT);
-        cfg.dynamicSmemBytes = (in_smem ? (size_t)R * LDS * 8 : 0) + 2 * TB * 8;
+        cfg.dynamicSmemBytes = ((in_smem ? (size_t)R * LDS : 0) + 2 * TB + (size_t)R) * sizeof(double);
         cfg.stream = st;
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeClusterDimension;
@@ -451,50 +498,43 @@ struct LuRun {
         at[0].val.clusterDim.z = 1;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        MPPS_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_lu_panel, a));
+        if (in_smem) MPPS_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_lu_panel<true>, a));
+        else MPPS_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_lu_panel<false>, a));
         MPPS_LAUNCH_CHECK();
         return MPPS_OK;
     }
 
-    // Q = P^T L U in place (tile-major), with the interchanges applied to P as well
+    // Q = P^T L U in place, and P's tiles := L^-1 (interchanged P)
     mpps_status factor(int* info) const {
-        const long long tt = (long long)TB * TB, trow = (long long)T * tt;
+        const long long tt = (long long)TB * TB, trow = (long long)W * tt;
         for (int kk = 0; kk < T; ++kk) {
             mpps_status rc = panel(kk, info);
             if (rc) return rc;
-            k_lu_swap<<<2 * T * 2, 32, 0, st>>>(Qt, Pt, T, kk, pairs);
+            k_lu_swap<<<2 * W, 256, 0, st>>>(M, W, kk, pairs);
             MPPS_LAUNCH_CHECK();
-            k_lu_tri_inv<<<dim3(TB, 2), TB, 0, st>>>(Qt, T, kk, invL, invU);
+            k_lu_tri_inv<<<dim3(TB, 2), TB, 0, st>>>(M, W, kk, invL, invU);
             MPPS_LAUNCH_CHECK();
-            const int nr = T - kk - 1;
-            if (nr == 0) break;
-            double* Ukj = Qt + tile_off(T, kk, kk + 1);
-            // U_kJ = L_kk^-1 A_kJ (J > k), written over A_kJ
-            if ((rc = products(invL + kk * tt, 0, 1, Ukj, tt, nr, Ukj, 0, 1, false))) return rc;
+            const int nr = T - kk - 1, nc = W - kk - 1;
+            double* Ukj = M + tile_off(W, kk, kk + 1);
+            // U_kJ = L_kk^-1 A_kJ (J > k, Q's columns and P's), written over A_kJ
+            if ((rc = products(invL + kk * tt, 0, 1, Ukj, tt, nc, Ukj, 0, 1, false))) return rc;
             // A_IJ -= L_Ik U_kJ (I, J > k)
-            if ((rc = products(Qt + tile_off(T, kk + 1, kk), trow, nr, Ukj, tt, nr,
-                               Qt + tile_off(T, kk + 1, kk + 1), T, 1, true)))
+            if ((rc = products(M + tile_off(W, kk + 1, kk), trow, nr, Ukj, tt, nc,
+                               M + tile_off(W, kk + 1, kk + 1), W, 1, true)))
                 return rc;
         }
         return MPPS_OK;
     }
 
-    // P := U^-1 L^-1 P (P already permuted)
-    mpps_status substitute() const {
-        const long long tt = (long long)TB * TB, trow = (long long)T * tt;
+    // P's tiles := U^-1 P's tiles
+    mpps_status back_substitute() const {
+        const long long tt = (long long)TB * TB, trow = (long long)W * tt;
         mpps_status rc;
-        for (int J = 0; J < T; ++J) {   // Y_J = L_JJ^-1 P_J, then P_I -= L_IJ Y_J (I > J)
-            double* PJ = Pt + tile_off(T, J, 0);
-            if ((rc = products(invL + J * tt, 0, 1, PJ, tt, T, PJ, 0, 1, false))) return rc;
-            if (J + 1 < T &&
-                (rc = products(Qt + tile_off(T, J + 1, J), trow, T - J - 1, PJ, tt, T,
-                               Pt + tile_off(T, J + 1, 0), T, 1, true)))
-                return rc;
-        }
         for (int J = T - 1; J >= 0; --J) {   // X_J = U_JJ^-1 Y_J, then Y_I -= U_IJ X_J (I < J)
-            double* PJ = Pt + tile_off(T, J, 0);
-            if ((rc = products(invU + J * tt, 0, 1, PJ, tt, T, PJ, 0, 1, false))) return rc;
-            if (J > 0 && (rc = products(Qt + tile_off(T, 0, J), trow, J, PJ, tt, T, Pt, T, 1, true)))
+            double* YJ = M + tile_off(W, J, T);
+            if ((rc = products(invU + J * tt, 0, 1, YJ, tt, T, YJ, 0, 1, false))) return rc;
+            if (J > 0 && (rc = products(M + tile_off(W, 0, J), trow, J, YJ, tt, T,
+                                        M + tile_off(W, 0, T), W, 1, true)))
                 return rc;
         }
         return MPPS_OK;
@@ -522,9 +562,9 @@ mpps_status lu_solve_dev(const double* Q, const double* P, double* R, int n, int
     char* base = (char*)ws;
     LuRun run;
     run.T = L.T;
+    run.W = L.W;
     run.k = k;
-    run.Qt = (double*)(base + L.off_Qt);
-    run.Pt = (double*)(base + L.off_Pt);
+    run.M = (double*)(base + L.off_M);
     run.invL = (double*)(base + L.off_invL);
     run.invU = (double*)(base + L.off_invU);
     run.pairs = (int*)(base + L.off_pairs);
@@ -532,22 +572,21 @@ mpps_status lu_solve_dev(const double* Q, const double* P, double* R, int n, int
     run.slB = k > 0 ? base + L.off_slB : nullptr;
     run.eA = k > 0 ? (int*)(base + L.off_eA) : nullptr;
     run.eB = k > 0 ? (int*)(base + L.off_eB) : nullptr;
-    run.cmx = k > 0 ? (unsigned long long*)(base + L.off_cmx) : nullptr;
     run.d_err = d_err;
     run.st = st;
     run.cl_max = panel_cluster_max(dev);
-    const dim3 cb(64, 4), cg_((L.N + 63) / 64, (L.N + 3) / 4), og((n + 63) / 64, (n + 3) / 4);
+    const dim3 cb(64, 4), tg((L.N + 63) / 64, (L.N + 3) / 4), og((n + 63) / 64, (n + 3) / 4);
     const size_t nn = (size_t)n * n;
     MPPS_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int) * (size_t)batch, st));
     for (int b = 0; b < batch; ++b) {   // one system after the other, in one workspace
-        k_lu_to_tiles<<<cg_, cb, 0, st>>>(Q + b * nn, n, L.T, 1.0, run.Qt);
+        k_lu_to_tiles<<<tg, cb, 0, st>>>(Q + b * nn, n, L.T, L.W, 0, 1.0, run.M);
         MPPS_LAUNCH_CHECK();
-        k_lu_to_tiles<<<cg_, cb, 0, st>>>(P + b * nn, n, L.T, 0.0, run.Pt);
+        k_lu_to_tiles<<<tg, cb, 0, st>>>(P + b * nn, n, L.T, L.W, L.N, 0.0, run.M);
         MPPS_LAUNCH_CHECK();
         mpps_status rc = run.factor(info + b);
-        if (!rc) rc = run.substitute();
+        if (!rc) rc = run.back_substitute();
         if (rc) return rc;
-        k_lu_from_tiles<<<og, cb, 0, st>>>(run.Pt, n, L.T, R + b * nn);
+        k_lu_from_tiles<<<og, cb, 0, st>>>(run.M, n, L.W, L.N, R + b * nn);
         MPPS_LAUNCH_CHECK();
     }
     return MPPS_OK;
