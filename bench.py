@@ -48,9 +48,9 @@ def parse():
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--m", type=int, default=30)
     ap.add_argument("--policy", default="ns_e",
-                    choices=["ns_e", "paper_e", "fixed_e", "ns", "paper", "fixed"],
+                    choices=["ns_e", "ns_e_mixp", "paper_e", "fixed_e", "ns", "paper", "fixed"],
                     help="headline policy (the others are timed beside it)")
-    ap.add_argument("--policies", default="fixed,ns,fixed_e,ns_e",
+    ap.add_argument("--policies", default="fixed,ns,fixed_e,ns_e,ns_e_mixp",
                     help="comma list of policies timed beside the headline (fixed is always kept)")
     ap.add_argument("--no-check", action="store_true", help="skip the oracle error check")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -58,8 +58,10 @@ def parse():
                     help="leave out the compact C3/C4/C5 results of the default line")
     ap.add_argument("--kernel", default=None,
                     choices=["gemm_f64", "gemm_bf16", "gemm_bf16x3", "gemm_tf32", "gemm_fp8",
-                             "gemm_f64e9", "gemm_f64e8", "gemm_f64e6"],
-                    help="time one product kernel alone (mpps_matmul) instead of the workload")
+                             "gemm_f64e9", "gemm_f64e8", "gemm_f64e6", "lu_solve_f64e8",
+                             "lu_solve_f64"],
+                    help="time one product kernel alone (mpps_matmul), or one linear solve "
+                         "R = Q^-1 P (lu_solve: the Pade exp's solve), instead of the workload")
     ap.add_argument("--batch", type=int, default=1, help="batch for --kernel")
     ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4", "c5"],
                     help="c2: exp n=1024 (the headline line); c3: 4096 uneven matrices; "
@@ -67,8 +69,41 @@ def parse():
     return ap.parse_args()
 
 
+def run_lu(args):
+    """One linear solve R = Q^-1 P (Gaussian Q and P of order n) per step through lu_solve,
+    timed with CUDA events around each call; 8 n^3 / 3 FP64 flops per solve (the LU and the
+    two triangular solves with n right-hand sides)."""
+    import numpy as np
+    import torch
+
+    import paper_2312_17396_gb300 as mpps
+    from paper_2312_17396_gb300 import inputs
+    dev = torch.device("cuda", 0)
+    n = args.n
+    pol = mpps.FIXED if args.kernel.endswith("_f64") else mpps.FIXED_E
+    Q = torch.from_numpy(inputs.gaussian_batch(1, n, seed=1)).to(dev)
+    P = torch.from_numpy(inputs.gaussian_batch(1, n, seed=2)).to(dev)
+    R = torch.empty_like(P)
+    for _ in range(args.warmup):
+        mpps.lu_solve(Q, P, policy=pol, out=R)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        mpps.lu_solve(Q, P, policy=pol, out=R)
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    avg = float(np.mean(ms))
+    print(json.dumps({"kernel": args.kernel, "n": n, "ms_per_solve": avg,
+                      "fp64_equiv_tflops": 8.0 * n ** 3 / 3.0 / (avg / 1e3) / 1e12}), flush=True)
+
+
 def run_kernel(args):
     """Single-product timing through mpps_matmul: CUDA events around each launch."""
+    if args.kernel.startswith("lu_solve"):
+        return run_lu(args)
     import numpy as np
     import torch
 
@@ -224,6 +259,8 @@ POLICY_DESC = {
     "ns": "mixed (eq. (2.8), FP64 floors on steps 1-2), working precision on the FP64 pipe",
     "paper": "mixed (eq. (2.8) as in Algorithm 3.1), FP64 pipe",
     "fixed": "fixed FP64 on the FP64 pipe (Algorithm 2.1 + eq. (3.6))",
+    "ns_e_mixp": "ns_e with mixed-precision powers: power tree X^2, X^3, Y = X^3 X^3, leaves "
+                 "X^4 = X^3 X and X^5 = X^3 X^2 in the slices the leaf rule allows",
 }
 
 
@@ -508,6 +545,7 @@ def main():
     # the n = 1024 exp workload's mixed ladder is FP64 / 3xBF16 / TF32 / BF16 (no FP8 steps)
     c2 = dict(formats=C2_FORMATS)
     pols = {"ns_e": dataclasses.replace(mpps.NS_E, **c2),
+            "ns_e_mixp": dataclasses.replace(mpps.NS_E, mixed_powers=True, **c2),
             "paper_e": dataclasses.replace(mpps.PAPER_E, **c2), "fixed_e": mpps.FIXED_E,
             "ns": dataclasses.replace(mpps.NS, **c2), "paper": dataclasses.replace(mpps.PAPER, **c2),
             "fixed": mpps.FIXED}
@@ -591,6 +629,7 @@ def main():
                                              if prof[c][1] > 0 and prof[c][2] > 0 else None}
                                   for c in classes},
                       "formats": [R["fmt"][1:] for R in reps[p]],
+                      "pow_fmt": [R["pow_fmt"][2:] for R in reps[p]],
                       "policy": POLICY_DESC[p], "_prof": prof}
 
     # the same three evaluations on three streams (independent problems overlap; the device
@@ -729,6 +768,14 @@ def main():
             "fp64_pipe (ns / fixed)": (results["ns"]["evals_per_s"] / fixed_value)
             if "ns" in results else None},
         "mixed_within_2x_fixed_error": within2x,
+        # the mixed precision inside the powers (power tree, leaves in fewer slices): its
+        # measured gain over the same policy with every power in the working precision
+        "mixed_powers": ({"value": results["ns_e_mixp"]["evals_per_s"],
+                          "gain_over_ns_e": results["ns_e_mixp"]["evals_per_s"] /
+                          results["ns_e"]["evals_per_s"],
+                          "leaf_formats": results["ns_e_mixp"].get("pow_fmt"),
+                          "rel_err_1norm_sampled": results["ns_e_mixp"].get("rel_err_1norm_sampled")}
+                         if "ns_e_mixp" in results and "ns_e" in results else None),
         "policies": results,
         "concurrent_streams": conc,
         "roofline": roofline,

@@ -110,6 +110,15 @@ typedef struct {
                                MPPS_ECHECK is reported (at once, or by the next call that finds
                                the error word).  0: sigma is read back early in the call (the
                                GPU does not wait for it) and exactly max sigma steps run */
+    int mixed_powers;       /* 1 (mixed modes, f64_slices = k > 0, host plan, fixed s >= 4):
+                               the powers are formed as a tree: X^2..X^h by X^j = X^(j-1) X
+                               (h = ceil(s/2)), Y = X^h X^(s-h), and the leaves X^(h+t) =
+                               X^h X^t (t = 1..s-h-1), which feed only the block sums, each as
+                               F64E(k') with k' <= k slices chosen by mpps_plan_powers (the
+                               mixed precision inside the powers that Section 5 asks for).
+                               0, or with device_plan, variable_s, the tape entries, a fixed
+                               mode or s < 4: X_j = X_(j-1) X, every power in the working
+                               precision */
 } mpps_policy;
 
 /* Per-matrix description of what a call did (filled when `rep` is non-NULL). */
@@ -124,11 +133,13 @@ typedef struct {
     double normX;                    /* ||X||_1 (after scaling, for expm) */
     int gemms[MPPS_NUM_FORMATS + 1]; /* products per format; [MPPS_NUM_FORMATS] = squarings */
     double cost_ratio;               /* eq. (3.8) with the digits of the chosen formats */
+    int pow_fmt[MPPS_MAX_S + 1];     /* pow_fmt[j]: format of the product that formed X^j,
+                                        j = 2..s (MPPS_FMT_NONE for j < 2 and past s) */
 } mpps_report;
 
 /* Fill *p with the defaults: MIXED_NS, tol 2^-53, delta 10, s 0, all formats, floor 2,
  * f64_slices 0 (working-precision products on the FP64 pipe), variable_s 0,
- * adjoint_recompute 0, device_plan 0, max_squarings 0. */
+ * adjoint_recompute 0, device_plan 0, max_squarings 0, mixed_powers 0. */
 void mpps_policy_default(mpps_policy* p);
 
 /*
@@ -155,6 +166,31 @@ int mpps_choose_s(int m, double normX, const double* normB0, const double* normY
  */
 mpps_status mpps_plan(int m, int n, const double* normB, double normY, const mpps_policy* policy,
                       mpps_report* out);
+
+/*
+ * Host-only rule for the leaves of the power tree of policy.mixed_powers (no GPU work).
+ * With h = ceil(s/2) the leaves are X^j, j = h+1..s-1, formed as X^h X^(j-h); they feed only
+ * the block sums B_i = sum_j b_{si+j} X^j, so a leaf's error dX^j reaches p(X) through
+ * sum_i |b_{si+j}| ||Y||^i ||dX^j||, and an emulated product with k' slices errs by about
+ * u_F64E(k') ||X^h|| ||X^(j-h)||.  In the manner of eq. (2.8), with the norms of the chain
+ * powers (the leaves not yet formed) and the L leaves sharing the budget:
+ *   u_j = ||B_0||_low tol / (L ||X^h|| ||X^(j-h)|| sum_{i >= 0, si+j <= m} |b_{si+j}| ||Y||^i),
+ *   ||B_0||_low = max(0, ||B_0||_partial - sum_j |b_j| ||X^h|| ||X^(j-h)||),
+ * and leaf j takes the fewest slices k' (4 <= k' <= f64_slices) with u_F64E(k') <= u_j
+ * (u_F64E(k') = 2^(2-7k') for k' <= 8, 2^-55 for k' = 9).
+ *   coeffs   : b_0..b_m.
+ *   normXpow : s values ||X^1||_1..||X^s||_1 (the leaves' entries are not read).
+ *   normBpart: r+1 values ||B_i||_1 (r = floor(m/s)) of the blocks without their leaf terms.
+ *   fmt_out  : s+1 entries: MPPS_FMT_F64E(k') for the leaves, MPPS_FMT_F64E(f64_slices) for
+ *              X^2..X^h and Y, MPPS_FMT_NONE for j < 2.
+ *   normB_out: r+1 values for the block rule (mpps_plan): ||B_0||_low, and for i >= 1 the
+ *              partial norm plus the bound of the block's leaf terms (upper bounds).
+ * Returns MPPS_EINVAL for bad sizes or NULL pointers, MPPS_ENOTSUP when the policy forms
+ * no tree (mixed_powers 0, a fixed mode, f64_slices 0, or s < 4).
+ */
+mpps_status mpps_plan_powers(int m, int s, const double* coeffs, const double* normXpow,
+                             const double* normBpart, const mpps_policy* policy, int* fmt_out,
+                             double* normB_out);
 
 /*
  * p_m(A) for a batch of matrices (Algorithm 2.1 / Algorithm 4.1).

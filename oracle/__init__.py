@@ -475,6 +475,53 @@ def plan(m: int, n: int, norms, normY: float, mode: int = MODE_PAPER, tol: float
     return dict(s=s, r=r, nu=nu, u=u, fmt=fmt, fold=fold)
 
 
+def plan_powers(m: int, s: int, coefs, normXpow, normBpart, f64_slices: int,
+                tol: float = 2.0 ** -53):
+    """Slices of the leaves of the power tree (mixed precision inside the powers, the future
+    work of Section 5), stated in the manner of eq. (2.8).
+
+    1. h = ceil(s/2); X^2..X^h come from the chain, Y = X^h X^(s-h), and the leaves
+       X^j = X^h X^(j-h), j = h+1..s-1 (L = s-h-1 of them), feed only the blocks
+       B_i = sum_j b_{si+j} X^j (i = 0..r, r = floor(m/s), si+j <= m).
+    2. A leaf's size is bounded by bx_j = ||X^h|| ||X^(j-h)||; its terms add at most
+       e_i = sum_j |b_{si+j}| bx_j to ||B_i||: the block rule gets
+       ||B_0||_low = max(0, ||B_0||_partial - e_0) and ||B_i||_partial + e_i (i >= 1).
+    3. With S_j = sum_{i: si+j <= m} |b_{si+j}| ||Y||^i (y^i by repeated multiplication),
+       u_j = ||B_0||_low tol / (L bx_j S_j) (+inf when the denominator is 0).
+    4. Leaf j takes F64E(k) for the smallest k in 4..f64_slices-1 with 2^(2-7k) <= u_j (2^-55
+       for k = 9), else the working precision F64E(f64_slices).
+    Returns (fmt list over j = 0..s: None for j < 2, the format of X^j otherwise; normB list).
+    """
+    r = m // s
+    h = (s + 1) // 2
+    L = s - h - 1
+    wp = FMT_F64E(f64_slices)
+    bx = {j: float(normXpow[h - 1]) * float(normXpow[j - h - 1]) for j in range(h + 1, s)}
+    e = [0.0] * (r + 1)
+    for j in range(h + 1, s):
+        for i in range(r + 1):
+            if s * i + j <= m:
+                e[i] += abs(float(coefs[s * i + j])) * bx[j]
+    nb = [max(0.0, float(normBpart[0]) - e[0])] + [float(normBpart[i]) + e[i]
+                                                     for i in range(1, r + 1)]
+    y = float(normXpow[s - 1])
+    fmt = [None, None] + [wp] * (s - 1)
+    for j in range(h + 1, s):
+        S, yi = 0.0, 1.0
+        for i in range(r + 1):
+            if s * i + j > m:
+                break
+            S += abs(float(coefs[s * i + j])) * yi
+            yi = yi * y
+        den = L * bx[j] * S
+        uj = math.inf if den == 0.0 else nb[0] * tol / den
+        for k in range(4, f64_slices):
+            if (2.0 ** (2 - 7 * k) if k <= 8 else 2.0 ** -55) <= uj:
+                fmt[j] = FMT_F64E(k)
+                break
+    return fmt, nb
+
+
 def cost_ratio(s: int, r: int, digits_wp: float, d):
     """Eq. (3.8) read as a ratio of digit-weighted product counts:
     C_r = ((s-1) D + sum_i d_i) / ((s+r-1) D), D = digits of the working precision.

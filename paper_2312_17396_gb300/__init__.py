@@ -61,7 +61,7 @@ class _Policy(ctypes.Structure):
                 ("s", ctypes.c_int), ("formats", ctypes.c_uint), ("fp64_floor_steps", ctypes.c_int),
                 ("f64_slices", ctypes.c_int), ("variable_s", ctypes.c_int),
                 ("adjoint_recompute", ctypes.c_int), ("device_plan", ctypes.c_int),
-                ("max_squarings", ctypes.c_int)]
+                ("max_squarings", ctypes.c_int), ("mixed_powers", ctypes.c_int)]
 
 
 class _GroupItem(ctypes.Structure):
@@ -80,7 +80,7 @@ class _Report(ctypes.Structure):
                 ("fmt", ctypes.c_int * (MAX_R + 1)), ("u", ctypes.c_double * (MAX_R + 1)),
                 ("normB", ctypes.c_double * (MAX_R + 1)), ("normY", ctypes.c_double),
                 ("normX", ctypes.c_double), ("gemms", ctypes.c_int * (NUM_FORMATS + 1)),
-                ("cost_ratio", ctypes.c_double)]
+                ("cost_ratio", ctypes.c_double), ("pow_fmt", ctypes.c_int * (MAX_S + 1))]
 
 
 EXPORTS = ("mpps_policy_default", "mpps_plan", "ps_eval", "expm_taylor_ss", "ps_eval_adjoint",
@@ -90,7 +90,7 @@ EXPORTS = ("mpps_policy_default", "mpps_plan", "ps_eval", "expm_taylor_ss", "ps_
            "expm_taylor_ss_adjoint", "mpps_choose_s", "mpps_autotune_enable",
            "mpps_autotune_clear", "mpps_autotune_entries", "expm_pade13", "mpps_plan_adjoint",
            "ps_eval_tape_bytes", "ps_eval_forward_tape", "ps_eval_adjoint_tape",
-           "ps_eval_adjoint_f32", "ps_eval_grouped", "lu_solve")
+           "ps_eval_adjoint_f32", "ps_eval_grouped", "lu_solve", "mpps_plan_powers")
 STORAGE_F64, STORAGE_F32 = 0, 1
 PROF_GEMM_F64, PROF_GEMM_TC, PROF_ELEMENTWISE, PROF_GEMM_F64E, PROF_SLICE = 0, 1, 2, 3, 4
 
@@ -133,6 +133,9 @@ def lib():
         L.expm_pade13.restype = ctypes.c_int
         L.lu_solve.argtypes = [vp, vp, ip, ip, ctypes.POINTER(_Policy), vp, vp]
         L.lu_solve.restype = ctypes.c_int
+        L.mpps_plan_powers.argtypes = [ip, ip, dp, dp, dp, ctypes.POINTER(_Policy),
+                                       ctypes.POINTER(ctypes.c_int), dp]
+        L.mpps_plan_powers.restype = ctypes.c_int
         L.mpps_autotune_enable.argtypes = [ctypes.c_int]
         L.mpps_autotune_enable.restype = None
         L.mpps_autotune_clear.argtypes = []
@@ -191,6 +194,7 @@ class Policy:
     adjoint_recompute: bool = False  # adjoints: keep ceil(sqrt(r)) iterates, recompute the rest
     device_plan: bool = False       # the precision rule on the GPU: no read-back of the norms
     max_squarings: int = 0          # expm with device_plan: squaring steps launched (0: read sigma)
+    mixed_powers: bool = False      # power tree with the leaves in fewer slices (mpps_plan_powers)
 
     def _c(self):
         fm = self.formats
@@ -202,7 +206,8 @@ class Policy:
         return _Policy(int(self.mode), float(self.tol), float(self.delta), int(self.s),
                        int(fm), int(self.fp64_floor_steps), int(self.f64_slices),
                        int(bool(self.variable_s)), int(bool(self.adjoint_recompute)),
-                       int(bool(self.device_plan)), int(self.max_squarings))
+                       int(bool(self.device_plan)), int(self.max_squarings),
+                       int(bool(self.mixed_powers)))
 
 
 FIXED = Policy(mode=FIXED_FP64)
@@ -222,7 +227,8 @@ def _report_dict(R: _Report) -> dict:
                 normB=[R.normB[i] for i in range(r + 1)], normY=R.normY, normX=R.normX,
                 gemms={FORMAT_NAMES[f]: R.gemms[f] for f in range(NUM_FORMATS)} |
                 {"squarings": R.gemms[NUM_FORMATS]},
-                cost_ratio=R.cost_ratio)
+                cost_ratio=R.cost_ratio,
+                pow_fmt=[FORMAT_NAMES.get(R.pow_fmt[j]) for j in range(R.s + 1)])
 
 
 def plan(m: int, n: int, normB, normY: float, policy: Policy | None = None) -> dict:
@@ -233,6 +239,24 @@ def plan(m: int, n: int, normB, normY: float, policy: Policy | None = None) -> d
     _check(lib().mpps_plan(int(m), int(n), nb.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                            float(normY), ctypes.byref(pol), ctypes.byref(R)))
     return _report_dict(R)
+
+
+def plan_powers(m: int, s: int, coeffs, normXpow, normBpart, policy: Policy | None = None):
+    """Host-only rule for the leaves of the power tree (mpps_plan_powers; no GPU needed):
+    returns (format names of X^0..X^s, the block norms handed to the block rule)."""
+    c = np.ascontiguousarray(coeffs, dtype=np.float64)
+    xp = np.ascontiguousarray(normXpow, dtype=np.float64)
+    nb = np.ascontiguousarray(normBpart, dtype=np.float64)
+    if c.size != m + 1 or xp.size != s or nb.size != m // s + 1:
+        raise ValueError("coeffs, normXpow and normBpart need m+1, s and m//s+1 values")
+    fmt = (ctypes.c_int * (s + 1))()
+    nbo = np.zeros(m // s + 1)
+    dp = ctypes.POINTER(ctypes.c_double)
+    pol = (policy or Policy())._c()
+    _check(lib().mpps_plan_powers(int(m), int(s), c.ctypes.data_as(dp), xp.ctypes.data_as(dp),
+                                  nb.ctypes.data_as(dp), ctypes.byref(pol), fmt,
+                                  nbo.ctypes.data_as(dp)))
+    return [FORMAT_NAMES.get(fmt[j]) for j in range(s + 1)], nbo
 
 
 def plan_adjoint(m: int, n: int, normB, normY: float, normX: float,

@@ -39,6 +39,7 @@ struct Pol {
     int recompute;  // adjoints: checkpoint the Horner iterates, recompute the rest
     int dplan;      // precision rule on the device
     int max_sq;     // expm, device plan: squaring steps launched (0: sigma read back)
+    int mixp;       // mixed-precision powers (power tree with cheaper leaves)
 };
 
 static Pol resolve(const mpps_policy* p) {
@@ -57,6 +58,7 @@ static Pol resolve(const mpps_policy* p) {
     r.recompute = p->adjoint_recompute != 0;
     r.dplan = p->device_plan != 0;
     r.max_sq = p->max_squarings > 0 ? p->max_squarings : 0;
+    r.mixp = p->mixed_powers != 0;
     return r;
 }
 
@@ -132,6 +134,50 @@ constexpr int kF64eMinRung = 4;
 // Planner for one matrix.  normB: r+1 norms ||B_0||..||B_r||; normY = ||X^s||.
 // div > 1 tightens every u_i of eq. (2.8) by that factor before nu and the formats are chosen
 // (the rule of the reverse pass, see plan_adjoint_divisor); div = 1 is the forward rule.
+// The leaves of the power tree (policy.mixed_powers): with h = ceil(s/2), X^2..X^h come from
+// the chain, Y = X^h X^(s-h), and X^j = X^h X^(j-h) for j = h+1..s-1 feed only the block sums.
+// A leaf's product error (about u_F64E(k) ||X^h|| ||X^(j-h)||) reaches p through
+// sum_i |b_{si+j}| ||Y||^i; with L leaves sharing eq. (2.8)'s budget ||B_0|| tol, leaf j takes
+// the fewest slices whose unit roundoff is at most
+//   u_j = ||B_0||_low tol / (L ||X^h|| ||X^(j-h)|| sum_{i: si+j <= m} |b_{si+j}| ||Y||^i).
+// The norms are those of the chain powers and of the blocks without their leaf terms
+// (normBpart); normB_out gets a lower bound of ||B_0|| and upper bounds of ||B_i||, i >= 1,
+// for the block rule.
+static bool forms_power_tree(const Pol& P, int s) {
+    return P.mixp && P.mode != MPPS_FIXED_FP64 && P.f64k > 0 && s >= 4;
+}
+
+static void plan_powers_core(int m, int s, const double* c, const double* nxp, const double* nbp,
+                             const Pol& P, int* fmt, double* nbo) {
+    const int r = m / s, h = (s + 1) / 2, L = s - h - 1;
+    const int wp = MPPS_FMT_F64E(P.f64k);
+    for (int j = 0; j <= s; ++j) fmt[j] = j < 2 ? MPPS_FMT_NONE : wp;
+    double extra[MPPS_MAX_R + 1];
+    for (int i = 0; i <= r; ++i) extra[i] = 0.0;
+    for (int j = h + 1; j < s; ++j) {
+        const double bx = nxp[h - 1] * nxp[j - h - 1];   // ||X^h|| ||X^(j-h)|| >= ||X^j||
+        for (int i = 0; i <= r && s * i + j <= m; ++i) extra[i] += fabs(c[s * i + j]) * bx;
+    }
+    nbo[0] = nbp[0] - extra[0] > 0.0 ? nbp[0] - extra[0] : 0.0;
+    for (int i = 1; i <= r; ++i) nbo[i] = nbp[i] + extra[i];
+    const double y = nxp[s - 1];
+    for (int j = h + 1; j < s; ++j) {
+        const double bx = nxp[h - 1] * nxp[j - h - 1];
+        double sum = 0.0, yi = 1.0;
+        for (int i = 0; i <= r && s * i + j <= m; ++i) {
+            sum += fabs(c[s * i + j]) * yi;
+            yi = yi * y;
+        }
+        const double den = (double)L * bx * sum;
+        const double uj = den == 0.0 ? (double)INFINITY : nbo[0] * P.tol / den;
+        for (int k = kF64eMinRung; k < P.f64k; ++k)
+            if (u_f64e(k) <= uj) {
+                fmt[j] = MPPS_FMT_F64E(k);
+                break;
+            }
+    }
+}
+
 static mpps_status plan_steps(int m, int n, const double* normB, double normY, const Pol& P,
                               double div, mpps_report* out);
 static mpps_status plan_one(int m, int n, const double* normB, double normY, const Pol& P,
@@ -157,6 +203,7 @@ static mpps_status plan_steps(int m, int n, const double* normB, double normY, c
                               double div, mpps_report* out) {
     memset(out, 0, sizeof(*out));
     for (int i = 0; i <= MPPS_MAX_R; ++i) out->fmt[i] = MPPS_FMT_NONE;
+    for (int j = 0; j <= MPPS_MAX_S; ++j) out->pow_fmt[j] = MPPS_FMT_NONE;
     if (m == 0) {
         out->s = 1; out->r = 0; out->nu = 1;
         out->normB[0] = normB ? normB[0] : 0.0;
@@ -696,25 +743,33 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
     // Device plan: the rule runs on the GPU (k_plan); not with variable s or a tape
     const bool dp = pol.dplan && !var_s && !keep;
     const int sq_steps = (dp && expm) ? pol.max_sq : 0;   // squarings launched blind (0: read)
+    // Mixed-precision powers (host plan, fixed s): the power tree of plan_powers_core, whose
+    // leaves X^(h+1)..X^(s-1) are formed after the norms, in the slices the rule allows
+    const bool mixp = forms_power_tree(pol, s) && !dp && !var_s && !keep;
+    const int h = (s + 1) / 2;
     const int s0 = s;
     const int s_cap = var_s ? std::min(std::min(m, MPPS_MAX_S), 2 * s0) : s;
     int r = m / s;
     bool fold = (m % s) == 0;
     int q = block_norms_count(m, s);   // largest at the smallest s
-    const int q_alloc = q;
+    // mixed powers with exp: ||X^2||..||X^h|| come out of the FP32 block-norm pass as well
+    const int ex_pn = (mixp && expm) ? block_norms_f32_power_norms(m, s) : 0;
+    const int q_alloc = q + ex_pn;
     size_t partial_elems = norm1_partial_elems(n, batch);
     for (int t = s0; t <= s_cap; ++t)
         partial_elems = std::max(partial_elems,
                                  std::max(block_norms_partial_elems(n, batch, m, t),
                                           block_norms_f32_partial_elems(n, batch, m, t)));
+    if (ex_pn > 0)
+        partial_elems = std::max(partial_elems, block_norms_f32_powers_partial_elems(n, batch, m, s));
     const long long pw_bs = (long long)s_cap * nn;
 
     // ---- phase-1 workspace (FP64 part, and slice planes when FP64 is emulated)
     const int K = pol.f64k;                      // slices of an emulated working-precision product
     Arena L;
-    double *d_coef, *pw, *Pb0, *Pb1, *partial, *norms, *d_anorm, *tmpT = nullptr;
-    int *d_sigma, *d_err, *d_bidx, *eA = nullptr, *eB = nullptr, *eY = nullptr;
-    __nv_bfloat16 *slA = nullptr, *slB = nullptr, *slY = nullptr;
+    double *d_coef, *pw, *Pb0, *Pb1, *partial, *norms, *d_anorm, *tmpT = nullptr, *d_pnorm = nullptr;
+    int *d_sigma, *d_err, *d_bidx, *eA = nullptr, *eB = nullptr, *eY = nullptr, *eT = nullptr;
+    __nv_bfloat16 *slA = nullptr, *slB = nullptr, *slY = nullptr, *slT = nullptr;
     char* split = nullptr;   // split-K scratch of the emulated products
     DevPlan* d_plan = nullptr;                      // device plan (dp)
     int *d_rfmt = nullptr, *d_rnu = nullptr, *d_sql = nullptr, *d_sqc = nullptr;
@@ -724,7 +779,8 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
     // (rows), Y (columns), Horner iterates P_0..P_r (rows).  Not with variable s.
     const bool pre = K > 0 && !var_s;
     int* mxbuf = nullptr;
-    const size_t mx_count = pre ? (size_t)(s + 1 + r + 1 + 1) * batch * n : 0;
+    // (mixed powers: also the columns of X^2..X^(s-h), the tree's B operands)
+    const size_t mx_count = pre ? (size_t)(s + 1 + r + 1 + 1 + (mixp ? s + 1 : 0)) * batch * n : 0;
     auto layout1 = [&](Arena& a) {
         d_coef = a.take<double>(m + 1);
         pw = keep ? keep->pw : a.take<double>((size_t)batch * pw_bs);
@@ -745,6 +801,11 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
             tmpT = a.take<double>((size_t)batch * nn);
             split = a.take<char>(f64e_split_bytes());
             if (pre) mxbuf = a.take<int>(mx_count);
+            if (mixp) {
+                slT = a.take<__nv_bfloat16>(f64e_plane_elems(n, batch, K));
+                eT = a.take<int>((size_t)batch * n);
+                d_pnorm = a.take<double>((size_t)batch * s);
+            }
         }
         if (dp) {
             d_plan = (DevPlan*)a.take<char>(sizeof(DevPlan));
@@ -771,6 +832,7 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
     auto mx_pow = [&](int j) { return mxbuf + (size_t)j * bn; };                // rows of X_j
     auto mx_iter = [&](int i) { return mxbuf + (size_t)(s + 1 + i) * bn; };     // rows of P_i
     int* mx_ycol = mxbuf ? mxbuf + (size_t)(s + 1 + r + 1) * bn : nullptr;
+    auto mx_colpow = [&](int j) { return mxbuf + (size_t)(s + 1 + r + 2 + j) * bn; };   // cols of X_j
     if ((rc = launch_fill(d_coef, coeffs, m + 1, st))) return rc;
     DevErr* derr = nullptr;
     if ((rc = dev_err_get(&derr))) return rc;
@@ -833,8 +895,41 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
         }
         return launch_gemm_f64(pw + (long long)(j - 2) * nn, pw_bs, pw, pw_bs, n, batch, ep, st);
     };
-    for (int j = 2; j <= s; ++j)
-        if ((rc = power(j))) return rc;
+    if (!mixp) {
+        for (int j = 2; j <= s; ++j)
+            if ((rc = power(j))) return rc;
+    } else {
+        // the power tree: X^2..X^h by the chain (rows recorded for the next product, columns of
+        // X^2..X^(s-h) for the tree's B operands), then Y = X^h X^(s-h); the leaf slots are
+        // zeroed, so that the norms below are those of the blocks without their leaf terms
+        for (int j = 2; j <= h; ++j) {
+            Epilogue ep = epilogue_plain(pw + (long long)(j - 1) * nn, pw_bs);
+            ep.rmax = mx_pow(j);
+            if (j <= s - h) ep.cmax = mx_colpow(j);
+            const double* Xa = pw + (long long)(j - 2) * nn;
+            rc = j > 2 ? launch_slice_rows_pre(Xa, pw_bs, n, batch, K, slA, eA, mx_pow(j - 1),
+                                               nullptr, st)
+                       : launch_slice_rows(Xa, pw_bs, n, batch, K, slA, eA, st);
+            if (!rc)
+                rc = launch_gemm_f64e(K, slA, K, eA, slB, K, eB, n, batch, batch, ep, d_err, st,
+                                      nullptr, split);
+            if (rc) return rc;
+        }
+        rc = launch_slice_rows_pre(pw + (long long)(h - 1) * nn, pw_bs, n, batch, K, slA, eA,
+                                   mx_pow(h), nullptr, st);
+        if (!rc)
+            rc = launch_slice_cols_pre(pw + (long long)(s - h - 1) * nn, pw_bs, n, batch, K, slT,
+                                       eT, mx_colpow(s - h), st);
+        if (!rc) {
+            Epilogue ep = epilogue_plain(pw + (long long)(s - 1) * nn, pw_bs);
+            ep.cmax = mx_ycol;
+            rc = launch_gemm_f64e(K, slA, K, eA, slT, K, eT, n, batch, batch, ep, d_err, st,
+                                  nullptr, split);
+        }
+        if (rc) return rc;
+        MPPS_CUDA_TRY(cudaMemset2DAsync(pw + (long long)h * nn, (size_t)pw_bs * sizeof(double), 0,
+                                        (size_t)(s - h - 1) * nn * sizeof(double), batch, st));
+    }
 
     // ---- variable s (Algorithm 3.1): while a matrix's rule asks for it (mpps_choose_s on
     // ||X||, and ||B_0||, ||Y|| for each s so far), s grows by one and X_s = X_{s-1} X_1 is
@@ -875,10 +970,20 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
     // ||X||_1 <= 1 after the scaling of exp: FP32 sums suffice for the precision rule
     // (the paper notes the norms are only needed to the right order of magnitude)
     if (expm)
-        rc = launch_block_norms_f32(pw, pw_bs, n, batch, s, m, coeffs, partial, norms, st);
+        rc = launch_block_norms_f32(pw, pw_bs, n, batch, s, m, coeffs, partial, norms, st,
+                                    ex_pn > 0);
     else
         rc = launch_block_norms(pw, pw_bs, n, batch, s, m, d_coef, partial, norms, st);
     if (rc) return rc;
+    // mixed powers: ||X^j||_1 of the chain powers X^2..X^h ([j-1][batch]; ||X|| and ||Y||
+    // come with the block norms), when the block-norm pass did not give them
+    for (int j = 2; mixp && ex_pn == 0 && j <= h; ++j)
+        if ((rc = launch_norm1(pw + (long long)(j - 1) * nn, pw_bs, n, batch, partial,
+                               d_pnorm + (size_t)(j - 1) * batch, st)))
+            return rc;
+    int powfmt[MPPS_MAX_S + 1];
+    for (int j = 0; j <= MPPS_MAX_S; ++j)
+        powfmt[j] = (j < 2 || j > s) ? MPPS_FMT_NONE : (K > 0 ? MPPS_FMT_F64E(K) : MPPS_FMT_FP64);
     std::vector<double> hn;
     std::vector<mpps_report> rp(batch);
     Pol pol_s = pol;
@@ -889,13 +994,44 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
     // device plan: the formats each step may take (fmt[i] is MPPS_FMT_DEVICE unless one)
     std::vector<std::vector<int>> cand(r + 1);
     if (!dp) {
-        hn.resize((size_t)batch * q);
+        hn.resize((size_t)batch * (q + ex_pn));
         MPPS_CUDA_TRY(cudaMemcpyAsync(hn.data(), norms, sizeof(double) * hn.size(),
                                       cudaMemcpyDeviceToHost, st));
+        std::vector<double> hpn(mixp ? (size_t)batch * s : 0);
+        if (mixp && ex_pn == 0)
+            MPPS_CUDA_TRY(cudaMemcpyAsync(hpn.data(), d_pnorm, sizeof(double) * hpn.size(),
+                                          cudaMemcpyDeviceToHost, st));
         if (expm)
             MPPS_CUDA_TRY(cudaMemcpyAsync(sigma.data(), d_sigma, sizeof(int) * batch,
                                           cudaMemcpyDeviceToHost, st));
         MPPS_CUDA_TRY(cudaStreamSynchronize(st));
+        if (ex_pn > 0) {   // the power norms follow each matrix's q block norms: move them out
+            const size_t qx = (size_t)q + ex_pn;
+            for (int b = 0; b < batch; ++b)
+                for (int e = 0; e < ex_pn; ++e)
+                    hpn[(size_t)(e + 1) * batch + b] = hn[(size_t)b * qx + q + e];
+            for (int b = 0; b < batch; ++b)   // compact to stride q (destinations never pass sources)
+                for (int i = 0; i < q; ++i) hn[(size_t)b * q + i] = hn[(size_t)b * qx + i];
+            hn.resize((size_t)batch * q);
+        }
+        // mixed powers: each leaf in the most precise format any matrix asks for; the block
+        // norms become the bounds the leaf rule derives (lower for B_0, upper for the rest)
+        if (mixp) {
+            for (int j = h + 1; j < s; ++j) powfmt[j] = MPPS_FMT_NONE;
+            for (int b = 0; b < batch; ++b) {
+                int pf[MPPS_MAX_S + 1];
+                double nbo[MPPS_MAX_R + 1], xp[MPPS_MAX_S];
+                for (int j = 1; j <= s; ++j)
+                    xp[j - 1] = j == 1 ? hn[(size_t)b * q + r + 2]
+                                       : j == s ? hn[(size_t)b * q + r + 1]
+                                                : j <= h ? hpn[(size_t)(j - 1) * batch + b] : 0.0;
+                plan_powers_core(m, s, coeffs, xp, &hn[(size_t)b * q], pol_s, pf, nbo);
+                for (int i = 0; i <= r; ++i) hn[(size_t)b * q + i] = nbo[i];
+                for (int j = h + 1; j < s; ++j)
+                    if (powfmt[j] == MPPS_FMT_NONE || prec_rank(pf[j]) > prec_rank(powfmt[j]))
+                        powfmt[j] = pf[j];
+            }
+        }
 
         // ---- a4: plan per matrix; a batch runs each step in the most precise format any
         // of its matrices asks for
@@ -912,6 +1048,19 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
             fmt[i] = (fold && i == r) ? MPPS_FMT_NONE : f;
             if (MPPS_FMT_IS_F64E(fmt[i])) any_f64e = true;
             if (fmt[i] != MPPS_FMT_NONE) cand[i].assign(1, fmt[i]);
+        }
+        // mixed powers: the leaves X^(h+t) = X^h X^t, rows of X^h still in the A slices,
+        // columns of X (t = 1) in the B slices, of X^t (t >= 2) sliced from its recorded codes
+        for (int j = h + 1; mixp && j < s; ++j) {
+            const int t = j - h;
+            if (t >= 2 && (rc = launch_slice_cols_pre(pw + (long long)(t - 1) * nn, pw_bs, n, batch,
+                                                      K, slT, eT, mx_colpow(t), st)))
+                return rc;
+            Epilogue ep = epilogue_plain(pw + (long long)(j - 1) * nn, pw_bs);
+            if ((rc = launch_gemm_f64e(MPPS_F64E_SLICES(powfmt[j]), slA, K, eA, t >= 2 ? slT : slB,
+                                       K, t >= 2 ? eT : eB, n, batch, batch, ep, d_err, st,
+                                       nullptr, split)))
+                return rc;
         }
     } else {
         // ---- a4 on the device: the same rule (plan_core) per matrix, the batch's formats,
@@ -1290,6 +1439,7 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
         for (int b = 0; b < batch; ++b) {
             mpps_report& R = rp[b];
             for (int i = 1; i <= r; ++i) R.fmt[i] = fmt[i];
+            for (int j = 0; j <= MPPS_MAX_S; ++j) R.pow_fmt[j] = powfmt[j];
             for (int f = 0; f <= MPPS_NUM_FORMATS; ++f) R.gemms[f] = 0;
             R.gemms[MPPS_FMT_FP64] += s - 1;   // emulated working-precision products count as FP64
             for (int i = 1; i <= r; ++i) {
@@ -1475,6 +1625,30 @@ void mpps_policy_default(mpps_policy* p) {
     p->adjoint_recompute = 0;
     p->device_plan = 0;
     p->max_squarings = 0;
+    p->mixed_powers = 0;
+}
+
+mpps_status mpps_plan_powers(int m, int s, const double* coeffs, const double* normXpow,
+                             const double* normBpart, const mpps_policy* policy, int* fmt_out,
+                             double* normB_out) {
+    clear_error();
+    if (!coeffs || !normXpow || !normBpart || !fmt_out || !normB_out || m < 1 || s < 1 ||
+        s > m || s > MPPS_MAX_S || m / s > MPPS_MAX_R) {
+        set_error("mpps_plan_powers: invalid argument (m=%d, s=%d)", m, s);
+        return MPPS_EINVAL;
+    }
+    const Pol P = resolve(policy);
+    if (P.f64k < 0 || P.f64k > MPPS_F64E_MAX_SLICES) {
+        set_error("f64_slices=%d outside 0..%d", P.f64k, MPPS_F64E_MAX_SLICES);
+        return MPPS_EINVAL;
+    }
+    if (!forms_power_tree(P, s)) {
+        set_error("mpps_plan_powers: the policy forms no power tree (mixed_powers %d, mode %d, "
+                  "f64_slices %d, s %d)", P.mixp, P.mode, P.f64k, s);
+        return MPPS_ENOTSUP;
+    }
+    plan_powers_core(m, s, coeffs, normXpow, normBpart, P, fmt_out, normB_out);
+    return MPPS_OK;
 }
 
 mpps_status mpps_release_workspace(void) {

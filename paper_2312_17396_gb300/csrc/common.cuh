@@ -442,7 +442,12 @@ mpps_status launch_block_norms(const double* pw, long long pw_bs, int n, int bat
 size_t block_norms_f32_partial_elems(int n, int batch, int m, int s);
 mpps_status launch_block_norms_f32(const double* pw, long long pw_bs, int n, int batch, int s,
                                    int m, const double* coeffs, double* partial, double* norms,
-                                   cudaStream_t st);
+                                   cudaStream_t st, bool power_norms = false);
+// power_norms: ||X_2||_1..||X_{h}||_1 (h = ceil(s/2)) follow the r + 3 usual outputs of each
+// matrix (the chain powers of the power tree), block_norms_f32_power_norms(m, s) of them (0:
+// not available for this m, s); partial then needs block_norms_f32_powers_partial_elems.
+int block_norms_f32_power_norms(int m, int s);
+size_t block_norms_f32_powers_partial_elems(int n, int batch, int m, int s);
 // ||M||_1 per matrix (partial: norm1_partial_elems doubles).
 size_t norm1_partial_elems(int n, int batch);
 mpps_status launch_norm1(const double* M, long long bs, int n, int batch, double* partial,

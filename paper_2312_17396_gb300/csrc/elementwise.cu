@@ -191,7 +191,7 @@ __global__ void k_block_norms_partial_f32(const double* __restrict__ pw, long lo
 // The same sums with compile-time bounds (s <= 8, r <= 8, the exp degrees up to 72):
 // the power values and the block accumulators stay in registers.
 constexpr int kRegS = 8, kRegR = 8;
-template <int S>
+template <int S, int EX>
 __global__ void __launch_bounds__(256) k_block_norms_partial_f32_reg(const double* __restrict__ pw,
                                                                      long long pw_bs, int n, int m,
                                                                      NormCoefs cf,
@@ -199,16 +199,18 @@ __global__ void __launch_bounds__(256) k_block_norms_partial_f32_reg(const doubl
     pdl_wait();
     // 2-D blocks as in k_colsum_partial: 32 columns x 8 row slots over a 64-row chunk, the slot
     // sums added in slot order.  S (the block size s) is a compile-time constant: the r full
-    // blocks take S FMAs each without predicates, the last block its top + 1.
-    __shared__ float red[kNormSlots][kRegR + 3][kNormCols];
+    // blocks take S FMAs each without predicates, the last block its top + 1.  EX > 0 adds the
+    // column sums of |X_2|..|X_{EX+1}| as outputs r + 3 .. r + 2 + EX.
+    constexpr int NA = kRegR + 3 + EX;
+    __shared__ float red[kNormSlots][NA][kNormCols];
     const int lane = threadIdx.x & 31, slot = threadIdx.x >> 5;
     const int col = blockIdx.x * kNormCols + lane;
     const int chunk = blockIdx.y, chunks = gridDim.y, b = blockIdx.z;
-    const int r = m / S, q = r + 3, top = m - S * r;
-    float acc[kRegR + 3];
+    const int r = m / S, q = r + 3 + EX, top = m - S * r;
+    float acc[NA];
     float x[S + 1];
 #pragma unroll
-    for (int t = 0; t < kRegR + 3; ++t) acc[t] = 0.f;
+    for (int t = 0; t < NA; ++t) acc[t] = 0.f;
     if (col < n) {
         const long long nn = (long long)n * n;
         const double* base = pw + (long long)b * pw_bs + col;
@@ -245,15 +247,18 @@ __global__ void __launch_bounds__(256) k_block_norms_partial_f32_reg(const doubl
                 acc[kRegR] += fabsf(v);
                 acc[kRegR + 1] += fabsf(x[S]);
                 acc[kRegR + 2] += fabsf(x[1]);
+#pragma unroll
+                for (int e = 0; e < EX; ++e) acc[kRegR + 3 + e] += fabsf(x[2 + e]);
             }
         }
     }
 #pragma unroll
-    for (int t = 0; t < kRegR + 3; ++t) red[slot][t][lane] = acc[t];
+    for (int t = 0; t < NA; ++t) red[slot][t][lane] = acc[t];
     __syncthreads();
     for (int idx = threadIdx.x; idx < q * kNormCols; idx += blockDim.x) {
         const int t = idx / kNormCols, l = idx % kNormCols, c = blockIdx.x * kNormCols + l;
-        // accumulator of output t: B_0..B_{r-1}, then B_r, |X_s|, |X_1| in the last three
+        // accumulator of output t: B_0..B_{r-1}, then B_r, |X_s|, |X_1| in the next three, then
+        // the EX extra powers
         const int ti = t < r ? t : kRegR + (t - r);
         if (c >= n) continue;
         float sum = red[0][ti][l];
@@ -264,7 +269,7 @@ __global__ void __launch_bounds__(256) k_block_norms_partial_f32_reg(const doubl
 }
 
 struct BlockScales {
-    double c[MPPS_MAX_R + 3];
+    double c[MPPS_MAX_R + 3 + 4];
 };
 
 // One thread per column (chunks summed in order), block max, then an order-independent
@@ -653,11 +658,25 @@ size_t block_norms_f32_partial_elems(int n, int batch, int m, int s) {
     return (size_t)batch * ((n + kRowsF32 - 1) / kRowsF32) * block_norms_count(m, s) * n;
 }
 
+int block_norms_f32_power_norms(int m, int s) {
+    return (s >= 4 && s <= kRegS && m / s <= kRegR) ? (s + 1) / 2 - 1 : 0;
+}
+
+size_t block_norms_f32_powers_partial_elems(int n, int batch, int m, int s) {
+    return (size_t)batch * ((n + kChunkRows - 1) / kChunkRows) *
+           (block_norms_count(m, s) + block_norms_f32_power_norms(m, s)) * n;
+}
+
 mpps_status launch_block_norms_f32(const double* pw, long long pw_bs, int n, int batch, int s,
                                    int m, const double* coeffs, double* partial, double* norms,
-                                   cudaStream_t st) {
+                                   cudaStream_t st, bool power_norms) {
     ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
-    const int r = m / s, q = block_norms_count(m, s);
+    const int ex = power_norms ? block_norms_f32_power_norms(m, s) : 0;
+    if (power_norms && ex == 0) {
+        set_error("block norms: no power norms for m=%d, s=%d", m, s);
+        return MPPS_EINVAL;
+    }
+    const int r = m / s, q = block_norms_count(m, s) + ex;
     NormCoefs cf;
     BlockScales sc;
     for (int i = 0; i <= r; ++i) {
@@ -670,6 +689,7 @@ mpps_status launch_block_norms_f32(const double* pw, long long pw_bs, int n, int
     }
     sc.c[r + 1] = 1.0;
     sc.c[r + 2] = 1.0;
+    for (int e = 0; e < ex; ++e) sc.c[r + 3 + e] = 1.0;
     const bool reg = s <= kRegS && m / s <= kRegR;
     const int chunks = reg ? (n + kChunkRows - 1) / kChunkRows : (n + kRowsF32 - 1) / kRowsF32;
     MPPS_CUDA_TRY(cudaMemsetAsync(norms, 0, sizeof(double) * (size_t)batch * q, st));
@@ -678,7 +698,10 @@ mpps_status launch_block_norms_f32(const double* pw, long long pw_bs, int n, int
         switch (s) {
 #define MPPS_BN_CASE(S)                                                                            \
             case S:                                                                                \
-                MPPS_CUDA_TRY(launch_pdl(k_block_norms_partial_f32_reg<S>, g2, dim3(256), 0, st, pw, pw_bs, n, m, cf, partial)); \
+                if (ex > 0)                                                                        \
+                    MPPS_CUDA_TRY(launch_pdl(k_block_norms_partial_f32_reg<S, (S >= 4 ? (S + 1) / 2 - 1 : 0)>, g2, dim3(256), 0, st, pw, pw_bs, n, m, cf, partial)); \
+                else                                                                               \
+                    MPPS_CUDA_TRY(launch_pdl(k_block_norms_partial_f32_reg<S, 0>, g2, dim3(256), 0, st, pw, pw_bs, n, m, cf, partial)); \
                 break;
             MPPS_BN_CASE(1) MPPS_BN_CASE(2) MPPS_BN_CASE(3) MPPS_BN_CASE(4)
             MPPS_BN_CASE(5) MPPS_BN_CASE(6) MPPS_BN_CASE(7) MPPS_BN_CASE(8)

@@ -4,6 +4,8 @@ statement of the rule (eq. (2.8), Algorithm 3.1 / 4.1, Section 4.1.1)."""
 import os
 import re
 
+import math
+
 import numpy as np
 import pytest
 
@@ -193,3 +195,93 @@ def test_adjoint_divisor_reading():
     assert oracle.adjoint_divisor(18, 9.0) == 18.0
     assert oracle.adjoint_divisor(18, 0.5) == 36.0
     assert oracle.adjoint_divisor(30, 0.0) == 30.0
+
+
+# ---- mixed-precision powers: the leaf rule of the power tree ------------------------------
+def _powers_case(rng):
+    m = int(rng.integers(12, 60))
+    s = oracle.ceil_sqrt(m)
+    r = m // s
+    coefs = [float(x) * (1.0 if rng.random() < 0.7 else -1.0)
+             for x in 10.0 ** -np.cumsum(rng.uniform(0.0, 1.5, size=m + 1))]
+    xp = [float(x) for x in 10.0 ** -np.cumsum(rng.uniform(0.0, 2.0, size=s))]
+    nbp = [float(x) for x in 10.0 ** rng.uniform(-3, 1, size=r + 1)]
+    if rng.random() < 0.1:
+        xp[int(rng.integers(0, s))] = 0.0
+    return m, s, coefs, xp, nbp
+
+
+@pytest.mark.parametrize("k", [8, 9])
+def test_plan_powers_matches_oracle_rule(mpps, k):
+    """mpps_plan_powers agrees bit for bit with the oracle's statement of the leaf rule."""
+    rng = np.random.default_rng(400 + k)
+    pol = mpps.Policy(mode=mpps.MIXED_NS, f64_slices=k, mixed_powers=True)
+    low = 0
+    for _ in range(400):
+        m, s, c, xp, nbp = _powers_case(rng)
+        if s < 4:
+            continue
+        fmt, nb = mpps.plan_powers(m, s, c, xp, nbp, pol)
+        ofmt, onb = oracle.plan_powers(m, s, c, xp, nbp, k)
+        assert fmt == [mpps.FORMAT_NAMES[mpps.FMT_NONE if f is None else f] for f in ofmt], (m, s)
+        assert list(nb) == onb
+        low += sum(f != f"f64e{k}" for f in fmt[2:])
+    assert low > 50          # the cases reach the cheaper rungs
+
+
+def test_plan_powers_rejects(mpps):
+    c, xp, nb = [1.0] * 17, [1.0] * 4, [1.0] * 5
+    for pol in (mpps.Policy(f64_slices=8), mpps.Policy(mode=mpps.FIXED_FP64, f64_slices=8,
+                                                       mixed_powers=True),
+                mpps.Policy(f64_slices=0, mixed_powers=True)):
+        with pytest.raises(mpps.MppsError) as e:
+            mpps.plan_powers(16, 4, c, xp, nb, pol)
+        assert e.value.status == 5
+    with pytest.raises(mpps.MppsError):   # s = 3: no leaf
+        mpps.plan_powers(9, 3, [1.0] * 10, [1.0] * 3, [1.0] * 4,
+                         mpps.Policy(f64_slices=8, mixed_powers=True))
+
+
+def test_plan_powers_bounds_hold_on_matrices():
+    """Pins of the leaf rule against the matrices themselves (exact powers, plain norms):
+    ||X^h|| ||X^(j-h)|| bounds ||X^j||, the norms handed to the block rule bound the true
+    ones (below for B_0, above for i >= 1), and every cheaper leaf keeps its share of the
+    budget: L ||X^h|| ||X^(j-h)|| S_j u_F64E(k_j) <= ||B_0||_low tol."""
+    rng = np.random.default_rng(77)
+    U = 2.0 ** -53
+    for trial in range(40):
+        n = 6
+        m = int(rng.integers(16, 40))
+        s = oracle.ceil_sqrt(m)
+        r = m // s
+        h = (s + 1) // 2
+        X = rng.standard_normal((n, n))
+        X *= float(10.0 ** rng.uniform(-1.5, 0)) / np.abs(X).sum(axis=0).max()
+        c = [1.0 / math.factorial(i) for i in range(m + 1)] if trial % 2 else \
+            [(-1) ** i * 0.5 ** i for i in range(m + 1)]
+        P = [np.eye(n)]
+        for _ in range(s):
+            P.append(P[-1] @ X)
+        n1 = lambda M: float(np.abs(M).sum(axis=0).max())
+        leaves = set(range(h + 1, s))
+        xp = [0.0 if j in leaves else n1(P[j]) for j in range(1, s + 1)]
+        def block(i, with_leaves):
+            B = np.zeros((n, n))
+            for j in range(s):
+                if s * i + j <= m and (with_leaves or j not in leaves):
+                    B += c[s * i + j] * P[j]
+            return B
+        nbp = [n1(block(i, False)) for i in range(r + 1)]
+        true = [n1(block(i, True)) for i in range(r + 1)]
+        fmt, nb = oracle.plan_powers(m, s, c, xp, nbp, 8)
+        for j in leaves:
+            assert n1(P[j]) <= xp[h - 1] * xp[j - h - 1] * (1 + 1e-12)
+        assert nb[0] <= true[0] * (1 + 1e-12)
+        assert all(nb[i] >= true[i] * (1 - 1e-12) for i in range(1, r + 1))
+        y = xp[s - 1]
+        for j in leaves:
+            k = fmt[j] - 16
+            if k == 8:
+                continue
+            S = sum(abs(c[s * i + j]) * y ** i for i in range(r + 1) if s * i + j <= m)
+            assert len(leaves) * xp[h - 1] * xp[j - h - 1] * S * 2.0 ** (2 - 7 * k) <= nb[0] * U * (1 + 1e-12)
