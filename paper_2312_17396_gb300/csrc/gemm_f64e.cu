@@ -738,30 +738,40 @@ struct TileMap {
 // owner's piece its last, so the owner waits only at the end of its own work, for pieces
 // that were computed first.  W of a whole tile sums at most FLUSH chunks, so split launches
 // are limited to K <= FLUSH x 512.  U = 0: whole tiles, blockIdx.x + i gridDim.x.
+// With dpw > 0 only the last, partial wave is split: every CTA first takes the whole tiles
+// blockIdx.x + i gridDim.x, i < dpw (all CTAs on neighbouring tiles at the same K offset,
+// so the slice planes they read stay in L2), then its share [base + c U / G, ...) of the
+// tail's units.  A contributor's piece is then its first split segment, and an owner's piece
+// still its last segment.
 constexpr int kMinSplitSlices = 7;
 
 struct Split {
-    long long U;            // units; 0: no split
+    long long U;            // units split between the CTAs; 0: no split
     long long* partW;       // [G][EPI_WARPS][EPI_COLS][32]
     float* partT;           // [G][EPI_WARPS][EPI_COLS][32]
     unsigned* flags;        // [G][EPI_WARPS]
     unsigned epoch;         // this launch's flag value (never 0)
+    long long base;         // first split unit (dpw G nkb)
+    int dpw;                // waves of whole tiles before the split tail
 };
 
-__device__ __forceinline__ long long split_start(int c, long long U) {
-    return (long long)c * U / gridDim.x;
+__device__ __forceinline__ long long split_start(int c, const Split& sp) {
+    return sp.base + (long long)c * sp.U / gridDim.x;
 }
 
 template <bool SPLIT>
 struct Segments {
     long long u, ue;        // split: units left
     int id, total, nkb;     // whole tiles: next tile
+    int dpi, dpw;           // split: whole tiles taken so far, and their count
     __device__ Segments(const Split& sp, int total_, int nkb_) {
         total = total_;
         nkb = nkb_;
         id = blockIdx.x;
-        u = SPLIT ? split_start(blockIdx.x, sp.U) : 0;
-        ue = SPLIT ? split_start(blockIdx.x + 1, sp.U) : 0;
+        dpi = 0;
+        dpw = SPLIT ? sp.dpw : 0;
+        u = SPLIT ? split_start(blockIdx.x, sp) : 0;
+        ue = SPLIT ? split_start(blockIdx.x + 1, sp) : 0;
     }
     __device__ bool next(int& tile, int& kb0, int& kb1) {
         if (!SPLIT) {
@@ -770,6 +780,13 @@ struct Segments {
             kb0 = 0;
             kb1 = nkb;
             id += gridDim.x;
+            return true;
+        }
+        if (dpi < dpw) {
+            tile = (int)blockIdx.x + dpi * (int)gridDim.x;
+            kb0 = 0;
+            kb1 = nkb;
+            ++dpi;
             return true;
         }
         if (u >= ue) return false;
@@ -899,7 +916,11 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int nbat = ep.dcount ? min(__ldg(ep.dcount), batch) : batch;
     const int total = tm.per_mat * nbat;
     Split spl = sp;
-    if (ep.dcount && sp.U) spl.U = (long long)total * nkb;
+    if (ep.dcount && sp.U) {   // the device plan's count: the whole range split
+        spl.U = (long long)total * nkb;
+        spl.base = 0;
+        spl.dpw = 0;
+    }
 
     if (warp == EPI_WARPS) {
         if (lane == 0) {   // TMA producer
@@ -1080,7 +1101,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
             if (kb1 < nkb) {   // the owner of a split tile adds the later pieces, in CTA order
                 const long long tend = (long long)(id + 1) * nkb;
-                for (int c2 = blockIdx.x + 1; c2 < (int)gridDim.x && split_start(c2, spl.U) < tend; ++c2) {
+                for (int c2 = blockIdx.x + 1; c2 < (int)gridDim.x && split_start(c2, spl) < tend; ++c2) {
+                    if (split_start(c2 + 1, spl) == split_start(c2, spl)) continue;   // no units: no piece
                     const unsigned* f = sp.flags + (size_t)c2 * EPI_WARPS + warp;
                     bool got = true;
                     if (lane == 0) got = flag_wait(f, sp.epoch, err);
@@ -1509,10 +1531,13 @@ mpps_status launch_gemm_f64e(int k, const void* slicesA, int ksA, const int* eA,
     const bool can_split = split && k >= kMinSplitSlices &&
                            (nkb + KCHUNK / KB - 1) / (KCHUNK / KB) <= FLUSH && tiles * nkb / G >= 16;
     const int tuned = can_split ? tune_lookup(TUNE_F64E_SPLIT, n, batch, k) : -1;
-    const bool rule = can_split && waves >= 2 && (waves * G - tiles) * 10 >= waves * G;
+    // (the split tail: the tiles past the last full wave, at least 16 K blocks per CTA)
+    const long long dpw_rule = tiles / G - (tiles % G == 0 ? 1 : 0);
+    const bool rule = can_split && waves >= 2 && (waves * G - tiles) * 10 >= waves * G &&
+                      (tiles - dpw_rule * G) * nkb >= 16LL * G;
     const int grid_tiles = grid;
     auto run = [&](bool use_split) -> mpps_status {
-        Split sp{0, nullptr, nullptr, nullptr, 0u};
+        Split sp{0, nullptr, nullptr, nullptr, 0u, 0, 0};
         int g = grid_tiles;
         if (use_split) {
             static std::atomic<unsigned> epoch{0};
@@ -1520,7 +1545,11 @@ mpps_status launch_gemm_f64e(int k, const void* slicesA, int ksA, const int* eA,
             if (e == 0u) e = epoch.fetch_add(1u) + 1u;
             char* base = (char*)split;
             const size_t nslot = (size_t)G * EPI_WARPS * EPI_COLS * 32;
-            sp.U = tiles * nkb;
+            // whole tiles for the full waves, the partial last wave split
+            sp.dpw = (int)(tiles / G);
+            if (sp.dpw * (long long)G == tiles) sp.dpw -= 1;   // (a full last wave: split it)
+            sp.base = (long long)sp.dpw * G * nkb;
+            sp.U = (tiles - (long long)sp.dpw * G) * nkb;
             sp.flags = (unsigned*)base;
             sp.partW = (long long*)(base + f64e_split_flag_bytes());
             sp.partT = (float*)(sp.partW + nslot);
@@ -1582,7 +1611,7 @@ mpps_status launch_gemm_f64e_grid(int k, const void* slicesA, const int* eA, int
     const int grid = (int)(tiles < G ? tiles : G);
     const int pairs = k <= 8 ? k * (k + 1) / 2 : 43;
     ProfScope prof(MPPS_PROF_GEMM_F64E, st, 2.0 * n * (double)n * n * (double)batch * pairs);
-    const Split sp{0, nullptr, nullptr, nullptr, 0u};
+    const Split sp{0, nullptr, nullptr, nullptr, 0u, 0, 0};
     const int nb = (int)batch;
     switch (k) {
         case 1: return launch_k<1, true>(dev, grid, ta, tb, n, kpA, kp, nb, eA, eB, ep, d_err, st, nullptr, sp);
