@@ -357,12 +357,15 @@ mpps_status launch_slice_cols(const double* M, long long bs, int n, int batch, i
 // The same two with the row / column maxima of |M| already known (recorded by the epilogue
 // of the emulated product that wrote M, Epilogue::rmax / cmax): no reduction pass.  The row
 // variant also zeroes rmax_clear ([batch][n], may be null) for the next product to fill.
+// list (device, optional): grid slice z slices matrix list[z] (batch = the listed count),
+// as the products' bidx: the squarings slice only the matrices they square.
 mpps_status launch_slice_rows_pre(const double* M, long long bs, int n, int batch, int k,
                                   void* planes, int* exps, const int* rmax, int* rmax_clear,
-                                  cudaStream_t st, const int* gate = nullptr);
+                                  cudaStream_t st, const int* gate = nullptr,
+                                  const int* list = nullptr);
 mpps_status launch_slice_cols_pre(const double* M, long long bs, int n, int batch, int k,
                                   void* planes, int* exps, const int* cmax, cudaStream_t st,
-                                  const int* gate = nullptr);
+                                  const int* gate = nullptr, const int* list = nullptr);
 // Scratch that lets the emulated product split the K range of output tiles between CTAs
 // (f64e_split_bytes() bytes, 256-byte aligned; its first f64e_split_flag_bytes() bytes
 // zeroed by the caller before the first product that uses it, on the same stream).  Without

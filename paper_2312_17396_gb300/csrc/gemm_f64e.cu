@@ -369,11 +369,11 @@ __global__ void __launch_bounds__(256) k_slice_rows_pre(const double* __restrict
                                                         __nv_bfloat16* __restrict__ planes,
                                                         long long plane_bs, int lld,
                                                         int* __restrict__ exps,
-        const int* __restrict__ gate) {
+        const int* __restrict__ gate, const int* __restrict__ bidx) {
     pdl_wait();
     if (gate && (int)blockIdx.z >= __ldg(gate)) return;   // device plan: not run
     pdl_trigger();
-    const int b = blockIdx.z;
+    const int b = bidx ? __ldg(bidx + blockIdx.z) : (int)blockIdx.z;   // listed matrices only
     const int n32 = (n + KB - 1) / KB * KB;
     const long long pstride = (long long)n * 2 * lld;
     int tpr = 1;   // threads per row: a power of two covering n32 / V columns, at most 256
@@ -543,12 +543,13 @@ __global__ void __launch_bounds__(256) k_slice_cols(const double* __restrict__ M
                                                     __nv_bfloat16* __restrict__ planes,
                                                     long long plane_bs, int lld,
                                                     int* __restrict__ exps,
-        const int* __restrict__ gate) {
+        const int* __restrict__ gate, const int* __restrict__ bidx) {
     pdl_wait();
     if (gate && (int)blockIdx.z >= __ldg(gate)) return;   // device plan: not run
     pdl_trigger();
     __shared__ double tile[32][65];
-    const int b = blockIdx.z, r0 = blockIdx.y * 64, c0 = blockIdx.x * 32;
+    const int b = bidx ? __ldg(bidx + blockIdx.z) : (int)blockIdx.z;   // listed matrices only
+    const int r0 = blockIdx.y * 64, c0 = blockIdx.x * 32;
     const double* src = M + (long long)b * bs;
     for (int i = threadIdx.y; i < 64; i += blockDim.y) {
         const int row = r0 + i, col = c0 + threadIdx.x;
@@ -743,7 +744,7 @@ struct TileMap {
 // so the slice planes they read stay in L2), then its share [base + c U / G, ...) of the
 // tail's units.  A contributor's piece is then its first split segment, and an owner's piece
 // still its last segment.
-constexpr int kMinSplitSlices = 7;
+constexpr int kMinSplitSlices = 4;   // the working precision and the leaves of the power tree
 
 struct Split {
     long long U;            // units split between the CTAs; 0: no split
@@ -1335,18 +1336,18 @@ mpps_status slice_rows_k(const double* M, long long bs, int n, int batch, __nv_b
 template <int KS>
 mpps_status slice_cols_k(const double* M, long long bs, int n, int batch, __nv_bfloat16* pl,
                          int* exps, unsigned long long* colmax, cudaStream_t st,
-                         const int* codes, const int* gate) {
+                         const int* codes, const int* gate, const int* list = nullptr) {
     const int lld = low_ld(n);
     if (codes) {
         MPPS_CUDA_TRY(launch_pdl(k_slice_cols<KS, true>, dim3(dim3((n + 31) / 32, (n + 63) / 64, batch)),
                                  dim3(dim3(32, 8)), 0, st, M, bs, n, digit_offset(KS),
                                  (const unsigned long long*)nullptr, codes, pl,
-                                 (long long)KS * n * lld, lld, exps, gate));
+                                 (long long)KS * n * lld, lld, exps, gate, list));
         MPPS_LAUNCH_CHECK();
         return MPPS_OK;
     }
     MPPS_CUDA_TRY(launch_pdl(k_slice_cols<KS, false>, dim3(dim3((n + 31) / 32, (n + 63) / 64, batch)), dim3(dim3(32, 8)), 0, st, M, bs, n, digit_offset(KS), (const unsigned long long*)colmax, (const int*)nullptr, pl, (long long)KS * n * lld, lld,
-        exps, gate));
+        exps, gate, (const int*)nullptr));
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }
@@ -1378,7 +1379,7 @@ namespace {
 template <int KS>
 mpps_status slice_rows_pre_k(const double* M, long long bs, int n, int batch, __nv_bfloat16* pl,
                              int* exps, const int* rmax, int* rclear, cudaStream_t st,
-                             const int* gate) {
+                             const int* gate, const int* list) {
     const int lld = low_ld(n);
     const long long goff = digit_offset(KS), pbs = (long long)num_pairs(KS) * n * 2 * lld;
     const int n32 = (n + KB - 1) / KB * KB;
@@ -1392,10 +1393,10 @@ mpps_status slice_rows_pre_k(const double* M, long long bs, int n, int batch, __
     };
     if (n % 4 == 0 && ((uintptr_t)M & 15) == 0 && bs % 2 == 0) {
         MPPS_CUDA_TRY(launch_pdl(k_slice_rows_pre<KS, 4>, grid_for(4), dim3(256), 0, st, M, bs, n,
-                                 goff, rmax, rclear, pl, pbs, lld, exps, gate));
+                                 goff, rmax, rclear, pl, pbs, lld, exps, gate, list));
     } else {
         MPPS_CUDA_TRY(launch_pdl(k_slice_rows_pre<KS, 1>, grid_for(1), dim3(256), 0, st, M, bs, n,
-                                 goff, rmax, rclear, pl, pbs, lld, exps, gate));
+                                 goff, rmax, rclear, pl, pbs, lld, exps, gate, list));
     }
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
@@ -1404,7 +1405,7 @@ mpps_status slice_rows_pre_k(const double* M, long long bs, int n, int batch, __
 
 mpps_status launch_slice_rows_pre(const double* M, long long bs, int n, int batch, int k,
                                   void* planes, int* exps, const int* rmax, int* rmax_clear,
-                                  cudaStream_t st, const int* gate) {
+                                  cudaStream_t st, const int* gate, const int* list) {
     k = f64e_planes(k);
     ProfScope prof(MPPS_PROF_SLICE, st);
     if (batch > 65535) {
@@ -1413,32 +1414,32 @@ mpps_status launch_slice_rows_pre(const double* M, long long bs, int n, int batc
     }
     __nv_bfloat16* pl = (__nv_bfloat16*)planes;
     switch (k) {
-        case 1: return slice_rows_pre_k<1>(M, bs, n, batch, pl, exps, rmax, rmax_clear, st, gate);
-        case 2: return slice_rows_pre_k<2>(M, bs, n, batch, pl, exps, rmax, rmax_clear, st, gate);
-        case 3: return slice_rows_pre_k<3>(M, bs, n, batch, pl, exps, rmax, rmax_clear, st, gate);
-        case 4: return slice_rows_pre_k<4>(M, bs, n, batch, pl, exps, rmax, rmax_clear, st, gate);
-        case 5: return slice_rows_pre_k<5>(M, bs, n, batch, pl, exps, rmax, rmax_clear, st, gate);
-        case 6: return slice_rows_pre_k<6>(M, bs, n, batch, pl, exps, rmax, rmax_clear, st, gate);
-        case 7: return slice_rows_pre_k<7>(M, bs, n, batch, pl, exps, rmax, rmax_clear, st, gate);
-        default: return slice_rows_pre_k<8>(M, bs, n, batch, pl, exps, rmax, rmax_clear, st, gate);
+        case 1: return slice_rows_pre_k<1>(M, bs, n, batch, pl, exps, rmax, rmax_clear, st, gate, list);
+        case 2: return slice_rows_pre_k<2>(M, bs, n, batch, pl, exps, rmax, rmax_clear, st, gate, list);
+        case 3: return slice_rows_pre_k<3>(M, bs, n, batch, pl, exps, rmax, rmax_clear, st, gate, list);
+        case 4: return slice_rows_pre_k<4>(M, bs, n, batch, pl, exps, rmax, rmax_clear, st, gate, list);
+        case 5: return slice_rows_pre_k<5>(M, bs, n, batch, pl, exps, rmax, rmax_clear, st, gate, list);
+        case 6: return slice_rows_pre_k<6>(M, bs, n, batch, pl, exps, rmax, rmax_clear, st, gate, list);
+        case 7: return slice_rows_pre_k<7>(M, bs, n, batch, pl, exps, rmax, rmax_clear, st, gate, list);
+        default: return slice_rows_pre_k<8>(M, bs, n, batch, pl, exps, rmax, rmax_clear, st, gate, list);
     }
 }
 
 mpps_status launch_slice_cols_pre(const double* M, long long bs, int n, int batch, int k,
                                   void* planes, int* exps, const int* cmax, cudaStream_t st,
-                                  const int* gate) {
+                                  const int* gate, const int* list) {
     k = f64e_planes(k);
     ProfScope prof(MPPS_PROF_SLICE, st);
     __nv_bfloat16* pl = (__nv_bfloat16*)planes;
     switch (k) {
-        case 1: return slice_cols_k<1>(M, bs, n, batch, pl, exps, nullptr, st, cmax, gate);
-        case 2: return slice_cols_k<2>(M, bs, n, batch, pl, exps, nullptr, st, cmax, gate);
-        case 3: return slice_cols_k<3>(M, bs, n, batch, pl, exps, nullptr, st, cmax, gate);
-        case 4: return slice_cols_k<4>(M, bs, n, batch, pl, exps, nullptr, st, cmax, gate);
-        case 5: return slice_cols_k<5>(M, bs, n, batch, pl, exps, nullptr, st, cmax, gate);
-        case 6: return slice_cols_k<6>(M, bs, n, batch, pl, exps, nullptr, st, cmax, gate);
-        case 7: return slice_cols_k<7>(M, bs, n, batch, pl, exps, nullptr, st, cmax, gate);
-        default: return slice_cols_k<8>(M, bs, n, batch, pl, exps, nullptr, st, cmax, gate);
+        case 1: return slice_cols_k<1>(M, bs, n, batch, pl, exps, nullptr, st, cmax, gate, list);
+        case 2: return slice_cols_k<2>(M, bs, n, batch, pl, exps, nullptr, st, cmax, gate, list);
+        case 3: return slice_cols_k<3>(M, bs, n, batch, pl, exps, nullptr, st, cmax, gate, list);
+        case 4: return slice_cols_k<4>(M, bs, n, batch, pl, exps, nullptr, st, cmax, gate, list);
+        case 5: return slice_cols_k<5>(M, bs, n, batch, pl, exps, nullptr, st, cmax, gate, list);
+        case 6: return slice_cols_k<6>(M, bs, n, batch, pl, exps, nullptr, st, cmax, gate, list);
+        case 7: return slice_cols_k<7>(M, bs, n, batch, pl, exps, nullptr, st, cmax, gate, list);
+        default: return slice_cols_k<8>(M, bs, n, batch, pl, exps, nullptr, st, cmax, gate, list);
     }
 }
 

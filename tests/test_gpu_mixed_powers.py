@@ -116,3 +116,34 @@ def test_mixed_powers_left_out_where_the_tree_is_not_formed(mpps):
     E0 = host(mpps.expm(dev(A), m=8, policy=mpps.NS_E))           # s = 3
     E1 = host(mpps.expm(dev(A), m=8, policy=dataclasses.replace(mpps.NS_E, mixed_powers=True)))
     assert np.array_equal(E1, E0)
+
+
+def test_expm_n1024_batched_step_vs_oracle(mpps):
+    """The benchmarked step: the three matrices (||A||_1 = 0.5, 4, 32; sigma 0, 2, 5) in one
+    batched call with mixed powers.  Each product has 384 tiles, so the full waves run whole
+    tiles and the last wave is split (F64E(8) and the leaves' F64E(6) and F64E(5)); the
+    squarings slice only the matrices of their lists.  Sampled columns against the oracle,
+    within 2x of the fixed-FP64 error, and the same result as three separate calls up to
+    the bound."""
+    n = 1024
+    A = np.stack([inputs.gaussian_matrix(n, seed=2 + k, norm1=nrm)
+                  for k, nrm in enumerate((0.5, 4.0, 32.0))])
+    pol = c2(mpps, mixed_powers=True)
+    Eb, rep = mpps.expm(dev(A), m=30, policy=pol, report=True)
+    Eb = host(Eb)
+    Ef = host(mpps.expm(dev(A), m=30, policy=mpps.FIXED))
+    cols = [0, 511, 1023]
+    for b in range(3):
+        assert rep[b]["pow_fmt"][4] != "f64e8" and rep[b]["pow_fmt"][5] != "f64e8"
+        sg = oracle.sigma_for(A[b])
+        V = np.zeros((n, len(cols)))
+        for t, j in enumerate(cols):
+            V[j, t] = 1.0
+        wh, wl = oracle.ps_apply_dd(oracle.taylor_exp_rational(30), np.ldexp(A[b], -sg), V,
+                                    reps=2 ** sg)
+        ref = np.abs(wh).sum(axis=0)
+        em = np.abs(Eb[b][:, cols] - wh - wl).sum(axis=0) / ref
+        ef = np.abs(Ef[b][:, cols] - wh - wl).sum(axis=0) / ref
+        assert np.all(em <= 2 * ef + FLOOR), (b, em, ef)
+        Es = host(mpps.expm(dev(A[b]), m=30, policy=pol))
+        assert np.abs(Es - Eb[b]).sum(axis=0).max() <= 100 * n * U * 2 ** sg * np.abs(Es).sum(axis=0).max()
