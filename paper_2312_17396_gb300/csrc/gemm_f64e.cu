@@ -744,7 +744,7 @@ struct TileMap {
 // so the slice planes they read stay in L2), then its share [base + c U / G, ...) of the
 // tail's units.  A contributor's piece is then its first split segment, and an owner's piece
 // still its last segment.
-constexpr int kMinSplitSlices = 4;   // the working precision and the leaves of the power tree
+constexpr int kMinSplitSlices = 7;
 
 struct Split {
     long long U;            // units split between the CTAs; 0: no split

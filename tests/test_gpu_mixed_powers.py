@@ -120,9 +120,9 @@ def test_mixed_powers_left_out_where_the_tree_is_not_formed(mpps):
 
 def test_expm_n1024_batched_step_vs_oracle(mpps):
     """The benchmarked step: the three matrices (||A||_1 = 0.5, 4, 32; sigma 0, 2, 5) in one
-    batched call with mixed powers.  Each product has 384 tiles, so the full waves run whole
-    tiles and the last wave is split (F64E(8) and the leaves' F64E(6) and F64E(5)); the
-    squarings slice only the matrices of their lists.  Sampled columns against the oracle,
+    batched call with mixed powers.  Each product has 384 tiles, so the F64E(8) products run
+    whole tiles in the full waves and split the last wave (the leaves' F64E(6) and F64E(5)
+    run whole tiles); the squarings slice only the matrices of their lists.  Sampled columns against the oracle,
     within 2x of the fixed-FP64 error, and the same result as three separate calls up to
     the bound."""
     n = 1024
