@@ -1048,7 +1048,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             const bool vec4 = ((uintptr_t)orow & 31) == 0;
             const bool head = !SPLIT || kb0 == 0;   // this CTA owns the tile
             const bool pre = !GRID && ep_pre && head && row < n && cb + EPI_COLS <= n;
-            if (GRID && ep.add && row < n && cb < n)   // the addend's 16 entries: one line, early
+            if (ep.add && row < n && cb < n)   // the addend's 16 entries: one line, early
                 asm volatile("prefetch.global.L1 [%0];" ::"l"(ep.add + (long long)b * ep.add_bstride +
                                                               (long long)row * n + cb));
             if (pre) f64e_block_sum16(ep, b, row, cb, n, orow);
