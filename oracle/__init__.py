@@ -22,6 +22,10 @@ Contents
 * ``cost_ratio``: eq. (3.8).
 * ``lu_solve``: R = Q^-1 P by Gaussian elimination with partial pivoting (the q^-1 p solve of
   the Pade approximant, Section 4.1), unblocked, in plain double.
+* ``e4m3_round``, ``mx_block_exp``, ``mxfp8_quantize_rows``, ``matmul_mxfp8``: the FP8
+  Horner product with block scales (the low-precision products of eq. (2.6) in the 8-bit
+  format, each row of the left factor and each column of the right one split into blocks
+  of 32 along the inner dimension with one power-of-two scale per block), summed in FP64.
 """
 from __future__ import annotations
 
@@ -527,3 +531,79 @@ def cost_ratio(s: int, r: int, digits_wp: float, d):
     C_r = ((s-1) D + sum_i d_i) / ((s+r-1) D), D = digits of the working precision.
     (The printed formula writes log10 u for D; Table 1's column is 1 - C_r.)"""
     return ((s - 1) * digits_wp + sum(d)) / ((s + r - 1) * digits_wp)
+
+
+# ------------------------------------------------------------------------------------
+# FP8 (E4M3) products with one power-of-two scale per 32 inner-dimension entries
+# ------------------------------------------------------------------------------------
+E4M3_MAX = 448.0
+MX_BLOCK = 32
+
+
+def e4m3_round(x):
+    """Nearest E4M3 number to x, ties to the even fraction.  E4M3 is the 8-bit float with 4
+    exponent bits (bias 7) and 3 fraction bits: normal numbers 2^e (1 + f/8) for e in
+    [-6, 8], subnormals j 2^-9 (j < 8), largest finite 448.  Requires |x| <= 448.  The
+    spacing of the numbers around |x| is 2^(e-3) with e = max(floor(log2 |x|), -6)."""
+    x = np.asarray(x, dtype=np.float64)
+    a = np.abs(x)
+    if np.any(a > E4M3_MAX):
+        raise ValueError("e4m3_round: |x| > 448")
+    _, E = np.frexp(a)                      # a = f 2^E, f in [0.5, 1): floor(log2 a) = E - 1
+    e = np.maximum(E - 1, -6)
+    quantum = np.ldexp(1.0, e - 3)
+    q = np.round(a / quantum) * quantum     # a / quantum is exact; np.round ties to even
+    return np.copysign(q, x)
+
+
+def mx_block_exp(amax: float) -> int:
+    """Shared exponent X of one block with largest magnitude amax: the smallest integer with
+    amax 2^-X <= 448, so that the block's entries scaled by 2^-X fit E4M3 without clamping
+    (0 for an all-zero block), kept in the range [-127, 127] of the 8-bit scale code
+    X + 127."""
+    if amax == 0.0:
+        return 0
+    f, E = math.frexp(amax)                 # amax = f 2^E, f in [0.5, 1)
+    X = E - 9 if 512.0 * f <= E4M3_MAX else E - 8
+    return min(max(X, -127), 127)
+
+
+def mxfp8_quantize_rows(M):
+    """Each row of M: first its own power of two, 2^-e with e the frexp exponent of the row's
+    largest magnitude (rows then lie in (-1, 1); e = 0 for a zero row), then blocks of 32
+    consecutive entries, block j scaled by 2^-X_j (mx_block_exp of the block's largest
+    magnitude) and rounded to E4M3.  Returns (q, X, e): q the E4M3 values (n_rows x n_cols),
+    X the block exponents (n_rows x ceil(n_cols/32)), e the row exponents.  The row equals
+    2^e sum_j 2^X_j q_block_j up to the rounding."""
+    M = np.asarray(M, dtype=np.float64)
+    nr, nc = M.shape
+    nb = -(-nc // MX_BLOCK)
+    e = np.zeros(nr, dtype=np.int64)
+    X = np.zeros((nr, nb), dtype=np.int64)
+    q = np.zeros_like(M)
+    for i in range(nr):
+        rmax = float(np.max(np.abs(M[i]))) if nc else 0.0
+        e[i] = math.frexp(rmax)[1] if rmax > 0.0 else 0
+        v = np.ldexp(M[i], -int(e[i]))
+        for j in range(nb):
+            blk = v[j * MX_BLOCK:(j + 1) * MX_BLOCK]
+            X[i, j] = mx_block_exp(float(np.max(np.abs(blk))))
+            q[i, j * MX_BLOCK:(j + 1) * MX_BLOCK] = e4m3_round(np.ldexp(blk, -int(X[i, j])))
+    return q, X, e
+
+
+def _mx_dequantize(q, X, e):
+    scale = np.repeat(np.ldexp(1.0, X), MX_BLOCK, axis=1)[:, :q.shape[1]]
+    return np.ldexp(q * scale, e[:, None])
+
+
+def matmul_mxfp8(A, B):
+    """A B with the rows of A and the columns of B quantised by ``mxfp8_quantize_rows``: the
+    quantised factors are exact in FP64 and the inner products are summed in FP64.  Also
+    returns |A~| |B~| of the quantised factors (the scale of an FP32 accumulation error)."""
+    qa, xa, ea = mxfp8_quantize_rows(A)
+    qb, xb, eb = mxfp8_quantize_rows(np.asarray(B, dtype=np.float64).T)
+    Aq = _mx_dequantize(qa, xa, ea)
+    Bq = _mx_dequantize(qb, xb, eb).T
+    return Aq @ Bq, np.abs(Aq) @ np.abs(Bq)
+

@@ -763,3 +763,109 @@ def test_lu_solve_zero_pivot_info():
     Z = np.array([[0.0, 1.0], [1.0, 0.0]])
     R, piv, info = oracle.lu_solve(Z, np.eye(2))
     assert info == 0 and list(piv) == [1, 1] and np.array_equal(R, Z)
+
+
+# --------------------------------------------------------------------------------
+# FP8 products with block scales
+# --------------------------------------------------------------------------------
+def _e4m3_table():
+    """Every non-negative finite E4M3 number, decoded from its bit fields (exponent bits
+    e, fraction bits f: e = 0 gives f 2^-9, otherwise 2^(e-7) (1 + f/8); e = 15, f = 7 is
+    NaN), with its code's lowest bit."""
+    vals, odd = [], []
+    for code in range(0x7F):
+        e, f = code >> 3, code & 7
+        vals.append(f * 2.0 ** -9 if e == 0 else 2.0 ** (e - 7) * (1 + f / 8))
+        odd.append(code & 1)
+    return np.array(vals), np.array(odd)
+
+
+def test_e4m3_table_endpoints():
+    v, _ = _e4m3_table()
+    assert np.all(np.diff(v) > 0)
+    assert v[-1] == oracle.E4M3_MAX and v[1] == 2.0 ** -9 and v[8] == 2.0 ** -6
+
+
+def test_e4m3_round_matches_torch_float8():
+    # torch's float8_e4m3fn conversion from float32 (round to nearest even) on a grid that
+    # holds every E4M3 number, every midpoint between neighbours and points just beside them
+    torch = pytest.importorskip("torch")
+    v, _ = _e4m3_table()
+    mids = (v[1:] + v[:-1]) / 2
+    pts = np.concatenate([v, mids, np.nextafter(mids.astype(np.float32), np.float32(0)),
+                          np.nextafter(mids.astype(np.float32), np.float32(np.inf)),
+                          RNG.uniform(0, 448, 20000), 2.0 ** RNG.uniform(-14, 8.8, 20000)])
+    pts = pts[pts <= 448].astype(np.float32).astype(np.float64)
+    pts = np.concatenate([pts, -pts])
+    ref = torch.tensor(pts, dtype=torch.float32).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    assert np.array_equal(oracle.e4m3_round(pts), ref)
+
+
+def test_e4m3_round_is_nearest_even_by_search():
+    # independent of the spacing formula: nearest entry of the decoded table, a tie going to
+    # the even code
+    v, odd = _e4m3_table()
+    x = np.concatenate([RNG.uniform(0, 448, 3000), 2.0 ** RNG.uniform(-12, 8.8, 3000),
+                        (v[1:] + v[:-1]) / 2])
+    x = x[x <= 448]
+    got = oracle.e4m3_round(x)
+    for xi, gi in zip(x, got):
+        d = np.abs(v - xi)
+        best = np.flatnonzero(d == d.min())
+        pick = best[0] if len(best) == 1 else best[odd[best] == 0][0]
+        assert gi == v[pick], (xi, gi, v[pick])
+    with pytest.raises(ValueError):
+        oracle.e4m3_round(np.array([449.0]))
+
+
+def test_mx_block_exp_brute_force_and_hand_cases():
+    for amax in np.concatenate([2.0 ** RNG.uniform(-60, 60, 2000), [448.0, 449.0, 1.0, 0.875, 0.8751]]):
+        X = next(x for x in range(-200, 200) if amax * 2.0 ** -x <= 448.0)
+        assert oracle.mx_block_exp(float(amax)) == X
+    assert oracle.mx_block_exp(448.0) == 0 and oracle.mx_block_exp(449.0) == 1
+    assert oracle.mx_block_exp(1.0) == -8          # 1 * 2^8 = 256 <= 448 < 512
+    assert oracle.mx_block_exp(0.0) == 0
+    assert oracle.mx_block_exp(2.0 ** -300) == -127 and oracle.mx_block_exp(2.0 ** 300) == 127
+
+
+def test_mxfp8_quantize_rows_per_block_scales():
+    # blocks of one row 2^30 apart: each block keeps 3 fraction bits (relative error 2^-4 at
+    # most); one scale per row would flush the small blocks to zero
+    n = 96
+    M = RNG.uniform(0.5, 1.0, (3, n)) * np.where(RNG.random((3, n)) < 0.5, -1, 1)
+    M[:, 32:64] *= 2.0 ** -30
+    M[1, 64:] *= 2.0 ** 20
+    q, X, e = oracle.mxfp8_quantize_rows(M)
+    assert X.shape == (3, 3) and np.all(np.abs(q) <= 448)
+    Mq = oracle._mx_dequantize(q, X, e)
+    assert np.all(np.abs(Mq - M) <= 2.0 ** -4 * np.abs(M))
+    assert X[0, 1] == X[0, 0] - 30
+    # integers up to 8 are exact; a ragged tail block and a zero row
+    Z = RNG.integers(-8, 9, (4, 45)).astype(float)
+    Z[2] = 0
+    qz, Xz, ez = oracle.mxfp8_quantize_rows(Z)
+    assert np.array_equal(oracle._mx_dequantize(qz, Xz, ez), Z) and ez[2] == 0 and np.all(Xz[2] == 0)
+
+
+def test_matmul_mxfp8_exact_on_integers_and_bound():
+    A = RNG.integers(-4, 5, (37, 70)).astype(float)
+    B = RNG.integers(-4, 5, (70, 29)).astype(float)
+    C, _ = oracle.matmul_mxfp8(A, B)
+    assert np.array_equal(C, A @ B)
+    # Gaussian factors: each quantised entry within 2^-4 of the original, or within half a
+    # subnormal step 2^(e + X - 10) of its row and block; the product error follows from the
+    # factor errors (a transposed or mis-scaled factor would not)
+    A = RNG.standard_normal((40, 100)); B = RNG.standard_normal((100, 30))
+    C, absprod = oracle.matmul_mxfp8(A, B)
+    u = 2.0 ** -4
+    deq = []
+    for M in (A, B.T):
+        q, X, e = oracle.mxfp8_quantize_rows(M)
+        Mq = oracle._mx_dequantize(q, X, e)
+        half_sub = np.ldexp(1.0, e[:, None] + np.repeat(X, 32, axis=1)[:, :M.shape[1]] - 10)
+        assert np.all(np.abs(Mq - M) <= np.maximum(u * np.abs(M), half_sub))
+        deq.append(Mq)
+    dA, dB = np.abs(deq[0] - A), np.abs(deq[1].T - B)
+    bound = dA @ np.abs(B) + np.abs(A) @ dB + dA @ dB + 4 * 100 * 2.0 ** -53 * (np.abs(A) @ np.abs(B))
+    assert np.all(np.abs(C - A @ B) <= bound)
+    assert np.allclose(absprod, np.abs(deq[0]) @ np.abs(deq[1].T))
