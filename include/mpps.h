@@ -57,8 +57,11 @@ typedef enum { MPPS_FIXED_FP64 = 0, MPPS_MIXED_PAPER = 1, MPPS_MIXED_NS = 2 } mp
 
 /* Product formats, ordered from most to least precise.  The unit roundoff of each format's
  * rounded inputs: FP64 2^-53; BF16X3 (operands split into bf16 hi+lo, three products
- * hi*hi + hi*lo + lo*hi accumulated in FP32) 2^-16; TF32 2^-11; BF16 2^-8; FP8 (E4M3, with a
- * power-of-two scale per operand) 2^-4.  All but FP64 accumulate in FP32 (unit 2^-24).
+ * hi*hi + hi*lo + lo*hi accumulated in FP32) 2^-16; TF32 2^-11; BF16 2^-8; FP8 (E4M3) 2^-4.
+ * The BF16/TF32 operands are scaled by a power of two per matrix; FP8 ones by a power of two
+ * per row of the left factor and per column of the right one, then by one per 32 entries
+ * along the inner dimension (block scales applied by the tensor core), so that every block
+ * keeps E4M3's 3 fraction bits.  All but FP64 accumulate in FP32 (unit 2^-24).
  * NONE marks a step with no product (B_r a scalar multiple of I, i.e. s divides m). */
 typedef enum {
     MPPS_FMT_NONE = -1,

@@ -1106,10 +1106,12 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
     void *Ylo_hi[MPPS_NUM_FORMATS] = {}, *Ylo_lo[MPPS_NUM_FORMATS] = {};
     void *Pl_hi[2] = {}, *Pl_lo[2] = {};
     double *d_sY, *d_sP, *d_alpha;
-    // FP8 operands get one power-of-two scale per row of P_i and per column of Y (the
-    // exponents that undo them, and column-maximum scratch)
+    // FP8 operands: one power of two per row of P_i and per column of Y (the exponents that
+    // undo them, and column-maximum scratch), then one per 32 entries along K (block scale
+    // codes of P_i and of Y)
     int *xrowP = nullptr, *xcolY = nullptr;
     unsigned long long* cmax8 = nullptr;
+    uint8_t *sfP = nullptr, *sfY = nullptr;
     auto layout2 = [&](Arena& a) {
         for (int f = 1; f < MPPS_NUM_FORMATS; ++f)
             if (used[f]) {
@@ -1124,6 +1126,8 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
             xrowP = a.take<int>((size_t)batch * n);
             xcolY = a.take<int>((size_t)batch * n);
             cmax8 = a.take<unsigned long long>((size_t)batch * n);
+            sfP = a.take<uint8_t>((size_t)batch * mx_scale_bytes_a(n));
+            sfY = a.take<uint8_t>((size_t)batch * mx_scale_bytes_b(n));
         }
         // one contiguous block (filled by a single copy, or by the device plan): sY | sP |
         // alpha
@@ -1173,9 +1177,9 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
         for (int f = 1; f < MPPS_NUM_FORMATS; ++f)
             if (used[f]) {
                 rc = f == MPPS_FMT_FP8
-                         ? launch_convert_scaled(f, pw + (long long)(s - 1) * nn, pw_bs, n, batch,
-                                                 Ylo_hi[f], nullptr, low_bs, lld, low_target_exp(f),
-                                                 true, xcolY, cmax8, st, yg[f])
+                         ? launch_convert_mx(pw + (long long)(s - 1) * nn, pw_bs, n, batch,
+                                             (uint8_t*)Ylo_hi[f], low_bs, lld, sfY,
+                                             mx_scale_bytes_b(n), true, xcolY, cmax8, st, yg[f])
                          : launch_convert(f, pw + (long long)(s - 1) * nn, pw_bs, n, batch, Ylo_hi[f],
                                           Ylo_lo[f], low_bs, lld, d_sY + (size_t)f * batch, true, st,
                                           yg[f]);
@@ -1313,15 +1317,17 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
                     rc = launch_gemm_f64e(k, slA, k, eA, slY, K, eY, n, batch, batch, ep, d_err, st,
                                           nullptr, split);
             } else if (f == MPPS_FMT_FP8) {
-                // per-row scales of P_i, per-column scales of Y (the paper's scaled low-precision
-                // products, with the scales as fine as a row / a column)
-                rc = launch_convert_scaled(f, Pdst[i], nn, n, batch, Pl_hi[i & 1], nullptr, low_bs,
-                                           lld, low_target_exp(f), false, xrowP, nullptr, st, g);
+                // the paper's scaled low-precision product with the scales as fine as E4M3
+                // needs: a power of two per row of P_i and per column of Y (undone in the
+                // epilogue), and one per 32 entries along K applied by the tensor core
+                rc = launch_convert_mx(Pdst[i], nn, n, batch, (uint8_t*)Pl_hi[i & 1], low_bs, lld,
+                                       sfP, mx_scale_bytes_a(n), false, xrowP, nullptr, st, g);
                 ep.row_exp = xrowP;
                 ep.col_exp = xcolY;
+                const MxScales mx{sfP, sfY, mx_scale_bytes_a(n), mx_scale_bytes_b(n), (n + 127) / 128};
                 if (!rc)
-                    rc = launch_gemm_tc(f, Pl_hi[i & 1], Pl_lo[i & 1], Ylo_hi[f], Ylo_lo[f], low_bs,
-                                        low_bs, lld, n, batch, ep, d_err, st);
+                    rc = launch_gemm_tc(f, Pl_hi[i & 1], nullptr, Ylo_hi[f], nullptr, low_bs, low_bs,
+                                        lld, n, batch, ep, d_err, st, &mx);
             } else {
                 ep.alpha_b = d_alpha + (size_t)i * batch;
                 rc = launch_gemm_tc(f, Pl_hi[i & 1], Pl_lo[i & 1], Ylo_hi[f], Ylo_lo[f], low_bs,
@@ -1910,6 +1916,22 @@ mpps_status mpps_matmul(const double* A, const double* B, double* C, int n, int 
             set_error("a bounded wait in the emulated FP64 product timed out");
             return MPPS_ETIMEOUT;
         }
+    } else if (format == MPPS_FMT_FP8) {   // block scales along K (tcgen05 kind::mxf8f6f4)
+        DevBuf ws;
+        const size_t wb = fp8mx_ws_bytes(n, batch);
+        if ((rc = ws.alloc(wb + 256, st))) return rc;
+        int* err = (int*)((char*)ws.p + wb);
+        MPPS_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+        rc = launch_product_fp8mx(a.dev, nn, b.dev, nn, n, batch, ep, fp8mx_ws_carve(ws.p, n, batch),
+                                  err, st);
+        if (rc) return rc;
+        int h_err = 0;
+        MPPS_CUDA_TRY(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        MPPS_CUDA_TRY(cudaStreamSynchronize(st));
+        if (h_err) {
+            set_error("a bounded wait in the tensor-core product timed out");
+            return MPPS_ETIMEOUT;
+        }
     } else {
         const int lld = low_ld(n);
         const long long low_bs = (long long)n * lld;
@@ -2014,6 +2036,7 @@ struct ProductWs {
     char* split = nullptr;
     char *ahi = nullptr, *alo = nullptr, *bhi = nullptr, *blo = nullptr;
     double *ma = nullptr, *mb = nullptr, *sa = nullptr, *sb = nullptr, *un = nullptr;
+    char* fp8 = nullptr;   // FP8 products with block scales (fp8mx_ws_bytes)
     void take(Arena& z, int n, int batch, int kmax, bool low) {
         if (kmax > 0) {
             slA = z.take<__nv_bfloat16>(f64e_plane_elems(n, batch, kmax));
@@ -2034,6 +2057,7 @@ struct ProductWs {
             sa = z.take<double>(batch);
             sb = z.take<double>(batch);
             un = z.take<double>(batch);
+            fp8 = z.take<char>(fp8mx_ws_bytes(n, batch));
         }
     }
 };
@@ -2060,6 +2084,9 @@ static mpps_status product_fmt(int fmt, const double* A, long long a_bs, const d
         set_error("product_fmt: format %d has no workspace", fmt);
         return MPPS_EINVAL;
     }
+    if (fmt == MPPS_FMT_FP8)   // block scales along K instead of one scale per matrix
+        return launch_product_fp8mx(A, a_bs, B, b_bs, n, batch, ep, fp8mx_ws_carve(w.fp8, n, batch),
+                                    d_err, st);
     const int lld = low_ld(n);
     const long long low_bs = (long long)n * lld;
     MPPS_CUDA_TRY(cudaMemsetAsync(w.ma, 0, sizeof(double) * batch, st));

@@ -336,12 +336,44 @@ mpps_status launch_gemm_f64(const double* A, long long a_bs, const double* B, lo
                             int n, int batch, const Epilogue& ep, cudaStream_t st,
                             const int* bidx = nullptr);
 
+// Block scales of an FP8 product (tcgen05 kind::mxf8f6f4): one 8-bit code c (scale
+// 2^(c - 127)) per row of A and per column of B per 32 entries of K.  Each array holds
+// 512-byte chunks, one per (128 rows of A | 64 columns of B) x (128 entries of K): chunk
+// (t, kc) at byte (t * kc_count + kc) * 512, and inside it row (column) r, K block j (0..3) at
+// (r % 32) * 16 + (r / 32) * 4 + j -- the arrangement tcgen05.cp 32x128b.warpx4 carries into
+// the TMEM words the MMA reads (lane r % 32, column r / 32, byte j).  a_bs, b_bs: bytes per
+// matrix; kc = ceil(n / 128).
+struct MxScales {
+    const uint8_t* a;
+    const uint8_t* b;
+    long long a_bs, b_bs;
+    int kc;
+};
+inline long long mx_scale_bytes_a(int n) { return (long long)((n + 127) / 128) * ((n + 127) / 128) * 512; }
+inline long long mx_scale_bytes_b(int n) { return (long long)((n + 63) / 64) * ((n + 127) / 128) * 512; }
+
 // Low-precision product on tcgen05: A_low (row-major, K-major, ld = lld) times B_low^T
 // where B_low holds B transposed (row j = column j of B), in format fmt.  acc * alpha is
-// passed to the epilogue (alpha undoes the operand scales).
+// passed to the epilogue (alpha undoes the operand scales).  FP8 needs the block scales mx.
 mpps_status launch_gemm_tc(int fmt, const void* A_hi, const void* A_lo, const void* Bt_hi,
                            const void* Bt_lo, long long a_bs, long long b_bs, int lld, int n,
-                           int batch, const Epilogue& ep, int* d_err, cudaStream_t st);
+                           int batch, const Epilogue& ep, int* d_err, cudaStream_t st,
+                           const MxScales* mx = nullptr);
+
+// Workspace of a plain FP8 product C = A B with block scales (fp8mx_ws_bytes bytes, carved
+// by fp8mx_ws_carve from a 256-byte aligned base) and the product itself: both conversions,
+// then the block-scaled tcgen05 product with the row and column exponents undone in the
+// epilogue (ep.row_exp / ep.col_exp are set here).
+struct Fp8MxWs {
+    uint8_t *qa, *qb, *sfa, *sfb;
+    int *ea, *eb;
+    unsigned long long* cmax;
+};
+size_t fp8mx_ws_bytes(int n, int batch);
+Fp8MxWs fp8mx_ws_carve(void* base, int n, int batch);
+mpps_status launch_product_fp8mx(const double* A, long long a_bs, const double* B, long long b_bs,
+                                 int n, int batch, Epilogue ep, const Fp8MxWs& w, int* d_err,
+                                 cudaStream_t st);
 
 // FP64-accurate product from exact bf16 slices (gemm_f64e.cu).  Slice planes of A (rows)
 // and of B^T (rows of B^T = columns of B) come from launch_slice_rows; eA/eB are the
@@ -489,15 +521,17 @@ mpps_status launch_convert(int fmt, const double* M, long long bs, int n, int ba
                            void* lo, long long low_bs, int lld, const double* d_scale,
                            bool transpose, cudaStream_t st, const int* gate = nullptr);
 // max_ij |M_ij| per matrix, written to out[b] (out must be zeroed first).
-// Rounded copy in format fmt with one power-of-two scale per row (transpose = false: rows of
-// M, the A operand) or per column (transpose = true: written transposed, row j = column j of
-// M, the B^T operand): the row or column maximum is brought below 2^target, and its unscaling
-// exponent (e - target, max < 2^e) goes to out_exp[batch][n].  colmax: batch * n scratch
-// words (transpose only).
-mpps_status launch_convert_scaled(int fmt, const double* M, long long bs, int n, int batch,
-                                  void* hi, void* lo, long long low_bs, int lld, int target,
-                                  bool transpose, int* out_exp, unsigned long long* colmax,
-                                  cudaStream_t st, const int* gate = nullptr);
+// FP8 (E4M3) copy with block scales, the operands of a block-scaled product: each row of M
+// (transpose = false, the A operand) or each column (transpose = true, written transposed:
+// row j = column j of M, the B^T operand) first gets its own power of two (largest magnitude
+// below 1; the exponent that undoes it goes to out_exp[batch][n]), then every 32 consecutive
+// entries along K a power-of-two scale code (in sf, the MxScales arrangement, sf_bs bytes per
+// matrix; mx_scale_bytes_a / _b) and their E4M3 values (q, row pitch lld bytes, q_bs bytes per
+// matrix).  colmax: batch * n scratch words (transpose only).
+mpps_status launch_convert_mx(const double* M, long long bs, int n, int batch, uint8_t* q,
+                              long long q_bs, int lld, uint8_t* sf, long long sf_bs, bool transpose,
+                              int* out_exp, unsigned long long* colmax, cudaStream_t st,
+                              const int* gate = nullptr);
 mpps_status launch_maxabs(const double* M, long long bs, int n, int batch, double* out,
                           cudaStream_t st);
 // For each matrix b: scale[b] = 2^(target - e) and unscale... (power-of-two operand scales)

@@ -510,37 +510,105 @@ __device__ __forceinline__ int frexp_exp_bits(unsigned long long a) {
     return ef != 0 ? ef - 1022 : (64 - __clzll((long long)a)) - 1074;
 }
 
-// Rounded copy of each row of M with its own power-of-two scale: the row maximum is brought
-// below 2^target (scale 2^(target - e)), and e - target, the exponent that undoes it, goes to
-// out_exp.  One 256-thread block per row.
-__global__ void __launch_bounds__(256) k_convert_rows_scaled(int fmt, const double* __restrict__ M,
-                                                             long long bs, int n, void* hi, void* lo,
-                                                             long long low_bs, int lld, int target,
-                                                             int* __restrict__ out_exp,
-        const int* __restrict__ gate) {
+// ---- FP8 copies with block scales (operands of the block-scaled tcgen05 product) --------
+// Shared exponent of a 32-entry block whose largest magnitude has the bit pattern `a`: the
+// smallest X with max 2^-X <= 448 (E4M3's largest finite number), 0 for a zero block,
+// clamped to [-127, 127], the range of the 8-bit code X + 127.
+__device__ __forceinline__ int mx_block_exp_bits(unsigned long long a) {
+    if (a == 0) return 0;
+    const int ef = (int)(a >> 52);
+    if (ef == 0) return -127;                        // subnormal double: below every scale
+    const int E = ef - 1022;                         // max = f 2^E, f in [0.5, 1)
+    // 512 f <= 448  <=>  1 + m 2^-52 <= 1.75  <=>  m <= 3 2^50
+    const int X = (a & 0xFFFFFFFFFFFFFULL) <= (3ULL << 50) ? E - 9 : E - 8;
+    return X < -127 ? -127 : (X > 127 ? 127 : X);
+}
+
+// Nearest E4M3 number to w, ties to the even fraction, from the bits of w.  E4M3: 4
+// exponent bits (bias 7), 3 fraction bits, subnormals j 2^-9, largest finite 448.  Callers
+// keep |w| <= 448; larger magnitudes give 448, NaN and infinity the NaN code.
+__device__ __forceinline__ uint8_t e4m3_rne(double w) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(w);
+    const unsigned sgn = (unsigned)(u >> 63) << 7;
+    const unsigned long long a = u & 0x7fffffffffffffffULL;
+    const int ef = (int)(a >> 52);
+    if (ef == 0x7ff) return (uint8_t)(sgn | 0x7F);
+    if (a > 0x407C000000000000ULL) return (uint8_t)(sgn | 0x7E);   // above 448
+    if (ef == 0) return (uint8_t)sgn;                              // zero, subnormal double
+    const int E = ef - 1023;                                       // |w| in [2^E, 2^(E+1))
+    const unsigned long long sig = (1ULL << 52) | (a & 0xFFFFFFFFFFFFFULL);
+    // |w| / quantum as sig >> sh plus the remainder: quantum 2^-9 below 2^-6, else 2^(E-3)
+    const int sh = E < -6 ? 43 - E : 49;
+    if (sh > 62) return (uint8_t)sgn;                              // |w| < 2^-19
+    unsigned long long qv = sig >> sh;
+    const unsigned long long rem = sig & ((1ULL << sh) - 1), half = 1ULL << (sh - 1);
+    if (rem > half || (rem == half && (qv & 1))) ++qv;
+    if (E < -6) return (uint8_t)(sgn | (unsigned)qv);              // code 8 is 2^-6
+    int e8 = E + 7;
+    if (qv == 16) {   // rounded up into the next binade
+        qv = 8;
+        ++e8;
+    }
+    return (uint8_t)(sgn | ((unsigned)e8 << 3) | (unsigned)(qv & 7));
+}
+
+// Offset of row (column) r's code for K block j inside the scale array of one matrix, in
+// 512-byte chunks per (rpc = 128 rows | 64 columns) x (4 K blocks): (r % 32) 16 +
+// (r % rpc) / 32 * 4 + j % 4 within the chunk.
+__device__ __forceinline__ long long mx_code_off(int r, int j, int rpc, int kc) {
+    return ((long long)(r / rpc) * kc + (j >> 2)) * 512 + (r & 31) * 16 + ((r % rpc) >> 5) * 4 +
+           (j & 3);
+}
+
+// FP8 copy of each row of M (the A operand): the row's power of two 2^-e (e the frexp
+// exponent of its largest magnitude, to out_exp), then per 32-entry block the scale code
+// and the E4M3 values.  Rows n .. 128 kc - 1 of the last chunk get neutral codes (127).
+// One 256-thread block per row; warp w takes blocks w, w + 8, ...
+__global__ void __launch_bounds__(256) k_convert_rows_mx(const double* __restrict__ M, long long bs,
+                                                         int n, uint8_t* __restrict__ q,
+                                                         long long q_bs, int lld,
+                                                         uint8_t* __restrict__ sf, long long sf_bs,
+                                                         int kc, int* __restrict__ out_exp,
+                                                         const int* __restrict__ gate) {
     pdl_wait();
     if (gate && (int)blockIdx.y >= __ldg(gate)) return;   // device plan: not run
     __shared__ unsigned long long red[8];
     const int row = blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31, nblk = 4 * kc;
+    uint8_t* sfm = sf + (long long)b * sf_bs;
+    if (row >= n) {
+        for (int j = tid; j < nblk; j += blockDim.x) sfm[mx_code_off(row, j, 128, kc)] = 127;
+        return;
+    }
     const double* src = M + (long long)b * bs + (long long)row * n;
     unsigned long long mx = 0;
     for (int j = tid; j < n; j += blockDim.x) {
-        const unsigned long long a = absbits(src[j]);
-        mx = a > mx ? a : mx;
+        const unsigned long long v = absbits(src[j]);
+        mx = v > mx ? v : mx;
     }
     for (int o = 16; o > 0; o >>= 1) {
         const unsigned long long t = __shfl_xor_sync(0xffffffffu, mx, o);
         mx = t > mx ? t : mx;
     }
-    if ((tid & 31) == 0) red[tid >> 5] = mx;
+    if (lane == 0) red[warp] = mx;
     __syncthreads();
     mx = red[0];
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = red[w] > mx ? red[w] : mx;
     const int e = frexp_exp_bits(mx);
-    if (tid == 0) out_exp[(long long)b * n + row] = e - target;
-    for (int j = tid; j < n; j += blockDim.x)
-        store_low(fmt, hi, lo, (long long)b * low_bs + (long long)row * lld + j,
-                  mul_exp2(src[j], target - e));
+    if (tid == 0) out_exp[(long long)b * n + row] = e;
+    uint8_t* dst = q + (long long)b * q_bs + (long long)row * lld;
+    for (int j = warp; j < nblk; j += (int)(blockDim.x >> 5)) {
+        const int k = 32 * j + lane;
+        const double v = k < n ? mul_exp2(src[k], -e) : 0.0;
+        unsigned long long bm = absbits(v);
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long t = __shfl_xor_sync(0xffffffffu, bm, o);
+            bm = t > bm ? t : bm;
+        }
+        const int X = mx_block_exp_bits(bm);
+        if (k < n) dst[k] = e4m3_rne(mul_exp2(v, -X));
+        if (lane == 0) sfm[mx_code_off(row, j, 128, kc)] = (uint8_t)(X + 127);
+    }
 }
 
 // Column maxima of |M| as bit patterns (out zeroed first), one thread per column over a
@@ -564,31 +632,50 @@ __global__ void k_colmax_bits(const double* __restrict__ M, long long bs, int n,
     atomicMax(out + (long long)b * n + col, mx);
 }
 
-// Transposed rounded copy (row j = column j of M) with one power-of-two scale per column of M
-// from its maximum (colmax); e - target per column to out_exp.
-__global__ void k_convert_t_scaled(int fmt, const double* __restrict__ M, long long bs, int n,
-                                   void* hi, void* lo, long long low_bs, int lld, int target,
-                                   const unsigned long long* __restrict__ colmax,
-                                   int* __restrict__ out_exp,
-        const int* __restrict__ gate) {
+// FP8 copy of M transposed (row j = column j of M: the B^T operand): column j's power of
+// two 2^-e (e from colmax, to out_exp), then per 32-entry block of the column the scale
+// code and the E4M3 values.  A 32 x 32 tile per block (32 x 8 threads): tile row block
+// blockIdx.y is one K block, each warp takes whole columns, lanes along K.  Columns n ..
+// 64 ceil(n / 64) - 1 and the chunks' unused words (columns 64 .. 127 of a 128-column
+// arrangement) get neutral codes (127).
+__global__ void k_convert_t_mx(const double* __restrict__ M, long long bs, int n,
+                               uint8_t* __restrict__ q, long long q_bs, int lld,
+                               uint8_t* __restrict__ sf, long long sf_bs, int kc,
+                               const unsigned long long* __restrict__ colmax,
+                               int* __restrict__ out_exp, const int* __restrict__ gate) {
     pdl_wait();
     if (gate && (int)blockIdx.z >= __ldg(gate)) return;   // device plan: not run
     __shared__ double tile[32][33];
-    const int b = blockIdx.z;
-    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    const int b = blockIdx.z, j = blockIdx.y, r0 = 32 * j, c0 = blockIdx.x * 32;
+    const int lane = threadIdx.x;
     const double* base = M + (long long)b * bs;
     for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-        const int row = r0 + i, col = c0 + threadIdx.x;
-        tile[i][threadIdx.x] = (row < n && col < n) ? base[(long long)row * n + col] : 0.0;
+        const int row = r0 + i, col = c0 + lane;
+        tile[i][lane] = (row < n && col < n) ? base[(long long)row * n + col] : 0.0;
     }
     __syncthreads();
+    uint8_t* sfm = sf + (long long)b * sf_bs;
     for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-        const int orow = c0 + i, ocol = r0 + threadIdx.x;   // out row = source column
-        if (orow >= n || ocol >= n) continue;
-        const int e = frexp_exp_bits(colmax[(long long)b * n + orow]);
-        if (blockIdx.y == 0 && threadIdx.x == 0) out_exp[(long long)b * n + orow] = e - target;
-        store_low(fmt, hi, lo, (long long)b * low_bs + (long long)orow * lld + ocol,
-                  mul_exp2(tile[threadIdx.x][i], target - e));
+        const int col = c0 + i;
+        const int e = col < n ? frexp_exp_bits(colmax[(long long)b * n + col]) : 0;
+        const double v = mul_exp2(tile[lane][i], -e);
+        unsigned long long bm = absbits(v);
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long t = __shfl_xor_sync(0xffffffffu, bm, o);
+            bm = t > bm ? t : bm;
+        }
+        const int X = mx_block_exp_bits(bm);
+        if (col < n && r0 + lane < n)
+            q[(long long)b * q_bs + (long long)col * lld + r0 + lane] = e4m3_rne(mul_exp2(v, -X));
+        if (lane == 0) {
+            const long long off = mx_code_off(col, j, 64, kc);
+            sfm[off] = (uint8_t)(X + 127);
+            if ((col & 63) < 32) {   // words 2 and 3 of this lane's row: not read at N = 64
+                sfm[off + 8] = 127;
+                sfm[off + 12] = 127;
+            }
+            if (j == 0 && col < n) out_exp[(long long)b * n + col] = e;
+        }
     }
 }
 
@@ -869,25 +956,27 @@ mpps_status launch_convert(int fmt, const double* M, long long bs, int n, int ba
     return MPPS_OK;
 }
 
-mpps_status launch_convert_scaled(int fmt, const double* M, long long bs, int n, int batch,
-                                  void* hi, void* lo, long long low_bs, int lld, int target,
-                                  bool transpose, int* out_exp, unsigned long long* colmax,
-                                  cudaStream_t st, const int* gate) {
+mpps_status launch_convert_mx(const double* M, long long bs, int n, int batch, uint8_t* q,
+                              long long q_bs, int lld, uint8_t* sf, long long sf_bs, bool transpose,
+                              int* out_exp, unsigned long long* colmax, cudaStream_t st,
+                              const int* gate) {
     ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
     if (batch > 65535) {
-        set_error("convert_scaled: batch %d exceeds the grid limit", batch);
+        set_error("convert_mx: batch %d exceeds the grid limit", batch);
         return MPPS_EINVAL;
     }
+    if (batch == 0 || n <= 0) return MPPS_OK;
+    const int kc = (n + 127) / 128;
     if (!transpose) {
-        MPPS_CUDA_TRY(launch_pdl(k_convert_rows_scaled, dim3(n, batch), dim3(256), 0, st, fmt, M, bs, n, hi, lo,
-                                 low_bs, lld, target, out_exp, gate));
+        MPPS_CUDA_TRY(launch_pdl(k_convert_rows_mx, dim3(128 * kc, batch), dim3(256), 0, st, M, bs, n,
+                                 q, q_bs, lld, sf, sf_bs, kc, out_exp, gate));
     } else {
         MPPS_CUDA_TRY(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * (size_t)batch * n, st));
         MPPS_CUDA_TRY(launch_pdl(k_colmax_bits, dim3((n + 127) / 128, (n + 15) / 16, batch), dim3(128), 0, st, M, bs, n,
                                  colmax, gate));
         MPPS_LAUNCH_CHECK();
-        MPPS_CUDA_TRY(launch_pdl(k_convert_t_scaled, dim3((n + 31) / 32, (n + 31) / 32, batch), dim3(32, 8), 0, st, fmt, M,
-                                 bs, n, hi, lo, low_bs, lld, target, colmax, out_exp, gate));
+        MPPS_CUDA_TRY(launch_pdl(k_convert_t_mx, dim3(2 * ((n + 63) / 64), 4 * kc, batch), dim3(32, 8), 0, st, M, bs,
+                                 n, q, q_bs, lld, sf, sf_bs, kc, colmax, out_exp, gate));
     }
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;

@@ -5,9 +5,17 @@
 //   BF16    kind::f16,     1 product                        (u = 2^-8)
 //   BF16X3  kind::f16,     hi*hi + hi*lo + lo*hi, one TMEM accumulator (u ~ 2^-16)
 //   TF32    kind::tf32,    1 product                        (u = 2^-11)
-//   FP8     kind::f8f6f4 (E4M3 x E4M3), 1 product          (u = 2^-4)
+//   FP8     kind::mxf8f6f4 with block scales (E4M3 x E4M3), 1 product   (u = 2^-4)
 // all accumulated in FP32.  The epilogue reads the 128 x 128 FP32 tile out of TMEM,
 // undoes the operand scales and adds B_{i-1} in FP64 (fused Horner add).
+//
+// FP8 products scale every 32 entries of K of each row of A and each column of B by their
+// own power of two (8-bit codes, MxScales): one scale per row or column cannot hold a row
+// whose entries span more than E4M3's 2^17 range, a scale per 32-entry block keeps each
+// block's 3 fraction bits.  The tensor core applies the scales itself: per stage the TMA
+// warp also fetches the 512-byte scale chunks of A and B, the MMA thread copies them into
+// TMEM (tcgen05.cp, one TMEM region per stage) and issues the block-scaled MMAs, the
+// instruction descriptor naming the block (byte) each of the four K = 32 steps reads.
 //
 // Structure: one CTA (8 warps) per 128 x TN output tile (TN = 64 when 128 x 128 tiles would
 // leave SMs idle, else 128), K walked in 128-byte slabs (64 bf16 / 32 tf32 / 128 fp8 per
@@ -50,8 +58,8 @@ struct Tc<MPPS_FMT_TF32> {
     static constexpr int kOps = 2, kStages = 4, kAB = 2;
 };
 template <>
-struct Tc<MPPS_FMT_FP8> {
-    static constexpr int kOps = 2, kStages = 4, kAB = 0;
+struct Tc<MPPS_FMT_FP8> {   // block-scaled only (make_idesc_mx)
+    static constexpr int kOps = 2, kStages = 4;
 };
 
 template <int FMT, int TN>
@@ -70,11 +78,6 @@ __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint3
             "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
             "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
             "l"(a), "l"(b), "r"(id), "r"(acc));
-    } else if constexpr (FMT == MPPS_FMT_FP8) {
-        asm volatile(
-            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-            "l"(a), "l"(b), "r"(id), "r"(acc));
     } else {
         asm volatile(
             "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
@@ -83,21 +86,28 @@ __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint3
     }
 }
 
-template <int FMT>
+constexpr int MX_CHUNK = 512;              // bytes of scale codes per operand and stage
+
+template <int FMT, bool MX>
 __host__ __device__ constexpr int smem_bytes() {
-    return Tc<FMT>::kStages * Tc<FMT>::kOps * TILE_BYTES + 1024 + 256;
+    return Tc<FMT>::kStages * (Tc<FMT>::kOps * TILE_BYTES + (MX ? 2 * MX_CHUNK : 0)) + 1024 + 256;
 }
 
 constexpr int TC_THREADS = 512;           // 16 warps: all of them run the epilogue
 constexpr int TC_COLGROUPS = TC_THREADS / 128;   // warps per TMEM lane quarter
 
-template <int FMT, int TN>
+template <int FMT, int TN, bool MX>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2,
-              int n, Epilogue ep, int* err) {
+              int n, Epilogue ep, MxScales mx, int* err) {
+    static_assert(!MX || (FMT == MPPS_FMT_FP8 && TN == 64), "block scales: FP8, 128 x 64 tiles");
     constexpr int OPS = Tc<FMT>::kOps, STAGES = Tc<FMT>::kStages;
-    constexpr int STAGE_BYTES = OPS * TILE_BYTES;
+    constexpr int STAGE_BYTES = OPS * TILE_BYTES + (MX ? 2 * MX_CHUNK : 0);
+    // TMEM: the accumulator (TN columns), then for block scales 8 columns per stage (4 for
+    // A's codes, 4 for B's)
+    constexpr uint32_t TMEM_COLS = MX ? 128 : TN;
+    static_assert(!MX || TN + 8 * STAGES <= 128, "scale regions exceed the TMEM allocation");
     constexpr int ESIZE = (FMT == MPPS_FMT_TF32) ? 4 : (FMT == MPPS_FMT_FP8 ? 1 : 2);
     constexpr int KSLAB = SLAB / ESIZE;   // K elements per stage
 
@@ -125,7 +135,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tmem_slot)),
-                     "r"(TN));
+                     "r"(TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     tc_fence_before();
@@ -138,7 +148,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         tc_fence_before();
         __syncthreads();
         if (warp == 0)
-            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TN));
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
         return;
     }
 
@@ -148,11 +158,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (; kb < nk; ++kb) {
             const int s = kb % STAGES;
             if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1, err)) break;
-            mbar_expect_tx(&full[s], (OPS / 2) * (TM + TN) * SLAB);
+            mbar_expect_tx(&full[s], (OPS / 2) * (TM + TN) * SLAB + (MX ? 2 * MX_CHUNK : 0));
             uint8_t* st = smem + s * STAGE_BYTES;
             const int kc = kb * KSLAB;
             tma_load_3d(st, &tmA, kc, m0, b, &full[s]);
             tma_load_3d(st + TILE_BYTES, &tmB, kc, n0, b, &full[s]);
+            if constexpr (MX) {   // this stage's scale chunks: rows m0.., columns n0.., K block kb
+                bulk_load(st + OPS * TILE_BYTES,
+                          mx.a + b * mx.a_bs + ((long long)(m0 / TM) * mx.kc + kb) * MX_CHUNK,
+                          MX_CHUNK, &full[s]);
+                bulk_load(st + OPS * TILE_BYTES + MX_CHUNK,
+                          mx.b + b * mx.b_bs + ((long long)(n0 / TN) * mx.kc + kb) * MX_CHUNK,
+                          MX_CHUNK, &full[s]);
+            }
             if constexpr (OPS == 4) {
                 tma_load_3d(st + 2 * TILE_BYTES, &tmA2, kc, m0, b, &full[s]);
                 tma_load_3d(st + 3 * TILE_BYTES, &tmB2, kc, n0, b, &full[s]);
@@ -175,10 +193,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             // descriptors of this stage; the K advance of 32 bytes is +2 in the address field
             const uint64_t da = sw128_desc(smem_u32(smem + s * STAGE_BYTES));
             const uint64_t db = da + (uint64_t)(TILE_BYTES >> 4);
+            uint32_t sfa = 0, sfb = 0;
+            if constexpr (MX) {   // scale codes into this stage's TMEM columns
+                sfa = tmem + (uint32_t)(TN + 8 * s);
+                sfb = sfa + 4;
+                const uint32_t ss = smem_u32(smem + s * STAGE_BYTES + OPS * TILE_BYTES);
+                tmem_cp_32x128b_x4(sfa, plain16_desc(ss));
+                tmem_cp_32x128b_x4(sfb, plain16_desc(ss + MX_CHUNK));
+            }
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
                 const uint64_t ad = da + (uint64_t)(2 * kk), bd = db + (uint64_t)(2 * kk);
-                tc_mma<FMT, TN>(tmem, ad, bd, (kb | kk) != 0 ? 1u : 0u);
+                if constexpr (MX)
+                    mma_mxf8(tmem, ad, bd, make_idesc_mx(TM, TN, kk, kk), sfa, sfb,
+                             (kb | kk) != 0 ? 1u : 0u);
+                else
+                    tc_mma<FMT, TN>(tmem, ad, bd, (kb | kk) != 0 ? 1u : 0u);
                 if constexpr (OPS == 4) {
                     const uint64_t ad2 = da + (uint64_t)((2 * TILE_BYTES >> 4) + 2 * kk);
                     const uint64_t bd2 = da + (uint64_t)((3 * TILE_BYTES >> 4) + 2 * kk);
@@ -240,7 +270,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_fence_before();
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TN));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
 }
 
 // ---- host side ----------------------------------------------------------------------
@@ -278,10 +308,10 @@ bool make_map(CUtensorMap* tm, int fmt, const void* ptr, int n, int batch, int l
     return r == CUDA_SUCCESS;
 }
 
-template <int FMT, int TN>
+template <int FMT, int TN, bool MX = false>
 mpps_status launch_fmt(const void* A_hi, const void* A_lo, const void* Bt_hi, const void* Bt_lo,
                        long long a_bs, long long b_bs, int lld, int n, int batch, const Epilogue& ep,
-                       int* d_err, cudaStream_t st) {
+                       int* d_err, cudaStream_t st, MxScales mx = MxScales{}) {
     CUtensorMap ta, tb, ta2, tb2;
     bool ok = make_map(&ta, FMT, A_hi, n, batch, lld, a_bs, TM) &&
               make_map(&tb, FMT, Bt_hi, n, batch, lld, b_bs, TN);
@@ -296,7 +326,7 @@ mpps_status launch_fmt(const void* A_hi, const void* A_lo, const void* Bt_hi, co
         set_error("cuTensorMapEncodeTiled failed (n=%d, lld=%d)", n, lld);
         return MPPS_ECUDA;
     }
-    constexpr int smem = smem_bytes<FMT>();
+    constexpr int smem = smem_bytes<FMT, MX>();
     // the attribute is a property of the kernel on the current device: set once per device
     static std::mutex attr_mu;
     static bool attr_set[64] = {false};
@@ -309,7 +339,7 @@ mpps_status launch_fmt(const void* A_hi, const void* A_lo, const void* Bt_hi, co
         }
         std::lock_guard<std::mutex> lk(attr_mu);
         if (!attr_set[dev]) {
-            MPPS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<FMT, TN>,
+            MPPS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<FMT, TN, MX>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
             attr_set[dev] = true;
         }
@@ -317,16 +347,66 @@ mpps_status launch_fmt(const void* A_hi, const void* A_lo, const void* Bt_hi, co
     dim3 grid((n + TN - 1) / TN, (n + TM - 1) / TM, batch);
     ProfScope prof(MPPS_PROF_GEMM_TC, st,
                    2.0 * n * (double)n * n * batch * (FMT == MPPS_FMT_BF16X3 ? 3 : 1));
-    MPPS_CUDA_TRY(launch_pdl(k_gemm_tc<FMT, TN>, dim3(grid), dim3(TC_THREADS), smem, st, ta, tb, ta2, tb2, n, ep, d_err));
+    MPPS_CUDA_TRY(launch_pdl(k_gemm_tc<FMT, TN, MX>, dim3(grid), dim3(TC_THREADS), smem, st, ta, tb, ta2, tb2, n, ep, mx, d_err));
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }
 
+size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
 }  // namespace
+
+size_t fp8mx_ws_bytes(int n, int batch) {
+    const size_t nb = (size_t)batch * n;
+    return 2 * al256(nb * low_ld(n)) + al256((size_t)batch * mx_scale_bytes_a(n)) +
+           al256((size_t)batch * mx_scale_bytes_b(n)) + 2 * al256(sizeof(int) * nb) +
+           al256(sizeof(unsigned long long) * nb);
+}
+
+Fp8MxWs fp8mx_ws_carve(void* base, int n, int batch) {
+    const size_t nb = (size_t)batch * n;
+    uint8_t* p = (uint8_t*)base;
+    Fp8MxWs w;
+    w.qa = p; p += al256(nb * low_ld(n));
+    w.qb = p; p += al256(nb * low_ld(n));
+    w.sfa = p; p += al256((size_t)batch * mx_scale_bytes_a(n));
+    w.sfb = p; p += al256((size_t)batch * mx_scale_bytes_b(n));
+    w.ea = (int*)p; p += al256(sizeof(int) * nb);
+    w.eb = (int*)p; p += al256(sizeof(int) * nb);
+    w.cmax = (unsigned long long*)p;
+    return w;
+}
+
+mpps_status launch_product_fp8mx(const double* A, long long a_bs, const double* B, long long b_bs,
+                                 int n, int batch, Epilogue ep, const Fp8MxWs& w, int* d_err,
+                                 cudaStream_t st) {
+    const int lld = low_ld(n);
+    const long long q_bs = (long long)n * lld;
+    mpps_status rc = launch_convert_mx(A, a_bs, n, batch, w.qa, q_bs, lld, w.sfa, mx_scale_bytes_a(n),
+                                       false, w.ea, nullptr, st);
+    if (!rc)
+        rc = launch_convert_mx(B, b_bs, n, batch, w.qb, q_bs, lld, w.sfb, mx_scale_bytes_b(n), true,
+                               w.eb, w.cmax, st);
+    if (rc) return rc;
+    ep.row_exp = w.ea;
+    ep.col_exp = w.eb;
+    const MxScales mx{w.sfa, w.sfb, mx_scale_bytes_a(n), mx_scale_bytes_b(n), (n + 127) / 128};
+    return launch_gemm_tc(MPPS_FMT_FP8, w.qa, nullptr, w.qb, nullptr, q_bs, q_bs, lld, n, batch, ep,
+                          d_err, st, &mx);
+}
 
 mpps_status launch_gemm_tc(int fmt, const void* A_hi, const void* A_lo, const void* Bt_hi,
                            const void* Bt_lo, long long a_bs, long long b_bs, int lld, int n,
-                           int batch, const Epilogue& ep, int* d_err, cudaStream_t st) {
+                           int batch, const Epilogue& ep, int* d_err, cudaStream_t st,
+                           const MxScales* mx) {
+    if (fmt == MPPS_FMT_FP8) {   // block-scaled, 128 x 64 tiles (the scale chunks' width)
+        if (!mx || !mx->a || !mx->b || mx->kc != (n + 127) / 128) {
+            set_error("launch_gemm_tc: an FP8 product needs its block scales");
+            return MPPS_EINVAL;
+        }
+        return launch_fmt<MPPS_FMT_FP8, 64, true>(A_hi, A_lo, Bt_hi, Bt_lo, a_bs, b_bs, lld, n, batch,
+                                                  ep, d_err, st, *mx);
+    }
     // 128 x 64 tiles when 128 x 128 ones would not give every SM two CTAs: the epilogue (FP64
     // block sums) then spreads over twice as many SMs
     const long long tiles128 = (long long)((n + 127) / 128) * ((n + 127) / 128) * batch;
@@ -343,7 +423,6 @@ mpps_status launch_gemm_tc(int fmt, const void* A_hi, const void* A_lo, const vo
             MPPS_TC_CASE(MPPS_FMT_BF16)
             MPPS_TC_CASE(MPPS_FMT_BF16X3)
             MPPS_TC_CASE(MPPS_FMT_TF32)
-            MPPS_TC_CASE(MPPS_FMT_FP8)
 #undef MPPS_TC_CASE
             default:
                 set_error("launch_gemm_tc: unsupported format %d", fmt);

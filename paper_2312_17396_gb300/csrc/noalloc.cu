@@ -86,6 +86,30 @@ extern "C" mpps_status mpps_matmul_noalloc(const double* A, const double* B, dou
     Epilogue ep = epilogue_plain(C, nn);
     if (format == MPPS_FMT_FP64)   // the FP64 product needs no scratch
         return launch_gemm_f64(A, nn, B, nn, n, batch, ep, st);
+    if (format == MPPS_FMT_FP8) {   // block scales along K: FP8 copies, scale codes, exponents
+        const size_t wb = align256(fp8mx_ws_bytes(n, batch));
+        if (wb + 256 > (size_t)MPPS_NOALLOC_SCRATCH_BYTES) {
+            set_error("mpps_matmul_noalloc: n=%d batch=%d format=%d needs %zu bytes of scratch, "
+                      "more than the fixed %zu",
+                      n, batch, format, wb + 256, (size_t)MPPS_NOALLOC_SCRATCH_BYTES);
+            return MPPS_EINVAL;
+        }
+        unsigned char* base = nullptr;
+        mpps_status rc = scratch_address(&base);
+        if (rc) return rc;
+        int* err = (int*)(base + wb);
+        MPPS_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+        if ((rc = launch_product_fp8mx(A, nn, B, nn, n, batch, ep, fp8mx_ws_carve(base, n, batch), err, st)))
+            return rc;
+        int h_err = 0;
+        MPPS_CUDA_TRY(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        MPPS_CUDA_TRY(cudaStreamSynchronize(st));
+        if (h_err) {
+            set_error("a bounded wait in the tensor-core product timed out");
+            return MPPS_ETIMEOUT;
+        }
+        return MPPS_OK;
+    }
 
     // scratch layout: A copy (hi, lo), B^T copy (hi, lo), maxabs a/b, scales a/b, unscale, err
     const int lld = low_ld(n);
@@ -121,8 +145,7 @@ extern "C" mpps_status mpps_matmul_noalloc(const double* A, const double* B, dou
     MPPS_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
     if ((rc = launch_maxabs(A, nn, n, batch, ma, st))) return rc;
     if ((rc = launch_maxabs(B, nn, n, batch, mb, st))) return rc;
-    const int target = format == MPPS_FMT_FP8 ? 8 : 0;
-    if ((rc = launch_pow2_scales(ma, mb, batch, target, sa, sb, un, st))) return rc;
+    if ((rc = launch_pow2_scales(ma, mb, batch, 0, sa, sb, un, st))) return rc;
     if ((rc = launch_convert(format, A, nn, n, batch, ahi, alo, low_bs, lld, sa, false, st))) return rc;
     if ((rc = launch_convert(format, B, nn, n, batch, bhi, blo, low_bs, lld, sb, true, st))) return rc;
     ep.alpha_b = un;

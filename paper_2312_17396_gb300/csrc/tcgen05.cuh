@@ -133,6 +133,54 @@ __host__ __device__ constexpr uint32_t make_idesc(uint32_t ab, uint32_t M, uint3
     return (1u << 4) | (ab << 7) | (ab << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
 }
 
+// Instruction descriptor, kind::mxf8f6f4 with block scales: E4M3 x E4M3 (format code 0 at
+// bits 7-9 and 10-12), both operands K-major, N>>3 at bit 17, M>>4 at bit 24, 8-bit
+// power-of-two scales (UE8M0, bit 23), and which byte of the 32-bit scale words this
+// instruction reads: `sfb` for B (bits 4-5), `sfa` for A (bits 29-30).  D is F32.
+__host__ __device__ constexpr uint32_t make_idesc_mx(uint32_t M, uint32_t N, uint32_t sfa,
+                                                     uint32_t sfb) {
+    return (sfb << 4) | ((N >> 3) << 17) | (1u << 23) | ((M >> 4) << 24) | (sfa << 29);
+}
+
+// D (+)= (A scaled per row and 32-entry K block) x (B scaled per column and K block): the
+// scales sit in TMEM at sfa / sfb (one byte per row / column per block, byte chosen by the
+// descriptor).
+__device__ __forceinline__ void mma_mxf8(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t sfa, uint32_t sfb, uint32_t acc) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::mxf8f6f4.block_scale.scale_vec::1X [%0], %1, %2, %3, [%5], "
+        "[%6], p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc), "r"(sfa), "r"(sfb));
+}
+
+// Copy 32 rows of 16 bytes from shared memory (descriptor `src`) into 4 TMEM columns at
+// taddr, the same 32 rows into each of the four 32-lane quarters.  Asynchronous; ordered
+// before the tcgen05.mma instructions the same thread issues after it.
+__device__ __forceinline__ void tmem_cp_32x128b_x4(uint32_t taddr, uint64_t src) {
+    asm volatile("tcgen05.cp.cta_group::1.32x128b.warpx4 [%0], %1;" ::"r"(taddr), "l"(src)
+                 : "memory");
+}
+
+// Shared-memory matrix descriptor without swizzle, 16-byte rows, 8-row groups 128 B apart
+// (a 32 x 16 B block stored row after row).
+__device__ __forceinline__ uint64_t plain16_desc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(128 >> 4) << 32;     // stride byte offset between 8-row groups
+    d |= (uint64_t)1 << 46;              // descriptor version
+    return d;                            // layout type 0: no swizzle
+}
+
+// Untiled bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16),
+// completing on the mbarrier's transaction count.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"((uint64_t)src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
 __device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
                                          uint32_t acc) {
     asm volatile(

@@ -126,7 +126,8 @@ def test_ps_eval_mixed_vs_fixed(mpps, n, norm):
 @pytest.mark.parametrize("graded", [False, True])
 def test_ps_eval_fp8_steps_row_column_scaled(mpps, n, graded):
     # A loose target lets the planner put the high-order Horner steps in FP8; those products
-    # scale each row of P_i and each column of Y by its own power of two.  A diagonally
+    # scale each row of P_i and each column of Y by its own power of two (and every 32 entries
+    # along K by a block scale).  A diagonally
     # similar matrix D G D^-1 (D spanning 2^12) gives rows and columns of very different
     # magnitude.  The normwise result must stay within the target's bound.
     m, tol = 30, 2.0 ** -30
