@@ -769,6 +769,7 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
     Arena L;
     double *d_coef, *pw, *Pb0, *Pb1, *partial, *norms, *d_anorm, *tmpT = nullptr, *d_pnorm = nullptr;
     int *d_sigma, *d_err, *d_bidx, *eA = nullptr, *eB = nullptr, *eY = nullptr, *eT = nullptr;
+    int* d_redo = nullptr;   // general X: matrices whose FP32 block norms are recomputed in FP64
     __nv_bfloat16 *slA = nullptr, *slB = nullptr, *slY = nullptr, *slT = nullptr;
     char* split = nullptr;   // split-K scratch of the emulated products
     DevPlan* d_plan = nullptr;                      // device plan (dp)
@@ -791,6 +792,7 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
         d_anorm = a.take<double>(batch);
         d_sigma = a.take<int>(batch);
         d_bidx = a.take<int>((size_t)batch * 64);
+        d_redo = expm ? nullptr : a.take<int>(batch);
         if (K > 0) {
             slA = a.take<__nv_bfloat16>(f64e_plane_elems(n, batch, K));
             slB = a.take<__nv_bfloat16>(f64e_plane_elems(n, batch, K));
@@ -940,10 +942,10 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
         for (;;) {
             q = block_norms_count(m, s);
             r = m / s;
-            if (expm)
-                rc = launch_block_norms_f32(pw, pw_bs, n, batch, s, m, coeffs, partial, norms, st);
-            else
-                rc = launch_block_norms(pw, pw_bs, n, batch, s, m, d_coef, partial, norms, st);
+            rc = launch_block_norms_f32(pw, pw_bs, n, batch, s, m, coeffs, partial, norms, st);
+            if (!rc && !expm)
+                rc = launch_block_norms_redo(pw, pw_bs, n, batch, s, m, d_coef, partial, norms,
+                                             d_redo, st);
             if (rc) return rc;
             std::vector<double> h((size_t)batch * q);
             MPPS_CUDA_TRY(cudaMemcpyAsync(h.data(), norms, sizeof(double) * h.size(),
@@ -966,14 +968,12 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
         q = block_norms_count(m, s);
     }
 
-    // ---- a3: ||B_i||_1, ||Y||_1, ||X||_1
-    // ||X||_1 <= 1 after the scaling of exp: FP32 sums suffice for the precision rule
-    // (the paper notes the norms are only needed to the right order of magnitude)
-    if (expm)
-        rc = launch_block_norms_f32(pw, pw_bs, n, batch, s, m, coeffs, partial, norms, st,
-                                    ex_pn > 0);
-    else
-        rc = launch_block_norms(pw, pw_bs, n, batch, s, m, d_coef, partial, norms, st);
+    // ---- a3: ||B_i||_1, ||Y||_1, ||X||_1 in FP32: the rule needs them only to the right
+    // order of magnitude (Section 3.3).  ||X||_1 <= 1 after the scaling of exp; for a general
+    // X the matrices whose FP32 norms are not finite get FP64 ones
+    rc = launch_block_norms_f32(pw, pw_bs, n, batch, s, m, coeffs, partial, norms, st, ex_pn > 0);
+    if (!rc && !expm)
+        rc = launch_block_norms_redo(pw, pw_bs, n, batch, s, m, d_coef, partial, norms, d_redo, st);
     if (rc) return rc;
     // mixed powers: ||X^j||_1 of the chain powers X^2..X^h ([j-1][batch]; ||X|| and ||Y||
     // come with the block norms), when the block-norm pass did not give them

@@ -463,14 +463,16 @@ inline int low_ld(int n) { return (n + 63) / 64 * 64; }
 // out = ep.alpha * extra + sum_j ep.coef[j] X_j  (extra may be null: treated as 0).
 mpps_status launch_combine(int n, int batch, const double* extra, long long extra_bs,
                            const Epilogue& ep, cudaStream_t st);
-// ||B_i||_1 (i = 0..r), ||X^s||_1, ||X||_1 per matrix from the power table pw (X_1..X_s,
-// batch stride pw_bs) and the device copy of the coefficients b_0..b_m.  partial must hold
-// block_norms_partial_elems(...) doubles; norms gets block_norms_count(m, s) per matrix.
+// ||B_i||_1 (i = 0..r), ||X^s||_1, ||X||_1 per matrix: block_norms_count(m, s) values per
+// matrix; the FP64 kernels' partial sums need block_norms_partial_elems(...) doubles.
 int block_norms_count(int m, int s);
 size_t block_norms_partial_elems(int n, int batch, int m, int s);
-mpps_status launch_block_norms(const double* pw, long long pw_bs, int n, int batch, int s,
-                               int m, const double* d_coeffs, double* partial, double* norms,
-                               cudaStream_t st);
+// After launch_block_norms_f32 on a general X: the matrices with a norm that is not finite
+// (a power entry or a sum beyond FP32's range) get their norms recomputed in FP64 (redo:
+// batch flags, scratch).
+mpps_status launch_block_norms_redo(const double* pw, long long pw_bs, int n, int batch, int s,
+                                    int m, const double* d_coeffs, double* partial, double* norms,
+                                    int* redo, cudaStream_t st);
 // The same norms in FP32 arithmetic, valid when ||X||_1 <= 1 (the scaled argument of exp):
 // the block sums only steer the precision rule and the operand scales, where a relative
 // error of 2^-20 is immaterial.  coeffs is the host array b_0..b_m.

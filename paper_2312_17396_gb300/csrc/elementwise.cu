@@ -35,12 +35,12 @@ __device__ __forceinline__ double block_max(double v) {
 // B_i = sum_{j=0}^{top_i} b_{si+j} X_j, top_i = s-1 (i < r), m - s r (i = r); X_0 = I.
 __global__ void k_block_norms_partial(const double* __restrict__ pw, long long pw_bs, int n,
                                       int s, int m, const double* __restrict__ coef,
-                                      double* __restrict__ partial) {
+                                      double* __restrict__ partial, const int* __restrict__ only) {
     pdl_wait();
     const int col = blockIdx.x * kColsPerBlock + threadIdx.x;
     const int chunk = blockIdx.y, chunks = gridDim.y, b = blockIdx.z;
     const int r = m / s, q = r + 3;
-    if (col >= n) return;
+    if (col >= n || (only && !__ldg(only + b))) return;
     double acc[MPPS_MAX_R + 3];
     double x[MPPS_MAX_S + 1];
     for (int t = 0; t < q; ++t) acc[t] = 0.0;
@@ -65,10 +65,11 @@ __global__ void k_block_norms_partial(const double* __restrict__ pw, long long p
 
 // norms[b*q + t] = max_col sum_chunk partial[b][chunk][t][col]  (fixed summation order).
 __global__ void k_norms_finalize(const double* __restrict__ partial, int n, int chunks, int q,
-                                 double* __restrict__ norms) {
+                                 double* __restrict__ norms, const int* __restrict__ only) {
     pdl_wait();
     pdl_trigger();
     const int t = blockIdx.x, b = blockIdx.y;
+    if (only && !__ldg(only + b)) return;
     double best = 0.0;
     for (int col = threadIdx.x; col < n; col += blockDim.x) {
         double sum = 0.0;
@@ -154,9 +155,11 @@ struct NormCoefs {
     float c[(MPPS_MAX_R + 1) * MPPS_MAX_S];   // b_{is+j} / scale_i
 };
 
-// Block norms in FP32 for ||X||_1 <= 1 (every power entry is at most 1 in magnitude):
-// coefficients come normalised per block (|c| <= 1), so nothing overflows; entries that
-// underflow are negligible against the block's norm.  Partial sums in 16-row chunks.
+// Block norms in FP32: coefficients come normalised per block (|c| <= 1); for exp (||X||_1 <=
+// 1, every power entry at most 1 in magnitude) nothing overflows, and entries that underflow
+// are negligible against the block's norm.  For a general X a power entry or a sum beyond
+// FP32's range gives an infinite norm, which launch_block_norms_redo recomputes in FP64.
+// Partial sums in 16-row chunks.
 __global__ void k_block_norms_partial_f32(const double* __restrict__ pw, long long pw_bs, int n,
                                           int s, int m, NormCoefs cf,
                                           double* __restrict__ partial) {
@@ -803,16 +806,33 @@ mpps_status launch_block_norms_f32(const double* pw, long long pw_bs, int n, int
     return MPPS_OK;
 }
 
-mpps_status launch_block_norms(const double* pw, long long pw_bs, int n, int batch, int s, int m,
-                               const double* d_coeffs, double* partial, double* norms,
-                               cudaStream_t st) {
+// redo[b] = 1 when a norm of matrix b is not finite (its FP32 block norms met an entry or a
+// sum beyond FP32's range, or the input holds a NaN or an infinity).
+__global__ void k_norms_redo_flags(const double* __restrict__ norms, int q, int batch,
+                                   int* __restrict__ redo) {
+    pdl_wait();
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= batch) return;
+    int f = 0;
+    for (int t = 0; t < q; ++t) f |= isfinite(norms[(long long)b * q + t]) ? 0 : 1;
+    redo[b] = f;
+}
+
+mpps_status launch_block_norms_redo(const double* pw, long long pw_bs, int n, int batch, int s,
+                                    int m, const double* d_coeffs, double* partial, double* norms,
+                                    int* redo, cudaStream_t st) {
     ProfScope prof(MPPS_PROF_ELEMENTWISE, st);
     const int chunks = (n + kRowsPerChunk - 1) / kRowsPerChunk;
     const int q = block_norms_count(m, s);
-    dim3 g((n + kColsPerBlock - 1) / kColsPerBlock, chunks, batch);
-    MPPS_CUDA_TRY(launch_pdl(k_block_norms_partial, dim3(g), dim3(kColsPerBlock), 0, st, pw, pw_bs, n, s, m, d_coeffs, partial));
+    MPPS_CUDA_TRY(launch_pdl(k_norms_redo_flags, dim3((batch + 127) / 128), dim3(128), 0, st,
+                             (const double*)norms, q, batch, redo));
     MPPS_LAUNCH_CHECK();
-    MPPS_CUDA_TRY(launch_pdl(k_norms_finalize, dim3(dim3(q, batch)), dim3(256), 0, st, partial, n, chunks, q, norms));
+    dim3 g((n + kColsPerBlock - 1) / kColsPerBlock, chunks, batch);
+    MPPS_CUDA_TRY(launch_pdl(k_block_norms_partial, dim3(g), dim3(kColsPerBlock), 0, st, pw, pw_bs, n, s, m, d_coeffs, partial,
+                             (const int*)redo));
+    MPPS_LAUNCH_CHECK();
+    MPPS_CUDA_TRY(launch_pdl(k_norms_finalize, dim3(dim3(q, batch)), dim3(256), 0, st, partial, n, chunks, q, norms,
+                             (const int*)redo));
     MPPS_LAUNCH_CHECK();
     return MPPS_OK;
 }
