@@ -406,6 +406,15 @@ mpps_status mpps_matmul(const double* A, const double* B, double* C, int n, int 
                         int format, void* stream);
 
 /*
+ * C = A^T B, otherwise as mpps_matmul (the transposed products of the reverse passes, exposed
+ * with the same formats).  The emulated formats slice A's columns directly as the rows of the
+ * left operand (no transpose is formed; the same slices as those of the rows of A^T, so the
+ * result equals mpps_matmul of A^T and B bit for bit); the other formats transpose A first.
+ */
+mpps_status mpps_matmul_ta(const double* A, const double* B, double* C, int n, int batch,
+                           int format, void* stream);
+
+/*
  * mpps_matmul_noalloc -- mpps_matmul for callers that may not allocate device memory.
  * (The paper has no counterpart: this is a deployment variant of the product above.)
  * Some callers cannot let a library allocate: code running beside a framework whose

@@ -90,7 +90,8 @@ EXPORTS = ("mpps_policy_default", "mpps_plan", "ps_eval", "expm_taylor_ss", "ps_
            "expm_taylor_ss_adjoint", "mpps_choose_s", "mpps_autotune_enable",
            "mpps_autotune_clear", "mpps_autotune_entries", "expm_pade13", "mpps_plan_adjoint",
            "ps_eval_tape_bytes", "ps_eval_forward_tape", "ps_eval_adjoint_tape",
-           "ps_eval_adjoint_f32", "ps_eval_grouped", "lu_solve", "mpps_plan_powers")
+           "ps_eval_adjoint_f32", "ps_eval_grouped", "lu_solve", "mpps_plan_powers",
+           "mpps_matmul_ta")
 STORAGE_F64, STORAGE_F32 = 0, 1
 PROF_GEMM_F64, PROF_GEMM_TC, PROF_ELEMENTWISE, PROF_GEMM_F64E, PROF_SLICE = 0, 1, 2, 3, 4
 
@@ -143,6 +144,8 @@ def lib():
         L.mpps_autotune_entries.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.c_int]
         L.mpps_autotune_entries.restype = ctypes.c_int
         L.mpps_matmul.argtypes = [vp, vp, vp, ip, ip, ip, vp]
+        L.mpps_matmul_ta.argtypes = [vp, vp, vp, ip, ip, ip, vp]
+        L.mpps_matmul_ta.restype = ctypes.c_int
         L.mpps_matmul_noalloc.argtypes = [vp, vp, vp, ip, ip, ip, vp]
         L.mpps_matmul_noalloc.restype = ctypes.c_int
         L.expm_taylor_ss_grouped.argtypes = [ctypes.POINTER(_GroupItem), ip, ctypes.POINTER(_Policy),
@@ -657,6 +660,21 @@ def matmul(A, B, fmt="fp64", out=None, stream=None):
     optr, _, _, _, _ = _prep(out, "out")
     _check(lib().mpps_matmul(ctypes.c_void_p(ptr), ctypes.c_void_p(bptr), ctypes.c_void_p(optr),
                              n, batch, f, _stream_for(kind, stream)))
+    return out
+
+
+def matmul_ta(A, B, fmt="fp64", out=None, stream=None):
+    """C = A^T B with the product computed in format `fmt` (mpps_matmul_ta)."""
+    f = _FMT_BY_NAME[fmt] if isinstance(fmt, str) else int(fmt)
+    ptr, batch, n, kind, keep = _prep(A, "A")
+    bptr, bb, bn, _, _ = _prep(B, "B")
+    if (bb, bn) != (batch, n):
+        raise ValueError("B must have the shape of A")
+    if out is None:
+        out = _empty_like(A, keep)
+    optr, _, _, _, _ = _prep(out, "out")
+    _check(lib().mpps_matmul_ta(ctypes.c_void_p(ptr), ctypes.c_void_p(bptr), ctypes.c_void_p(optr),
+                                n, batch, f, _stream_for(kind, stream)))
     return out
 
 

@@ -1847,27 +1847,36 @@ mpps_status ps_eval_grouped(const mpps_poly_item* items, int count, const mpps_p
     return grouped_eval(g.data(), count, policy, rep, (cudaStream_t)stream, false);
 }
 
-mpps_status mpps_matmul(const double* A, const double* B, double* C, int n, int batch, int format,
-                        void* stream) {
+// C = op(A) B, op(A) = A or (trans_a) A^T: the emulated formats slice A's columns as the A
+// operand; the others form the transpose first.
+static mpps_status matmul_impl(const char* fn, const double* A, const double* B, double* C, int n,
+                               int batch, int format, bool trans_a, void* stream) {
     clear_error();
     mpps_status rc = check_sizes(n, batch);
     if (rc) return rc;
     if (!(format >= MPPS_FMT_FP64 && format <= MPPS_FMT_FP8) && !MPPS_FMT_IS_F64E(format)) {
-        set_error("mpps_matmul: invalid format %d", format);
+        set_error("%s: invalid format %d", fn, format);
         return MPPS_EINVAL;
     }
     if (batch == 0) return MPPS_OK;
     if (!A || !B || !C) {
-        set_error("mpps_matmul: null matrix pointer");
+        set_error("%s: null matrix pointer", fn);
         return MPPS_EINVAL;
     }
-    if ((rc = check_same_device("mpps_matmul", {A, B, C}))) return rc;
+    if ((rc = check_same_device(fn, {A, B, C}))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     const long long nn = (long long)n * n;
     const size_t elems = (size_t)batch * nn;
     Staged a, b;
     if ((rc = stage_in(A, elems, st, a))) return rc;
     if ((rc = stage_in(B, elems, st, b))) return rc;
+    const bool slice_t = trans_a && MPPS_FMT_IS_F64E(format);
+    DevBuf tbuf;
+    if (trans_a && !slice_t) {   // the other formats take A^T formed explicitly
+        if ((rc = tbuf.alloc(elems * sizeof(double), st))) return rc;
+        if ((rc = launch_transpose(a.dev, nn, (double*)tbuf.p, n, batch, st))) return rc;
+        a.dev = (double*)tbuf.p;
+    }
     const bool c_dev = is_device_ptr(C);
     DevBuf cb;
     double* dC = C;
@@ -1903,7 +1912,10 @@ mpps_status mpps_matmul(const double* A, const double* B, double* C, int n, int 
         lay(L);
         MPPS_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
         MPPS_CUDA_TRY(cudaMemsetAsync(split, 0, f64e_split_flag_bytes(), st));
-        if ((rc = launch_slice_rows(a.dev, nn, n, batch, k, sa, ea, st))) return rc;
+        if ((rc = slice_t ? launch_slice_cols_a(a.dev, nn, n, batch, k, sa, ea,
+                                                (unsigned long long*)bt, st)
+                          : launch_slice_rows(a.dev, nn, n, batch, k, sa, ea, st)))
+            return rc;
         if ((rc = launch_slice_cols(b.dev, nn, n, batch, k, sb, eb, (unsigned long long*)bt, st)))
             return rc;
         if ((rc = launch_gemm_f64e(k, sa, k, ea, sb, k, eb, n, batch, batch, ep, err, st, nullptr,
@@ -1989,6 +2001,16 @@ mpps_status mpps_matmul(const double* A, const double* B, double* C, int n, int 
     return MPPS_OK;
 }
 
+mpps_status mpps_matmul(const double* A, const double* B, double* C, int n, int batch, int format,
+                        void* stream) {
+    return matmul_impl("mpps_matmul", A, B, C, n, batch, format, false, stream);
+}
+
+mpps_status mpps_matmul_ta(const double* A, const double* B, double* C, int n, int batch,
+                           int format, void* stream) {
+    return matmul_impl("mpps_matmul_ta", A, B, C, n, batch, format, true, stream);
+}
+
 }  // extern "C"
 
 namespace mpps {
@@ -2066,18 +2088,35 @@ struct ProductWs {
 // F64E(k) from exact slices of the rows of A and the columns of B, or a low-precision
 // tensor-core product of A and B each scaled by a power of two from its largest entry
 // (the building block mpps_matmul offers, used here with an epilogue).
+// B's column slices made once for several emulated products with the same B (`planes`
+// slices: any product of at most that many uses their leading planes).
+struct SlicedB {
+    const __nv_bfloat16* pl = nullptr;
+    const int* e = nullptr;
+    int planes = 0;
+};
+
+// a_t (emulated formats only): the A operand is A^T, sliced from A's columns.
 static mpps_status product_fmt(int fmt, const double* A, long long a_bs, const double* B,
                                long long b_bs, int n, int batch, Epilogue ep, ProductWs& w,
-                               int* d_err, cudaStream_t st) {
+                               int* d_err, cudaStream_t st, const SlicedB* preB = nullptr,
+                               bool a_t = false) {
     const long long nn = (long long)n * n;
+    if (a_t && !MPPS_FMT_IS_F64E(fmt)) {
+        set_error("product_fmt: a transposed A operand needs an emulated format");
+        return MPPS_EINVAL;
+    }
     if (fmt == MPPS_FMT_FP64) return launch_gemm_f64(A, a_bs, B, b_bs, n, batch, ep, st);
     if (MPPS_FMT_IS_F64E(fmt)) {
         const int k = MPPS_F64E_SLICES(fmt);
-        mpps_status rc = launch_slice_rows(A, a_bs, n, batch, k, w.slA, w.eA, st);
-        if (!rc) rc = launch_slice_cols(B, b_bs, n, batch, k, w.slB, w.eB, w.cmx, st);
+        const bool pre = preB && preB->pl && preB->planes >= k;
+        mpps_status rc = a_t ? launch_slice_cols_a(A, a_bs, n, batch, k, w.slA, w.eA, w.cmx, st)
+                             : launch_slice_rows(A, a_bs, n, batch, k, w.slA, w.eA, st);
+        if (!rc && !pre) rc = launch_slice_cols(B, b_bs, n, batch, k, w.slB, w.eB, w.cmx, st);
         if (!rc)
-            rc = launch_gemm_f64e(k, w.slA, k, w.eA, w.slB, k, w.eB, n, batch, batch, ep, d_err, st,
-                                  nullptr, w.split);
+            rc = launch_gemm_f64e(k, w.slA, k, w.eA, pre ? preB->pl : w.slB, pre ? preB->planes : k,
+                                  pre ? preB->e : w.eB, n, batch, batch, ep, d_err, st, nullptr,
+                                  w.split);
         return rc;
     }
     if (!is_low(fmt) || !w.ahi) {
@@ -2195,8 +2234,15 @@ static mpps_status adjoint_tape_dev(const double* coeffs, int m, const char* tap
             if (MPPS_FMT_IS_F64E(f)) kmax = std::max(kmax, MPPS_F64E_SLICES(f));
         }
     }
+    // Y^T and X_1^T are the B operand of every reverse step and of every power's adjoint:
+    // emulated products slice their columns once
+    bool rev_f64e = false;
+    for (int i = 1; i <= r; ++i) rev_f64e = rev_f64e || MPPS_FMT_IS_F64E(h.fmt_adj[i]);
+    const bool pow_f64e = MPPS_FMT_IS_F64E(wp);
     Arena Z;
     double *xbar, *Ybar, *Pbar0, *Pbar1, *Yt, *X1t, *T;
+    __nv_bfloat16 *plYt = nullptr, *plX1t = nullptr;
+    int *eYt = nullptr, *eX1t = nullptr;
     ProductWs w;
     auto lay = [&](Arena& z) {
         xbar = z.take<double>((size_t)batch * pw_bs);
@@ -2206,6 +2252,14 @@ static mpps_status adjoint_tape_dev(const double* coeffs, int m, const char* tap
         Yt = z.take<double>(elems);
         X1t = z.take<double>(elems);
         T = z.take<double>(elems);
+        if (rev_f64e) {
+            plYt = z.take<__nv_bfloat16>(f64e_plane_elems(n, batch, kmax));
+            eYt = z.take<int>((size_t)batch * n);
+        }
+        if (pow_f64e) {
+            plX1t = z.take<__nv_bfloat16>(f64e_plane_elems(n, batch, kmax));
+            eX1t = z.take<int>((size_t)batch * n);
+        }
         w = ProductWs();
         w.take(z, n, batch, kmax, any_low);
     };
@@ -2221,8 +2275,9 @@ static mpps_status adjoint_tape_dev(const double* coeffs, int m, const char* tap
     if ((rc = dev_err_get(&derr))) return rc;
     if ((rc = dev_err_check(derr, false))) return rc;
     auto product = [&](int fmt, const double* Am, long long a_bs, const double* Bm, long long b_bs,
-                       const Epilogue& ep) -> mpps_status {
-        return product_fmt(fmt, Am, a_bs, Bm, b_bs, n, batch, ep, w, derr->d, st);
+                       const Epilogue& ep, const SlicedB* preB = nullptr,
+                       bool a_t = false) -> mpps_status {
+        return product_fmt(fmt, Am, a_bs, Bm, b_bs, n, batch, ep, w, derr->d, st, preB, a_t);
     };
     auto slotp = [&](int k) { return Pst + (size_t)k * batch * nn; };
     std::vector<double*> loc(r + 1, nullptr);   // where P_j is held now
@@ -2258,6 +2313,15 @@ static mpps_status adjoint_tape_dev(const double* coeffs, int m, const char* tap
     if ((rc = launch_transpose(T, nn, Yt, n, batch, st))) return rc;
     if ((rc = launch_scale_copy(pw, pw_bs, T, nn, n, batch, nullptr, st))) return rc;
     if ((rc = launch_transpose(T, nn, X1t, n, batch, st))) return rc;
+    SlicedB sYt, sX1t;
+    if (rev_f64e) {
+        if ((rc = launch_slice_cols(Yt, nn, n, batch, kmax, plYt, eYt, w.cmx, st))) return rc;
+        sYt.pl = plYt; sYt.e = eYt; sYt.planes = kmax;
+    }
+    if (pow_f64e) {
+        if ((rc = launch_slice_cols(X1t, nn, n, batch, kmax, plX1t, eX1t, w.cmx, st))) return rc;
+        sX1t.pl = plX1t; sX1t.e = eX1t; sX1t.planes = kmax;
+    }
     double* Pbar[2] = {Pbar0, Pbar1};
     if ((rc = launch_scale_copy(dG, nn, Pbar[0], nn, n, batch, nullptr, st))) return rc;
     int cur = 0;
@@ -2278,16 +2342,20 @@ static mpps_status adjoint_tape_dev(const double* coeffs, int m, const char* tap
         // Ybar += P_i^T Pbar_{i-1}
         double* Pi = P_at(i, &rc);
         if (rc) return rc;
-        if ((rc = launch_transpose(Pi, nn, T, n, batch, st))) return rc;
         {
             Epilogue ep = epilogue_plain(Ybar, nn);
             ep.add = Ybar; ep.add_bstride = nn; ep.add_coef = 1.0;
-            if ((rc = product(h.fmt_adj[i], T, nn, Pbar[cur], nn, ep))) return rc;
+            if (MPPS_FMT_IS_F64E(h.fmt_adj[i])) {   // P_i^T sliced from P_i's columns
+                if ((rc = product(h.fmt_adj[i], Pi, nn, Pbar[cur], nn, ep, nullptr, true))) return rc;
+            } else {
+                if ((rc = launch_transpose(Pi, nn, T, n, batch, st))) return rc;
+                if ((rc = product(h.fmt_adj[i], T, nn, Pbar[cur], nn, ep))) return rc;
+            }
         }
         // Pbar_i = Pbar_{i-1} Y^T
         {
             Epilogue ep = epilogue_plain(Pbar[cur ^ 1], nn);
-            if ((rc = product(h.fmt_adj[i], Pbar[cur], nn, Yt, nn, ep))) return rc;
+            if ((rc = product(h.fmt_adj[i], Pbar[cur], nn, Yt, nn, ep, &sYt))) return rc;
         }
         cur ^= 1;
     }
@@ -2311,14 +2379,19 @@ static mpps_status adjoint_tape_dev(const double* coeffs, int m, const char* tap
         // Xbar_{j-1} += Xbar_j X_1^T
         Epilogue e1 = epilogue_plain(xjm, pw_bs);
         e1.add = xjm; e1.add_bstride = pw_bs; e1.add_coef = 1.0;
-        if ((rc = product(wp, xj, pw_bs, X1t, nn, e1))) return rc;
+        if ((rc = product(wp, xj, pw_bs, X1t, nn, e1, &sX1t))) return rc;
         // Xbar_1 += X_{j-1}^T Xbar_j
-        if ((rc = launch_scale_copy(pw + (long long)(j - 2) * nn, pw_bs, T, nn, n, batch, nullptr, st)))
-            return rc;
-        if ((rc = launch_transpose(T, nn, Pbar0, n, batch, st))) return rc;
         Epilogue e2 = epilogue_plain(xbar, pw_bs);
         e2.add = xbar; e2.add_bstride = pw_bs; e2.add_coef = 1.0;
-        if ((rc = product(wp, Pbar0, nn, xj, pw_bs, e2))) return rc;
+        if (pow_f64e) {   // X_{j-1}^T sliced from the power table's columns
+            if ((rc = product(wp, pw + (long long)(j - 2) * nn, pw_bs, xj, pw_bs, e2, nullptr, true)))
+                return rc;
+        } else {
+            if ((rc = launch_scale_copy(pw + (long long)(j - 2) * nn, pw_bs, T, nn, n, batch, nullptr, st)))
+                return rc;
+            if ((rc = launch_transpose(T, nn, Pbar0, n, batch, st))) return rc;
+            if ((rc = product(wp, Pbar0, nn, xj, pw_bs, e2))) return rc;
+        }
     }
     if ((rc = launch_scale_copy(xbar, pw_bs, dGrad, nn, n, batch, nullptr, st))) return rc;
     return dev_err_enqueue(derr, st);

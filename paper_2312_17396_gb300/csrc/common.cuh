@@ -382,6 +382,10 @@ size_t f64e_plane_elems(int n, int batch, int k);
 // gate (device, optional): the device plan's count; 0 = the launch does nothing.
 mpps_status launch_slice_rows(const double* M, long long bs, int n, int batch, int k, void* planes,
                               int* exps, cudaStream_t st, const int* gate = nullptr);
+// Column slices of M in the A operand's layout (the A operand M^T, no transpose formed),
+// with per-column exponents; colmax: batch * n scratch words.
+mpps_status launch_slice_cols_a(const double* M, long long bs, int n, int batch, int k, void* planes,
+                                int* exps, unsigned long long* colmax, cudaStream_t st);
 // Column slices of M written as rows of the B^T planes; colmax: batch * n scratch words.
 mpps_status launch_slice_cols(const double* M, long long bs, int n, int batch, int k, void* planes,
                               int* exps, unsigned long long* colmax, cudaStream_t st,

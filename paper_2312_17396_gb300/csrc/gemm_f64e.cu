@@ -572,6 +572,43 @@ __global__ void __launch_bounds__(256) k_slice_cols(const double* __restrict__ M
     }
 }
 
+// Slices of M's columns in the A operand's pair layout (plane row c = column c of M): the A
+// operand M^T without forming the transpose.  e_c from colmax; the K positions n .. n32 get
+// zero digits, as the row slicers write them.  64 x 32 transposing tiles (32 x 8 threads),
+// two digits per 4-byte store.
+template <int KS>
+__global__ void __launch_bounds__(256) k_slice_cols_a(const double* __restrict__ M, long long bs,
+                                                      int n, long long goff,
+                                                      const unsigned long long* __restrict__ colmax,
+                                                      __nv_bfloat16* __restrict__ planes,
+                                                      long long plane_bs, int lld,
+                                                      int* __restrict__ exps) {
+    pdl_wait();
+    pdl_trigger();
+    __shared__ double tile[32][65];
+    const int b = blockIdx.z, r0 = blockIdx.y * 64, c0 = blockIdx.x * 32;
+    const double* src = M + (long long)b * bs;
+    for (int i = threadIdx.y; i < 64; i += blockDim.y) {
+        const int row = r0 + i, col = c0 + threadIdx.x;
+        tile[threadIdx.x][i] = (row < n && col < n) ? src[(long long)row * n + col] : 0.0;
+    }
+    __syncthreads();
+    const int n32 = (n + KB - 1) / KB * KB;
+    const long long pstride = (long long)n * 2 * lld;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int col = c0 + i, k0 = r0 + 2 * threadIdx.x;   // plane row col, K k0 and k0 + 1
+        if (col >= n || k0 >= n32) continue;
+        const int e = exp_above(colmax[(long long)b * n + col]);
+        if (blockIdx.y == 0 && threadIdx.x == 0) exps[(long long)b * n + col] = e;
+        const long long G0 = scaled_int_fp64(tile[i][2 * threadIdx.x], e) + goff;
+        const long long G1 = scaled_int_fp64(tile[i][2 * threadIdx.x + 1], e) + goff;   // 0 past n
+        __nv_bfloat16* dst = planes + (long long)b * plane_bs + (long long)col * 2 * lld + kpos(k0);
+#pragma unroll
+        for (int t = 0; t < KS; ++t)
+            *reinterpret_cast<unsigned*>(dst + slice_off(t, pstride)) = digit_pair(G0, G1, t);
+    }
+}
+
 // w 2^s rounded to the nearest double (ties to even) on the integer pipe, for |w| < 2^62;
 // false (and *out untouched) when the result would not be a normal double.  The magnitude is
 // normalised so that its top bit sits at bit 62 (bit 0 is then zero: |w| < 2^62 shifts by at
@@ -1352,7 +1389,44 @@ mpps_status slice_cols_k(const double* M, long long bs, int n, int batch, __nv_b
     return MPPS_OK;
 }
 
+template <int KS>
+mpps_status slice_cols_a_k(const double* M, long long bs, int n, int batch, __nv_bfloat16* pl,
+                           int* exps, const unsigned long long* colmax, cudaStream_t st) {
+    const int lld = low_ld(n);
+    const int n32 = (n + KB - 1) / KB * KB;
+    MPPS_CUDA_TRY(launch_pdl(k_slice_cols_a<KS>, dim3((n + 31) / 32, (n32 + 63) / 64, batch), dim3(32, 8), 0, st,
+                             M, bs, n, digit_offset(KS), colmax, pl,
+                             (long long)num_pairs(KS) * n * 2 * lld, lld, exps));
+    MPPS_LAUNCH_CHECK();
+    return MPPS_OK;
+}
+
 }  // namespace
+
+mpps_status launch_slice_cols_a(const double* M, long long bs, int n, int batch, int k, void* planes,
+                                int* exps, unsigned long long* colmax, cudaStream_t st) {
+    k = f64e_planes(k);
+    ProfScope prof(MPPS_PROF_SLICE, st);
+    if (batch > 65535) {
+        set_error("slice_cols_a: batch %d exceeds the grid limit", batch);
+        return MPPS_EINVAL;
+    }
+    MPPS_CUDA_TRY(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * (size_t)batch * n, st));
+    MPPS_CUDA_TRY(launch_pdl(k_colmax, dim3(dim3((n + 127) / 128, (n + 15) / 16, batch)), dim3(128), 0, st, M, bs, n, colmax,
+                             (const int*)nullptr));
+    MPPS_LAUNCH_CHECK();
+    __nv_bfloat16* pl = (__nv_bfloat16*)planes;
+    switch (k) {
+        case 1: return slice_cols_a_k<1>(M, bs, n, batch, pl, exps, colmax, st);
+        case 2: return slice_cols_a_k<2>(M, bs, n, batch, pl, exps, colmax, st);
+        case 3: return slice_cols_a_k<3>(M, bs, n, batch, pl, exps, colmax, st);
+        case 4: return slice_cols_a_k<4>(M, bs, n, batch, pl, exps, colmax, st);
+        case 5: return slice_cols_a_k<5>(M, bs, n, batch, pl, exps, colmax, st);
+        case 6: return slice_cols_a_k<6>(M, bs, n, batch, pl, exps, colmax, st);
+        case 7: return slice_cols_a_k<7>(M, bs, n, batch, pl, exps, colmax, st);
+        default: return slice_cols_a_k<8>(M, bs, n, batch, pl, exps, colmax, st);
+    }
+}
 
 mpps_status launch_slice_rows(const double* M, long long bs, int n, int batch, int k, void* planes,
                               int* exps, cudaStream_t st, const int* gate) {
