@@ -2306,13 +2306,10 @@ static mpps_status adjoint_tape_dev(const double* coeffs, int m, const char* tap
         }
         return loc[i];
     };
-    MPPS_CUDA_TRY(cudaMemsetAsync(xbar, 0, sizeof(double) * batch * pw_bs, st));
     MPPS_CUDA_TRY(cudaMemsetAsync(Ybar, 0, elems * sizeof(double), st));
-    // Y^T and X_1^T (strided power table -> contiguous copies first)
-    if ((rc = launch_scale_copy(Y, pw_bs, T, nn, n, batch, nullptr, st))) return rc;
-    if ((rc = launch_transpose(T, nn, Yt, n, batch, st))) return rc;
-    if ((rc = launch_scale_copy(pw, pw_bs, T, nn, n, batch, nullptr, st))) return rc;
-    if ((rc = launch_transpose(T, nn, X1t, n, batch, st))) return rc;
+    // Y^T and X_1^T, transposed from the strided power table
+    if ((rc = launch_transpose(Y, pw_bs, Yt, n, batch, st))) return rc;
+    if ((rc = launch_transpose(pw, pw_bs, X1t, n, batch, st))) return rc;
     SlicedB sYt, sX1t;
     if (rev_f64e) {
         if ((rc = launch_slice_cols(Yt, nn, n, batch, kmax, plYt, eYt, w.cmx, st))) return rc;
@@ -2322,21 +2319,22 @@ static mpps_status adjoint_tape_dev(const double* coeffs, int m, const char* tap
         if ((rc = launch_slice_cols(X1t, nn, n, batch, kmax, plX1t, eX1t, w.cmx, st))) return rc;
         sX1t.pl = plX1t; sX1t.e = eX1t; sX1t.planes = kmax;
     }
-    double* Pbar[2] = {Pbar0, Pbar1};
-    if ((rc = launch_scale_copy(dG, nn, Pbar[0], nn, n, batch, nullptr, st))) return rc;
-    int cur = 0;
+    // Pbar_0 = G (read only); Pbar_1, Pbar_2, ... alternate between two buffers
+    MPPS_CUDA_TRY(cudaMemsetAsync(xbar, 0, sizeof(double) * batch * pw_bs, st));
+    const double* pc = dG;
+    bool folded = false;
     for (int i = 1; i <= r; ++i) {
-        // Bbar_{i-1} = Pbar_{i-1}: Xbar_j += b_{(i-1)s+j} Pbar for j = 1..s-1
+        // Bbar_{i-1} = Pbar_{i-1}: Xbar_j += b_{(i-1)s+j} Pbar_{i-1} for j = 1..s-1
         double c[MPPS_MAX_S + 1];
         for (int j = 0; j < s; ++j) c[j] = coeffs[(i - 1) * s + j];
-        if ((rc = launch_axpy_blocks(xbar, pw_bs, n, batch, s - 1, c, Pbar[cur], nn, st))) return rc;
+        if ((rc = launch_axpy_blocks(xbar, pw_bs, n, batch, s - 1, c, pc, nn, st))) return rc;
         if (fold && i == r) {
             // P_r = b_m I: Ybar += b_m Pbar_{r-1}
             Epilogue ep = epilogue_plain(Ybar, nn);
             ep.alpha = coeffs[m];
             ep.add = Ybar; ep.add_bstride = nn; ep.add_coef = 1.0;
-            if ((rc = launch_combine(n, batch, Pbar[cur], nn, ep, st))) return rc;
-            cur = -1;
+            if ((rc = launch_combine(n, batch, pc, nn, ep, st))) return rc;
+            folded = true;
             break;
         }
         // Ybar += P_i^T Pbar_{i-1}
@@ -2346,24 +2344,25 @@ static mpps_status adjoint_tape_dev(const double* coeffs, int m, const char* tap
             Epilogue ep = epilogue_plain(Ybar, nn);
             ep.add = Ybar; ep.add_bstride = nn; ep.add_coef = 1.0;
             if (MPPS_FMT_IS_F64E(h.fmt_adj[i])) {   // P_i^T sliced from P_i's columns
-                if ((rc = product(h.fmt_adj[i], Pi, nn, Pbar[cur], nn, ep, nullptr, true))) return rc;
+                if ((rc = product(h.fmt_adj[i], Pi, nn, pc, nn, ep, nullptr, true))) return rc;
             } else {
                 if ((rc = launch_transpose(Pi, nn, T, n, batch, st))) return rc;
-                if ((rc = product(h.fmt_adj[i], T, nn, Pbar[cur], nn, ep))) return rc;
+                if ((rc = product(h.fmt_adj[i], T, nn, pc, nn, ep))) return rc;
             }
         }
         // Pbar_i = Pbar_{i-1} Y^T
+        double* pn = (i & 1) ? Pbar0 : Pbar1;
         {
-            Epilogue ep = epilogue_plain(Pbar[cur ^ 1], nn);
-            if ((rc = product(h.fmt_adj[i], Pbar[cur], nn, Yt, nn, ep, &sYt))) return rc;
+            Epilogue ep = epilogue_plain(pn, nn);
+            if ((rc = product(h.fmt_adj[i], pc, nn, Yt, nn, ep, &sYt))) return rc;
         }
-        cur ^= 1;
+        pc = pn;
     }
-    if (cur >= 0) {   // not folded: Bbar_r = Pbar_r, B_r = sum_{j<=m-sr} b_{sr+j} X_j
+    if (!folded) {   // Bbar_r = Pbar_r, B_r = sum_{j<=m-sr} b_{sr+j} X_j
         double c[MPPS_MAX_S + 1];
         const int t = m - s * r;
         for (int j = 0; j <= t; ++j) c[j] = coeffs[s * r + j];
-        if ((rc = launch_axpy_blocks(xbar, pw_bs, n, batch, t, c, Pbar[cur], nn, st))) return rc;
+        if ((rc = launch_axpy_blocks(xbar, pw_bs, n, batch, t, c, pc, nn, st))) return rc;
     }
     // Xbar_s += Ybar
     {
