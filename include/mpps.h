@@ -423,7 +423,8 @@ mpps_status mpps_matmul_ta(const double* A, const double* B, double* C, int n, i
  * can synchronise the device and take unbounded time, and plug-ins that are handed their
  * buffers and are not allowed to own device memory.  This entry point calls no cudaMalloc,
  * cudaFree or other allocating routine: the scratch the tensor-core product needs (rounded
- * operand copies, per-matrix scales, an error word) lives in one fixed device array of
+ * operand copies, their power-of-two scales or FP8 block-scale codes, an error word) lives in
+ * one fixed device array of
  * MPPS_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that loads the library
  * holds until the process exits.
  *   A, B, C : device pointers only (host pointers give MPPS_EINVAL); batch x n x n FP64,
