@@ -54,6 +54,16 @@ def test_invalid_arguments_rejected_without_gpu(mpps):
     assert e.value.status == 1
     with pytest.raises(mpps.MppsError):
         mpps.plan(16, 0, [1.0] * 5, 1.0)
+    # the products reject a bad format or a null matrix before any GPU work, and do nothing
+    # for an empty batch
+    L = mpps.lib()
+    for f in (L.mpps_matmul, L.mpps_matmul_ta):
+        assert f(None, None, None, 8, 1, 7, None) == 1
+        assert f(None, None, None, 8, 1, 0, None) == 1
+        assert f(None, None, None, 0, 1, 0, None) == 1
+        assert f(None, None, None, 8, 0, 0, None) == 0
+    assert L.mpps_matmul_ta(None, None, None, 8, 1, 7, None) == 1
+    assert b"mpps_matmul_ta" in L.mpps_last_error()
 
 
 def _rand_case(rng):
