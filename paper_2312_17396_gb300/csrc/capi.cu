@@ -1381,13 +1381,13 @@ static mpps_status eval_device(const double* coeffs, int m, const double* dA, in
                 // with the recorded maxima only the matrices of this step's list are sliced
                 const int* lk = d_lists + (size_t)k * batch;
                 const int* gk = d_counts ? d_counts + k : nullptr;
-                rc = have ? launch_slice_rows_pre(Pbuf[k & 1], nn, n, counts[k], K, slA, eA,
-                                                  mx_sq_row(k), nullptr, st, gk, lk)
-                          : launch_slice_rows(Pbuf[k & 1], nn, n, batch, K, slA, eA, st);
-                if (!rc)
-                    rc = have ? launch_slice_cols_pre(Pbuf[k & 1], nn, n, counts[k], K, slB, eB,
-                                                      mx_sq_col(k), st, gk, lk)
-                              : slice_cols(Pbuf[k & 1], nn, K, slB, eB);
+                if (have)   // rows and columns of Q_k from one read
+                    rc = launch_slice_both_pre(Pbuf[k & 1], nn, n, counts[k], K, slA, eA,
+                                               mx_sq_row(k), slB, eB, mx_sq_col(k), st, gk, lk);
+                else {
+                    rc = launch_slice_rows(Pbuf[k & 1], nn, n, batch, K, slA, eA, st);
+                    if (!rc) rc = slice_cols(Pbuf[k & 1], nn, K, slB, eB);
+                }
                 if (!rc)
                     rc = launch_gemm_f64e(K, slA, K, eA, slB, K, eB, n, counts[k], batch, ep, d_err,
                                           st, d_lists + (size_t)k * batch, split);

@@ -402,6 +402,12 @@ mpps_status launch_slice_rows_pre(const double* M, long long bs, int n, int batc
 mpps_status launch_slice_cols_pre(const double* M, long long bs, int n, int batch, int k,
                                   void* planes, int* exps, const int* cmax, cudaStream_t st,
                                   const int* gate = nullptr, const int* list = nullptr);
+// Both of the above from one read of M (the operands of M M): rows into planesA with the
+// recorded row codes rcodes, columns into planesB with the column codes ccodes.
+mpps_status launch_slice_both_pre(const double* M, long long bs, int n, int batch, int k,
+                                  void* planesA, int* expsA, const int* rcodes, void* planesB,
+                                  int* expsB, const int* ccodes, cudaStream_t st,
+                                  const int* gate = nullptr, const int* list = nullptr);
 // Scratch that lets the emulated product split the K range of output tiles between CTAs
 // (f64e_split_bytes() bytes, 256-byte aligned; its first f64e_split_flag_bytes() bytes
 // zeroed by the caller before the first product that uses it, on the same stream).  Without

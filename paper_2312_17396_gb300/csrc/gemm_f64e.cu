@@ -572,6 +572,73 @@ __global__ void __launch_bounds__(256) k_slice_cols(const double* __restrict__ M
     }
 }
 
+// Both operands of a squaring Q Q from one read of Q: the rows of Q in the A operand's pair
+// layout (exponents from the recorded row codes) and its columns as the rows of the B^T planes
+// (from the column codes).  64 x 32 tiles (32 x 8 threads) staged in shared memory; the B part
+// is k_slice_cols's, the A part takes each tile row in pairs of columns (K positions up to n32:
+// the tiles cover them, with zeros past n).  bidx: the listed matrices (planes, exponents and
+// codes indexed by the matrix).
+template <int KS>
+__global__ void __launch_bounds__(256) k_slice_both_pre(const double* __restrict__ M, long long bs,
+                                                        int n, long long goff,
+                                                        const int* __restrict__ rcodes,
+                                                        const int* __restrict__ ccodes,
+                                                        __nv_bfloat16* __restrict__ planesA,
+                                                        long long plane_bsA,
+                                                        __nv_bfloat16* __restrict__ planesB,
+                                                        long long plane_bsB, int lld,
+                                                        int* __restrict__ expsA,
+                                                        int* __restrict__ expsB,
+                                                        const int* __restrict__ gate,
+                                                        const int* __restrict__ bidx) {
+    pdl_wait();
+    if (gate && (int)blockIdx.z >= __ldg(gate)) return;   // device plan: not run
+    pdl_trigger();
+    __shared__ double tile[32][65];
+    const int b = bidx ? __ldg(bidx + blockIdx.z) : (int)blockIdx.z;   // listed matrices only
+    const int r0 = blockIdx.y * 64, c0 = blockIdx.x * 32;
+    const double* src = M + (long long)b * bs;
+    for (int i = threadIdx.y; i < 64; i += blockDim.y) {
+        const int row = r0 + i, col = c0 + threadIdx.x;
+        tile[threadIdx.x][i] = (row < n && col < n) ? src[(long long)row * n + col] : 0.0;
+    }
+    __syncthreads();
+    // B^T planes: plane row col, K positions k0 and k0 + 1 (rows of Q)
+    {
+        const long long pstride = (long long)n * lld;
+        for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+            const int col = c0 + i, k0 = r0 + 2 * threadIdx.x;
+            if (col >= n || k0 >= n) continue;
+            const int e = exp_from_code(ccodes[(long long)b * n + col]);
+            if (blockIdx.y == 0 && threadIdx.x == 0) expsB[(long long)b * n + col] = e;
+            const long long G0 = scaled_int_fp64(tile[i][2 * threadIdx.x], e) + goff;
+            const long long G1 = scaled_int_fp64(tile[i][2 * threadIdx.x + 1], e) + goff;
+            unsigned* dst = reinterpret_cast<unsigned*>(planesB + (long long)b * plane_bsB +
+                                                        (long long)col * lld + k0);
+#pragma unroll
+            for (int t = 0; t < KS; ++t) dst[(long long)t * (pstride / 2)] = digit_pair(G0, G1, t);
+        }
+    }
+    // A pair layout: row r0 + rho, K positions c and c + 1 (columns of Q), c = c0 + 2 pi
+    {
+        const long long pstride = (long long)n * 2 * lld;
+        const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+        for (int item = tid; item < 64 * 16; item += blockDim.x * blockDim.y) {
+            const int rho = item >> 4, pi = item & 15;
+            const int row = r0 + rho, c = c0 + 2 * pi;
+            if (row >= n) continue;
+            const int e = exp_from_code(rcodes[(long long)b * n + row]);
+            if (blockIdx.x == 0 && pi == 0) expsA[(long long)b * n + row] = e;
+            const long long G0 = scaled_int_fp64(tile[2 * pi][rho], e) + goff;
+            const long long G1 = scaled_int_fp64(tile[2 * pi + 1][rho], e) + goff;   // 0 past n
+            __nv_bfloat16* dst = planesA + (long long)b * plane_bsA + (long long)row * 2 * lld + kpos(c);
+#pragma unroll
+            for (int t = 0; t < KS; ++t)
+                *reinterpret_cast<unsigned*>(dst + slice_off(t, pstride)) = digit_pair(G0, G1, t);
+        }
+    }
+}
+
 // Slices of M's columns in the A operand's pair layout (plane row c = column c of M): the A
 // operand M^T without forming the transpose.  e_c from colmax; the K positions n .. n32 get
 // zero digits, as the row slicers write them.  64 x 32 transposing tiles (32 x 8 threads),
@@ -1497,6 +1564,37 @@ mpps_status launch_slice_rows_pre(const double* M, long long bs, int n, int batc
         case 7: return slice_rows_pre_k<7>(M, bs, n, batch, pl, exps, rmax, rmax_clear, st, gate, list);
         default: return slice_rows_pre_k<8>(M, bs, n, batch, pl, exps, rmax, rmax_clear, st, gate, list);
     }
+}
+
+mpps_status launch_slice_both_pre(const double* M, long long bs, int n, int batch, int k,
+                                  void* planesA, int* expsA, const int* rcodes, void* planesB,
+                                  int* expsB, const int* ccodes, cudaStream_t st, const int* gate,
+                                  const int* list) {
+    k = f64e_planes(k);
+    ProfScope prof(MPPS_PROF_SLICE, st);
+    if (batch > 65535 || n > 65535 * 64) {
+        set_error("slice_both: batch %d or n %d exceeds the grid limit", batch, n);
+        return MPPS_EINVAL;
+    }
+    if (batch == 0) return MPPS_OK;
+    const int lld = low_ld(n);
+    __nv_bfloat16* pa = (__nv_bfloat16*)planesA;
+    __nv_bfloat16* pb = (__nv_bfloat16*)planesB;
+    const dim3 g((n + 31) / 32, (n + 63) / 64, batch);
+#define MPPS_SB_CASE(KS)                                                                            \
+    case KS:                                                                                        \
+        MPPS_CUDA_TRY(launch_pdl(k_slice_both_pre<KS>, g, dim3(32, 8), 0, st, M, bs, n, digit_offset(KS), \
+                                 rcodes, ccodes, pa, (long long)num_pairs(KS) * n * 2 * lld, pb,     \
+                                 (long long)KS * n * lld, lld, expsA, expsB, gate, list));           \
+        break;
+    switch (k) {
+        MPPS_SB_CASE(1) MPPS_SB_CASE(2) MPPS_SB_CASE(3) MPPS_SB_CASE(4)
+        MPPS_SB_CASE(5) MPPS_SB_CASE(6) MPPS_SB_CASE(7)
+        default: MPPS_SB_CASE(8)
+    }
+#undef MPPS_SB_CASE
+    MPPS_LAUNCH_CHECK();
+    return MPPS_OK;
 }
 
 mpps_status launch_slice_cols_pre(const double* M, long long bs, int n, int batch, int k,
